@@ -1,0 +1,80 @@
+/*
+ * FP64 CPU oracle of the multi-detection GLMB update (arXiv 2512.06230,
+ * Section 3).  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the
+ * benchmark's CPU-baseline leg call it; the library never does.  It shares
+ * no code, header or constant with the CUDA path.
+ *
+ * Readings of the paper that this oracle fixes (the paper prints no
+ * formula for them) are stated at each function in glmb_oracle.c.
+ */
+#ifndef GLMB_ORACLE_H
+#define GLMB_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t dim_x, dim_z;          /* 4/2 or 6/3 constant velocity, positions measured */
+  double dt, q;                  /* frame period, white-acceleration PSD */
+  double R[9];                   /* dim_z x dim_z detection covariance, row-major */
+  double p_s, p_d, lambda_d;     /* survival, detection, extra-detection Poisson mean */
+  double clutter_rate, volume;   /* kappa = clutter_rate / volume */
+  double gate;                   /* Mahalanobis gate on d^2 (INFINITY = off) */
+  int32_t h_max, h_up;           /* retained hypotheses, draws per parent */
+  double tau;                    /* weight threshold */
+  uint64_t seed;
+  int32_t score_mode;            /* 0 joint likelihood, 1 product of C entries */
+  int32_t n_threads;             /* OpenMP threads over parents (<=0: 1) */
+} orc_config;
+
+typedef struct {
+  double r;
+  double mean[6];
+  double cov[36];                /* dim_x x dim_x row-major in the first dim_x^2 */
+} orc_birth;
+
+typedef struct orc_filter orc_filter;
+
+orc_filter* orc_create(const orc_config* cfg);
+void orc_destroy(orc_filter* f);
+void orc_reset(orc_filter* f);
+int orc_import(orc_filter* f, int frame, int H, const double* logw, const uint64_t* uid,
+               const int32_t* n_tracks, const uint32_t* lk, const uint32_t* lb,
+               const double* mean, const double* cov);
+int orc_export_counts(const orc_filter* f, int* H, int* n_total, int* frame);
+int orc_export(const orc_filter* f, double* logw, uint64_t* uid, int32_t* n_tracks,
+               uint32_t* lk, uint32_t* lb, double* mean, double* cov);
+
+int orc_predict(orc_filter* f, const orc_birth* births, int n_births);
+int orc_update(orc_filter* f, const float* Z, int M);
+int orc_prune(orc_filter* f);
+
+/* introspection of the last predict/update/prune */
+int orc_num_parents(const orc_filter* f);
+int orc_parent_slots(const orc_filter* f, int h);
+int orc_slot(const orc_filter* f, int h, int t, uint32_t* lk, uint32_t* lb, double* mean,
+             double* cov, double* p, double* dprob, double* logdetS);
+int orc_pair(const orc_filter* f, int h, int t, int i, double* d2, double* logC, double* e,
+             double* q);
+double orc_gate_margin(const orc_filter* f, int h);
+int orc_children(const orc_filter* f, int8_t* status, double* logw, double* margin,
+                 int32_t* n_alive, uint64_t* uid);
+int orc_child(const orc_filter* f, int h, int n, uint8_t* dead, uint16_t* theta);
+int orc_kept(const orc_filter* f, int64_t* idx, double* logw_norm, double* lse_all);
+int orc_kept_theta(const orc_filter* f, uint16_t* theta);
+int orc_estimates(const orc_filter* f, int cap, int* n_out, uint32_t* lk, uint32_t* lb,
+                  double* mean, double* cov, double* r, double* pmf, int pmf_cap,
+                  int* map_index);
+int orc_meas_assoc(const orc_filter* f, double* r_u);
+int orc_bruteforce(const orc_filter* f, int h, int cap, uint8_t* dead, uint16_t* theta,
+                   double* logw);
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+uint64_t orc_mix64(uint64_t x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,238 @@
+"""Seeded synthetic multi-object scenes: the one input source shared by the
+FP64 oracle and the CUDA path.
+
+This module draws ground truth, detections, clutter and the per-frame LMB
+birth sets.  It holds none of the filter's arithmetic (no prediction, no
+likelihood, no association): it only samples the *world* that the filter
+observes, so both implementations can be fed identical inputs.
+
+Model of the world (one reading per item, the paper is silent on these
+details for the Gaussian form):
+
+* Objects move with a constant-velocity model driven by continuous white
+  acceleration noise of power spectral density ``q`` (per axis, per frame of
+  length ``dt``).  State order is ``[positions..., velocities...]``.
+* Each frame an existing object survives with probability ``p_s``.
+* A live object is detected with probability ``p_d``; a detected object
+  yields ``1 + Poisson(lambda_d)`` i.i.d. position detections with noise
+  ``N(0, sigma^2 I)`` (the multi-detection model of Section 3 of the paper;
+  the paper's convoy experiment fixes the count at ``D`` instead).
+* Clutter is Poisson(``clutter_rate``) per frame, uniform over the region.
+* Detections of a frame are shuffled (the paper notes the update does not
+  depend on their order, Section 4.1).
+* Births: the LMB birth set of a frame holds one component per object that
+  appears in that frame (centred on its true position plus N(0, (2 sigma)^2)
+  noise, zero velocity, existence ``r_birth``) and Poisson(``false_births``)
+  spurious components uniform over the region (existence ``r_false``).
+
+Seeds: ``scene_seed = 1000 * cfg + rep`` by convention, filter seed
+``scene_seed ^ 0x5eed``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+__all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene",
+           "random_state", "chi2_gate"]
+
+
+@dataclasses.dataclass(frozen=True)
+class SceneParams:
+    name: str
+    dim: int                    # spatial dimension (2 or 3); state is 2*dim
+    n_objects: int
+    frames: int
+    extent: float               # region is [0, extent]^dim
+    dt: float = 1.0
+    q: float = 1.0              # white-acceleration PSD [m^2/s^3]
+    sigma: float = 5.0          # detection noise std [m]
+    p_s: float = 0.99
+    p_d: float = 0.9
+    lambda_d: float = 1.0       # detected object yields 1+Poisson(lambda_d)
+    clutter_rate: float = 5.0
+    birth_window: Optional[Tuple[int, int]] = (0, 24)   # birth frame ~ U{lo..hi}
+    births_per_frame: float = 0.0   # extra Poisson births per frame (sweep scenes)
+    speed_max: float = 10.0
+    r_birth: float = 0.5
+    r_false: float = 0.05
+    false_births: float = 1.0
+    birth_vel_std: float = 10.0
+    h_max: int = 100
+    h_up: int = 100
+    tau: float = 1e-5
+
+
+# Scene presets.  "tiny" and "mid" are the 2-D constant-velocity scenes with
+# 10 and 100 objects; "sweep_N<n>" are the 3-D scalability scenes.
+PRESETS = {
+    "tiny": SceneParams(name="tiny", dim=2, n_objects=10, frames=50, extent=1000.0,
+                        lambda_d=1.0, clutter_rate=5.0, birth_window=(0, 24),
+                        h_max=100),
+    "mid": SceneParams(name="mid", dim=2, n_objects=100, frames=100, extent=1000.0,
+                       lambda_d=1.5, clutter_rate=20.0, birth_window=(0, 49),
+                       h_max=1000),
+}
+for _n in (50, 200, 500, 1000):
+    PRESETS[f"sweep_N{_n}"] = SceneParams(
+        name=f"sweep_N{_n}", dim=3, n_objects=_n, frames=50, extent=5000.0,
+        p_d=0.85, lambda_d=2.0, clutter_rate=50.0, birth_window=None,
+        births_per_frame=0.01 * _n, h_max=1000)
+
+
+def preset(name: str, **overrides) -> SceneParams:
+    return dataclasses.replace(PRESETS[name], **overrides)
+
+
+def chi2_gate(dim_z: int, tail: float = 1e-4) -> float:
+    """Mahalanobis gate G: the chi-square(dim_z) quantile at 1 - tail."""
+    from scipy.stats import chi2
+    return float(chi2.isf(tail, dim_z))
+
+
+@dataclasses.dataclass
+class Frame:
+    Z: np.ndarray                 # (M, dim) float32, shuffled
+    births: List[Tuple[float, np.ndarray, np.ndarray]]   # (r, mean (2dim,), cov (2dim,2dim)) float64
+    truth: np.ndarray             # (n_alive, 2dim) float64
+    truth_ids: np.ndarray         # (n_alive,) int
+
+
+@dataclasses.dataclass
+class Scene:
+    params: SceneParams
+    seed: int
+    frames: List[Frame]
+
+    @property
+    def dim_x(self) -> int:
+        return 2 * self.params.dim
+
+    @property
+    def dim_z(self) -> int:
+        return self.params.dim
+
+    def filter_config(self, **overrides) -> dict:
+        """Model parameters of the world, as the filter's configuration."""
+        p = self.params
+        cfg = dict(dim_x=2 * p.dim, dim_z=p.dim, dt=float(np.float32(p.dt)), q=p.q,
+                   R=(p.sigma ** 2 * np.eye(p.dim)).tolist(), p_s=p.p_s, p_d=p.p_d,
+                   lambda_d=p.lambda_d, clutter_rate=p.clutter_rate,
+                   volume=p.extent ** p.dim, gate=chi2_gate(p.dim),
+                   h_max=p.h_max, h_up=p.h_up, tau=p.tau,
+                   seed=(self.seed ^ 0x5EED) & ((1 << 64) - 1), score_mode=0)
+        cfg.update(overrides)
+        return cfg
+
+
+def _cv_matrices(dim: int, dt: float, q: float):
+    """Transition and process-noise covariance used only to *simulate* truth."""
+    I = np.eye(dim)
+    F = np.block([[I, dt * I], [np.zeros((dim, dim)), I]])
+    Q = q * np.block([[dt ** 3 / 3 * I, dt ** 2 / 2 * I], [dt ** 2 / 2 * I, dt * I]])
+    return F, Q
+
+
+def _random_velocity(rng, dim, speed_max):
+    speed = rng.uniform(0.0, speed_max)
+    d = rng.normal(size=dim)
+    d /= np.linalg.norm(d)
+    return speed * d
+
+
+def make_scene(params: SceneParams, seed: int) -> Scene:
+    """Draw a full scene (truth, detections, clutter, births) from ``seed``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = params
+    dim = p.dim
+    F, Q = _cv_matrices(dim, p.dt, p.q)
+    Lq = np.linalg.cholesky(Q + 1e-12 * np.eye(2 * dim))
+
+    # birth frames
+    if p.birth_window is not None:
+        lo, hi = p.birth_window
+        t_birth = [int(rng.integers(lo, hi + 1)) for _ in range(p.n_objects)]
+    else:
+        t_birth = [0] * p.n_objects
+        for f in range(1, p.frames):
+            t_birth += [f] * int(rng.poisson(p.births_per_frame))
+    n_total = len(t_birth)
+
+    alive = {}          # id -> state
+    dead = set()
+    next_id = 0
+    order = sorted(range(n_total), key=lambda j: t_birth[j])
+    born_ptr = 0
+    frames: List[Frame] = []
+    sb = 2.0 * p.sigma
+    birth_cov = np.diag([sb ** 2] * dim + [p.birth_vel_std ** 2] * dim)
+    for f in range(p.frames):
+        # survival + motion of existing objects
+        for oid in sorted(alive):
+            if rng.uniform() >= p.p_s:
+                dead.add(oid)
+                del alive[oid]
+                continue
+            alive[oid] = F @ alive[oid] + Lq @ rng.normal(size=2 * dim)
+        # appearances
+        births = []
+        while born_ptr < n_total and t_birth[order[born_ptr]] == f:
+            pos = rng.uniform(0.0, p.extent, size=dim)
+            vel = _random_velocity(rng, dim, p.speed_max)
+            x = np.concatenate([pos, vel])
+            alive[next_id] = x
+            mean = np.concatenate([pos + rng.normal(scale=sb, size=dim), np.zeros(dim)])
+            births.append((p.r_birth, mean, birth_cov.copy()))
+            next_id += 1
+            born_ptr += 1
+        for _ in range(int(rng.poisson(p.false_births))):
+            mean = np.concatenate([rng.uniform(0.0, p.extent, size=dim), np.zeros(dim)])
+            births.append((p.r_false, mean, birth_cov.copy()))
+        # detections
+        Z = []
+        for oid in sorted(alive):
+            if rng.uniform() < p.p_d:
+                m = 1 + int(rng.poisson(p.lambda_d))
+                Z.append(alive[oid][:dim] + p.sigma * rng.normal(size=(m, dim)))
+        nc = int(rng.poisson(p.clutter_rate))
+        if nc:
+            Z.append(rng.uniform(0.0, p.extent, size=(nc, dim)))
+        Z = np.concatenate(Z, axis=0) if Z else np.zeros((0, dim))
+        Z = Z[rng.permutation(len(Z))].astype(np.float32)
+        ids = np.array(sorted(alive), dtype=np.int64)
+        truth = np.array([alive[i] for i in ids]) if len(ids) else np.zeros((0, 2 * dim))
+        frames.append(Frame(Z=Z, births=births, truth=truth, truth_ids=ids))
+    return Scene(params=p, seed=seed, frames=frames)
+
+
+def random_state(rng: np.random.Generator, dim: int, H: int, n_labels: int,
+                 extent: float, frame: int, keep: float = 0.8, spread: float = 5.0):
+    """A synthetic GLMB state: ``H`` hypotheses over ``n_labels`` labelled
+    tracks.  Each hypothesis keeps each label with probability ``keep`` and
+    carries its own jittered copy of the track density, so hypotheses share
+    labels but not means.  Returns plain arrays (log-weights normalised,
+    hypothesis uids, per-hypothesis track lists).
+    """
+    dx = 2 * dim
+    base = np.concatenate([rng.uniform(0, extent, size=(n_labels, dim)),
+                           rng.uniform(-8, 8, size=(n_labels, dim))], axis=1)
+    labels = [(int(rng.integers(0, max(frame, 1))), j) for j in range(n_labels)]
+    labels = sorted(set(labels))
+    n_labels = len(labels)
+    logw = rng.normal(scale=2.0, size=H)
+    logw -= np.log(np.sum(np.exp(logw - logw.max()))) + logw.max()
+    uids = rng.integers(0, 2 ** 63, size=H, dtype=np.int64).astype(np.uint64)
+    hyps = []
+    for h in range(H):
+        keep_mask = rng.uniform(size=n_labels) < keep
+        tr = []
+        for j in np.nonzero(keep_mask)[0]:
+            A = rng.normal(size=(dx, dx))
+            P = np.diag([spread ** 2] * dim + [2.0 ** 2] * dim) + 0.3 * A @ A.T
+            mean = base[j % len(base)] + rng.normal(scale=spread, size=dx) * 0.2
+            tr.append((labels[j][0], labels[j][1], mean, P))
+        hyps.append(tr)
+    return logw, uids, hyps
