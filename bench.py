@@ -1,0 +1,302 @@
+"""Throughput of the multi-detection GLMB update on one GB300.
+
+A step is one frame of the whole update (predict, compatibility table,
+death probabilities, child expansion and scoring, normalisation and top-H,
+track update, estimates) on a seeded synthetic scene: 2-D constant velocity,
+100 objects appearing over the first 50 frames, 100 frames, clutter
+Poisson(20), 1 + Poisson(1.5) detections per detected object, H_max = 1000,
+H_up = 100.  Steps walk through the scene's frames in order; the filter is
+reset when the scene restarts.
+
+value  frames/s with each frame's detections already in device memory.
+e2e    frames/s through the same C ABI with host buffers: detections copied
+       host->device and the estimates read back inside every step.
+Between steps a 256 MiB buffer is written to flush L2 (outside the timed
+events).  Under torchrun every rank runs its own independent scene (no
+collective on the data path); value is the frames of all ranks over the
+slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this method in this repository) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "GLMB update frames/sec & hypothesis-track updates/s vs N objects, H cap (1 GB300)"
+UNIT = "frames/s"
+INT_PEAK_NOTE = "152 SMs x 128 lanes x 2070 MHz"
+
+
+def scene_for_rank(args, rank):
+    p = scenes.preset(args.scene)
+    return scenes.make_scene(p, 1000 * 2 + rank if args.seed is None else args.seed + rank)
+
+
+def filter_cfg(sc):
+    n_max_births = max(len(f.births) for f in sc.frames)
+    cfg = sc.filter_config(max_meas=max(64, max(len(f.Z) for f in sc.frames) + 16),
+                           max_births=max(8, n_max_births),
+                           max_tracks=sc.params.n_objects * 2 + n_max_births + 64)
+    return cfg
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+           "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    def reader():
+        for line in p.stdout:
+            out.append(line.strip())
+    t = threading.Thread(target=reader, daemon=True)
+    t.start()
+    stop.wait()
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    t.join(timeout=2)
+
+
+def summarize_clocks(lines, dev):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9 or f[0] != str(dev):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def run_oracle(args, sc, cfg, budget_s):
+    """FP64 oracle over the scene's frames from the initial GLMB, all host
+    threads, until the scene ends or the time budget is spent."""
+    import oracle
+    threads = os.cpu_count() or 1
+    o = oracle.Oracle(cfg, n_threads=threads)
+    t0 = time.perf_counter()
+    n = 0
+    for fr in sc.frames:
+        o.step(fr.births, fr.Z)
+        o.estimates()
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, threads, f"{args.scene} scene frames 0..{n - 1} of {len(sc.frames)} " \
+        f"from the initial GLMB ({dt:.1f} s, {threads} threads)"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scene", default="mid")
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--stages", action="store_true", help="also report per-stage times")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sc = scene_for_rank(args, 0)
+        cfg = filter_cfg(sc)
+        v, threads, sample = run_oracle(args, sc, cfg, min(args.cpu_budget, 20.0 + 2 * args.steps))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": f"{args.scene} scene", "scene": args.scene},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2512_06230_gb300 as glmb
+    if rank == 0:
+        glmb.build()
+    if world > 1:
+        torch.distributed.barrier()
+    glmb.load()
+
+    sc = scene_for_rank(args, rank)
+    cfg = filter_cfg(sc)
+    F = len(sc.frames)
+    stream = torch.cuda.current_stream(dev)
+    f = glmb.Filter(cfg, stream=stream.cuda_stream)
+    Zdev = [torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
+            for fr in sc.frames]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    h_up = cfg["h_up"]
+
+    def run(n_steps, start, host, profile=False, record=None):
+        """Runs n_steps frames starting at global step index `start`; returns
+        per-step event times (ms) and per-step work counters."""
+        times, work = [], []
+        if profile:
+            f.set_profiling(["expand"])
+        for s in range(start, start + n_steps):
+            fi = s % F
+            fr = sc.frames[fi]
+            if not args.no_flush:
+                flush.zero_()
+            info0 = f.info() if fi != 0 else None
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if fi == 0:
+                f.reset()
+            f.predict(fr.births)
+            if host:
+                f.update(fr.Z)
+            else:
+                f.update(Zdev[fi], device=True)
+            f.prune()
+            est = f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            info = f.info()
+            H_par = 1 if info0 is None else info0["n_hyp"]
+            E_par = 0 if info0 is None else info0["n_entries"]
+            M = len(fr.Z)
+            work.append(dict(entries=info["n_entries"], n_est=est["n"], M=M,
+                             draws=h_up * (E_par + H_par * (len(fr.births) + M)),
+                             h2d=fr.Z.nbytes + len(fr.births) * 43 * 8,
+                             d2h=est["n"] * 352 + 64 * 8))
+        return times, work
+
+    # warm-up, then the timed steps
+    run(args.warmup, 0, host=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk_lines, stop = [], threading.Event()
+    th = threading.Thread(target=sample_clocks, args=(stop, clk_lines), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    launches0 = f.info()["n_launches"]
+    torch.cuda.synchronize()
+    times, work = run(args.steps, args.warmup, host=False, profile=True)
+    torch.cuda.synchronize()
+    launches = f.info()["n_launches"] - launches0
+    tim = f.timing()
+    stop.set()
+    th.join(timeout=10)
+    f.set_profiling([])
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    # end to end through the host-buffer path
+    times_h, work_h = run(args.steps, args.warmup, host=True)
+    total_h = float(sum(times_h))
+    if world > 1:
+        t = torch.tensor([total_h], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_h = float(t.item())
+    stage = None
+    if args.stages:
+        f.set_profiling(list(glmb.Filter.STAGES))
+        run(args.steps, args.warmup, host=False)
+        stage = {k: {"ms_per_step": v[0] / max(v[1], 1), "calls": v[1]} for k, v in f.timing().items()}
+        f.set_profiling([])
+
+    if rank != 0:
+        return
+    frames = args.steps * world
+    value = frames / (total_ms / 1000.0)
+    entries = sum(w["entries"] for w in work)
+    # roofline of the dominant kernel (child expansion): integer ALU work of
+    # the counter-based sampler, 100 32-bit operations per Philox4x32-10
+    # call and one call per four uniforms, one uniform per slot and per
+    # detection row of every child drawn
+    exp_ms, exp_calls = tim["expand"]
+    draws = sum(w["draws"] for w in work)
+    ops = 25.0 * draws
+    clocks = summarize_clocks(clk_lines, local)
+    peak_ops = 152 * 128 * 2070e6
+    achieved = ops / (exp_ms / 1000.0) if exp_ms > 0 else None
+    cpu_v, cpu_threads, cpu_sample = run_oracle(args, sc, cfg, args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.scene} scene: 2-D CV, {sc.params.n_objects} objects, "
+                               f"{F} frames, H_max={cfg['h_max']}, H_up={h_up}",
+                   "scene": args.scene, "h_max": cfg["h_max"], "h_up": h_up,
+                   "frames_per_scene": F, "l2": "flushed between steps (256 MiB write, outside "
+                   "the timed events)" if not args.no_flush else "not flushed",
+                   "inputs": "detections resident in device memory; births (<1 KB) copied in predict"},
+        "hypothesis_track_updates_per_s": entries * world / (total_ms / 1000.0),
+        "e2e": {"value": frames / (total_h / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": sum(w["h2d"] for w in work_h) / len(work_h),
+                "d2h_bytes_per_step": sum(w["d2h"] for w in work_h) / len(work_h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "expand_kernel (child expansion + scoring)",
+                     "achieved": achieved / 1e12 if achieved else None,
+                     "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",
+                     "frac": achieved / peak_ops if achieved else None, "traffic": None,
+                     "peak_source": INT_PEAK_NOTE,
+                     "kernel_ms_per_step": exp_ms / max(exp_calls, 1),
+                     "kernel_share_of_step": exp_ms / total_ms if total_ms else None},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                         "sample": cpu_sample},
+        "clocks": clocks,
+    }
+    if stage:
+        line["stages"] = stage
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * glmb.h - C ABI of the GB300 (sm_103a) multi-detection GLMB filter update.
+ *
+ * The method is the GLMB update of arXiv 2512.06230 ("GPU-GLMB"), Section 3:
+ * every predicted track is compared with every detection (compatibility
+ * matrix, Eq. 2), each retained hypothesis spawns H_up children by two-stage
+ * sampling (Bernoulli track deaths, then an independent categorical draw per
+ * detection row, possible because an object may yield several detections),
+ * each unique child is weighted by its parent's weight times the joint
+ * likelihood of its deaths and associations, and the set is truncated to the
+ * H_max heaviest hypotheses above a threshold tau and renormalised.  Track
+ * densities are Gaussian with a constant-velocity model (the paper uses
+ * particles with a turn-rate model; this library uses linear Gaussian
+ * tracks).
+ *
+ * Conventions shared by every call:
+ *  - All pointers are host pointers unless the argument name says "device".
+ *    The caller owns every buffer it passes; the library copies inputs
+ *    before the call returns and writes outputs only on GLMB_OK.
+ *  - The handle owns all device memory.  It is allocated once, in
+ *    glmb_create, from the capacities in glmb_config; no call allocates
+ *    device memory afterwards.
+ *  - Work is issued on glmb_config.stream (a cudaStream_t; NULL means a
+ *    stream owned by the handle).  Calls that return sizes or host data
+ *    synchronise that stream; glmb_predict and glmb_update do not return
+ *    until their inputs have been copied.
+ *  - Call order per frame: glmb_predict -> glmb_update -> glmb_prune ->
+ *    any number of glmb_estimates / glmb_meas_assoc / glmb_get_* calls.
+ *    A call out of order returns GLMB_E_STATE and changes nothing.
+ *  - No call throws or aborts.  On error the status is returned and a
+ *    message is kept for glmb_last_error.  A failed glmb_update or
+ *    glmb_prune leaves the filter state of the previous frame intact
+ *    (call glmb_predict again to retry a frame).
+ *  - Labels are (birth frame, birth index) pairs; they are unique within a
+ *    hypothesis and persist across frames (Section 3).
+ */
+#ifndef GLMB_H
+#define GLMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GLMB_OK = 0,
+  GLMB_E_INVALID = 1,   /* bad argument: null pointer, NaN/Inf input, bad size */
+  GLMB_E_OOM = 2,       /* device or host allocation failed in glmb_create */
+  GLMB_E_CAPACITY = 3,  /* a size exceeds a capacity fixed at glmb_create */
+  GLMB_E_CUDA = 4,      /* a CUDA runtime call failed */
+  GLMB_E_NUMERIC = 5,   /* no child has a finite weight, or a covariance lost definiteness */
+  GLMB_E_STATE = 6,     /* call out of order, or a malformed state buffer */
+  GLMB_E_TIMEOUT = 7    /* a bounded device-side wait ran out */
+} glmb_status;
+
+typedef struct glmb_handle glmb_handle;
+
+/* Filter configuration (Section 3 model terms; Section 4.1 tracker
+ * parameters H_max, H_up, tau). */
+typedef struct {
+  int32_t dim_x, dim_z;     /* 4/2 (2-D) or 6/3 (3-D) constant velocity; state
+                               [positions, velocities], positions measured */
+  float dt;                 /* frame period [s] */
+  double q;                 /* white-acceleration power spectral density */
+  double R[9];              /* dim_z x dim_z detection covariance, row-major, SPD */
+  double p_s;               /* survival probability per frame */
+  double p_d;               /* detection probability */
+  double lambda_d;          /* a detected object yields 1 + Poisson(lambda_d) detections */
+  double clutter_rate;      /* mean clutter detections per frame */
+  double volume;            /* surveillance volume; kappa = clutter_rate / volume */
+  double gate;              /* Mahalanobis gate on d^2 (INFINITY disables gating) */
+  int32_t h_max;            /* hypotheses retained by glmb_prune */
+  int32_t h_up;             /* children sampled per hypothesis (<= 65535) */
+  double tau;               /* children with normalised weight < tau are dropped */
+  uint64_t seed;            /* key of the counter-based random numbers */
+  int32_t score_mode;       /* 0: joint likelihood of each track's detections */
+  int32_t max_tracks;       /* capacity: tracks per hypothesis incl. this frame's births */
+  int32_t max_meas;         /* capacity: detections per frame (<= 65535) */
+  int32_t max_births;       /* capacity: births per frame */
+  int64_t max_pairs;        /* capacity: gated (component, detection) pairs per frame;
+                               0 selects 16 per component */
+  void* stream;             /* cudaStream_t, or NULL */
+} glmb_config;
+
+/* An LMB birth component (Section 3): existence r, Gaussian density. */
+typedef struct {
+  double r;
+  double mean[6];           /* first dim_x entries used */
+  double cov[36];           /* dim_x x dim_x row-major in the first dim_x^2 entries */
+} glmb_birth;
+
+/* One estimated track. */
+typedef struct {
+  uint32_t label_k, label_b;
+  double r;                 /* existence: total weight of hypotheses holding the label */
+  double mean[6];
+  double cov[36];           /* dim_x x dim_x row-major */
+} glmb_track;
+
+/* Sizes of the current state and of the last frame's work. */
+typedef struct {
+  int32_t frame;            /* frames predicted so far */
+  int32_t n_hyp;            /* hypotheses */
+  int64_t n_entries;        /* sum over hypotheses of their track counts */
+  int32_t n_components;     /* distinct Gaussian components */
+  int32_t n_meas;           /* detections of the last update */
+  int64_t n_pairs;          /* gated pairs of the last update */
+  int64_t n_children;       /* children drawn by the last update (parents x h_up) */
+  int64_t n_unique;         /* unique children with finite weight */
+  int32_t n_updates;        /* distinct (component, detection set) track updates */
+  int32_t n_fp64_chol;      /* innovation covariances factorised in FP64 */
+  int64_t n_launches;       /* CUDA kernels launched by the library so far (all handles) */
+} glmb_info;
+
+/* Creates a filter holding the initial GLMB: one hypothesis with no tracks
+ * and weight one.  All device memory is allocated here from the capacities.
+ * Errors: GLMB_E_INVALID (bad model or capacity), GLMB_E_OOM, GLMB_E_CUDA. */
+glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out);
+
+/* Frees every resource of the handle.  Accepts NULL. */
+glmb_status glmb_destroy(glmb_handle* h);
+
+/* Returns the filter to the initial GLMB and frame 0. */
+glmb_status glmb_reset(glmb_handle* h);
+
+/* Prediction (Section 3): every track of every hypothesis is propagated with
+ * the CV model and kept with prior existence p_s (its death is sampled in
+ * glmb_update); the n_births birth components (host array, copied) are
+ * appended to every hypothesis with existence r and label (frame, index).
+ * Errors: GLMB_E_INVALID (r outside [0,1], NaN), GLMB_E_CAPACITY. */
+glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births);
+
+/* Update (Section 3, Eq. 2 and the two-stage sampling): Z holds M detections,
+ * M x dim_z row-major float32, in host memory (z_is_device = 0) or device
+ * memory on the handle's GPU (z_is_device = 1).  Builds the gated
+ * compatibility table, the posterior death probabilities, and the h_up
+ * children of each hypothesis with their exact log-weights; unique children
+ * stay on the device for glmb_prune.
+ * Errors: GLMB_E_STATE (no predict), GLMB_E_INVALID (M < 0, NaN/Inf in Z),
+ * GLMB_E_CAPACITY (M, pairs or per-hypothesis table beyond capacity). */
+glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device);
+
+/* Pruning (Section 3): normalises the children's weights over all unique
+ * children (FP64), drops those below tau, keeps the h_max heaviest (ties by
+ * parent then draw index), renormalises, and builds the new hypotheses with
+ * one Kalman update per distinct (component, detection set).
+ * Errors: GLMB_E_STATE, GLMB_E_NUMERIC (no child with finite weight),
+ * GLMB_E_CAPACITY (components or entries beyond capacity). */
+glmb_status glmb_prune(glmb_handle* h);
+
+/* Estimates: writes the tracks of the heaviest hypothesis among those with
+ * the most probable cardinality into out[0..n_out) (n_out <= cap), each with
+ * its existence r.  card_pmf (nullable) receives the cardinality
+ * distribution for n = 0..pmf_cap-1.  Synchronises.
+ * Errors: GLMB_E_INVALID, GLMB_E_CAPACITY (cap too small; n_out is set). */
+glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out,
+                           double* card_pmf, int pmf_cap);
+
+/* For each detection i of the last update, the total weight of retained
+ * hypotheses that assign it to clutter (r_u[i], i < M <= cap). Synchronises. */
+glmb_status glmb_meas_assoc(glmb_handle* h, double* r_u, int cap);
+
+/* Current sizes (synchronises). */
+glmb_status glmb_get_info(glmb_handle* h, glmb_info* info);
+
+/* State buffer (host memory), little-endian:
+ *   u32 magic 0x424D4C47 ('GLMB'), u32 version 1, i32 dim_x, i32 frame,
+ *   i32 n_hyp, i32 pad, i64 n_tracks_total;
+ *   per hypothesis: f64 logw, u64 uid, i32 n_tracks, i32 pad;
+ *   per track (hypotheses in order): u32 label_k, u32 label_b,
+ *     f64 mean[dim_x], f64 cov[dim_x * dim_x] (row-major).
+ * glmb_export_state writes it into buf (cap bytes) and sets *n_out; with
+ * buf == NULL it only sets *n_out.  glmb_import_state replaces the filter
+ * state; the next call must be glmb_predict.  Log-weights must be
+ * normalised.  Errors: GLMB_E_CAPACITY, GLMB_E_STATE (malformed buffer). */
+glmb_status glmb_export_state(glmb_handle* h, void* buf, size_t cap, size_t* n_out);
+glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n);
+
+/* Retained hypotheses after glmb_prune: logw[n_h], uid[n_h],
+ * hyp_ptr[n_h + 1] (offsets into the label arrays), label_k/label_b per
+ * track, and theta[n_h][M] (0 = clutter, j + 1 = the hypothesis's j-th
+ * track).  Any output pointer may be NULL.  Synchronises.
+ * Errors: GLMB_E_STATE, GLMB_E_CAPACITY (cap_h or cap_entries too small). */
+glmb_status glmb_get_hypotheses(glmb_handle* h, double* logw, uint64_t* uid, uint32_t* hyp_ptr,
+                                uint32_t* label_k, uint32_t* label_b, uint16_t* theta, int cap_h,
+                                int64_t cap_entries, int* n_h);
+
+/* Inspection of the last glmb_update, for checking each step on its own.
+ *
+ * glmb_get_parents: slot lists of the parents (the hypotheses before the
+ * update, in order), births included: ptr[n_parents + 1], comp[] (component
+ * index of each slot).
+ * glmb_get_components: the predicted components the update used: labels,
+ * mean (dim_x), cov (dim_x^2 row-major), existence prior p, posterior death
+ * probability dprob, log det S.
+ * glmb_get_pairs: the gated table, CSR by component: comp_ptr[n_comp + 1],
+ * meas[], logC[] (log of the Eq. 2 entry), q[] (e^T R^-1 e), e[] (dim_z per
+ * pair, e = z - H m).
+ * glmb_get_children: for each child (parent-major, h_up per parent): its
+ * unnormalised log-weight (FP64), status (0 zero weight, 1 unique,
+ * 2 duplicate of a lower draw) and number of surviving tracks.
+ * All synchronise; GLMB_E_STATE before the first update, GLMB_E_CAPACITY
+ * when a cap is too small (the needed size is still written). */
+glmb_status glmb_get_parents(glmb_handle* h, uint32_t* ptr, uint32_t* comp, int cap_parents,
+                             int64_t cap_slots, int* n_parents);
+glmb_status glmb_get_components(glmb_handle* h, uint32_t* label_k, uint32_t* label_b,
+                                double* mean, double* cov, double* p, double* dprob,
+                                double* logdetS, int cap, int* n_comp);
+glmb_status glmb_get_pairs(glmb_handle* h, uint32_t* comp_ptr, uint32_t* meas, float* logC,
+                           float* q, float* e, int cap_comp, int64_t cap_pairs, int64_t* n_pairs);
+glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint16_t* n_alive,
+                              int64_t cap, int64_t* n_children);
+
+/* Optional timing of the update's stages with CUDA events on the handle's
+ * stream.  stage_mask bit s enables stage s: 0 predict, 1 compatibility
+ * table and death probabilities, 2 child expansion and scoring, 3
+ * normalisation and top-H selection, 4 regeneration of retained children,
+ * 5 track update and component compaction, 6 estimates.  Setting the mask
+ * clears the totals.  glmb_get_timing returns, per stage, total milliseconds
+ * and the number of timed calls (n entries each; either pointer may be
+ * NULL); it synchronises. */
+glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask);
+glmb_status glmb_get_timing(glmb_handle* h, double* ms, long long* calls, int n);
+
+/* Message of the last error on this handle ("" if none). */
+const char* glmb_last_error(glmb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLMB_H */

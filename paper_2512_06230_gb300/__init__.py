@@ -1,0 +1,396 @@
+"""Python binding of the GB300 multi-detection GLMB update library.
+
+Thin ctypes marshalling over the C ABI declared in ``include/glmb.h``; every
+step of the filter runs in the library's CUDA kernels.  The library is
+built in-tree by :func:`build` (sm_103a only).  Importing this module never
+falls back to another implementation: if ``libglmb.so`` is missing,
+:class:`Filter` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import struct
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_HERE, "libglmb.so")
+HEADER = os.path.join(_ROOT, "include", "glmb.h")
+SOURCES = ["kernels_table.cu", "kernels_expand.cu", "kernels_prune.cu", "glmb_api.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
+
+STATUS = {0: "GLMB_OK", 1: "GLMB_E_INVALID", 2: "GLMB_E_OOM", 3: "GLMB_E_CAPACITY",
+          4: "GLMB_E_CUDA", 5: "GLMB_E_NUMERIC", 6: "GLMB_E_STATE", 7: "GLMB_E_TIMEOUT"}
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (one TU per process, in parallel)
+    and link ``libglmb.so`` next to this file."""
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)] + [HEADER]
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(_CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose and (r.stdout or r.stderr):
+            sys.stderr.write(r.stdout + r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp,
+                        *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# --------------------------------------------------------------------------
+# C structs (layouts of include/glmb.h)
+# --------------------------------------------------------------------------
+class GlmbConfig(C.Structure):
+    _fields_ = [("dim_x", C.c_int32), ("dim_z", C.c_int32), ("dt", C.c_float), ("q", C.c_double),
+                ("R", C.c_double * 9), ("p_s", C.c_double), ("p_d", C.c_double),
+                ("lambda_d", C.c_double), ("clutter_rate", C.c_double), ("volume", C.c_double),
+                ("gate", C.c_double), ("h_max", C.c_int32), ("h_up", C.c_int32), ("tau", C.c_double),
+                ("seed", C.c_uint64), ("score_mode", C.c_int32), ("max_tracks", C.c_int32),
+                ("max_meas", C.c_int32), ("max_births", C.c_int32), ("max_pairs", C.c_int64),
+                ("stream", C.c_void_p)]
+
+
+class GlmbBirth(C.Structure):
+    _fields_ = [("r", C.c_double), ("mean", C.c_double * 6), ("cov", C.c_double * 36)]
+
+
+class GlmbTrack(C.Structure):
+    _fields_ = [("label_k", C.c_uint32), ("label_b", C.c_uint32), ("r", C.c_double),
+                ("mean", C.c_double * 6), ("cov", C.c_double * 36)]
+
+
+class GlmbInfo(C.Structure):
+    _fields_ = [("frame", C.c_int32), ("n_hyp", C.c_int32), ("n_entries", C.c_int64),
+                ("n_components", C.c_int32), ("n_meas", C.c_int32), ("n_pairs", C.c_int64),
+                ("n_children", C.c_int64), ("n_unique", C.c_int64), ("n_updates", C.c_int32),
+                ("n_fp64_chol", C.c_int32), ("n_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def declared_functions() -> List[str]:
+    """Names of the entry points declared in include/glmb.h."""
+    import re
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:glmb_status|const char\*)\s+(glmb_\w+)\s*\(", text,
+                                 re.M)))
+
+
+def load() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libglmb.so is not built: run paper_2512_06230_gb300.build() "
+                           "(needs nvcc); there is no fallback implementation")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    I, L = C.c_int, C.c_int64
+    sig = {
+        "glmb_create": [P, P], "glmb_destroy": [P], "glmb_reset": [P],
+        "glmb_predict": [P, P, I], "glmb_update": [P, P, I, I], "glmb_prune": [P],
+        "glmb_estimates": [P, P, I, P, P, I], "glmb_meas_assoc": [P, P, I],
+        "glmb_get_info": [P, P], "glmb_export_state": [P, P, C.c_size_t, P],
+        "glmb_import_state": [P, P, C.c_size_t],
+        "glmb_get_hypotheses": [P, P, P, P, P, P, P, I, L, P],
+        "glmb_get_parents": [P, P, P, I, L, P],
+        "glmb_get_components": [P, P, P, P, P, P, P, P, I, P],
+        "glmb_get_pairs": [P, P, P, P, P, P, I, L, P],
+        "glmb_get_children": [P, P, P, P, L, P],
+        "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.glmb_last_error.argtypes = [P]
+    lib.glmb_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class GlmbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def make_config(cfg: dict, stream: Optional[int] = None) -> GlmbConfig:
+    c = GlmbConfig()
+    c.dim_x, c.dim_z = int(cfg["dim_x"]), int(cfg["dim_z"])
+    c.dt, c.q = float(cfg["dt"]), float(cfg["q"])
+    d = c.dim_z
+    R = np.asarray(cfg["R"], dtype=np.float64).reshape(d, d).ravel()
+    for i in range(d * d):
+        c.R[i] = R[i]
+    c.p_s, c.p_d, c.lambda_d = float(cfg["p_s"]), float(cfg["p_d"]), float(cfg["lambda_d"])
+    c.clutter_rate, c.volume, c.gate = float(cfg["clutter_rate"]), float(cfg["volume"]), float(cfg["gate"])
+    c.h_max, c.h_up, c.tau = int(cfg["h_max"]), int(cfg["h_up"]), float(cfg["tau"])
+    c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
+    c.score_mode = int(cfg.get("score_mode", 0))
+    c.max_tracks = int(cfg.get("max_tracks", 0))
+    c.max_meas = int(cfg.get("max_meas", 0))
+    c.max_births = int(cfg.get("max_births", 0))
+    c.max_pairs = int(cfg.get("max_pairs", 0))
+    c.stream = stream
+    return c
+
+
+def pack_state(frame: int, logw, uid, tracks, dim_x: int) -> bytes:
+    """State buffer of include/glmb.h from per-hypothesis track lists of
+    (label_k, label_b, mean, cov)."""
+    H = len(logw)
+    n = sum(len(t) for t in tracks)
+    out = [struct.pack("<IIiiiiq", 0x424D4C47, 1, dim_x, frame, H, 0, n)]
+    for h in range(H):
+        out.append(struct.pack("<dQii", float(logw[h]), int(uid[h]), len(tracks[h]), 0))
+    for tr in tracks:
+        for (k, b, m, P) in tr:
+            out.append(struct.pack("<II", int(k), int(b)))
+            out.append(np.asarray(m, dtype="<f8").reshape(dim_x).tobytes())
+            out.append(np.asarray(P, dtype="<f8").reshape(dim_x, dim_x).tobytes())
+    return b"".join(out)
+
+
+def unpack_state(buf: bytes):
+    magic, ver, dx, frame, H, _, n = struct.unpack_from("<IIiiiiq", buf, 0)
+    off = struct.calcsize("<IIiiiiq")
+    logw, uid, ntr = [], [], []
+    for _ in range(H):
+        lw, u, nt, _ = struct.unpack_from("<dQii", buf, off)
+        off += struct.calcsize("<dQii")
+        logw.append(lw)
+        uid.append(u)
+        ntr.append(nt)
+    tracks = []
+    for nt in ntr:
+        tr = []
+        for _ in range(nt):
+            k, b = struct.unpack_from("<II", buf, off)
+            off += 8
+            m = np.frombuffer(buf, "<f8", dx, off).copy()
+            off += 8 * dx
+            P = np.frombuffer(buf, "<f8", dx * dx, off).reshape(dx, dx).copy()
+            off += 8 * dx * dx
+            tr.append((k, b, m, P))
+        tracks.append(tr)
+    return frame, np.array(logw), np.array(uid, dtype=np.uint64), tracks
+
+
+class Filter:
+    """One GLMB filter on the current CUDA device (see include/glmb.h)."""
+
+    def __init__(self, cfg: dict, stream: Optional[int] = None):
+        self.lib = load()
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg, stream)
+        self.dx, self.dz = self._c.dim_x, self._c.dim_z
+        h = C.c_void_p()
+        st = self.lib.glmb_create(C.byref(self._c), C.byref(h))
+        if st != 0:
+            raise GlmbError(st, "glmb_create rejected the configuration")
+        self.h = h
+        self.M = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.glmb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise GlmbError(st, self.lib.glmb_last_error(self.h).decode())
+
+    # ---- filter steps ----
+    def reset(self):
+        self._check(self.lib.glmb_reset(self.h))
+
+    def predict(self, births: Sequence[Tuple[float, np.ndarray, np.ndarray]]):
+        arr = (GlmbBirth * max(1, len(births)))()
+        dx = self.dx
+        for j, (r, m, P) in enumerate(births):
+            arr[j].r = float(r)
+            mm = np.asarray(m, np.float64).reshape(dx)
+            PP = np.asarray(P, np.float64).reshape(dx * dx)
+            for a in range(dx):
+                arr[j].mean[a] = mm[a]
+            for a in range(dx * dx):
+                arr[j].cov[a] = PP[a]
+        self._check(self.lib.glmb_predict(self.h, C.cast(arr, C.c_void_p), len(births)))
+
+    def update(self, Z, device: bool = False):
+        if device:
+            # a CUDA tensor (torch) of shape (M, dim_z), float32, contiguous
+            M = int(Z.shape[0])
+            self.M = M
+            self._check(self.lib.glmb_update(self.h, C.c_void_p(Z.data_ptr()), M, 1))
+            return
+        Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
+        self.M = len(Zf)
+        self._check(self.lib.glmb_update(self.h, _ptr(Zf), len(Zf), 0))
+
+    def prune(self):
+        self._check(self.lib.glmb_prune(self.h))
+
+    def step(self, births, Z):
+        self.predict(births)
+        self.update(Z)
+        self.prune()
+
+    # ---- outputs ----
+    def estimates(self, cap: int = 4096, pmf_cap: int = 4096):
+        out = (GlmbTrack * cap)()
+        n = C.c_int()
+        pmf = np.zeros(pmf_cap)
+        self._check(self.lib.glmb_estimates(self.h, C.cast(out, C.c_void_p), cap, C.byref(n),
+                                            _ptr(pmf), pmf_cap))
+        k, dx = n.value, self.dx
+        mean = np.array([[out[j].mean[a] for a in range(dx)] for j in range(k)]).reshape(k, dx)
+        cov = np.array([[out[j].cov[a] for a in range(dx * dx)] for j in range(k)]).reshape(k, dx, dx)
+        return dict(n=k, labels=[(out[j].label_k, out[j].label_b) for j in range(k)],
+                    r=np.array([out[j].r for j in range(k)]), mean=mean, cov=cov, pmf=pmf)
+
+    STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")
+
+    def set_profiling(self, stages: Iterable[str] = ()):
+        mask = 0
+        for s in stages:
+            mask |= 1 << self.STAGES.index(s)
+        self._check(self.lib.glmb_set_profiling(self.h, mask))
+
+    def timing(self) -> dict:
+        n = len(self.STAGES)
+        ms = np.zeros(n)
+        calls = np.zeros(n, np.int64)
+        self._check(self.lib.glmb_get_timing(self.h, _ptr(ms), _ptr(calls), n))
+        return {s: (float(ms[i]), int(calls[i])) for i, s in enumerate(self.STAGES)}
+
+    def meas_assoc(self):
+        r = np.zeros(max(self.M, 1))
+        self._check(self.lib.glmb_meas_assoc(self.h, _ptr(r), len(r)))
+        return r[: self.M]
+
+    def info(self) -> dict:
+        inf = GlmbInfo()
+        self._check(self.lib.glmb_get_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in GlmbInfo._fields_}
+
+    def export_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self.lib.glmb_export_state(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.glmb_export_state(self.h, buf, n.value, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def import_state(self, buf: bytes):
+        self._check(self.lib.glmb_import_state(self.h, buf, len(buf)))
+
+    def hypotheses(self):
+        inf = self.info()
+        H, E = inf["n_hyp"], inf["n_entries"]
+        logw = np.zeros(H)
+        uid = np.zeros(H, np.uint64)
+        ptr = np.zeros(H + 1, np.uint32)
+        lk = np.zeros(max(E, 1), np.uint32)
+        lb = np.zeros(max(E, 1), np.uint32)
+        theta = np.zeros((H, max(self.M, 1)), np.uint16)
+        n = C.c_int()
+        self._check(self.lib.glmb_get_hypotheses(self.h, _ptr(logw), _ptr(uid), _ptr(ptr), _ptr(lk),
+                                                 _ptr(lb), _ptr(theta), H, max(E, 1), C.byref(n)))
+        return dict(logw=logw, uid=uid, ptr=ptr, label_k=lk[:E], label_b=lb[:E],
+                    theta=theta[:, : self.M])
+
+    def parents(self):
+        n = C.c_int()
+        self.lib.glmb_get_parents(self.h, None, None, 0, 0, C.byref(n))
+        H = n.value
+        cap = (H + 1) * (self._c.max_tracks or 256) + 16
+        ptr = np.zeros(H + 1, np.uint32)
+        comp = np.zeros(cap, np.uint32)
+        self._check(self.lib.glmb_get_parents(self.h, _ptr(ptr), _ptr(comp), H, cap, C.byref(n)))
+        return ptr, comp[: ptr[H]]
+
+    def components(self):
+        n = C.c_int()
+        self.lib.glmb_get_components(self.h, None, None, None, None, None, None, None, 0, C.byref(n))
+        T, dx = n.value, self.dx
+        lk = np.zeros(max(T, 1), np.uint32)
+        lb = np.zeros(max(T, 1), np.uint32)
+        mean = np.zeros((max(T, 1), dx))
+        cov = np.zeros((max(T, 1), dx, dx))
+        p = np.zeros(max(T, 1))
+        dp = np.zeros(max(T, 1))
+        ld = np.zeros(max(T, 1))
+        self._check(self.lib.glmb_get_components(self.h, _ptr(lk), _ptr(lb), _ptr(mean), _ptr(cov),
+                                                 _ptr(p), _ptr(dp), _ptr(ld), max(T, 1), C.byref(n)))
+        return dict(label_k=lk[:T], label_b=lb[:T], mean=mean[:T], cov=cov[:T], p=p[:T],
+                    dprob=dp[:T], logdetS=ld[:T])
+
+    def pairs(self):
+        T = self.components()["p"].shape[0]
+        K = C.c_int64()
+        self.lib.glmb_get_pairs(self.h, None, None, None, None, None, 0, 0, C.byref(K))
+        k = K.value
+        ptr = np.zeros(T + 1, np.uint32)
+        meas = np.zeros(max(k, 1), np.uint32)
+        logC = np.zeros(max(k, 1), np.float32)
+        q = np.zeros(max(k, 1), np.float32)
+        e = np.zeros((max(k, 1), self.dz), np.float32)
+        self._check(self.lib.glmb_get_pairs(self.h, _ptr(ptr), _ptr(meas), _ptr(logC), _ptr(q), _ptr(e),
+                                            T + 1, max(k, 1), C.byref(K)))
+        return dict(ptr=ptr, meas=meas[:k], logC=logC[:k], q=q[:k], e=e[:k])
+
+    def children(self):
+        n = C.c_int64()
+        self.lib.glmb_get_children(self.h, None, None, None, 0, C.byref(n))
+        k = n.value
+        logw = np.zeros(max(k, 1))
+        st = np.zeros(max(k, 1), np.int8)
+        na = np.zeros(max(k, 1), np.uint16)
+        self._check(self.lib.glmb_get_children(self.h, _ptr(logw), _ptr(st), _ptr(na), max(k, 1),
+                                               C.byref(n)))
+        return dict(logw=logw[:k], status=st[:k], n_alive=na[:k])

@@ -1,0 +1,1057 @@
+// C ABI of the multi-detection GLMB update (include/glmb.h): handle, device
+// memory (allocated once at create), per-frame orchestration of the kernels
+// on one stream, state import/export and inspection.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/glmb.h"
+#include "glmb_kernels.h"
+
+using namespace glmb;
+
+namespace {
+
+constexpr unsigned long long kGolden = 0x9E3779B97F4A7C15ULL;
+constexpr int kBirthRec = 43;  // r, mean[6], cov[36]
+
+// stages timed by glmb_set_profiling
+enum { kStagePredict = 0, kStageTable, kStageExpand, kStageSelect, kStageMat, kStageGc,
+       kStageEstimates, kNumStages };
+
+// device scalar slots
+enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_N = 16 };
+
+}  // namespace
+
+struct glmb_handle {
+  glmb_config cfg{};
+  Model md{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<void*> allocs;
+  std::vector<void*> host_allocs;
+  // capacities
+  int cap_h = 0, cap_meas = 0, cap_births = 0, max_tracks = 0;
+  long long cap_entries = 0, cap_comp = 0, cap_pairs = 0, cap_children = 0, cap_upd = 0;
+  uint32_t hmask = 0;
+  int smem_limit = 0, n_sm = 0;
+  // state (table A = comps[cur]) and working table (B)
+  CompTable comps[2];
+  int cur = 0;
+  int n_comp = 0;
+  HypTable hyps[2];
+  int hcur = 0;
+  int H = 1;
+  long long n_entries = 0;
+  int frame = 0;
+  int stage = 0;            // 0 ready for predict, 1 predicted, 2 updated
+  // last frame
+  int nb = 0, T_work = 0, M = 0, H_par = 0, par_buf = 0, birth_base = 0;
+  bool have_update = false, theta_M_valid = false;
+  int theta_M = 0;
+  double* d_births = nullptr;
+  double* h_births = nullptr;
+  float* d_Z = nullptr;
+  float* h_Z = nullptr;
+  PairTable pt{};
+  uint32_t* scan_tmp32 = nullptr;
+  long long* child_key = nullptr;
+  int8_t* child_status = nullptr;
+  uint16_t* child_alive = nullptr;
+  PruneWork pw{};
+  unsigned long long* hkeys = nullptr;
+  uint32_t* hvals = nullptr;
+  uint32_t* upd_src = nullptr;
+  uint32_t* upd_m = nullptr;
+  long long* upd_se = nullptr;
+  uint32_t* gc_flag = nullptr;
+  uint32_t* gc_newpos = nullptr;
+  unsigned* d_scal = nullptr;
+  unsigned* h_scal = nullptr;
+  double* d_pmf = nullptr;
+  int* d_nb = nullptr;
+  double* d_r = nullptr;
+  double* d_ru = nullptr;
+  glmb_track* d_tracks = nullptr;
+  glmb_track* h_tracks = nullptr;
+  // stage timing
+  unsigned prof_mask = 0;
+  cudaEvent_t ev[kNumStages][2] = {};
+  bool ev_pending[kNumStages] = {};
+  double stage_ms[kNumStages] = {};
+  long long stage_calls[kNumStages] = {};
+  // stats
+  long long n_pairs = 0, n_unique = 0;
+  int n_upd = 0, n_fp64 = 0;
+  int T_max = 0, K_max = 0;
+};
+
+namespace {
+
+// optional CUDA-event timing of the update's stages (glmb_set_profiling)
+void prof_begin(glmb_handle* h, int st);
+void prof_end(glmb_handle* h, int st);
+void prof_collect(glmb_handle* h);
+
+glmb_status fail(glmb_handle* h, glmb_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return st;
+}
+
+#define CU(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(h, GLMB_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+template <typename T>
+bool dalloc(glmb_handle* h, T** p, long long n) {
+  void* q = nullptr;
+  if (n <= 0) n = 1;
+  if (cudaMalloc(&q, (size_t)n * sizeof(T)) != cudaSuccess) return false;
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return true;
+}
+
+template <typename T>
+bool halloc(glmb_handle* h, T** p, long long n) {
+  void* q = nullptr;
+  if (n <= 0) n = 1;
+  if (cudaMallocHost(&q, (size_t)n * sizeof(T)) != cudaSuccess) return false;
+  h->host_allocs.push_back(q);
+  *p = (T*)q;
+  return true;
+}
+
+bool alloc_comps(glmb_handle* h, CompTable& c, long long cap, int dx) {
+  c.cap = (int)cap;
+  const int ncov = dx * (dx + 1) / 2;
+  return dalloc(h, &c.mhi, cap * dx) && dalloc(h, &c.mlo, cap * dx) &&
+         dalloc(h, &c.cov, cap * ncov) && dalloc(h, &c.lk, cap) && dalloc(h, &c.lb, cap) &&
+         dalloc(h, &c.logp, cap) && dalloc(h, &c.log1mp, cap);
+}
+
+bool alloc_hyps(glmb_handle* h, HypTable& y) {
+  return dalloc(h, &y.ptr, h->cap_h + 1) && dalloc(h, &y.comp, h->cap_entries) &&
+         dalloc(h, &y.logw, h->cap_h) && dalloc(h, &y.uid, h->cap_h) &&
+         dalloc(h, &y.theta, (long long)h->cap_h * h->cap_meas);
+}
+
+void free_all(glmb_handle* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->host_allocs) cudaFreeHost(p);
+  h->allocs.clear();
+  h->host_allocs.clear();
+}
+
+long long next_pow2(long long x) {
+  long long p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+bool spd_inverse(int n, const double* A, double* Ainv, double* logdet) {
+  double L[9] = {0};
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+    if (!(s > 0)) return false;
+    L[j * n + j] = std::sqrt(s);
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = t / L[j * n + j];
+    }
+  }
+  *logdet = 0;
+  for (int i = 0; i < n; ++i) *logdet += 2 * std::log(L[i * n + i]);
+  for (int c = 0; c < n; ++c) {
+    double y[3], x[3];
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c);
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+      x[i] = s / L[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) Ainv[i * n + c] = x[i];
+  }
+  return true;
+}
+
+uint2 philox_key(const glmb_handle* h) {
+  return make_uint2((uint32_t)h->cfg.seed, (uint32_t)(h->cfg.seed >> 32) ^ (uint32_t)h->frame);
+}
+
+glmb_status sync_scal(glmb_handle* h) {
+  CU(cudaMemcpyAsync(h->h_scal, h->d_scal, S_N * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GLMB_OK;
+}
+
+const char* err_text(unsigned e) {
+  if (e & kErrPairs) return "gated pairs exceed max_pairs";
+  if (e & kErrSlots) return "per-hypothesis staging exceeded its plan";
+  if (e & kErrEntries) return "hypothesis entries exceed h_max * max_tracks";
+  if (e & kErrComps) return "components exceed capacity";
+  if (e & kErrUpdates) return "distinct track updates exceed capacity";
+  if (e & kErrHash) return "update table full";
+  if (e & kErrNumeric) return "covariance not positive definite";
+  return "device error";
+}
+
+glmb_status set_initial(glmb_handle* h) {
+  const uint32_t ptr0[2] = {0, 0};
+  const double lw = 0.0;
+  const unsigned long long uid = mix64(h->cfg.seed + kGolden);
+  HypTable& y = h->hyps[h->hcur];
+  CU(cudaMemcpyAsync(y.ptr, ptr0, sizeof ptr0, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(y.logw, &lw, sizeof lw, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(y.uid, &uid, sizeof uid, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->H = 1;
+  h->n_entries = 0;
+  h->n_comp = 0;
+  h->frame = 0;
+  h->stage = 0;
+  h->have_update = false;
+  h->theta_M_valid = false;
+  return GLMB_OK;
+}
+
+void prof_begin(glmb_handle* h, int st) {
+  if (!(h->prof_mask & (1u << st))) return;
+  if (!h->ev[st][0]) {
+    cudaEventCreate(&h->ev[st][0]);
+    cudaEventCreate(&h->ev[st][1]);
+  }
+  cudaEventRecord(h->ev[st][0], h->stream);
+}
+
+void prof_end(glmb_handle* h, int st) {
+  if (!(h->prof_mask & (1u << st)) || !h->ev[st][0]) return;
+  cudaEventRecord(h->ev[st][1], h->stream);
+  h->ev_pending[st] = true;
+}
+
+void prof_collect(glmb_handle* h) {
+  for (int st = 0; st < kNumStages; ++st) {
+    if (!h->ev_pending[st]) continue;
+    float ms = 0.f;
+    if (cudaEventSynchronize(h->ev[st][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, h->ev[st][0], h->ev[st][1]) == cudaSuccess) {
+      h->stage_ms[st] += ms;
+      h->stage_calls[st] += 1;
+    }
+    h->ev_pending[st] = false;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask) {
+  if (!h) return GLMB_E_INVALID;
+  h->prof_mask = stage_mask;
+  for (int st = 0; st < kNumStages; ++st) {
+    h->stage_ms[st] = 0.0;
+    h->stage_calls[st] = 0;
+  }
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_timing(glmb_handle* h, double* ms, long long* calls, int n) {
+  if (!h || n < 0) return GLMB_E_INVALID;
+  CU(cudaStreamSynchronize(h->stream));
+  prof_collect(h);
+  for (int st = 0; st < n; ++st) {
+    if (ms) ms[st] = st < kNumStages ? h->stage_ms[st] : 0.0;
+    if (calls) calls[st] = st < kNumStages ? h->stage_calls[st] : 0;
+  }
+  return GLMB_OK;
+}
+
+glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
+  if (!cfg || !out) return GLMB_E_INVALID;
+  *out = nullptr;
+  const glmb_config& c = *cfg;
+  if (!((c.dim_x == 4 && c.dim_z == 2) || (c.dim_x == 6 && c.dim_z == 3))) return GLMB_E_INVALID;
+  if (!(c.dt > 0) || !(c.q >= 0) || !(c.p_s >= 0 && c.p_s <= 1) || !(c.p_d >= 0 && c.p_d <= 1) ||
+      !(c.lambda_d >= 0) || !(c.clutter_rate >= 0) || !(c.volume > 0) || !(c.gate > 0) ||
+      c.h_max < 1 || c.h_up < 1 || c.h_up > 65535 || !(c.tau > 0) || c.score_mode != 0)
+    return GLMB_E_INVALID;
+  glmb_handle* h = new glmb_handle();
+  h->cfg = c;
+  const int dx = c.dim_x, dz = c.dim_z;
+  h->cap_h = c.h_max;
+  h->max_tracks = c.max_tracks > 0 ? c.max_tracks : 256;
+  h->cap_meas = c.max_meas > 0 ? c.max_meas : 4096;
+  h->cap_births = c.max_births > 0 ? c.max_births : 256;
+  if (h->cap_meas > 65535 || h->max_tracks > 65535) {
+    delete h;
+    return GLMB_E_INVALID;
+  }
+  h->cap_entries = (long long)h->cap_h * h->max_tracks;
+  h->cap_comp = h->cap_entries + h->cap_births;
+  h->cap_pairs = c.max_pairs > 0 ? c.max_pairs : 16 * h->cap_comp;
+  h->cap_children = (long long)h->cap_h * c.h_up;
+  h->cap_upd = h->cap_entries;
+  const long long hcap = next_pow2(2 * h->cap_entries);
+  h->hmask = (uint32_t)(hcap - 1);
+  if (h->cap_comp >= (1LL << 31) || hcap > (1LL << 31) || h->cap_pairs >= (1LL << 32)) {
+    delete h;
+    return GLMB_E_INVALID;
+  }
+
+  // model constants (FP64 on the host, stored as FP32)
+  Model& md = h->md;
+  md.dx = dx;
+  md.dz = dz;
+  md.ncov = dx * (dx + 1) / 2;
+  md.h_up = c.h_up;
+  md.dt = c.dt;
+  const double dt = c.dt;
+  double Q[36] = {0};
+  for (int a = 0; a < dz; ++a) {
+    Q[a * dx + a] = c.q * dt * dt * dt / 3.0;
+    Q[a * dx + dz + a] = c.q * dt * dt / 2.0;
+    Q[(dz + a) * dx + a] = c.q * dt * dt / 2.0;
+    Q[(dz + a) * dx + dz + a] = c.q * dt;
+  }
+  for (int i = 0; i < dx; ++i)
+    for (int j = i; j < dx; ++j) md.Q[pidx(dx, i, j)] = (float)Q[i * dx + j];
+  double Rinv[9], ldR;
+  if (!spd_inverse(dz, c.R, Rinv, &ldR)) {
+    delete h;
+    return GLMB_E_INVALID;
+  }
+  for (int k = 0; k < dz * dz; ++k) {
+    md.R[k] = (float)c.R[k];
+    md.Rinv[k] = (float)Rinv[k];
+  }
+  md.logdetR = (float)ldR;
+  md.log_pd = c.p_d > 0 ? (float)std::log(c.p_d) : -INFINITY;
+  md.log_1mpd = c.p_d < 1 ? (float)std::log1p(-c.p_d) : -INFINITY;
+  md.lambda_d = (float)c.lambda_d;
+  md.log_lambda_d = c.lambda_d > 0 ? (float)std::log(c.lambda_d) : -INFINITY;
+  const double kappa = c.clutter_rate / c.volume;
+  md.kappa_zero = !(kappa > 0);
+  md.log_kappa = md.kappa_zero ? -INFINITY : (float)std::log(kappa);
+  md.fx_log_kappa = md.kappa_zero ? 0 : (long long)std::llrint((double)md.log_kappa * 4294967296.0);
+  md.gate = std::isinf(c.gate) ? INFINITY : (float)c.gate;
+  md.log_ps = c.p_s > 0 ? (float)std::log(c.p_s) : -INFINITY;
+  md.log_1mps = c.p_s < 1 ? (float)std::log1p(-c.p_s) : -INFINITY;
+  md.seed_lo = (uint32_t)c.seed;
+  md.seed_hi = (uint32_t)(c.seed >> 32);
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    delete h;
+    return GLMB_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&h->smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (c.stream) {
+    h->stream = (cudaStream_t)c.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return GLMB_E_CUDA;
+    }
+    h->own_stream = true;
+  }
+  const long long scan_n = std::max(h->cap_comp, h->cap_children);
+  bool ok = alloc_comps(h, h->comps[0], h->cap_comp, dx) && alloc_comps(h, h->comps[1], h->cap_comp, dx) &&
+            alloc_hyps(h, h->hyps[0]) && alloc_hyps(h, h->hyps[1]) &&
+            dalloc(h, &h->d_births, (long long)h->cap_births * kBirthRec) &&
+            halloc(h, &h->h_births, (long long)h->cap_births * kBirthRec) &&
+            dalloc(h, &h->d_Z, (long long)h->cap_meas * dz) &&
+            halloc(h, &h->h_Z, (long long)h->cap_meas * dz) &&
+            dalloc(h, &h->pt.cnt, h->cap_comp + 1) && dalloc(h, &h->pt.ptr, h->cap_comp + 1) &&
+            dalloc(h, &h->pt.meas, h->cap_pairs) && dalloc(h, &h->pt.logC, h->cap_pairs) &&
+            dalloc(h, &h->pt.q, h->cap_pairs) && dalloc(h, &h->pt.e, h->cap_pairs * dz) &&
+            dalloc(h, &h->pt.dthr, h->cap_comp) && dalloc(h, &h->pt.dprob, h->cap_comp) &&
+            dalloc(h, &h->pt.logdetS, h->cap_comp) &&
+            dalloc(h, &h->scan_tmp32, scan_tmp_elems(scan_n)) &&
+            dalloc(h, &h->child_key, h->cap_children) && dalloc(h, &h->child_status, h->cap_children) &&
+            dalloc(h, &h->child_alive, h->cap_children) &&
+            dalloc(h, &h->pw.blk_max, 4097) && dalloc(h, &h->pw.blk_sum, 4097) &&
+            dalloc(h, &h->pw.blk_done, 4) && dalloc(h, &h->pw.lse, 2) && dalloc(h, &h->pw.thr, 1) &&
+            dalloc(h, &h->pw.hist, 4096) && dalloc(h, &h->pw.sel, 4) &&
+            dalloc(h, &h->pw.flags, h->cap_children) &&
+            dalloc(h, &h->pw.flags_tmp, scan_tmp_elems(h->cap_children)) &&
+            dalloc(h, &h->pw.surv_idx, h->cap_h) && dalloc(h, &h->pw.counts, 8) &&
+            dalloc(h, &h->hkeys, hcap) && dalloc(h, &h->hvals, hcap) &&
+            dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
+            dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
+            dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
+            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_pmf, h->max_tracks + 2) &&
+            dalloc(h, &h->d_nb, 2) && dalloc(h, &h->d_r, h->max_tracks + 1) &&
+            dalloc(h, &h->d_ru, h->cap_meas) && dalloc(h, &h->d_tracks, h->max_tracks + 1) &&
+            halloc(h, &h->h_tracks, h->max_tracks + 1);
+  if (!ok) {
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return GLMB_E_OOM;
+  }
+  h->pt.cap_pairs = h->cap_pairs;
+  cudaMemsetAsync(h->pw.blk_done, 0, 4 * sizeof(unsigned), h->stream);
+  cudaMemsetAsync(h->pw.hist, 0, 4096 * sizeof(unsigned), h->stream);
+  if (set_initial(h) != GLMB_OK) {
+    free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return GLMB_E_CUDA;
+  }
+  *out = h;
+  return GLMB_OK;
+}
+
+glmb_status glmb_destroy(glmb_handle* h) {
+  if (!h) return GLMB_OK;
+  cudaStreamSynchronize(h->stream);
+  for (int st = 0; st < kNumStages; ++st)
+    if (h->ev[st][0]) {
+      cudaEventDestroy(h->ev[st][0]);
+      cudaEventDestroy(h->ev[st][1]);
+    }
+  free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return GLMB_OK;
+}
+
+glmb_status glmb_reset(glmb_handle* h) {
+  if (!h) return GLMB_E_INVALID;
+  h->err.clear();
+  return set_initial(h);
+}
+
+const char* glmb_last_error(glmb_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 0) return fail(h, GLMB_E_STATE, "predict: previous frame not pruned");
+  if (n_births < 0 || (n_births > 0 && !births)) return fail(h, GLMB_E_INVALID, "predict: births");
+  if (n_births > h->cap_births)
+    return fail(h, GLMB_E_CAPACITY, "predict: %d births > max_births %d", n_births, h->cap_births);
+  if ((long long)h->n_comp + n_births > h->cap_comp)
+    return fail(h, GLMB_E_CAPACITY, "predict: components exceed capacity");
+  const int dx = h->md.dx;
+  for (int b = 0; b < n_births; ++b) {
+    const glmb_birth& B = births[b];
+    if (!(B.r >= 0 && B.r <= 1)) return fail(h, GLMB_E_INVALID, "predict: birth %d r", b);
+    double* rec = h->h_births + (size_t)b * kBirthRec;
+    rec[0] = B.r;
+    for (int a = 0; a < 6; ++a) rec[1 + a] = a < dx ? B.mean[a] : 0.0;
+    for (int k = 0; k < 36; ++k) rec[7 + k] = k < dx * dx ? B.cov[k] : 0.0;
+    for (int k = 0; k < 1 + dx; ++k)
+      if (!std::isfinite(rec[k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
+    for (int k = 0; k < dx * dx; ++k)
+      if (!std::isfinite(rec[7 + k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
+  }
+  h->frame += 1;
+  h->nb = n_births;
+  CompTable& A = h->comps[h->cur];
+  CompTable& B = h->comps[1 - h->cur];
+  prof_begin(h, kStagePredict);
+  launch_predict(h->md, A, B, h->n_comp, h->stream);
+  if (n_births) {
+    CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
+                       cudaMemcpyHostToDevice, h->stream));
+    launch_births(h->md, B, h->n_comp, h->d_births, n_births, h->frame, h->stream);
+  }
+  prof_end(h, kStagePredict);
+  CU(cudaGetLastError());
+  h->T_work = h->n_comp + n_births;
+  h->stage = 1;
+  h->have_update = false;
+  return GLMB_OK;
+}
+
+glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 1) return fail(h, GLMB_E_STATE, "update: call glmb_predict first");
+  if (M < 0 || (M > 0 && !Z)) return fail(h, GLMB_E_INVALID, "update: detections");
+  if (M > h->cap_meas) return fail(h, GLMB_E_CAPACITY, "update: M=%d > max_meas %d", M, h->cap_meas);
+  const int dz = h->md.dz;
+  auto abandon = [&](glmb_status st, const char* msg) {
+    h->frame -= 1;
+    h->stage = 0;
+    return fail(h, st, "update: %s", msg);
+  };
+  if (M > 0) {
+    if (z_is_device) {
+      CU(cudaMemcpyAsync(h->d_Z, Z, (size_t)M * dz * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      for (long long k = 0; k < (long long)M * dz; ++k)
+        if (!std::isfinite(Z[k])) return abandon(GLMB_E_INVALID, "non-finite detection");
+      std::memcpy(h->h_Z, Z, (size_t)M * dz * sizeof(float));
+      CU(cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)M * dz * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
+  }
+  h->M = M;
+  const int T = h->T_work;
+  const CompTable& B = h->comps[1 - h->cur];
+  CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
+  prof_begin(h, kStageTable);
+  if (z_is_device) launch_check_finite(h->d_Z, (long long)M * dz, h->d_scal + S_ERR, h->stream);
+  launch_table_count(h->md, B, h->pt, T, h->d_Z, M, h->stream);
+  scan_u32(h->pt.cnt, h->pt.ptr, T, h->pt.ptr + T, h->scan_tmp32, h->stream);
+  CU(cudaMemcpyAsync(h->d_scal + S_K, h->pt.ptr + T, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream));
+  launch_table_write(h->md, B, h->pt, T, h->d_Z, M, h->d_scal + S_FP64, h->d_scal + S_ERR, h->stream);
+  const HypTable& P = h->hyps[h->hcur];
+  launch_parent_stats(P, h->H, h->pt, h->n_comp, h->nb, h->d_scal + S_MAXT, h->d_scal + S_MAXK, h->stream);
+  prof_end(h, kStageTable);
+  CU(cudaGetLastError());
+  glmb_status st = sync_scal(h);
+  if (st != GLMB_OK) return st;
+  const unsigned e = h->h_scal[S_ERR];
+  if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
+  h->n_pairs = h->h_scal[S_K];
+  h->n_fp64 = (int)h->h_scal[S_FP64];
+  if (h->n_pairs > h->cap_pairs) return abandon(GLMB_E_CAPACITY, "gated pairs exceed max_pairs");
+  if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
+  h->T_max = (int)std::max(1u, h->h_scal[S_MAXT]);
+  h->K_max = (int)std::max(1u, h->h_scal[S_MAXK]);
+  if (h->T_max > 65535) return abandon(GLMB_E_CAPACITY, "tracks per hypothesis exceed 65535");
+  const int G = expand_plan_groups(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit);
+  const int Gm = expand_plan_groups(dz, 1, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit);
+  if (G == 0 || Gm == 0)
+    return abandon(GLMB_E_CAPACITY, "per-hypothesis table does not fit in shared memory");
+  ExpandArgs a{};
+  a.md = h->md;
+  a.ct = B;
+  a.pt = h->pt;
+  a.parents = P;
+  a.H = h->H;
+  a.birth_base = h->n_comp;
+  a.nb = h->nb;
+  a.Z = h->d_Z;
+  a.M = M;
+  a.key = philox_key(h);
+  a.T_max = h->T_max;
+  a.K_max = h->K_max;
+  a.n_groups = G;
+  a.smem_bytes = expand_smem_bytes(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, G);
+  a.child_key = h->child_key;
+  a.child_status = h->child_status;
+  a.child_alive = h->child_alive;
+  a.materialize = 0;
+  a.err = h->d_scal + S_ERR;
+  prof_begin(h, kStageExpand);
+  launch_expand(a, h->stream);
+  prof_end(h, kStageExpand);
+  CU(cudaGetLastError());
+  h->H_par = h->H;
+  h->par_buf = h->hcur;
+  h->birth_base = h->n_comp;
+  h->stage = 2;
+  h->have_update = true;
+  return GLMB_OK;
+}
+
+glmb_status glmb_prune(glmb_handle* h) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 2) return fail(h, GLMB_E_STATE, "prune: call glmb_update first");
+  const int dz = h->md.dz;
+  const long long n = (long long)h->H * h->cfg.h_up;
+  const int nblk = (int)std::min<long long>(std::max(1LL, (n + 255) / 256), 2LL * h->n_sm);
+  const double log_tau = std::log(h->cfg.tau);
+  const double vmax = std::max(1.0, -log_tau) * 4294967296.0 + 2.0;
+  const int nbits = std::max(1, (int)std::ceil(std::log2(vmax)));
+  cudaStream_t s = h->stream;
+  const HypTable& P = h->hyps[h->hcur];
+  HypTable& O = h->hyps[1 - h->hcur];
+  const CompTable& B = h->comps[1 - h->cur];
+  CompTable& A = h->comps[h->cur];
+  auto abandon = [&](glmb_status st, const char* msg) {
+    h->frame -= 1;
+    h->stage = 0;
+    return fail(h, st, "prune: %s", msg);
+  };
+  CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
+  prof_begin(h, kStageSelect);
+  launch_lse(h->child_key, n, h->pw, log_tau, h->cap_h, nblk, s);
+  launch_select(h->child_key, n, h->cap_h, nbits, h->pw, nblk, s);
+  launch_compact(h->child_key, n, h->pw, h->cap_h, s);
+  launch_finalize(h->pw, h->child_key, h->child_alive, P, h->cfg.h_up, O, h->cap_h,
+                  h->d_scal + S_ERR, h->cap_entries, s);
+  prof_end(h, kStageSelect);
+  CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), s));
+  CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));
+  ExpandArgs a{};
+  a.md = h->md;
+  a.ct = B;
+  a.pt = h->pt;
+  a.parents = P;
+  a.H = h->H;
+  a.birth_base = h->n_comp;
+  a.nb = h->nb;
+  a.Z = h->d_Z;
+  a.M = h->M;
+  a.key = philox_key(h);
+  a.T_max = h->T_max;
+  a.K_max = h->K_max;
+  a.n_groups = expand_plan_groups(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, h->smem_limit);
+  a.smem_bytes = expand_smem_bytes(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, a.n_groups);
+  a.materialize = 1;
+  a.surv_idx = h->pw.surv_idx;
+  a.n_surv = h->pw.counts;
+  a.out_ptr = O.ptr;
+  a.out_comp = O.comp;
+  a.out_theta = O.theta;
+  a.hkeys = h->hkeys;
+  a.hvals = h->hvals;
+  a.hmask = h->hmask;
+  a.upd_src = h->upd_src;
+  a.upd_m = h->upd_m;
+  a.upd_se = h->upd_se;
+  a.upd_count = h->d_scal + S_NUPD;
+  a.cap_upd = (int)h->cap_upd;
+  a.err = h->d_scal + S_ERR;
+  prof_begin(h, kStageMat);
+  launch_expand(a, s);
+  prof_end(h, kStageMat);
+  const int T = h->T_work;
+  prof_begin(h, kStageGc);
+  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)std::max(T, 1) * sizeof(uint32_t), s));
+  launch_mark_old(O.comp, h->pw.counts + 1, h->cap_entries, h->d_scal + S_ERR, h->gc_flag, s);
+  scan_u32(h->gc_flag, h->gc_newpos, T, h->d_scal + S_NKEEP, h->scan_tmp32, s);
+  launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, T, h->d_scal + S_NKEEP, h->upd_src,
+                        h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts,
+                        h->d_scal + S_ERR, s);
+  launch_remap(O.comp, h->pw.counts + 1, h->cap_entries, h->gc_newpos, h->hvals,
+               h->d_scal + S_NKEEP, h->d_scal + S_ERR, s);
+  prof_end(h, kStageGc);
+  CU(cudaGetLastError());
+  unsigned cnt[8];
+  CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, s));
+  glmb_status st = sync_scal(h);
+  if (st != GLMB_OK) return st;
+  const unsigned e = h->h_scal[S_ERR];
+  if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
+  const unsigned n_surv = cnt[0];
+  if (n_surv == 0) return abandon(GLMB_E_NUMERIC, "no child has a finite weight above tau");
+  const unsigned n_keep = h->h_scal[S_NKEEP], n_upd = h->h_scal[S_NUPD];
+  if ((long long)n_keep + n_upd > h->cap_comp) return abandon(GLMB_E_CAPACITY, "components exceed capacity");
+  prof_collect(h);
+  // commit
+  h->n_unique = cnt[2];
+  h->n_upd = (int)n_upd;
+  h->n_comp = (int)(n_keep + n_upd);
+  h->H = (int)n_surv;
+  h->n_entries = cnt[1];
+  h->hcur = 1 - h->hcur;
+  h->theta_M = h->M;
+  h->theta_M_valid = true;
+  h->stage = 0;
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
+  if (!h || !info) return GLMB_E_INVALID;
+  CU(cudaStreamSynchronize(h->stream));
+  std::memset(info, 0, sizeof *info);
+  info->frame = h->frame;
+  info->n_hyp = h->H;
+  info->n_entries = h->n_entries;
+  info->n_components = h->n_comp;
+  info->n_meas = h->M;
+  info->n_pairs = h->n_pairs;
+  info->n_children = h->have_update ? (long long)h->H_par * h->cfg.h_up : 0;
+  info->n_unique = h->n_unique;
+  info->n_updates = h->n_upd;
+  info->n_fp64_chol = h->n_fp64;
+  info->n_launches = g_launches;
+  return GLMB_OK;
+}
+
+glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out, double* card_pmf,
+                           int pmf_cap) {
+  if (!h || !n_out || (cap > 0 && !out)) return GLMB_E_INVALID;
+  if (h->stage == 2) return fail(h, GLMB_E_STATE, "estimates: call glmb_prune first");
+  cudaStream_t s = h->stream;
+  const HypTable& Y = h->hyps[h->hcur];
+  const CompTable& A = h->comps[h->cur];
+  const int pcap = h->max_tracks + 1;
+  prof_begin(h, kStageEstimates);
+  launch_card(Y, h->H, h->d_pmf, pcap, h->d_nb, s);
+  CU(cudaMemsetAsync(h->d_r, 0, (size_t)pcap * sizeof(double), s));
+  launch_existence(Y, h->H, A, h->d_nb, h->d_r, s);
+  CU(cudaGetLastError());
+  int nb[2];
+  CU(cudaMemcpyAsync(nb, h->d_nb, sizeof nb, cudaMemcpyDeviceToHost, s));
+  std::vector<double> pmf(pcap), r(pcap);
+  CU(cudaMemcpyAsync(pmf.data(), h->d_pmf, pcap * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(r.data(), h->d_r, pcap * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  const int nhat = nb[0], best = nb[1];
+  *n_out = nhat;
+  if (card_pmf)
+    for (int k = 0; k < pmf_cap; ++k) card_pmf[k] = k < pcap ? pmf[k] : 0.0;
+  if (nhat > cap) return fail(h, GLMB_E_CAPACITY, "estimates: %d tracks > cap %d", nhat, cap);
+  if (nhat == 0) return GLMB_OK;
+  (void)best;
+  launch_gather_tracks(Y, A, h->md.dx, h->d_nb, h->d_r, h->d_tracks, nhat, s);
+  prof_end(h, kStageEstimates);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(h->h_tracks, h->d_tracks, (size_t)nhat * sizeof(glmb_track),
+                     cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  std::memcpy(out, h->h_tracks, (size_t)nhat * sizeof(glmb_track));
+  return GLMB_OK;
+}
+
+glmb_status glmb_meas_assoc(glmb_handle* h, double* r_u, int cap) {
+  if (!h || (cap > 0 && !r_u)) return GLMB_E_INVALID;
+  if (!h->theta_M_valid || h->stage == 2) return fail(h, GLMB_E_STATE, "meas_assoc: no pruned frame");
+  if (h->theta_M > cap) return fail(h, GLMB_E_CAPACITY, "meas_assoc: cap < M");
+  launch_meas_assoc(h->hyps[h->hcur], h->H, h->theta_M, h->d_ru, h->stream);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(r_u, h->d_ru, (size_t)h->theta_M * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GLMB_OK;
+}
+
+// ---- state buffer ------------------------------------------------------------
+namespace {
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t dim_x, frame, n_hyp, pad;
+  int64_t n_tracks;
+};
+struct HypRec {
+  double logw;
+  uint64_t uid;
+  int32_t n_tracks, pad;
+};
+}  // namespace
+
+glmb_status glmb_export_state(glmb_handle* h, void* buf, size_t cap, size_t* n_out) {
+  if (!h || !n_out) return GLMB_E_INVALID;
+  if (h->stage != 0) return fail(h, GLMB_E_STATE, "export: frame in progress");
+  const int dx = h->md.dx, ncov = h->md.ncov;
+  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx;
+  const size_t need = sizeof(StateHeader) + sizeof(HypRec) * h->H + trk * (size_t)h->n_entries;
+  *n_out = need;
+  if (!buf) return GLMB_OK;
+  if (cap < need) return fail(h, GLMB_E_CAPACITY, "export: buffer too small");
+  CU(cudaStreamSynchronize(h->stream));
+  const HypTable& Y = h->hyps[h->hcur];
+  const CompTable& A = h->comps[h->cur];
+  std::vector<uint32_t> ptr(h->H + 1), comp(std::max<long long>(1, h->n_entries));
+  std::vector<double> logw(h->H);
+  std::vector<unsigned long long> uid(h->H);
+  CU(cudaMemcpy(ptr.data(), Y.ptr, ptr.size() * 4, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(comp.data(), Y.comp, (size_t)h->n_entries * 4, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(logw.data(), Y.logw, (size_t)h->H * 8, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(uid.data(), Y.uid, (size_t)h->H * 8, cudaMemcpyDeviceToHost));
+  const size_t nc = std::max(1, h->n_comp);
+  std::vector<float> mh(nc * dx), ml(nc * dx), cv(nc * ncov);
+  std::vector<uint32_t> lk(nc), lb(nc);
+  for (int a = 0; a < dx; ++a) {
+    CU(cudaMemcpy(mh.data() + a * nc, A.mhi + (size_t)a * A.cap, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ml.data() + a * nc, A.mlo + (size_t)a * A.cap, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+  }
+  for (int k = 0; k < ncov; ++k)
+    CU(cudaMemcpy(cv.data() + k * nc, A.cov + (size_t)k * A.cap, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(lk.data(), A.lk, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(lb.data(), A.lb, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+  unsigned char* p = (unsigned char*)buf;
+  StateHeader hd{0x424D4C47u, 1u, dx, h->frame, h->H, 0, h->n_entries};
+  std::memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  for (int y = 0; y < h->H; ++y) {
+    HypRec r{logw[y], uid[y], (int32_t)(ptr[y + 1] - ptr[y]), 0};
+    std::memcpy(p, &r, sizeof r);
+    p += sizeof r;
+  }
+  for (long long e = 0; e < h->n_entries; ++e) {
+    const size_t c = comp[e];
+    std::memcpy(p, &lk[c], 4);
+    std::memcpy(p + 4, &lb[c], 4);
+    p += 8;
+    for (int a = 0; a < dx; ++a) {
+      const double v = (double)mh[a * nc + c] + (double)ml[a * nc + c];
+      std::memcpy(p, &v, 8);
+      p += 8;
+    }
+    for (int i = 0; i < dx; ++i)
+      for (int k = 0; k < dx; ++k) {
+        const double v = cv[(size_t)pidx(dx, std::min(i, k), std::max(i, k)) * nc + c];
+        std::memcpy(p, &v, 8);
+        p += 8;
+      }
+  }
+  return GLMB_OK;
+}
+
+glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
+  if (!h || !buf) return GLMB_E_INVALID;
+  const int dx = h->md.dx, ncov = h->md.ncov;
+  if (n < sizeof(StateHeader)) return fail(h, GLMB_E_STATE, "import: short buffer");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof hd);
+  if (hd.magic != 0x424D4C47u || hd.version != 1u || hd.dim_x != dx || hd.n_hyp < 1 ||
+      hd.n_tracks < 0 || hd.frame < 0)
+    return fail(h, GLMB_E_STATE, "import: bad header");
+  if (hd.n_hyp > h->cap_h) return fail(h, GLMB_E_CAPACITY, "import: hypotheses exceed h_max");
+  if (hd.n_tracks > h->cap_entries) return fail(h, GLMB_E_CAPACITY, "import: entries exceed capacity");
+  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx;
+  const size_t need = sizeof(StateHeader) + sizeof(HypRec) * hd.n_hyp + trk * (size_t)hd.n_tracks;
+  if (n < need) return fail(h, GLMB_E_STATE, "import: truncated buffer");
+  const unsigned char* p = (const unsigned char*)buf + sizeof hd;
+  std::vector<uint32_t> ptr(hd.n_hyp + 1, 0);
+  std::vector<double> logw(hd.n_hyp);
+  std::vector<unsigned long long> uid(hd.n_hyp);
+  for (int y = 0; y < hd.n_hyp; ++y) {
+    HypRec r;
+    std::memcpy(&r, p, sizeof r);
+    p += sizeof r;
+    if (r.n_tracks < 0 || r.n_tracks > h->max_tracks || !std::isfinite(r.logw))
+      return fail(h, GLMB_E_STATE, "import: hypothesis %d", y);
+    logw[y] = r.logw;
+    uid[y] = r.uid;
+    ptr[y + 1] = ptr[y] + (uint32_t)r.n_tracks;
+  }
+  if ((long long)ptr[hd.n_hyp] != hd.n_tracks) return fail(h, GLMB_E_STATE, "import: track count");
+  // identical (label, mean, cov) records become one shared component
+  std::unordered_map<std::string, uint32_t> seen;
+  std::vector<uint32_t> comp(std::max<long long>(1, hd.n_tracks));
+  std::vector<float> mh, ml, cv;
+  std::vector<uint32_t> lk, lb;
+  for (long long e = 0; e < hd.n_tracks; ++e) {
+    std::string key((const char*)p, trk);
+    auto it = seen.find(key);
+    if (it != seen.end()) {
+      comp[e] = it->second;
+      p += trk;
+      continue;
+    }
+    const uint32_t c = (uint32_t)lk.size();
+    seen.emplace(std::move(key), c);
+    comp[e] = c;
+    uint32_t k0, b0;
+    std::memcpy(&k0, p, 4);
+    std::memcpy(&b0, p + 4, 4);
+    lk.push_back(k0);
+    lb.push_back(b0);
+    p += 8;
+    for (int a = 0; a < dx; ++a) {
+      double v;
+      std::memcpy(&v, p, 8);
+      p += 8;
+      if (!std::isfinite(v)) return fail(h, GLMB_E_STATE, "import: mean not finite");
+      const float hi = (float)v;
+      mh.push_back(hi);
+      ml.push_back((float)(v - (double)hi));
+    }
+    double P[36];
+    std::memcpy(P, p, 8 * dx * dx);
+    p += 8 * dx * dx;
+    for (int i = 0; i < dx; ++i)
+      for (int k = i; k < dx; ++k) cv.push_back((float)(0.5 * (P[i * dx + k] + P[k * dx + i])));
+  }
+  const int nc = (int)lk.size();
+  if (nc > h->cap_comp) return fail(h, GLMB_E_CAPACITY, "import: components exceed capacity");
+  CU(cudaStreamSynchronize(h->stream));
+  const CompTable& A = h->comps[h->cur];
+  if (nc > 0) {
+    std::vector<float> col(nc);
+    for (int a = 0; a < dx; ++a) {
+      for (int c = 0; c < nc; ++c) col[c] = mh[(size_t)c * dx + a];
+      CU(cudaMemcpy(A.mhi + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+      for (int c = 0; c < nc; ++c) col[c] = ml[(size_t)c * dx + a];
+      CU(cudaMemcpy(A.mlo + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+    }
+    for (int k = 0; k < ncov; ++k) {
+      for (int c = 0; c < nc; ++c) col[c] = cv[(size_t)c * ncov + k];
+      CU(cudaMemcpy(A.cov + (size_t)k * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+    }
+    CU(cudaMemcpy(A.lk, lk.data(), nc * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(A.lb, lb.data(), nc * 4, cudaMemcpyHostToDevice));
+  }
+  const HypTable& Y = h->hyps[h->hcur];
+  CU(cudaMemcpy(Y.ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
+  if (hd.n_tracks > 0) CU(cudaMemcpy(Y.comp, comp.data(), (size_t)hd.n_tracks * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(Y.logw, logw.data(), logw.size() * 8, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(Y.uid, uid.data(), uid.size() * 8, cudaMemcpyHostToDevice));
+  h->n_comp = nc;
+  h->H = hd.n_hyp;
+  h->n_entries = hd.n_tracks;
+  h->frame = hd.frame;
+  h->stage = 0;
+  h->have_update = false;
+  h->theta_M_valid = false;
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_hypotheses(glmb_handle* h, double* logw, uint64_t* uid, uint32_t* hyp_ptr,
+                                uint32_t* label_k, uint32_t* label_b, uint16_t* theta, int cap_h,
+                                int64_t cap_entries, int* n_h) {
+  if (!h || !n_h) return GLMB_E_INVALID;
+  if (h->stage != 0) return fail(h, GLMB_E_STATE, "get_hypotheses: frame in progress");
+  CU(cudaStreamSynchronize(h->stream));
+  *n_h = h->H;
+  if (h->H > cap_h || h->n_entries > cap_entries) return fail(h, GLMB_E_CAPACITY, "get_hypotheses: caps");
+  const HypTable& Y = h->hyps[h->hcur];
+  const CompTable& A = h->comps[h->cur];
+  if (logw) CU(cudaMemcpy(logw, Y.logw, (size_t)h->H * 8, cudaMemcpyDeviceToHost));
+  if (uid) CU(cudaMemcpy(uid, Y.uid, (size_t)h->H * 8, cudaMemcpyDeviceToHost));
+  if (hyp_ptr) CU(cudaMemcpy(hyp_ptr, Y.ptr, (size_t)(h->H + 1) * 4, cudaMemcpyDeviceToHost));
+  if ((label_k || label_b) && h->n_entries > 0) {
+    std::vector<uint32_t> comp(h->n_entries), lk(std::max(1, h->n_comp)), lb(std::max(1, h->n_comp));
+    CU(cudaMemcpy(comp.data(), Y.comp, comp.size() * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(lk.data(), A.lk, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(lb.data(), A.lb, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+    for (long long e = 0; e < h->n_entries; ++e) {
+      if (label_k) label_k[e] = lk[comp[e]];
+      if (label_b) label_b[e] = lb[comp[e]];
+    }
+  }
+  if (theta && h->theta_M_valid && h->theta_M > 0)
+    CU(cudaMemcpy(theta, Y.theta, (size_t)h->H * h->theta_M * 2, cudaMemcpyDeviceToHost));
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_parents(glmb_handle* h, uint32_t* ptr, uint32_t* comp, int cap_parents,
+                             int64_t cap_slots, int* n_parents) {
+  if (!h || !n_parents) return GLMB_E_INVALID;
+  if (!h->have_update) return fail(h, GLMB_E_STATE, "get_parents: no update");
+  CU(cudaStreamSynchronize(h->stream));
+  const HypTable& P = h->hyps[h->par_buf];
+  const int H = h->H_par;
+  *n_parents = H;
+  std::vector<uint32_t> p(H + 1);
+  CU(cudaMemcpy(p.data(), P.ptr, (H + 1) * 4, cudaMemcpyDeviceToHost));
+  const long long total = (long long)p[H] + (long long)H * h->nb;
+  if (H > cap_parents || total > cap_slots) return fail(h, GLMB_E_CAPACITY, "get_parents: caps");
+  std::vector<uint32_t> c(std::max<uint32_t>(1, p[H]));
+  if (p[H]) CU(cudaMemcpy(c.data(), P.comp, (size_t)p[H] * 4, cudaMemcpyDeviceToHost));
+  long long o = 0;
+  for (int y = 0; y < H; ++y) {
+    if (ptr) ptr[y] = (uint32_t)o;
+    for (uint32_t j = p[y]; j < p[y + 1]; ++j, ++o)
+      if (comp) comp[o] = c[j];
+    for (int b = 0; b < h->nb; ++b, ++o)
+      if (comp) comp[o] = (uint32_t)(h->birth_base + b);
+  }
+  if (ptr) ptr[H] = (uint32_t)o;
+  return GLMB_OK;
+}
+
+
+glmb_status glmb_get_components(glmb_handle* h, uint32_t* label_k, uint32_t* label_b,
+                                double* mean, double* cov, double* p, double* dprob,
+                                double* logdetS, int cap, int* n_comp) {
+  if (!h || !n_comp) return GLMB_E_INVALID;
+  if (!h->have_update) return fail(h, GLMB_E_STATE, "get_components: no update");
+  CU(cudaStreamSynchronize(h->stream));
+  const int T = h->T_work, dx = h->md.dx, ncov = h->md.ncov;
+  *n_comp = T;
+  if (T > cap) return fail(h, GLMB_E_CAPACITY, "get_components: cap");
+  if (T == 0) return GLMB_OK;
+  const CompTable& B = h->comps[1 - h->cur];
+  std::vector<float> f(T);
+  auto col = [&](const float* src) -> glmb_status {
+    CU(cudaMemcpy(f.data(), src, (size_t)T * 4, cudaMemcpyDeviceToHost));
+    return GLMB_OK;
+  };
+  if (label_k) CU(cudaMemcpy(label_k, B.lk, (size_t)T * 4, cudaMemcpyDeviceToHost));
+  if (label_b) CU(cudaMemcpy(label_b, B.lb, (size_t)T * 4, cudaMemcpyDeviceToHost));
+  if (mean) {
+    std::vector<float> lo(T);
+    for (int a = 0; a < dx; ++a) {
+      if (col(B.mhi + (size_t)a * B.cap) != GLMB_OK) return GLMB_E_CUDA;
+      CU(cudaMemcpy(lo.data(), B.mlo + (size_t)a * B.cap, (size_t)T * 4, cudaMemcpyDeviceToHost));
+      for (int c = 0; c < T; ++c) mean[(size_t)c * dx + a] = (double)f[c] + (double)lo[c];
+    }
+  }
+  if (cov) {
+    for (int i = 0; i < dx; ++i)
+      for (int k = i; k < dx; ++k) {
+        if (col(B.cov + (size_t)pidx(dx, i, k) * B.cap) != GLMB_OK) return GLMB_E_CUDA;
+        for (int c = 0; c < T; ++c)
+          cov[(size_t)c * dx * dx + i * dx + k] = cov[(size_t)c * dx * dx + k * dx + i] = f[c];
+      }
+  }
+  if (p) {
+    if (col(B.logp) != GLMB_OK) return GLMB_E_CUDA;
+    for (int c = 0; c < T; ++c) p[c] = std::exp((double)f[c]);
+  }
+  if (dprob) {
+    if (col(h->pt.dprob) != GLMB_OK) return GLMB_E_CUDA;
+    for (int c = 0; c < T; ++c) dprob[c] = f[c];
+  }
+  if (logdetS) {
+    if (col(h->pt.logdetS) != GLMB_OK) return GLMB_E_CUDA;
+    for (int c = 0; c < T; ++c) logdetS[c] = f[c];
+  }
+  (void)ncov;
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_pairs(glmb_handle* h, uint32_t* comp_ptr, uint32_t* meas, float* logC,
+                           float* q, float* e, int cap_comp, int64_t cap_pairs, int64_t* n_pairs) {
+  if (!h || !n_pairs) return GLMB_E_INVALID;
+  if (!h->have_update) return fail(h, GLMB_E_STATE, "get_pairs: no update");
+  CU(cudaStreamSynchronize(h->stream));
+  const int T = h->T_work, dz = h->md.dz;
+  const long long K = h->n_pairs;
+  *n_pairs = K;
+  if (T + 1 > cap_comp || K > cap_pairs) return fail(h, GLMB_E_CAPACITY, "get_pairs: caps");
+  if (comp_ptr) CU(cudaMemcpy(comp_ptr, h->pt.ptr, (size_t)(T + 1) * 4, cudaMemcpyDeviceToHost));
+  if (K == 0) return GLMB_OK;
+  if (meas) CU(cudaMemcpy(meas, h->pt.meas, (size_t)K * 4, cudaMemcpyDeviceToHost));
+  if (logC) CU(cudaMemcpy(logC, h->pt.logC, (size_t)K * 4, cudaMemcpyDeviceToHost));
+  if (q) CU(cudaMemcpy(q, h->pt.q, (size_t)K * 4, cudaMemcpyDeviceToHost));
+  if (e)
+    for (int a = 0; a < dz; ++a) {
+      std::vector<float> col(K);
+      CU(cudaMemcpy(col.data(), h->pt.e + (size_t)a * h->cap_pairs, (size_t)K * 4, cudaMemcpyDeviceToHost));
+      for (long long j = 0; j < K; ++j) e[j * dz + a] = col[j];
+    }
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint16_t* n_alive,
+                              int64_t cap, int64_t* n_children) {
+  if (!h || !n_children) return GLMB_E_INVALID;
+  if (!h->have_update) return fail(h, GLMB_E_STATE, "get_children: no update");
+  CU(cudaStreamSynchronize(h->stream));
+  const long long n = (long long)h->H_par * h->cfg.h_up;
+  *n_children = n;
+  if (n > cap) return fail(h, GLMB_E_CAPACITY, "get_children: cap");
+  if (logw) {
+    std::vector<long long> k(n);
+    CU(cudaMemcpy(k.data(), h->child_key, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    for (long long j = 0; j < n; ++j)
+      logw[j] = k[j] == kKeyInvalid ? -INFINITY : (double)k[j] * kFxInv;
+  }
+  if (status) CU(cudaMemcpy(status, h->child_status, (size_t)n, cudaMemcpyDeviceToHost));
+  if (n_alive) CU(cudaMemcpy(n_alive, h->child_alive, (size_t)n * 2, cudaMemcpyDeviceToHost));
+  return GLMB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Device-side data layout and arithmetic shared by the kernels of the
+// multi-detection GLMB update (arXiv 2512.06230, Section 3).
+//
+// Layout in HBM (all structure-of-arrays, one GPU):
+//   components  mean as two float32 words per coordinate (hi + lo, so a
+//               position of 5 km keeps ~1e-9 m resolution while all
+//               arithmetic stays FP32), packed upper-triangular FP32
+//               covariance, labels, log prior existence;
+//   table       gated (component, detection) pairs in CSR by component;
+//   hypotheses  CSR of component indices, FP64 log-weights, 64-bit uids;
+//   children    one int64 fixed-point log-weight per (parent, draw).
+//
+// Log-weights of children are sums of thousands of FP32 terms.  Each term is
+// converted to int64 fixed point (2^-32 resolution) and the sums are exact
+// integer sums, so identical terms cancel exactly between children and the
+// result does not depend on summation order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace glmb {
+
+// device error flags (sticky per frame, read by the host at sync points)
+enum : uint32_t {
+  kErrPairs = 1u,       // gated pairs beyond capacity
+  kErrHash = 2u,        // update hash table full
+  kErrUpdates = 4u,     // distinct track updates beyond capacity
+  kErrComps = 8u,       // components beyond capacity
+  kErrNumeric = 16u,    // covariance not positive definite even in FP64
+  kErrEntries = 32u,    // hypothesis entries beyond capacity
+  kErrSlots = 64u,      // per-hypothesis staging beyond the planned size
+  kErrInput = 128u,     // a detection is NaN or infinite
+};
+
+constexpr float kFxScale = 4294967296.0f;          // 2^32
+constexpr double kFxInv = 2.3283064365386963e-10;  // 2^-32
+constexpr long long kKeyInvalid = (long long)0x8000000000000000ULL;
+constexpr uint32_t kNewTag = 0x80000000u;          // hypothesis entry -> hash-table slot
+constexpr float kLog2Pi = 1.8378770664093453f;
+constexpr uint32_t kOne24 = 1u << 24;
+
+struct Model {
+  int dx, dz, ncov;       // state dim, detection dim, packed covariance length
+  int h_up;
+  float dt;
+  float Q[21];            // packed upper triangle, row-major
+  float R[9], Rinv[9];    // dz x dz full
+  float logdetR;
+  float log_pd, log_1mpd; // log P_D, log(1 - P_D) (may be -inf)
+  float lambda_d, log_lambda_d;
+  float log_kappa;        // -inf when kappa == 0
+  int kappa_zero;
+  float gate;
+  float log_ps, log_1mps;
+  long long fx_log_kappa; // fixed-point log kappa (0 when kappa == 0)
+  uint32_t seed_lo, seed_hi;
+};
+
+struct CompTable {
+  float* mhi;             // [dx][cap]
+  float* mlo;             // [dx][cap]
+  float* cov;             // [ncov][cap]
+  uint32_t* lk;
+  uint32_t* lb;
+  float* logp;            // log prior existence
+  float* log1mp;          // log(1 - prior existence)
+  int cap;
+};
+
+struct PairTable {
+  uint32_t* cnt;          // [comp] gated count (count pass)
+  uint32_t* ptr;          // [comp + 1] CSR offsets
+  uint32_t* meas;         // [pair]
+  float* logC;            // [pair] log Eq. 2 entry
+  float* q;               // [pair] e^T R^-1 e
+  float* e;               // [dz][cap_pairs]
+  uint32_t* dthr;         // [comp] death threshold on 24-bit uniforms
+  float* dprob;           // [comp]
+  float* logdetS;         // [comp]
+  long long cap_pairs;
+};
+
+struct HypTable {
+  uint32_t* ptr;          // [cap_h + 1]
+  uint32_t* comp;         // [cap_entries]
+  double* logw;
+  unsigned long long* uid;
+  uint16_t* theta;        // [cap_h][max_meas]
+};
+
+__host__ __device__ __forceinline__ int pidx(int n, int i, int j) {
+  // packed upper-triangular index, i <= j, row-major
+  return i * n - (i * (i - 1)) / 2 + (j - i);
+}
+
+// splitmix64 output function (Steele, Lea, Flood, OOPSLA 2014)
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies, with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& r, int b) {
+  return b == 0 ? r.x : b == 1 ? r.y : b == 2 ? r.z : r.w;
+}
+
+__device__ __forceinline__ long long fx_of(float x) { return __float2ll_rn(x * kFxScale); }
+
+// a + b for hi/lo float pairs (Knuth two-sum, then renormalise)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  const float l = lo + err;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+
+// Cholesky of an N x N SPD matrix (full, row-major) in type T; returns false
+// when a pivot is not above 16 eps trace(S) (then the caller redoes the
+// factorisation in FP64).
+template <typename T, int N>
+__device__ __forceinline__ bool chol_n(const T (&S)[N][N], T (&L)[N][N], T& logdet, T eps) {
+  T tr = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) tr += S[i][i];
+  const T thr = T(16) * eps * tr;
+  logdet = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T s = S[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > thr)) return false;
+    const T d = sqrt(s);
+    L[j][j] = d;
+    logdet += T(2) * log(d);
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      T t = S[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / d;
+    }
+#pragma unroll
+    for (int i = 0; i < j; ++i) L[i][j] = 0;
+  }
+  return true;
+}
+
+// x^T (L L^T)^-1 x by forward substitution
+template <typename T, int N>
+__device__ __forceinline__ T mahal_n(const T (&L)[N][N], const T (&x)[N]) {
+  T y[N];
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T t = x[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t / L[i][i];
+    s += y[i] * y[i];
+  }
+  return s;
+}
+
+// logdet(S) and x^T S^-1 x with an FP64 fallback for ill-conditioned S.
+// Returns 0 (FP32), 1 (FP64 used) or -1 (not positive definite).
+template <int N>
+__device__ __forceinline__ int logdet_mahal(const float (&S)[N][N], const float (&x)[N],
+                                            float& logdet, float& d2) {
+  float L[N][N];
+  float ld;
+  if (chol_n<float, N>(S, L, ld, 1.1920929e-7f)) {
+    logdet = ld;
+    d2 = mahal_n<float, N>(L, x);
+    return 0;
+  }
+  double Sd[N][N], Ld[N][N], xd[N], ldd;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    xd[i] = x[i];
+#pragma unroll
+    for (int j = 0; j < N; ++j) Sd[i][j] = S[i][j];
+  }
+  if (!chol_n<double, N>(Sd, Ld, ldd, 2.220446049250313e-16)) return -1;
+  logdet = (float)ldd;
+  d2 = (float)mahal_n<double, N>(Ld, xd);
+  return 1;
+}
+
+// Per-track term of the child log-weight (exact GLMB target weight).
+// alive with m >= 1 detections:
+//   log p + log P_D - lambda_d + (m-1) log lambda_d + log m + J(W)
+//   J = -(m dz/2) log 2pi - ((m-1)/2) log|R| - (dz/2) log m
+//       - 1/2 (sum q - m ebar^T R^-1 ebar) - 1/2 log|S_m| - 1/2 ebar^T S_m^-1 ebar,
+//   S_m = H P H^T + R/m, ebar = (sum e)/m  (prod_i N(z_i;Hx,R) = N(zbar;Hx,R/m) c(W));
+// alive, undetected: log p + log(1 - P_D).
+// The finite part is returned in fixed point; infinite parts are counted.
+template <int DZ>
+__device__ __forceinline__ long long alive_term(const Model& md, const float (&HPH)[DZ][DZ],
+                                                float logp, int m, const long long* se,
+                                                long long sq, int& ninf) {
+  ninf = 0;
+  float t = 0.f;
+  if (isinf(logp)) ++ninf; else t += logp;
+  if (m == 0) {
+    if (isinf(md.log_1mpd)) ++ninf; else t += md.log_1mpd;
+    return fx_of(t);
+  }
+  if (isinf(md.log_pd)) ++ninf; else t += md.log_pd;
+  t -= md.lambda_d;
+  if (m > 1) {
+    if (md.lambda_d <= 0.f) ++ninf; else t += (float)(m - 1) * md.log_lambda_d;
+  }
+  const float fm = (float)m, inv_m = 1.f / fm, logm = logf(fm);
+  t += logm;
+  float sum_e[DZ], ebar[DZ];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) {
+    sum_e[a] = (float)((double)se[a] * kFxInv);
+    ebar[a] = sum_e[a] * inv_m;
+  }
+  float qR = 0.f;
+#pragma unroll
+  for (int a = 0; a < DZ; ++a)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) qR += sum_e[a] * md.Rinv[a * DZ + b] * sum_e[b];
+  const float spread = (float)((double)sq * kFxInv) - qR * inv_m;
+  float Sm[DZ][DZ];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) Sm[a][b] = HPH[a][b] + md.R[a * DZ + b] * inv_m;
+  float ld, d2;
+  if (logdet_mahal<DZ>(Sm, ebar, ld, d2) < 0) { ++ninf; return 0; }
+  t += -0.5f * fm * (float)DZ * kLog2Pi - 0.5f * (fm - 1.f) * md.logdetR
+       - 0.5f * (float)DZ * logm - 0.5f * spread - 0.5f * ld - 0.5f * d2;
+  return fx_of(t);
+}
+
+__device__ __forceinline__ long long dead_term(float log1mp, int& ninf) {
+  ninf = isinf(log1mp) ? 1 : 0;
+  return ninf ? 0 : fx_of(log1mp);
+}
+
+template <int DZ>
+__device__ __forceinline__ void load_HPH(const CompTable& ct, int ncov, int dx, int c,
+                                         float (&HPH)[DZ][DZ]) {
+#pragma unroll
+  for (int a = 0; a < DZ; ++a)
+#pragma unroll
+    for (int b = a; b < DZ; ++b) {
+      const float v = ct.cov[(size_t)pidx(dx, a, b) * ct.cap + c];
+      HPH[a][b] = v;
+      HPH[b][a] = v;
+    }
+}
+
+// key of one association decision for the per-parent duplicate test
+__device__ __forceinline__ unsigned long long row_key(int i, int theta) {
+  return mix64(((unsigned long long)(uint32_t)i << 32) | (uint32_t)theta);
+}
+__device__ __forceinline__ unsigned long long dead_key(int t) {
+  return mix64(0xFFFFFFFF00000000ULL | (uint32_t)t);
+}
+__device__ __forceinline__ unsigned long long wset_key(int i) {
+  return mix64(0x5A5A5A5A00000000ULL ^ (unsigned long long)(uint32_t)i);
+}
+
+}  // namespace glmb

@@ -1,0 +1,122 @@
+// Host-side launch functions of the GLMB kernels (one GPU, one stream).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "glmb_dev.cuh"
+
+namespace glmb {
+
+// kernels launched by this library (all handles), for the benchmark's count
+extern long long g_launches;
+
+// ---- prediction, births, table (kernels_table.cu) ----
+void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
+                    cudaStream_t s);
+void launch_births(const Model& md, const CompTable& ct, int base, const double* births_dev,
+                   int nb, int frame, cudaStream_t s);
+void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt, int T,
+                        const float* Z, int M, cudaStream_t s);
+void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt, int T,
+                        const float* Z, int M, unsigned* n_fp64, unsigned* err, cudaStream_t s);
+void launch_check_finite(const float* Z, long long n, unsigned* err, cudaStream_t s);
+void launch_parent_stats(const HypTable& hp, int H, const PairTable& pt, int birth_base, int nb,
+                         unsigned* max_T, unsigned* max_K, cudaStream_t s);
+
+// exclusive scans; tmp must hold scan_tmp_elems(n) elements of the value type
+long long scan_tmp_elems(long long n);
+void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* total, uint32_t* tmp,
+              cudaStream_t s);
+void scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
+              unsigned long long* total, unsigned long long* tmp, cudaStream_t s);
+
+// ---- expansion / materialisation (kernels_expand.cu) ----
+struct ExpandArgs {
+  Model md;
+  CompTable ct;
+  PairTable pt;
+  HypTable parents;       // hypotheses before the update
+  int H;                  // number of parents
+  int birth_base, nb;     // birth components of this frame
+  const float* Z;
+  int M;
+  uint2 key;              // Philox key (seed_lo, seed_hi ^ frame)
+  // staging plan (sizes fixed by the host from the per-parent maxima)
+  int T_max, K_max, n_groups;
+  int smem_bytes;
+  // expansion outputs
+  long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
+  int8_t* child_status;   // 0 zero weight, 1 unique, 2 duplicate
+  uint16_t* child_alive;  // surviving tracks
+  // materialisation inputs / outputs
+  int materialize;
+  const long long* surv_idx;   // [n_surv] child index h*h_up + n, ascending
+  const unsigned* n_surv;      // device count of survivors
+  const uint32_t* out_ptr;     // [n_surv + 1]
+  uint32_t* out_comp;          // entries: component index, or kNewTag | hash slot
+  uint16_t* out_theta;         // [n_surv][M]
+  unsigned long long* hkeys;   // hash table of (component, detection set) keys
+  uint32_t* hvals;             // slot -> update id
+  uint32_t hmask;
+  uint32_t* upd_src;           // update id -> source component
+  uint32_t* upd_m;             // update id -> |W|
+  long long* upd_se;           // [dz][cap_upd] fixed-point sum of innovations
+  uint32_t* upd_count;
+  int cap_upd;
+  unsigned* err;
+};
+int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int h_up,
+                      int n_groups);
+int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
+                       int smem_limit);
+void launch_expand(const ExpandArgs& a, cudaStream_t s);
+
+// ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
+struct PruneWork {
+  long long* blk_max;           // per-block partials
+  double* blk_sum;
+  unsigned* blk_done;           // last-block counters [4]
+  double* lse;                  // [2]: LSE over unique children, LSE over retained
+  long long* thr;               // fixed-point threshold log(tau) + LSE
+  unsigned* hist;               // [4096]
+  long long* sel;               // [4]: prefix, need, boundary key, flags
+  unsigned long long* flags;    // [n_children] packed (gt, eq) prefix counts
+  unsigned long long* flags_tmp;
+  long long* surv_idx;          // [cap_h]
+  unsigned* counts;             // [8]: n_surv, n_entries, n_keep, n_upd, ...
+};
+void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau, int h_max,
+                int nblk, cudaStream_t s);
+void launch_select(const long long* keys, long long n, int h_max, int nbits, PruneWork w,
+                   int nblk, cudaStream_t s);
+void launch_compact(const long long* keys, long long n, PruneWork w, int h_max,
+                    cudaStream_t s);
+void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
+                     const HypTable& parents, int h_up, HypTable out, int h_max,
+                     unsigned* err, long long cap_entries, cudaStream_t s);
+void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
+                     const unsigned* err, uint32_t* flag, cudaStream_t s);
+void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
+                           const uint32_t* newpos, const uint32_t* flag, int n_src,
+                           const unsigned* n_keep_dev, const uint32_t* upd_src,
+                           const uint32_t* upd_m, const long long* upd_se, int cap_upd,
+                           const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
+                           cudaStream_t s);
+void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
+                  const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
+                  const unsigned* err, cudaStream_t s);
+// device error flags that abandon a frame (state left untouched)
+constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
+                               kErrEntries | kErrSlots | kErrInput;
+
+// estimates
+void launch_card(const HypTable& hp, int H, double* pmf, int pmf_cap, int* nhat_best,
+                 cudaStream_t s);
+void launch_existence(const HypTable& hp, int H, const CompTable& ct, const int* nhat_best,
+                      double* r, cudaStream_t s);
+void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s);
+// MAP tracks into glmb_track records (out must hold max_tracks records)
+void launch_gather_tracks(const HypTable& hp, const CompTable& ct, int dx, const int* nhat_best,
+                          const double* r, void* out, int cap, cudaStream_t s);
+
+}  // namespace glmb

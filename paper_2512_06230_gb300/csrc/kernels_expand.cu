@@ -1,0 +1,686 @@
+// Child expansion, scoring and per-parent deduplication (arXiv 2512.06230,
+// Section 3: two-stage sampling of H_up children per hypothesis, weight =
+// parent weight x joint likelihood of the sampled deaths and associations,
+// retention of unique children), and the regeneration of the retained
+// children for the batched track update.
+//
+// One CTA per parent hypothesis.  The CTA stages the parent's gated pairs in
+// shared memory re-indexed by detection row (slots ascending within a row),
+// with per-row integer thresholds of the categorical draw under "all slots
+// alive", and a reference association (each row's most likely option) whose
+// exact score is computed once.  Each warp then draws children:
+//   phase 1  Philox words for the slots that can die; dead slots are marked;
+//   phase 2  one Philox word per detection row; the row's option is the first
+//            whose threshold exceeds the 24-bit uniform (rows with a dead
+//            candidate fall back to the FP32 normalised row of C'_k); rows
+//            that leave the reference move fixed-point sums (count, sum of
+//            innovations, sum of e^T R^-1 e) between slots;
+//   phase 3  only the touched slots are rescored; the child's log-weight is
+//            the reference score plus the exact integer change.
+// The duplicate test keys a child by the order-free sum of mix64 keys of its
+// deviations and deaths.
+#include "glmb_kernels.h"
+
+namespace glmb {
+
+struct Lay {
+  int scal;
+  int comp, dthr, logp, log1mp, mref, seref, sqref, termref, ninfref, hwref, refnew;
+  int rowoff, rowfill, rowref, rowflag, rowthr0, roww0;
+  int cslot, cthr, ceidx, cw;
+  int dpc;
+  int score, hash, valid, nalive;
+  int grp, grp_bytes;
+  int g_cnt, g_se, g_sq, g_hw, g_newval, g_tmask, g_dmask, g_dpre, g_tlist, g_nt;
+  int total;
+};
+
+struct Bump {
+  int off = 0;
+  __host__ __device__ int take(long long bytes) {
+    const int o = off;
+    off += (int)((bytes + 15) & ~15LL);
+    return o;
+  }
+};
+
+struct Scal {
+  long long ref_score;
+  unsigned long long uid;
+  double logw;
+  int ninf_ref, nclut_ref, T, Town, K, ndpc, s_lo, s_hi, bad;
+};
+
+__host__ __device__ inline Lay make_lay(int dz, int mat, int T, int K, int M, int HU, int G) {
+  Lay L;
+  Bump b;
+  const int W = (T + 31) / 32 + 1;
+  L.scal = b.take(sizeof(Scal));
+  L.seref = b.take(8LL * dz * T);
+  L.sqref = b.take(8LL * T);
+  L.termref = b.take(8LL * T);
+  L.hwref = mat ? b.take(8LL * T) : 0;
+  L.score = b.take(8LL * HU);
+  L.hash = b.take(8LL * HU);
+  L.comp = b.take(4LL * T);
+  L.dthr = b.take(4LL * T);
+  L.logp = b.take(4LL * T);
+  L.log1mp = b.take(4LL * T);
+  L.mref = b.take(4LL * T);
+  L.refnew = mat ? b.take(4LL * T) : 0;
+  L.rowoff = b.take(4LL * (M + 1));
+  L.rowfill = b.take(4LL * (M + 1));
+  L.rowthr0 = b.take(4LL * M);
+  L.roww0 = b.take(4LL * M);
+  L.cthr = b.take(4LL * K);
+  L.ceidx = b.take(4LL * K);
+  L.cw = b.take(4LL * K);
+  L.dpc = b.take(4LL * (T / 4 + 2));
+  L.cslot = b.take(2LL * K);
+  L.rowref = b.take(2LL * M);
+  L.nalive = b.take(2LL * HU);
+  L.rowflag = b.take(M);
+  L.ninfref = b.take(T);
+  L.valid = b.take(HU);
+  L.grp = b.off;
+  Bump g;
+  L.g_se = g.take(8LL * dz * T);
+  L.g_sq = g.take(8LL * T);
+  L.g_hw = mat ? g.take(8LL * T) : 0;
+  L.g_cnt = g.take(4LL * T);
+  L.g_newval = mat ? g.take(4LL * T) : 0;
+  L.g_tmask = g.take(4LL * W);
+  L.g_dmask = g.take(4LL * W);
+  L.g_dpre = g.take(4LL * W);
+  L.g_nt = g.take(16);
+  L.g_tlist = g.take(2LL * T);
+  L.grp_bytes = g.off;
+  L.total = L.grp + G * L.grp_bytes;
+  return L;
+}
+
+int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int h_up,
+                      int n_groups) {
+  return make_lay(dz, materialize, T_max, K_max, M, h_up, n_groups).total;
+}
+
+int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
+                       int smem_limit) {
+  for (int G = 8; G >= 1; --G)
+    if (expand_smem_bytes(dz, materialize, T_max, K_max, M, h_up, G) <= smem_limit) return G;
+  return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T* at(unsigned char* base, int off) {
+  return reinterpret_cast<T*>(base + off);
+}
+
+__device__ __forceinline__ uint32_t thr_of(float frac) {
+  // smallest integer k0 with k0 >= frac * 2^24, clamped to [0, 2^24]
+  if (!(frac > 0.f)) return 0u;
+  if (frac >= 1.f) return kOne24;
+  return (uint32_t)ceilf(frac * 16777216.f);
+}
+
+__device__ __forceinline__ void touch(uint32_t* tmask, uint16_t* tlist, int* nt, int t) {
+  const uint32_t bit = 1u << (t & 31);
+  const uint32_t old = atomicOr(&tmask[t >> 5], bit);
+  if (!(old & bit)) tlist[atomicAdd(nt, 1)] = (uint16_t)t;
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t* m, int t) {
+  return (m[t >> 5] >> (t & 31)) & 1u;
+}
+
+// insert (component, detection-set key) into the update table; returns the
+// tagged hash slot to be resolved to a component index after the kernel
+template <int DZ>
+__device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long long hw, int m,
+                               const long long (&se)[DZ]) {
+  unsigned long long key = mix64(hw + 0x9E3779B97F4A7C15ULL * ((unsigned long long)comp + 1ULL));
+  if (key == 0ULL) key = 1ULL;
+  uint32_t slot = (uint32_t)key & a.hmask;
+  for (uint32_t probe = 0; probe <= a.hmask; ++probe) {
+    const unsigned long long prev = atomicCAS(&a.hkeys[slot], 0ULL, key);
+    if (prev == 0ULL) {
+      const uint32_t id = atomicAdd(a.upd_count, 1u);
+      if (id < (uint32_t)a.cap_upd) {
+        a.upd_src[id] = comp;
+        a.upd_m[id] = (uint32_t)m;
+#pragma unroll
+        for (int d = 0; d < DZ; ++d) a.upd_se[(size_t)d * a.cap_upd + id] = se[d];
+        a.hvals[slot] = id;
+      } else {
+        atomicOr(a.err, kErrUpdates);
+        a.hvals[slot] = 0u;
+      }
+      return kNewTag | slot;
+    }
+    if (prev == key) return kNewTag | slot;
+    slot = (slot + 1u) & a.hmask;
+  }
+  atomicOr(a.err, kErrHash);
+  return kNewTag;
+}
+
+template <int DZ, bool MAT>
+__global__ void __launch_bounds__(256) expand_kernel(const ExpandArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Model& md = a.md;
+  const int HU = md.h_up;
+  const int M = a.M;
+  const int h = blockIdx.x;
+  const Lay L = make_lay(DZ, MAT, a.T_max, a.K_max, M, HU, a.n_groups);
+  Scal& sc = *at<Scal>(sm, L.scal);
+  uint32_t* s_comp = at<uint32_t>(sm, L.comp);
+  uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
+  float* s_logp = at<float>(sm, L.logp);
+  float* s_log1mp = at<float>(sm, L.log1mp);
+  int* s_mref = at<int>(sm, L.mref);
+  long long* s_seref = at<long long>(sm, L.seref);
+  long long* s_sqref = at<long long>(sm, L.sqref);
+  long long* s_termref = at<long long>(sm, L.termref);
+  uint8_t* s_ninfref = at<uint8_t>(sm, L.ninfref);
+  unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
+  uint32_t* s_refnew = at<uint32_t>(sm, L.refnew);
+  uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
+  uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
+  uint16_t* s_rowref = at<uint16_t>(sm, L.rowref);
+  uint8_t* s_rowflag = at<uint8_t>(sm, L.rowflag);
+  uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
+  float* s_roww0 = at<float>(sm, L.roww0);
+  uint16_t* s_cslot = at<uint16_t>(sm, L.cslot);
+  uint32_t* s_cthr = at<uint32_t>(sm, L.cthr);
+  uint32_t* s_ceidx = at<uint32_t>(sm, L.ceidx);
+  float* s_cw = at<float>(sm, L.cw);
+  uint32_t* s_dpc = at<uint32_t>(sm, L.dpc);
+  long long* s_score = at<long long>(sm, L.score);
+  unsigned long long* s_hash = at<unsigned long long>(sm, L.hash);
+  uint8_t* s_valid = at<uint8_t>(sm, L.valid);
+  uint16_t* s_nalive = at<uint16_t>(sm, L.nalive);
+  const CompTable& ct = a.ct;
+  const PairTable& pt = a.pt;
+  const size_t capp = (size_t)pt.cap_pairs;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+
+  // ---- parent header ----
+  if (tid == 0) {
+    const uint32_t lo = a.parents.ptr[h], hi = a.parents.ptr[h + 1];
+    sc.Town = (int)(hi - lo);
+    sc.T = sc.Town + a.nb;
+    sc.ref_score = 0;
+    sc.ninf_ref = 0;
+    sc.nclut_ref = 0;
+    sc.ndpc = 0;
+    sc.bad = 0;
+    sc.uid = a.parents.uid[h];
+    sc.logw = a.parents.logw[h];
+    sc.s_lo = sc.s_hi = 0;
+    if (MAT) {
+      // survivors of this parent: child indices in [h*HU, (h+1)*HU)
+      const long long lo_key = (long long)h * HU, hi_key = lo_key + HU;
+      const int ns = (int)*a.n_surv;
+      int l = 0, r = ns;
+      while (l < r) { const int mid = (l + r) >> 1; if (a.surv_idx[mid] < lo_key) l = mid + 1; else r = mid; }
+      sc.s_lo = l;
+      r = ns;
+      while (l < r) { const int mid = (l + r) >> 1; if (a.surv_idx[mid] < hi_key) l = mid + 1; else r = mid; }
+      sc.s_hi = l;
+    }
+    if (sc.T > a.T_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+    // a frame already abandoned (e.g. entries beyond capacity) writes nothing
+    if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) sc.bad = 1;
+  }
+  __syncthreads();
+  if (sc.bad) return;
+  if (MAT && sc.s_lo == sc.s_hi) return;
+  const int T = sc.T, Town = sc.Town;
+  const uint32_t plo = a.parents.ptr[h];
+
+  // ---- slots ----
+  for (int t = tid; t < T; t += nthr) {
+    const uint32_t c = t < Town ? a.parents.comp[plo + t] : (uint32_t)(a.birth_base + (t - Town));
+    s_comp[t] = c;
+    s_dthr[t] = pt.dthr[c];
+    s_logp[t] = ct.logp[c];
+    s_log1mp[t] = ct.log1mp[c];
+    s_mref[t] = 0;
+#pragma unroll
+    for (int d = 0; d < DZ; ++d) s_seref[d * T + t] = 0;
+    s_sqref[t] = 0;
+    if (MAT) s_hwref[t] = 0;
+  }
+  for (int i = tid; i <= M; i += nthr) s_rowfill[i] = 0;
+  __syncthreads();
+  for (int t = tid; t < T; t += nthr) {
+    const uint32_t c = s_comp[t];
+    for (uint32_t j = pt.ptr[c], je = pt.ptr[c + 1]; j < je; ++j) atomicAdd(&s_rowfill[pt.meas[j]], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the row counts (single warp, serial carry over chunks)
+  if (tid < 32) {
+    uint32_t carry = 0;
+    for (int base = 0; base < M; base += 32) {
+      const int i = base + tid;
+      const uint32_t v = i < M ? s_rowfill[i] : 0u;
+      uint32_t x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (tid >= o) x += y;
+      }
+      if (i < M) s_rowoff[i] = carry + x - v;
+      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+    if (tid == 0) {
+      s_rowoff[M] = carry;
+      sc.K = (int)carry;
+      if ((int)carry > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+    }
+  }
+  __syncthreads();
+  if (sc.bad) return;
+  for (int i = tid; i < M; i += nthr) s_rowfill[i] = 0;
+  __syncthreads();
+  for (int t = tid; t < T; t += nthr) {
+    const uint32_t c = s_comp[t];
+    for (uint32_t j = pt.ptr[c], je = pt.ptr[c + 1]; j < je; ++j) {
+      const uint32_t i = pt.meas[j];
+      const uint32_t pos = s_rowoff[i] + atomicAdd(&s_rowfill[i], 1u);
+      s_cslot[pos] = (uint16_t)t;
+      s_ceidx[pos] = j;
+    }
+  }
+  __syncthreads();
+
+  // ---- rows: order, weights, thresholds, reference option ----
+  {
+    int my_clut = 0;
+    for (int i = tid; i < M; i += nthr) {
+      const uint32_t off = s_rowoff[i];
+      const int nc = (int)(s_rowoff[i + 1] - off);
+      for (int x = 1; x < nc; ++x) {   // insertion sort by slot
+        const uint16_t ks = s_cslot[off + x];
+        const uint32_t ke = s_ceidx[off + x];
+        int y = x - 1;
+        while (y >= 0 && s_cslot[off + y] > ks) {
+          s_cslot[off + y + 1] = s_cslot[off + y];
+          s_ceidx[off + y + 1] = s_ceidx[off + y];
+          --y;
+        }
+        s_cslot[off + y + 1] = ks;
+        s_ceidx[off + y + 1] = ke;
+      }
+      if (nc == 0) {
+        s_rowref[i] = 0;
+        s_rowflag[i] = 0;
+        s_rowthr0[i] = kOne24;
+        s_roww0[i] = 1.f;
+        ++my_clut;
+        continue;
+      }
+      float smax = md.kappa_zero ? -INFINITY : md.log_kappa;
+      for (int j = 0; j < nc; ++j) smax = fmaxf(smax, pt.logC[s_ceidx[off + j]]);
+      const float w0 = md.kappa_zero ? 0.f : expf(md.log_kappa - smax);
+      float sum = w0;
+      for (int j = 0; j < nc; ++j) {
+        const float w = expf(pt.logC[s_ceidx[off + j]] - smax);
+        s_cw[off + j] = w;
+        sum += w;
+      }
+      float cum = w0, best = w0;
+      int ref = 0;
+      bool flag = false;
+      s_rowthr0[i] = (nc == 0) ? kOne24 : thr_of(cum / sum);
+      for (int j = 0; j < nc; ++j) {
+        const float w = s_cw[off + j];
+        cum += w;
+        s_cthr[off + j] = (j == nc - 1) ? kOne24 : thr_of(cum / sum);
+        if (w > best) { best = w; ref = j + 1; }
+        flag |= s_dthr[s_cslot[off + j]] > 0u;
+      }
+      s_rowref[i] = (uint16_t)ref;
+      s_rowflag[i] = flag ? 1 : 0;
+      s_roww0[i] = w0;
+      if (ref == 0) {
+        ++my_clut;
+      } else {
+        const int r = s_cslot[off + ref - 1];
+        const uint32_t e = s_ceidx[off + ref - 1];
+        atomicAdd(&s_mref[r], 1);
+#pragma unroll
+        for (int d = 0; d < DZ; ++d)
+          atomicAdd((unsigned long long*)&s_seref[d * T + r], (unsigned long long)fx_of(pt.e[d * capp + e]));
+        atomicAdd((unsigned long long*)&s_sqref[r], (unsigned long long)fx_of(pt.q[e]));
+        if (MAT) atomicAdd(&s_hwref[r], wset_key(i));
+      }
+    }
+    if (my_clut) atomicAdd(&sc.nclut_ref, my_clut);
+  }
+  __syncthreads();
+
+  // ---- reference terms, death-possible chunks ----
+  {
+    long long my_term = 0;
+    int my_ninf = 0;
+    for (int t = tid; t < T; t += nthr) {
+      float HPH[DZ][DZ];
+      load_HPH<DZ>(ct, md.ncov, md.dx, (int)s_comp[t], HPH);
+      long long se[DZ];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t];
+      int ninf;
+      const long long term = alive_term<DZ>(md, HPH, s_logp[t], s_mref[t], se, s_sqref[t], ninf);
+      s_termref[t] = term;
+      s_ninfref[t] = (uint8_t)ninf;
+      my_term += term;
+      my_ninf += ninf;
+      if (MAT) {
+        s_refnew[t] = s_mref[t] >= 1 ? upd_insert<DZ>(a, s_comp[t], s_hwref[t], s_mref[t], se)
+                                     : s_comp[t];
+      }
+    }
+    if (my_term) atomicAdd((unsigned long long*)&sc.ref_score, (unsigned long long)my_term);
+    if (my_ninf) atomicAdd(&sc.ninf_ref, my_ninf);
+    const int nch = (T + 3) >> 2;
+    for (int cc = tid; cc < nch; cc += nthr) {
+      uint32_t mask = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int t = 4 * cc + b;
+        if (t < T && s_dthr[t] > 0u) mask |= 1u << b;
+      }
+      if (mask) s_dpc[atomicAdd(&sc.ndpc, 1)] = ((uint32_t)cc << 4) | mask;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    sc.ref_score += __double2ll_rn(sc.logw * 4294967296.0);
+    if (md.kappa_zero) sc.ninf_ref += sc.nclut_ref;
+    else sc.ref_score += (long long)sc.nclut_ref * md.fx_log_kappa;
+  }
+  __syncthreads();
+
+  // ---- draws, one warp per child ----
+  const int g = tid >> 5, lane = tid & 31;
+  unsigned char* gb = sm + L.grp + g * L.grp_bytes;
+  int* acc_cnt = at<int>(gb, L.g_cnt);
+  long long* acc_se = at<long long>(gb, L.g_se);
+  long long* acc_sq = at<long long>(gb, L.g_sq);
+  unsigned long long* acc_hw = at<unsigned long long>(gb, L.g_hw);
+  uint32_t* newval = at<uint32_t>(gb, L.g_newval);
+  uint32_t* tmask = at<uint32_t>(gb, L.g_tmask);
+  uint32_t* dmask = at<uint32_t>(gb, L.g_dmask);
+  uint32_t* dpre = at<uint32_t>(gb, L.g_dpre);
+  uint16_t* tlist = at<uint16_t>(gb, L.g_tlist);
+  int* ntp = at<int>(gb, L.g_nt);
+  const int W = (T + 31) >> 5;
+  for (int t = lane; t < T; t += 32) {
+    acc_cnt[t] = 0;
+#pragma unroll
+    for (int d = 0; d < DZ; ++d) acc_se[d * T + t] = 0;
+    acc_sq[t] = 0;
+    if (MAT) acc_hw[t] = 0;
+  }
+  for (int w = lane; w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
+  if (lane == 0) *ntp = 0;
+  __syncwarp();
+
+  const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
+  const int ndpc = sc.ndpc;
+  const int nrc = (M + 3) >> 2;
+  const long long ref_score = sc.ref_score;
+  const int ninf_ref = sc.ninf_ref;
+  const int n_items = MAT ? (sc.s_hi - sc.s_lo) : HU;
+  for (int it = g; it < n_items; it += a.n_groups) {
+    const int n = MAT ? (int)(a.surv_idx[sc.s_lo + it] - (long long)h * HU) : it;
+    const int s_out = MAT ? sc.s_lo + it : 0;
+    // phase 1: deaths
+    int my_dead = 0;
+    unsigned long long hsh = 0;
+    for (int x = lane; x < ndpc; x += 32) {
+      const uint32_t ent = s_dpc[x];
+      const uint32_t cc = ent >> 4, mask = ent & 15u;
+      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), a.key);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (!((mask >> b) & 1u)) continue;
+        const int t = 4 * (int)cc + b;
+        if ((word_of(r, b) >> 8) < s_dthr[t]) {
+          atomicOr(&dmask[t >> 5], 1u << (t & 31));
+          touch(tmask, tlist, ntp, t);
+          ++my_dead;
+          hsh += dead_key(t);
+        }
+      }
+    }
+    __syncwarp();
+    if (MAT) {
+      uint32_t carry = 0;
+      for (int base = 0; base < W; base += 32) {
+        const int w = base + lane;
+        const uint32_t v = w < W ? (uint32_t)__popc(dmask[w]) : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (w < W) dpre[w] = carry + x - v;
+        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+      }
+      __syncwarp();
+    }
+    // phase 2: one categorical draw per detection row
+    int my_dclut = 0;
+    bool bad_row = false;
+    for (int cc = lane; cc < nrc; cc += 32) {
+      const int i0 = 4 * cc;
+      const int i1 = min(i0 + 4, M);
+      if (s_rowoff[i1] == s_rowoff[i0]) {
+        if (MAT)
+          for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
+        continue;
+      }
+      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), a.key);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = i0 + b;
+        if (i >= i1) break;
+        const uint32_t off = s_rowoff[i];
+        const int nc = (int)(s_rowoff[i + 1] - off);
+        if (nc == 0) {
+          if (MAT) a.out_theta[(size_t)s_out * M + i] = 0;
+          continue;
+        }
+        const uint32_t k = word_of(r, b) >> 8;
+        bool fast = true;
+        if (s_rowflag[i])
+          for (int j = 0; j < nc; ++j)
+            if (bit_of(dmask, s_cslot[off + j])) { fast = false; break; }
+        int opt;
+        if (fast) {
+          if (k < s_rowthr0[i]) {
+            opt = 0;
+          } else {
+            int j = 0;
+            while (j < nc - 1 && k >= s_cthr[off + j]) ++j;
+            opt = j + 1;
+          }
+        } else {
+          const float w0 = md.kappa_zero ? 0.f : s_roww0[i];
+          float sum = w0;
+          for (int j = 0; j < nc; ++j)
+            if (!bit_of(dmask, s_cslot[off + j])) sum += s_cw[off + j];
+          if (!(sum > 0.f)) {
+            bad_row = true;
+            opt = 0;
+          } else {
+            const float xk = (float)k * 5.9604644775390625e-8f * sum;
+            float cum = w0;
+            int last = w0 > 0.f ? 0 : -1;
+            opt = -1;
+            if (w0 > 0.f && xk < cum) opt = 0;
+            for (int j = 0; j < nc; ++j) {
+              if (bit_of(dmask, s_cslot[off + j])) continue;
+              const float w = s_cw[off + j];
+              if (!(w > 0.f)) continue;
+              cum += w;
+              last = j + 1;
+              if (opt < 0 && xk < cum) opt = j + 1;
+            }
+            if (opt < 0) opt = last < 0 ? 0 : last;
+          }
+        }
+        const int ref = s_rowref[i];
+        int ns = -1;
+        if (opt > 0) ns = s_cslot[off + opt - 1];
+        if (opt != ref) {
+          int rs = -1;
+          if (ref > 0) {
+            rs = s_cslot[off + ref - 1];
+            const uint32_t e = s_ceidx[off + ref - 1];
+            atomicSub(&acc_cnt[rs], 1);
+#pragma unroll
+            for (int d = 0; d < DZ; ++d)
+              atomicAdd((unsigned long long*)&acc_se[d * T + rs], (unsigned long long)(-fx_of(pt.e[d * capp + e])));
+            atomicAdd((unsigned long long*)&acc_sq[rs], (unsigned long long)(-fx_of(pt.q[e])));
+            if (MAT) atomicAdd(&acc_hw[rs], (unsigned long long)(0ULL - wset_key(i)));
+            touch(tmask, tlist, ntp, rs);
+          } else {
+            --my_dclut;
+          }
+          if (opt > 0) {
+            const uint32_t e = s_ceidx[off + opt - 1];
+            atomicAdd(&acc_cnt[ns], 1);
+#pragma unroll
+            for (int d = 0; d < DZ; ++d)
+              atomicAdd((unsigned long long*)&acc_se[d * T + ns], (unsigned long long)fx_of(pt.e[d * capp + e]));
+            atomicAdd((unsigned long long*)&acc_sq[ns], (unsigned long long)fx_of(pt.q[e]));
+            if (MAT) atomicAdd(&acc_hw[ns], wset_key(i));
+            touch(tmask, tlist, ntp, ns);
+          } else {
+            ++my_dclut;
+          }
+          hsh += row_key(i, opt > 0 ? ns + 1 : 0) - row_key(i, ref > 0 ? rs + 1 : 0);
+        }
+        if (MAT) {
+          uint16_t th = 0;
+          if (ns >= 0) {
+            const uint32_t below = dpre[ns >> 5] + __popc(dmask[ns >> 5] & ((1u << (ns & 31)) - 1u));
+            th = (uint16_t)(ns - (int)below + 1);
+          }
+          a.out_theta[(size_t)s_out * M + i] = th;
+        }
+      }
+    }
+    __syncwarp();
+    // phase 3: rescore touched slots
+    const int nt = *((volatile int*)ntp);
+    long long my_delta = 0;
+    int my_dninf = 0;
+    for (int x = lane; x < nt; x += 32) {
+      const int t = tlist[x];
+      int ninf;
+      long long term;
+      long long se[DZ];
+      int m = 0;
+      const bool dead = bit_of(dmask, t);
+      if (dead) {
+        term = dead_term(s_log1mp[t], ninf);
+      } else {
+        float HPH[DZ][DZ];
+        load_HPH<DZ>(ct, md.ncov, md.dx, (int)s_comp[t], HPH);
+        m = s_mref[t] + acc_cnt[t];
+#pragma unroll
+        for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + acc_se[d * T + t];
+        term = alive_term<DZ>(md, HPH, s_logp[t], m, se, s_sqref[t] + acc_sq[t], ninf);
+      }
+      my_delta += term - s_termref[t];
+      my_dninf += ninf - (int)s_ninfref[t];
+      if (MAT && !dead)
+        newval[t] = m >= 1 ? upd_insert<DZ>(a, s_comp[t], s_hwref[t] + acc_hw[t], m, se) : s_comp[t];
+      acc_cnt[t] = 0;
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) acc_se[d * T + t] = 0;
+      acc_sq[t] = 0;
+      if (MAT) acc_hw[t] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      my_delta += __shfl_xor_sync(0xFFFFFFFFu, my_delta, o);
+      my_dninf += __shfl_xor_sync(0xFFFFFFFFu, my_dninf, o);
+      my_dclut += __shfl_xor_sync(0xFFFFFFFFu, my_dclut, o);
+      my_dead += __shfl_xor_sync(0xFFFFFFFFu, my_dead, o);
+      hsh += __shfl_xor_sync(0xFFFFFFFFu, hsh, o);
+    }
+    const bool any_bad = __any_sync(0xFFFFFFFFu, bad_row);
+    __syncwarp();
+    if (MAT) {
+      const uint32_t base = a.out_ptr[s_out];
+      for (int t = lane; t < T; t += 32) {
+        if (bit_of(dmask, t)) continue;
+        const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
+        a.out_comp[base + (uint32_t)t - below] = bit_of(tmask, t) ? newval[t] : s_refnew[t];
+      }
+      __syncwarp();
+    }
+    for (int w = lane; w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
+    if (lane == 0) {
+      *ntp = 0;
+      if (!MAT) {
+        const long long score = ref_score + my_delta + (md.kappa_zero ? 0LL : (long long)my_dclut * md.fx_log_kappa);
+        const int ninf = ninf_ref + my_dninf + (md.kappa_zero ? my_dclut : 0);
+        s_score[n] = score;
+        s_hash[n] = hsh;
+        s_valid[n] = (!any_bad && ninf == 0) ? 1 : 0;
+        s_nalive[n] = (uint16_t)(T - my_dead);
+      }
+    }
+    __syncwarp();
+  }
+  if (MAT) return;
+  __syncthreads();
+  // ---- unique children of this parent (lowest draw kept) ----
+  for (int n = tid; n < HU; n += nthr) {
+    const size_t j = (size_t)h * HU + n;
+    int8_t st = 0;
+    long long key = kKeyInvalid;
+    if (s_valid[n]) {
+      st = 1;
+      const unsigned long long hv = s_hash[n];
+      for (int n2 = 0; n2 < n; ++n2)
+        if (s_valid[n2] && s_hash[n2] == hv) { st = 2; break; }
+      if (st == 1) key = s_score[n];
+    }
+    a.child_key[j] = key;
+    a.child_status[j] = st;
+    a.child_alive[j] = s_nalive[n];
+  }
+}
+
+void launch_expand(const ExpandArgs& a, cudaStream_t s) {
+  const int nblk = a.H;
+  if (nblk <= 0) return;
+  const int threads = 32 * a.n_groups;
+  if (a.md.dz == 2) {
+    if (a.materialize) {
+      cudaFuncSetAttribute(expand_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+      expand_kernel<2, true><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
+    } else {
+      cudaFuncSetAttribute(expand_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+      expand_kernel<2, false><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
+    }
+  } else {
+    if (a.materialize) {
+      cudaFuncSetAttribute(expand_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+      expand_kernel<3, true><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
+    } else {
+      cudaFuncSetAttribute(expand_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
+      expand_kernel<3, false><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
+    }
+  }
+}
+
+}  // namespace glmb

@@ -1,0 +1,727 @@
+// Normalisation, truncation and the batched track update of the retained
+// children (arXiv 2512.06230, Section 3: weights below tau are discarded,
+// the H_max most likely hypotheses are kept, and one update is run per
+// distinct (track, detection set)), plus the estimate reductions.
+#include "../../include/glmb.h"
+#include "glmb_kernels.h"
+
+namespace glmb {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Global log-sum-exp over unique children, FP64.  Two grid passes (max, then
+// sum of exp); each pass's last block combines the per-block partials in
+// block order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+__global__ void lse_max_kernel(const long long* __restrict__ keys, long long n, PruneWork w) {
+  __shared__ long long red[kRedThreads / 32];
+  __shared__ bool last;
+  long long m = kKeyInvalid;
+  unsigned valid = 0;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long k = keys[j];
+    m = max(m, k);
+    valid += (k != kKeyInvalid);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) valid += __shfl_xor_sync(0xFFFFFFFFu, valid, o);
+  if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&w.counts[2], valid);
+  m = warp_max_ll(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long v = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : kKeyInvalid;
+    v = warp_max_ll(v);
+    if (threadIdx.x == 0) {
+      w.blk_max[blockIdx.x] = v;
+      __threadfence();
+      last = atomicAdd(&w.blk_done[0], 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    long long g = kKeyInvalid;
+    for (unsigned b = 0; b < gridDim.x; ++b) g = max(g, ((volatile long long*)w.blk_max)[b]);
+    w.blk_max[gridDim.x] = g;
+    w.blk_done[0] = 0;
+  }
+}
+
+__global__ void lse_sum_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
+                               double log_tau, int h_max) {
+  __shared__ double red[kRedThreads / 32];
+  __shared__ bool last;
+  const long long g = w.blk_max[gridDim.x];
+  double s = 0.0;
+  if (g != kKeyInvalid)
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+      const long long k = keys[j];
+      if (k != kKeyInvalid) s += exp((double)(k - g) * kFxInv);
+    }
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : 0.0;
+    v = warp_sum_d(v);
+    if (threadIdx.x == 0) {
+      w.blk_sum[blockIdx.x] = v;
+      __threadfence();
+      last = atomicAdd(&w.blk_done[1], 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double S = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) S += ((volatile double*)w.blk_sum)[b];
+    w.blk_done[1] = 0;
+    if (g == kKeyInvalid || !(S > 0.0)) {
+      w.lse[0] = -INFINITY;
+      w.thr[0] = LLONG_MAX;
+      w.sel[3] = 2;   // nothing to keep
+    } else {
+      const double lse = (double)g * kFxInv + log(S);
+      w.lse[0] = lse;
+      w.thr[0] = (long long)ceil((lse + log_tau) * 4294967296.0);
+      w.sel[3] = 0;
+    }
+    w.sel[0] = 0;        // radix prefix
+    w.sel[1] = h_max;    // still needed
+    w.sel[2] = 0;        // boundary key
+  }
+}
+
+void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau, int h_max,
+                int nblk, cudaStream_t s) {
+  lse_max_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w); ++g_launches;
+  lse_sum_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w, log_tau, h_max); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Top-H_max by 12-bit radix select on v = key - thr (>= 0 for candidates).
+// sel[0] prefix of the selected digits, sel[1] elements still needed,
+// sel[2] boundary key, sel[3] 0 running / 1 done-keep-all / 2 empty.
+// ---------------------------------------------------------------------------
+constexpr int kDigit = 12, kBins = 1 << kDigit;
+
+__global__ void radix_hist_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
+                                  int shift) {
+  __shared__ unsigned hist[kBins];
+  if (w.sel[3] != 0) return;
+  for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const long long thr = w.thr[0];
+  const unsigned long long prefix = (unsigned long long)w.sel[0];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long k = keys[j];
+    if (k == kKeyInvalid || k < thr) continue;
+    const unsigned long long v = (unsigned long long)(k - thr);
+    if ((v >> (shift + kDigit)) != prefix) continue;
+    atomicAdd(&hist[(v >> shift) & (kBins - 1)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBins; b += blockDim.x)
+    if (hist[b]) atomicAdd(&w.hist[b], hist[b]);
+}
+
+__global__ void radix_find_kernel(PruneWork w, int shift, int first) {
+  // one warp: lane l owns bins [l*128, l*128+128), highest bins first
+  if (w.sel[3] != 0) {
+    for (int b = threadIdx.x; b < kBins; b += 32) w.hist[b] = 0;
+    return;
+  }
+  const int lane = threadIdx.x;
+  constexpr int per = kBins / 32;
+  unsigned mine = 0;
+  for (int b = 0; b < per; ++b) mine += w.hist[lane * per + b];
+  // counts above lane l: sum of lanes > l
+  unsigned above = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_down_sync(0xFFFFFFFFu, above, o);
+    if (lane + o < 32) above += y;
+  }
+  const unsigned total = __shfl_sync(0xFFFFFFFFu, above, 0);
+  above -= mine;   // strictly above this lane
+  const long long need = w.sel[1];
+  __syncwarp();
+  if (first && (long long)total <= need) {
+    if (lane == 0) {
+      w.sel[3] = 1;
+      w.sel[2] = w.thr[0] - 1;   // every candidate is above the boundary
+      w.sel[1] = 0;
+    }
+  } else {
+    const bool hit = (long long)above < need && (long long)(above + mine) >= need;
+    if (hit) {
+      unsigned cum = above;
+      int b = lane * per + per - 1;
+      for (; b >= lane * per; --b) {
+        const unsigned hb = w.hist[b];
+        if ((long long)(cum + hb) >= need) break;
+        cum += hb;
+      }
+      w.sel[0] = (w.sel[0] << kDigit) | b;
+      w.sel[1] = need - cum;
+      if (shift == 0) w.sel[2] = w.thr[0] + w.sel[0];
+    }
+  }
+  __syncwarp();
+  for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+}
+
+void launch_select(const long long* keys, long long n, int h_max, int nbits, PruneWork w,
+                   int nblk, cudaStream_t s) {
+  (void)h_max;
+  const int passes = (nbits + kDigit - 1) / kDigit;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = (passes - 1 - p) * kDigit;
+    radix_hist_kernel<<<nblk, 256, 0, s>>>(keys, n, w, shift); ++g_launches;
+    radix_find_kernel<<<1, 32, 0, s>>>(w, shift, p == 0); ++g_launches;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stable compaction of the retained children in (parent, draw) order:
+// gt = key > boundary, eq = key == boundary (the first sel[1] of these in
+// index order are kept).  One packed scan gives both prefix counts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long keep_bits(long long k, long long thr, long long bnd,
+                                                        long long need_eq, long long mode) {
+  if (mode == 2 || k == kKeyInvalid || k < thr) return 0ULL;
+  if (k > bnd) return 1ULL;
+  if (k == bnd && need_eq > 0) return 1ULL << 32;
+  return 0ULL;
+}
+
+__global__ void keep_flags_kernel(const long long* __restrict__ keys, long long n, PruneWork w) {
+  const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    w.flags[j] = keep_bits(keys[j], thr, bnd, need, mode);
+}
+
+__global__ void keep_write_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
+                                  int h_max) {
+  const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long f = keep_bits(keys[j], thr, bnd, need, mode);
+    if (!f) continue;
+    const unsigned long long pre = w.flags[j];
+    const long long gt = (long long)(pre & 0xFFFFFFFFULL), eq = (long long)(pre >> 32);
+    if ((f >> 32) && eq >= need) continue;
+    const long long pos = gt + min(eq, need);
+    if (pos < h_max) w.surv_idx[pos] = j;
+  }
+}
+
+void launch_compact(const long long* keys, long long n, PruneWork w, int h_max,
+                    cudaStream_t s) {
+  const int nb = (int)min((n + 255) / 256, 4096LL);
+  keep_flags_kernel<<<nb, 256, 0, s>>>(keys, n, w); ++g_launches;
+  scan_u64(w.flags, w.flags, n, (unsigned long long*)(w.counts + 4), w.flags_tmp, s);
+  keep_write_kernel<<<nb, 256, 0, s>>>(keys, n, w, h_max); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Survivors: renormalised FP64 log-weights, child uids, CSR offsets.
+// counts[0] survivors, counts[1] entries, counts[4..5] packed scan total.
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
+                                const uint16_t* __restrict__ child_alive, HypTable parents,
+                                int h_up, HypTable out, int h_max, unsigned* err,
+                                long long cap_entries) {
+  __shared__ double red[32];
+  __shared__ long long s_n;
+  __shared__ double s_m, s_lse;
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    const unsigned long long tot = *(const unsigned long long*)(w.counts + 4);
+    long long n = 0;
+    if (w.sel[3] != 2) n = (long long)(tot & 0xFFFFFFFFULL) + min((long long)(tot >> 32), (long long)w.sel[1]);
+    if (n > h_max) n = h_max;
+    s_n = n;
+    w.counts[0] = (unsigned)n;
+    carry = 0;
+  }
+  __syncthreads();
+  const long long n = s_n;
+  const double lse_all = w.lse[0];
+  // max
+  double m = -INFINITY;
+  for (long long s = tid; s < n; s += nthr) m = fmax(m, (double)keys[w.surv_idx[s]] * kFxInv - lse_all);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  if (tid == 0) {
+    double g = -INFINITY;
+    for (int k = 0; k < (nthr + 31) / 32; ++k) g = fmax(g, red[k]);
+    s_m = g;
+  }
+  __syncthreads();
+  double sum = 0.0;
+  for (long long s = tid; s < n; s += nthr) sum += exp((double)keys[w.surv_idx[s]] * kFxInv - lse_all - s_m);
+  sum = warp_sum_d(sum);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    double S = 0.0;
+    for (int k = 0; k < (nthr + 31) / 32; ++k) S += red[k];
+    s_lse = s_m + log(S);
+    w.lse[1] = s_lse;
+  }
+  __syncthreads();
+  for (long long base = 0; base < n; base += nthr) {
+    const long long s = base + tid;
+    uint32_t na = 0;
+    if (s < n) {
+      const long long j = w.surv_idx[s];
+      out.logw[s] = (double)keys[j] * kFxInv - lse_all - s_lse;
+      const long long hpar = j / h_up, nd = j % h_up;
+      out.uid[s] = mix64(parents.uid[hpar] + 0x9E3779B97F4A7C15ULL * (unsigned long long)(nd + 1));
+      na = child_alive[j];
+    }
+    // block exclusive scan of na
+    uint32_t x = na;
+    const int lane = tid & 31, wp = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    __shared__ uint32_t ws[32];
+    if (lane == 31) ws[wp] = x;
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t v = tid < (nthr + 31) / 32 ? ws[tid] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (tid >= o) v += y;
+      }
+      ws[tid] = v;
+    }
+    __syncthreads();
+    const uint32_t excl = carry + (wp > 0 ? ws[wp - 1] : 0u) + x - na;
+    if (s < n) out.ptr[s] = excl;
+    __syncthreads();
+    if (tid == 0) carry += ws[(nthr + 31) / 32 - 1];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out.ptr[n] = carry;
+    w.counts[1] = carry;
+    if ((long long)carry > cap_entries) atomicOr(err, kErrEntries);
+  }
+}
+
+void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
+                     const HypTable& parents, int h_up, HypTable out, int h_max, unsigned* err,
+                     long long cap_entries, cudaStream_t s) {
+  finalize_kernel<<<1, 1024, 0, s>>>(w, keys, child_alive, parents, h_up, out, h_max, err,
+                                     cap_entries); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Garbage collection of components and the batched track update (Kalman
+// with the mean detection and R/m, Joseph form).
+// ---------------------------------------------------------------------------
+__global__ void mark_old_kernel(const uint32_t* __restrict__ out_comp,
+                                const unsigned* __restrict__ n_entries, long long cap,
+                                const unsigned* err, uint32_t* flag) {
+  if (*(volatile const unsigned*)err & kErrFatal) return;
+  const long long n = min((long long)*n_entries, cap);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const uint32_t v = out_comp[e];
+    if (!(v & kNewTag)) flag[v] = 1u;
+  }
+}
+
+void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
+                     const unsigned* err, uint32_t* flag, cudaStream_t s) {
+  const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
+  mark_old_kernel<<<nb, 256, 0, s>>>(out_comp, n_entries_dev, cap, err, flag); ++g_launches;
+}
+
+template <int DZ>
+__device__ void copy_comp(const Model& md, const CompTable& src, int c, const CompTable& dst, int d) {
+  constexpr int DX = 2 * DZ;
+  const size_t cs = src.cap, cd = dst.cap;
+#pragma unroll
+  for (int a = 0; a < DX; ++a) {
+    dst.mhi[a * cd + d] = src.mhi[a * cs + c];
+    dst.mlo[a * cd + d] = src.mlo[a * cs + c];
+  }
+#pragma unroll
+  for (int k = 0; k < DX * (DX + 1) / 2; ++k) dst.cov[k * cd + d] = src.cov[k * cs + c];
+  dst.lk[d] = src.lk[c];
+  dst.lb[d] = src.lb[c];
+  dst.logp[d] = src.logp[c];
+  dst.log1mp[d] = src.log1mp[c];
+}
+
+template <int DZ>
+__device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
+                            const long long (&se)[DZ], const CompTable& dst, int d) {
+  constexpr int DX = 2 * DZ;
+  const size_t cs = src.cap, cd = dst.cap;
+  float P[DX][DX];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = i; j < DX; ++j) {
+      const float v = src.cov[(size_t)pidx(DX, i, j) * cs + c];
+      P[i][j] = v;
+      P[j][i] = v;
+    }
+  const float inv_m = 1.f / (float)m;
+  float ebar[DZ], S[DZ][DZ], Rm[DZ][DZ];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) {
+    ebar[a] = (float)((double)se[a] * kFxInv) * inv_m;
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      Rm[a][b] = md.R[a * DZ + b] * inv_m;
+      S[a][b] = P[a][b] + Rm[a][b];
+    }
+  }
+  // S^-1 from the Cholesky factor (FP64 when ill-conditioned)
+  float Si[DZ][DZ];
+  {
+    float L[DZ][DZ], ld;
+    if (chol_n<float, DZ>(S, L, ld, 1.1920929e-7f)) {
+      float Li[DZ][DZ];
+#pragma unroll
+      for (int j = 0; j < DZ; ++j)
+#pragma unroll
+        for (int i = 0; i < DZ; ++i) {
+          float t = (i == j) ? 1.f : 0.f;
+#pragma unroll
+          for (int k = 0; k < i; ++k) t -= L[i][k] * Li[k][j];
+          Li[i][j] = (i < j) ? 0.f : t / L[i][i];
+        }
+#pragma unroll
+      for (int i = 0; i < DZ; ++i)
+#pragma unroll
+        for (int j = 0; j < DZ; ++j) {
+          float t = 0.f;
+#pragma unroll
+          for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
+          Si[i][j] = t;
+        }
+    } else {
+      double Sd[DZ][DZ], Ld[DZ][DZ], ldd, Li[DZ][DZ];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a)
+#pragma unroll
+        for (int b = 0; b < DZ; ++b) Sd[a][b] = S[a][b];
+      if (!chol_n<double, DZ>(Sd, Ld, ldd, 2.220446049250313e-16)) return false;
+#pragma unroll
+      for (int j = 0; j < DZ; ++j)
+#pragma unroll
+        for (int i = 0; i < DZ; ++i) {
+          double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+          for (int k = 0; k < i; ++k) t -= Ld[i][k] * Li[k][j];
+          Li[i][j] = (i < j) ? 0.0 : t / Ld[i][i];
+        }
+#pragma unroll
+      for (int i = 0; i < DZ; ++i)
+#pragma unroll
+        for (int j = 0; j < DZ; ++j) {
+          double t = 0.0;
+#pragma unroll
+          for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
+          Si[i][j] = (float)t;
+        }
+    }
+  }
+  float K[DX][DZ];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      float t = 0.f;
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t += P[i][a] * Si[a][b];
+      K[i][b] = t;
+    }
+#pragma unroll
+  for (int i = 0; i < DX; ++i) {
+    float delta = 0.f;
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) delta += K[i][b] * ebar[b];
+    float hi = src.mhi[i * cs + c], lo = src.mlo[i * cs + c];
+    df_add(hi, lo, delta);
+    dst.mhi[i * cd + d] = hi;
+    dst.mlo[i * cd + d] = lo;
+  }
+  // Joseph form: (I - K H) P (I - K H)^T + K (R/m) K^T
+  float AP[DX][DX];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = 0; j < DX; ++j) {
+      float t = P[i][j];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t -= K[i][a] * P[a][j];
+      AP[i][j] = t;
+    }
+  float KR[DX][DZ];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      float t = 0.f;
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t += K[i][a] * Rm[a][b];
+      KR[i][b] = t;
+    }
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = i; j < DX; ++j) {
+      float t = AP[i][j], t2 = AP[j][i];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) {
+        t -= AP[i][a] * K[j][a];
+        t2 -= AP[j][a] * K[i][a];
+      }
+      float r = 0.f;
+#pragma unroll
+      for (int b = 0; b < DZ; ++b) r += KR[i][b] * K[j][b];
+      dst.cov[(size_t)pidx(DX, i, j) * cd + d] = 0.5f * (t + t2) + r;
+    }
+  dst.lk[d] = src.lk[c];
+  dst.lb[d] = src.lb[c];
+  dst.logp[d] = src.logp[c];
+  dst.log1mp[d] = src.log1mp[c];
+  return true;
+}
+
+template <int DZ>
+__global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
+                          const uint32_t* __restrict__ flag, int n_src,
+                          const unsigned* __restrict__ n_keep_dev, const uint32_t* __restrict__ upd_src,
+                          const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,
+                          int cap_upd, const unsigned* __restrict__ n_upd_dev,
+                          const unsigned* __restrict__ n_surv_dev, unsigned* err) {
+  if (*n_surv_dev == 0u || (*(volatile unsigned*)err & kErrFatal)) return;
+  const unsigned n_keep = *n_keep_dev;
+  const unsigned n_upd = min(*n_upd_dev, (unsigned)cap_upd);
+  if ((long long)n_keep + n_upd > dst.cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrComps);
+    return;
+  }
+  const long long total = (long long)n_src + n_upd;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    if (x < n_src) {
+      const int c = (int)x;
+      if (flag[c]) copy_comp<DZ>(md, src, c, dst, (int)newpos[c]);
+    } else {
+      const int u = (int)(x - n_src);
+      long long se[DZ];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) se[a] = upd_se[(size_t)a * cap_upd + u];
+      if (!kalman_comp<DZ>(md, src, (int)upd_src[u], (int)upd_m[u], se, dst, (int)n_keep + u))
+        atomicOr(err, kErrNumeric);
+    }
+  }
+}
+
+void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
+                           const uint32_t* newpos, const uint32_t* flag, int n_src,
+                           const unsigned* n_keep_dev, const uint32_t* upd_src,
+                           const uint32_t* upd_m, const long long* upd_se, int cap_upd,
+                           const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
+                           cudaStream_t s) {
+  const long long bound = (long long)n_src + cap_upd;
+  const int nb = (int)max(1LL, min((bound + 127) / 128, 2048LL));
+  if (md.dz == 2) {
+    gc_kernel<2><<<nb, 128, 0, s>>>(md, src, dst, newpos, flag, n_src, n_keep_dev, upd_src, upd_m,
+                                    upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
+  } else {
+    gc_kernel<3><<<nb, 128, 0, s>>>(md, src, dst, newpos, flag, n_src, n_keep_dev, upd_src, upd_m,
+                                    upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
+  }
+  ++g_launches;
+}
+
+__global__ void remap_kernel(uint32_t* out_comp, const unsigned* __restrict__ n_entries,
+                             long long cap, const uint32_t* __restrict__ newpos,
+                             const uint32_t* __restrict__ hvals,
+                             const unsigned* __restrict__ n_keep_dev, const unsigned* err) {
+  if (*(volatile const unsigned*)err & kErrFatal) return;
+  const long long n = min((long long)*n_entries, cap);
+  const uint32_t n_keep = *n_keep_dev;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const uint32_t v = out_comp[e];
+    out_comp[e] = (v & kNewTag) ? n_keep + hvals[v & ~kNewTag] : newpos[v];
+  }
+}
+
+void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
+                  const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
+                  const unsigned* err, cudaStream_t s) {
+  const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
+  remap_kernel<<<nb, 256, 0, s>>>(out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Estimates: cardinality distribution, MAP cardinality, heaviest hypothesis
+// of that cardinality (ties to the lower index), label existence, and the
+// clutter probability of each detection.
+// ---------------------------------------------------------------------------
+__global__ void card_kernel(HypTable hp, int H, double* pmf, int pmf_cap, int* nhat_best) {
+  __shared__ int s_nhat;
+  __shared__ double bw[32];
+  __shared__ int bi[32];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int n = tid; n < pmf_cap; n += nthr) pmf[n] = 0.0;
+  __syncthreads();
+  for (int h = tid; h < H; h += nthr) {
+    const int n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
+    if (n < pmf_cap) atomicAdd(&pmf[n], exp(hp.logw[h]));
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (tid == 0) {
+    int best = 0;
+    for (int n = 1; n < pmf_cap; ++n)
+      if (pmf[n] > pmf[best]) best = n;
+    s_nhat = best;
+  }
+  __syncthreads();
+  double bwv = -INFINITY;
+  int biv = -1;
+  for (int h = tid; h < H; h += nthr) {
+    if ((int)(hp.ptr[h + 1] - hp.ptr[h]) != s_nhat) continue;
+    const double lw = hp.logw[h];
+    if (lw > bwv || (lw == bwv && h < biv)) { bwv = lw; biv = h; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w2 = __shfl_xor_sync(0xFFFFFFFFu, bwv, o);
+    const int i2 = __shfl_xor_sync(0xFFFFFFFFu, biv, o);
+    if (w2 > bwv || (w2 == bwv && i2 >= 0 && (biv < 0 || i2 < biv))) { bwv = w2; biv = i2; }
+  }
+  if ((tid & 31) == 0) { bw[tid >> 5] = bwv; bi[tid >> 5] = biv; }
+  __syncthreads();
+  if (tid == 0) {
+    double w = -INFINITY;
+    int b = -1;
+    for (int k = 0; k < (nthr + 31) / 32; ++k)
+      if (bi[k] >= 0 && (bw[k] > w || (bw[k] == w && bi[k] < b))) { w = bw[k]; b = bi[k]; }
+    nhat_best[0] = s_nhat;
+    nhat_best[1] = b;
+  }
+}
+
+void launch_card(const HypTable& hp, int H, double* pmf, int pmf_cap, int* nhat_best,
+                 cudaStream_t s) {
+  card_kernel<<<1, 1024, 0, s>>>(hp, H, pmf, pmf_cap, nhat_best); ++g_launches;
+}
+
+// r[j] = sum_h w_h [label of MAP track j in hypothesis h]; hypotheses list
+// their tracks in label order, so each is a binary search.
+__global__ void existence_kernel(HypTable hp, int H, CompTable ct, const int* __restrict__ nb,
+                                 double* r) {
+  const int best = nb[1];
+  if (best < 0) return;
+  const uint32_t b0 = hp.ptr[best], nmap = hp.ptr[best + 1] - b0;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < (long long)H * nmap;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(x / nmap), j = (int)(x % nmap);
+    const uint32_t c = hp.comp[b0 + j];
+    const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
+    uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t cm = hp.comp[mid];
+      const unsigned long long km = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
+      if (km < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo < hp.ptr[h + 1]) {
+      const uint32_t cm = hp.comp[lo];
+      if (ct.lk[cm] == ct.lk[c] && ct.lb[cm] == ct.lb[c]) atomicAdd(&r[j], exp(hp.logw[h]));
+    }
+  }
+}
+
+void launch_existence(const HypTable& hp, int H, const CompTable& ct, const int* nhat_best,
+                      double* r, cudaStream_t s) {
+  existence_kernel<<<304, 256, 0, s>>>(hp, H, ct, nhat_best, r); ++g_launches;
+}
+
+__global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double s = 0.0;
+  for (int h = 0; h < H; ++h)
+    if (hp.theta[(size_t)h * M + i] == 0) s += exp(hp.logw[h]);
+  r_u[i] = s;
+}
+
+void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s) {
+  if (M <= 0) return;
+  meas_assoc_kernel<<<(M + 127) / 128, 128, 0, s>>>(hp, H, M, r_u); ++g_launches;
+}
+
+// MAP hypothesis tracks as glmb_track records: labels, existence, mean
+// (hi + lo in FP64) and the full covariance.
+__global__ void gather_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* __restrict__ nb,
+                                     const double* __restrict__ r, glmb_track* out, int cap) {
+  const int best = nb[1];
+  if (best < 0) return;
+  const uint32_t b0 = hp.ptr[best];
+  const int n = min((int)(hp.ptr[best + 1] - b0), cap);
+  const size_t cc = ct.cap;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t c = hp.comp[b0 + j];
+    glmb_track& t = out[j];
+    t.label_k = ct.lk[c];
+    t.label_b = ct.lb[c];
+    t.r = r[j];
+    for (int a = 0; a < 6; ++a)
+      t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
+    for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
+    for (int i = 0; i < dx; ++i)
+      for (int k = i; k < dx; ++k) {
+        const double v = ct.cov[(size_t)pidx(dx, i, k) * cc + c];
+        t.cov[i * dx + k] = v;
+        t.cov[k * dx + i] = v;
+      }
+  }
+}
+
+void launch_gather_tracks(const HypTable& hp, const CompTable& ct, int dx, const int* nhat_best,
+                          const double* r, void* out, int cap, cudaStream_t s) {
+  gather_tracks_kernel<<<(cap + 127) / 128, 128, 0, s>>>(hp, ct, dx, nhat_best, r,
+                                                         (glmb_track*)out, cap); ++g_launches;
+}
+
+}  // namespace glmb

@@ -1,0 +1,462 @@
+// Prediction, births, and the gated compatibility table of Eq. 2 with the
+// posterior death probability (arXiv 2512.06230, Section 3), plus the
+// device-wide scans used across the update.
+#include <algorithm>
+#include <cfloat>
+
+#include "glmb_kernels.h"
+
+namespace glmb {
+
+long long g_launches = 0;
+
+// ---------------------------------------------------------------------------
+// Prediction: m <- F m, P <- F P F^T + Q for the constant-velocity model,
+// F = [[I, dt I], [0, I]], from the state table into the working table
+// (out of place, so a failed frame leaves the state untouched).  One
+// thread per component; the mean's position
+// coordinates advance in hi/lo arithmetic.  Survivors carry prior existence
+// P_S (their death is sampled in the update).
+// ---------------------------------------------------------------------------
+template <int DZ>
+__global__ void predict_kernel(Model md, CompTable src, CompTable ct, int n) {
+  constexpr int DX = 2 * DZ;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const size_t cap = ct.cap, scap = src.cap;
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) {
+    float hi = src.mhi[a * scap + c], lo = src.mlo[a * scap + c];
+    const float vhi = src.mhi[(DZ + a) * scap + c], vlo = src.mlo[(DZ + a) * scap + c];
+    ct.mhi[(DZ + a) * cap + c] = vhi;
+    ct.mlo[(DZ + a) * cap + c] = vlo;
+    const float p = md.dt * vhi;
+    const float perr = fmaf(md.dt, vhi, -p);   // exact product error
+    df_add(hi, lo, p);
+    df_add(hi, lo, perr + md.dt * vlo);
+    ct.mhi[a * cap + c] = hi;
+    ct.mlo[a * cap + c] = lo;
+  }
+  float P[DX][DX];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = i; j < DX; ++j) {
+      const float v = src.cov[(size_t)pidx(DX, i, j) * scap + c];
+      P[i][j] = v;
+      P[j][i] = v;
+    }
+  // blocks A (pos,pos), B (pos,vel), C (vel,vel):
+  // F P F^T = [[A + dt (B + B^T) + dt^2 C, B + dt C], [B^T + dt C, C]]
+  const float dt = md.dt;
+  float Pn[DX][DX];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      const float A = P[a][b], B = P[a][DZ + b], Bt = P[DZ + a][b], Cv = P[DZ + a][DZ + b];
+      Pn[a][b] = A + dt * (B + Bt) + dt * dt * Cv;
+      Pn[a][DZ + b] = B + dt * Cv;
+      Pn[DZ + a][b] = Bt + dt * Cv;
+      Pn[DZ + a][DZ + b] = Cv;
+    }
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = i; j < DX; ++j) {
+      const int k = pidx(DX, i, j);
+      ct.cov[(size_t)k * cap + c] = 0.5f * (Pn[i][j] + Pn[j][i]) + md.Q[k];
+    }
+  ct.lk[c] = src.lk[c];
+  ct.lb[c] = src.lb[c];
+  ct.logp[c] = md.log_ps;
+  ct.log1mp[c] = md.log_1mps;
+}
+
+void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
+                    cudaStream_t s) {
+  if (n <= 0) return;
+  const int bs = 256, nb = (n + bs - 1) / bs;
+  if (md.dz == 2) { predict_kernel<2><<<nb, bs, 0, s>>>(md, src, dst, n); } else { predict_kernel<3><<<nb, bs, 0, s>>>(md, src, dst, n); }
+  ++g_launches;
+}
+
+// LMB births: component base + b gets the birth density, existence r and
+// label (frame, b).  births_dev holds per birth [r, mean[6], cov[36]] (FP64).
+__global__ void births_kernel(Model md, CompTable ct, int base, const double* __restrict__ bd,
+                              int nb, int frame) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int c = base + b;
+  const size_t cap = ct.cap;
+  const double* rec = bd + (size_t)b * 43;
+  const double r = rec[0];
+  const int dx = md.dx;
+  for (int a = 0; a < dx; ++a) {
+    const double m = rec[1 + a];
+    const float hi = (float)m;
+    ct.mhi[a * cap + c] = hi;
+    ct.mlo[a * cap + c] = (float)(m - (double)hi);
+  }
+  for (int i = 0; i < dx; ++i)
+    for (int j = i; j < dx; ++j)
+      ct.cov[(size_t)pidx(dx, i, j) * cap + c] =
+          (float)(0.5 * (rec[7 + i * dx + j] + rec[7 + j * dx + i]));
+  ct.lk[c] = (uint32_t)frame;
+  ct.lb[c] = (uint32_t)b;
+  ct.logp[c] = r > 0.0 ? (float)log(r) : -INFINITY;
+  ct.log1mp[c] = r < 1.0 ? (float)log1p(-r) : -INFINITY;
+}
+
+void launch_births(const Model& md, const CompTable& ct, int base, const double* births_dev,
+                   int nb, int frame, cudaStream_t s) {
+  if (nb <= 0) return;
+  births_kernel<<<(nb + 127) / 128, 128, 0, s>>>(md, ct, base, births_dev, nb, frame); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 2 with the gate: one warp per component, lanes over detections.
+// S = H P H^T + R and its Cholesky factor are computed once per component
+// (FP64 when a pivot falls below 16 eps trace(S)); each lane forms the
+// innovation e = (z - m_hi) - m_lo, d^2 = e^T S^-1 e and the gate d^2 <= G.
+// The count pass sizes the CSR; the write pass stores the gated entries in
+// detection order (warp ballot compaction) and reduces
+//   psi = (1 - P_D) + sum_gated C[i, j] / kappa
+// into the death probability d = (1 - p) / ((1 - p) + p psi).
+// ---------------------------------------------------------------------------
+template <int DZ>
+struct CompGeom {
+  float mh[DZ], ml[DZ];
+  float L[DZ][DZ];
+  double Ld[DZ][DZ];
+  float logdet;
+  bool fp64;
+  bool ok;
+};
+
+template <int DZ>
+__device__ __forceinline__ void comp_geom(const Model& md, const CompTable& ct, int c,
+                                          CompGeom<DZ>& g) {
+  const size_t cap = ct.cap;
+  float S[DZ][DZ];
+  load_HPH<DZ>(ct, md.ncov, md.dx, c, S);
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) {
+    g.mh[a] = ct.mhi[a * cap + c];
+    g.ml[a] = ct.mlo[a * cap + c];
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) S[a][b] += md.R[a * DZ + b];
+  }
+  g.ok = true;
+  g.fp64 = !chol_n<float, DZ>(S, g.L, g.logdet, 1.1920929e-7f);
+  if (g.fp64) {
+    double Sd[DZ][DZ], ld;
+#pragma unroll
+    for (int a = 0; a < DZ; ++a)
+#pragma unroll
+      for (int b = 0; b < DZ; ++b) Sd[a][b] = S[a][b];
+    g.ok = chol_n<double, DZ>(Sd, g.Ld, ld, 2.220446049250313e-16);
+    g.logdet = (float)ld;
+  }
+}
+
+template <int DZ>
+__device__ __forceinline__ bool pair_eval(const Model& md, const CompGeom<DZ>& g,
+                                          const float* __restrict__ Z, int i, float (&e)[DZ],
+                                          float& d2) {
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) e[a] = (__ldg(Z + i * DZ + a) - g.mh[a]) - g.ml[a];
+  if (!g.fp64) {
+    d2 = mahal_n<float, DZ>(g.L, e);
+  } else {
+    double ed[DZ];
+#pragma unroll
+    for (int a = 0; a < DZ; ++a) ed[a] = e[a];
+    d2 = (float)mahal_n<double, DZ>(g.Ld, ed);
+  }
+  return d2 <= md.gate;
+}
+
+template <int DZ>
+__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, int T,
+                                   const float* __restrict__ Z, int M) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= T) return;
+  CompGeom<DZ> g;
+  comp_geom<DZ>(md, ct, c, g);
+  unsigned cnt = 0;
+  if (g.ok) {
+    for (int i0 = 0; i0 < M; i0 += 32) {
+      const int i = i0 + lane;
+      bool gated = false;
+      if (i < M) {
+        float e[DZ], d2;
+        gated = pair_eval<DZ>(md, g, Z, i, e, d2);
+      }
+      cnt += __popc(__ballot_sync(0xFFFFFFFFu, gated));
+    }
+  }
+  if (lane == 0) pt.cnt[c] = cnt;
+}
+
+__device__ __forceinline__ void lse_push(float& m, float& s, float x) {
+  if (x == -INFINITY) return;
+  if (x > m) {
+    s = (m == -INFINITY ? 0.f : s * __expf(m - x)) + 1.f;
+    m = x;
+  } else {
+    s += __expf(x - m);
+  }
+}
+
+template <int DZ>
+__global__ void table_write_kernel(Model md, CompTable ct, PairTable pt, int T,
+                                   const float* __restrict__ Z, int M, unsigned* n_fp64,
+                                   unsigned* err) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= T) return;
+  CompGeom<DZ> g;
+  comp_geom<DZ>(md, ct, c, g);
+  if (!g.ok) {
+    if (lane == 0) {
+      atomicOr(err, kErrNumeric);
+      pt.dthr[c] = kOne24;
+      pt.dprob[c] = 1.f;
+      pt.logdetS[c] = NAN;
+    }
+    return;
+  }
+  if (lane == 0 && g.fp64) atomicAdd(n_fp64, 1u);
+  const unsigned base = pt.ptr[c];
+  const size_t capp = (size_t)pt.cap_pairs;
+  unsigned off = 0;
+  float lm = -INFINITY, ls = 0.f;     // per-lane LSE of log C - log kappa
+  bool any = false;
+  const float c0 = md.log_pd - 0.5f * (g.logdet + (float)DZ * kLog2Pi);
+  for (int i0 = 0; i0 < M; i0 += 32) {
+    const int i = i0 + lane;
+    bool gated = false;
+    float e[DZ], d2 = 0.f;
+    if (i < M) gated = pair_eval<DZ>(md, g, Z, i, e, d2);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, gated);
+    if (gated) {
+      const unsigned pos = base + off + __popc(bal & ((1u << lane) - 1u));
+      if (pos < capp) {
+        const float logC = c0 - 0.5f * d2;
+        float q = 0.f;
+#pragma unroll
+        for (int a = 0; a < DZ; ++a)
+#pragma unroll
+          for (int b = 0; b < DZ; ++b) q += e[a] * md.Rinv[a * DZ + b] * e[b];
+        pt.meas[pos] = (uint32_t)i;
+        pt.logC[pos] = logC;
+        pt.q[pos] = q;
+#pragma unroll
+        for (int a = 0; a < DZ; ++a) pt.e[a * capp + pos] = e[a];
+        any = true;
+        if (!md.kappa_zero) lse_push(lm, ls, logC - md.log_kappa);
+      } else {
+        atomicOr(err, kErrPairs);
+      }
+    }
+    off += __popc(bal);
+  }
+  // warp-combine the log-sum-exp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float m2 = __shfl_xor_sync(0xFFFFFFFFu, lm, o);
+    const float s2 = __shfl_xor_sync(0xFFFFFFFFu, ls, o);
+    const float m = fmaxf(lm, m2);
+    if (m != -INFINITY) {
+      ls = (lm == -INFINITY ? 0.f : ls * __expf(lm - m)) + (m2 == -INFINITY ? 0.f : s2 * __expf(m2 - m));
+      lm = m;
+    }
+  }
+  const bool any_w = __any_sync(0xFFFFFFFFu, any);
+  if (lane == 0) {
+    // log psi = log((1 - P_D) + sum C / kappa)
+    float logpsi;
+    if (md.kappa_zero && any_w) {
+      logpsi = INFINITY;
+    } else {
+      float m = lm, s = ls;
+      lse_push(m, s, md.log_1mpd);
+      logpsi = (m == -INFINITY) ? -INFINITY : m + logf(s);
+    }
+    const float logp = ct.logp[c], log1mp = ct.log1mp[c];
+    float d;
+    if (logp == -INFINITY) d = 1.f;
+    else if (log1mp == -INFINITY) d = 0.f;
+    else if (logpsi == INFINITY) d = 0.f;
+    else if (logpsi == -INFINITY) d = 1.f;
+    else d = 1.f / (1.f + expf(logp + logpsi - log1mp));
+    pt.dprob[c] = d;
+    pt.dthr[c] = d >= 1.f ? kOne24 : (d <= 0.f ? 0u : (uint32_t)ceilf(d * 16777216.f));
+    pt.logdetS[c] = g.logdet;
+  }
+}
+
+void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt, int T,
+                        const float* Z, int M, cudaStream_t s) {
+  if (T <= 0) return;
+  const int bs = 256, nb = (int)(((long long)T * 32 + bs - 1) / bs);
+  if (md.dz == 2) { table_count_kernel<2><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M); } else { table_count_kernel<3><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M); }
+  ++g_launches;
+}
+
+void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt, int T,
+                        const float* Z, int M, unsigned* n_fp64, unsigned* err, cudaStream_t s) {
+  if (T <= 0) return;
+  const int bs = 256, nb = (int)(((long long)T * 32 + bs - 1) / bs);
+  if (md.dz == 2) { table_write_kernel<2><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M, n_fp64, err); } else { table_write_kernel<3><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M, n_fp64, err); }
+  ++g_launches;
+}
+
+__global__ void check_finite_kernel(const float* __restrict__ Z, long long n, unsigned* err) {
+  bool bad = false;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(Z[k]);
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrInput);
+}
+
+void launch_check_finite(const float* Z, long long n, unsigned* err, cudaStream_t s) {
+  if (n <= 0) return;
+  check_finite_kernel<<<(int)std::min<long long>((n + 255) / 256, 64), 256, 0, s>>>(Z, n, err); ++g_launches;
+}
+
+// per-parent slot and table sizes (max over parents), births included
+__global__ void parent_stats_kernel(HypTable hp, int H, PairTable pt, int birth_base, int nb,
+                                    unsigned* max_T, unsigned* max_K) {
+  __shared__ unsigned kb;
+  if (threadIdx.x == 0) {
+    unsigned s = 0;
+    for (int b = 0; b < nb; ++b) s += pt.cnt[birth_base + b];
+    kb = s;
+  }
+  __syncthreads();
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const unsigned lo = hp.ptr[h], hi = hp.ptr[h + 1];
+  unsigned k = kb;
+  for (unsigned j = lo; j < hi; ++j) k += pt.cnt[hp.comp[j]];
+  atomicMax(max_T, hi - lo + (unsigned)nb);
+  atomicMax(max_K, k);
+}
+
+void launch_parent_stats(const HypTable& hp, int H, const PairTable& pt, int birth_base, int nb,
+                         unsigned* max_T, unsigned* max_K, cudaStream_t s) {
+  if (H <= 0) return;
+  parent_stats_kernel<<<(H + 127) / 128, 128, 0, s>>>(hp, H, pt, birth_base, nb, max_T, max_K); ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan: tiles of 2048 elements (256 threads x 8), tile sums scanned
+// by one block, then applied.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T& total) {
+  __shared__ T warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < kScanThreads / 32 ? warp_sums[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const T before = (w > 0 ? warp_sums[w - 1] : T(0)) + x - v;
+  total = warp_sums[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+template <typename T>
+__global__ void scan_tile_sums(const T* __restrict__ in, long long n, T* tile_sums) {
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += in[base + k];
+  T total;
+  block_exclusive_scan<T>(s, total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void scan_single(T* v, int n, T* total) {
+  __shared__ T carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const T x = i < n ? v[i] : T(0);
+    T tot;
+    const T ex = block_exclusive_scan<T>(x, tot);
+    if (i < n) v[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename T>
+__global__ void scan_apply(const T* in, T* out, long long n, const T* __restrict__ tile_off) {
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  T vals[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    vals[k] = base + k < n ? in[base + k] : T(0);
+    s += vals[k];
+  }
+  T total;
+  T run = block_exclusive_scan<T>(s, total) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) {
+      out[base + k] = run;
+      run += vals[k];
+    }
+}
+
+long long scan_tmp_elems(long long n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+template <typename T>
+static void scan_impl(const T* in, T* out, long long n, T* total, T* tmp, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) cudaMemsetAsync(total, 0, sizeof(T), s);
+    return;
+  }
+  const int nt = (int)((n + kScanTile - 1) / kScanTile);
+  scan_tile_sums<T><<<nt, kScanThreads, 0, s>>>(in, n, tmp); ++g_launches;
+  scan_single<T><<<1, kScanThreads, 0, s>>>(tmp, nt, total); ++g_launches;
+  scan_apply<T><<<nt, kScanThreads, 0, s>>>(in, out, n, tmp); ++g_launches;
+}
+
+void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* total, uint32_t* tmp,
+              cudaStream_t s) {
+  scan_impl<uint32_t>(in, out, n, total, tmp, s);
+}
+void scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
+              unsigned long long* total, unsigned long long* tmp, cudaStream_t s) {
+  scan_impl<unsigned long long>(in, out, n, total, tmp, s);
+}
+
+}  // namespace glmb

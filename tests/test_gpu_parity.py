@@ -1,0 +1,176 @@
+"""CUDA library against the FP64 oracle, step by step, through the C ABI.
+
+Every test imports the same state into both implementations (a state the
+oracle produced on a seeded synthetic scene), runs one frame and compares
+each step of the update (tests/parity.py lists the tolerances)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import scenes
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def glmb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_06230_gb300 as g
+    g.build()
+    g.load()
+    return g
+
+
+def _frame(oracle_mod, glmb, cfg, scene, k):
+    state = parity.oracle_state(oracle_mod, cfg, scene, k)
+    fr = scene.frames[k]
+    o, g, d = parity.run_frame(oracle_mod, glmb, cfg, state, fr.births, fr.Z)
+    rep = parity.compare(o, g, d, cfg, fr.Z)
+    print(f"\nchecks {rep.checks} excused {rep.excused} max_err "
+          + " ".join(f"{k}={v:.2e}" for k, v in sorted(rep.max_err.items())))
+    assert rep.ok(), rep.failures[:10]
+    return rep
+
+
+@pytest.mark.parametrize("k", [0, 1, 6, 20, 35])
+def test_tiny_scene_frame(oracle_mod, glmb, k):
+    sc = scenes.make_scene(scenes.preset("tiny"), 1001)
+    _frame(oracle_mod, glmb, sc.filter_config(), sc, k)
+
+
+@pytest.mark.parametrize("k", [12, 40])
+def test_mid_scene_frame(oracle_mod, glmb, k):
+    """The 2-D scene with 100 objects and H_max = 1000 at full size."""
+    sc = scenes.make_scene(scenes.preset("mid"), 2001)
+    rep = _frame(oracle_mod, glmb, sc.filter_config(), sc, k)
+    assert rep.checks["children"] >= 1000
+
+
+def test_3d_scene_frame(oracle_mod, glmb):
+    sc = scenes.make_scene(scenes.preset("sweep_N50", frames=12), 3050)
+    _frame(oracle_mod, glmb, sc.filter_config(h_max=200), sc, 8)
+
+
+def test_no_detections(oracle_mod, glmb):
+    sc = scenes.make_scene(scenes.preset("tiny"), 1003)
+    cfg = sc.filter_config()
+    state = parity.oracle_state(oracle_mod, cfg, sc, 10)
+    fr = sc.frames[10]
+    Z = np.zeros((0, 2), np.float32)
+    o, g, d = parity.run_frame(oracle_mod, glmb, cfg, state, fr.births, Z)
+    rep = parity.compare(o, g, d, cfg, Z)
+    assert rep.ok(), rep.failures[:10]
+
+
+def test_no_births_and_no_clutter(oracle_mod, glmb):
+    """kappa = 0: every detection must go to a track.  The frame keeps only
+    the detections that gate some track of the first hypothesis (found with
+    the oracle), so children without a zero-weight row exist."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1004)
+    cfg = sc.filter_config(clutter_rate=0.0)
+    state = parity.oracle_state(oracle_mod, sc.filter_config(), sc, 15)
+    fr = sc.frames[15]
+    o = oracle_mod.Oracle(cfg)
+    o.import_state(*state)
+    o.predict([])
+    o.update(fr.Z)
+    keep = [i for i in range(len(fr.Z))
+            if any(o.pair(0, t, i)["gated"] for t in range(o.parent_slots(0)))]
+    Z = fr.Z[keep]
+    assert 0 < len(Z) < len(fr.Z)
+    o2, g, d = parity.run_frame(oracle_mod, glmb, cfg, state, [], Z)
+    rep = parity.compare(o2, g, d, cfg, Z)
+    assert rep.ok(), rep.failures[:10]
+
+
+def test_zero_weight_frame_is_an_error_and_keeps_state(oracle_mod, glmb):
+    """kappa = 0 and a detection far from every track: no child has a
+    finite weight.  Both implementations report it; the library keeps the
+    previous state and accepts the frame again."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1004)
+    cfg = sc.filter_config(clutter_rate=0.0)
+    state = parity.oracle_state(oracle_mod, sc.filter_config(), sc, 10)
+    Z = np.array([[-5.0e4, -5.0e4]], np.float32)
+    o = oracle_mod.Oracle(cfg)
+    o.import_state(*state)
+    o.predict([])
+    o.update(Z)
+    with pytest.raises(oracle_mod.OracleError):
+        o.prune()
+    g = glmb.Filter(cfg)
+    g.import_state(glmb.pack_state(*state, g.dx))
+    before = g.export_state()
+    g.predict([])
+    g.update(Z)
+    with pytest.raises(glmb.GlmbError) as ei:
+        g.prune()
+    assert ei.value.status == 5
+    assert g.export_state() == before
+    g.predict([])
+    g.update(sc.frames[10].Z[:0])
+    g.prune()
+
+
+def test_invalid_inputs_are_rejected(glmb):
+    sc = scenes.make_scene(scenes.preset("tiny"), 1006)
+    g = glmb.Filter(sc.filter_config())
+    with pytest.raises(glmb.GlmbError) as ei:
+        g.update(sc.frames[0].Z)
+    assert ei.value.status == 6
+    g.predict(sc.frames[0].births)
+    Z = sc.frames[0].Z.copy()
+    Z[0, 0] = np.nan
+    with pytest.raises(glmb.GlmbError) as ei:
+        g.update(Z)
+    assert ei.value.status == 1
+    import torch
+    g.predict(sc.frames[0].births)
+    with pytest.raises(glmb.GlmbError) as ei:
+        g.update(torch.from_numpy(Z).cuda(), device=True)
+    assert ei.value.status == 1
+    g.predict(sc.frames[0].births)
+    g.update(torch.from_numpy(sc.frames[0].Z).cuda(), device=True)
+    g.prune()
+    assert g.info()["n_hyp"] >= 1
+    with pytest.raises(glmb.GlmbError) as ei:
+        g.predict([(1.5, np.zeros(4), np.eye(4))])
+    assert ei.value.status == 1
+
+
+def test_certain_detection(oracle_mod, glmb):
+    sc = scenes.make_scene(scenes.preset("tiny"), 1005)
+    cfg = sc.filter_config(p_d=1.0)
+    state = parity.oracle_state(oracle_mod, cfg, sc, 8)
+    fr = sc.frames[8]
+    o, g, d = parity.run_frame(oracle_mod, glmb, cfg, state, fr.births, fr.Z)
+    rep = parity.compare(o, g, d, cfg, fr.Z)
+    assert rep.ok(), rep.failures[:10]
+
+
+def test_multi_frame_run_tracks_the_oracle(oracle_mod, glmb):
+    """Both filters from the initial GLMB over a whole scene.  Random draws
+    are keyed by hypothesis uid, so the two stay identical as long as their
+    retained sets agree; frames are counted until an excused decision makes
+    them part."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1001)
+    cfg = sc.filter_config()
+    o = oracle_mod.Oracle(cfg, n_threads=8)
+    g = glmb.Filter(cfg)
+    same = 0
+    card = 0
+    for f, fr in enumerate(sc.frames):
+        o.step(fr.births, fr.Z)
+        g.step(fr.births, fr.Z)
+        ou = set(o.export_state()[2].tolist())
+        gu = set(g.hypotheses()["uid"].tolist())
+        if ou == gu:
+            same += 1
+        card += o.estimates()["n"] == g.estimates()["n"]
+    print(f"\nframes with identical hypothesis sets: {same}/{len(sc.frames)}, "
+          f"equal MAP cardinality: {card}/{len(sc.frames)}")
+    assert same >= len(sc.frames) // 2
+    assert card >= 0.9 * len(sc.frames)
