@@ -75,12 +75,12 @@ struct glmb_handle {
   uint32_t* gc_newpos = nullptr;
   unsigned* d_scal = nullptr;
   unsigned* h_scal = nullptr;
-  double* d_pmf = nullptr;
-  int* d_nb = nullptr;
-  double* d_r = nullptr;
+  // estimates: one device block [nb (16 B)][pmf][tracks][r][done], mirrored on
+  // the host up to r
+  unsigned char* d_est = nullptr;
+  unsigned char* h_est = nullptr;
+  size_t est_off_pmf = 0, est_off_tr = 0, est_off_r = 0, est_off_done = 0;
   double* d_ru = nullptr;
-  glmb_track* d_tracks = nullptr;
-  glmb_track* h_tracks = nullptr;
   // stage timing
   unsigned prof_mask = 0;
   cudaEvent_t ev[kNumStages][2] = {};
@@ -156,6 +156,17 @@ void free_all(glmb_handle* h) {
   for (void* p : h->host_allocs) cudaFreeHost(p);
   h->allocs.clear();
   h->host_allocs.clear();
+}
+
+bool alloc_est(glmb_handle* h) {
+  const size_t pcap = (size_t)h->max_tracks + 1;
+  h->est_off_pmf = 16;
+  h->est_off_tr = h->est_off_pmf + 8 * pcap;
+  h->est_off_r = h->est_off_tr + sizeof(glmb_track) * pcap;
+  h->est_off_done = h->est_off_r + 8 * pcap;
+  const size_t bytes = h->est_off_done + 16;
+  return dalloc(h, &h->d_est, (long long)bytes) && halloc(h, &h->h_est, (long long)h->est_off_r) &&
+         cudaMemset(h->d_est, 0, bytes) == cudaSuccess;
 }
 
 long long next_pow2(long long x) {
@@ -384,6 +395,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             alloc_hyps(h, h->hyps[0]) && alloc_hyps(h, h->hyps[1]) &&
             dalloc(h, &h->d_births, (long long)h->cap_births * kBirthRec) &&
             halloc(h, &h->h_births, (long long)h->cap_births * kBirthRec) &&
+            alloc_est(h) &&
             dalloc(h, &h->d_Z, (long long)h->cap_meas * dz) &&
             halloc(h, &h->h_Z, (long long)h->cap_meas * dz) &&
             dalloc(h, &h->pt.cnt, h->cap_comp + 1) && dalloc(h, &h->pt.ptr, h->cap_comp + 1) &&
@@ -404,10 +416,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
             dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
             dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
-            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_pmf, h->max_tracks + 2) &&
-            dalloc(h, &h->d_nb, 2) && dalloc(h, &h->d_r, h->max_tracks + 1) &&
-            dalloc(h, &h->d_ru, h->cap_meas) && dalloc(h, &h->d_tracks, h->max_tracks + 1) &&
-            halloc(h, &h->h_tracks, h->max_tracks + 1);
+            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_ru, h->cap_meas);
   if (!ok) {
     free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -475,12 +484,10 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
   CompTable& A = h->comps[h->cur];
   CompTable& B = h->comps[1 - h->cur];
   prof_begin(h, kStagePredict);
-  launch_predict(h->md, A, B, h->n_comp, h->stream);
-  if (n_births) {
+  if (n_births)
     CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
                        cudaMemcpyHostToDevice, h->stream));
-    launch_births(h->md, B, h->n_comp, h->d_births, n_births, h->frame, h->stream);
-  }
+  launch_predict(h->md, A, B, h->n_comp, h->d_births, n_births, h->frame, h->stream);
   prof_end(h, kStagePredict);
   CU(cudaGetLastError());
   h->T_work = h->n_comp + n_births;
@@ -535,8 +542,12 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
   h->T_max = (int)std::max(1u, h->h_scal[S_MAXT]);
   h->K_max = (int)std::max(1u, h->h_scal[S_MAXK]);
   if (h->T_max > 65535) return abandon(GLMB_E_CAPACITY, "tracks per hypothesis exceed 65535");
-  const int G = expand_plan_groups(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit);
-  const int Gm = expand_plan_groups(dz, 1, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit);
+  // one CTA per parent; with few parents each CTA gets more warps so that
+  // about 32 warps per SM draw children
+  const int want = std::max(4, std::min(16, (32 * h->n_sm + h->H - 1) / std::max(1, h->H)));
+  const int G = expand_plan_groups(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit,
+                                   std::min(want, h->cfg.h_up));
+  const int Gm = expand_plan_groups(dz, 1, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit, 8);
   if (G == 0 || Gm == 0)
     return abandon(GLMB_E_CAPACITY, "per-hypothesis table does not fit in shared memory");
   ExpandArgs a{};
@@ -613,7 +624,7 @@ glmb_status glmb_prune(glmb_handle* h) {
   a.key = philox_key(h);
   a.T_max = h->T_max;
   a.K_max = h->K_max;
-  a.n_groups = expand_plan_groups(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, h->smem_limit);
+  a.n_groups = expand_plan_groups(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, h->smem_limit, 8);
   a.smem_bytes = expand_smem_bytes(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, a.n_groups);
   a.materialize = 1;
   a.surv_idx = h->pw.surv_idx;
@@ -695,31 +706,26 @@ glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out,
   const HypTable& Y = h->hyps[h->hcur];
   const CompTable& A = h->comps[h->cur];
   const int pcap = h->max_tracks + 1;
+  int* d_nb = (int*)h->d_est;
+  double* d_pmf = (double*)(h->d_est + h->est_off_pmf);
+  double* d_r = (double*)(h->d_est + h->est_off_r);
   prof_begin(h, kStageEstimates);
-  launch_card(Y, h->H, h->d_pmf, pcap, h->d_nb, s);
-  CU(cudaMemsetAsync(h->d_r, 0, (size_t)pcap * sizeof(double), s));
-  launch_existence(Y, h->H, A, h->d_nb, h->d_r, s);
+  CU(cudaMemsetAsync(d_r, 0, (size_t)pcap * sizeof(double), s));
+  launch_estimates(Y, h->H, A, h->md.dx, d_pmf, pcap, d_nb, d_r, h->d_est + h->est_off_tr,
+                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, s);
+  prof_end(h, kStageEstimates);
   CU(cudaGetLastError());
-  int nb[2];
-  CU(cudaMemcpyAsync(nb, h->d_nb, sizeof nb, cudaMemcpyDeviceToHost, s));
-  std::vector<double> pmf(pcap), r(pcap);
-  CU(cudaMemcpyAsync(pmf.data(), h->d_pmf, pcap * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(r.data(), h->d_r, pcap * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  const int nhat = nb[0], best = nb[1];
+  int nb[2];
+  std::memcpy(nb, h->h_est, sizeof nb);
+  const int nhat = nb[0];
   *n_out = nhat;
+  const double* pmf = (const double*)(h->h_est + h->est_off_pmf);
   if (card_pmf)
     for (int k = 0; k < pmf_cap; ++k) card_pmf[k] = k < pcap ? pmf[k] : 0.0;
   if (nhat > cap) return fail(h, GLMB_E_CAPACITY, "estimates: %d tracks > cap %d", nhat, cap);
-  if (nhat == 0) return GLMB_OK;
-  (void)best;
-  launch_gather_tracks(Y, A, h->md.dx, h->d_nb, h->d_r, h->d_tracks, nhat, s);
-  prof_end(h, kStageEstimates);
-  CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(h->h_tracks, h->d_tracks, (size_t)nhat * sizeof(glmb_track),
-                     cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
-  std::memcpy(out, h->h_tracks, (size_t)nhat * sizeof(glmb_track));
+  if (nhat > 0) std::memcpy(out, h->h_est + h->est_off_tr, (size_t)nhat * sizeof(glmb_track));
   return GLMB_OK;
 }
 

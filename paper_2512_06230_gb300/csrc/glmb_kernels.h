@@ -11,10 +11,10 @@ namespace glmb {
 extern long long g_launches;
 
 // ---- prediction, births, table (kernels_table.cu) ----
+// prediction of n components from src into dst, then nb births appended at
+// dst[n..n+nb) (births_dev: per birth [r, mean[6], cov[36]] in FP64)
 void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
-                    cudaStream_t s);
-void launch_births(const Model& md, const CompTable& ct, int base, const double* births_dev,
-                   int nb, int frame, cudaStream_t s);
+                    const double* births_dev, int nb, int frame, cudaStream_t s);
 void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt, int T,
                         const float* Z, int M, cudaStream_t s);
 void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt, int T,
@@ -67,8 +67,9 @@ struct ExpandArgs {
 };
 int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int h_up,
                       int n_groups);
+// draw groups (warps) per CTA: as many as fit, up to max_groups (<= 16)
 int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                       int smem_limit);
+                       int smem_limit, int max_groups);
 void launch_expand(const ExpandArgs& a, cudaStream_t s);
 
 // ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
@@ -109,14 +110,10 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
                                kErrEntries | kErrSlots | kErrInput;
 
-// estimates
-void launch_card(const HypTable& hp, int H, double* pmf, int pmf_cap, int* nhat_best,
-                 cudaStream_t s);
-void launch_existence(const HypTable& hp, int H, const CompTable& ct, const int* nhat_best,
-                      double* r, cudaStream_t s);
+// estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, r[pcap] (zeroed by the
+// caller), tracks = glmb_track[pcap]; done is a zeroed counter
+void launch_estimates(const HypTable& hp, int H, const CompTable& ct, int dx, double* pmf, int pcap,
+                      int* nb, double* r, void* tracks, unsigned* done, int n_sm, cudaStream_t s);
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s);
-// MAP tracks into glmb_track records (out must hold max_tracks records)
-void launch_gather_tracks(const HypTable& hp, const CompTable& ct, int dx, const int* nhat_best,
-                          const double* r, void* out, int cap, cudaStream_t s);
 
 }  // namespace glmb

@@ -105,8 +105,8 @@ int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int 
 }
 
 int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                       int smem_limit) {
-  for (int G = 8; G >= 1; --G)
+                       int smem_limit, int max_groups) {
+  for (int G = max_groups < 1 ? 1 : (max_groups > 16 ? 16 : max_groups); G >= 1; --G)
     if (expand_smem_bytes(dz, materialize, T_max, K_max, M, h_up, G) <= smem_limit) return G;
   return 0;
 }
@@ -165,7 +165,7 @@ __device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long
 }
 
 template <int DZ, bool MAT>
-__global__ void __launch_bounds__(256) expand_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const Model& md = a.md;
   const int HU = md.h_up;

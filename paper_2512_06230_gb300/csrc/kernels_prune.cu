@@ -2,6 +2,8 @@
 // children (arXiv 2512.06230, Section 3: weights below tau are discarded,
 // the H_max most likely hypotheses are kept, and one update is run per
 // distinct (track, detection set)), plus the estimate reductions.
+#include <algorithm>
+
 #include "../../include/glmb.h"
 #include "glmb_kernels.h"
 
@@ -25,78 +27,83 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // sum of exp); each pass's last block combines the per-block partials in
 // block order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-__global__ void lse_max_kernel(const long long* __restrict__ keys, long long n, PruneWork w) {
-  __shared__ long long red[kRedThreads / 32];
+// (max, sum of exp(x - max)) pairs in fixed-point keys; combine two pairs
+struct Lse {
+  long long m;
+  double s;
+};
+__device__ __forceinline__ Lse lse_combine(Lse a, Lse b) {
+  if (a.m == kKeyInvalid) return b;
+  if (b.m == kKeyInvalid) return a;
+  if (a.m >= b.m) return {a.m, a.s + b.s * exp((double)(b.m - a.m) * kFxInv)};
+  return {b.m, b.s + a.s * exp((double)(a.m - b.m) * kFxInv)};
+}
+__device__ __forceinline__ Lse warp_lse(Lse v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Lse u{__shfl_xor_sync(0xFFFFFFFFu, v.m, o), __shfl_xor_sync(0xFFFFFFFFu, v.s, o)};
+    v = lse_combine(v, u);
+  }
+  return v;
+}
+// block-wide combine; result valid in thread 0
+__device__ Lse block_lse(Lse v) {
+  __shared__ long long sm[32];
+  __shared__ double ss[32];
+  v = warp_lse(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) { sm[w] = v.m; ss[w] = v.s; }
+  __syncthreads();
+  if (w == 0) {
+    Lse u = lane < nw ? Lse{sm[lane], ss[lane]} : Lse{kKeyInvalid, 0.0};
+    v = warp_lse(u);
+  }
+  return v;
+}
+
+// Global log-sum-exp over the unique children (FP64) in one pass: each
+// thread keeps a running (max, sum of shifted exponentials); blocks write
+// partials; the last block combines them in a fixed tree, so the result does
+// not depend on scheduling.  Also counts the unique children and sets the
+// fixed-point threshold log(tau) + LSE.
+__global__ void lse_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
+                           double log_tau, int h_max) {
   __shared__ bool last;
-  long long m = kKeyInvalid;
+  Lse v{kKeyInvalid, 0.0};
   unsigned valid = 0;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
     const long long k = keys[j];
-    m = max(m, k);
-    valid += (k != kKeyInvalid);
+    if (k == kKeyInvalid) continue;
+    ++valid;
+    v = lse_combine(v, Lse{k, 1.0});
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) valid += __shfl_xor_sync(0xFFFFFFFFu, valid, o);
   if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&w.counts[2], valid);
-  m = warp_max_ll(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    long long v = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : kKeyInvalid;
-    v = warp_max_ll(v);
-    if (threadIdx.x == 0) {
-      w.blk_max[blockIdx.x] = v;
-      __threadfence();
-      last = atomicAdd(&w.blk_done[0], 1u) == gridDim.x - 1;
-    }
+  v = block_lse(v);
+  if (threadIdx.x == 0) {
+    w.blk_max[blockIdx.x] = v.m;
+    w.blk_sum[blockIdx.x] = v.s;
+    __threadfence();
+    last = atomicAdd(&w.blk_done[0], 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    long long g = kKeyInvalid;
-    for (unsigned b = 0; b < gridDim.x; ++b) g = max(g, ((volatile long long*)w.blk_max)[b]);
-    w.blk_max[gridDim.x] = g;
+  if (!last) return;
+  __threadfence();
+  Lse u{kKeyInvalid, 0.0};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    u = lse_combine(u, Lse{((volatile long long*)w.blk_max)[b], ((volatile double*)w.blk_sum)[b]});
+  u = block_lse(u);
+  if (threadIdx.x == 0) {
     w.blk_done[0] = 0;
-  }
-}
-
-__global__ void lse_sum_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
-                               double log_tau, int h_max) {
-  __shared__ double red[kRedThreads / 32];
-  __shared__ bool last;
-  const long long g = w.blk_max[gridDim.x];
-  double s = 0.0;
-  if (g != kKeyInvalid)
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (long long)gridDim.x * blockDim.x) {
-      const long long k = keys[j];
-      if (k != kKeyInvalid) s += exp((double)(k - g) * kFxInv);
-    }
-  s = warp_sum_d(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : 0.0;
-    v = warp_sum_d(v);
-    if (threadIdx.x == 0) {
-      w.blk_sum[blockIdx.x] = v;
-      __threadfence();
-      last = atomicAdd(&w.blk_done[1], 1u) == gridDim.x - 1;
-    }
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double S = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) S += ((volatile double*)w.blk_sum)[b];
-    w.blk_done[1] = 0;
-    if (g == kKeyInvalid || !(S > 0.0)) {
+    if (u.m == kKeyInvalid || !(u.s > 0.0)) {
       w.lse[0] = -INFINITY;
       w.thr[0] = LLONG_MAX;
       w.sel[3] = 2;   // nothing to keep
     } else {
-      const double lse = (double)g * kFxInv + log(S);
+      const double lse = (double)u.m * kFxInv + log(u.s);
       w.lse[0] = lse;
       w.thr[0] = (long long)ceil((lse + log_tau) * 4294967296.0);
       w.sel[3] = 0;
@@ -109,8 +116,7 @@ __global__ void lse_sum_kernel(const long long* __restrict__ keys, long long n, 
 
 void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau, int h_max,
                 int nblk, cudaStream_t s) {
-  lse_max_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w); ++g_launches;
-  lse_sum_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w, log_tau, h_max); ++g_launches;
+  lse_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w, log_tau, h_max); ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -142,49 +148,62 @@ __global__ void radix_hist_kernel(const long long* __restrict__ keys, long long 
 }
 
 __global__ void radix_find_kernel(PruneWork w, int shift, int first) {
-  // one warp: lane l owns bins [l*128, l*128+128), highest bins first
-  if (w.sel[3] != 0) {
-    for (int b = threadIdx.x; b < kBins; b += 32) w.hist[b] = 0;
-    return;
+  // thread t owns bins [4t, 4t + 4) (blockDim.x == kBins / 4 == 1024);
+  // the count of bins above a thread's range is total - inclusive prefix
+  __shared__ unsigned wsum[32];
+  const int t = threadIdx.x;
+  const int lane = t & 31, wp = t >> 5;
+  const bool running = w.sel[3] == 0;
+  const long long need = w.sel[1];
+  unsigned b4[4], mine = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    b4[k] = w.hist[4 * t + k];
+    mine += b4[k];
+    w.hist[4 * t + k] = 0;
   }
-  const int lane = threadIdx.x;
-  constexpr int per = kBins / 32;
-  unsigned mine = 0;
-  for (int b = 0; b < per; ++b) mine += w.hist[lane * per + b];
-  // counts above lane l: sum of lanes > l
-  unsigned above = mine;
+  unsigned x = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_down_sync(0xFFFFFFFFu, above, o);
-    if (lane + o < 32) above += y;
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
   }
-  const unsigned total = __shfl_sync(0xFFFFFFFFu, above, 0);
-  above -= mine;   // strictly above this lane
-  const long long need = w.sel[1];
-  __syncwarp();
+  if (lane == 31) wsum[wp] = x;
+  __syncthreads();
+  if (wp == 0) {
+    unsigned s = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s;
+  }
+  __syncthreads();
+  if (!running) return;
+  const unsigned incl = x + (wp > 0 ? wsum[wp - 1] : 0u);
+  const unsigned total = wsum[31];
+  const unsigned above = total - incl;       // bins above this thread's range
+  const unsigned upto = above + mine;
   if (first && (long long)total <= need) {
-    if (lane == 0) {
+    if (t == 0) {
       w.sel[3] = 1;
       w.sel[2] = w.thr[0] - 1;   // every candidate is above the boundary
       w.sel[1] = 0;
     }
-  } else {
-    const bool hit = (long long)above < need && (long long)(above + mine) >= need;
-    if (hit) {
-      unsigned cum = above;
-      int b = lane * per + per - 1;
-      for (; b >= lane * per; --b) {
-        const unsigned hb = w.hist[b];
-        if ((long long)(cum + hb) >= need) break;
-        cum += hb;
-      }
-      w.sel[0] = (w.sel[0] << kDigit) | b;
-      w.sel[1] = need - cum;
-      if (shift == 0) w.sel[2] = w.thr[0] + w.sel[0];
-    }
+    return;
   }
-  __syncwarp();
-  for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+  if ((long long)above < need && (long long)upto >= need) {
+    unsigned cum = above;
+    int b = 3;
+    for (; b > 0; --b) {
+      if ((long long)(cum + b4[b]) >= need) break;
+      cum += b4[b];
+    }
+    w.sel[0] = (w.sel[0] << kDigit) | (4 * t + b);
+    w.sel[1] = need - cum;
+    if (shift == 0) w.sel[2] = w.thr[0] + w.sel[0];
+  }
 }
 
 void launch_select(const long long* keys, long long n, int h_max, int nbits, PruneWork w,
@@ -194,7 +213,7 @@ void launch_select(const long long* keys, long long n, int h_max, int nbits, Pru
   for (int p = 0; p < passes; ++p) {
     const int shift = (passes - 1 - p) * kDigit;
     radix_hist_kernel<<<nblk, 256, 0, s>>>(keys, n, w, shift); ++g_launches;
-    radix_find_kernel<<<1, 32, 0, s>>>(w, shift, p == 0); ++g_launches;
+    radix_find_kernel<<<1, kBins / 4, 0, s>>>(w, shift, p == 0); ++g_launches;
   }
 }
 
@@ -596,85 +615,137 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
 // of that cardinality (ties to the lower index), label existence, and the
 // clutter probability of each detection.
 // ---------------------------------------------------------------------------
-__global__ void card_kernel(HypTable hp, int H, double* pmf, int pmf_cap, int* nhat_best) {
-  __shared__ int s_nhat;
+// Cardinality distribution, MAP cardinality (ties to the smaller n) and the
+// heaviest hypothesis of that cardinality (ties to the lower index); one
+// block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
+__global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* nb) {
   __shared__ double bw[32];
   __shared__ int bi[32];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int n = tid; n < pmf_cap; n += nthr) pmf[n] = 0.0;
+  __shared__ int s_nhat;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5;
+  const int nw = (nthr + 31) >> 5;
+  for (int n = tid; n < pcap; n += nthr) pmf[n] = 0.0;
   __syncthreads();
   for (int h = tid; h < H; h += nthr) {
     const int n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
-    if (n < pmf_cap) atomicAdd(&pmf[n], exp(hp.logw[h]));
+    if (n < pcap) atomicAdd(&pmf[n], exp(hp.logw[h]));
   }
-  __threadfence_block();
+  __threadfence();
   __syncthreads();
-  if (tid == 0) {
-    int best = 0;
-    for (int n = 1; n < pmf_cap; ++n)
-      if (pmf[n] > pmf[best]) best = n;
-    s_nhat = best;
-  }
-  __syncthreads();
-  double bwv = -INFINITY;
-  int biv = -1;
-  for (int h = tid; h < H; h += nthr) {
-    if ((int)(hp.ptr[h + 1] - hp.ptr[h]) != s_nhat) continue;
-    const double lw = hp.logw[h];
-    if (lw > bwv || (lw == bwv && h < biv)) { bwv = lw; biv = h; }
+  // argmax over bins
+  double v = -1.0;
+  int vi = 0x7FFFFFFF;
+  for (int n = tid; n < pcap; n += nthr) {
+    const double p = ((volatile double*)pmf)[n];
+    if (p > v) { v = p; vi = n; }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double w2 = __shfl_xor_sync(0xFFFFFFFFu, bwv, o);
-    const int i2 = __shfl_xor_sync(0xFFFFFFFFu, biv, o);
-    if (w2 > bwv || (w2 == bwv && i2 >= 0 && (biv < 0 || i2 < biv))) { bwv = w2; biv = i2; }
+    const double v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int i2 = __shfl_xor_sync(0xFFFFFFFFu, vi, o);
+    if (v2 > v || (v2 == v && i2 < vi)) { v = v2; vi = i2; }
   }
-  if ((tid & 31) == 0) { bw[tid >> 5] = bwv; bi[tid >> 5] = biv; }
+  if (lane == 0) { bw[wp] = v; bi[wp] = vi; }
   __syncthreads();
   if (tid == 0) {
-    double w = -INFINITY;
-    int b = -1;
-    for (int k = 0; k < (nthr + 31) / 32; ++k)
-      if (bi[k] >= 0 && (bw[k] > w || (bw[k] == w && bi[k] < b))) { w = bw[k]; b = bi[k]; }
-    nhat_best[0] = s_nhat;
-    nhat_best[1] = b;
+    double b = -1.0;
+    int k = 0;
+    for (int w = 0; w < nw; ++w)
+      if (bw[w] > b || (bw[w] == b && bi[w] < k)) { b = bw[w]; k = bi[w]; }
+    s_nhat = k;
+  }
+  __syncthreads();
+  const int nhat = s_nhat;
+  double lw = -INFINITY;
+  int li = -1;
+  for (int h = tid; h < H; h += nthr) {
+    if ((int)(hp.ptr[h + 1] - hp.ptr[h]) != nhat) continue;
+    const double x = hp.logw[h];
+    if (li < 0 || x > lw) { lw = x; li = h; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w2 = __shfl_xor_sync(0xFFFFFFFFu, lw, o);
+    const int i2 = __shfl_xor_sync(0xFFFFFFFFu, li, o);
+    if (i2 >= 0 && (li < 0 || w2 > lw || (w2 == lw && i2 < li))) { lw = w2; li = i2; }
+  }
+  __syncthreads();
+  if (lane == 0) { bw[wp] = lw; bi[wp] = li; }
+  __syncthreads();
+  if (tid == 0) {
+    double b = -INFINITY;
+    int k = -1;
+    for (int w = 0; w < nw; ++w)
+      if (bi[w] >= 0 && (k < 0 || bw[w] > b || (bw[w] == b && bi[w] < k))) { b = bw[w]; k = bi[w]; }
+    nb[0] = nhat;
+    nb[1] = k;
   }
 }
 
-void launch_card(const HypTable& hp, int H, double* pmf, int pmf_cap, int* nhat_best,
-                 cudaStream_t s) {
-  card_kernel<<<1, 1024, 0, s>>>(hp, H, pmf, pmf_cap, nhat_best); ++g_launches;
-}
-
-// r[j] = sum_h w_h [label of MAP track j in hypothesis h]; hypotheses list
-// their tracks in label order, so each is a binary search.
-__global__ void existence_kernel(HypTable hp, int H, CompTable ct, const int* __restrict__ nb,
-                                 double* r) {
+// r[j] = total weight of hypotheses holding the label of MAP track j (one
+// warp per hypothesis, binary search in the MAP track list, which is in
+// label order); the last block then writes the MAP tracks as glmb_track
+// records (mean hi + lo in FP64, full covariance).
+__global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const int* __restrict__ nb,
+                                 double* r, glmb_track* out, int cap, unsigned* done) {
+  __shared__ bool last;
   const int best = nb[1];
-  if (best < 0) return;
-  const uint32_t b0 = hp.ptr[best], nmap = hp.ptr[best + 1] - b0;
-  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < (long long)H * nmap;
-       x += (long long)gridDim.x * blockDim.x) {
-    const int h = (int)(x / nmap), j = (int)(x % nmap);
-    const uint32_t c = hp.comp[b0 + j];
-    const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
-    uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      const uint32_t cm = hp.comp[mid];
-      const unsigned long long km = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
-      if (km < key) lo = mid + 1; else hi = mid;
-    }
-    if (lo < hp.ptr[h + 1]) {
-      const uint32_t cm = hp.comp[lo];
-      if (ct.lk[cm] == ct.lk[c] && ct.lb[cm] == ct.lb[c]) atomicAdd(&r[j], exp(hp.logw[h]));
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t b0 = best >= 0 ? hp.ptr[best] : 0u;
+  const int nmap = best >= 0 ? (int)(hp.ptr[best + 1] - b0) : 0;
+  for (int h = gw; h < H && nmap > 0; h += warps) {
+    const uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
+    const double wgt = exp(hp.logw[h]);
+    for (uint32_t e = lo + lane; e < hi; e += 32) {
+      const uint32_t c = hp.comp[e];
+      const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
+      int l = 0, u = nmap;
+      while (l < u) {
+        const int mid = (l + u) >> 1;
+        const uint32_t cm = hp.comp[b0 + mid];
+        const unsigned long long km = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
+        if (km < key) l = mid + 1; else u = mid;
+      }
+      if (l < nmap) {
+        const uint32_t cm = hp.comp[b0 + l];
+        if (ct.lk[cm] == ct.lk[c] && ct.lb[cm] == ct.lb[c]) atomicAdd(&r[l], wgt);
+      }
     }
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const size_t cc = ct.cap;
+  for (int j = threadIdx.x; j < min(nmap, cap); j += blockDim.x) {
+    const uint32_t c = hp.comp[b0 + j];
+    glmb_track& t = out[j];
+    t.label_k = ct.lk[c];
+    t.label_b = ct.lb[c];
+    t.r = ((volatile double*)r)[j];
+    for (int a = 0; a < 6; ++a)
+      t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
+    for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
+    for (int i = 0; i < dx; ++i)
+      for (int k = i; k < dx; ++k) {
+        const double v = ct.cov[(size_t)pidx(dx, i, k) * cc + c];
+        t.cov[i * dx + k] = v;
+        t.cov[k * dx + i] = v;
+      }
+  }
+  if (threadIdx.x == 0) *done = 0u;
 }
 
-void launch_existence(const HypTable& hp, int H, const CompTable& ct, const int* nhat_best,
-                      double* r, cudaStream_t s) {
-  existence_kernel<<<304, 256, 0, s>>>(hp, H, ct, nhat_best, r); ++g_launches;
+void launch_estimates(const HypTable& hp, int H, const CompTable& ct, int dx, double* pmf, int pcap,
+                      int* nb, double* r, void* tracks, unsigned* done, int n_sm, cudaStream_t s) {
+  est_card_kernel<<<1, 1024, 0, s>>>(hp, H, pmf, pcap, nb); ++g_launches;
+  const int blocks = std::max(1, std::min((H + 7) / 8, 2 * n_sm));
+  est_exist_kernel<<<blocks, 256, 0, s>>>(hp, H, ct, dx, nb, r, (glmb_track*)tracks, pcap, done);
+  ++g_launches;
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
@@ -689,39 +760,6 @@ __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s) {
   if (M <= 0) return;
   meas_assoc_kernel<<<(M + 127) / 128, 128, 0, s>>>(hp, H, M, r_u); ++g_launches;
-}
-
-// MAP hypothesis tracks as glmb_track records: labels, existence, mean
-// (hi + lo in FP64) and the full covariance.
-__global__ void gather_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* __restrict__ nb,
-                                     const double* __restrict__ r, glmb_track* out, int cap) {
-  const int best = nb[1];
-  if (best < 0) return;
-  const uint32_t b0 = hp.ptr[best];
-  const int n = min((int)(hp.ptr[best + 1] - b0), cap);
-  const size_t cc = ct.cap;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t c = hp.comp[b0 + j];
-    glmb_track& t = out[j];
-    t.label_k = ct.lk[c];
-    t.label_b = ct.lb[c];
-    t.r = r[j];
-    for (int a = 0; a < 6; ++a)
-      t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
-    for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
-    for (int i = 0; i < dx; ++i)
-      for (int k = i; k < dx; ++k) {
-        const double v = ct.cov[(size_t)pidx(dx, i, k) * cc + c];
-        t.cov[i * dx + k] = v;
-        t.cov[k * dx + i] = v;
-      }
-  }
-}
-
-void launch_gather_tracks(const HypTable& hp, const CompTable& ct, int dx, const int* nhat_best,
-                          const double* r, void* out, int cap, cudaStream_t s) {
-  gather_tracks_kernel<<<(cap + 127) / 128, 128, 0, s>>>(hp, ct, dx, nhat_best, r,
-                                                         (glmb_track*)out, cap); ++g_launches;
 }
 
 }  // namespace glmb

@@ -18,11 +18,18 @@ long long g_launches = 0;
 // coordinates advance in hi/lo arithmetic.  Survivors carry prior existence
 // P_S (their death is sampled in the update).
 // ---------------------------------------------------------------------------
+__device__ void birth_comp(const Model& md, const CompTable& ct, int c, const double* __restrict__ rec,
+                           int b, int frame);
+
 template <int DZ>
-__global__ void predict_kernel(Model md, CompTable src, CompTable ct, int n) {
+__global__ void predict_kernel(Model md, CompTable src, CompTable ct, int n,
+                               const double* __restrict__ births, int nb, int frame) {
   constexpr int DX = 2 * DZ;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  if (c >= n) {
+    if (c < n + nb) birth_comp(md, ct, c, births + (size_t)(c - n) * 43, c - n, frame);
+    return;
+  }
   const size_t cap = ct.cap, scap = src.cap;
 #pragma unroll
   for (int a = 0; a < DZ; ++a) {
@@ -73,23 +80,11 @@ __global__ void predict_kernel(Model md, CompTable src, CompTable ct, int n) {
   ct.log1mp[c] = md.log_1mps;
 }
 
-void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
-                    cudaStream_t s) {
-  if (n <= 0) return;
-  const int bs = 256, nb = (n + bs - 1) / bs;
-  if (md.dz == 2) { predict_kernel<2><<<nb, bs, 0, s>>>(md, src, dst, n); } else { predict_kernel<3><<<nb, bs, 0, s>>>(md, src, dst, n); }
-  ++g_launches;
-}
-
-// LMB births: component base + b gets the birth density, existence r and
-// label (frame, b).  births_dev holds per birth [r, mean[6], cov[36]] (FP64).
-__global__ void births_kernel(Model md, CompTable ct, int base, const double* __restrict__ bd,
-                              int nb, int frame) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  const int c = base + b;
+// LMB births: component c gets birth b's density, existence r and label
+// (frame, b).  rec = [r, mean[6], cov[36]] (FP64).
+__device__ void birth_comp(const Model& md, const CompTable& ct, int c, const double* __restrict__ rec,
+                           int b, int frame) {
   const size_t cap = ct.cap;
-  const double* rec = bd + (size_t)b * 43;
   const double r = rec[0];
   const int dx = md.dx;
   for (int a = 0; a < dx; ++a) {
@@ -108,10 +103,17 @@ __global__ void births_kernel(Model md, CompTable ct, int base, const double* __
   ct.log1mp[c] = r < 1.0 ? (float)log1p(-r) : -INFINITY;
 }
 
-void launch_births(const Model& md, const CompTable& ct, int base, const double* births_dev,
-                   int nb, int frame, cudaStream_t s) {
-  if (nb <= 0) return;
-  births_kernel<<<(nb + 127) / 128, 128, 0, s>>>(md, ct, base, births_dev, nb, frame); ++g_launches;
+void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
+                    const double* births_dev, int nb, int frame, cudaStream_t s) {
+  const int total = n + nb;
+  if (total <= 0) return;
+  const int bs = 128, nblk = (total + bs - 1) / bs;
+  if (md.dz == 2) {
+    predict_kernel<2><<<nblk, bs, 0, s>>>(md, src, dst, n, births_dev, nb, frame);
+  } else {
+    predict_kernel<3><<<nblk, bs, 0, s>>>(md, src, dst, n, births_dev, nb, frame);
+  }
+  ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -436,12 +438,36 @@ __global__ void scan_apply(const T* in, T* out, long long n, const T* __restrict
     }
 }
 
+// whole scan in one block for small inputs (up to 64 items per thread)
+constexpr long long kScanSmall = (long long)kScanThreads * 64;
+template <typename T>
+__global__ void scan_small(const T* in, T* out, long long n, T* total) {
+  const int per = (int)((n + kScanThreads - 1) / kScanThreads);
+  const long long b = (long long)threadIdx.x * per;
+  T s = 0;
+  for (int k = 0; k < per; ++k)
+    if (b + k < n) s += in[b + k];
+  T tot;
+  T run = block_exclusive_scan<T>(s, tot);
+  for (int k = 0; k < per; ++k)
+    if (b + k < n) {
+      const T v = in[b + k];
+      out[b + k] = run;
+      run += v;
+    }
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
 long long scan_tmp_elems(long long n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 template <typename T>
 static void scan_impl(const T* in, T* out, long long n, T* total, T* tmp, cudaStream_t s) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(T), s);
+    return;
+  }
+  if (n <= kScanSmall) {
+    scan_small<T><<<1, kScanThreads, 0, s>>>(in, out, n, total); ++g_launches;
     return;
   }
   const int nt = (int)((n + kScanTile - 1) / kScanTile);
