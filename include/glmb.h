@@ -187,6 +187,14 @@ glmb_status glmb_get_hypotheses(glmb_handle* h, double* logw, uint64_t* uid, uin
                                 uint32_t* label_k, uint32_t* label_b, uint16_t* theta, int cap_h,
                                 int64_t cap_entries, int* n_h);
 
+/* The children retained by the last successful glmb_prune, in the order of
+ * the hypotheses: child_idx[j] = parent * h_up + draw (parents in the order
+ * they had during glmb_update), logw[j] their renormalised FP64
+ * log-weights.  Either pointer may be NULL.  Synchronises.
+ * Errors: GLMB_E_STATE (no pruned frame since create/reset/import),
+ * GLMB_E_CAPACITY (cap < n; *n is still set). */
+glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n);
+
 /* Inspection of the last glmb_update, for checking each step on its own.
  *
  * glmb_get_parents: slot lists of the parents (the hypotheses before the

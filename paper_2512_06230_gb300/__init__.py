@@ -132,6 +132,7 @@ def load() -> C.CDLL:
         "glmb_get_pairs": [P, P, P, P, P, P, I, L, P],
         "glmb_get_children": [P, P, P, P, L, P],
         "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
+        "glmb_get_retained": [P, P, P, I, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -343,6 +344,17 @@ class Filter:
                                                  _ptr(lb), _ptr(theta), H, max(E, 1), C.byref(n)))
         return dict(logw=logw, uid=uid, ptr=ptr, label_k=lk[:E], label_b=lb[:E],
                     theta=theta[:, : self.M])
+
+    def retained(self):
+        """Child indices (parent * h_up + draw) and renormalised log-weights
+        of the hypotheses kept by the last prune."""
+        n = C.c_int()
+        self.lib.glmb_get_retained(self.h, None, None, 0, C.byref(n))
+        k = n.value
+        idx = np.zeros(max(k, 1), np.int64)
+        lw = np.zeros(max(k, 1))
+        self._check(self.lib.glmb_get_retained(self.h, _ptr(idx), _ptr(lw), max(k, 1), C.byref(n)))
+        return idx[:k], lw[:k]
 
     def parents(self):
         n = C.c_int()

@@ -54,7 +54,7 @@ struct glmb_handle {
   int stage = 0;            // 0 ready for predict, 1 predicted, 2 updated
   // last frame
   int nb = 0, T_work = 0, M = 0, H_par = 0, par_buf = 0, birth_base = 0;
-  bool have_update = false, theta_M_valid = false;
+  bool have_update = false, theta_M_valid = false, retained_valid = false;
   int theta_M = 0;
   double* d_births = nullptr;
   double* h_births = nullptr;
@@ -585,6 +585,7 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
 glmb_status glmb_prune(glmb_handle* h) {
   if (!h) return GLMB_E_INVALID;
   if (h->stage != 2) return fail(h, GLMB_E_STATE, "prune: call glmb_update first");
+  h->retained_valid = false;
   const int dz = h->md.dz;
   const long long n = (long long)h->H * h->cfg.h_up;
   const int nblk = (int)std::min<long long>(std::max(1LL, (n + 255) / 256), 2LL * h->n_sm);
@@ -676,7 +677,21 @@ glmb_status glmb_prune(glmb_handle* h) {
   h->hcur = 1 - h->hcur;
   h->theta_M = h->M;
   h->theta_M_valid = true;
+  h->retained_valid = true;
   h->stage = 0;
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n) {
+  if (!h || !n) return GLMB_E_INVALID;
+  if (!h->retained_valid) return fail(h, GLMB_E_STATE, "get_retained: no pruned frame");
+  CU(cudaStreamSynchronize(h->stream));
+  *n = h->H;
+  if (h->H > cap) return fail(h, GLMB_E_CAPACITY, "get_retained: cap");
+  if (child_idx)
+    CU(cudaMemcpy(child_idx, h->pw.surv_idx, (size_t)h->H * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (logw)
+    CU(cudaMemcpy(logw, h->hyps[h->hcur].logw, (size_t)h->H * sizeof(double), cudaMemcpyDeviceToHost));
   return GLMB_OK;
 }
 
@@ -910,6 +925,7 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
   h->stage = 0;
   h->have_update = false;
   h->theta_M_valid = false;
+  h->retained_valid = false;
   return GLMB_OK;
 }
 

@@ -67,6 +67,7 @@ def run_frame(oracle_mod, glmb, cfg, state, births, Z, n_threads=8):
     g.prune()
     d.update(o_state=o.export_state(), o_kept=o.kept(), o_theta=o.kept_theta(),
              g_hyp=g.hypotheses(), g_state=glmb.unpack_state(g.export_state()),
+             g_retained=g.retained(),
              o_est=o.estimates(), g_est=g.estimates(), o_ru=o.meas_assoc(), g_ru=g.meas_assoc())
     return o, g, d
 
@@ -183,6 +184,14 @@ def compare(o, g, d, cfg, Z, report: Report | None = None) -> Report:
                f"boundary {boundary:.6f})")
     r.excused["boundary"] = n_boundary
     r.checks["retained"] = len(kept_g)
+    # retained child indices: the same children in the same (parent, draw) order
+    gidx, glw_ret = d["g_retained"]
+    if not np.array_equal(glw_ret, g_hyp["logw"]):
+        r.fail("retained log-weights differ from the hypothesis table")
+    if len(gidx) != len(g_uid) or np.any(np.diff(gidx) <= 0):
+        r.fail("retained child indices not strictly ascending")
+    elif not np.array_equal(oc["uid"][gidx], g_uid):
+        r.fail("retained child indices do not match the hypothesis uids")
     # ---- a8 theta, labels, tracks, weights of hypotheses kept on both sides
     o_tr = d["o_state"][3]
     g_tr = d["g_state"][3]
