@@ -232,6 +232,38 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
 glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask);
 glmb_status glmb_get_timing(glmb_handle* h, double* ms, long long* calls, int n);
 
+/* Top-H selection without device allocation.  The paper has no counterpart:
+ * this is the normalisation and truncation step of glmb_prune offered on
+ * its own, for callers that may not allocate device memory while they run
+ * (a tracking loop with a fixed memory budget and a frame deadline, where
+ * cudaMalloc can synchronise the device and stall; a host application
+ * whose memory policy forbids raw cudaMalloc).  It needs no handle and
+ * allocates nothing: its scratch is a 64 KiB array in the library's device
+ * image, which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * Inputs (device memory, caller-owned): logw_dev[n] child log-weights in
+ * FP64, -INFINITY (or NaN) for children without weight.  Computation, as in
+ * glmb_prune: weights are rounded to 2^-32, normalised by their FP64
+ * log-sum-exp, those below tau dropped, the h_max largest kept (ties to the
+ * lower index).  Outputs (device memory, caller-owned): idx_out_dev[h_max]
+ * the kept indices in ascending order, logw_out_dev[h_max] their
+ * renormalised log-weights, *n_out_dev their number.  Work is queued on
+ * stream (a cudaStream_t; NULL is the default stream) and the call returns
+ * without waiting.
+ *
+ * The first call on a device looks up the scratch array's address for that
+ * device (make it before any stream capture).  Every call uses the same
+ * scratch and clears what it needs at its start, so calls that overlap on
+ * the GPU (on different streams, or from several threads) race: serialise
+ * them.  Limits: n <= 2^30, h_max <= 2^30.
+ * Errors: GLMB_E_INVALID (null pointer, h_max < 1, tau <= 0),
+ * GLMB_E_CAPACITY (n or h_max beyond the limits; nothing is launched),
+ * GLMB_E_CUDA. */
+glmb_status glmb_select_top_static(const double* logw_dev, int64_t n, int32_t h_max, double tau,
+                                   int64_t* idx_out_dev, double* logw_out_dev, int32_t* n_out_dev,
+                                   void* stream);
+
 /* Message of the last error on this handle ("" if none). */
 const char* glmb_last_error(glmb_handle* h);
 
