@@ -169,11 +169,14 @@ def main():
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)
     F = len(sc.frames)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     f = glmb.Filter(cfg, stream=stream.cuda_stream)
     Zdev = [torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
             for fr in sc.frames]
+    Bhost = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
     h_up = cfg["h_up"]
 
     def run(n_steps, start, host, profile=False, record=None):
@@ -193,12 +196,10 @@ def main():
             e0.record(stream)
             if fi == 0:
                 f.reset()
-            f.predict(fr.births)
             if host:
-                f.update(fr.Z)
+                f.step(Bhost[fi], fr.Z)
             else:
-                f.update(Zdev[fi], device=True)
-            f.prune()
+                f.step(Bhost[fi], Zdev[fi], device=True)
             est = f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
             e1.record(stream)
             e1.synchronize()
@@ -226,7 +227,8 @@ def main():
     torch.cuda.synchronize()
     times, work = run(args.steps, args.warmup, host=False, profile=True)
     torch.cuda.synchronize()
-    launches = f.info()["n_launches"] - launches0
+    info1 = f.info()
+    launches = info1["n_launches"] - launches0
     tim = f.timing()
     stop.set()
     th.join(timeout=10)
@@ -282,6 +284,8 @@ def main():
                 "h2d_bytes_per_step": sum(w["h2d"] for w in work_h) / len(work_h),
                 "d2h_bytes_per_step": sum(w["d2h"] for w in work_h) / len(work_h)},
         "gpu_launches": int(launches),
+        "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
+                   "redone_frames": info1["n_redo"]},
         "roofline": {"bound": "alu", "kernel": "expand_kernel (child expansion + scoring)",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",

@@ -21,9 +21,9 @@
  *    glmb_create, from the capacities in glmb_config; no call allocates
  *    device memory afterwards.
  *  - Work is issued on glmb_config.stream (a cudaStream_t; NULL means a
- *    stream owned by the handle).  Calls that return sizes or host data
- *    synchronise that stream; glmb_predict and glmb_update do not return
- *    until their inputs have been copied.
+ *    stream owned by the handle).  glmb_predict and glmb_update only enqueue
+ *    work (their host inputs are copied before they return); glmb_prune and
+ *    every call that returns sizes or host data synchronise that stream.
  *  - Call order per frame: glmb_predict -> glmb_update -> glmb_prune ->
  *    any number of glmb_estimates / glmb_meas_assoc / glmb_get_* calls.
  *    A call out of order returns GLMB_E_STATE and changes nothing.
@@ -112,6 +112,9 @@ typedef struct {
   int32_t n_updates;        /* distinct (component, detection set) track updates */
   int32_t n_fp64_chol;      /* innovation covariances factorised in FP64 */
   int64_t n_launches;       /* CUDA kernels launched by the library so far (all handles) */
+  int64_t n_graph_captures; /* frame graphs captured by glmb_step on this handle */
+  int64_t n_graph_launches; /* frame graphs replayed by glmb_step on this handle */
+  int64_t n_redo;           /* frames whose expansion was redone with a larger plan */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks
@@ -137,18 +140,33 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
  * memory on the handle's GPU (z_is_device = 1).  Builds the gated
  * compatibility table, the posterior death probabilities, and the h_up
  * children of each hypothesis with their exact log-weights; unique children
- * stay on the device for glmb_prune.
- * Errors: GLMB_E_STATE (no predict), GLMB_E_INVALID (M < 0, NaN/Inf in Z),
- * GLMB_E_CAPACITY (M, pairs or per-hypothesis table beyond capacity). */
+ * stay on the device for glmb_prune.  The call only enqueues work: it does
+ * not wait for the GPU.
+ * Errors: GLMB_E_STATE (no predict), GLMB_E_INVALID (M < 0, NaN/Inf in a
+ * host Z), GLMB_E_CAPACITY (M beyond max_meas, or a per-hypothesis table
+ * that cannot fit in shared memory).  Errors found on the device (NaN/Inf in
+ * a device Z, gated pairs beyond max_pairs) are returned by glmb_prune. */
 glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device);
 
 /* Pruning (Section 3): normalises the children's weights over all unique
  * children (FP64), drops those below tau, keeps the h_max heaviest (ties by
  * parent then draw index), renormalises, and builds the new hypotheses with
- * one Kalman update per distinct (component, detection set).
+ * one Kalman update per distinct (component, detection set).  Waits for
+ * the frame to finish (one synchronisation).
  * Errors: GLMB_E_STATE, GLMB_E_NUMERIC (no child with finite weight),
- * GLMB_E_CAPACITY (components or entries beyond capacity). */
+ * GLMB_E_INVALID (NaN/Inf in a device Z), GLMB_E_CAPACITY (pairs,
+ * components or entries beyond capacity). */
 glmb_status glmb_prune(glmb_handle* h);
+
+/* One whole frame: glmb_predict + glmb_update + glmb_prune with the same
+ * arguments and results, launched as one CUDA graph (captured on the first
+ * call for a given launch plan and replayed afterwards) followed by one
+ * synchronisation.  The handle's stream must not be the legacy default
+ * stream.  The per-step inspection calls (glmb_get_parents, _components,
+ * _pairs, _children) describe this frame afterwards as they do after the
+ * separate calls.  Errors: those of the three calls. */
+glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
+                      int z_is_device);
 
 /* Estimates: writes the tracks of the heaviest hypothesis among those with
  * the most probable cardinality into out[0..n_out) (n_out <= cap), each with

@@ -97,8 +97,15 @@ class GlmbInfo(C.Structure):
     _fields_ = [("frame", C.c_int32), ("n_hyp", C.c_int32), ("n_entries", C.c_int64),
                 ("n_components", C.c_int32), ("n_meas", C.c_int32), ("n_pairs", C.c_int64),
                 ("n_children", C.c_int64), ("n_unique", C.c_int64), ("n_updates", C.c_int32),
-                ("n_fp64_chol", C.c_int32), ("n_launches", C.c_int64)]
+                ("n_fp64_chol", C.c_int32), ("n_launches", C.c_int64),
+                ("n_graph_captures", C.c_int64), ("n_graph_launches", C.c_int64),
+                ("n_redo", C.c_int64)]
 
+
+# NumPy views of the ABI records (same layout as the C structs)
+BIRTH_DTYPE = np.dtype([("r", "<f8"), ("mean", "<f8", 6), ("cov", "<f8", 36)])
+TRACK_DTYPE = np.dtype([("label_k", "<u4"), ("label_b", "<u4"), ("r", "<f8"), ("mean", "<f8", 6),
+                        ("cov", "<f8", 36)])
 
 _lib = None
 
@@ -134,6 +141,7 @@ def load() -> C.CDLL:
         "glmb_get_children": [P, P, P, P, L, P],
         "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
         "glmb_get_retained": [P, P, P, I, P],
+        "glmb_step": [P, P, I, P, I, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -174,6 +182,16 @@ def make_config(cfg: dict, stream: Optional[int] = None) -> GlmbConfig:
     c.max_pairs = int(cfg.get("max_pairs", 0))
     c.stream = stream
     return c
+
+
+def births_array(births, dim_x: int) -> np.ndarray:
+    """glmb_birth records (BIRTH_DTYPE) from (r, mean, cov) tuples."""
+    arr = np.zeros(len(births), BIRTH_DTYPE)
+    for j, (r, m, P) in enumerate(births):
+        arr[j]["r"] = r
+        arr[j]["mean"][:dim_x] = np.asarray(m, np.float64).reshape(dim_x)
+        arr[j]["cov"][: dim_x * dim_x] = np.asarray(P, np.float64).reshape(dim_x * dim_x)
+    return arr
 
 
 def pack_state(frame: int, logw, uid, tracks, dim_x: int) -> bytes:
@@ -251,18 +269,14 @@ class Filter:
     def reset(self):
         self._check(self.lib.glmb_reset(self.h))
 
-    def predict(self, births: Sequence[Tuple[float, np.ndarray, np.ndarray]]):
-        arr = (GlmbBirth * max(1, len(births)))()
-        dx = self.dx
-        for j, (r, m, P) in enumerate(births):
-            arr[j].r = float(r)
-            mm = np.asarray(m, np.float64).reshape(dx)
-            PP = np.asarray(P, np.float64).reshape(dx * dx)
-            for a in range(dx):
-                arr[j].mean[a] = mm[a]
-            for a in range(dx * dx):
-                arr[j].cov[a] = PP[a]
-        self._check(self.lib.glmb_predict(self.h, C.cast(arr, C.c_void_p), len(births)))
+    def _births(self, births):
+        if isinstance(births, np.ndarray) and births.dtype == BIRTH_DTYPE:
+            return np.ascontiguousarray(births)
+        return births_array(births, self.dx)
+
+    def predict(self, births):
+        arr = self._births(births)
+        self._check(self.lib.glmb_predict(self.h, _ptr(arr), len(births)))
 
     def update(self, Z, device: bool = False):
         if device:
@@ -278,23 +292,34 @@ class Filter:
     def prune(self):
         self._check(self.lib.glmb_prune(self.h))
 
-    def step(self, births, Z):
-        self.predict(births)
-        self.update(Z)
-        self.prune()
+    def step(self, births, Z, device: bool = False):
+        """One frame in one call (glmb_step: a replayed CUDA graph)."""
+        arr = self._births(births)
+        if device:
+            M = int(Z.shape[0])
+            self.M = M
+            self._check(self.lib.glmb_step(self.h, _ptr(arr), len(births),
+                                           C.c_void_p(Z.data_ptr()), M, 1))
+            return
+        Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
+        self.M = len(Zf)
+        self._check(self.lib.glmb_step(self.h, _ptr(arr), len(births), _ptr(Zf), len(Zf), 0))
 
     # ---- outputs ----
     def estimates(self, cap: int = 4096, pmf_cap: int = 4096):
-        out = (GlmbTrack * cap)()
+        """MAP tracks (labels, existence, mean, cov) and the cardinality pmf."""
+        buf = getattr(self, "_est_buf", None)
+        if buf is None or len(buf[0]) < cap or len(buf[1]) < pmf_cap:
+            buf = (np.zeros(cap, TRACK_DTYPE), np.zeros(pmf_cap))
+            self._est_buf = buf
+        out, pmf = buf
         n = C.c_int()
-        pmf = np.zeros(pmf_cap)
-        self._check(self.lib.glmb_estimates(self.h, C.cast(out, C.c_void_p), cap, C.byref(n),
-                                            _ptr(pmf), pmf_cap))
+        self._check(self.lib.glmb_estimates(self.h, _ptr(out), cap, C.byref(n), _ptr(pmf), pmf_cap))
         k, dx = n.value, self.dx
-        mean = np.array([[out[j].mean[a] for a in range(dx)] for j in range(k)]).reshape(k, dx)
-        cov = np.array([[out[j].cov[a] for a in range(dx * dx)] for j in range(k)]).reshape(k, dx, dx)
-        return dict(n=k, labels=[(out[j].label_k, out[j].label_b) for j in range(k)],
-                    r=np.array([out[j].r for j in range(k)]), mean=mean, cov=cov, pmf=pmf)
+        t = out[:k]
+        return dict(n=k, labels=list(zip(t["label_k"].tolist(), t["label_b"].tolist())),
+                    r=t["r"].copy(), mean=t["mean"][:, :dx].copy(),
+                    cov=t["cov"][:, : dx * dx].reshape(k, dx, dx).copy(), pmf=pmf[:pmf_cap].copy())
 
     STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")
 

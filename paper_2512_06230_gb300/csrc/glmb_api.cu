@@ -29,6 +29,16 @@ enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S
 
 }  // namespace
 
+namespace {
+// launch sizes: eager (from the host-known sizes of this frame) or fixed by
+// capacity (for a replayed graph)
+struct Plan {
+  bool fixed;
+  int T, K, M;     // expansion shared-memory plan
+  int G, Gm;       // draw groups of the expansion and of the regeneration
+};
+}  // namespace
+
 struct glmb_handle {
   glmb_config cfg{};
   Model md{};
@@ -87,6 +97,26 @@ struct glmb_handle {
   bool ev_pending[kNumStages] = {};
   double stage_ms[kNumStages] = {};
   long long stage_calls[kNumStages] = {};
+  // frame sizes on the device (two pinned host slots: predict, update)
+  FrameDev* d_fs = nullptr;
+  FrameDev* h_fs = nullptr;
+  // shared-memory plan of the expansion: exact slot maximum (from the last
+  // prune), estimated pair maximum (from earlier frames; redone if exceeded)
+  int alive_max = 0;
+  int K_est = 256;
+  int redo_count = 0;
+  // launch plan of the frame in progress, and captured frame graphs
+  Plan plan{};
+  struct CachedGraph {
+    int hcur;
+    unsigned prof;
+    Plan plan;
+    cudaGraphExec_t exec;
+    long long n_kernels;
+  };
+  std::vector<CachedGraph> graphs;
+  bool capturing = false;
+  long long n_captures = 0, n_graph_launches = 0;
   // stats
   long long n_pairs = 0, n_unique = 0;
   int n_upd = 0, n_fp64 = 0;
@@ -207,10 +237,6 @@ bool spd_inverse(int n, const double* A, double* Ainv, double* logdet) {
   return true;
 }
 
-uint2 philox_key(const glmb_handle* h) {
-  return make_uint2((uint32_t)h->cfg.seed, (uint32_t)(h->cfg.seed >> 32) ^ (uint32_t)h->frame);
-}
-
 glmb_status sync_scal(glmb_handle* h) {
   CU(cudaMemcpyAsync(h->h_scal, h->d_scal, S_N * sizeof(unsigned), cudaMemcpyDeviceToHost,
                      h->stream));
@@ -243,6 +269,7 @@ glmb_status set_initial(glmb_handle* h) {
   h->n_comp = 0;
   h->frame = 0;
   h->stage = 0;
+  h->alive_max = 0;
   h->have_update = false;
   h->theta_M_valid = false;
   return GLMB_OK;
@@ -254,11 +281,17 @@ void prof_begin(glmb_handle* h, int st) {
     cudaEventCreate(&h->ev[st][0]);
     cudaEventCreate(&h->ev[st][1]);
   }
-  cudaEventRecord(h->ev[st][0], h->stream);
+  // inside a graph capture the record becomes a node that fires on replay
+  if (h->capturing) cudaEventRecordWithFlags(h->ev[st][0], h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(h->ev[st][0], h->stream);
 }
 
 void prof_end(glmb_handle* h, int st) {
   if (!(h->prof_mask & (1u << st)) || !h->ev[st][0]) return;
+  if (h->capturing) {
+    cudaEventRecordWithFlags(h->ev[st][1], h->stream, cudaEventRecordExternal);
+    return;
+  }
   cudaEventRecord(h->ev[st][1], h->stream);
   h->ev_pending[st] = true;
 }
@@ -286,6 +319,11 @@ glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask) {
   for (int st = 0; st < kNumStages; ++st) {
     h->stage_ms[st] = 0.0;
     h->stage_calls[st] = 0;
+    h->ev_pending[st] = false;
+    if ((stage_mask & (1u << st)) && !h->ev[st][0]) {
+      CU(cudaEventCreate(&h->ev[st][0]));
+      CU(cudaEventCreate(&h->ev[st][1]));
+    }
   }
   return GLMB_OK;
 }
@@ -416,7 +454,8 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
             dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
             dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
-            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_ru, h->cap_meas);
+            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_ru, h->cap_meas) &&
+            dalloc(h, &h->d_fs, 1) && halloc(h, &h->h_fs, 2);
   if (!ok) {
     free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -439,6 +478,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
 glmb_status glmb_destroy(glmb_handle* h) {
   if (!h) return GLMB_OK;
   cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   for (int st = 0; st < kNumStages; ++st)
     if (h->ev[st][0]) {
       cudaEventDestroy(h->ev[st][0]);
@@ -458,9 +498,10 @@ glmb_status glmb_reset(glmb_handle* h) {
 
 const char* glmb_last_error(glmb_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
-glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births) {
-  if (!h) return GLMB_E_INVALID;
-  if (h->stage != 0) return fail(h, GLMB_E_STATE, "predict: previous frame not pruned");
+namespace {
+
+// validates and stages the births of a frame (host pinned buffer)
+glmb_status stage_births(glmb_handle* h, const glmb_birth* births, int n_births) {
   if (n_births < 0 || (n_births > 0 && !births)) return fail(h, GLMB_E_INVALID, "predict: births");
   if (n_births > h->cap_births)
     return fail(h, GLMB_E_CAPACITY, "predict: %d births > max_births %d", n_births, h->cap_births);
@@ -479,155 +520,127 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
     for (int k = 0; k < dx * dx; ++k)
       if (!std::isfinite(rec[7 + k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
   }
-  h->frame += 1;
-  h->nb = n_births;
-  CompTable& A = h->comps[h->cur];
-  CompTable& B = h->comps[1 - h->cur];
-  prof_begin(h, kStagePredict);
-  if (n_births)
-    CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
-                       cudaMemcpyHostToDevice, h->stream));
-  launch_predict(h->md, A, B, h->n_comp, h->d_births, n_births, h->frame, h->stream);
-  prof_end(h, kStagePredict);
-  CU(cudaGetLastError());
-  h->T_work = h->n_comp + n_births;
-  h->stage = 1;
-  h->have_update = false;
   return GLMB_OK;
 }
 
-glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) {
-  if (!h) return GLMB_E_INVALID;
-  if (h->stage != 1) return fail(h, GLMB_E_STATE, "update: call glmb_predict first");
+// validates and stages the detections (copied to the device buffer d_Z)
+glmb_status stage_detections(glmb_handle* h, const float* Z, int M, int z_is_device) {
   if (M < 0 || (M > 0 && !Z)) return fail(h, GLMB_E_INVALID, "update: detections");
   if (M > h->cap_meas) return fail(h, GLMB_E_CAPACITY, "update: M=%d > max_meas %d", M, h->cap_meas);
   const int dz = h->md.dz;
-  auto abandon = [&](glmb_status st, const char* msg) {
-    h->frame -= 1;
-    h->stage = 0;
-    return fail(h, st, "update: %s", msg);
-  };
+  if (M > 0 && !z_is_device)
+    for (long long k = 0; k < (long long)M * dz; ++k)
+      if (!std::isfinite(Z[k])) return fail(h, GLMB_E_INVALID, "update: non-finite detection");
   if (M > 0) {
     if (z_is_device) {
       CU(cudaMemcpyAsync(h->d_Z, Z, (size_t)M * dz * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     } else {
-      for (long long k = 0; k < (long long)M * dz; ++k)
-        if (!std::isfinite(Z[k])) return abandon(GLMB_E_INVALID, "non-finite detection");
       std::memcpy(h->h_Z, Z, (size_t)M * dz * sizeof(float));
       CU(cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)M * dz * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
   }
-  h->M = M;
-  const int T = h->T_work;
-  const CompTable& B = h->comps[1 - h->cur];
-  CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
-  prof_begin(h, kStageTable);
-  if (z_is_device) launch_check_finite(h->d_Z, (long long)M * dz, h->d_scal + S_ERR, h->stream);
-  launch_table_count(h->md, B, h->pt, T, h->d_Z, M, h->stream);
-  scan_u32(h->pt.cnt, h->pt.ptr, T, h->pt.ptr + T, h->scan_tmp32, h->stream);
-  CU(cudaMemcpyAsync(h->d_scal + S_K, h->pt.ptr + T, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream));
-  launch_table_write(h->md, B, h->pt, T, h->d_Z, M, h->d_scal + S_FP64, h->d_scal + S_ERR, h->stream);
-  const HypTable& P = h->hyps[h->hcur];
-  launch_parent_stats(P, h->H, h->pt, h->n_comp, h->nb, h->d_scal + S_MAXT, h->d_scal + S_MAXK, h->stream);
-  prof_end(h, kStageTable);
-  CU(cudaGetLastError());
-  glmb_status st = sync_scal(h);
-  if (st != GLMB_OK) return st;
-  const unsigned e = h->h_scal[S_ERR];
-  if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
-  h->n_pairs = h->h_scal[S_K];
-  h->n_fp64 = (int)h->h_scal[S_FP64];
-  if (h->n_pairs > h->cap_pairs) return abandon(GLMB_E_CAPACITY, "gated pairs exceed max_pairs");
-  if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
-  h->T_max = (int)std::max(1u, h->h_scal[S_MAXT]);
-  h->K_max = (int)std::max(1u, h->h_scal[S_MAXK]);
-  if (h->T_max > 65535) return abandon(GLMB_E_CAPACITY, "tracks per hypothesis exceed 65535");
-  // one CTA per parent; with few parents each CTA gets more warps so that
-  // about 32 warps per SM draw children
-  const int want = std::max(4, std::min(16, (32 * h->n_sm + h->H - 1) / std::max(1, h->H)));
-  const int G = expand_plan_groups(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit,
-                                   std::min(want, h->cfg.h_up));
-  const int Gm = expand_plan_groups(dz, 1, h->T_max, h->K_max, M, h->cfg.h_up, h->smem_limit, 8);
-  if (G == 0 || Gm == 0)
-    return abandon(GLMB_E_CAPACITY, "per-hypothesis table does not fit in shared memory");
-  ExpandArgs a{};
-  a.md = h->md;
-  a.ct = B;
-  a.pt = h->pt;
-  a.parents = P;
-  a.H = h->H;
-  a.birth_base = h->n_comp;
-  a.nb = h->nb;
-  a.Z = h->d_Z;
-  a.M = M;
-  a.key = philox_key(h);
-  a.T_max = h->T_max;
-  a.K_max = h->K_max;
-  a.n_groups = G;
-  a.smem_bytes = expand_smem_bytes(dz, 0, h->T_max, h->K_max, M, h->cfg.h_up, G);
-  a.child_key = h->child_key;
-  a.child_status = h->child_status;
-  a.child_alive = h->child_alive;
-  a.materialize = 0;
-  a.err = h->d_scal + S_ERR;
-  prof_begin(h, kStageExpand);
-  launch_expand(a, h->stream);
-  prof_end(h, kStageExpand);
-  CU(cudaGetLastError());
-  h->H_par = h->H;
-  h->par_buf = h->hcur;
-  h->birth_base = h->n_comp;
-  h->stage = 2;
-  h->have_update = true;
   return GLMB_OK;
 }
 
-glmb_status glmb_prune(glmb_handle* h) {
-  if (!h) return GLMB_E_INVALID;
-  if (h->stage != 2) return fail(h, GLMB_E_STATE, "prune: call glmb_update first");
-  h->retained_valid = false;
-  const int dz = h->md.dz;
-  const long long n = (long long)h->H * h->cfg.h_up;
+// frame sizes to the device (pinned slot -> d_fs)
+glmb_status upload_sizes(glmb_handle* h, int slot) {
+  FrameDev& f = h->h_fs[slot];
+  f = FrameDev{};
+  f.n_comp = h->n_comp;
+  f.nb = h->nb;
+  f.T = h->T_work;
+  f.M = h->M;
+  f.H = h->H;
+  f.frame = h->frame;
+  CU(cudaMemcpyAsync(h->d_fs, &f, sizeof f, cudaMemcpyHostToDevice, h->stream));
+  return GLMB_OK;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+glmb_status enqueue_predict(glmb_handle* h, const Plan& p) {
+  const CompTable& A = h->comps[h->cur];
+  const CompTable& B = h->comps[1 - h->cur];
+  const int gp = p.fixed ? 8 * h->n_sm : std::max(1, std::min((h->T_work + 127) / 128, 8 * h->n_sm));
+  prof_begin(h, kStagePredict);
+  launch_predict(h->md, A, B, h->d_fs, h->d_births, gp, h->stream);
+  prof_end(h, kStagePredict);
+  return GLMB_OK;
+}
+
+glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
+  const CompTable& B = h->comps[1 - h->cur];
+  const int T = h->T_work, dz = h->md.dz;
+  const long long cap = p.fixed ? h->cap_comp : std::max(T, 1);
+  CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
+  prof_begin(h, kStageTable);
+  launch_check_finite(h->d_Z, h->d_fs, dz, h->d_scal + S_ERR, h->stream);
+  const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
+  launch_table_count(h->md, B, h->pt, h->d_fs, h->d_Z, gt, h->stream);
+  scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32,
+           h->stream);
+  launch_table_write(h->md, B, h->pt, h->d_fs, h->d_Z, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
+                     h->stream);
+  const int gs = p.fixed ? 4 * h->n_sm : std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm));
+  launch_parent_stats(h->hyps[h->hcur], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
+                      gs, h->stream);
+  prof_end(h, kStageTable);
+  return GLMB_OK;
+}
+
+ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
+  ExpandArgs a{};
+  a.md = h->md;
+  a.ct = h->comps[1 - h->cur];
+  a.pt = h->pt;
+  a.parents = h->hyps[h->hcur];
+  a.fs = h->d_fs;
+  a.T_max = p.T;
+  a.K_max = p.K;
+  a.M_plan = p.M;
+  a.n_groups = mat ? p.Gm : p.G;
+  a.smem_bytes = expand_smem_bytes(h->md.dz, mat ? 1 : 0, p.T, p.K, p.M, h->cfg.h_up, a.n_groups);
+  a.materialize = mat ? 1 : 0;
+  a.err = h->d_scal + S_ERR;
+  return a;
+}
+
+glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
+  ExpandArgs a = expand_args(h, p, false);
+  a.child_key = h->child_key;
+  a.child_status = h->child_status;
+  a.child_alive = h->child_alive;
+  const int full = std::max(1, expand_max_ctas(a)) * h->n_sm;
+  const int grid = p.fixed ? full : std::min(h->H, full);
+  prof_begin(h, kStageExpand);
+  launch_expand(a, grid, h->stream);
+  prof_end(h, kStageExpand);
+  return GLMB_OK;
+}
+
+glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
+  cudaStream_t s = h->stream;
+  const int h_up = h->cfg.h_up;
+  const long long n = p.fixed ? h->cap_children : (long long)h->H * h_up;
   const int nblk = (int)std::min<long long>(std::max(1LL, (n + 255) / 256), 2LL * h->n_sm);
   const double log_tau = std::log(h->cfg.tau);
   const double vmax = std::max(1.0, -log_tau) * 4294967296.0 + 2.0;
   const int nbits = std::max(1, (int)std::ceil(std::log2(vmax)));
-  cudaStream_t s = h->stream;
   const HypTable& P = h->hyps[h->hcur];
   HypTable& O = h->hyps[1 - h->hcur];
   const CompTable& B = h->comps[1 - h->cur];
   CompTable& A = h->comps[h->cur];
-  auto abandon = [&](glmb_status st, const char* msg) {
-    h->frame -= 1;
-    h->stage = 0;
-    return fail(h, st, "prune: %s", msg);
-  };
   CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
   prof_begin(h, kStageSelect);
-  launch_lse(h->child_key, n, h->pw, log_tau, h->cap_h, nblk, s);
-  launch_select(h->child_key, n, h->cap_h, nbits, h->pw, nblk, s);
-  launch_compact(h->child_key, n, h->pw, h->cap_h, s);
-  launch_finalize(h->pw, h->child_key, h->child_alive, P, h->cfg.h_up, O, h->cap_h,
-                  h->d_scal + S_ERR, h->cap_entries, s);
+  launch_lse(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nblk, s);
+  launch_select(h->child_key, h->d_fs, h_up, nbits, h->pw, nblk, s);
+  launch_compact(h->child_key, h->d_fs, h_up, n, h->pw, h->cap_h, nblk, s);
+  launch_finalize(h->pw, h->child_key, h->child_alive, P, h_up, O, h->cap_h, h->d_scal + S_ERR,
+                  h->cap_entries, s);
   prof_end(h, kStageSelect);
   CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), s));
   CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));
-  ExpandArgs a{};
-  a.md = h->md;
-  a.ct = B;
-  a.pt = h->pt;
-  a.parents = P;
-  a.H = h->H;
-  a.birth_base = h->n_comp;
-  a.nb = h->nb;
-  a.Z = h->d_Z;
-  a.M = h->M;
-  a.key = philox_key(h);
-  a.T_max = h->T_max;
-  a.K_max = h->K_max;
-  a.n_groups = expand_plan_groups(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, h->smem_limit, 8);
-  a.smem_bytes = expand_smem_bytes(dz, 1, h->T_max, h->K_max, h->M, h->cfg.h_up, a.n_groups);
-  a.materialize = 1;
+  ExpandArgs a = expand_args(h, p, true);
   a.surv_idx = h->pw.surv_idx;
   a.n_surv = h->pw.counts;
   a.out_ptr = O.ptr;
@@ -641,28 +654,79 @@ glmb_status glmb_prune(glmb_handle* h) {
   a.upd_se = h->upd_se;
   a.upd_count = h->d_scal + S_NUPD;
   a.cap_upd = (int)h->cap_upd;
-  a.err = h->d_scal + S_ERR;
+  const int full = std::max(1, expand_max_ctas(a)) * h->n_sm;
   prof_begin(h, kStageMat);
-  launch_expand(a, s);
+  launch_expand(a, p.fixed ? full : std::min(h->H, full), s);
   prof_end(h, kStageMat);
   const int T = h->T_work;
+  const long long capT = p.fixed ? h->cap_comp : std::max(T, 1);
   prof_begin(h, kStageGc);
-  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)std::max(T, 1) * sizeof(uint32_t), s));
+  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));
   launch_mark_old(O.comp, h->pw.counts + 1, h->cap_entries, h->d_scal + S_ERR, h->gc_flag, s);
-  scan_u32(h->gc_flag, h->gc_newpos, T, h->d_scal + S_NKEEP, h->scan_tmp32, s);
-  launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, T, h->d_scal + S_NKEEP, h->upd_src,
-                        h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts,
-                        h->d_scal + S_ERR, s);
+  scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
+           h->scan_tmp32, s);
+  const int ggc = p.fixed ? 8 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
+  launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP,
+                        h->upd_src, h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD,
+                        h->pw.counts, h->d_scal + S_ERR, ggc, s);
   launch_remap(O.comp, h->pw.counts + 1, h->cap_entries, h->gc_newpos, h->hvals,
                h->d_scal + S_NKEEP, h->d_scal + S_ERR, s);
   prof_end(h, kStageGc);
   CU(cudaGetLastError());
+  return GLMB_OK;
+}
+
+// expansion plan of this frame: slots exactly (largest survivor of the last
+// prune plus births), gated pairs from earlier frames (redone if exceeded)
+bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, Plan& p) {
+  p.fixed = fixed;
+  p.T = std::max(1, T_plan);
+  p.K = std::max(64, K_plan);
+  p.M = std::max(1, h->M);
+  int want = std::max(4, std::min(16, (32 * h->n_sm + h->H - 1) / std::max(1, h->H)));
+  if (fixed) {
+    p.T = round_up(p.T, 32);
+    p.K = round_up(p.K, 256);
+    p.M = round_up(p.M, 64);
+    want = h->H <= 2 * h->n_sm ? 16 : (h->H <= 4 * h->n_sm ? 8 : 4);
+  }
+  const int dz = h->md.dz;
+  p.G = expand_plan_groups(dz, 0, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit,
+                           std::min(want, h->cfg.h_up));
+  p.Gm = expand_plan_groups(dz, 1, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit, 8);
+  return p.G > 0 && p.Gm > 0;
+}
+
+// frame result: commit, abandon, or redo with exact maxima; `done` on return
+glmb_status finish_frame(glmb_handle* h) {
+  auto abandon = [&](glmb_status st, const char* msg) {
+    h->frame -= 1;
+    h->stage = 0;
+    return fail(h, st, "prune: %s", msg);
+  };
   unsigned cnt[8];
-  CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
   glmb_status st = sync_scal(h);
   if (st != GLMB_OK) return st;
-  const unsigned e = h->h_scal[S_ERR];
+  unsigned e = h->h_scal[S_ERR];
+  if ((e & kErrSlots) && !(e & (kErrFatal & ~kErrSlots))) {
+    // a parent had more gated pairs than planned: redo the expansion and
+    // the pruning with the exact maxima of this frame
+    ++h->redo_count;
+    Plan p;
+    if (!make_plan(h, false, std::max(1, (int)h->h_scal[S_MAXT]), std::max(1, (int)h->h_scal[S_MAXK]), p))
+      return abandon(GLMB_E_CAPACITY, "per-hypothesis table does not fit in shared memory");
+    CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
+    if ((st = enqueue_expand(h, p)) != GLMB_OK) return st;
+    if ((st = enqueue_prune(h, p)) != GLMB_OK) return st;
+    CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+    if ((st = sync_scal(h)) != GLMB_OK) return st;
+    e = h->h_scal[S_ERR];
+  }
+  if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
   if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
+  h->n_pairs = h->h_scal[S_K];
+  h->n_fp64 = (int)h->h_scal[S_FP64];
   const unsigned n_surv = cnt[0];
   if (n_surv == 0) return abandon(GLMB_E_NUMERIC, "no child has a finite weight above tau");
   const unsigned n_keep = h->h_scal[S_NKEEP], n_upd = h->h_scal[S_NUPD];
@@ -670,6 +734,8 @@ glmb_status glmb_prune(glmb_handle* h) {
   prof_collect(h);
   // commit
   h->n_unique = cnt[2];
+  h->alive_max = (int)cnt[3];
+  h->K_est = round_up((int)(1.25 * h->h_scal[S_MAXK]) + 32, 64);
   h->n_upd = (int)n_upd;
   h->n_comp = (int)(n_keep + n_upd);
   h->H = (int)n_surv;
@@ -680,6 +746,184 @@ glmb_status glmb_prune(glmb_handle* h) {
   h->retained_valid = true;
   h->stage = 0;
   return GLMB_OK;
+}
+
+}  // namespace
+
+glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 0) return fail(h, GLMB_E_STATE, "predict: previous frame not pruned");
+  glmb_status st = stage_births(h, births, n_births);
+  if (st != GLMB_OK) return st;
+  h->frame += 1;
+  h->nb = n_births;
+  h->T_work = h->n_comp + n_births;
+  h->M = 0;
+  if ((st = upload_sizes(h, 0)) != GLMB_OK) return st;
+  if (n_births)
+    CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
+                       cudaMemcpyHostToDevice, h->stream));
+  Plan p{};
+  p.fixed = false;
+  enqueue_predict(h, p);
+  CU(cudaGetLastError());
+  h->stage = 1;
+  h->have_update = false;
+  return GLMB_OK;
+}
+
+glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 1) return fail(h, GLMB_E_STATE, "update: call glmb_predict first");
+  glmb_status st = stage_detections(h, Z, M, z_is_device);
+  if (st != GLMB_OK) {
+    if (st == GLMB_E_INVALID && M > 0 && Z) {
+      h->frame -= 1;
+      h->stage = 0;
+    }
+    return st;
+  }
+  h->M = M;
+  if ((st = upload_sizes(h, 1)) != GLMB_OK) return st;
+  Plan p;
+  if (!make_plan(h, false, h->alive_max + h->nb, h->K_est, p)) {
+    // the estimate does not fit; plan from the exact maxima of this frame
+    Plan q{};
+    q.fixed = false;
+    enqueue_table(h, q);
+    CU(cudaStreamSynchronize(h->stream));
+    unsigned mk = 0;
+    CU(cudaMemcpy(&mk, h->d_scal + S_MAXK, sizeof mk, cudaMemcpyDeviceToHost));
+    if (!make_plan(h, false, h->alive_max + h->nb, (int)mk, p)) {
+      h->frame -= 1;
+      h->stage = 0;
+      return fail(h, GLMB_E_CAPACITY, "update: per-hypothesis table does not fit in shared memory");
+    }
+  } else {
+    enqueue_table(h, p);
+  }
+  h->plan = p;
+  enqueue_expand(h, p);
+  CU(cudaGetLastError());
+  h->H_par = h->H;
+  h->par_buf = h->hcur;
+  h->birth_base = h->n_comp;
+  h->stage = 2;
+  h->have_update = true;
+  return GLMB_OK;
+}
+
+glmb_status glmb_prune(glmb_handle* h) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 2) return fail(h, GLMB_E_STATE, "prune: call glmb_update first");
+  h->retained_valid = false;
+  glmb_status st = enqueue_prune(h, h->plan);
+  if (st != GLMB_OK) return st;
+  return finish_frame(h);
+}
+
+glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
+                      int z_is_device) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 0) return fail(h, GLMB_E_STATE, "step: a frame is in progress");
+  glmb_status st = stage_births(h, births, n_births);
+  if (st != GLMB_OK) return st;
+  st = stage_detections(h, Z, M, z_is_device);
+  if (st != GLMB_OK) return st;
+  h->frame += 1;
+  h->nb = n_births;
+  h->T_work = h->n_comp + n_births;
+  h->M = M;
+  Plan p;
+  if (!make_plan(h, true, h->alive_max + h->nb, h->K_est, p) &&
+      !make_plan(h, false, h->alive_max + h->nb, h->K_est, p)) {
+    h->frame -= 1;
+    return fail(h, GLMB_E_CAPACITY, "step: per-hypothesis table does not fit in shared memory");
+  }
+  if ((st = upload_sizes(h, 1)) != GLMB_OK) return st;
+  if (n_births)
+    CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
+                       cudaMemcpyHostToDevice, h->stream));
+  h->retained_valid = false;
+  h->plan = p;
+  if (p.fixed) {
+    // Replay a captured graph whose plan covers this frame (same buffer
+    // parity and profiling mask; slots, pairs and detections at least this
+    // frame's); otherwise capture one with headroom.  Plans only grow, so
+    // captures are rare after the first frames.
+    int best = -1;
+    for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
+      const glmb_handle::CachedGraph& g = h->graphs[gi];
+      if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.T < p.T || g.plan.K < p.K ||
+          g.plan.M < p.M)
+        continue;
+      if (best < 0 || (g.plan.G == p.G && h->graphs[best].plan.G != p.G)) best = gi;
+    }
+    if (best < 0) {
+      Plan q = p;
+      q.T = round_up(p.T + p.T / 4, 32);
+      q.K = round_up(p.K + p.K / 2, 256);
+      q.M = round_up(p.M + p.M / 4, 64);
+      if (!make_plan(h, true, q.T, q.K, q) || q.M < p.M) {
+        q = p;
+      } else {
+        q.M = std::max(q.M, round_up(p.M + p.M / 4, 64));
+        const int dz = h->md.dz;
+        q.G = expand_plan_groups(dz, 0, q.T, q.K, q.M, h->cfg.h_up, h->smem_limit, p.G);
+        q.Gm = expand_plan_groups(dz, 1, q.T, q.K, q.M, h->cfg.h_up, h->smem_limit, p.Gm);
+        if (q.G == 0 || q.Gm == 0) q = p;
+      }
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
+      enqueue_predict(h, q);
+      enqueue_table(h, q);
+      enqueue_expand(h, q);
+      enqueue_prune(h, q);
+      h->capturing = false;
+      CU(cudaStreamEndCapture(h->stream, &graph));
+      size_t n_nodes = 0;
+      cudaGraphGetNodes(graph, nullptr, &n_nodes);
+      std::vector<cudaGraphNode_t> nodes(n_nodes);
+      long long n_kernels = 0;
+      if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+        for (auto nd : nodes) {
+          cudaGraphNodeType ty;
+          if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_kernels;
+        }
+      g_launches -= n_kernels;   // counted once per replay below, not at capture
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return fail(h, GLMB_E_CUDA, "step: graph instantiation: %s", cudaGetErrorString(ie));
+      if (h->graphs.size() >= 8) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+      }
+      h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels});
+      ++h->n_captures;
+      best = (int)h->graphs.size() - 1;
+    }
+    const glmb_handle::CachedGraph& g = h->graphs[best];
+    h->plan = g.plan;
+    g_launches += g.n_kernels;
+    CU(cudaGraphLaunch(g.exec, h->stream));
+    ++h->n_graph_launches;
+    for (int s = 0; s < kStageEstimates; ++s)
+      if ((h->prof_mask & (1u << s)) && h->ev[s][0]) h->ev_pending[s] = true;
+  } else {
+    enqueue_predict(h, p);
+    enqueue_table(h, p);
+    enqueue_expand(h, p);
+    enqueue_prune(h, p);
+  }
+  CU(cudaGetLastError());
+  h->H_par = h->H;
+  h->par_buf = h->hcur;
+  h->birth_base = h->n_comp;
+  h->have_update = true;
+  h->stage = 2;
+  return finish_frame(h);
 }
 
 glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n) {
@@ -705,11 +949,19 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
   info->n_components = h->n_comp;
   info->n_meas = h->M;
   info->n_pairs = h->n_pairs;
+  if (h->have_update) {
+    uint32_t K32 = 0;
+    CU(cudaMemcpy(&K32, h->pt.ptr + h->T_work, sizeof K32, cudaMemcpyDeviceToHost));
+    info->n_pairs = K32;
+  }
   info->n_children = h->have_update ? (long long)h->H_par * h->cfg.h_up : 0;
   info->n_unique = h->n_unique;
   info->n_updates = h->n_upd;
   info->n_fp64_chol = h->n_fp64;
   info->n_launches = g_launches;
+  info->n_graph_captures = h->n_captures;
+  info->n_graph_launches = h->n_graph_launches;
+  info->n_redo = h->redo_count;
   return GLMB_OK;
 }
 
@@ -921,6 +1173,8 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
   h->n_comp = nc;
   h->H = hd.n_hyp;
   h->n_entries = hd.n_tracks;
+  h->alive_max = 0;
+  for (int y = 0; y < hd.n_hyp; ++y) h->alive_max = std::max(h->alive_max, (int)(ptr[y + 1] - ptr[y]));
   h->frame = hd.frame;
   h->stage = 0;
   h->have_update = false;
@@ -1040,7 +1294,9 @@ glmb_status glmb_get_pairs(glmb_handle* h, uint32_t* comp_ptr, uint32_t* meas, f
   if (!h->have_update) return fail(h, GLMB_E_STATE, "get_pairs: no update");
   CU(cudaStreamSynchronize(h->stream));
   const int T = h->T_work, dz = h->md.dz;
-  const long long K = h->n_pairs;
+  uint32_t K32 = 0;
+  CU(cudaMemcpy(&K32, h->pt.ptr + T, sizeof K32, cudaMemcpyDeviceToHost));
+  const long long K = std::min<long long>(K32, h->cap_pairs);
   *n_pairs = K;
   if (T + 1 > cap_comp || K > cap_pairs) return fail(h, GLMB_E_CAPACITY, "get_pairs: caps");
   if (comp_ptr) CU(cudaMemcpy(comp_ptr, h->pt.ptr, (size_t)(T + 1) * 4, cudaMemcpyDeviceToHost));

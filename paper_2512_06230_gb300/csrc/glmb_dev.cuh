@@ -56,6 +56,19 @@ struct Model {
   uint32_t seed_lo, seed_hi;
 };
 
+// Sizes of the current frame.  Kernels read them from device memory, so a
+// frame's launches depend only on capacities (grids are grid-stride or
+// persistent) and the host needs no synchronisation inside a frame.
+struct FrameDev {
+  int n_comp;             // components of the state table
+  int nb;                 // births of this frame
+  int T;                  // n_comp + nb: components of the working table
+  int M;                  // detections
+  int H;                  // parents (hypotheses before the update)
+  int frame;              // frame number: birth labels and the random-number key
+  int pad[2];
+};
+
 struct CompTable {
   float* mhi;             // [dx][cap]
   float* mlo;             // [dx][cap]

@@ -11,38 +11,41 @@ namespace glmb {
 extern long long g_launches;
 
 // ---- prediction, births, table (kernels_table.cu) ----
-// prediction of n components from src into dst, then nb births appended at
-// dst[n..n+nb) (births_dev: per birth [r, mean[6], cov[36]] in FP64)
-void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
-                    const double* births_dev, int nb, int frame, cudaStream_t s);
-void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt, int T,
-                        const float* Z, int M, cudaStream_t s);
-void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt, int T,
-                        const float* Z, int M, unsigned* n_fp64, unsigned* err, cudaStream_t s);
-void launch_check_finite(const float* Z, long long n, unsigned* err, cudaStream_t s);
-void launch_parent_stats(const HypTable& hp, int H, const PairTable& pt, int birth_base, int nb,
-                         unsigned* max_T, unsigned* max_K, cudaStream_t s);
+// Sizes come from the device FrameDev; grid is the number of blocks of a
+// grid-stride launch.
+// prediction of fs->n_comp components from src into dst, then fs->nb births
+// appended at dst[n_comp..) (births_dev: per birth [r, mean[6], cov[36]] FP64)
+void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, const FrameDev* fs,
+                    const double* births_dev, int grid, cudaStream_t s);
+void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
+                        const FrameDev* fs, const float* Z, int grid, cudaStream_t s);
+void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
+                        const FrameDev* fs, const float* Z, unsigned* n_fp64, unsigned* err,
+                        int grid, cudaStream_t s);
+void launch_check_finite(const float* Z, const FrameDev* fs, int dz, unsigned* err, cudaStream_t s);
+void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
+                         unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s);
 
-// exclusive scans; tmp must hold scan_tmp_elems(n) elements of the value type
-long long scan_tmp_elems(long long n);
-void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* total, uint32_t* tmp,
-              cudaStream_t s);
-void scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
-              unsigned long long* total, unsigned long long* tmp, cudaStream_t s);
+// exclusive scans of (*n_dev * mult) elements, at most cap; tmp must hold
+// scan_tmp_elems(cap) elements; total (nullable) receives the sum, and with
+// total_at_end the sum is also written to out[n]
+long long scan_tmp_elems(long long cap);
+void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
+              uint32_t* total, bool total_at_end, uint32_t* tmp, cudaStream_t s);
+void scan_u64(const unsigned long long* in, unsigned long long* out, const int* n_dev, int mult,
+              long long cap, unsigned long long* total, bool total_at_end,
+              unsigned long long* tmp, cudaStream_t s);
 
 // ---- expansion / materialisation (kernels_expand.cu) ----
 struct ExpandArgs {
   Model md;
-  CompTable ct;
+  CompTable ct;           // working (predicted) table
   PairTable pt;
   HypTable parents;       // hypotheses before the update
-  int H;                  // number of parents
-  int birth_base, nb;     // birth components of this frame
-  const float* Z;
-  int M;
-  uint2 key;              // Philox key (seed_lo, seed_hi ^ frame)
-  // staging plan (sizes fixed by the host from the per-parent maxima)
-  int T_max, K_max, n_groups;
+  const FrameDev* fs;     // H, M, births, frame
+  // shared-memory plan: largest slots, gated pairs and detections per parent
+  // (a parent beyond the plan sets kErrSlots and is redone with a larger plan)
+  int T_max, K_max, M_plan, n_groups;
   int smem_bytes;
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
@@ -70,7 +73,10 @@ int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int 
 // draw groups (warps) per CTA: as many as fit, up to max_groups (<= 16)
 int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
                        int smem_limit, int max_groups);
-void launch_expand(const ExpandArgs& a, cudaStream_t s);
+// resident CTAs per SM for this plan
+int expand_max_ctas(const ExpandArgs& a);
+// one persistent CTA per grid slot, looping over the parents
+void launch_expand(const ExpandArgs& a, int grid, cudaStream_t s);
 
 // ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
 struct PruneWork {
@@ -84,25 +90,26 @@ struct PruneWork {
   unsigned long long* flags;    // [n_children] packed (gt, eq) prefix counts
   unsigned long long* flags_tmp;
   long long* surv_idx;          // [cap_h]
-  unsigned* counts;             // [8]: n_surv, n_entries, n_keep, n_upd, ...
+  unsigned* counts;             // [8]: n_surv, n_entries, n_unique, max alive, [4..5] scan total
 };
-void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau, int h_max,
-                int nblk, cudaStream_t s);
-void launch_select(const long long* keys, long long n, int h_max, int nbits, PruneWork w,
+// the children are the fs->H * h_up entries of keys
+void launch_lse(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
+                int h_max, int nblk, cudaStream_t s);
+void launch_select(const long long* keys, const FrameDev* fs, int h_up, int nbits, PruneWork w,
                    int nblk, cudaStream_t s);
-void launch_compact(const long long* keys, long long n, PruneWork w, int h_max,
-                    cudaStream_t s);
+void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long long cap, PruneWork w,
+                    int h_max, int nblk, cudaStream_t s);
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
                      const HypTable& parents, int h_up, HypTable out, int h_max,
                      unsigned* err, long long cap_entries, cudaStream_t s);
 void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
                      const unsigned* err, uint32_t* flag, cudaStream_t s);
 void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
-                           const uint32_t* newpos, const uint32_t* flag, int n_src,
+                           const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
                            const unsigned* n_keep_dev, const uint32_t* upd_src,
                            const uint32_t* upd_m, const long long* upd_se, int cap_upd,
                            const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
-                           cudaStream_t s);
+                           int grid, cudaStream_t s);
 void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
                   const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
                   const unsigned* err, cudaStream_t s);

@@ -165,13 +165,27 @@ __device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long
 }
 
 template <int DZ, bool MAT>
+__device__ void expand_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm);
+
+// Persistent: each CTA takes parents blockIdx.x, blockIdx.x + gridDim.x, ...
+template <int DZ, bool MAT>
 __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
+  const Lay L = make_lay(DZ, MAT, a.T_max, a.K_max, a.M_plan, a.md.h_up, a.n_groups);
+  const int H = a.fs->H;
+  for (int h = blockIdx.x; h < H; h += gridDim.x) {
+    __syncthreads();   // the previous parent's shared memory is free
+    expand_parent<DZ, MAT>(a, h, L, sm);
+  }
+}
+
+template <int DZ, bool MAT>
+__device__ void expand_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm) {
   const Model& md = a.md;
   const int HU = md.h_up;
-  const int M = a.M;
-  const int h = blockIdx.x;
-  const Lay L = make_lay(DZ, MAT, a.T_max, a.K_max, M, HU, a.n_groups);
+  const int M = a.fs->M;
+  const int birth_base = a.fs->n_comp, nb = a.fs->nb;
+  const uint2 key = make_uint2(md.seed_lo, md.seed_hi ^ (uint32_t)a.fs->frame);
   Scal& sc = *at<Scal>(sm, L.scal);
   uint32_t* s_comp = at<uint32_t>(sm, L.comp);
   uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
@@ -208,7 +222,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
   if (tid == 0) {
     const uint32_t lo = a.parents.ptr[h], hi = a.parents.ptr[h + 1];
     sc.Town = (int)(hi - lo);
-    sc.T = sc.Town + a.nb;
+    sc.T = sc.Town + nb;
     sc.ref_score = 0;
     sc.ninf_ref = 0;
     sc.nclut_ref = 0;
@@ -228,7 +242,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
       while (l < r) { const int mid = (l + r) >> 1; if (a.surv_idx[mid] < hi_key) l = mid + 1; else r = mid; }
       sc.s_hi = l;
     }
-    if (sc.T > a.T_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+    if (sc.T > a.T_max || M > a.M_plan) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
     // a frame already abandoned (e.g. entries beyond capacity) writes nothing
     if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) sc.bad = 1;
   }
@@ -240,7 +254,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
 
   // ---- slots ----
   for (int t = tid; t < T; t += nthr) {
-    const uint32_t c = t < Town ? a.parents.comp[plo + t] : (uint32_t)(a.birth_base + (t - Town));
+    const uint32_t c = t < Town ? a.parents.comp[plo + t] : (uint32_t)(birth_base + (t - Town));
     s_comp[t] = c;
     s_dthr[t] = pt.dthr[c];
     s_logp[t] = ct.logp[c];
@@ -442,7 +456,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
     for (int x = lane; x < ndpc; x += 32) {
       const uint32_t ent = s_dpc[x];
       const uint32_t cc = ent >> 4, mask = ent & 15u;
-      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), a.key);
+      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (!((mask >> b) & 1u)) continue;
@@ -483,7 +497,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
           for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
         continue;
       }
-      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), a.key);
+      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), key);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int i = i0 + b;
@@ -660,26 +674,35 @@ __global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
   }
 }
 
-void launch_expand(const ExpandArgs& a, cudaStream_t s) {
-  const int nblk = a.H;
-  if (nblk <= 0) return;
+template <int DZ, bool MAT>
+static void launch_one(const ExpandArgs& a, int grid, cudaStream_t s) {
+  cudaFuncSetAttribute(expand_kernel<DZ, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       a.smem_bytes);
+  expand_kernel<DZ, MAT><<<grid, 32 * a.n_groups, a.smem_bytes, s>>>(a);
+  ++g_launches;
+}
+
+int expand_max_ctas(const ExpandArgs& a) {
+  int per_sm = 0;
   const int threads = 32 * a.n_groups;
+  cudaError_t e;
+  if (a.md.dz == 2)
+    e = a.materialize ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<2, true>, threads, a.smem_bytes)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<2, false>, threads, a.smem_bytes);
+  else
+    e = a.materialize ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<3, true>, threads, a.smem_bytes)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<3, false>, threads, a.smem_bytes);
+  return e == cudaSuccess ? per_sm : 0;
+}
+
+void launch_expand(const ExpandArgs& a, int grid, cudaStream_t s) {
+  if (grid <= 0) return;
   if (a.md.dz == 2) {
-    if (a.materialize) {
-      cudaFuncSetAttribute(expand_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
-      expand_kernel<2, true><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
-    } else {
-      cudaFuncSetAttribute(expand_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
-      expand_kernel<2, false><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
-    }
+    if (a.materialize) launch_one<2, true>(a, grid, s);
+    else launch_one<2, false>(a, grid, s);
   } else {
-    if (a.materialize) {
-      cudaFuncSetAttribute(expand_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
-      expand_kernel<3, true><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
-    } else {
-      cudaFuncSetAttribute(expand_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes);
-      expand_kernel<3, false><<<nblk, threads, a.smem_bytes, s>>>(a); ++g_launches;
-    }
+    if (a.materialize) launch_one<3, true>(a, grid, s);
+    else launch_one<3, false>(a, grid, s);
   }
 }
 

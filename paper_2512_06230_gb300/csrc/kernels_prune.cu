@@ -67,9 +67,10 @@ __device__ Lse block_lse(Lse v) {
 // partials; the last block combines them in a fixed tree, so the result does
 // not depend on scheduling.  Also counts the unique children and sets the
 // fixed-point threshold log(tau) + LSE.
-__global__ void lse_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
-                           double log_tau, int h_max) {
+__global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* __restrict__ fs,
+                           int h_up, PruneWork w, double log_tau, int h_max) {
   __shared__ bool last;
+  const long long n = (long long)fs->H * h_up;
   Lse v{kKeyInvalid, 0.0};
   unsigned valid = 0;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -114,9 +115,9 @@ __global__ void lse_kernel(const long long* __restrict__ keys, long long n, Prun
   }
 }
 
-void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau, int h_max,
-                int nblk, cudaStream_t s) {
-  lse_kernel<<<nblk, kRedThreads, 0, s>>>(keys, n, w, log_tau, h_max); ++g_launches;
+void launch_lse(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
+                int h_max, int nblk, cudaStream_t s) {
+  lse_kernel<<<nblk, kRedThreads, 0, s>>>(keys, fs, h_up, w, log_tau, h_max); ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -126,9 +127,10 @@ void launch_lse(const long long* keys, long long n, PruneWork w, double log_tau,
 // ---------------------------------------------------------------------------
 constexpr int kDigit = 12, kBins = 1 << kDigit;
 
-__global__ void radix_hist_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
-                                  int shift) {
+__global__ void radix_hist_kernel(const long long* __restrict__ keys,
+                                  const FrameDev* __restrict__ fs, int h_up, PruneWork w, int shift) {
   __shared__ unsigned hist[kBins];
+  const long long n = (long long)fs->H * h_up;
   if (w.sel[3] != 0) return;
   for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist[b] = 0;
   __syncthreads();
@@ -206,13 +208,12 @@ __global__ void radix_find_kernel(PruneWork w, int shift, int first) {
   }
 }
 
-void launch_select(const long long* keys, long long n, int h_max, int nbits, PruneWork w,
+void launch_select(const long long* keys, const FrameDev* fs, int h_up, int nbits, PruneWork w,
                    int nblk, cudaStream_t s) {
-  (void)h_max;
   const int passes = (nbits + kDigit - 1) / kDigit;
   for (int p = 0; p < passes; ++p) {
     const int shift = (passes - 1 - p) * kDigit;
-    radix_hist_kernel<<<nblk, 256, 0, s>>>(keys, n, w, shift); ++g_launches;
+    radix_hist_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w, shift); ++g_launches;
     radix_find_kernel<<<1, kBins / 4, 0, s>>>(w, shift, p == 0); ++g_launches;
   }
 }
@@ -230,15 +231,18 @@ __device__ __forceinline__ unsigned long long keep_bits(long long k, long long t
   return 0ULL;
 }
 
-__global__ void keep_flags_kernel(const long long* __restrict__ keys, long long n, PruneWork w) {
+__global__ void keep_flags_kernel(const long long* __restrict__ keys,
+                                  const FrameDev* __restrict__ fs, int h_up, PruneWork w) {
+  const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x)
     w.flags[j] = keep_bits(keys[j], thr, bnd, need, mode);
 }
 
-__global__ void keep_write_kernel(const long long* __restrict__ keys, long long n, PruneWork w,
-                                  int h_max) {
+__global__ void keep_write_kernel(const long long* __restrict__ keys,
+                                  const FrameDev* __restrict__ fs, int h_up, PruneWork w, int h_max) {
+  const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
@@ -252,12 +256,12 @@ __global__ void keep_write_kernel(const long long* __restrict__ keys, long long 
   }
 }
 
-void launch_compact(const long long* keys, long long n, PruneWork w, int h_max,
-                    cudaStream_t s) {
-  const int nb = (int)min((n + 255) / 256, 4096LL);
-  keep_flags_kernel<<<nb, 256, 0, s>>>(keys, n, w); ++g_launches;
-  scan_u64(w.flags, w.flags, n, (unsigned long long*)(w.counts + 4), w.flags_tmp, s);
-  keep_write_kernel<<<nb, 256, 0, s>>>(keys, n, w, h_max); ++g_launches;
+void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long long cap, PruneWork w,
+                    int h_max, int nblk, cudaStream_t s) {
+  keep_flags_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w); ++g_launches;
+  scan_u64(w.flags, w.flags, &fs->H, h_up, cap, (unsigned long long*)(w.counts + 4), false,
+           w.flags_tmp, s);
+  keep_write_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w, h_max); ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -320,6 +324,7 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
       const long long hpar = j / h_up, nd = j % h_up;
       out.uid[s] = mix64(parents.uid[hpar] + 0x9E3779B97F4A7C15ULL * (unsigned long long)(nd + 1));
       na = child_alive[j];
+      atomicMax(&w.counts[3], na);
     }
     // block exclusive scan of na
     uint32_t x = na;
@@ -542,12 +547,13 @@ __device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
 
 template <int DZ>
 __global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
-                          const uint32_t* __restrict__ flag, int n_src,
+                          const uint32_t* __restrict__ flag, const FrameDev* __restrict__ fs,
                           const unsigned* __restrict__ n_keep_dev, const uint32_t* __restrict__ upd_src,
                           const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,
                           int cap_upd, const unsigned* __restrict__ n_upd_dev,
                           const unsigned* __restrict__ n_surv_dev, unsigned* err) {
   if (*n_surv_dev == 0u || (*(volatile unsigned*)err & kErrFatal)) return;
+  const int n_src = fs->T;
   const unsigned n_keep = *n_keep_dev;
   const unsigned n_upd = min(*n_upd_dev, (unsigned)cap_upd);
   if ((long long)n_keep + n_upd > dst.cap) {
@@ -572,19 +578,17 @@ __global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t
 }
 
 void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
-                           const uint32_t* newpos, const uint32_t* flag, int n_src,
+                           const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
                            const unsigned* n_keep_dev, const uint32_t* upd_src,
                            const uint32_t* upd_m, const long long* upd_se, int cap_upd,
                            const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
-                           cudaStream_t s) {
-  const long long bound = (long long)n_src + cap_upd;
-  const int nb = (int)max(1LL, min((bound + 127) / 128, 2048LL));
+                           int grid, cudaStream_t s) {
   if (md.dz == 2) {
-    gc_kernel<2><<<nb, 128, 0, s>>>(md, src, dst, newpos, flag, n_src, n_keep_dev, upd_src, upd_m,
-                                    upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
+    gc_kernel<2><<<grid, 128, 0, s>>>(md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+                                      upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
   } else {
-    gc_kernel<3><<<nb, 128, 0, s>>>(md, src, dst, newpos, flag, n_src, n_keep_dev, upd_src, upd_m,
-                                    upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
+    gc_kernel<3><<<grid, 128, 0, s>>>(md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+                                      upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
   }
   ++g_launches;
 }

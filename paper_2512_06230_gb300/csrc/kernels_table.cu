@@ -22,14 +22,21 @@ __device__ void birth_comp(const Model& md, const CompTable& ct, int c, const do
                            int b, int frame);
 
 template <int DZ>
-__global__ void predict_kernel(Model md, CompTable src, CompTable ct, int n,
-                               const double* __restrict__ births, int nb, int frame) {
-  constexpr int DX = 2 * DZ;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) {
-    if (c < n + nb) birth_comp(md, ct, c, births + (size_t)(c - n) * 43, c - n, frame);
-    return;
+__device__ void predict_comp(const Model& md, const CompTable& src, const CompTable& ct, int c);
+
+template <int DZ>
+__global__ void predict_kernel(Model md, CompTable src, CompTable ct, const FrameDev* __restrict__ fs,
+                               const double* __restrict__ births) {
+  const int n = fs->n_comp, nb = fs->nb, frame = fs->frame;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n + nb; c += gridDim.x * blockDim.x) {
+    if (c < n) predict_comp<DZ>(md, src, ct, c);
+    else birth_comp(md, ct, c, births + (size_t)(c - n) * 43, c - n, frame);
   }
+}
+
+template <int DZ>
+__device__ void predict_comp(const Model& md, const CompTable& src, const CompTable& ct, int c) {
+  constexpr int DX = 2 * DZ;
   const size_t cap = ct.cap, scap = src.cap;
 #pragma unroll
   for (int a = 0; a < DZ; ++a) {
@@ -103,15 +110,12 @@ __device__ void birth_comp(const Model& md, const CompTable& ct, int c, const do
   ct.log1mp[c] = r < 1.0 ? (float)log1p(-r) : -INFINITY;
 }
 
-void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, int n,
-                    const double* births_dev, int nb, int frame, cudaStream_t s) {
-  const int total = n + nb;
-  if (total <= 0) return;
-  const int bs = 128, nblk = (total + bs - 1) / bs;
+void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, const FrameDev* fs,
+                    const double* births_dev, int grid, cudaStream_t s) {
   if (md.dz == 2) {
-    predict_kernel<2><<<nblk, bs, 0, s>>>(md, src, dst, n, births_dev, nb, frame);
+    predict_kernel<2><<<grid, 128, 0, s>>>(md, src, dst, fs, births_dev);
   } else {
-    predict_kernel<3><<<nblk, bs, 0, s>>>(md, src, dst, n, births_dev, nb, frame);
+    predict_kernel<3><<<grid, 128, 0, s>>>(md, src, dst, fs, births_dev);
   }
   ++g_launches;
 }
@@ -180,11 +184,12 @@ __device__ __forceinline__ bool pair_eval(const Model& md, const CompGeom<DZ>& g
 }
 
 template <int DZ>
-__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, int T,
-                                   const float* __restrict__ Z, int M) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt,
+                                   const FrameDev* __restrict__ fs, const float* __restrict__ Z) {
+  const int T = fs->T, M = fs->M;
   const int lane = threadIdx.x & 31;
-  if (c >= T) return;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps) {
   CompGeom<DZ> g;
   comp_geom<DZ>(md, ct, c, g);
   unsigned cnt = 0;
@@ -200,6 +205,7 @@ __global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, int T,
     }
   }
   if (lane == 0) pt.cnt[c] = cnt;
+  }
 }
 
 __device__ __forceinline__ void lse_push(float& m, float& s, float x) {
@@ -213,12 +219,25 @@ __device__ __forceinline__ void lse_push(float& m, float& s, float x) {
 }
 
 template <int DZ>
-__global__ void table_write_kernel(Model md, CompTable ct, PairTable pt, int T,
-                                   const float* __restrict__ Z, int M, unsigned* n_fp64,
-                                   unsigned* err) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ void table_write_comp(const Model& md, const CompTable& ct, const PairTable& pt, int c,
+                                 const float* __restrict__ Z, int M, unsigned* n_fp64,
+                                 unsigned* err);
+
+template <int DZ>
+__global__ void table_write_kernel(Model md, CompTable ct, PairTable pt,
+                                   const FrameDev* __restrict__ fs, const float* __restrict__ Z,
+                                   unsigned* n_fp64, unsigned* err) {
+  const int T = fs->T, M = fs->M;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps)
+    table_write_comp<DZ>(md, ct, pt, c, Z, M, n_fp64, err);
+}
+
+template <int DZ>
+__device__ void table_write_comp(const Model& md, const CompTable& ct, const PairTable& pt, int c,
+                                 const float* __restrict__ Z, int M, unsigned* n_fp64,
+                                 unsigned* err) {
   const int lane = threadIdx.x & 31;
-  if (c >= T) return;
   CompGeom<DZ> g;
   comp_geom<DZ>(md, ct, c, g);
   if (!g.ok) {
@@ -300,23 +319,24 @@ __global__ void table_write_kernel(Model md, CompTable ct, PairTable pt, int T,
   }
 }
 
-void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt, int T,
-                        const float* Z, int M, cudaStream_t s) {
-  if (T <= 0) return;
-  const int bs = 256, nb = (int)(((long long)T * 32 + bs - 1) / bs);
-  if (md.dz == 2) { table_count_kernel<2><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M); } else { table_count_kernel<3><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M); }
+void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
+                        const FrameDev* fs, const float* Z, int grid, cudaStream_t s) {
+  if (md.dz == 2) { table_count_kernel<2><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z); }
+  else { table_count_kernel<3><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z); }
   ++g_launches;
 }
 
-void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt, int T,
-                        const float* Z, int M, unsigned* n_fp64, unsigned* err, cudaStream_t s) {
-  if (T <= 0) return;
-  const int bs = 256, nb = (int)(((long long)T * 32 + bs - 1) / bs);
-  if (md.dz == 2) { table_write_kernel<2><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M, n_fp64, err); } else { table_write_kernel<3><<<nb, bs, 0, s>>>(md, ct, pt, T, Z, M, n_fp64, err); }
+void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
+                        const FrameDev* fs, const float* Z, unsigned* n_fp64, unsigned* err,
+                        int grid, cudaStream_t s) {
+  if (md.dz == 2) { table_write_kernel<2><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z, n_fp64, err); }
+  else { table_write_kernel<3><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z, n_fp64, err); }
   ++g_launches;
 }
 
-__global__ void check_finite_kernel(const float* __restrict__ Z, long long n, unsigned* err) {
+__global__ void check_finite_kernel(const float* __restrict__ Z, const FrameDev* __restrict__ fs,
+                                    int dz, unsigned* err) {
+  const long long n = (long long)fs->M * dz;
   bool bad = false;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
@@ -324,34 +344,33 @@ __global__ void check_finite_kernel(const float* __restrict__ Z, long long n, un
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrInput);
 }
 
-void launch_check_finite(const float* Z, long long n, unsigned* err, cudaStream_t s) {
-  if (n <= 0) return;
-  check_finite_kernel<<<(int)std::min<long long>((n + 255) / 256, 64), 256, 0, s>>>(Z, n, err); ++g_launches;
+void launch_check_finite(const float* Z, const FrameDev* fs, int dz, unsigned* err, cudaStream_t s) {
+  check_finite_kernel<<<16, 256, 0, s>>>(Z, fs, dz, err); ++g_launches;
 }
 
 // per-parent slot and table sizes (max over parents), births included
-__global__ void parent_stats_kernel(HypTable hp, int H, PairTable pt, int birth_base, int nb,
+__global__ void parent_stats_kernel(HypTable hp, const FrameDev* __restrict__ fs, PairTable pt,
                                     unsigned* max_T, unsigned* max_K) {
   __shared__ unsigned kb;
+  const int H = fs->H, nb = fs->nb, birth_base = fs->n_comp;
   if (threadIdx.x == 0) {
     unsigned s = 0;
     for (int b = 0; b < nb; ++b) s += pt.cnt[birth_base + b];
     kb = s;
   }
   __syncthreads();
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= H) return;
-  const unsigned lo = hp.ptr[h], hi = hp.ptr[h + 1];
-  unsigned k = kb;
-  for (unsigned j = lo; j < hi; ++j) k += pt.cnt[hp.comp[j]];
-  atomicMax(max_T, hi - lo + (unsigned)nb);
-  atomicMax(max_K, k);
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < H; h += gridDim.x * blockDim.x) {
+    const unsigned lo = hp.ptr[h], hi = hp.ptr[h + 1];
+    unsigned k = kb;
+    for (unsigned j = lo; j < hi; ++j) k += pt.cnt[hp.comp[j]];
+    atomicMax(max_T, hi - lo + (unsigned)nb);
+    atomicMax(max_K, k);
+  }
 }
 
-void launch_parent_stats(const HypTable& hp, int H, const PairTable& pt, int birth_base, int nb,
-                         unsigned* max_T, unsigned* max_K, cudaStream_t s) {
-  if (H <= 0) return;
-  parent_stats_kernel<<<(H + 127) / 128, 128, 0, s>>>(hp, H, pt, birth_base, nb, max_T, max_K); ++g_launches;
+void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
+                         unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s) {
+  parent_stats_kernel<<<grid, 128, 0, s>>>(hp, fs, pt, max_T, max_K); ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -388,8 +407,14 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T& total) {
   return before;
 }
 
+// length of a scan: count in device memory times a constant factor
+__device__ __forceinline__ long long scan_len(const int* n_dev, int mult) {
+  return (long long)(*n_dev) * mult;
+}
+
 template <typename T>
-__global__ void scan_tile_sums(const T* __restrict__ in, long long n, T* tile_sums) {
+__global__ void scan_tile_sums(const T* __restrict__ in, const int* n_dev, int mult, T* tile_sums) {
+  const long long n = scan_len(n_dev, mult);
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   T s = 0;
 #pragma unroll
@@ -400,27 +425,36 @@ __global__ void scan_tile_sums(const T* __restrict__ in, long long n, T* tile_su
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
+// scans the tile sums in place (one block); writes the grand total to
+// *total and, when asked, to out[n]
 template <typename T>
-__global__ void scan_single(T* v, int n, T* total) {
+__global__ void scan_single(T* v, int n_tiles, T* total, T* out, const int* n_dev, int mult,
+                            int total_at_end) {
   __shared__ T carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < n; base += kScanThreads) {
+  for (int base = 0; base < n_tiles; base += kScanThreads) {
     const int i = base + threadIdx.x;
-    const T x = i < n ? v[i] : T(0);
+    const T x = i < n_tiles ? v[i] : T(0);
     T tot;
     const T ex = block_exclusive_scan<T>(x, tot);
-    if (i < n) v[i] = carry + ex;
+    if (i < n_tiles) v[i] = carry + ex;
     __syncthreads();
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0 && total) *total = carry;
+  if (threadIdx.x == 0) {
+    if (total) *total = carry;
+    if (total_at_end) out[scan_len(n_dev, mult)] = carry;
+  }
 }
 
 template <typename T>
-__global__ void scan_apply(const T* in, T* out, long long n, const T* __restrict__ tile_off) {
+__global__ void scan_apply(const T* in, T* out, const int* n_dev, int mult,
+                           const T* __restrict__ tile_off) {
+  const long long n = scan_len(n_dev, mult);
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  if ((long long)blockIdx.x * kScanTile >= n) return;
   T vals[kScanItems];
   T s = 0;
 #pragma unroll
@@ -438,10 +472,12 @@ __global__ void scan_apply(const T* in, T* out, long long n, const T* __restrict
     }
 }
 
-// whole scan in one block for small inputs (up to 64 items per thread)
+// whole scan in one block when the capacity is small (up to 64 items per thread)
 constexpr long long kScanSmall = (long long)kScanThreads * 64;
 template <typename T>
-__global__ void scan_small(const T* in, T* out, long long n, T* total) {
+__global__ void scan_small(const T* in, T* out, const int* n_dev, int mult, T* total,
+                           int total_at_end) {
+  const long long n = scan_len(n_dev, mult);
   const int per = (int)((n + kScanThreads - 1) / kScanThreads);
   const long long b = (long long)threadIdx.x * per;
   T s = 0;
@@ -455,34 +491,38 @@ __global__ void scan_small(const T* in, T* out, long long n, T* total) {
       out[b + k] = run;
       run += v;
     }
-  if (threadIdx.x == 0 && total) *total = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (total) *total = tot;
+    if (total_at_end) out[n] = tot;
+  }
 }
 
-long long scan_tmp_elems(long long n) { return (n + kScanTile - 1) / kScanTile + 1; }
+long long scan_tmp_elems(long long cap) { return (cap + kScanTile - 1) / kScanTile + 1; }
 
 template <typename T>
-static void scan_impl(const T* in, T* out, long long n, T* total, T* tmp, cudaStream_t s) {
-  if (n <= 0) {
-    if (total) cudaMemsetAsync(total, 0, sizeof(T), s);
+static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long cap, T* total,
+                      bool total_at_end, T* tmp, cudaStream_t s) {
+  if (cap <= kScanSmall) {
+    scan_small<T><<<1, kScanThreads, 0, s>>>(in, out, n_dev, mult, total, total_at_end ? 1 : 0);
+    ++g_launches;
     return;
   }
-  if (n <= kScanSmall) {
-    scan_small<T><<<1, kScanThreads, 0, s>>>(in, out, n, total); ++g_launches;
-    return;
-  }
-  const int nt = (int)((n + kScanTile - 1) / kScanTile);
-  scan_tile_sums<T><<<nt, kScanThreads, 0, s>>>(in, n, tmp); ++g_launches;
-  scan_single<T><<<1, kScanThreads, 0, s>>>(tmp, nt, total); ++g_launches;
-  scan_apply<T><<<nt, kScanThreads, 0, s>>>(in, out, n, tmp); ++g_launches;
+  const int nt = (int)((cap + kScanTile - 1) / kScanTile);
+  scan_tile_sums<T><<<nt, kScanThreads, 0, s>>>(in, n_dev, mult, tmp); ++g_launches;
+  scan_single<T><<<1, kScanThreads, 0, s>>>(tmp, nt, total, out, n_dev, mult, total_at_end ? 1 : 0);
+  ++g_launches;
+  scan_apply<T><<<nt, kScanThreads, 0, s>>>(in, out, n_dev, mult, tmp); ++g_launches;
 }
 
-void scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* total, uint32_t* tmp,
-              cudaStream_t s) {
-  scan_impl<uint32_t>(in, out, n, total, tmp, s);
+void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
+              uint32_t* total, bool total_at_end, uint32_t* tmp, cudaStream_t s) {
+  scan_impl<uint32_t>(in, out, n_dev, mult, cap, total, total_at_end, tmp, s);
 }
-void scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
-              unsigned long long* total, unsigned long long* tmp, cudaStream_t s) {
-  scan_impl<unsigned long long>(in, out, n, total, tmp, s);
+void scan_u64(const unsigned long long* in, unsigned long long* out, const int* n_dev, int mult,
+              long long cap, unsigned long long* total, bool total_at_end,
+              unsigned long long* tmp, cudaStream_t s) {
+  scan_impl<unsigned long long>(in, out, n_dev, mult, cap, total, total_at_end, tmp, s);
 }
 
 }  // namespace glmb

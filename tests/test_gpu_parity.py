@@ -129,8 +129,9 @@ def test_invalid_inputs_are_rejected(glmb):
     assert ei.value.status == 1
     import torch
     g.predict(sc.frames[0].births)
+    g.update(torch.from_numpy(Z).cuda(), device=True)   # checked on the device
     with pytest.raises(glmb.GlmbError) as ei:
-        g.update(torch.from_numpy(Z).cuda(), device=True)
+        g.prune()
     assert ei.value.status == 1
     g.predict(sc.frames[0].births)
     g.update(torch.from_numpy(sc.frames[0].Z).cuda(), device=True)
