@@ -286,6 +286,8 @@ def main():
         "gpu_launches": int(launches),
         "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
                    "redone_frames": info1["n_redo"]},
+        "expand_plan": {"smem_bytes": info1["expand_smem_bytes"],
+                        "ctas_per_sm": info1["expand_ctas_per_sm"]},
         "roofline": {"bound": "alu", "kernel": "expand_kernel (child expansion + scoring)",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",

@@ -115,6 +115,8 @@ typedef struct {
   int64_t n_graph_captures; /* frame graphs captured by glmb_step on this handle */
   int64_t n_graph_launches; /* frame graphs replayed by glmb_step on this handle */
   int64_t n_redo;           /* frames whose expansion was redone with a larger plan */
+  int32_t expand_smem_bytes;   /* shared memory per CTA of the last expansion */
+  int32_t expand_ctas_per_sm;  /* resident CTAs per SM of the last expansion */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks

@@ -36,6 +36,7 @@ struct Plan {
   bool fixed;
   int T, K, M;     // expansion shared-memory plan
   int G, Gm;       // draw groups of the expansion and of the regeneration
+  bool thread;     // expansion: one thread per child (many parents) or one warp per child
 };
 }  // namespace
 
@@ -73,6 +74,7 @@ struct glmb_handle {
   PairTable pt{};
   uint32_t* scan_tmp32 = nullptr;
   long long* child_key = nullptr;
+  unsigned long long* child_hash = nullptr;
   int8_t* child_status = nullptr;
   uint16_t* child_alive = nullptr;
   PruneWork pw{};
@@ -104,6 +106,7 @@ struct glmb_handle {
   // prune), estimated pair maximum (from earlier frames; redone if exceeded)
   int alive_max = 0;
   int K_est = 256;
+  int exp_smem = 0, exp_ctas = 0;
   int redo_count = 0;
   // launch plan of the frame in progress, and captured frame graphs
   Plan plan{};
@@ -419,6 +422,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   }
   cudaDeviceGetAttribute(&h->smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  expand_init(h->smem_limit);
   if (c.stream) {
     h->stream = (cudaStream_t)c.stream;
   } else {
@@ -443,6 +447,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->pt.logdetS, h->cap_comp) &&
             dalloc(h, &h->scan_tmp32, scan_tmp_elems(scan_n)) &&
             dalloc(h, &h->child_key, h->cap_children) && dalloc(h, &h->child_status, h->cap_children) &&
+            dalloc(h, &h->child_hash, h->cap_children) &&
             dalloc(h, &h->child_alive, h->cap_children) &&
             dalloc(h, &h->pw.blk_max, 4097) && dalloc(h, &h->pw.blk_sum, 4097) &&
             dalloc(h, &h->pw.blk_done, 4) && dalloc(h, &h->pw.lse, 2) && dalloc(h, &h->pw.thr, 1) &&
@@ -599,7 +604,14 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
   a.K_max = p.K;
   a.M_plan = p.M;
   a.n_groups = mat ? p.Gm : p.G;
-  a.smem_bytes = expand_smem_bytes(h->md.dz, mat ? 1 : 0, p.T, p.K, p.M, h->cfg.h_up, a.n_groups);
+  // the expansion runs one thread per child; only children beyond its local
+  // lists go to per-warp work areas, so one such area suffices unless the
+  // parents are too large for the thread path
+  a.n_fb_groups = (!mat && p.thread && p.T <= 2048) ? 1 : a.n_groups;
+  a.thread_path = (!mat && p.thread) ? 1 : 0;
+  a.max_slices = mat ? 1 : std::max(1, h->cfg.h_up / std::max(1, a.n_groups));
+  a.target_warps = 32LL * h->n_sm;
+  a.smem_bytes = expand_smem_bytes(h->md.dz, mat ? 1 : 0, p.T, p.K, p.M, h->cfg.h_up, a.n_fb_groups);
   a.materialize = mat ? 1 : 0;
   a.err = h->d_scal + S_ERR;
   return a;
@@ -608,12 +620,17 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
 glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   ExpandArgs a = expand_args(h, p, false);
   a.child_key = h->child_key;
+  a.child_hash = h->child_hash;
   a.child_status = h->child_status;
   a.child_alive = h->child_alive;
-  const int full = std::max(1, expand_max_ctas(a)) * h->n_sm;
-  const int grid = p.fixed ? full : std::min(h->H, full);
+  h->exp_smem = a.smem_bytes;
+  h->exp_ctas = expand_max_ctas(a);
+  const int full = std::max(1, h->exp_ctas) * h->n_sm;
+  const int grid = p.fixed ? full : (int)std::min<long long>((long long)h->H * a.max_slices, full);
   prof_begin(h, kStageExpand);
   launch_expand(a, grid, h->stream);
+  launch_dedup(h->d_fs, h->cfg.h_up, h->child_key, h->child_hash, h->child_status,
+               p.fixed ? 2 * h->n_sm : std::max(1, std::min(h->H, 2 * h->n_sm)), h->stream);
   prof_end(h, kStageExpand);
   return GLMB_OK;
 }
@@ -683,17 +700,23 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, Plan& p) {
   p.T = std::max(1, T_plan);
   p.K = std::max(64, K_plan);
   p.M = std::max(1, h->M);
-  int want = std::max(4, std::min(16, (32 * h->n_sm + h->H - 1) / std::max(1, h->H)));
+  // many parents: one thread per child in CTAs of h_up threads (rounded to
+  // warps); few parents: one warp per child, 16 warps per CTA, the draws of a
+  // parent split over several CTAs
+  p.thread = h->H >= 3 * h->n_sm && h->cfg.h_up >= 32;
+  const int want = p.thread ? std::max(1, std::min(16, (h->cfg.h_up + 31) / 32)) : 16;
   if (fixed) {
     p.T = round_up(p.T, 32);
     p.K = round_up(p.K, 256);
     p.M = round_up(p.M, 64);
-    want = h->H <= 2 * h->n_sm ? 16 : (h->H <= 4 * h->n_sm ? 8 : 4);
   }
   const int dz = h->md.dz;
-  p.G = expand_plan_groups(dz, 0, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit,
-                           std::min(want, h->cfg.h_up));
-  p.Gm = expand_plan_groups(dz, 1, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit, 8);
+  if (p.thread && p.T <= 2048)
+    p.G = expand_smem_bytes(dz, 0, p.T, p.K, p.M, h->cfg.h_up, 1) <= h->smem_limit ? want : 0;
+  else
+    p.G = expand_plan_groups(dz, 0, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit,
+                             std::min(want, h->cfg.h_up));
+  p.Gm = expand_plan_groups(dz, 1, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit, 4);
   return p.G > 0 && p.Gm > 0;
 }
 
@@ -854,8 +877,8 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
     int best = -1;
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
       const glmb_handle::CachedGraph& g = h->graphs[gi];
-      if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.T < p.T || g.plan.K < p.K ||
-          g.plan.M < p.M)
+      if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread ||
+          g.plan.T < p.T || g.plan.K < p.K || g.plan.M < p.M)
         continue;
       if (best < 0 || (g.plan.G == p.G && h->graphs[best].plan.G != p.G)) best = gi;
     }
@@ -962,6 +985,8 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
   info->n_graph_captures = h->n_captures;
   info->n_graph_launches = h->n_graph_launches;
   info->n_redo = h->redo_count;
+  info->expand_smem_bytes = h->exp_smem;
+  info->expand_ctas_per_sm = h->exp_ctas;
   return GLMB_OK;
 }
 

@@ -46,9 +46,16 @@ struct ExpandArgs {
   // shared-memory plan: largest slots, gated pairs and detections per parent
   // (a parent beyond the plan sets kErrSlots and is redone with a larger plan)
   int T_max, K_max, M_plan, n_groups;
+  int n_fb_groups;        // warps with a per-child work area (children the thread path cannot take)
   int smem_bytes;
+  // draw mapping: one thread per child (thread_path) or one warp per child;
+  // with the warp path a parent's draws are split into up to max_slices
+  // slices so that about target_warps warps are in flight
+  int thread_path, max_slices;
+  long long target_warps;
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
+  unsigned long long* child_hash;   // [H * h_up] order-free key of (deaths, associations)
   int8_t* child_status;   // 0 zero weight, 1 unique, 2 duplicate
   uint16_t* child_alive;  // surviving tracks
   // materialisation inputs / outputs
@@ -75,8 +82,13 @@ int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int
                        int smem_limit, int max_groups);
 // resident CTAs per SM for this plan
 int expand_max_ctas(const ExpandArgs& a);
-// one persistent CTA per grid slot, looping over the parents
+// allows the expansion kernels the device's opt-in shared memory (call once)
+void expand_init(int smem_limit);
+// one persistent CTA per grid slot, looping over the parents (and slices)
 void launch_expand(const ExpandArgs& a, int grid, cudaStream_t s);
+// marks duplicate children (status 2, key dropped), one block per parent
+void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
+                  int8_t* child_status, int grid, cudaStream_t s);
 
 // ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
 struct PruneWork {
