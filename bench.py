@@ -287,7 +287,10 @@ def main():
         "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
                    "redone_frames": info1["n_redo"]},
         "expand_plan": {"smem_bytes": info1["expand_smem_bytes"],
-                        "ctas_per_sm": info1["expand_ctas_per_sm"]},
+                        "ctas_per_sm": info1["expand_ctas_per_sm"],
+                        "threads": info1["expand_threads"],
+                        "T": info1["expand_plan_T"], "K": info1["expand_plan_K"],
+                        "M": info1["expand_plan_M"]},
         "roofline": {"bound": "alu", "kernel": "expand_kernel (child expansion + scoring)",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",

@@ -117,6 +117,10 @@ typedef struct {
   int64_t n_redo;           /* frames whose expansion was redone with a larger plan */
   int32_t expand_smem_bytes;   /* shared memory per CTA of the last expansion */
   int32_t expand_ctas_per_sm;  /* resident CTAs per SM of the last expansion */
+  int32_t expand_plan_T;       /* slots per hypothesis the last expansion was planned for */
+  int32_t expand_plan_K;       /* gated pairs per hypothesis it was planned for */
+  int32_t expand_plan_M;       /* detection rows it was planned for */
+  int32_t expand_threads;      /* threads per CTA of the last expansion */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks

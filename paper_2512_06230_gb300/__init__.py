@@ -100,7 +100,9 @@ class GlmbInfo(C.Structure):
                 ("n_fp64_chol", C.c_int32), ("n_launches", C.c_int64),
                 ("n_graph_captures", C.c_int64), ("n_graph_launches", C.c_int64),
                 ("n_redo", C.c_int64), ("expand_smem_bytes", C.c_int32),
-                ("expand_ctas_per_sm", C.c_int32)]
+                ("expand_ctas_per_sm", C.c_int32), ("expand_plan_T", C.c_int32),
+                ("expand_plan_K", C.c_int32), ("expand_plan_M", C.c_int32),
+                ("expand_threads", C.c_int32)]
 
 
 # NumPy views of the ABI records (same layout as the C structs)

@@ -25,7 +25,7 @@ enum { kStagePredict = 0, kStageTable, kStageExpand, kStageSelect, kStageMat, kS
        kStageEstimates, kNumStages };
 
 // device scalar slots
-enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_N = 16 };
+enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_REDO = 7, S_N = 16 };
 
 }  // namespace
 
@@ -34,9 +34,10 @@ namespace {
 // capacity (for a replayed graph)
 struct Plan {
   bool fixed;
-  int T, K, M;     // expansion shared-memory plan
-  int G, Gm;       // draw groups of the expansion and of the regeneration
-  bool thread;     // expansion: one thread per child (many parents) or one warp per child
+  int T, K, M;     // per-parent image plan: slots, gated pairs, detection rows
+  bool thread;     // draws: one thread per child (many parents) or one warp per child
+  bool smem;       // parents staged in shared memory (else in the image)
+  int Gw, Gm;      // warps per CTA of the warp kernel: expansion, regeneration
 };
 }  // namespace
 
@@ -77,6 +78,11 @@ struct glmb_handle {
   unsigned long long* child_hash = nullptr;
   int8_t* child_status = nullptr;
   uint16_t* child_alive = nullptr;
+  // per-parent images of the expansion (grown on demand) and the draws the
+  // thread-per-child kernel hands to the warp kernel
+  unsigned char* img = nullptr;
+  size_t img_alloc = 0;
+  uint32_t* redo_list = nullptr;
   PruneWork pw{};
   unsigned long long* hkeys = nullptr;
   uint32_t* hvals = nullptr;
@@ -107,6 +113,7 @@ struct glmb_handle {
   int alive_max = 0;
   int K_est = 256;
   int exp_smem = 0, exp_ctas = 0;
+  int exp_plan[4] = {0, 0, 0, 0};   // T, K, M, threads of the last expansion
   int redo_count = 0;
   // launch plan of the frame in progress, and captured frame graphs
   Plan plan{};
@@ -116,6 +123,8 @@ struct glmb_handle {
     Plan plan;
     cudaGraphExec_t exec;
     long long n_kernels;
+    int smem;              // shared memory per CTA of its expansion
+    long long last_use;
   };
   std::vector<CachedGraph> graphs;
   bool capturing = false;
@@ -449,6 +458,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->child_key, h->cap_children) && dalloc(h, &h->child_status, h->cap_children) &&
             dalloc(h, &h->child_hash, h->cap_children) &&
             dalloc(h, &h->child_alive, h->cap_children) &&
+            dalloc(h, &h->redo_list, h->cap_children) &&
             dalloc(h, &h->pw.blk_max, 4097) && dalloc(h, &h->pw.blk_sum, 4097) &&
             dalloc(h, &h->pw.blk_done, 4) && dalloc(h, &h->pw.lse, 2) && dalloc(h, &h->pw.thr, 1) &&
             dalloc(h, &h->pw.hist, 4096) && dalloc(h, &h->pw.sel, 4) &&
@@ -484,6 +494,7 @@ glmb_status glmb_destroy(glmb_handle* h) {
   if (!h) return GLMB_OK;
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->img) cudaFree(h->img);
   for (int st = 0; st < kNumStages; ++st)
     if (h->ev[st][0]) {
       cudaEventDestroy(h->ev[st][0]);
@@ -603,34 +614,79 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
   a.T_max = p.T;
   a.K_max = p.K;
   a.M_plan = p.M;
-  a.n_groups = mat ? p.Gm : p.G;
-  // the expansion runs one thread per child; only children beyond its local
-  // lists go to per-warp work areas, so one such area suffices unless the
-  // parents are too large for the thread path
-  a.n_fb_groups = (!mat && p.thread && p.T <= 2048) ? 1 : a.n_groups;
-  a.thread_path = (!mat && p.thread) ? 1 : 0;
-  a.max_slices = mat ? 1 : std::max(1, h->cfg.h_up / std::max(1, a.n_groups));
-  a.target_warps = 32LL * h->n_sm;
-  a.smem_bytes = expand_smem_bytes(h->md.dz, mat ? 1 : 0, p.T, p.K, p.M, h->cfg.h_up, a.n_fb_groups);
+  a.img = h->img;
+  a.img_stride = expand_image_bytes(h->md.dz, p.T, p.K, p.M);
+  a.stage_smem = p.smem ? 1 : 0;
+  a.warp_all = p.thread ? 0 : 1;
+  a.redo_list = h->redo_list;
+  a.redo_count = h->d_scal + S_REDO;
   a.materialize = mat ? 1 : 0;
   a.err = h->d_scal + S_ERR;
   return a;
 }
 
+// the image buffer holds cap_h parents of plan p; growing it invalidates the
+// captured graphs (they hold its address)
+glmb_status ensure_img(glmb_handle* h, const Plan& p) {
+  const size_t need = (size_t)h->cap_h * (size_t)expand_image_bytes(h->md.dz, p.T, p.K, p.M);
+  if (need <= h->img_alloc) return GLMB_OK;
+  CU(cudaStreamSynchronize(h->stream));
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  if (h->img) cudaFree(h->img);
+  h->img = nullptr;
+  h->img_alloc = 0;
+  const size_t want = need + need / 4;
+  void* q = nullptr;
+  if (cudaMalloc(&q, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GLMB_E_CAPACITY, "expansion images: %zu bytes not available", want);
+  }
+  h->img = (unsigned char*)q;
+  h->img_alloc = want;
+  return GLMB_OK;
+}
+
 glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
+  cudaStream_t s = h->stream;
+  const int n_sm = h->n_sm, h_up = h->cfg.h_up, dz = h->md.dz;
   ExpandArgs a = expand_args(h, p, false);
   a.child_key = h->child_key;
   a.child_hash = h->child_hash;
   a.child_status = h->child_status;
   a.child_alive = h->child_alive;
-  h->exp_smem = a.smem_bytes;
-  h->exp_ctas = expand_max_ctas(a);
-  const int full = std::max(1, h->exp_ctas) * h->n_sm;
-  const int grid = p.fixed ? full : (int)std::min<long long>((long long)h->H * a.max_slices, full);
+  const int img = (int)a.img_stride;
+  // stage: one 128-thread CTA per parent
+  const int st_smem = p.smem ? img : 0;
+  const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, 128, st_smem));
+  const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
+  // draws: one thread per child, blocks of up to 256 draws of one parent
+  const int d_thr = std::min(256, round_up(h_up, 32));
+  const int nsl = (h_up + d_thr - 1) / d_thr;
+  const int d_smem = expand_draw_smem(d_thr);
+  const int d_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kDraw, d_thr, d_smem));
+  const int d_grid = p.fixed ? d_ctas * n_sm : (int)std::max(1LL, std::min((long long)h->H * nsl, (long long)d_ctas * n_sm));
+  // warp kernel: the overflow list, or every child
+  const int w_thr = 32 * p.Gw;
+  const int w_smem = expand_warp_smem(dz, 0, p.T, p.Gw);
+  const int w_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kWarp, w_thr, w_smem));
+  int w_grid = w_ctas * n_sm;
+  if (p.thread) w_grid = n_sm;
+  else if (!p.fixed)
+    w_grid = (int)std::max(1LL, std::min(((long long)h->H * h_up + p.Gw - 1) / p.Gw, (long long)w_grid));
+  h->exp_smem = p.thread ? img : w_smem;
+  h->exp_ctas = p.thread ? d_ctas : w_ctas;
+  h->exp_plan[0] = p.T;
+  h->exp_plan[1] = p.K;
+  h->exp_plan[2] = p.M;
+  h->exp_plan[3] = p.thread ? d_thr : w_thr;
   prof_begin(h, kStageExpand);
-  launch_expand(a, grid, h->stream);
-  launch_dedup(h->d_fs, h->cfg.h_up, h->child_key, h->child_hash, h->child_status,
-               p.fixed ? 2 * h->n_sm : std::max(1, std::min(h->H, 2 * h->n_sm)), h->stream);
+  CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, sizeof(unsigned), s));
+  launch_expand_kernel(a, ExpandKernel::kStage, st_grid, 128, st_smem, s);
+  if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
+  launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
+  launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status,
+               p.fixed ? 2 * n_sm : std::max(1, std::min(h->H, 2 * n_sm)), s);
   prof_end(h, kStageExpand);
   return GLMB_OK;
 }
@@ -671,9 +727,15 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   a.upd_se = h->upd_se;
   a.upd_count = h->d_scal + S_NUPD;
   a.cap_upd = (int)h->cap_upd;
-  const int full = std::max(1, expand_max_ctas(a)) * h->n_sm;
+  const int m_thr = 32 * p.Gm;
+  const int m_smem = expand_warp_smem(h->md.dz, 1, p.T, p.Gm);
+  const int m_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kWarp, m_thr, m_smem));
+  const int m_grid = p.fixed ? m_ctas * h->n_sm
+                             : std::max(1, std::min((h->cap_h + p.Gm - 1) / p.Gm, m_ctas * h->n_sm));
   prof_begin(h, kStageMat);
-  launch_expand(a, p.fixed ? full : std::min(h->H, full), s);
+  launch_expand_kernel(a, ExpandKernel::kMatPrep, std::max(1, std::min((h->cap_h + 7) / 8, 2 * h->n_sm)),
+                       256, 0, s);
+  launch_expand_kernel(a, ExpandKernel::kWarp, m_grid, m_thr, m_smem, s);
   prof_end(h, kStageMat);
   const int T = h->T_work;
   const long long capT = p.fixed ? h->cap_comp : std::max(T, 1);
@@ -695,29 +757,32 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
 
 // expansion plan of this frame: slots exactly (largest survivor of the last
 // prune plus births), gated pairs from earlier frames (redone if exceeded)
-bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, Plan& p) {
+bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, Plan& p) {
   p.fixed = fixed;
   p.T = std::max(1, T_plan);
   p.K = std::max(64, K_plan);
-  p.M = std::max(1, h->M);
-  // many parents: one thread per child in CTAs of h_up threads (rounded to
-  // warps); few parents: one warp per child, 16 warps per CTA, the draws of a
-  // parent split over several CTAs
-  p.thread = h->H >= 3 * h->n_sm && h->cfg.h_up >= 32;
-  const int want = p.thread ? std::max(1, std::min(16, (h->cfg.h_up + 31) / 32)) : 16;
+  p.M = std::max(1, M_plan);
   if (fixed) {
-    p.T = round_up(p.T, 32);
-    p.K = round_up(p.K, 256);
-    p.M = round_up(p.M, 64);
+    p.T = round_up(p.T, 16);
+    p.K = round_up(p.K, 64);
+    p.M = round_up(p.M, 32);
   }
   const int dz = h->md.dz;
-  if (p.thread && p.T <= 2048)
-    p.G = expand_smem_bytes(dz, 0, p.T, p.K, p.M, h->cfg.h_up, 1) <= h->smem_limit ? want : 0;
-  else
-    p.G = expand_plan_groups(dz, 0, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit,
-                             std::min(want, h->cfg.h_up));
-  p.Gm = expand_plan_groups(dz, 1, p.T, p.K, p.M, h->cfg.h_up, h->smem_limit, 4);
-  return p.G > 0 && p.Gm > 0;
+  // one thread per child once the children give every SM four warps (the
+  // register lists address pairs with 16 bits); else one warp per child
+  p.thread = (long long)h->H * h->cfg.h_up >= 4LL * 32 * h->n_sm && p.K <= 65536;
+  p.smem = expand_image_bytes(dz, p.T, p.K, p.M) <= h->smem_limit;
+  p.Gw = p.Gm = 0;
+  for (int g = 16; g >= 1 && !p.Gw; --g)
+    if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
+  for (int g = 8; g >= 1 && !p.Gm; --g)
+    if (expand_warp_smem(dz, 1, p.T, g) <= h->smem_limit) p.Gm = g;
+  return p.T <= 32767 && p.Gw > 0 && p.Gm > 0;
+}
+
+// footprint of a plan's per-parent image
+int plan_smem(const glmb_handle* h, const Plan& p) {
+  return expand_image_bytes(h->md.dz, p.T, p.K, p.M);
 }
 
 // frame result: commit, abandon, or redo with exact maxima; `done` on return
@@ -737,8 +802,9 @@ glmb_status finish_frame(glmb_handle* h) {
     // the pruning with the exact maxima of this frame
     ++h->redo_count;
     Plan p;
-    if (!make_plan(h, false, std::max(1, (int)h->h_scal[S_MAXT]), std::max(1, (int)h->h_scal[S_MAXK]), p))
-      return abandon(GLMB_E_CAPACITY, "per-hypothesis table does not fit in shared memory");
+    if (!make_plan(h, false, std::max(1, (int)h->h_scal[S_MAXT]), std::max(1, (int)h->h_scal[S_MAXK]), h->M, p))
+      return abandon(GLMB_E_CAPACITY, "per-hypothesis table exceeds the supported sizes");
+    if ((st = ensure_img(h, p)) != GLMB_OK) return abandon(st, "expansion images do not fit");
     CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
     if ((st = enqueue_expand(h, p)) != GLMB_OK) return st;
     if ((st = enqueue_prune(h, p)) != GLMB_OK) return st;
@@ -758,7 +824,7 @@ glmb_status finish_frame(glmb_handle* h) {
   // commit
   h->n_unique = cnt[2];
   h->alive_max = (int)cnt[3];
-  h->K_est = round_up((int)(1.25 * h->h_scal[S_MAXK]) + 32, 64);
+  h->K_est = round_up((int)(h->h_scal[S_MAXK] + h->h_scal[S_MAXK] / 8) + 16, 64);
   h->n_upd = (int)n_upd;
   h->n_comp = (int)(n_keep + n_upd);
   h->H = (int)n_surv;
@@ -809,18 +875,19 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
   h->M = M;
   if ((st = upload_sizes(h, 1)) != GLMB_OK) return st;
   Plan p;
-  if (!make_plan(h, false, h->alive_max + h->nb, h->K_est, p)) {
+  if (!make_plan(h, false, h->alive_max + h->nb, h->K_est, h->M, p) || ensure_img(h, p) != GLMB_OK) {
     // the estimate does not fit; plan from the exact maxima of this frame
+    h->err.clear();
     Plan q{};
     q.fixed = false;
     enqueue_table(h, q);
     CU(cudaStreamSynchronize(h->stream));
     unsigned mk = 0;
     CU(cudaMemcpy(&mk, h->d_scal + S_MAXK, sizeof mk, cudaMemcpyDeviceToHost));
-    if (!make_plan(h, false, h->alive_max + h->nb, (int)mk, p)) {
+    if (!make_plan(h, false, h->alive_max + h->nb, (int)mk, h->M, p) || ensure_img(h, p) != GLMB_OK) {
       h->frame -= 1;
       h->stage = 0;
-      return fail(h, GLMB_E_CAPACITY, "update: per-hypothesis table does not fit in shared memory");
+      return fail(h, GLMB_E_CAPACITY, "update: per-hypothesis table exceeds the supported sizes");
     }
   } else {
     enqueue_table(h, p);
@@ -858,8 +925,8 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->T_work = h->n_comp + n_births;
   h->M = M;
   Plan p;
-  if (!make_plan(h, true, h->alive_max + h->nb, h->K_est, p) &&
-      !make_plan(h, false, h->alive_max + h->nb, h->K_est, p)) {
+  if (!make_plan(h, true, h->alive_max + h->nb, h->K_est, h->M, p) &&
+      !make_plan(h, false, h->alive_max + h->nb, h->K_est, h->M, p)) {
     h->frame -= 1;
     return fail(h, GLMB_E_CAPACITY, "step: per-hypothesis table does not fit in shared memory");
   }
@@ -870,31 +937,29 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->retained_valid = false;
   h->plan = p;
   if (p.fixed) {
-    // Replay a captured graph whose plan covers this frame (same buffer
-    // parity and profiling mask; slots, pairs and detections at least this
-    // frame's); otherwise capture one with headroom.  Plans only grow, so
-    // captures are rare after the first frames.
+    // Replay the captured graph with the smallest expansion footprint whose
+    // plan covers this frame (same buffer parity and profiling mask; slots,
+    // pairs and detections at least this frame's).  The footprint sets how
+    // many CTAs share an SM, so a covering graph much larger than this
+    // frame needs is replaced by a tighter capture.
+    const int need_smem = plan_smem(h, p);
     int best = -1;
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
       const glmb_handle::CachedGraph& g = h->graphs[gi];
       if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread ||
           g.plan.T < p.T || g.plan.K < p.K || g.plan.M < p.M)
         continue;
-      if (best < 0 || (g.plan.G == p.G && h->graphs[best].plan.G != p.G)) best = gi;
+      if (best < 0 || g.smem < h->graphs[best].smem) best = gi;
     }
+    if (best >= 0 && (long long)h->graphs[best].smem * 4 > (long long)need_smem * 5) best = -1;
     if (best < 0) {
       Plan q = p;
-      q.T = round_up(p.T + p.T / 4, 32);
-      q.K = round_up(p.K + p.K / 2, 256);
-      q.M = round_up(p.M + p.M / 4, 64);
-      if (!make_plan(h, true, q.T, q.K, q) || q.M < p.M) {
+      if (!make_plan(h, true, p.T + p.T / 8, p.K + p.K / 8, p.M + p.M / 8, q) || q.thread != p.thread ||
+          (p.smem && !q.smem))
         q = p;
-      } else {
-        q.M = std::max(q.M, round_up(p.M + p.M / 4, 64));
-        const int dz = h->md.dz;
-        q.G = expand_plan_groups(dz, 0, q.T, q.K, q.M, h->cfg.h_up, h->smem_limit, p.G);
-        q.Gm = expand_plan_groups(dz, 1, q.T, q.K, q.M, h->cfg.h_up, h->smem_limit, p.Gm);
-        if (q.G == 0 || q.Gm == 0) q = p;
+      if ((st = ensure_img(h, q)) != GLMB_OK) {
+        h->frame -= 1;
+        return st;
       }
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
@@ -919,14 +984,19 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (ie != cudaSuccess) return fail(h, GLMB_E_CUDA, "step: graph instantiation: %s", cudaGetErrorString(ie));
-      if (h->graphs.size() >= 8) {
-        cudaGraphExecDestroy(h->graphs.front().exec);
-        h->graphs.erase(h->graphs.begin());
+      if (h->graphs.size() >= 16) {
+        // evict the least recently replayed graph
+        int lru = 0;
+        for (int gi = 1; gi < (int)h->graphs.size(); ++gi)
+          if (h->graphs[gi].last_use < h->graphs[lru].last_use) lru = gi;
+        cudaGraphExecDestroy(h->graphs[lru].exec);
+        h->graphs.erase(h->graphs.begin() + lru);
       }
-      h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels});
+      h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels, plan_smem(h, q), 0});
       ++h->n_captures;
       best = (int)h->graphs.size() - 1;
     }
+    h->graphs[best].last_use = h->frame;
     const glmb_handle::CachedGraph& g = h->graphs[best];
     h->plan = g.plan;
     g_launches += g.n_kernels;
@@ -987,6 +1057,10 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
   info->n_redo = h->redo_count;
   info->expand_smem_bytes = h->exp_smem;
   info->expand_ctas_per_sm = h->exp_ctas;
+  info->expand_plan_T = h->exp_plan[0];
+  info->expand_plan_K = h->exp_plan[1];
+  info->expand_plan_M = h->exp_plan[2];
+  info->expand_threads = h->exp_plan[3];
   return GLMB_OK;
 }
 

@@ -133,6 +133,12 @@ __device__ __forceinline__ uint32_t word_of(const uint4& r, int b) {
 
 __device__ __forceinline__ long long fx_of(float x) { return __float2ll_rn(x * kFxScale); }
 
+// v * 2^-32 as a float, from the two 32-bit halves of v (no FP64 arithmetic,
+// which runs at a small fraction of the FP32 rate on this part)
+__device__ __forceinline__ float fx_to_f(long long v) {
+  return (float)(int)(v >> 32) + (float)(uint32_t)v * 2.3283064365386963e-10f;
+}
+
 // a + b for hi/lo float pairs (Knuth two-sum, then renormalise)
 __device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
   const float s = hi + b;
@@ -223,29 +229,102 @@ __device__ __forceinline__ int logdet_mahal(const float (&S)[N][N], const float 
 //       - 1/2 (sum q - m ebar^T R^-1 ebar) - 1/2 log|S_m| - 1/2 ebar^T S_m^-1 ebar,
 //   S_m = H P H^T + R/m, ebar = (sum e)/m  (prod_i N(z_i;Hx,R) = N(zbar;Hx,R/m) c(W));
 // alive, undetected: log p + log(1 - P_D).
-// The finite part is returned in fixed point; infinite parts are counted.
+// The part that depends only on (track, m) -- S_m^-1, log|S_m| and the
+// constant terms -- is SlotM; the rest is a quadratic form of the fixed-point
+// sums.  Every evaluation goes through these two functions, so equal inputs
+// give bit-identical terms.  The finite part is returned in fixed point;
+// infinite parts are counted.
 template <int DZ>
-__device__ __forceinline__ long long alive_term(const Model& md, const float (&HPH)[DZ][DZ],
-                                                float logp, int m, const long long* se,
-                                                long long sq, int& ninf) {
-  ninf = 0;
-  float t = 0.f;
-  if (isinf(logp)) ++ninf; else t += logp;
-  if (m == 0) {
-    if (isinf(md.log_1mpd)) ++ninf; else t += md.log_1mpd;
-    return fx_of(t);
-  }
-  if (isinf(md.log_pd)) ++ninf; else t += md.log_pd;
-  t -= md.lambda_d;
+struct SlotM {
+  float Sinv[DZ * (DZ + 1) / 2];   // packed upper triangle of S_m^-1
+  float c;                         // all m-only terms, log|S_m| included
+  int ninf;                        // infinite terms (or -1: S_m not positive definite)
+};
+
+template <int DZ>
+__device__ __forceinline__ SlotM<DZ> make_slot_m(const Model& md, const float (&HPH)[DZ][DZ],
+                                                 float logp, int m) {
+  SlotM<DZ> s;
+  s.ninf = 0;
+  float c = 0.f;
+  if (isinf(logp)) ++s.ninf; else c += logp;
+  if (isinf(md.log_pd)) ++s.ninf; else c += md.log_pd;
+  c -= md.lambda_d;
   if (m > 1) {
-    if (md.lambda_d <= 0.f) ++ninf; else t += (float)(m - 1) * md.log_lambda_d;
+    if (md.lambda_d <= 0.f) ++s.ninf; else c += (float)(m - 1) * md.log_lambda_d;
   }
   const float fm = (float)m, inv_m = 1.f / fm, logm = logf(fm);
-  t += logm;
+  c += logm;
+  c += -0.5f * fm * (float)DZ * kLog2Pi - 0.5f * (fm - 1.f) * md.logdetR - 0.5f * (float)DZ * logm;
+  float Sm[DZ][DZ];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) Sm[a][b] = HPH[a][b] + md.R[a * DZ + b] * inv_m;
+  // S_m^-1 = L^-T L^-1 and log|S_m| from the Cholesky factor (FP64 when a
+  // pivot falls below 16 eps trace)
+  float L[DZ][DZ], ld;
+  float Li[DZ][DZ];
+  if (chol_n<float, DZ>(Sm, L, ld, 1.1920929e-7f)) {
+#pragma unroll
+    for (int j = 0; j < DZ; ++j)
+#pragma unroll
+      for (int i = 0; i < DZ; ++i) {
+        float t = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= L[i][k] * Li[k][j];
+        Li[i][j] = (i < j) ? 0.f : t / L[i][i];
+      }
+  } else {
+    double Sd[DZ][DZ], Ld[DZ][DZ], ldd, Lid[DZ][DZ];
+#pragma unroll
+    for (int a = 0; a < DZ; ++a)
+#pragma unroll
+      for (int b = 0; b < DZ; ++b) Sd[a][b] = Sm[a][b];
+    if (!chol_n<double, DZ>(Sd, Ld, ldd, 2.220446049250313e-16)) {
+      s.ninf = -1;
+      s.c = 0.f;
+      return s;
+    }
+#pragma unroll
+    for (int j = 0; j < DZ; ++j)
+#pragma unroll
+      for (int i = 0; i < DZ; ++i) {
+        double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= Ld[i][k] * Lid[k][j];
+        Lid[i][j] = (i < j) ? 0.0 : t / Ld[i][i];
+      }
+#pragma unroll
+    for (int i = 0; i < DZ; ++i)
+#pragma unroll
+      for (int j = 0; j < DZ; ++j) Li[i][j] = (float)Lid[i][j];
+    ld = (float)ldd;
+  }
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < DZ; ++i)
+#pragma unroll
+    for (int j = i; j < DZ; ++j, ++k) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < DZ; ++q) t += Li[q][i] * Li[q][j];
+      s.Sinv[k] = t;
+    }
+  s.c = c - 0.5f * ld;
+  return s;
+}
+
+template <int DZ>
+__device__ __forceinline__ long long term_from(const Model& md, const SlotM<DZ>& s, int m,
+                                               const long long* se, long long sq, int& ninf) {
+  if (s.ninf < 0) { ninf = 1; return 0; }
+  ninf = s.ninf;
+  const float inv_m = 1.f / (float)m;
   float sum_e[DZ], ebar[DZ];
 #pragma unroll
   for (int a = 0; a < DZ; ++a) {
-    sum_e[a] = (float)((double)se[a] * kFxInv);
+    sum_e[a] = fx_to_f(se[a]);
     ebar[a] = sum_e[a] * inv_m;
   }
   float qR = 0.f;
@@ -253,17 +332,29 @@ __device__ __forceinline__ long long alive_term(const Model& md, const float (&H
   for (int a = 0; a < DZ; ++a)
 #pragma unroll
     for (int b = 0; b < DZ; ++b) qR += sum_e[a] * md.Rinv[a * DZ + b] * sum_e[b];
-  const float spread = (float)((double)sq * kFxInv) - qR * inv_m;
-  float Sm[DZ][DZ];
+  const float spread = fx_to_f(sq) - qR * inv_m;
+  float d2 = 0.f;
+  int k = 0;
 #pragma unroll
-  for (int a = 0; a < DZ; ++a)
+  for (int i = 0; i < DZ; ++i)
 #pragma unroll
-    for (int b = 0; b < DZ; ++b) Sm[a][b] = HPH[a][b] + md.R[a * DZ + b] * inv_m;
-  float ld, d2;
-  if (logdet_mahal<DZ>(Sm, ebar, ld, d2) < 0) { ++ninf; return 0; }
-  t += -0.5f * fm * (float)DZ * kLog2Pi - 0.5f * (fm - 1.f) * md.logdetR
-       - 0.5f * (float)DZ * logm - 0.5f * spread - 0.5f * ld - 0.5f * d2;
-  return fx_of(t);
+    for (int j = i; j < DZ; ++j, ++k) d2 += (i == j ? 1.f : 2.f) * ebar[i] * s.Sinv[k] * ebar[j];
+  return fx_of(s.c - 0.5f * spread - 0.5f * d2);
+}
+
+template <int DZ>
+__device__ __forceinline__ long long alive_term(const Model& md, const float (&HPH)[DZ][DZ],
+                                                float logp, int m, const long long* se,
+                                                long long sq, int& ninf) {
+  if (m == 0) {
+    ninf = 0;
+    float t = 0.f;
+    if (isinf(logp)) ++ninf; else t += logp;
+    if (isinf(md.log_1mpd)) ++ninf; else t += md.log_1mpd;
+    return fx_of(t);
+  }
+  const SlotM<DZ> s = make_slot_m<DZ>(md, HPH, logp, m);
+  return term_from<DZ>(md, s, m, se, sq, ninf);
 }
 
 __device__ __forceinline__ long long dead_term(float log1mp, int& ninf) {

@@ -43,16 +43,16 @@ struct ExpandArgs {
   PairTable pt;
   HypTable parents;       // hypotheses before the update
   const FrameDev* fs;     // H, M, births, frame
-  // shared-memory plan: largest slots, gated pairs and detections per parent
-  // (a parent beyond the plan sets kErrSlots and is redone with a larger plan)
-  int T_max, K_max, M_plan, n_groups;
-  int n_fb_groups;        // warps with a per-child work area (children the thread path cannot take)
-  int smem_bytes;
-  // draw mapping: one thread per child (thread_path) or one warp per child;
-  // with the warp path a parent's draws are split into up to max_slices
-  // slices so that about target_warps warps are in flight
-  int thread_path, max_slices;
-  long long target_warps;
+  // plan: largest slots, gated pairs and detections per parent (a parent
+  // beyond it sets kErrSlots and the frame is redone with a larger plan)
+  int T_max, K_max, M_plan;
+  // per-parent images: parent h at img + h * img_stride
+  unsigned char* img;
+  long long img_stride;
+  int stage_smem;         // staged in shared memory (else in the image itself)
+  int warp_all;           // warp kernel: every child of every parent (else the overflow list)
+  uint32_t* redo_list;    // children the draw kernel could not take
+  unsigned* redo_count;
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
   unsigned long long* child_hash;   // [H * h_up] order-free key of (deaths, associations)
@@ -75,17 +75,23 @@ struct ExpandArgs {
   int cap_upd;
   unsigned* err;
 };
-int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                      int n_groups);
-// draw groups (warps) per CTA: as many as fit, up to max_groups (<= 16)
-int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                       int smem_limit, int max_groups);
-// resident CTAs per SM for this plan
-int expand_max_ctas(const ExpandArgs& a);
+// bytes of one parent's image (the staging kernel's shared memory when it
+// stages there)
+int expand_image_bytes(int dz, int T_max, int K_max, int M);
+// shared memory of a draw-kernel CTA of `threads` threads
+int expand_draw_smem(int threads);
+// shared memory of a warp-kernel CTA of `warps` warps
+int expand_warp_smem(int dz, int materialize, int T_max, int warps);
+enum class ExpandKernel { kStage, kDraw, kWarp, kMatPrep };
+// resident CTAs per SM of one of the kernels
+int expand_occupancy(const ExpandArgs& a, ExpandKernel k, int threads, int smem);
 // allows the expansion kernels the device's opt-in shared memory (call once)
 void expand_init(int smem_limit);
-// one persistent CTA per grid slot, looping over the parents (and slices)
-void launch_expand(const ExpandArgs& a, int grid, cudaStream_t s);
+// stage: persistent CTAs over parents; draw: persistent over (parent, slice
+// of blockDim draws); warp: persistent warps over a list of children;
+// mat_prep: one warp per retained parent
+void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int threads, int smem,
+                          cudaStream_t s);
 // marks duplicate children (status 2, key dropped), one block per parent
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
                   int8_t* child_status, int grid, cudaStream_t s);

@@ -4,34 +4,46 @@
 // retention of unique children), and the regeneration of the retained
 // children for the batched track update.
 //
-// One CTA per parent hypothesis.  The CTA stages the parent's gated pairs in
-// shared memory re-indexed by detection row (slots ascending within a row),
-// with per-row integer thresholds of the categorical draw under "all slots
-// alive", and a reference association (each row's most likely option) whose
-// exact score is computed once.  Each warp then draws children:
-//   phase 1  Philox words for the slots that can die; dead slots are marked;
-//   phase 2  one Philox word per detection row; the row's option is the first
-//            whose threshold exceeds the 24-bit uniform (rows with a dead
-//            candidate fall back to the FP32 normalised row of C'_k); rows
-//            that leave the reference move fixed-point sums (count, sum of
-//            innovations, sum of e^T R^-1 e) between slots;
-//   phase 3  only the touched slots are rescored; the child's log-weight is
-//            the reference score plus the exact integer change.
+// Four kernels share one per-parent image in global memory:
+//   stage     one CTA per parent builds the parent's tables (in shared memory
+//             when they fit, then copied out; else in place): its gated pairs
+//             re-indexed by detection row (slots ascending within a row), per
+//             row integer thresholds of the categorical draw under "all slots
+//             alive", a reference association (each row's most likely option)
+//             with its exact score, and per slot the m-only part of the track
+//             term for m_ref - 1, m_ref and m_ref + 1 detections;
+//             The stage also tabulates the exact score change of every single
+//             deviation from the reference: a detection joining a candidate
+//             pair's slot, leaving its reference slot, a slot dying;
+//   draw      one thread per child: Philox words for the slots that can die
+//             (stage 1) and one per detection row (stage 2); the row's option
+//             is the first whose threshold exceeds the 24-bit uniform (rows
+//             with a dead candidate fall back to the FP32 normalised row of
+//             C'_k); deaths and rows that leave the reference are listed in
+//             shared memory; the child's log-weight is the reference score
+//             plus the tabulated changes, or, when a slot is met twice, the
+//             exact rescoring of every met slot (stage 3), in fixed point;
+//   warp      one warp per child, rows split over the lanes and per-slot sums
+//             in shared memory: children whose lists overflow the draw
+//             kernel's, every child when parents are too few to fill
+//             the GPU with threads, and the regeneration of retained children
+//             (association rows, track lists, updated-component requests);
+//   mat_prep  the updated components of each retained parent's reference
+//             association, requested once per parent.
 // The duplicate test keys a child by the order-free sum of mix64 keys of its
 // deviations and deaths.
 #include "glmb_kernels.h"
 
 namespace glmb {
 
+// ---- per-parent image ----
 struct Lay {
   int scal;
-  int comp, dthr, logp, log1mp, mref, seref, sqref, termref, ninfref, hwref, refnew;
-  int rowoff, rowfill, rowref, rowflag, rowthr0, roww0;
-  int cslot, cthr, ceidx, cw, ce, cq, hph;
-  int dpc;
-  int redo;
-  int grp, grp_bytes;
-  int g_cnt, g_se, g_sq, g_hw, g_newval, g_tmask, g_dmask, g_dpre, g_tlist, g_nt;
+  int row, rowbl, seref, sqref, termref, hwref, gaind, lossd, deadd;
+  int rowrk, rca, rowoff, rowfill, roww0;
+  int comp, dthr, logp, log1mp, mref, refnew, hph, slm, dpc;
+  int cthr, ceidx, cw, ce, cq, cslot;
+  int ninfref, sln, gninf, lninf, dninf;
   int total;
 };
 
@@ -48,72 +60,97 @@ struct Scal {
   long long ref_score;
   unsigned long long uid;
   double logw;
-  int ninf_ref, nclut_ref, T, Town, K, ndpc, s_lo, s_hi, bad, nredo;
+  int ninf_ref, nclut_ref, T, Town, K, ndpc, nrca, bad;
 };
 
-__host__ __device__ inline Lay make_lay(int dz, int mat, int T, int K, int M, int HU, int G) {
+// T, K, M: the plan's slots, gated pairs and detection rows per parent.
+// Per-slot arrays are indexed with the parent's own slot count as stride,
+// per-pair arrays with K.
+__host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   Lay L;
   Bump b;
-  const int W = (T + 31) / 32 + 1;
+  const int NP = dz * (dz + 1) / 2;
   L.scal = b.take(sizeof(Scal));
-  L.seref = b.take(8LL * dz * T);
-  L.sqref = b.take(8LL * T);
-  L.termref = b.take(8LL * T);
-  L.hwref = mat ? b.take(8LL * T) : 0;
+  L.row = b.take(16LL * M);                 // packed row descriptors (uint4)
+  L.rowbl = b.take(8LL * M);                // bit (slot mod 64) of each candidate slot
+  L.seref = b.take(8LL * dz * T);           // reference sums of innovations (fixed point)
+  L.sqref = b.take(8LL * T);                // reference sums of e^T R^-1 e
+  L.termref = b.take(8LL * T);              // reference track terms
+  L.hwref = b.take(8LL * T);                // reference detection-set keys
+  // exact score change of one deviation from the reference: a row's
+  // detection joining candidate pair p's slot (gaind[p]), leaving its
+  // reference slot (lossd[i]), a slot dying (deadd[t]); with the changes of
+  // the infinite-term counts (gninf, lninf, dninf)
+  L.gaind = b.take(8LL * K);
+  L.lossd = b.take(8LL * M);
+  L.deadd = b.take(8LL * T);
+  L.rowrk = b.take(4LL * M);                // reference option's slot and pair
+  L.rca = b.take(4LL * ((M + 3) / 4 + 1));  // chunks of 4 rows with candidates
+  L.rowoff = b.take(4LL * (M + 1));
+  L.rowfill = b.take(4LL * (M + 1));
+  L.roww0 = b.take(4LL * M);
   L.comp = b.take(4LL * T);
   L.dthr = b.take(4LL * T);
   L.logp = b.take(4LL * T);
   L.log1mp = b.take(4LL * T);
   L.mref = b.take(4LL * T);
-  L.refnew = mat ? b.take(4LL * T) : 0;
-  L.rowoff = b.take(4LL * (M + 1));
-  L.rowfill = b.take(4LL * (M + 1));
-  L.rowthr0 = b.take(4LL * M);
-  L.roww0 = b.take(4LL * M);
+  L.refnew = b.take(4LL * T);
+  L.hph = b.take(4LL * NP * T);             // H P H^T of each slot (packed)
+  L.slm = b.take(4LL * 3 * (NP + 1) * T);   // m-only term parts, m = m_ref - 1 .. m_ref + 1
+  L.dpc = b.take(4LL * (T / 4 + 2));        // chunks of 4 slots that can die
   L.cthr = b.take(4LL * K);
   L.ceidx = b.take(4LL * K);
   L.cw = b.take(4LL * K);
   L.ce = b.take(4LL * dz * K);              // innovation of each candidate pair
   L.cq = b.take(4LL * K);                   // e^T R^-1 e of each candidate pair
-  L.hph = b.take(4LL * (dz * (dz + 1) / 2) * T);   // H P H^T of each slot (packed)
-  L.dpc = b.take(4LL * (T / 4 + 2));
   L.cslot = b.take(2LL * K);
-  L.rowref = b.take(2LL * M);
-  L.redo = b.take(2LL * HU);
-  L.rowflag = b.take(M);
   L.ninfref = b.take(T);
-  L.grp = b.off;
-  Bump g;
-  L.g_se = g.take(8LL * dz * T);
-  L.g_sq = g.take(8LL * T);
-  L.g_hw = mat ? g.take(8LL * T) : 0;
-  L.g_cnt = g.take(4LL * T);
-  L.g_newval = mat ? g.take(4LL * T) : 0;
-  L.g_tmask = g.take(4LL * W);
-  L.g_dmask = g.take(4LL * W);
-  L.g_dpre = g.take(4LL * W);
-  L.g_nt = g.take(16);
-  L.g_tlist = g.take(2LL * T);
-  L.grp_bytes = g.off;
-  L.total = L.grp + G * L.grp_bytes;
+  L.sln = b.take(3LL * T);
+  L.gninf = b.take(K);
+  L.lninf = b.take(M);
+  L.dninf = b.take(T);
+  L.total = b.off;
   return L;
 }
 
-int expand_smem_bytes(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                      int n_groups) {
-  return make_lay(dz, materialize, T_max, K_max, M, h_up, n_groups).total;
+int expand_image_bytes(int dz, int T, int K, int M) {
+  return (make_lay(dz, T, K, M).total + 127) & ~127;
 }
 
-int expand_plan_groups(int dz, int materialize, int T_max, int K_max, int M, int h_up,
-                       int smem_limit, int max_groups) {
-  for (int G = max_groups < 1 ? 1 : (max_groups > 16 ? 16 : max_groups); G >= 1; --G)
-    if (expand_smem_bytes(dz, materialize, T_max, K_max, M, h_up, G) <= smem_limit) return G;
-  return 0;
+// per-warp work area of the warp kernel
+struct WLay {
+  int se, sq, hw, cnt, newval, tmask, dmask, dpre, nt, tlist, total;
+};
+
+__host__ __device__ inline WLay make_wlay(int dz, int mat, int T) {
+  WLay L;
+  Bump b;
+  const int W = (T + 31) / 32 + 1;
+  L.se = b.take(8LL * dz * T);
+  L.sq = b.take(8LL * T);
+  L.hw = mat ? b.take(8LL * T) : 0;
+  L.cnt = b.take(4LL * T);
+  L.newval = mat ? b.take(4LL * T) : 0;
+  L.tmask = b.take(4LL * W);
+  L.dmask = b.take(4LL * W);
+  L.dpre = b.take(4LL * W);
+  L.nt = b.take(16);
+  L.tlist = b.take(2LL * T);
+  L.total = b.off;
+  return L;
+}
+
+int expand_warp_smem(int dz, int materialize, int T, int warps) {
+  return warps * make_wlay(dz, materialize, T).total;
 }
 
 template <typename T>
 __device__ __forceinline__ T* at(unsigned char* base, int off) {
   return reinterpret_cast<T*>(base + off);
+}
+template <typename T>
+__device__ __forceinline__ const T* at(const unsigned char* base, int off) {
+  return reinterpret_cast<const T*>(base + off);
 }
 
 __device__ __forceinline__ uint32_t thr_of(float frac) {
@@ -140,6 +177,105 @@ __device__ __forceinline__ void slot_HPH(const float* s_hph, int T, int t, float
       HPH[x][y] = v;
       HPH[y][x] = v;
     }
+}
+
+// Cached m-only parts of slot t's term, v = m - m_ref + 1 in {0, 1, 2};
+// kNoSlm marks an entry that was not built (m < 1).
+constexpr int8_t kNoSlm = 127;
+
+template <int DZ>
+__device__ __forceinline__ void store_slm(float* s_slm, int8_t* s_sln, int T, int v, int t,
+                                          const SlotM<DZ>& s) {
+  constexpr int NP = DZ * (DZ + 1) / 2;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) s_slm[(v * (NP + 1) + k) * T + t] = s.Sinv[k];
+  s_slm[(v * (NP + 1) + NP) * T + t] = s.c;
+  s_sln[v * T + t] = (int8_t)s.ninf;
+}
+
+template <int DZ>
+__device__ __forceinline__ SlotM<DZ> load_slm(const float* s_slm, const int8_t* s_sln, int T, int v,
+                                              int t) {
+  constexpr int NP = DZ * (DZ + 1) / 2;
+  SlotM<DZ> s;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) s.Sinv[k] = s_slm[(v * (NP + 1) + k) * T + t];
+  s.c = s_slm[(v * (NP + 1) + NP) * T + t];
+  s.ninf = s_sln[v * T + t];
+  return s;
+}
+
+// Term of slot t alive with m detections, built from H P H^T (kept out of
+// line: it is rare and needs many registers)
+template <int DZ>
+__device__ __noinline__ long long slot_term_full(const Model& md, const float* s_hph, const float* s_logp,
+                                                 int T, int t, int m, const long long (&se)[DZ], long long sq,
+                                                 int& ninf) {
+  float HPH[DZ][DZ];
+  slot_HPH<DZ>(s_hph, T, t, HPH);
+  return alive_term<DZ>(md, HPH, s_logp[t], m, se, sq, ninf);
+}
+
+// read-only view of a staged parent
+struct View {
+  const Scal* sc;
+  const uint4* row;
+  const unsigned long long* rowbl;
+  const long long *seref, *sqref, *termref, *gaind, *lossd, *deadd;
+  const unsigned long long* hwref;
+  const uint32_t *rowrk, *rca, *comp, *dthr, *refnew, *dpc, *cthr;
+  const float *roww0, *logp, *log1mp, *hph, *slm, *cw, *ce, *cq;
+  const int* mref;
+  const uint16_t* cslot;
+  const uint8_t* ninfref;
+  const int8_t *sln, *gninf, *lninf, *dninf;
+};
+
+__device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) {
+  View v;
+  v.sc = at<Scal>(b, L.scal);
+  v.row = at<uint4>(b, L.row);
+  v.rowbl = at<unsigned long long>(b, L.rowbl);
+  v.seref = at<long long>(b, L.seref);
+  v.sqref = at<long long>(b, L.sqref);
+  v.termref = at<long long>(b, L.termref);
+  v.gaind = at<long long>(b, L.gaind);
+  v.lossd = at<long long>(b, L.lossd);
+  v.deadd = at<long long>(b, L.deadd);
+  v.gninf = at<int8_t>(b, L.gninf);
+  v.lninf = at<int8_t>(b, L.lninf);
+  v.dninf = at<int8_t>(b, L.dninf);
+  v.hwref = at<unsigned long long>(b, L.hwref);
+  v.rowrk = at<uint32_t>(b, L.rowrk);
+  v.rca = at<uint32_t>(b, L.rca);
+  v.comp = at<uint32_t>(b, L.comp);
+  v.dthr = at<uint32_t>(b, L.dthr);
+  v.refnew = at<uint32_t>(b, L.refnew);
+  v.dpc = at<uint32_t>(b, L.dpc);
+  v.cthr = at<uint32_t>(b, L.cthr);
+  v.roww0 = at<float>(b, L.roww0);
+  v.logp = at<float>(b, L.logp);
+  v.log1mp = at<float>(b, L.log1mp);
+  v.hph = at<float>(b, L.hph);
+  v.slm = at<float>(b, L.slm);
+  v.cw = at<float>(b, L.cw);
+  v.ce = at<float>(b, L.ce);
+  v.cq = at<float>(b, L.cq);
+  v.mref = at<int>(b, L.mref);
+  v.cslot = at<uint16_t>(b, L.cslot);
+  v.ninfref = at<uint8_t>(b, L.ninfref);
+  v.sln = at<int8_t>(b, L.sln);
+  return v;
+}
+
+// Term of slot t alive with m = m_ref + dcnt detections whose sums are
+// (se, sq): from the cache when it holds m, else built from H P H^T.
+template <int DZ>
+__device__ __forceinline__ long long slot_term(const Model& md, const View& v, int T, int t, int m, int dcnt,
+                                               const long long (&se)[DZ], long long sq, int& ninf) {
+  if (m >= 1 && dcnt >= -1 && dcnt <= 1 && v.sln[(dcnt + 1) * T + t] != kNoSlm)
+    return term_from<DZ>(md, load_slm<DZ>(v.slm, v.sln, T, dcnt + 1, t), m, se, sq, ninf);
+  return slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, se, sq, ninf);
 }
 
 __device__ __forceinline__ bool bit_of(const uint32_t* m, int t) {
@@ -177,65 +313,42 @@ __device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long
   return kNewTag;
 }
 
-template <int DZ, bool MAT>
-__device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, const int S, const Lay& L,
-                              unsigned char* sm);
-
-// Persistent: each CTA takes parents blockIdx.x, blockIdx.x + gridDim.x, ...
-template <int DZ, bool MAT>
-__global__ void __launch_bounds__(512) expand_kernel(const ExpandArgs a) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const Lay L = make_lay(DZ, MAT, a.T_max, a.K_max, a.M_plan, a.md.h_up, a.n_fb_groups);
-  const int H = a.fs->H;
-  // draws of a parent are split into S slices when parents are too few to
-  // fill the GPU (about target_warps warps in flight)
-  int S = 1;
-  if (!MAT) {
-    const long long per = (long long)H * (blockDim.x >> 5);
-    S = per > 0 ? (int)min((long long)a.max_slices, (a.target_warps + per - 1) / per) : 1;
-    if (S < 1) S = 1;
-  }
-  for (int job = blockIdx.x; job < H * S; job += gridDim.x) {
-    __syncthreads();   // the previous job's shared memory is free
-    expand_parent<DZ, MAT>(a, job / S, job % S, S, L, sm);
-  }
-}
-
-template <int DZ, bool MAT>
-__device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, const int S, const Lay& L,
-                              unsigned char* sm) {
+// ====================== stage: one CTA per parent ======================
+// Builds parent h's image at `sm` (shared memory, or the image itself).
+template <int DZ>
+__device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm) {
   const Model& md = a.md;
-  const int HU = md.h_up;
   const int M = a.fs->M;
   const int birth_base = a.fs->n_comp, nb = a.fs->nb;
-  const uint2 key = make_uint2(md.seed_lo, md.seed_hi ^ (uint32_t)a.fs->frame);
   Scal& sc = *at<Scal>(sm, L.scal);
+  uint4* s_row = at<uint4>(sm, L.row);
+  unsigned long long* s_rowbl = at<unsigned long long>(sm, L.rowbl);
+  long long* s_seref = at<long long>(sm, L.seref);
+  long long* s_sqref = at<long long>(sm, L.sqref);
+  long long* s_termref = at<long long>(sm, L.termref);
+  unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
+  uint32_t* s_rowrk = at<uint32_t>(sm, L.rowrk);
+  uint32_t* s_rca = at<uint32_t>(sm, L.rca);
+  uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
+  uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
+  float* s_roww0 = at<float>(sm, L.roww0);
   uint32_t* s_comp = at<uint32_t>(sm, L.comp);
   uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
   float* s_logp = at<float>(sm, L.logp);
   float* s_log1mp = at<float>(sm, L.log1mp);
   int* s_mref = at<int>(sm, L.mref);
-  long long* s_seref = at<long long>(sm, L.seref);
-  long long* s_sqref = at<long long>(sm, L.sqref);
-  long long* s_termref = at<long long>(sm, L.termref);
-  uint8_t* s_ninfref = at<uint8_t>(sm, L.ninfref);
-  unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
-  uint32_t* s_refnew = at<uint32_t>(sm, L.refnew);
-  uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
-  uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
-  uint16_t* s_rowref = at<uint16_t>(sm, L.rowref);
-  uint8_t* s_rowflag = at<uint8_t>(sm, L.rowflag);
-  uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
-  float* s_roww0 = at<float>(sm, L.roww0);
-  uint16_t* s_cslot = at<uint16_t>(sm, L.cslot);
+  float* s_hph = at<float>(sm, L.hph);
+  float* s_slm = at<float>(sm, L.slm);
+  uint32_t* s_dpc = at<uint32_t>(sm, L.dpc);
   uint32_t* s_cthr = at<uint32_t>(sm, L.cthr);
   uint32_t* s_ceidx = at<uint32_t>(sm, L.ceidx);
   float* s_cw = at<float>(sm, L.cw);
   float* s_ce = at<float>(sm, L.ce);
   float* s_cq = at<float>(sm, L.cq);
-  float* s_hph = at<float>(sm, L.hph);
+  uint16_t* s_cslot = at<uint16_t>(sm, L.cslot);
+  uint8_t* s_ninfref = at<uint8_t>(sm, L.ninfref);
+  int8_t* s_sln = at<int8_t>(sm, L.sln);
   const int Kp = a.K_max;                   // stride of the candidate arrays
-  uint32_t* s_dpc = at<uint32_t>(sm, L.dpc);
   const CompTable& ct = a.ct;
   const PairTable& pt = a.pt;
   const size_t capp = (size_t)pt.cap_pairs;
@@ -250,29 +363,15 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
     sc.ninf_ref = 0;
     sc.nclut_ref = 0;
     sc.ndpc = 0;
+    sc.nrca = 0;
     sc.bad = 0;
-    sc.nredo = 0;
+    sc.K = 0;
     sc.uid = a.parents.uid[h];
     sc.logw = a.parents.logw[h];
-    sc.s_lo = sc.s_hi = 0;
-    if (MAT) {
-      // survivors of this parent: child indices in [h*HU, (h+1)*HU)
-      const long long lo_key = (long long)h * HU, hi_key = lo_key + HU;
-      const int ns = (int)*a.n_surv;
-      int l = 0, r = ns;
-      while (l < r) { const int mid = (l + r) >> 1; if (a.surv_idx[mid] < lo_key) l = mid + 1; else r = mid; }
-      sc.s_lo = l;
-      r = ns;
-      while (l < r) { const int mid = (l + r) >> 1; if (a.surv_idx[mid] < hi_key) l = mid + 1; else r = mid; }
-      sc.s_hi = l;
-    }
     if (sc.T > a.T_max || M > a.M_plan) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
-    // a frame already abandoned (e.g. entries beyond capacity) writes nothing
-    if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) sc.bad = 1;
   }
   __syncthreads();
   if (sc.bad) return;
-  if (MAT && sc.s_lo == sc.s_hi) return;
   const int T = sc.T, Town = sc.Town;
   const uint32_t plo = a.parents.ptr[h];
 
@@ -294,7 +393,7 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
 #pragma unroll
     for (int d = 0; d < DZ; ++d) s_seref[d * T + t] = 0;
     s_sqref[t] = 0;
-    if (MAT) s_hwref[t] = 0;
+    s_hwref[t] = 0;
   }
   for (int i = tid; i <= M; i += nthr) s_rowfill[i] = 0;
   __syncthreads();
@@ -358,9 +457,9 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
         s_ceidx[off + y + 1] = ke;
       }
       if (nc == 0) {
-        s_rowref[i] = 0;
-        s_rowflag[i] = 0;
-        s_rowthr0[i] = kOne24;
+        s_row[i] = make_uint4(off, 0u, kOne24, kOne24);
+        s_rowbl[i] = 0ull;
+        s_rowrk[i] = 0u;
         s_roww0[i] = 1.f;
         ++my_clut;
         continue;
@@ -383,16 +482,22 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
       float cum = w0, best = w0;
       int ref = 0;
       bool flag = false;
-      s_rowthr0[i] = (nc == 0) ? kOne24 : thr_of(cum / sum);
+      const uint32_t thr0 = thr_of(cum / sum);
+      unsigned long long bl = 0ull;
       for (int j = 0; j < nc; ++j) {
         const float w = s_cw[off + j];
+        bl |= 1ull << (s_cslot[off + j] & 63);
         cum += w;
         s_cthr[off + j] = (j == nc - 1) ? kOne24 : thr_of(cum / sum);
         if (w > best) { best = w; ref = j + 1; }
         flag |= s_dthr[s_cslot[off + j]] > 0u;
       }
-      s_rowref[i] = (uint16_t)ref;
-      s_rowflag[i] = flag ? 1 : 0;
+      // row i: x = first candidate, y = count | may-die flag << 15 |
+      // reference option << 16, z = clutter threshold, w = first candidate's
+      s_row[i] = make_uint4(off, (uint32_t)nc | (flag ? 0x8000u : 0u) | ((uint32_t)ref << 16), thr0,
+                            s_cthr[off]);
+      s_rowbl[i] = bl;
+      s_rowrk[i] = ref > 0 ? (((uint32_t)s_cslot[off + ref - 1] + 1u) << 16) | (off + ref - 1) : 0u;
       s_roww0[i] = w0;
       if (ref == 0) {
         ++my_clut;
@@ -404,36 +509,26 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
         for (int d = 0; d < DZ; ++d)
           atomicAdd((unsigned long long*)&s_seref[d * T + r], (unsigned long long)fx_of(s_ce[d * Kp + pos]));
         atomicAdd((unsigned long long*)&s_sqref[r], (unsigned long long)fx_of(s_cq[pos]));
-        if (MAT) atomicAdd(&s_hwref[r], wset_key(i));
+        atomicAdd(&s_hwref[r], wset_key(i));
       }
     }
     if (my_clut) atomicAdd(&sc.nclut_ref, my_clut);
   }
   __syncthreads();
 
-  // ---- reference terms, death-possible chunks ----
-  {
-    long long my_term = 0;
-    int my_ninf = 0;
-    for (int t = tid; t < T; t += nthr) {
-      float HPH[DZ][DZ];
-      slot_HPH<DZ>(s_hph, T, t, HPH);
-      long long se[DZ];
-#pragma unroll
-      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t];
-      int ninf;
-      const long long term = alive_term<DZ>(md, HPH, s_logp[t], s_mref[t], se, s_sqref[t], ninf);
-      s_termref[t] = term;
-      s_ninfref[t] = (uint8_t)ninf;
-      my_term += term;
-      my_ninf += ninf;
-      if (MAT) {
-        s_refnew[t] = s_mref[t] >= 1 ? upd_insert<DZ>(a, s_comp[t], s_hwref[t], s_mref[t], se)
-                                     : s_comp[t];
-      }
+  // ---- m-only term parts (slot x {m_ref - 1, m_ref, m_ref + 1}), chunk lists ----
+  for (int x = tid; x < 3 * T; x += nthr) {
+    const int t = x % T, v = x / T;
+    const int m = s_mref[t] - 1 + v;
+    if (m < 1) {
+      s_sln[v * T + t] = kNoSlm;
+      continue;
     }
-    if (my_term) atomicAdd((unsigned long long*)&sc.ref_score, (unsigned long long)my_term);
-    if (my_ninf) atomicAdd(&sc.ninf_ref, my_ninf);
+    float HPH[DZ][DZ];
+    slot_HPH<DZ>(s_hph, T, t, HPH);
+    store_slm<DZ>(s_slm, s_sln, T, v, t, make_slot_m<DZ>(md, HPH, s_logp[t], m));
+  }
+  {
     const int nch = (T + 3) >> 2;
     for (int cc = tid; cc < nch; cc += nthr) {
       uint32_t mask = 0;
@@ -444,494 +539,661 @@ __device__ void expand_parent(const ExpandArgs& a, const int h, const int sl, co
       }
       if (mask) s_dpc[atomicAdd(&sc.ndpc, 1)] = ((uint32_t)cc << 4) | mask;
     }
+    for (int cc = tid; cc < ((M + 3) >> 2); cc += nthr) {
+      uint32_t mask = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * cc + b;
+        if (i < M && s_rowoff[i + 1] > s_rowoff[i]) mask |= 1u << b;
+      }
+      if (mask) s_rca[atomicAdd(&sc.nrca, 1)] = ((uint32_t)cc << 4) | mask;
+    }
   }
   __syncthreads();
+
+  // ---- reference terms ----
+  {
+    long long my_term = 0;
+    int my_ninf = 0;
+    for (int t = tid; t < T; t += nthr) {
+      long long se[DZ];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t];
+      const int mr = s_mref[t];
+      int ninf;
+      long long term;
+      if (mr >= 1 && s_sln[T + t] != kNoSlm) {
+        term = term_from<DZ>(md, load_slm<DZ>(s_slm, s_sln, T, 1, t), mr, se, s_sqref[t], ninf);
+      } else {
+        float HPH[DZ][DZ];
+        slot_HPH<DZ>(s_hph, T, t, HPH);
+        term = alive_term<DZ>(md, HPH, s_logp[t], mr, se, s_sqref[t], ninf);
+      }
+      s_termref[t] = term;
+      s_ninfref[t] = (uint8_t)ninf;
+      my_term += term;
+      my_ninf += ninf;
+    }
+    if (my_term) atomicAdd((unsigned long long*)&sc.ref_score, (unsigned long long)my_term);
+    if (my_ninf) atomicAdd(&sc.ninf_ref, my_ninf);
+  }
+  __syncthreads();
+
+  // ---- single-deviation deltas (same functions and inputs as a child's
+  // rescoring of a slot touched once, so the sums are bit-identical) ----
+  {
+    const View v = make_view(sm, L);
+    long long* s_gaind = at<long long>(sm, L.gaind);
+    long long* s_lossd = at<long long>(sm, L.lossd);
+    long long* s_deadd = at<long long>(sm, L.deadd);
+    int8_t* s_gninf = at<int8_t>(sm, L.gninf);
+    int8_t* s_lninf = at<int8_t>(sm, L.lninf);
+    int8_t* s_dninf = at<int8_t>(sm, L.dninf);
+    const int K = sc.K;
+    for (int pos = tid; pos < K; pos += nthr) {
+      const int t = s_cslot[pos];
+      long long se[DZ];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + fx_of(s_ce[d * Kp + pos]);
+      int ninf;
+      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] + 1, 1, se, s_sqref[t] + fx_of(s_cq[pos]), ninf);
+      s_gaind[pos] = term - s_termref[t];
+      s_gninf[pos] = (int8_t)(ninf - (int)s_ninfref[t]);
+    }
+    for (int i = tid; i < M; i += nthr) {
+      const uint4 R = s_row[i];
+      const int ref = (int)(R.y >> 16);
+      if (ref == 0) {
+        s_lossd[i] = 0;
+        s_lninf[i] = 0;
+        continue;
+      }
+      const uint32_t pos = R.x + (uint32_t)ref - 1u;
+      const int t = s_cslot[pos];
+      long long se[DZ];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] - fx_of(s_ce[d * Kp + pos]);
+      int ninf;
+      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] - 1, -1, se, s_sqref[t] - fx_of(s_cq[pos]), ninf);
+      s_lossd[i] = term - s_termref[t];
+      s_lninf[i] = (int8_t)(ninf - (int)s_ninfref[t]);
+    }
+    for (int t = tid; t < T; t += nthr) {
+      int ninf;
+      const long long term = dead_term(s_log1mp[t], ninf);
+      s_deadd[t] = term - s_termref[t];
+      s_dninf[t] = (int8_t)(ninf - (int)s_ninfref[t]);
+    }
+  }
   if (tid == 0) {
     sc.ref_score += __double2ll_rn(sc.logw * 4294967296.0);
     if (md.kappa_zero) sc.ninf_ref += sc.nclut_ref;
     else sc.ref_score += (long long)sc.nclut_ref * md.fx_log_kappa;
   }
-  __syncthreads();
+}
 
-  // ---- draws, one thread per child ----
-  // Every thread walks the same rows (broadcast shared-memory reads) with its
-  // own random words, keeps its deaths and deviating rows in short local
-  // lists, and rescores only the slots they touch.  Children whose lists
-  // overflow (or parents with more than kTwMax * 32 slots) are redone below
-  // by one warp each.
-  uint16_t* s_redo = at<uint16_t>(sm, L.redo);
-  const int chunk = (HU + S - 1) / S;
-  const int n_lo = MAT ? 0 : sl * chunk;
-  const int n_items = MAT ? (sc.s_hi - sc.s_lo) : max(0, min(HU, n_lo + chunk) - n_lo);
+// Persistent: each CTA stages parents blockIdx.x, blockIdx.x + gridDim.x, ...
+// SMEM: staged in shared memory and copied to the image (16-byte words).
+template <int DZ, bool SMEM>
+__global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
+  const int H = a.fs->H;
+  for (int h = blockIdx.x; h < H; h += gridDim.x) {
+    unsigned char* img = a.img + (size_t)h * a.img_stride;
+    __syncthreads();   // the previous parent's copy-out has read shared memory
+    stage_parent<DZ>(a, h, L, SMEM ? sm : img);
+    __syncthreads();
+    if (SMEM) {
+      // a parent whose staging failed copies only its header
+      const int bytes = at<Scal>(sm, L.scal)->bad ? (int)sizeof(Scal) : L.total;
+      const uint4* src = reinterpret_cast<const uint4*>(sm);
+      uint4* dst = reinterpret_cast<uint4*>(img);
+      for (int w = threadIdx.x; w < (bytes + 15) / 16; w += blockDim.x) dst[w] = src[w];
+    }
+  }
+}
+
+// ====================== draw: one thread per child ======================
+constexpr int kDrawDead = 16, kDrawDev = 24;   // per-thread list capacities (shared memory)
+
+// Returns false when the child's deaths or deviations overflow its lists
+// (the child is then queued for the warp kernel).  s_dl / s_dv / s_ds: this
+// thread's lists of dead slots, deviations (row << 16 | option) and their
+// (reference slot + 1, new slot + 1), entry j at [j * stride].
+template <int DZ>
+__device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v, const int T, const int Kp,
+                                             const int h, const int n, const uint2 key, uint16_t* s_dl,
+                                             uint32_t* s_dv, uint32_t* s_ds, const int stride) {
+  const Model& md = a.md;
+  const Scal& sc = *v.sc;
   const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
-  const int ndpc = sc.ndpc;
-  const int nrc = (M + 3) >> 2;
-  const long long ref_score = sc.ref_score;
-  const int ninf_ref = sc.ninf_ref;
-  const int W = (T + 31) >> 5;
-  {
-    constexpr int kTwMax = 64, kDeadMax = 64, kDevMax = 128, kTouchMax = 2 * kDevMax + kDeadMax;
-    for (int it = tid; it < n_items; it += nthr) {
-      if (MAT || !a.thread_path || W > kTwMax) {
-        s_redo[atomicAdd(&sc.nredo, 1)] = (uint16_t)it;
-        continue;
-      }
-      const int n = MAT ? (int)(a.surv_idx[sc.s_lo + it] - (long long)h * HU) : n_lo + it;
-      const int s_out = MAT ? sc.s_lo + it : 0;
-      uint32_t deadw[kTwMax];
-      uint16_t dl[kDeadMax];
-      uint32_t dv[kDevMax];
-      for (int w = 0; w < W; ++w) deadw[w] = 0u;
-      int nd = 0, ndv = 0, dclut = 0;
-      bool over = false, bad_row = false;
-      unsigned long long hsh = 0;
-      // stage 1: deaths
-      for (int x = 0; x < ndpc; ++x) {
-        const uint32_t ent = s_dpc[x];
-        const uint32_t cc = ent >> 4, mask = ent & 15u;
-        const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
+  const int ndpc = sc.ndpc, nrca = sc.nrca;
+  unsigned long long bloom = 0ull, hsh = 0ull;
+  long long delta = 0;
+  int nd = 0, ndv = 0, dclut = 0, dninf = 0;
+  bool bad_row = false;
+  // stage 1: deaths (a dead slot's change is its dead term)
+  for (int x = 0; x < ndpc; ++x) {
+    const uint32_t ent = v.dpc[x];
+    const uint32_t cc = ent >> 4, mask = ent & 15u;
+    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
+    const uint4 th = *reinterpret_cast<const uint4*>(v.dthr + 4 * cc);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          if (!((mask >> b) & 1u)) continue;
-          const int t = 4 * (int)cc + b;
-          if ((word_of(r, b) >> 8) < s_dthr[t]) {
-            deadw[t >> 5] |= 1u << (t & 31);
-            if (nd < kDeadMax) dl[nd] = (uint16_t)t;
-            ++nd;
-          }
-        }
-      }
-      over |= nd > kDeadMax;
-      // dead slots below each 32-slot word (child track index = slot - dead below)
-      uint32_t dpw[kTwMax];
-      if (MAT) {
-        uint32_t run = 0;
-        for (int w = 0; w < W; ++w) {
-          dpw[w] = run;
-          run += __popc(deadw[w]);
-        }
-      }
-      // stage 2: one categorical draw per detection row
-      for (int cc = 0; cc < nrc; ++cc) {
-        const int i0 = 4 * cc;
-        const int i1 = min(i0 + 4, M);
-        if (s_rowoff[i1] == s_rowoff[i0]) {
-          if (MAT)
-            for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
-          continue;
-        }
-        const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), key);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int i = i0 + b;
-          if (i >= i1) break;
-          const uint32_t off = s_rowoff[i];
-          const int nc = (int)(s_rowoff[i + 1] - off);
-          if (nc == 0) {
-            if (MAT) a.out_theta[(size_t)s_out * M + i] = 0;
-            continue;
-          }
-          const uint32_t k = word_of(r, b) >> 8;
-          bool fast = true;
-          if (s_rowflag[i])
-            for (int j = 0; j < nc; ++j) {
-              const int t = s_cslot[off + j];
-              if ((deadw[t >> 5] >> (t & 31)) & 1u) { fast = false; break; }
-            }
-          int opt;
-          if (fast) {
-            if (k < s_rowthr0[i]) {
-              opt = 0;
-            } else {
-              int j = 0;
-              while (j < nc - 1 && k >= s_cthr[off + j]) ++j;
-              opt = j + 1;
-            }
-          } else {
-            const float w0 = md.kappa_zero ? 0.f : s_roww0[i];
-            float sum = w0;
-            for (int j = 0; j < nc; ++j) {
-              const int t = s_cslot[off + j];
-              if (!((deadw[t >> 5] >> (t & 31)) & 1u)) sum += s_cw[off + j];
-            }
-            if (!(sum > 0.f)) {
-              bad_row = true;
-              opt = 0;
-            } else {
-              const float xk = (float)k * 5.9604644775390625e-8f * sum;
-              float cum = w0;
-              int last = w0 > 0.f ? 0 : -1;
-              opt = -1;
-              if (w0 > 0.f && xk < cum) opt = 0;
-              for (int j = 0; j < nc; ++j) {
-                const int t = s_cslot[off + j];
-                if ((deadw[t >> 5] >> (t & 31)) & 1u) continue;
-                const float w = s_cw[off + j];
-                if (!(w > 0.f)) continue;
-                cum += w;
-                last = j + 1;
-                if (opt < 0 && xk < cum) opt = j + 1;
-              }
-              if (opt < 0) opt = last < 0 ? 0 : last;
-            }
-          }
-          // deviations are rare and differ between lanes: only record them here
-          if (opt != s_rowref[i]) {
-            if (ndv < kDevMax) dv[ndv] = ((uint32_t)i << 16) | (uint32_t)opt;
-            ++ndv;
-          }
-          if (MAT) {
-            const int ns = opt > 0 ? (int)s_cslot[off + opt - 1] : -1;
-            uint16_t th = 0;
-            if (ns >= 0)
-              th = (uint16_t)(ns - (int)(dpw[ns >> 5] + __popc(deadw[ns >> 5] & ((1u << (ns & 31)) - 1u))) + 1);
-            a.out_theta[(size_t)s_out * M + i] = th;
-          }
-        }
-      }
-      over |= ndv > kDevMax;
-      if (over) {
-        s_redo[atomicAdd(&sc.nredo, 1)] = (uint16_t)it;
-        continue;
-      }
-      // duplicate-test key and clutter count of the deaths and deviations
-      for (int j = 0; j < nd; ++j) hsh += dead_key(dl[j]);
-      for (int q = 0; q < ndv; ++q) {
-        const int iq = (int)(dv[q] >> 16), oq = (int)(dv[q] & 0xFFFFu);
-        const uint32_t offq = s_rowoff[iq];
-        const int refq = s_rowref[iq];
-        const int nsq = oq > 0 ? (int)s_cslot[offq + oq - 1] : -1;
-        const int rsq = refq > 0 ? (int)s_cslot[offq + refq - 1] : -1;
-        dclut += (oq == 0) - (refq == 0);
-        hsh += row_key(iq, oq > 0 ? nsq + 1 : 0) - row_key(iq, refq > 0 ? rsq + 1 : 0);
-      }
-      // stage 3: rescore the touched slots (exact fixed-point deltas)
-      long long delta = 0;
-      int dninf = 0;
-      uint16_t tsl[kTouchMax];
-      uint32_t tval[MAT ? kTouchMax : 1];
-      int ntouch = 0;
-      for (int j = 0; j < nd; ++j) {
-        const int t = dl[j];
-        int ninf;
-        const long long term = dead_term(s_log1mp[t], ninf);
-        delta += term - s_termref[t];
-        dninf += ninf - (int)s_ninfref[t];
-        tsl[ntouch++] = (uint16_t)t;
-      }
-      for (int q = 0; q < ndv; ++q) {
-        const int iq = (int)(dv[q] >> 16), oq = (int)(dv[q] & 0xFFFFu);
-        const uint32_t offq = s_rowoff[iq];
-        const int refq = s_rowref[iq];
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const int o = side == 0 ? refq : oq;
-          if (o <= 0) continue;
-          const int t = s_cslot[offq + o - 1];
-          if ((deadw[t >> 5] >> (t & 31)) & 1u) continue;
-          bool seen = false;
-          for (int u = nd; u < ntouch; ++u)
-            if (tsl[u] == t) { seen = true; break; }
-          if (seen) continue;
-          // all deviating rows that leave or join slot t
-          int dcnt = 0;
-          long long dse[DZ], dsq = 0;
-          unsigned long long dhw = 0;
-#pragma unroll
-          for (int d = 0; d < DZ; ++d) dse[d] = 0;
-          for (int q2 = 0; q2 < ndv; ++q2) {
-            const int i2 = (int)(dv[q2] >> 16), o2 = (int)(dv[q2] & 0xFFFFu);
-            const uint32_t off2 = s_rowoff[i2];
-            const int r2 = s_rowref[i2];
-            if (r2 > 0 && (int)s_cslot[off2 + r2 - 1] == t) {
-              const uint32_t pos = off2 + r2 - 1;
-              --dcnt;
-#pragma unroll
-              for (int d = 0; d < DZ; ++d) dse[d] -= fx_of(s_ce[d * Kp + pos]);
-              dsq -= fx_of(s_cq[pos]);
-              if (MAT) dhw -= wset_key(i2);
-            }
-            if (o2 > 0 && (int)s_cslot[off2 + o2 - 1] == t) {
-              const uint32_t pos = off2 + o2 - 1;
-              ++dcnt;
-#pragma unroll
-              for (int d = 0; d < DZ; ++d) dse[d] += fx_of(s_ce[d * Kp + pos]);
-              dsq += fx_of(s_cq[pos]);
-              if (MAT) dhw += wset_key(i2);
-            }
-          }
-          float HPH[DZ][DZ];
-          slot_HPH<DZ>(s_hph, T, t, HPH);
-          const int m = s_mref[t] + dcnt;
-          long long se[DZ];
-#pragma unroll
-          for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + dse[d];
-          int ninf;
-          const long long term = alive_term<DZ>(md, HPH, s_logp[t], m, se, s_sqref[t] + dsq, ninf);
-          delta += term - s_termref[t];
-          dninf += ninf - (int)s_ninfref[t];
-          if (MAT) tval[ntouch] = m >= 1 ? upd_insert<DZ>(a, s_comp[t], s_hwref[t] + dhw, m, se) : s_comp[t];
-          tsl[ntouch++] = (uint16_t)t;
-        }
-      }
-      if (MAT) {
-        // the child's track list: alive slots in slot order
-        const uint32_t base = a.out_ptr[s_out];
-        for (int t = 0; t < T; ++t) {
-          if ((deadw[t >> 5] >> (t & 31)) & 1u) continue;
-          uint32_t v = s_refnew[t];
-          for (int u = nd; u < ntouch; ++u)
-            if (tsl[u] == t) { v = tval[u]; break; }
-          a.out_comp[base + (uint32_t)t - (dpw[t >> 5] + __popc(deadw[t >> 5] & ((1u << (t & 31)) - 1u)))] = v;
-        }
-      } else {
-        const long long score = ref_score + delta + (md.kappa_zero ? 0LL : (long long)dclut * md.fx_log_kappa);
-        const int ninf = ninf_ref + dninf + (md.kappa_zero ? dclut : 0);
-        const bool valid = !bad_row && ninf == 0;
-        const size_t j = (size_t)h * HU + n;
-        a.child_key[j] = valid ? score : kKeyInvalid;
-        a.child_hash[j] = hsh;
-        a.child_status[j] = valid ? 1 : 0;
-        a.child_alive[j] = (uint16_t)(T - nd);
+    for (int b = 0; b < 4; ++b) {
+      const uint32_t thb = b == 0 ? th.x : b == 1 ? th.y : b == 2 ? th.z : th.w;
+      if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < thb) {
+        const uint32_t t = 4u * cc + (uint32_t)b;
+        if (nd < kDrawDead) s_dl[nd * stride] = (uint16_t)t;
+        ++nd;
+        bloom |= 1ull << (t & 63u);
+        hsh += dead_key((int)t);
+        delta += v.deadd[t];
+        dninf += v.dninf[t];
       }
     }
   }
-  __syncthreads();
-  const int n_redo = sc.nredo;
+  const int ndc = min(nd, kDrawDead);
+  auto dead = [&](uint32_t t) -> bool {
+    if (!((bloom >> (t & 63u)) & 1ull)) return false;
+    for (int j = 0; j < ndc; ++j)
+      if (s_dl[j * stride] == t) return true;
+    return false;
+  };
+  // stage 2: one categorical draw per detection row with candidates; rows
+  // that leave the reference option are only recorded here
+  for (int x = 0; x < nrca; ++x) {
+    const uint32_t ent = v.rca[x];
+    const uint32_t cc = ent >> 4, mask = ent & 15u;
+    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, cc), key);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (!((mask >> b) & 1u)) continue;
+      const int i = 4 * (int)cc + b;
+      const uint4 R = v.row[i];
+      const uint32_t k = word_of(r, b) >> 8;
+      const uint32_t off = R.x;
+      const int nc = (int)(R.y & 0x7FFFu);
+      int opt;
+      if (nd > 0 && (R.y & 0x8000u) && (v.rowbl[i] & bloom) && [&] {
+            for (int j = 0; j < nc; ++j)
+              if (dead(v.cslot[off + j])) return true;
+            return false;
+          }()) {
+        // some candidates are dead: draw among the living in proportion to
+        // their weights (clutter first)
+        const float w0 = md.kappa_zero ? 0.f : v.roww0[i];
+        float sum = w0;
+        for (int j = 0; j < nc; ++j)
+          if (!dead(v.cslot[off + j])) sum += v.cw[off + j];
+        if (!(sum > 0.f)) {
+          bad_row = true;
+          opt = 0;
+        } else {
+          const float xk = (float)k * 5.9604644775390625e-8f * sum;
+          float cum = w0;
+          int last = w0 > 0.f ? 0 : -1;
+          opt = -1;
+          if (w0 > 0.f && xk < cum) opt = 0;
+          for (int j = 0; j < nc; ++j) {
+            if (dead(v.cslot[off + j])) continue;
+            const float w = v.cw[off + j];
+            if (!(w > 0.f)) continue;
+            cum += w;
+            last = j + 1;
+            if (opt < 0 && xk < cum) opt = j + 1;
+          }
+          if (opt < 0) opt = last < 0 ? 0 : last;
+        }
+      } else if (k < R.z) {
+        opt = 0;
+      } else if (k < R.w) {
+        opt = 1;
+      } else {
+        int j = 1;
+        while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
+        opt = j + 1;
+      }
+      if (opt != (int)(R.y >> 16)) {
+        if (ndv < kDrawDev) s_dv[ndv * stride] = ((uint32_t)i << 16) | (uint32_t)opt;
+        ++ndv;
+      }
+    }
+  }
+  if (nd > kDrawDead || ndv > kDrawDev) return false;
+  // stage 3: each deviation moves one detection from its reference slot to
+  // its new slot; a slot met once changes by the staged single-deviation
+  // change (a dead reference slot is not met: its change is the death's)
+  unsigned long long tb0 = 0ull, tb1 = 0ull;   // slots met (bit slot mod 128)
+  bool twice = false;
+  auto meet = [&](uint32_t t) {
+    const unsigned long long bit = 1ull << (t & 63u);
+    unsigned long long& w = (t & 64u) ? tb1 : tb0;
+    twice |= (w & bit) != 0ull;
+    w |= bit;
+  };
+  for (int q = 0; q < ndv; ++q) {
+    const uint32_t e = s_dv[q * stride];
+    const int i = (int)(e >> 16), opt = (int)(e & 0xFFFFu);
+    const uint4 R = v.row[i];
+    const int ref = (int)(R.y >> 16);
+    uint32_t rs1 = ref > 0 ? (uint32_t)v.cslot[R.x + ref - 1] + 1u : 0u;
+    const uint32_t ns1 = opt > 0 ? (uint32_t)v.cslot[R.x + opt - 1] + 1u : 0u;
+    hsh += row_key(i, (int)ns1) - row_key(i, (int)rs1);
+    dclut += (opt == 0) - (ref == 0);
+    if (rs1 && dead(rs1 - 1u)) rs1 = 0u;
+    if (rs1) {
+      meet(rs1 - 1u);
+      delta += v.lossd[i];
+      dninf += v.lninf[i];
+    }
+    if (ns1) {
+      meet(ns1 - 1u);
+      delta += v.gaind[R.x + opt - 1];
+      dninf += v.gninf[R.x + opt - 1];
+    }
+    s_ds[q * stride] = (rs1 << 16) | ns1;
+  }
+  if (twice) {
+    // a slot met more than once (or two sharing a bit): its change is the
+    // exact rescoring with all deviations that move it, in place of the sum
+    // of their single changes
+    for (int w = 0; w < 2 * ndv; ++w) {
+      const uint32_t sw = s_ds[(w >> 1) * stride];
+      const uint32_t sp = (w & 1) ? (sw & 0xFFFFu) : (sw >> 16);
+      if (sp == 0u) continue;
+      int cnt = 0;
+      bool first = true;
+      for (int w2 = 0; w2 < 2 * ndv; ++w2) {
+        const uint32_t s2 = s_ds[(w2 >> 1) * stride];
+        if (((w2 & 1) ? (s2 & 0xFFFFu) : (s2 >> 16)) != sp) continue;
+        ++cnt;
+        if (w2 < w) first = false;
+      }
+      if (cnt < 2 || !first) continue;
+      int dcnt = 0, sninf = 0;
+      long long dse[DZ], dsq = 0, single = 0;
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) dse[d] = 0;
+      for (int w2 = w; w2 < 2 * ndv; ++w2) {
+        const uint32_t s2 = s_ds[(w2 >> 1) * stride];
+        if (((w2 & 1) ? (s2 & 0xFFFFu) : (s2 >> 16)) != sp) continue;
+        const uint32_t e2 = s_dv[(w2 >> 1) * stride];
+        const int i2 = (int)(e2 >> 16);
+        const uint4 R2 = v.row[i2];
+        uint32_t pos;
+        int sg;
+        if (w2 & 1) {
+          pos = R2.x + (e2 & 0xFFFFu) - 1u;
+          sg = 1;
+          single += v.gaind[pos];
+          sninf += v.gninf[pos];
+        } else {
+          pos = R2.x + (R2.y >> 16) - 1u;
+          sg = -1;
+          single += v.lossd[i2];
+          sninf += v.lninf[i2];
+        }
+        dcnt += sg;
+#pragma unroll
+        for (int d = 0; d < DZ; ++d) dse[d] += sg * fx_of(v.ce[d * Kp + pos]);
+        dsq += sg * fx_of(v.cq[pos]);
+      }
+      const int t = (int)sp - 1;
+      long long se[DZ];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + dse[d];
+      int ninf;
+      const long long term = slot_term<DZ>(md, v, T, t, v.mref[t] + dcnt, dcnt, se, v.sqref[t] + dsq, ninf);
+      delta += term - v.termref[t] - single;
+      dninf += ninf - (int)v.ninfref[t] - sninf;
+    }
+  }
+  const long long score = sc.ref_score + delta + (md.kappa_zero ? 0LL : (long long)dclut * md.fx_log_kappa);
+  const int ninf = sc.ninf_ref + dninf + (md.kappa_zero ? dclut : 0);
+  const bool valid = !bad_row && ninf == 0;
+  const size_t j = (size_t)h * md.h_up + n;
+  a.child_key[j] = valid ? score : kKeyInvalid;
+  a.child_hash[j] = hsh;
+  a.child_status[j] = valid ? 1 : 0;
+  a.child_alive[j] = (uint16_t)(T - nd);
+  return true;
+}
 
-  // ---- redone children: one warp per child ----
-  const int g = tid >> 5, lane = tid & 31;
-  unsigned char* gb = sm + L.grp + g * L.grp_bytes;
-  int* acc_cnt = at<int>(gb, L.g_cnt);
-  long long* acc_se = at<long long>(gb, L.g_se);
-  long long* acc_sq = at<long long>(gb, L.g_sq);
-  unsigned long long* acc_hw = at<unsigned long long>(gb, L.g_hw);
-  uint32_t* newval = at<uint32_t>(gb, L.g_newval);
-  uint32_t* tmask = at<uint32_t>(gb, L.g_tmask);
-  uint32_t* dmask = at<uint32_t>(gb, L.g_dmask);
-  uint32_t* dpre = at<uint32_t>(gb, L.g_dpre);
-  uint16_t* tlist = at<uint16_t>(gb, L.g_tlist);
-  int* ntp = at<int>(gb, L.g_nt);
-  for (int t = lane; g < a.n_fb_groups && t < T; t += 32) {
+int expand_draw_smem(int threads) { return threads * (2 * kDrawDead + 8 * kDrawDev); }
+
+// Persistent over jobs (parent, slice of blockDim.x draws); no block-level
+// synchronisation: every thread draws its own child from the parent's image.
+template <int DZ>
+__global__ void __launch_bounds__(256) draw_kernel(const ExpandArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int stride = blockDim.x;
+  uint32_t* s_dv = reinterpret_cast<uint32_t*>(sm) + threadIdx.x;
+  uint32_t* s_ds = reinterpret_cast<uint32_t*>(sm + 4 * kDrawDev * stride) + threadIdx.x;
+  uint16_t* s_dl = reinterpret_cast<uint16_t*>(sm + 8 * kDrawDev * stride) + threadIdx.x;
+  const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
+  const int H = a.fs->H, HU = a.md.h_up;
+  const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
+  const int nsl = (HU + (int)blockDim.x - 1) / (int)blockDim.x;
+  for (int job = blockIdx.x; job < H * nsl; job += gridDim.x) {
+    const int h = job / nsl;
+    const int n = (job % nsl) * (int)blockDim.x + (int)threadIdx.x;
+    const unsigned char* img = a.img + (size_t)h * a.img_stride;
+    const View v = make_view(img, L);
+    if (n >= HU || v.sc->bad) continue;
+    if (!thread_child<DZ>(a, v, v.sc->T, a.K_max, h, n, key, s_dl, s_dv, s_ds, stride))
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(h * HU + n);
+  }
+}
+
+// ====================== warp: one warp per child ======================
+// The work area's sums, masks and touched list are zero on entry and are
+// left zero on return.
+template <int DZ, bool MAT>
+__device__ void warp_child(const ExpandArgs& a, const View& v, const int T, const int Kp, const int M,
+                           const int h, const int n, const int s_out, const uint2 key, unsigned char* gb,
+                           const WLay& WL) {
+  const Model& md = a.md;
+  const Scal& sc = *v.sc;
+  const int HU = md.h_up;
+  const int lane = threadIdx.x & 31;
+  const int W = (T + 31) >> 5;
+  const int nrc = (M + 3) >> 2;
+  const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
+  const int ndpc = sc.ndpc;
+  int* acc_cnt = at<int>(gb, WL.cnt);
+  long long* acc_se = at<long long>(gb, WL.se);
+  long long* acc_sq = at<long long>(gb, WL.sq);
+  unsigned long long* acc_hw = at<unsigned long long>(gb, WL.hw);
+  uint32_t* newval = at<uint32_t>(gb, WL.newval);
+  uint32_t* tmask = at<uint32_t>(gb, WL.tmask);
+  uint32_t* dmask = at<uint32_t>(gb, WL.dmask);
+  uint32_t* dpre = at<uint32_t>(gb, WL.dpre);
+  uint16_t* tlist = at<uint16_t>(gb, WL.tlist);
+  int* ntp = at<int>(gb, WL.nt);
+
+  // phase 1: deaths
+  int my_dead = 0;
+  unsigned long long hsh = 0;
+  for (int x = lane; x < ndpc; x += 32) {
+    const uint32_t ent = v.dpc[x];
+    const uint32_t cc = ent >> 4, mask = ent & 15u;
+    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (!((mask >> b) & 1u)) continue;
+      const int t = 4 * (int)cc + b;
+      if ((word_of(r, b) >> 8) < v.dthr[t]) {
+        atomicOr(&dmask[t >> 5], 1u << (t & 31));
+        touch(tmask, tlist, ntp, t);
+        ++my_dead;
+        hsh += dead_key(t);
+      }
+    }
+  }
+  __syncwarp();
+  if (MAT) {
+    uint32_t carry = 0;
+    for (int base = 0; base < W; base += 32) {
+      const int w = base + lane;
+      const uint32_t val = w < W ? (uint32_t)__popc(dmask[w]) : 0u;
+      uint32_t x = val;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (w < W) dpre[w] = carry + x - val;
+      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+    __syncwarp();
+  }
+  // phase 2: one categorical draw per detection row
+  int my_dclut = 0;
+  bool bad_row = false;
+  for (int cc = lane; cc < nrc; cc += 32) {
+    const int i0 = 4 * cc;
+    const int i1 = min(i0 + 4, M);
+    bool any = false;
+    for (int i = i0; i < i1; ++i) any |= (v.row[i].y & 0x7FFFu) != 0u;
+    if (!any) {
+      if (MAT)
+        for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
+      continue;
+    }
+    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), key);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + b;
+      if (i >= i1) break;
+      const uint4 R = v.row[i];
+      const uint32_t off = R.x;
+      const int nc = (int)(R.y & 0x7FFFu);
+      if (nc == 0) {
+        if (MAT) a.out_theta[(size_t)s_out * M + i] = 0;
+        continue;
+      }
+      const uint32_t k = word_of(r, b) >> 8;
+      bool fast = true;
+      if (R.y & 0x8000u)
+        for (int j = 0; j < nc; ++j)
+          if (bit_of(dmask, v.cslot[off + j])) { fast = false; break; }
+      int opt;
+      if (fast) {
+        if (k < R.z) {
+          opt = 0;
+        } else {
+          int j = 0;
+          while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
+          opt = j + 1;
+        }
+      } else {
+        const float w0 = md.kappa_zero ? 0.f : v.roww0[i];
+        float sum = w0;
+        for (int j = 0; j < nc; ++j)
+          if (!bit_of(dmask, v.cslot[off + j])) sum += v.cw[off + j];
+        if (!(sum > 0.f)) {
+          bad_row = true;
+          opt = 0;
+        } else {
+          const float xk = (float)k * 5.9604644775390625e-8f * sum;
+          float cum = w0;
+          int last = w0 > 0.f ? 0 : -1;
+          opt = -1;
+          if (w0 > 0.f && xk < cum) opt = 0;
+          for (int j = 0; j < nc; ++j) {
+            if (bit_of(dmask, v.cslot[off + j])) continue;
+            const float w = v.cw[off + j];
+            if (!(w > 0.f)) continue;
+            cum += w;
+            last = j + 1;
+            if (opt < 0 && xk < cum) opt = j + 1;
+          }
+          if (opt < 0) opt = last < 0 ? 0 : last;
+        }
+      }
+      const int ref = (int)(R.y >> 16);
+      int ns = -1;
+      if (opt > 0) ns = v.cslot[off + opt - 1];
+      if (opt != ref) {
+        int rs = -1;
+        if (ref > 0) {
+          rs = v.cslot[off + ref - 1];
+          const uint32_t pos = off + ref - 1;
+          atomicSub(&acc_cnt[rs], 1);
+#pragma unroll
+          for (int d = 0; d < DZ; ++d)
+            atomicAdd((unsigned long long*)&acc_se[d * T + rs], (unsigned long long)(-fx_of(v.ce[d * Kp + pos])));
+          atomicAdd((unsigned long long*)&acc_sq[rs], (unsigned long long)(-fx_of(v.cq[pos])));
+          if (MAT) atomicAdd(&acc_hw[rs], (unsigned long long)(0ULL - wset_key(i)));
+          touch(tmask, tlist, ntp, rs);
+        } else {
+          --my_dclut;
+        }
+        if (opt > 0) {
+          const uint32_t pos = off + opt - 1;
+          atomicAdd(&acc_cnt[ns], 1);
+#pragma unroll
+          for (int d = 0; d < DZ; ++d)
+            atomicAdd((unsigned long long*)&acc_se[d * T + ns], (unsigned long long)fx_of(v.ce[d * Kp + pos]));
+          atomicAdd((unsigned long long*)&acc_sq[ns], (unsigned long long)fx_of(v.cq[pos]));
+          if (MAT) atomicAdd(&acc_hw[ns], wset_key(i));
+          touch(tmask, tlist, ntp, ns);
+        } else {
+          ++my_dclut;
+        }
+        hsh += row_key(i, opt > 0 ? ns + 1 : 0) - row_key(i, ref > 0 ? rs + 1 : 0);
+      }
+      if (MAT) {
+        uint16_t th = 0;
+        if (ns >= 0) {
+          const uint32_t below = dpre[ns >> 5] + __popc(dmask[ns >> 5] & ((1u << (ns & 31)) - 1u));
+          th = (uint16_t)(ns - (int)below + 1);
+        }
+        a.out_theta[(size_t)s_out * M + i] = th;
+      }
+    }
+  }
+  __syncwarp();
+  // phase 3: rescore touched slots
+  const int nt = *((volatile int*)ntp);
+  long long my_delta = 0;
+  int my_dninf = 0;
+  for (int x = lane; x < nt; x += 32) {
+    const int t = tlist[x];
+    int ninf;
+    long long term;
+    long long se[DZ];
+    int m = 0;
+    const bool is_dead = bit_of(dmask, t);
+    if (is_dead) {
+      term = dead_term(v.log1mp[t], ninf);
+    } else {
+      m = v.mref[t] + acc_cnt[t];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + acc_se[d * T + t];
+      term = slot_term<DZ>(md, v, T, t, m, acc_cnt[t], se, v.sqref[t] + acc_sq[t], ninf);
+    }
+    my_delta += term - v.termref[t];
+    my_dninf += ninf - (int)v.ninfref[t];
+    if (MAT && !is_dead)
+      newval[t] = m >= 1 ? upd_insert<DZ>(a, v.comp[t], v.hwref[t] + acc_hw[t], m, se) : v.comp[t];
     acc_cnt[t] = 0;
 #pragma unroll
     for (int d = 0; d < DZ; ++d) acc_se[d * T + t] = 0;
     acc_sq[t] = 0;
     if (MAT) acc_hw[t] = 0;
   }
-  for (int w = lane; g < a.n_fb_groups && w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
-  if (lane == 0 && g < a.n_fb_groups) *ntp = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_delta += __shfl_xor_sync(0xFFFFFFFFu, my_delta, o);
+    my_dninf += __shfl_xor_sync(0xFFFFFFFFu, my_dninf, o);
+    my_dclut += __shfl_xor_sync(0xFFFFFFFFu, my_dclut, o);
+    my_dead += __shfl_xor_sync(0xFFFFFFFFu, my_dead, o);
+    hsh += __shfl_xor_sync(0xFFFFFFFFu, hsh, o);
+  }
+  const bool any_bad = __any_sync(0xFFFFFFFFu, bad_row);
   __syncwarp();
+  if (MAT) {
+    const uint32_t base = a.out_ptr[s_out];
+    for (int t = lane; t < T; t += 32) {
+      if (bit_of(dmask, t)) continue;
+      const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
+      a.out_comp[base + (uint32_t)t - below] = bit_of(tmask, t) ? newval[t] : v.refnew[t];
+    }
+    __syncwarp();
+  }
+  for (int w = lane; w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
+  if (lane == 0) {
+    *ntp = 0;
+    if (!MAT) {
+      const long long score = sc.ref_score + my_delta + (md.kappa_zero ? 0LL : (long long)my_dclut * md.fx_log_kappa);
+      const int ninf = sc.ninf_ref + my_dninf + (md.kappa_zero ? my_dclut : 0);
+      const bool valid = !any_bad && ninf == 0;
+      const size_t j = (size_t)h * HU + n;
+      a.child_key[j] = valid ? score : kKeyInvalid;
+      a.child_hash[j] = hsh;
+      a.child_status[j] = valid ? 1 : 0;
+      a.child_alive[j] = (uint16_t)(T - my_dead);
+    }
+  }
+  __syncwarp();
+}
 
-  for (int rr = g; g < a.n_fb_groups && rr < n_redo; rr += a.n_fb_groups) {
-    const int it = s_redo[rr];
-    const int n = MAT ? (int)(a.surv_idx[sc.s_lo + it] - (long long)h * HU) : n_lo + it;
-    const int s_out = MAT ? sc.s_lo + it : 0;
-    // phase 1: deaths
-    int my_dead = 0;
-    unsigned long long hsh = 0;
-    for (int x = lane; x < ndpc; x += 32) {
-      const uint32_t ent = s_dpc[x];
-      const uint32_t cc = ent >> 4, mask = ent & 15u;
-      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        if (!((mask >> b) & 1u)) continue;
-        const int t = 4 * (int)cc + b;
-        if ((word_of(r, b) >> 8) < s_dthr[t]) {
-          atomicOr(&dmask[t >> 5], 1u << (t & 31));
-          touch(tmask, tlist, ntp, t);
-          ++my_dead;
-          hsh += dead_key(t);
-        }
-      }
-    }
-    __syncwarp();
-    if (MAT) {
-      uint32_t carry = 0;
-      for (int base = 0; base < W; base += 32) {
-        const int w = base + lane;
-        const uint32_t v = w < W ? (uint32_t)__popc(dmask[w]) : 0u;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-          if (lane >= o) x += y;
-        }
-        if (w < W) dpre[w] = carry + x - v;
-        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
-      }
-      __syncwarp();
-    }
-    // phase 2: one categorical draw per detection row
-    int my_dclut = 0;
-    bool bad_row = false;
-    for (int cc = lane; cc < nrc; cc += 32) {
-      const int i0 = 4 * cc;
-      const int i1 = min(i0 + 4, M);
-      if (s_rowoff[i1] == s_rowoff[i0]) {
-        if (MAT)
-          for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
-        continue;
-      }
-      const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), key);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = i0 + b;
-        if (i >= i1) break;
-        const uint32_t off = s_rowoff[i];
-        const int nc = (int)(s_rowoff[i + 1] - off);
-        if (nc == 0) {
-          if (MAT) a.out_theta[(size_t)s_out * M + i] = 0;
-          continue;
-        }
-        const uint32_t k = word_of(r, b) >> 8;
-        bool fast = true;
-        if (s_rowflag[i])
-          for (int j = 0; j < nc; ++j)
-            if (bit_of(dmask, s_cslot[off + j])) { fast = false; break; }
-        int opt;
-        if (fast) {
-          if (k < s_rowthr0[i]) {
-            opt = 0;
-          } else {
-            int j = 0;
-            while (j < nc - 1 && k >= s_cthr[off + j]) ++j;
-            opt = j + 1;
-          }
-        } else {
-          const float w0 = md.kappa_zero ? 0.f : s_roww0[i];
-          float sum = w0;
-          for (int j = 0; j < nc; ++j)
-            if (!bit_of(dmask, s_cslot[off + j])) sum += s_cw[off + j];
-          if (!(sum > 0.f)) {
-            bad_row = true;
-            opt = 0;
-          } else {
-            const float xk = (float)k * 5.9604644775390625e-8f * sum;
-            float cum = w0;
-            int last = w0 > 0.f ? 0 : -1;
-            opt = -1;
-            if (w0 > 0.f && xk < cum) opt = 0;
-            for (int j = 0; j < nc; ++j) {
-              if (bit_of(dmask, s_cslot[off + j])) continue;
-              const float w = s_cw[off + j];
-              if (!(w > 0.f)) continue;
-              cum += w;
-              last = j + 1;
-              if (opt < 0 && xk < cum) opt = j + 1;
-            }
-            if (opt < 0) opt = last < 0 ? 0 : last;
-          }
-        }
-        const int ref = s_rowref[i];
-        int ns = -1;
-        if (opt > 0) ns = s_cslot[off + opt - 1];
-        if (opt != ref) {
-          int rs = -1;
-          if (ref > 0) {
-            rs = s_cslot[off + ref - 1];
-            const uint32_t pos = off + ref - 1;
-            atomicSub(&acc_cnt[rs], 1);
-#pragma unroll
-            for (int d = 0; d < DZ; ++d)
-              atomicAdd((unsigned long long*)&acc_se[d * T + rs], (unsigned long long)(-fx_of(s_ce[d * Kp + pos])));
-            atomicAdd((unsigned long long*)&acc_sq[rs], (unsigned long long)(-fx_of(s_cq[pos])));
-            if (MAT) atomicAdd(&acc_hw[rs], (unsigned long long)(0ULL - wset_key(i)));
-            touch(tmask, tlist, ntp, rs);
-          } else {
-            --my_dclut;
-          }
-          if (opt > 0) {
-            const uint32_t pos = off + opt - 1;
-            atomicAdd(&acc_cnt[ns], 1);
-#pragma unroll
-            for (int d = 0; d < DZ; ++d)
-              atomicAdd((unsigned long long*)&acc_se[d * T + ns], (unsigned long long)fx_of(s_ce[d * Kp + pos]));
-            atomicAdd((unsigned long long*)&acc_sq[ns], (unsigned long long)fx_of(s_cq[pos]));
-            if (MAT) atomicAdd(&acc_hw[ns], wset_key(i));
-            touch(tmask, tlist, ntp, ns);
-          } else {
-            ++my_dclut;
-          }
-          hsh += row_key(i, opt > 0 ? ns + 1 : 0) - row_key(i, ref > 0 ? rs + 1 : 0);
-        }
-        if (MAT) {
-          uint16_t th = 0;
-          if (ns >= 0) {
-            const uint32_t below = dpre[ns >> 5] + __popc(dmask[ns >> 5] & ((1u << (ns & 31)) - 1u));
-            th = (uint16_t)(ns - (int)below + 1);
-          }
-          a.out_theta[(size_t)s_out * M + i] = th;
-        }
-      }
-    }
-    __syncwarp();
-    // phase 3: rescore touched slots
-    const int nt = *((volatile int*)ntp);
-    long long my_delta = 0;
-    int my_dninf = 0;
-    for (int x = lane; x < nt; x += 32) {
-      const int t = tlist[x];
-      int ninf;
-      long long term;
-      long long se[DZ];
-      int m = 0;
-      const bool dead = bit_of(dmask, t);
-      if (dead) {
-        term = dead_term(s_log1mp[t], ninf);
-      } else {
-        float HPH[DZ][DZ];
-        slot_HPH<DZ>(s_hph, T, t, HPH);
-        m = s_mref[t] + acc_cnt[t];
-#pragma unroll
-        for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + acc_se[d * T + t];
-        term = alive_term<DZ>(md, HPH, s_logp[t], m, se, s_sqref[t] + acc_sq[t], ninf);
-      }
-      my_delta += term - s_termref[t];
-      my_dninf += ninf - (int)s_ninfref[t];
-      if (MAT && !dead)
-        newval[t] = m >= 1 ? upd_insert<DZ>(a, s_comp[t], s_hwref[t] + acc_hw[t], m, se) : s_comp[t];
+// Persistent over a list of children, one warp each: the survivors (MAT),
+// every child of every parent (a.warp_all), or the draw kernel's overflow.
+template <int DZ, bool MAT>
+__global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
+  const WLay WL = make_wlay(DZ, MAT, a.T_max);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int HU = a.md.h_up, M = a.fs->M;
+  const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
+  // a frame already abandoned (e.g. entries beyond capacity) writes nothing
+  if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) return;
+  unsigned char* gb = sm + g * WL.total;
+  {
+    // the sums are indexed d * T + t with each parent's own T <= T_max
+    const int Wm = (a.T_max + 31) / 32 + 1;
+    int* acc_cnt = at<int>(gb, WL.cnt);
+    long long* acc_se = at<long long>(gb, WL.se);
+    long long* acc_sq = at<long long>(gb, WL.sq);
+    unsigned long long* acc_hw = at<unsigned long long>(gb, WL.hw);
+    for (int t = lane; t < a.T_max; t += 32) {
       acc_cnt[t] = 0;
 #pragma unroll
-      for (int d = 0; d < DZ; ++d) acc_se[d * T + t] = 0;
+      for (int d = 0; d < DZ; ++d) acc_se[d * a.T_max + t] = 0;
       acc_sq[t] = 0;
       if (MAT) acc_hw[t] = 0;
     }
+    for (int w = lane; w < Wm; w += 32) {
+      at<uint32_t>(gb, WL.tmask)[w] = 0;
+      at<uint32_t>(gb, WL.dmask)[w] = 0;
+    }
+    if (lane == 0) *at<int>(gb, WL.nt) = 0;
+    __syncwarp();
+  }
+  const long long count = MAT ? (long long)*a.n_surv
+                              : (a.warp_all ? (long long)a.fs->H * HU : (long long)*a.redo_count);
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + g; c < count; c += nw) {
+    const long long ci = MAT ? a.surv_idx[c] : (a.warp_all ? c : (long long)a.redo_list[c]);
+    const int h = (int)(ci / HU), n = (int)(ci % HU);
+    const View v = make_view(a.img + (size_t)h * a.img_stride, L);
+    if (v.sc->bad) continue;
+    warp_child<DZ, MAT>(a, v, v.sc->T, a.K_max, M, h, n, (int)c, key, gb, WL);
+  }
+}
+
+// The reference association's updated components of every retained parent,
+// requested once per parent (one warp per first survivor of a parent).
+template <int DZ>
+__global__ void __launch_bounds__(256) mat_prep_kernel(const ExpandArgs a) {
+  const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
+  const int lane = threadIdx.x & 31;
+  const int HU = a.md.h_up;
+  if (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs)) return;
+  const long long count = (long long)*a.n_surv;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < count; c += nw) {
+    const int h = (int)(a.surv_idx[c] / HU);
+    if (c > 0 && (int)(a.surv_idx[c - 1] / HU) == h) continue;
+    unsigned char* img = a.img + (size_t)h * a.img_stride;
+    const Scal& sc = *at<Scal>(img, L.scal);
+    if (sc.bad) continue;
+    const int T = sc.T;
+    const int* mref = at<int>(img, L.mref);
+    const uint32_t* comp = at<uint32_t>(img, L.comp);
+    const long long* seref = at<long long>(img, L.seref);
+    const unsigned long long* hwref = at<unsigned long long>(img, L.hwref);
+    uint32_t* refnew = at<uint32_t>(img, L.refnew);
+    for (int t = lane; t < T; t += 32) {
+      long long se[DZ];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      my_delta += __shfl_xor_sync(0xFFFFFFFFu, my_delta, o);
-      my_dninf += __shfl_xor_sync(0xFFFFFFFFu, my_dninf, o);
-      my_dclut += __shfl_xor_sync(0xFFFFFFFFu, my_dclut, o);
-      my_dead += __shfl_xor_sync(0xFFFFFFFFu, my_dead, o);
-      hsh += __shfl_xor_sync(0xFFFFFFFFu, hsh, o);
+      for (int d = 0; d < DZ; ++d) se[d] = seref[d * T + t];
+      refnew[t] = mref[t] >= 1 ? upd_insert<DZ>(a, comp[t], hwref[t], mref[t], se) : comp[t];
     }
-    const bool any_bad = __any_sync(0xFFFFFFFFu, bad_row);
-    __syncwarp();
-    if (MAT) {
-      const uint32_t base = a.out_ptr[s_out];
-      for (int t = lane; t < T; t += 32) {
-        if (bit_of(dmask, t)) continue;
-        const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
-        a.out_comp[base + (uint32_t)t - below] = bit_of(tmask, t) ? newval[t] : s_refnew[t];
-      }
-      __syncwarp();
-    }
-    for (int w = lane; w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
-    if (lane == 0) {
-      *ntp = 0;
-      if (!MAT) {
-        const long long score = ref_score + my_delta + (md.kappa_zero ? 0LL : (long long)my_dclut * md.fx_log_kappa);
-        const int ninf = ninf_ref + my_dninf + (md.kappa_zero ? my_dclut : 0);
-        const bool valid = !any_bad && ninf == 0;
-        const size_t j = (size_t)h * HU + n;
-        a.child_key[j] = valid ? score : kKeyInvalid;
-        a.child_hash[j] = hsh;
-        a.child_status[j] = valid ? 1 : 0;
-        a.child_alive[j] = (uint16_t)(T - my_dead);
-      }
-    }
-    __syncwarp();
   }
 }
 
@@ -973,41 +1235,49 @@ void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsign
   ++g_launches;
 }
 
-template <int DZ, bool MAT>
-static void launch_one(const ExpandArgs& a, int grid, cudaStream_t s) {
-  expand_kernel<DZ, MAT><<<grid, 32 * a.n_groups, a.smem_bytes, s>>>(a);
-  ++g_launches;
+// ---- host side ----
+using KernelFn = void (*)(const ExpandArgs);
+
+static KernelFn stage_fn(int dz, bool smem) {
+  if (dz == 2) return smem ? stage_kernel<2, true> : stage_kernel<2, false>;
+  return smem ? stage_kernel<3, true> : stage_kernel<3, false>;
 }
+static KernelFn draw_fn(int dz) { return dz == 2 ? draw_kernel<2> : draw_kernel<3>; }
+static KernelFn warp_fn(int dz, bool mat) {
+  if (dz == 2) return mat ? warp_kernel<2, true> : warp_kernel<2, false>;
+  return mat ? warp_kernel<3, true> : warp_kernel<3, false>;
+}
+static KernelFn prep_fn(int dz) { return dz == 2 ? mat_prep_kernel<2> : mat_prep_kernel<3>; }
 
 void expand_init(int smem_limit) {
-  cudaFuncSetAttribute(expand_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-  cudaFuncSetAttribute(expand_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-  cudaFuncSetAttribute(expand_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-  cudaFuncSetAttribute(expand_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  for (int dz = 2; dz <= 3; ++dz) {
+    cudaFuncSetAttribute(stage_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    cudaFuncSetAttribute(draw_fn(dz), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    cudaFuncSetAttribute(warp_fn(dz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    cudaFuncSetAttribute(warp_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  }
 }
 
-int expand_max_ctas(const ExpandArgs& a) {
+static KernelFn kernel_of(const ExpandArgs& a, ExpandKernel k) {
+  switch (k) {
+    case ExpandKernel::kStage: return stage_fn(a.md.dz, a.stage_smem != 0);
+    case ExpandKernel::kDraw: return draw_fn(a.md.dz);
+    case ExpandKernel::kWarp: return warp_fn(a.md.dz, a.materialize != 0);
+    default: return prep_fn(a.md.dz);
+  }
+}
+
+int expand_occupancy(const ExpandArgs& a, ExpandKernel k, int threads, int smem) {
   int per_sm = 0;
-  const int threads = 32 * a.n_groups;
-  cudaError_t e;
-  if (a.md.dz == 2)
-    e = a.materialize ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<2, true>, threads, a.smem_bytes)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<2, false>, threads, a.smem_bytes);
-  else
-    e = a.materialize ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<3, true>, threads, a.smem_bytes)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<3, false>, threads, a.smem_bytes);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(a, k), threads, smem);
   return e == cudaSuccess ? per_sm : 0;
 }
 
-void launch_expand(const ExpandArgs& a, int grid, cudaStream_t s) {
+void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int threads, int smem,
+                          cudaStream_t s) {
   if (grid <= 0) return;
-  if (a.md.dz == 2) {
-    if (a.materialize) launch_one<2, true>(a, grid, s);
-    else launch_one<2, false>(a, grid, s);
-  } else {
-    if (a.materialize) launch_one<3, true>(a, grid, s);
-    else launch_one<3, false>(a, grid, s);
-  }
+  kernel_of(a, k)<<<grid, threads, smem, s>>>(a);
+  ++g_launches;
 }
 
 }  // namespace glmb
