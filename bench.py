@@ -285,7 +285,8 @@ def main():
                 "d2h_bytes_per_step": sum(w["d2h"] for w in work_h) / len(work_h)},
         "gpu_launches": int(launches),
         "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
-                   "redone_frames": info1["n_redo"]},
+                   "redone_frames": info1["n_redo"],
+                   "capture_ms_total": round(info1["graph_capture_ms"], 3)},
         "expand_plan": {"smem_bytes": info1["expand_smem_bytes"],
                         "ctas_per_sm": info1["expand_ctas_per_sm"],
                         "threads": info1["expand_threads"],

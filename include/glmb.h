@@ -121,6 +121,7 @@ typedef struct {
   int32_t expand_plan_K;       /* gated pairs per hypothesis it was planned for */
   int32_t expand_plan_M;       /* detection rows it was planned for */
   int32_t expand_threads;      /* threads per CTA of the last expansion */
+  double graph_capture_ms;     /* host time spent capturing and instantiating frame graphs */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks

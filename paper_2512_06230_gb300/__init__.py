@@ -102,7 +102,7 @@ class GlmbInfo(C.Structure):
                 ("n_redo", C.c_int64), ("expand_smem_bytes", C.c_int32),
                 ("expand_ctas_per_sm", C.c_int32), ("expand_plan_T", C.c_int32),
                 ("expand_plan_K", C.c_int32), ("expand_plan_M", C.c_int32),
-                ("expand_threads", C.c_int32)]
+                ("expand_threads", C.c_int32), ("graph_capture_ms", C.c_double)]
 
 
 # NumPy views of the ABI records (same layout as the C structs)

@@ -2,6 +2,7 @@
 // memory (allocated once at create), per-frame orchestration of the kernels
 // on one stream, state import/export and inspection.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,6 +75,7 @@ struct glmb_handle {
   float* h_Z = nullptr;
   PairTable pt{};
   uint32_t* scan_tmp32 = nullptr;
+  long long scan_cap32 = 0;   // capacity scan_tmp32 was sized for
   long long* child_key = nullptr;
   unsigned long long* child_hash = nullptr;
   int8_t* child_status = nullptr;
@@ -129,6 +131,7 @@ struct glmb_handle {
   std::vector<CachedGraph> graphs;
   bool capturing = false;
   long long n_captures = 0, n_graph_launches = 0;
+  double capture_ms = 0.0;   // host time spent capturing and instantiating graphs
   // stats
   long long n_pairs = 0, n_unique = 0;
   int n_upd = 0, n_fp64 = 0;
@@ -471,6 +474,15 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
             halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_ru, h->cap_meas) &&
             dalloc(h, &h->d_fs, 1) && halloc(h, &h->h_fs, 2);
+  if (ok) {
+    h->pw.err = h->d_scal + S_ERR;
+    h->pw.flags_tmp_cap = h->cap_children;
+    h->scan_cap32 = scan_n;
+    // scan work areas start zeroed (each scan leaves its own zeroed)
+    ok = cudaMemset(h->scan_tmp32, 0, sizeof(uint32_t) * scan_tmp_elems(scan_n)) == cudaSuccess &&
+         cudaMemset(h->pw.flags_tmp, 0, sizeof(unsigned long long) * scan_tmp_elems(h->cap_children)) ==
+             cudaSuccess;
+  }
   if (!ok) {
     free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -593,7 +605,7 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
   launch_check_finite(h->d_Z, h->d_fs, dz, h->d_scal + S_ERR, h->stream);
   const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
   launch_table_count(h->md, B, h->pt, h->d_fs, h->d_Z, gt, h->stream);
-  scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32,
+  scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR,
            h->stream);
   launch_table_write(h->md, B, h->pt, h->d_fs, h->d_Z, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
                      h->stream);
@@ -686,7 +698,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
   launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
   launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status,
-               p.fixed ? 2 * n_sm : std::max(1, std::min(h->H, 2 * n_sm)), s);
+               p.fixed ? 8 * n_sm : std::max(1, std::min(h->H, 8 * n_sm)), s);
   prof_end(h, kStageExpand);
   return GLMB_OK;
 }
@@ -743,7 +755,7 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));
   launch_mark_old(O.comp, h->pw.counts + 1, h->cap_entries, h->d_scal + S_ERR, h->gc_flag, s);
   scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
-           h->scan_tmp32, s);
+           h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR, s);
   const int ggc = p.fixed ? 8 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
   launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP,
                         h->upd_src, h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD,
@@ -937,11 +949,11 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->retained_valid = false;
   h->plan = p;
   if (p.fixed) {
-    // Replay the captured graph with the smallest expansion footprint whose
+    // Replay the captured graph with the smallest per-parent image whose
     // plan covers this frame (same buffer parity and profiling mask; slots,
-    // pairs and detections at least this frame's).  The footprint sets how
-    // many CTAs share an SM, so a covering graph much larger than this
-    // frame needs is replaced by a tighter capture.
+    // pairs and detections at least this frame's).  A cover more than three
+    // times larger than this frame needs is replaced by a tighter capture;
+    // captures take headroom so that a growing scene needs few of them.
     const int need_smem = plan_smem(h, p);
     int best = -1;
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
@@ -951,10 +963,11 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
         continue;
       if (best < 0 || g.smem < h->graphs[best].smem) best = gi;
     }
-    if (best >= 0 && (long long)h->graphs[best].smem * 4 > (long long)need_smem * 5) best = -1;
+    if (best >= 0 && (long long)h->graphs[best].smem > 3LL * need_smem) best = -1;
     if (best < 0) {
       Plan q = p;
-      if (!make_plan(h, true, p.T + p.T / 8, p.K + p.K / 8, p.M + p.M / 8, q) || q.thread != p.thread ||
+      if (!make_plan(h, true, round_up(p.T + p.T / 2, 32), round_up(p.K + p.K / 2, 128), round_up(p.M + p.M / 4, 64), q) ||
+          q.thread != p.thread ||
           (p.smem && !q.smem))
         q = p;
       if ((st = ensure_img(h, q)) != GLMB_OK) {
@@ -963,6 +976,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       }
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
+      const auto t_cap = std::chrono::steady_clock::now();
       CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
       enqueue_predict(h, q);
@@ -994,6 +1008,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       }
       h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels, plan_smem(h, q), 0});
       ++h->n_captures;
+      h->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_cap).count();
       best = (int)h->graphs.size() - 1;
     }
     h->graphs[best].last_use = h->frame;
@@ -1061,6 +1076,7 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
   info->expand_plan_K = h->exp_plan[1];
   info->expand_plan_M = h->exp_plan[2];
   info->expand_threads = h->exp_plan[3];
+  info->graph_capture_ms = h->capture_ms;
   return GLMB_OK;
 }
 

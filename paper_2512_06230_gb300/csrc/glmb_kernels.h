@@ -26,15 +26,19 @@ void launch_check_finite(const float* Z, const FrameDev* fs, int dz, unsigned* e
 void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
                          unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s);
 
-// exclusive scans of (*n_dev * mult) elements, at most cap; tmp must hold
-// scan_tmp_elems(cap) elements; total (nullable) receives the sum, and with
-// total_at_end the sum is also written to out[n]
+// exclusive scans of (*n_dev * mult) elements, at most cap, in one launch;
+// tmp holds scan_tmp_elems(tmp_cap) elements (tmp_cap >= cap; one work area
+// may serve scans of different capacities), zero before the first scan (each
+// scan leaves it zero); total (nullable) receives the sum, and with
+// total_at_end the sum is also written to out[n]; a look-back that waits too
+// long sets kErrNumeric in *err
 long long scan_tmp_elems(long long cap);
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
-              uint32_t* total, bool total_at_end, uint32_t* tmp, cudaStream_t s);
+              uint32_t* total, bool total_at_end, uint32_t* tmp, long long tmp_cap, unsigned* err,
+              cudaStream_t s);
 void scan_u64(const unsigned long long* in, unsigned long long* out, const int* n_dev, int mult,
               long long cap, unsigned long long* total, bool total_at_end,
-              unsigned long long* tmp, cudaStream_t s);
+              unsigned long long* tmp, long long tmp_cap, unsigned* err, cudaStream_t s);
 
 // ---- expansion / materialisation (kernels_expand.cu) ----
 struct ExpandArgs {
@@ -107,8 +111,10 @@ struct PruneWork {
   long long* sel;               // [4]: prefix, need, boundary key, flags
   unsigned long long* flags;    // [n_children] packed (gt, eq) prefix counts
   unsigned long long* flags_tmp;
+  long long flags_tmp_cap;      // capacity flags_tmp was sized for
   long long* surv_idx;          // [cap_h]
   unsigned* counts;             // [8]: n_surv, n_entries, n_unique, max alive, [4..5] scan total
+  unsigned* err;                // device error flags
 };
 // the children are the fs->H * h_up entries of keys
 void launch_lse(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,

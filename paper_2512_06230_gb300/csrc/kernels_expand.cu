@@ -1199,27 +1199,58 @@ __global__ void __launch_bounds__(256) mat_prep_kernel(const ExpandArgs a) {
 
 // Unique children of each parent (Section 3: only unique hypotheses are
 // retained): a valid child whose key equals a lower valid draw's is a
-// duplicate; its weight is dropped.  One block per parent.
+// duplicate; its weight is dropped.  One block per parent: every valid child
+// enters an open-addressing table in shared memory (key -> lowest draw).
+__device__ __forceinline__ int dedup_table_size(int HU) {
+  int ts = 64;
+  while (ts < 2 * HU) ts <<= 1;
+  return ts;
+}
+
 __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long* child_key,
                              const unsigned long long* __restrict__ child_hash, int8_t* child_status) {
-  extern __shared__ unsigned long long s_h[];
-  uint8_t* s_v = reinterpret_cast<uint8_t*>(s_h + HU);
+  extern __shared__ unsigned long long s_k[];   // [ts] keys, 0 = empty
+  const int ts = dedup_table_size(HU);
+  uint32_t* s_n = reinterpret_cast<uint32_t*>(s_k + ts);   // [ts] lowest draw
+  __shared__ uint32_t s_zero;                                // lowest draw whose key is 0
   const int H = fs->H;
   for (int h = blockIdx.x; h < H; h += gridDim.x) {
     const size_t base = (size_t)h * HU;
     __syncthreads();
+    for (int i = threadIdx.x; i < ts; i += blockDim.x) {
+      s_k[i] = 0ull;
+      s_n[i] = 0xFFFFFFFFu;
+    }
+    if (threadIdx.x == 0) s_zero = 0xFFFFFFFFu;
+    __syncthreads();
     for (int n = threadIdx.x; n < HU; n += blockDim.x) {
-      s_h[n] = child_hash[base + n];
-      s_v[n] = child_status[base + n] != 0;
+      if (child_status[base + n] == 0) continue;
+      const unsigned long long hv = child_hash[base + n];
+      if (hv == 0ull) {
+        atomicMin(&s_zero, (uint32_t)n);
+        continue;
+      }
+      uint32_t slot = (uint32_t)(hv ^ (hv >> 32)) & (uint32_t)(ts - 1);
+      for (int probe = 0; probe < ts; ++probe) {   // ts > entries: a slot is found
+        const unsigned long long prev = atomicCAS(&s_k[slot], 0ull, hv);
+        if (prev == 0ull || prev == hv) {
+          atomicMin(&s_n[slot], (uint32_t)n);
+          break;
+        }
+        slot = (slot + 1u) & (uint32_t)(ts - 1);
+      }
     }
     __syncthreads();
     for (int n = threadIdx.x; n < HU; n += blockDim.x) {
-      if (!s_v[n]) continue;
-      const unsigned long long hv = s_h[n];
-      bool dup = false;
-      for (int n2 = 0; n2 < n; ++n2)
-        if (s_v[n2] && s_h[n2] == hv) { dup = true; break; }
-      if (dup) {
+      if (child_status[base + n] == 0) continue;
+      const unsigned long long hv = child_hash[base + n];
+      uint32_t low = s_zero;
+      if (hv != 0ull) {
+        uint32_t slot = (uint32_t)(hv ^ (hv >> 32)) & (uint32_t)(ts - 1);
+        for (int probe = 0; probe < ts && s_k[slot] != hv; ++probe) slot = (slot + 1u) & (uint32_t)(ts - 1);
+        low = s_n[slot];
+      }
+      if (low < (uint32_t)n) {
         child_status[base + n] = 2;
         child_key[base + n] = kKeyInvalid;
       }
@@ -1229,7 +1260,9 @@ __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long*
 
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
                   int8_t* child_status, int grid, cudaStream_t s) {
-  const int smem = HU * 9 + 16;
+  int ts = 64;
+  while (ts < 2 * HU) ts <<= 1;
+  const int smem = ts * 12;
   if (smem > 48 * 1024) cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   dedup_kernel<<<grid, 128, smem, s>>>(fs, HU, child_key, child_hash, child_status);
   ++g_launches;

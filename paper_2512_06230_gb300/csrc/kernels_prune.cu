@@ -27,43 +27,49 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // sum of exp); each pass's last block combines the per-block partials in
 // block order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-// (max, sum of exp(x - max)) pairs in fixed-point keys; combine two pairs
+// (max, sum of exp(x - max)) pairs in fixed-point keys
 struct Lse {
-  long long m;
+  long long m;   // kKeyInvalid (the smallest 64-bit integer) when empty
   double s;
 };
-__device__ __forceinline__ Lse lse_combine(Lse a, Lse b) {
-  if (a.m == kKeyInvalid) return b;
-  if (b.m == kKeyInvalid) return a;
-  if (a.m >= b.m) return {a.m, a.s + b.s * exp((double)(b.m - a.m) * kFxInv)};
-  return {b.m, b.s + a.s * exp((double)(a.m - b.m) * kFxInv)};
-}
-__device__ __forceinline__ Lse warp_lse(Lse v) {
+__device__ __forceinline__ long long warp_max_key(long long v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    Lse u{__shfl_xor_sync(0xFFFFFFFFu, v.m, o), __shfl_xor_sync(0xFFFFFFFFu, v.s, o)};
-    v = lse_combine(v, u);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
   return v;
 }
-// block-wide combine; result valid in thread 0
+// Block-wide pair from per-thread pairs: the block maximum first (integer),
+// then each thread's sum rescaled to it with one FP32 exponential of the key
+// difference and summed in FP64; result valid in every thread.
 __device__ Lse block_lse(Lse v) {
   __shared__ long long sm[32];
   __shared__ double ss[32];
-  v = warp_lse(v);
+  __shared__ long long s_max;
+  __shared__ double s_sum;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  long long mm = warp_max_key(v.m);
   __syncthreads();
-  if (lane == 0) { sm[w] = v.m; ss[w] = v.s; }
+  if (lane == 0) sm[w] = mm;
   __syncthreads();
   if (w == 0) {
-    Lse u = lane < nw ? Lse{sm[lane], ss[lane]} : Lse{kKeyInvalid, 0.0};
-    v = warp_lse(u);
+    mm = warp_max_key(lane < nw ? sm[lane] : kKeyInvalid);
+    if (lane == 0) s_max = mm;
   }
-  return v;
+  __syncthreads();
+  const long long M = s_max;
+  double r = (v.m == kKeyInvalid || !(v.s > 0.0)) ? 0.0 : v.s * (double)expf(fx_to_f(v.m - M));
+  r = warp_sum_d(r);
+  if (lane == 0) ss[w] = r;
+  __syncthreads();
+  if (w == 0) {
+    r = warp_sum_d(lane < nw ? ss[lane] : 0.0);
+    if (lane == 0) s_sum = r;
+  }
+  __syncthreads();
+  return Lse{M, s_sum};
 }
 
-// Global log-sum-exp over the unique children (FP64) in one pass: each
-// thread keeps a running (max, sum of shifted exponentials); blocks write
+// Global log-sum-exp over the unique children in one pass: each thread
+// keeps a running (max, sum of shifted exponentials); blocks write
 // partials; the last block combines them in a fixed tree, so the result does
 // not depend on scheduling.  Also counts the unique children and sets the
 // fixed-point threshold log(tau) + LSE.
@@ -71,15 +77,33 @@ __global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* _
                            int h_up, PruneWork w, double log_tau, int h_max) {
   __shared__ bool last;
   const long long n = (long long)fs->H * h_up;
-  Lse v{kKeyInvalid, 0.0};
+  // per thread: running maximum and a compensated FP32 sum of exp(key - max)
+  // (FP32 exponentials of differences; FP64 only from the block partials on)
+  long long m = kKeyInvalid;
+  float sum = 0.f, comp = 0.f;
   unsigned valid = 0;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
     const long long k = keys[j];
     if (k == kKeyInvalid) continue;
     ++valid;
-    v = lse_combine(v, Lse{k, 1.0});
+    float term = 1.f;
+    if (m == kKeyInvalid) {
+      m = k;
+    } else if (k > m) {
+      const float sc = expf(fx_to_f(m - k));
+      sum *= sc;
+      comp *= sc;
+      m = k;
+    } else {
+      term = expf(fx_to_f(k - m));
+    }
+    const float y = term - comp;   // Kahan summation
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
   }
+  Lse v{m, (double)sum - (double)comp};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) valid += __shfl_xor_sync(0xFFFFFFFFu, valid, o);
   if ((threadIdx.x & 31) == 0 && valid) atomicAdd(&w.counts[2], valid);
@@ -93,9 +117,20 @@ __global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* _
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // block partials, each thread folding its share onto its own maximum
   Lse u{kKeyInvalid, 0.0};
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-    u = lse_combine(u, Lse{((volatile long long*)w.blk_max)[b], ((volatile double*)w.blk_sum)[b]});
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const long long bm = ((volatile long long*)w.blk_max)[b];
+    const double bs = ((volatile double*)w.blk_sum)[b];
+    if (bm == kKeyInvalid || !(bs > 0.0)) continue;
+    if (u.m == kKeyInvalid) {
+      u = Lse{bm, bs};
+    } else if (bm > u.m) {
+      u = Lse{bm, bs + u.s * (double)expf(fx_to_f(u.m - bm))};
+    } else {
+      u.s += bs * (double)expf(fx_to_f(bm - u.m));
+    }
+  }
   u = block_lse(u);
   if (threadIdx.x == 0) {
     w.blk_done[0] = 0;
@@ -260,7 +295,7 @@ void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long lo
                     int h_max, int nblk, cudaStream_t s) {
   keep_flags_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w); ++g_launches;
   scan_u64(w.flags, w.flags, &fs->H, h_up, cap, (unsigned long long*)(w.counts + 4), false,
-           w.flags_tmp, s);
+           w.flags_tmp, w.flags_tmp_cap, w.err, s);
   keep_write_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w, h_max); ++g_launches;
 }
 
@@ -272,9 +307,8 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
                                 const uint16_t* __restrict__ child_alive, HypTable parents,
                                 int h_up, HypTable out, int h_max, unsigned* err,
                                 long long cap_entries) {
-  __shared__ double red[32];
   __shared__ long long s_n;
-  __shared__ double s_m, s_lse;
+  __shared__ double s_lse;
   __shared__ uint32_t carry;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid == 0) {
@@ -289,29 +323,18 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
   __syncthreads();
   const long long n = s_n;
   const double lse_all = w.lse[0];
-  // max
-  double m = -INFINITY;
-  for (long long s = tid; s < n; s += nthr) m = fmax(m, (double)keys[w.surv_idx[s]] * kFxInv - lse_all);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-  if ((tid & 31) == 0) red[tid >> 5] = m;
-  __syncthreads();
-  if (tid == 0) {
-    double g = -INFINITY;
-    for (int k = 0; k < (nthr + 31) / 32; ++k) g = fmax(g, red[k]);
-    s_m = g;
+  // log-sum-exp of the retained keys: integer maximum, FP32 exponentials of
+  // the key differences, FP64 sums
+  Lse v{kKeyInvalid, 0.0};
+  for (long long s = tid; s < n; s += nthr) {
+    const long long k = keys[w.surv_idx[s]];
+    if (v.m == kKeyInvalid) v = Lse{k, 1.0};
+    else if (k > v.m) v = Lse{k, 1.0 + v.s * (double)expf(fx_to_f(v.m - k))};
+    else v.s += (double)expf(fx_to_f(k - v.m));
   }
-  __syncthreads();
-  double sum = 0.0;
-  for (long long s = tid; s < n; s += nthr) sum += exp((double)keys[w.surv_idx[s]] * kFxInv - lse_all - s_m);
-  sum = warp_sum_d(sum);
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = sum;
-  __syncthreads();
+  v = block_lse(v);
   if (tid == 0) {
-    double S = 0.0;
-    for (int k = 0; k < (nthr + 31) / 32; ++k) S += red[k];
-    s_lse = s_m + log(S);
+    s_lse = (double)v.m * kFxInv - lse_all + log(v.s);
     w.lse[1] = s_lse;
   }
   __syncthreads();
@@ -619,44 +642,55 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
 // of that cardinality (ties to the lower index), label existence, and the
 // clutter probability of each detection.
 // ---------------------------------------------------------------------------
+// Hypothesis weights enter the estimate sums as unsigned fixed point with 40
+// fractional bits (FP32 exponential of the normalised log-weight), so the
+// atomic sums are exact and independent of their order.
+constexpr double kWfxInv = 9.094947017729282e-13;   // 2^-40
+__device__ __forceinline__ unsigned long long w_fx(double logw) {
+  return __float2ull_rn(expf((float)logw) * 1099511627776.0f);
+}
+
 // Cardinality distribution, MAP cardinality (ties to the smaller n) and the
 // heaviest hypothesis of that cardinality (ties to the lower index); one
 // block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
 __global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* nb) {
-  __shared__ double bw[32];
+  extern __shared__ unsigned long long s_pmf[];   // [pcap]
+  __shared__ unsigned long long bw[32];
   __shared__ int bi[32];
+  __shared__ double lw_w[32];
+  __shared__ int li_w[32];
   __shared__ int s_nhat;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5;
   const int nw = (nthr + 31) >> 5;
-  for (int n = tid; n < pcap; n += nthr) pmf[n] = 0.0;
+  for (int n = tid; n < pcap; n += nthr) s_pmf[n] = 0ull;
   __syncthreads();
   for (int h = tid; h < H; h += nthr) {
     const int n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
-    if (n < pcap) atomicAdd(&pmf[n], exp(hp.logw[h]));
+    if (n < pcap) atomicAdd(&s_pmf[n], w_fx(hp.logw[h]));
   }
-  __threadfence();
   __syncthreads();
-  // argmax over bins
-  double v = -1.0;
+  // argmax over bins (exact integer sums)
+  unsigned long long v = 0ull;
   int vi = 0x7FFFFFFF;
   for (int n = tid; n < pcap; n += nthr) {
-    const double p = ((volatile double*)pmf)[n];
-    if (p > v) { v = p; vi = n; }
+    const unsigned long long p = s_pmf[n];
+    pmf[n] = (double)p * kWfxInv;
+    if (vi == 0x7FFFFFFF || p > v) { v = p; vi = n; }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const unsigned long long v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
     const int i2 = __shfl_xor_sync(0xFFFFFFFFu, vi, o);
-    if (v2 > v || (v2 == v && i2 < vi)) { v = v2; vi = i2; }
+    if (i2 != 0x7FFFFFFF && (vi == 0x7FFFFFFF || v2 > v || (v2 == v && i2 < vi))) { v = v2; vi = i2; }
   }
   if (lane == 0) { bw[wp] = v; bi[wp] = vi; }
   __syncthreads();
   if (tid == 0) {
-    double b = -1.0;
-    int k = 0;
+    unsigned long long b = 0ull;
+    int k = 0x7FFFFFFF;
     for (int w = 0; w < nw; ++w)
-      if (bw[w] > b || (bw[w] == b && bi[w] < k)) { b = bw[w]; k = bi[w]; }
-    s_nhat = k;
+      if (bi[w] != 0x7FFFFFFF && (k == 0x7FFFFFFF || bw[w] > b || (bw[w] == b && bi[w] < k))) { b = bw[w]; k = bi[w]; }
+    s_nhat = k == 0x7FFFFFFF ? 0 : k;
   }
   __syncthreads();
   const int nhat = s_nhat;
@@ -673,51 +707,56 @@ __global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* 
     const int i2 = __shfl_xor_sync(0xFFFFFFFFu, li, o);
     if (i2 >= 0 && (li < 0 || w2 > lw || (w2 == lw && i2 < li))) { lw = w2; li = i2; }
   }
-  __syncthreads();
-  if (lane == 0) { bw[wp] = lw; bi[wp] = li; }
+  if (lane == 0) { lw_w[wp] = lw; li_w[wp] = li; }
   __syncthreads();
   if (tid == 0) {
     double b = -INFINITY;
     int k = -1;
     for (int w = 0; w < nw; ++w)
-      if (bi[w] >= 0 && (k < 0 || bw[w] > b || (bw[w] == b && bi[w] < k))) { b = bw[w]; k = bi[w]; }
+      if (li_w[w] >= 0 && (k < 0 || lw_w[w] > b || (lw_w[w] == b && li_w[w] < k))) { b = lw_w[w]; k = li_w[w]; }
     nb[0] = nhat;
     nb[1] = k;
   }
 }
 
 // r[j] = total weight of hypotheses holding the label of MAP track j (one
-// warp per hypothesis, binary search in the MAP track list, which is in
-// label order); the last block then writes the MAP tracks as glmb_track
+// warp per hypothesis; the MAP track list, in label order, is binary searched
+// in shared memory and the weights summed per block there, then once per
+// block into r_fx); the last block writes the MAP tracks as glmb_track
 // records (mean hi + lo in FP64, full covariance).
 __global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const int* __restrict__ nb,
-                                 double* r, glmb_track* out, int cap, unsigned* done) {
+                                 unsigned long long* r_fx, glmb_track* out, int cap, unsigned* done) {
+  extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
+  unsigned long long* s_r = s_key + cap;
   __shared__ bool last;
   const int best = nb[1];
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int wpb = blockDim.x >> 5;
   const uint32_t b0 = best >= 0 ? hp.ptr[best] : 0u;
-  const int nmap = best >= 0 ? (int)(hp.ptr[best + 1] - b0) : 0;
-  for (int h = gw; h < H && nmap > 0; h += warps) {
+  const int nmap = best >= 0 ? min((int)(hp.ptr[best + 1] - b0), cap) : 0;
+  for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
+    const uint32_t cm = hp.comp[b0 + j];
+    s_key[j] = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
+    s_r[j] = 0ull;
+  }
+  __syncthreads();
+  for (int h = blockIdx.x * wpb + (threadIdx.x >> 5); h < H && nmap > 0; h += gridDim.x * wpb) {
     const uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
-    const double wgt = exp(hp.logw[h]);
+    const unsigned long long wgt = w_fx(hp.logw[h]);
     for (uint32_t e = lo + lane; e < hi; e += 32) {
       const uint32_t c = hp.comp[e];
       const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
       int l = 0, u = nmap;
       while (l < u) {
         const int mid = (l + u) >> 1;
-        const uint32_t cm = hp.comp[b0 + mid];
-        const unsigned long long km = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
-        if (km < key) l = mid + 1; else u = mid;
+        if (s_key[mid] < key) l = mid + 1; else u = mid;
       }
-      if (l < nmap) {
-        const uint32_t cm = hp.comp[b0 + l];
-        if (ct.lk[cm] == ct.lk[c] && ct.lb[cm] == ct.lb[c]) atomicAdd(&r[l], wgt);
-      }
+      if (l < nmap && s_key[l] == key) atomicAdd(&s_r[l], wgt);
     }
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nmap; j += blockDim.x)
+    if (s_r[j]) atomicAdd(&r_fx[j], s_r[j]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -725,12 +764,12 @@ __global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const
   if (!last) return;
   __threadfence();
   const size_t cc = ct.cap;
-  for (int j = threadIdx.x; j < min(nmap, cap); j += blockDim.x) {
+  for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
     const uint32_t c = hp.comp[b0 + j];
     glmb_track& t = out[j];
     t.label_k = ct.lk[c];
     t.label_b = ct.lb[c];
-    t.r = ((volatile double*)r)[j];
+    t.r = (double)((volatile unsigned long long*)r_fx)[j] * kWfxInv;
     for (int a = 0; a < 6; ++a)
       t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
     for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
@@ -746,19 +785,24 @@ __global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const
 
 void launch_estimates(const HypTable& hp, int H, const CompTable& ct, int dx, double* pmf, int pcap,
                       int* nb, double* r, void* tracks, unsigned* done, int n_sm, cudaStream_t s) {
-  est_card_kernel<<<1, 1024, 0, s>>>(hp, H, pmf, pcap, nb); ++g_launches;
+  if (pcap * 16 > 48 * 1024) {
+    cudaFuncSetAttribute(est_card_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
+    cudaFuncSetAttribute(est_exist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
+  }
+  est_card_kernel<<<1, 1024, (size_t)pcap * 8, s>>>(hp, H, pmf, pcap, nb); ++g_launches;
   const int blocks = std::max(1, std::min((H + 7) / 8, 2 * n_sm));
-  est_exist_kernel<<<blocks, 256, 0, s>>>(hp, H, ct, dx, nb, r, (glmb_track*)tracks, pcap, done);
+  est_exist_kernel<<<blocks, 256, (size_t)pcap * 16, s>>>(hp, H, ct, dx, nb, reinterpret_cast<unsigned long long*>(r),
+                                                         (glmb_track*)tracks, pcap, done);
   ++g_launches;
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  double s = 0.0;
+  unsigned long long s = 0ull;
   for (int h = 0; h < H; ++h)
-    if (hp.theta[(size_t)h * M + i] == 0) s += exp(hp.logw[h]);
-  r_u[i] = s;
+    if (hp.theta[(size_t)h * M + i] == 0) s += w_fx(hp.logw[h]);
+  r_u[i] = (double)s * kWfxInv;
 }
 
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s) {

@@ -412,64 +412,99 @@ __device__ __forceinline__ long long scan_len(const int* n_dev, int mult) {
   return (long long)(*n_dev) * mult;
 }
 
-template <typename T>
-__global__ void scan_tile_sums(const T* __restrict__ in, const int* n_dev, int mult, T* tile_sums) {
-  const long long n = scan_len(n_dev, mult);
-  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-  T s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < n) s += in[base + k];
-  T total;
-  block_exclusive_scan<T>(s, total);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
-}
+// Single-pass scan with decoupled look-back (Merrill and Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016): blocks take tiles in
+// the order they start (an atomic counter), publish their tile's sum, and
+// add up their predecessors' published sums back to the nearest published
+// inclusive prefix.  A tile waits only on tiles taken before it, by blocks
+// already running.  Work area (elements of T), laid out for the largest scan
+// it serves (nw tiles): counters [2], status [nw], aggregates [nw], inclusive
+// prefixes [nw]; counters and status are zero before the first use and left
+// zero by the last block to finish.
+constexpr unsigned kStAgg = 1u, kStInc = 2u;
+constexpr long long kScanSpin = 1LL << 22;   // look-back wait limit (iterations)
 
-// scans the tile sums in place (one block); writes the grand total to
-// *total and, when asked, to out[n]
 template <typename T>
-__global__ void scan_single(T* v, int n_tiles, T* total, T* out, const int* n_dev, int mult,
-                            int total_at_end) {
-  __shared__ T carry;
-  if (threadIdx.x == 0) carry = 0;
+__global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T* total, int total_at_end,
+                             T* work, int nw, unsigned* err) {
+  __shared__ int s_tile;
+  __shared__ T s_excl;
+  T* ctr = work;
+  T* st = work + 2;
+  T* agg = work + 2 + nw;
+  T* inc = work + 2 + 2 * nw;
+  const int nt = (int)gridDim.x;
+  const long long n = scan_len(n_dev, mult);
+  const int ntiles = (int)min((long long)nt, (n + kScanTile - 1) / kScanTile);
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], T(1));
   __syncthreads();
-  for (int base = 0; base < n_tiles; base += kScanThreads) {
-    const int i = base + threadIdx.x;
-    const T x = i < n_tiles ? v[i] : T(0);
-    T tot;
-    const T ex = block_exclusive_scan<T>(x, tot);
-    if (i < n_tiles) v[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (total) *total = carry;
-    if (total_at_end) out[scan_len(n_dev, mult)] = carry;
-  }
-}
-
-template <typename T>
-__global__ void scan_apply(const T* in, T* out, const int* n_dev, int mult,
-                           const T* __restrict__ tile_off) {
-  const long long n = scan_len(n_dev, mult);
-  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-  if ((long long)blockIdx.x * kScanTile >= n) return;
-  T vals[kScanItems];
-  T s = 0;
+  const int tile = s_tile;
+  if (tile < ntiles) {
+    const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+    T vals[kScanItems];
+    T sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    vals[k] = base + k < n ? in[base + k] : T(0);
-    s += vals[k];
-  }
-  T total;
-  T run = block_exclusive_scan<T>(s, total) + tile_off[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < n) {
-      out[base + k] = run;
-      run += vals[k];
+    for (int k = 0; k < kScanItems; ++k) {
+      vals[k] = base + k < n ? in[base + k] : T(0);
+      sum += vals[k];
     }
+    T tile_sum;
+    T run = block_exclusive_scan<T>(sum, tile_sum);
+    if (threadIdx.x == 0) {
+      T excl = 0;
+      if (tile > 0) {
+        ((volatile T*)agg)[tile] = tile_sum;
+        __threadfence();
+        ((volatile T*)st)[tile] = (T)kStAgg;
+        for (int p = tile - 1; p >= 0;) {
+          T f = ((volatile T*)st)[p];
+          long long spin = 0;
+          while (f == 0 && ++spin < kScanSpin) f = ((volatile T*)st)[p];
+          if (f == 0) {   // a predecessor never published: give up on this scan
+            atomicOr(err, kErrNumeric);
+            break;
+          }
+          __threadfence();
+          if (f == (T)kStInc) {
+            excl += ((volatile T*)inc)[p];
+            break;
+          }
+          excl += ((volatile T*)agg)[p];
+          --p;
+        }
+      }
+      ((volatile T*)inc)[tile] = excl + tile_sum;
+      __threadfence();
+      ((volatile T*)st)[tile] = (T)kStInc;
+      s_excl = excl;
+      if (tile == ntiles - 1) {
+        if (total) *total = excl + tile_sum;
+        if (total_at_end) out[n] = excl + tile_sum;
+      }
+    }
+    __syncthreads();
+    run += s_excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (base + k < n) {
+        out[base + k] = run;
+        run += vals[k];
+      }
+  } else if (tile == 0 && threadIdx.x == 0) {   // empty input
+    if (total) *total = 0;
+    if (total_at_end) out[n] = 0;
+  }
+  // the last block to finish clears the work area for the next scan
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr[1], T(1)) == (T)(gridDim.x - 1)) {
+      for (int t = 0; t < ntiles; ++t) st[t] = 0;
+      ctr[0] = 0;
+      ctr[1] = 0;
+      __threadfence();
+    }
+  }
 }
 
 // whole scan in one block when the capacity is small (up to 64 items per thread)
@@ -498,31 +533,35 @@ __global__ void scan_small(const T* in, T* out, const int* n_dev, int mult, T* t
   }
 }
 
-long long scan_tmp_elems(long long cap) { return (cap + kScanTile - 1) / kScanTile + 1; }
+static int scan_tiles(long long cap) { return (int)((cap + kScanTile - 1) / kScanTile + 1); }
+long long scan_tmp_elems(long long cap) { return 3LL * scan_tiles(cap) + 2; }
 
 template <typename T>
 static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long cap, T* total,
-                      bool total_at_end, T* tmp, cudaStream_t s) {
+                      bool total_at_end, T* tmp, long long tmp_cap, unsigned* err, cudaStream_t s) {
   if (cap <= kScanSmall) {
     scan_small<T><<<1, kScanThreads, 0, s>>>(in, out, n_dev, mult, total, total_at_end ? 1 : 0);
     ++g_launches;
     return;
   }
-  const int nt = (int)((cap + kScanTile - 1) / kScanTile);
-  scan_tile_sums<T><<<nt, kScanThreads, 0, s>>>(in, n_dev, mult, tmp); ++g_launches;
-  scan_single<T><<<1, kScanThreads, 0, s>>>(tmp, nt, total, out, n_dev, mult, total_at_end ? 1 : 0);
+  const int nt = scan_tiles(cap), nw = scan_tiles(tmp_cap);
+  if (nt > nw) {   // work area smaller than this capacity (a caller error): flag, no scan
+    cudaMemsetAsync(err, (int)kErrNumeric, 1, s);
+    return;
+  }
+  scan_onepass<T><<<nt, kScanThreads, 0, s>>>(in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err);
   ++g_launches;
-  scan_apply<T><<<nt, kScanThreads, 0, s>>>(in, out, n_dev, mult, tmp); ++g_launches;
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
-              uint32_t* total, bool total_at_end, uint32_t* tmp, cudaStream_t s) {
-  scan_impl<uint32_t>(in, out, n_dev, mult, cap, total, total_at_end, tmp, s);
+              uint32_t* total, bool total_at_end, uint32_t* tmp, long long tmp_cap, unsigned* err,
+              cudaStream_t s) {
+  scan_impl<uint32_t>(in, out, n_dev, mult, cap, total, total_at_end, tmp, tmp_cap, err, s);
 }
 void scan_u64(const unsigned long long* in, unsigned long long* out, const int* n_dev, int mult,
               long long cap, unsigned long long* total, bool total_at_end,
-              unsigned long long* tmp, cudaStream_t s) {
-  scan_impl<unsigned long long>(in, out, n_dev, mult, cap, total, total_at_end, tmp, s);
+              unsigned long long* tmp, long long tmp_cap, unsigned* err, cudaStream_t s) {
+  scan_impl<unsigned long long>(in, out, n_dev, mult, cap, total, total_at_end, tmp, tmp_cap, err, s);
 }
 
 }  // namespace glmb
