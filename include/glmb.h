@@ -168,10 +168,12 @@ glmb_status glmb_prune(glmb_handle* h);
 /* One whole frame: glmb_predict + glmb_update + glmb_prune with the same
  * arguments and results, launched as one CUDA graph (captured on the first
  * call for a given launch plan and replayed afterwards) followed by one
- * synchronisation.  The handle's stream must not be the legacy default
- * stream.  The per-step inspection calls (glmb_get_parents, _components,
- * _pairs, _children) describe this frame afterwards as they do after the
- * separate calls.  Errors: those of the three calls. */
+ * synchronisation.  The graph also computes the frame's estimates (unless
+ * glmb_set_step_estimates turned that off), so that a following
+ * glmb_estimates only copies them out.  The handle's stream must not be the
+ * legacy default stream.  The per-step inspection calls (glmb_get_parents,
+ * _components, _pairs, _children) describe this frame afterwards as they do
+ * after the separate calls.  Errors: those of the three calls. */
 glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
                       int z_is_device);
 
@@ -255,6 +257,11 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
  * and the number of timed calls (n entries each; either pointer may be
  * NULL); it synchronises. */
 glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask);
+
+/* Whether glmb_step computes the frame's estimates in its graph (on by
+ * default; with it off, glmb_estimates computes them when called).  Not part
+ * of the paper's method: a launch option. */
+glmb_status glmb_set_step_estimates(glmb_handle* h, int on);
 glmb_status glmb_get_timing(glmb_handle* h, double* ms, long long* calls, int n);
 
 /* Top-H selection without device allocation.  The paper has no counterpart:

@@ -144,7 +144,7 @@ def load() -> C.CDLL:
         "glmb_get_children": [P, P, P, P, L, P],
         "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
         "glmb_get_retained": [P, P, P, I, P],
-        "glmb_step": [P, P, I, P, I, I],
+        "glmb_step": [P, P, I, P, I, I], "glmb_set_step_estimates": [P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -325,6 +325,9 @@ class Filter:
                     cov=t["cov"][:, : dx * dx].reshape(k, dx, dx).copy(), pmf=pmf[:pmf_cap].copy())
 
     STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")
+
+    def set_step_estimates(self, on: bool = True):
+        self._check(self.lib.glmb_set_step_estimates(self.h, 1 if on else 0))
 
     def set_profiling(self, stages: Iterable[str] = ()):
         mask = 0

@@ -100,6 +100,12 @@ struct glmb_handle {
   unsigned char* d_est = nullptr;
   unsigned char* h_est = nullptr;
   size_t est_off_pmf = 0, est_off_tr = 0, est_off_r = 0, est_off_done = 0;
+  // state generation (bumped by every change of the filter state) and the
+  // generation whose estimates h_est holds; glmb_step computes them in its
+  // graph unless step_estimates is off
+  long long gen = 0, est_gen = -1;
+  bool step_estimates = true;
+  unsigned* h_cnt = nullptr;   // pinned copy of the prune counters
   double* d_ru = nullptr;
   // stage timing
   unsigned prof_mask = 0;
@@ -252,12 +258,6 @@ bool spd_inverse(int n, const double* A, double* Ainv, double* logdet) {
   return true;
 }
 
-glmb_status sync_scal(glmb_handle* h) {
-  CU(cudaMemcpyAsync(h->h_scal, h->d_scal, S_N * sizeof(unsigned), cudaMemcpyDeviceToHost,
-                     h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  return GLMB_OK;
-}
 
 const char* err_text(unsigned e) {
   if (e & kErrPairs) return "gated pairs exceed max_pairs";
@@ -327,6 +327,18 @@ void prof_collect(glmb_handle* h) {
 }  // namespace
 
 extern "C" {
+
+glmb_status glmb_set_step_estimates(glmb_handle* h, int on) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->step_estimates != (on != 0)) {
+    // captured graphs were built with the other setting
+    cudaStreamSynchronize(h->stream);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+  }
+  h->step_estimates = on != 0;
+  return GLMB_OK;
+}
 
 glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask) {
   if (!h) return GLMB_E_INVALID;
@@ -472,7 +484,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
             dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
             dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
-            halloc(h, &h->h_scal, S_N) && dalloc(h, &h->d_ru, h->cap_meas) &&
+            halloc(h, &h->h_scal, S_N) && halloc(h, &h->h_cnt, 8) && dalloc(h, &h->d_ru, h->cap_meas) &&
             dalloc(h, &h->d_fs, 1) && halloc(h, &h->h_fs, 2);
   if (ok) {
     h->pw.err = h->d_scal + S_ERR;
@@ -521,6 +533,7 @@ glmb_status glmb_destroy(glmb_handle* h) {
 glmb_status glmb_reset(glmb_handle* h) {
   if (!h) return GLMB_E_INVALID;
   h->err.clear();
+  ++h->gen;
   return set_initial(h);
 }
 
@@ -798,16 +811,39 @@ int plan_smem(const glmb_handle* h, const Plan& p) {
 }
 
 // frame result: commit, abandon, or redo with exact maxima; `done` on return
-glmb_status finish_frame(glmb_handle* h) {
+// the frame's counters (and, with estimates, the estimate block) to pinned
+// host memory, on the stream
+glmb_status enqueue_results(glmb_handle* h, bool with_est) {
+  CU(cudaMemcpyAsync(h->h_cnt, h->pw.counts, 8 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(h->h_scal, h->d_scal, S_N * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  if (with_est)
+    CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, h->stream));
+  return GLMB_OK;
+}
+
+// estimates of table (Y, A) with Y's hypothesis count on the device
+// (H_dev) or on the host
+void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, const unsigned* H_dev, int H) {
+  const int pcap = h->max_tracks + 1;
+  prof_begin(h, kStageEstimates);
+  launch_estimates(Y, H, H_dev, A, h->md.dx, (double*)(h->d_est + h->est_off_pmf), pcap, (int*)h->d_est,
+                   (double*)(h->d_est + h->est_off_r), h->d_est + h->est_off_tr,
+                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, h->stream);
+  prof_end(h, kStageEstimates);
+}
+
+// results: the counters (and estimates, when est_enqueued) were copied by the
+// frame's launches; redo, abandon or commit
+glmb_status finish_frame(glmb_handle* h, bool est_enqueued = false) {
   auto abandon = [&](glmb_status st, const char* msg) {
     h->frame -= 1;
     h->stage = 0;
     return fail(h, st, "prune: %s", msg);
   };
-  unsigned cnt[8];
-  CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
-  glmb_status st = sync_scal(h);
-  if (st != GLMB_OK) return st;
+  glmb_status st;
+  if (!est_enqueued && (st = enqueue_results(h, false)) != GLMB_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  const unsigned* cnt = h->h_cnt;
   unsigned e = h->h_scal[S_ERR];
   if ((e & kErrSlots) && !(e & (kErrFatal & ~kErrSlots))) {
     // a parent had more gated pairs than planned: redo the expansion and
@@ -820,9 +856,10 @@ glmb_status finish_frame(glmb_handle* h) {
     CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
     if ((st = enqueue_expand(h, p)) != GLMB_OK) return st;
     if ((st = enqueue_prune(h, p)) != GLMB_OK) return st;
-    CU(cudaMemcpyAsync(cnt, h->pw.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
-    if ((st = sync_scal(h)) != GLMB_OK) return st;
+    if ((st = enqueue_results(h, false)) != GLMB_OK) return st;
+    CU(cudaStreamSynchronize(h->stream));
     e = h->h_scal[S_ERR];
+    est_enqueued = false;   // the estimates copied with the first pass are stale
   }
   if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
   if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
@@ -846,6 +883,8 @@ glmb_status finish_frame(glmb_handle* h) {
   h->theta_M_valid = true;
   h->retained_valid = true;
   h->stage = 0;
+  ++h->gen;
+  if (est_enqueued) h->est_gen = h->gen;
   return GLMB_OK;
 }
 
@@ -983,6 +1022,9 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       enqueue_table(h, q);
       enqueue_expand(h, q);
       enqueue_prune(h, q);
+      if (h->step_estimates)
+        enqueue_estimates(h, h->hyps[1 - h->hcur], h->comps[h->cur], h->pw.counts, 0);
+      enqueue_results(h, h->step_estimates);
       h->capturing = false;
       CU(cudaStreamEndCapture(h->stream, &graph));
       size_t n_nodes = 0;
@@ -1017,13 +1059,17 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
     g_launches += g.n_kernels;
     CU(cudaGraphLaunch(g.exec, h->stream));
     ++h->n_graph_launches;
-    for (int s = 0; s < kStageEstimates; ++s)
-      if ((h->prof_mask & (1u << s)) && h->ev[s][0]) h->ev_pending[s] = true;
+    for (int s = 0; s <= kStageEstimates; ++s)
+      if ((h->prof_mask & (1u << s)) && h->ev[s][0] && (s < kStageEstimates || h->step_estimates))
+        h->ev_pending[s] = true;
   } else {
     enqueue_predict(h, p);
     enqueue_table(h, p);
     enqueue_expand(h, p);
     enqueue_prune(h, p);
+    if (h->step_estimates)
+      enqueue_estimates(h, h->hyps[1 - h->hcur], h->comps[h->cur], h->pw.counts, 0);
+    enqueue_results(h, h->step_estimates);
   }
   CU(cudaGetLastError());
   h->H_par = h->H;
@@ -1031,7 +1077,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->birth_base = h->n_comp;
   h->have_update = true;
   h->stage = 2;
-  return finish_frame(h);
+  return finish_frame(h, true);
 }
 
 glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n) {
@@ -1085,20 +1131,14 @@ glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out,
   if (!h || !n_out || (cap > 0 && !out)) return GLMB_E_INVALID;
   if (h->stage == 2) return fail(h, GLMB_E_STATE, "estimates: call glmb_prune first");
   cudaStream_t s = h->stream;
-  const HypTable& Y = h->hyps[h->hcur];
-  const CompTable& A = h->comps[h->cur];
   const int pcap = h->max_tracks + 1;
-  int* d_nb = (int*)h->d_est;
-  double* d_pmf = (double*)(h->d_est + h->est_off_pmf);
-  double* d_r = (double*)(h->d_est + h->est_off_r);
-  prof_begin(h, kStageEstimates);
-  CU(cudaMemsetAsync(d_r, 0, (size_t)pcap * sizeof(double), s));
-  launch_estimates(Y, h->H, A, h->md.dx, d_pmf, pcap, d_nb, d_r, h->d_est + h->est_off_tr,
-                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, s);
-  prof_end(h, kStageEstimates);
-  CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
+  if (h->est_gen != h->gen) {   // not computed with this state's step
+    enqueue_estimates(h, h->hyps[h->hcur], h->comps[h->cur], nullptr, h->H);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    h->est_gen = h->gen;
+  }
   int nb[2];
   std::memcpy(nb, h->h_est, sizeof nb);
   const int nhat = nb[0];
@@ -1295,6 +1335,7 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
   h->have_update = false;
   h->theta_M_valid = false;
   h->retained_valid = false;
+  ++h->gen;
   return GLMB_OK;
 }
 

@@ -141,10 +141,12 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
                                kErrEntries | kErrSlots | kErrInput;
 
-// estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, r[pcap] (zeroed by the
-// caller), tracks = glmb_track[pcap]; done is a zeroed counter
-void launch_estimates(const HypTable& hp, int H, const CompTable& ct, int dx, double* pmf, int pcap,
-                      int* nb, double* r, void* tracks, unsigned* done, int n_sm, cudaStream_t s);
+// estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, r[pcap] (existence
+// sums, zeroed by the first kernel), tracks = glmb_track[pcap]; done is a
+// zeroed counter (left zeroed); H_dev (nullable) gives H on the device
+void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
+                      double* pmf, int pcap, int* nb, double* r, void* tracks, unsigned* done, int n_sm,
+                      cudaStream_t s);
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s);
 
 }  // namespace glmb

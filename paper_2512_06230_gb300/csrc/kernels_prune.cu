@@ -653,7 +653,8 @@ __device__ __forceinline__ unsigned long long w_fx(double logw) {
 // Cardinality distribution, MAP cardinality (ties to the smaller n) and the
 // heaviest hypothesis of that cardinality (ties to the lower index); one
 // block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
-__global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* nb) {
+__global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap,
+                                int* nb, unsigned long long* r_fx) {
   extern __shared__ unsigned long long s_pmf[];   // [pcap]
   __shared__ unsigned long long bw[32];
   __shared__ int bi[32];
@@ -662,7 +663,11 @@ __global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* 
   __shared__ int s_nhat;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5;
   const int nw = (nthr + 31) >> 5;
-  for (int n = tid; n < pcap; n += nthr) s_pmf[n] = 0ull;
+  const int H = H_dev ? (int)*H_dev : H_host;
+  for (int n = tid; n < pcap; n += nthr) {
+    s_pmf[n] = 0ull;
+    r_fx[n] = 0ull;   // existence sums of the next kernel
+  }
   __syncthreads();
   for (int h = tid; h < H; h += nthr) {
     const int n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
@@ -724,11 +729,13 @@ __global__ void est_card_kernel(HypTable hp, int H, double* pmf, int pcap, int* 
 // in shared memory and the weights summed per block there, then once per
 // block into r_fx); the last block writes the MAP tracks as glmb_track
 // records (mean hi + lo in FP64, full covariance).
-__global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const int* __restrict__ nb,
-                                 unsigned long long* r_fx, glmb_track* out, int cap, unsigned* done) {
+__global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev, CompTable ct, int dx,
+                                 const int* __restrict__ nb, unsigned long long* r_fx, glmb_track* out,
+                                 int cap, unsigned* done) {
   extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
   unsigned long long* s_r = s_key + cap;
   __shared__ bool last;
+  const int H = H_dev ? (int)*H_dev : H_host;
   const int best = nb[1];
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -783,16 +790,18 @@ __global__ void est_exist_kernel(HypTable hp, int H, CompTable ct, int dx, const
   if (threadIdx.x == 0) *done = 0u;
 }
 
-void launch_estimates(const HypTable& hp, int H, const CompTable& ct, int dx, double* pmf, int pcap,
-                      int* nb, double* r, void* tracks, unsigned* done, int n_sm, cudaStream_t s) {
+void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
+                      double* pmf, int pcap, int* nb, double* r, void* tracks, unsigned* done, int n_sm,
+                      cudaStream_t s) {
   if (pcap * 16 > 48 * 1024) {
     cudaFuncSetAttribute(est_card_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
     cudaFuncSetAttribute(est_exist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
   }
-  est_card_kernel<<<1, 1024, (size_t)pcap * 8, s>>>(hp, H, pmf, pcap, nb); ++g_launches;
-  const int blocks = std::max(1, std::min((H + 7) / 8, 2 * n_sm));
-  est_exist_kernel<<<blocks, 256, (size_t)pcap * 16, s>>>(hp, H, ct, dx, nb, reinterpret_cast<unsigned long long*>(r),
-                                                         (glmb_track*)tracks, pcap, done);
+  unsigned long long* r_fx = reinterpret_cast<unsigned long long*>(r);
+  est_card_kernel<<<1, 1024, (size_t)pcap * 8, s>>>(hp, H, H_dev, pmf, pcap, nb, r_fx); ++g_launches;
+  const int blocks = H_dev ? 2 * n_sm : std::max(1, std::min((H + 7) / 8, 2 * n_sm));
+  est_exist_kernel<<<blocks, 256, (size_t)pcap * 16, s>>>(hp, H, H_dev, ct, dx, nb, r_fx, (glmb_track*)tracks,
+                                                         pcap, done);
   ++g_launches;
 }
 
