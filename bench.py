@@ -179,10 +179,13 @@ def main():
     torch.cuda.synchronize()
     h_up = cfg["h_up"]
 
+    host_times = []
+
     def run(n_steps, start, host, profile=False, record=None):
         """Runs n_steps frames starting at global step index `start`; returns
         per-step event times (ms) and per-step work counters."""
         times, work = [], []
+        host_times.clear()
         if profile:
             f.set_profiling(["expand"])
         for s in range(start, start + n_steps):
@@ -196,14 +199,18 @@ def main():
             e0.record(stream)
             if fi == 0:
                 f.reset()
+            t0 = time.perf_counter()
             if host:
                 f.step(Bhost[fi], fr.Z)
             else:
                 f.step(Bhost[fi], Zdev[fi], device=True)
+            t1 = time.perf_counter()
             est = f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+            t2 = time.perf_counter()
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            host_times.append((t1 - t0, t2 - t1))
             info = f.info()
             H_par = 1 if info0 is None else info0["n_hyp"]
             E_par = 0 if info0 is None else info0["n_entries"]
@@ -227,6 +234,8 @@ def main():
     torch.cuda.synchronize()
     times, work = run(args.steps, args.warmup, host=False, profile=True)
     torch.cuda.synchronize()
+    host_step_ms = 1e3 * sum(t[0] for t in host_times) / max(1, len(host_times))
+    host_est_ms = 1e3 * sum(t[1] for t in host_times) / max(1, len(host_times))
     info1 = f.info()
     launches = info1["n_launches"] - launches0
     tim = f.timing()
@@ -284,6 +293,7 @@ def main():
                 "h2d_bytes_per_step": sum(w["h2d"] for w in work_h) / len(work_h),
                 "d2h_bytes_per_step": sum(w["d2h"] for w in work_h) / len(work_h)},
         "gpu_launches": int(launches),
+        "host_ms_per_step": {"step_call": round(host_step_ms, 4), "estimates_call": round(host_est_ms, 4)},
         "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
                    "redone_frames": info1["n_redo"],
                    "capture_ms_total": round(info1["graph_capture_ms"], 3)},

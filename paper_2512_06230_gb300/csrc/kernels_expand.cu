@@ -11,7 +11,7 @@
 //             row integer thresholds of the categorical draw under "all slots
 //             alive", a reference association (each row's most likely option)
 //             with its exact score, and per slot the m-only part of the track
-//             term for m_ref - 1, m_ref and m_ref + 1 detections;
+//             term for m_ref - 2 .. m_ref + 2 detections;
 //             The stage also tabulates the exact score change of every single
 //             deviation from the reference: a detection joining a candidate
 //             pair's slot, leaving its reference slot, a slot dying;
@@ -37,10 +37,12 @@
 namespace glmb {
 
 // ---- per-parent image ----
+constexpr int kSlmN = 5;   // cached m-only term parts per slot (m_ref - 2 .. m_ref + 2)
+
 struct Lay {
   int scal;
   int row, rowbl, seref, sqref, termref, hwref, gaind, lossd, deadd;
-  int rowrk, rca, rowoff, rowfill, roww0;
+  int rowrk, rca, rowoff, rowfill, roww0, rowthr0;
   int comp, dthr, logp, log1mp, mref, refnew, hph, slm, dpc;
   int cthr, ceidx, cw, ce, cq, cslot;
   int ninfref, sln, gninf, lninf, dninf;
@@ -89,6 +91,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.rowoff = b.take(4LL * (M + 1));
   L.rowfill = b.take(4LL * (M + 1));
   L.roww0 = b.take(4LL * M);
+  L.rowthr0 = b.take(4LL * M);              // clutter option's threshold
   L.comp = b.take(4LL * T);
   L.dthr = b.take(4LL * T);
   L.logp = b.take(4LL * T);
@@ -96,7 +99,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.mref = b.take(4LL * T);
   L.refnew = b.take(4LL * T);
   L.hph = b.take(4LL * NP * T);             // H P H^T of each slot (packed)
-  L.slm = b.take(4LL * 3 * (NP + 1) * T);   // m-only term parts, m = m_ref - 1 .. m_ref + 1
+  L.slm = b.take(4LL * kSlmN * (NP + 1) * T);   // m-only term parts, m = m_ref - 2 .. m_ref + 2
   L.dpc = b.take(4LL * (T / 4 + 2));        // chunks of 4 slots that can die
   L.cthr = b.take(4LL * K);
   L.ceidx = b.take(4LL * K);
@@ -105,7 +108,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.cq = b.take(4LL * K);                   // e^T R^-1 e of each candidate pair
   L.cslot = b.take(2LL * K);
   L.ninfref = b.take(T);
-  L.sln = b.take(3LL * T);
+  L.sln = b.take((long long)kSlmN * T);
   L.gninf = b.take(K);
   L.lninf = b.take(M);
   L.dninf = b.take(T);
@@ -179,7 +182,7 @@ __device__ __forceinline__ void slot_HPH(const float* s_hph, int T, int t, float
     }
 }
 
-// Cached m-only parts of slot t's term, v = m - m_ref + 1 in {0, 1, 2};
+// Cached m-only parts of slot t's term, v = m - m_ref + 2 in {0 .. 4};
 // kNoSlm marks an entry that was not built (m < 1).
 constexpr int8_t kNoSlm = 127;
 
@@ -223,7 +226,7 @@ struct View {
   const unsigned long long* rowbl;
   const long long *seref, *sqref, *termref, *gaind, *lossd, *deadd;
   const unsigned long long* hwref;
-  const uint32_t *rowrk, *rca, *comp, *dthr, *refnew, *dpc, *cthr;
+  const uint32_t *rowrk, *rca, *rowthr0, *comp, *dthr, *refnew, *dpc, *cthr;
   const float *roww0, *logp, *log1mp, *hph, *slm, *cw, *ce, *cq;
   const int* mref;
   const uint16_t* cslot;
@@ -248,6 +251,7 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) 
   v.hwref = at<unsigned long long>(b, L.hwref);
   v.rowrk = at<uint32_t>(b, L.rowrk);
   v.rca = at<uint32_t>(b, L.rca);
+  v.rowthr0 = at<uint32_t>(b, L.rowthr0);
   v.comp = at<uint32_t>(b, L.comp);
   v.dthr = at<uint32_t>(b, L.dthr);
   v.refnew = at<uint32_t>(b, L.refnew);
@@ -273,8 +277,8 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) 
 template <int DZ>
 __device__ __forceinline__ long long slot_term(const Model& md, const View& v, int T, int t, int m, int dcnt,
                                                const long long (&se)[DZ], long long sq, int& ninf) {
-  if (m >= 1 && dcnt >= -1 && dcnt <= 1 && v.sln[(dcnt + 1) * T + t] != kNoSlm)
-    return term_from<DZ>(md, load_slm<DZ>(v.slm, v.sln, T, dcnt + 1, t), m, se, sq, ninf);
+  if (m >= 1 && dcnt >= -2 && dcnt <= 2 && v.sln[(dcnt + 2) * T + t] != kNoSlm)
+    return term_from<DZ>(md, load_slm<DZ>(v.slm, v.sln, T, dcnt + 2, t), m, se, sq, ninf);
   return slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, se, sq, ninf);
 }
 
@@ -329,6 +333,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
   uint32_t* s_rowrk = at<uint32_t>(sm, L.rowrk);
   uint32_t* s_rca = at<uint32_t>(sm, L.rca);
+  uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
   uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
   uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
   float* s_roww0 = at<float>(sm, L.roww0);
@@ -457,7 +462,8 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         s_ceidx[off + y + 1] = ke;
       }
       if (nc == 0) {
-        s_row[i] = make_uint4(off, 0u, kOne24, kOne24);
+        s_row[i] = make_uint4(off, 0u, 0u, kOne24);
+        s_rowthr0[i] = kOne24;
         s_rowbl[i] = 0ull;
         s_rowrk[i] = 0u;
         s_roww0[i] = 1.f;
@@ -493,9 +499,12 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         flag |= s_dthr[s_cslot[off + j]] > 0u;
       }
       // row i: x = first candidate, y = count | may-die flag << 15 |
-      // reference option << 16, z = clutter threshold, w = first candidate's
-      s_row[i] = make_uint4(off, (uint32_t)nc | (flag ? 0x8000u : 0u) | ((uint32_t)ref << 16), thr0,
-                            s_cthr[off]);
+      // reference option << 16, [z, w) = the uniforms that pick the reference
+      // option when every candidate is alive
+      const uint32_t lo = ref == 0 ? 0u : (ref == 1 ? thr0 : s_cthr[off + ref - 2]);
+      const uint32_t hi = ref == 0 ? thr0 : s_cthr[off + ref - 1];
+      s_row[i] = make_uint4(off, (uint32_t)nc | (flag ? 0x8000u : 0u) | ((uint32_t)ref << 16), lo, hi);
+      s_rowthr0[i] = thr0;
       s_rowbl[i] = bl;
       s_rowrk[i] = ref > 0 ? (((uint32_t)s_cslot[off + ref - 1] + 1u) << 16) | (off + ref - 1) : 0u;
       s_roww0[i] = w0;
@@ -516,10 +525,10 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   }
   __syncthreads();
 
-  // ---- m-only term parts (slot x {m_ref - 1, m_ref, m_ref + 1}), chunk lists ----
-  for (int x = tid; x < 3 * T; x += nthr) {
+  // ---- m-only term parts (slot x {m_ref - 2 .. m_ref + 2}), chunk lists ----
+  for (int x = tid; x < kSlmN * T; x += nthr) {
     const int t = x % T, v = x / T;
-    const int m = s_mref[t] - 1 + v;
+    const int m = s_mref[t] - 2 + v;
     if (m < 1) {
       s_sln[v * T + t] = kNoSlm;
       continue;
@@ -562,8 +571,8 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       const int mr = s_mref[t];
       int ninf;
       long long term;
-      if (mr >= 1 && s_sln[T + t] != kNoSlm) {
-        term = term_from<DZ>(md, load_slm<DZ>(s_slm, s_sln, T, 1, t), mr, se, s_sqref[t], ninf);
+      if (mr >= 1 && s_sln[2 * T + t] != kNoSlm) {
+        term = term_from<DZ>(md, load_slm<DZ>(s_slm, s_sln, T, 2, t), mr, se, s_sqref[t], ninf);
       } else {
         float HPH[DZ][DZ];
         slot_HPH<DZ>(s_hph, T, t, HPH);
@@ -715,17 +724,22 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v,
       const uint32_t off = R.x;
       const int nc = (int)(R.y & 0x7FFFu);
       int opt;
-      if (nd > 0 && (R.y & 0x8000u) && (v.rowbl[i] & bloom) && [&] {
-            for (int j = 0; j < nc; ++j)
-              if (dead(v.cslot[off + j])) return true;
-            return false;
-          }()) {
+      // dead candidates of this row, bit j (rows beyond 32 candidates test
+      // the rest one by one)
+      uint32_t dm = 0u;
+      if (nd > 0 && (R.y & 0x8000u) && (v.rowbl[i] & bloom))
+        for (int j = 0; j < nc; ++j)
+          if (dead(v.cslot[off + j])) dm |= 1u << min(j, 31);
+      if (dm) {
         // some candidates are dead: draw among the living in proportion to
         // their weights (clutter first)
+        auto is_dead = [&](int j) -> bool {
+          return j < 31 ? ((dm >> j) & 1u) != 0u : dead(v.cslot[off + j]);
+        };
         const float w0 = md.kappa_zero ? 0.f : v.roww0[i];
         float sum = w0;
         for (int j = 0; j < nc; ++j)
-          if (!dead(v.cslot[off + j])) sum += v.cw[off + j];
+          if (!is_dead(j)) sum += v.cw[off + j];
         if (!(sum > 0.f)) {
           bad_row = true;
           opt = 0;
@@ -736,7 +750,7 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v,
           opt = -1;
           if (w0 > 0.f && xk < cum) opt = 0;
           for (int j = 0; j < nc; ++j) {
-            if (dead(v.cslot[off + j])) continue;
+            if (is_dead(j)) continue;
             const float w = v.cw[off + j];
             if (!(w > 0.f)) continue;
             cum += w;
@@ -745,12 +759,12 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v,
           }
           if (opt < 0) opt = last < 0 ? 0 : last;
         }
-      } else if (k < R.z) {
+      } else if (k - R.z < R.w - R.z) {
+        continue;   // the reference option
+      } else if (k < v.rowthr0[i]) {
         opt = 0;
-      } else if (k < R.w) {
-        opt = 1;
       } else {
-        int j = 1;
+        int j = 0;
         while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
         opt = j + 1;
       }
@@ -980,7 +994,7 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
           if (bit_of(dmask, v.cslot[off + j])) { fast = false; break; }
       int opt;
       if (fast) {
-        if (k < R.z) {
+        if (k < v.rowthr0[i]) {
           opt = 0;
         } else {
           int j = 0;
