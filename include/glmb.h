@@ -258,6 +258,22 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
  * NULL); it synchronises. */
 glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask);
 
+/* Launch-path overrides, for tests and tuning (not part of the paper's
+ * method).  The paths compute the same arithmetic, so children's keys,
+ * hashes and statuses do not depend on them.
+ *   GLMB_OPT_STAGE_GLOBAL  build the per-parent tables in global memory even
+ *                          when they fit in shared memory;
+ *   GLMB_OPT_DRAW_WARP     draw every child with one warp;
+ *   GLMB_OPT_DRAW_THREAD   draw children one per thread whatever the number
+ *                          of parents (children whose lists overflow still
+ *                          go to the warp path).
+ * Default 0: shared-memory staging when it fits, one thread per child once
+ * the children give every SM four warps. */
+#define GLMB_OPT_STAGE_GLOBAL 1u
+#define GLMB_OPT_DRAW_WARP 2u
+#define GLMB_OPT_DRAW_THREAD 4u
+glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts);
+
 /* Whether glmb_step computes the frame's estimates in its graph (on by
  * default; with it off, glmb_estimates computes them when called).  Not part
  * of the paper's method: a launch option. */

@@ -144,7 +144,7 @@ def load() -> C.CDLL:
         "glmb_get_children": [P, P, P, P, L, P],
         "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
         "glmb_get_retained": [P, P, P, I, P],
-        "glmb_step": [P, P, I, P, I, I], "glmb_set_step_estimates": [P, I],
+        "glmb_step": [P, P, I, P, I, I], "glmb_set_step_estimates": [P, I], "glmb_set_launch_options": [P, C.c_uint],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -319,12 +319,19 @@ class Filter:
         n = C.c_int()
         self._check(self.lib.glmb_estimates(self.h, _ptr(out), cap, C.byref(n), _ptr(pmf), pmf_cap))
         k, dx = n.value, self.dx
-        t = out[:k]
-        return dict(n=k, labels=list(zip(t["label_k"].tolist(), t["label_b"].tolist())),
-                    r=t["r"].copy(), mean=t["mean"][:, :dx].copy(),
-                    cov=t["cov"][:, : dx * dx].reshape(k, dx, dx).copy(), pmf=pmf[:pmf_cap].copy())
+        t = out[:k].copy()
+        # labels: (k, 2) array of (label_k, label_b); the rest are views of
+        # this call's own copy of the records
+        return dict(n=k, labels=np.stack((t["label_k"], t["label_b"]), axis=1),
+                    r=t["r"], mean=t["mean"][:, :dx],
+                    cov=t["cov"][:, : dx * dx].reshape(k, dx, dx), pmf=pmf[:pmf_cap].copy())
 
     STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")
+
+    OPT_STAGE_GLOBAL, OPT_DRAW_WARP, OPT_DRAW_THREAD = 1, 2, 4
+
+    def set_launch_options(self, opts: int = 0):
+        self._check(self.lib.glmb_set_launch_options(self.h, int(opts)))
 
     def set_step_estimates(self, on: bool = True):
         self._check(self.lib.glmb_set_step_estimates(self.h, 1 if on else 0))

@@ -105,6 +105,7 @@ struct glmb_handle {
   // graph unless step_estimates is off
   long long gen = 0, est_gen = -1;
   bool step_estimates = true;
+  unsigned launch_opts = 0;   // GLMB_OPT_* overrides
   unsigned* h_cnt = nullptr;   // pinned copy of the prune counters
   double* d_ru = nullptr;
   // stage timing
@@ -327,6 +328,19 @@ void prof_collect(glmb_handle* h) {
 }  // namespace
 
 extern "C" {
+
+glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
+  if (!h) return GLMB_E_INVALID;
+  if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD))
+    return fail(h, GLMB_E_INVALID, "set_launch_options: unknown option bits 0x%x", opts);
+  if (opts != h->launch_opts) {
+    cudaStreamSynchronize(h->stream);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+  }
+  h->launch_opts = opts;
+  return GLMB_OK;
+}
 
 glmb_status glmb_set_step_estimates(glmb_handle* h, int on) {
   if (!h) return GLMB_E_INVALID;
@@ -795,8 +809,11 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   const int dz = h->md.dz;
   // one thread per child once the children give every SM four warps (the
   // register lists address pairs with 16 bits); else one warp per child
-  p.thread = (long long)h->H * h->cfg.h_up >= 4LL * 32 * h->n_sm && p.K <= 65536;
-  p.smem = expand_image_bytes(dz, p.T, p.K, p.M) <= h->smem_limit;
+  p.thread = (long long)h->H * h->cfg.h_up >= 4LL * 32 * h->n_sm;
+  if (h->launch_opts & GLMB_OPT_DRAW_THREAD) p.thread = true;
+  if (h->launch_opts & GLMB_OPT_DRAW_WARP) p.thread = false;
+  p.thread = p.thread && p.K <= 65536;
+  p.smem = expand_image_bytes(dz, p.T, p.K, p.M) <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL);
   p.Gw = p.Gm = 0;
   for (int g = 16; g >= 1 && !p.Gw; --g)
     if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
@@ -832,16 +849,17 @@ void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, co
   prof_end(h, kStageEstimates);
 }
 
-// results: the counters (and estimates, when est_enqueued) were copied by the
-// frame's launches; redo, abandon or commit
-glmb_status finish_frame(glmb_handle* h, bool est_enqueued = false) {
+// results: the counters were copied by the frame's launches when
+// copies_enqueued (with the estimates when est_enqueued); redo, abandon or
+// commit
+glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_enqueued = false) {
   auto abandon = [&](glmb_status st, const char* msg) {
     h->frame -= 1;
     h->stage = 0;
     return fail(h, st, "prune: %s", msg);
   };
   glmb_status st;
-  if (!est_enqueued && (st = enqueue_results(h, false)) != GLMB_OK) return st;
+  if (!copies_enqueued && (st = enqueue_results(h, false)) != GLMB_OK) return st;
   CU(cudaStreamSynchronize(h->stream));
   const unsigned* cnt = h->h_cnt;
   unsigned e = h->h_scal[S_ERR];
@@ -1077,7 +1095,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->birth_base = h->n_comp;
   h->have_update = true;
   h->stage = 2;
-  return finish_frame(h, true);
+  return finish_frame(h, true, h->step_estimates);
 }
 
 glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n) {

@@ -232,7 +232,7 @@ def compare(o, g, d, cfg, Z, report: Report | None = None) -> Report:
     if set(kept_o) == set(kept_g):
         r.err("pmf_abs", np.max(np.abs(oe["pmf"][:50] - ge["pmf"][:50])))
         r.err("ru_abs", np.max(np.abs(d["o_ru"] - d["g_ru"])) if len(d["o_ru"]) else 0.0)
-        if oe["n"] == ge["n"] and oe["labels"] == ge["labels"]:
+        if oe["n"] == ge["n"] and list(map(tuple, oe["labels"])) == list(map(tuple, np.asarray(ge["labels"]).tolist())):
             r.err("r_abs", np.max(np.abs(oe["r"] - ge["r"])) if oe["n"] else 0.0)
             for m1, m2 in zip(oe["mean"], ge["mean"]):
                 r.err("est_mean_rel", _rel(m2, m1))
