@@ -143,8 +143,10 @@ glmb_status glmb_reset(glmb_handle* h);
 glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births);
 
 /* Update (Section 3, Eq. 2 and the two-stage sampling): Z holds M detections,
- * M x dim_z row-major float32, in host memory (z_is_device = 0) or device
- * memory on the handle's GPU (z_is_device = 1).  Builds the gated
+ * M x dim_z row-major float32, in host memory (z_is_device = 0; copied) or
+ * device memory on the handle's GPU (z_is_device = 1; read in place by the
+ * kernels, so it must stay valid and unchanged until glmb_prune returns, and
+ * the handle's stream must be ordered after its writes).  Builds the gated
  * compatibility table, the posterior death probabilities, and the h_up
  * children of each hypothesis with their exact log-weights; unique children
  * stay on the device for glmb_prune.  The call only enqueues work: it does

@@ -72,6 +72,7 @@ struct glmb_handle {
   double* d_births = nullptr;
   double* h_births = nullptr;
   float* d_Z = nullptr;
+  const float* z_dev = nullptr;   // detections the kernels read: d_Z or the caller's device buffer
   float* h_Z = nullptr;
   PairTable pt{};
   uint32_t* scan_tmp32 = nullptr;
@@ -578,27 +579,32 @@ glmb_status stage_births(glmb_handle* h, const glmb_birth* births, int n_births)
   return GLMB_OK;
 }
 
-// validates and stages the detections (copied to the device buffer d_Z)
-glmb_status stage_detections(glmb_handle* h, const float* Z, int M, int z_is_device) {
+// validates the detections: device ones are read in place by the kernels,
+// host ones are staged in pinned memory and copied to d_Z (by this call,
+// or by the frame graph when copy is false)
+glmb_status stage_detections(glmb_handle* h, const float* Z, int M, int z_is_device, bool copy = true) {
   if (M < 0 || (M > 0 && !Z)) return fail(h, GLMB_E_INVALID, "update: detections");
   if (M > h->cap_meas) return fail(h, GLMB_E_CAPACITY, "update: M=%d > max_meas %d", M, h->cap_meas);
   const int dz = h->md.dz;
+  h->z_dev = h->d_Z;
   if (M > 0 && !z_is_device)
     for (long long k = 0; k < (long long)M * dz; ++k)
       if (!std::isfinite(Z[k])) return fail(h, GLMB_E_INVALID, "update: non-finite detection");
   if (M > 0) {
     if (z_is_device) {
-      CU(cudaMemcpyAsync(h->d_Z, Z, (size_t)M * dz * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+      h->z_dev = Z;
     } else {
       std::memcpy(h->h_Z, Z, (size_t)M * dz * sizeof(float));
-      CU(cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)M * dz * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+      if (copy)
+        CU(cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)M * dz * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
   }
   return GLMB_OK;
 }
 
-// frame sizes to the device (pinned slot -> d_fs)
-glmb_status upload_sizes(glmb_handle* h, int slot) {
+// frame sizes to the device (pinned slot -> d_fs; by this call, or by the
+// frame graph when copy is false)
+glmb_status upload_sizes(glmb_handle* h, int slot, bool copy = true) {
   FrameDev& f = h->h_fs[slot];
   f = FrameDev{};
   f.n_comp = h->n_comp;
@@ -607,7 +613,8 @@ glmb_status upload_sizes(glmb_handle* h, int slot) {
   f.M = h->M;
   f.H = h->H;
   f.frame = h->frame;
-  CU(cudaMemcpyAsync(h->d_fs, &f, sizeof f, cudaMemcpyHostToDevice, h->stream));
+  f.Z = h->z_dev;
+  if (copy) CU(cudaMemcpyAsync(h->d_fs, &f, sizeof f, cudaMemcpyHostToDevice, h->stream));
   return GLMB_OK;
 }
 
@@ -629,12 +636,12 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
   const long long cap = p.fixed ? h->cap_comp : std::max(T, 1);
   CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
   prof_begin(h, kStageTable);
-  launch_check_finite(h->d_Z, h->d_fs, dz, h->d_scal + S_ERR, h->stream);
+  launch_check_finite(h->d_fs, dz, h->d_scal + S_ERR, h->stream);
   const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
-  launch_table_count(h->md, B, h->pt, h->d_fs, h->d_Z, gt, h->stream);
+  launch_table_count(h->md, B, h->pt, h->d_fs, gt, h->stream);
   scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR,
            h->stream);
-  launch_table_write(h->md, B, h->pt, h->d_fs, h->d_Z, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
+  launch_table_write(h->md, B, h->pt, h->d_fs, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
                      h->stream);
   const int gs = p.fixed ? 4 * h->n_sm : std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm));
   launch_parent_stats(h->hyps[h->hcur], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
@@ -987,7 +994,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   if (h->stage != 0) return fail(h, GLMB_E_STATE, "step: a frame is in progress");
   glmb_status st = stage_births(h, births, n_births);
   if (st != GLMB_OK) return st;
-  st = stage_detections(h, Z, M, z_is_device);
+  st = stage_detections(h, Z, M, z_is_device, false);
   if (st != GLMB_OK) return st;
   h->frame += 1;
   h->nb = n_births;
@@ -999,10 +1006,17 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
     h->frame -= 1;
     return fail(h, GLMB_E_CAPACITY, "step: per-hypothesis table does not fit in shared memory");
   }
-  if ((st = upload_sizes(h, 1)) != GLMB_OK) return st;
-  if (n_births)
-    CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
-                       cudaMemcpyHostToDevice, h->stream));
+  // the frame's sizes, births and host detections go up with the frame: as
+  // copy nodes of the graph when one is replayed, else as separate copies
+  if ((st = upload_sizes(h, 1, !p.fixed)) != GLMB_OK) return st;
+  if (!p.fixed) {
+    if (n_births)
+      CU(cudaMemcpyAsync(h->d_births, h->h_births, (size_t)n_births * kBirthRec * sizeof(double),
+                         cudaMemcpyHostToDevice, h->stream));
+    if (M > 0 && !z_is_device)
+      CU(cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)M * h->md.dz * sizeof(float), cudaMemcpyHostToDevice,
+                         h->stream));
+  }
   h->retained_valid = false;
   h->plan = p;
   if (p.fixed) {
@@ -1036,6 +1050,11 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       const auto t_cap = std::chrono::steady_clock::now();
       CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
+      cudaMemcpyAsync(h->d_fs, &h->h_fs[1], sizeof(FrameDev), cudaMemcpyHostToDevice, h->stream);
+      cudaMemcpyAsync(h->d_births, h->h_births, (size_t)h->cap_births * kBirthRec * sizeof(double),
+                      cudaMemcpyHostToDevice, h->stream);
+      cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)std::min(q.M, h->cap_meas) * h->md.dz * sizeof(float),
+                      cudaMemcpyHostToDevice, h->stream);
       enqueue_predict(h, q);
       enqueue_table(h, q);
       enqueue_expand(h, q);

@@ -66,7 +66,7 @@ struct FrameDev {
   int M;                  // detections
   int H;                  // parents (hypotheses before the update)
   int frame;              // frame number: birth labels and the random-number key
-  int pad[2];
+  const float* Z;         // detections [M][dz] (device memory)
 };
 
 struct CompTable {
@@ -129,6 +129,13 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 
 __device__ __forceinline__ uint32_t word_of(const uint4& r, int b) {
   return b == 0 ? r.x : b == 1 ? r.y : b == 2 ? r.z : r.w;
+}
+
+// Programmatic dependent launch: wait until the kernel this one depends on
+// has finished and its writes are visible (the next kernel is launched when
+// this one completes, without a separate launch round trip).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 __device__ __forceinline__ long long fx_of(float x) { return __float2ll_rn(x * kFxScale); }

@@ -10,6 +10,26 @@ namespace glmb {
 // kernels launched by this library (all handles), for the benchmark's count
 extern long long g_launches;
 
+// Launches kernel k with programmatic stream serialisation: its blocks may
+// start while the previous kernel in the stream finishes; every kernel of
+// the library begins with pdl_enter(), which waits for that kernel first.
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+  ++g_launches;
+}
+
 // ---- prediction, births, table (kernels_table.cu) ----
 // Sizes come from the device FrameDev; grid is the number of blocks of a
 // grid-stride launch.
@@ -17,12 +37,12 @@ extern long long g_launches;
 // appended at dst[n_comp..) (births_dev: per birth [r, mean[6], cov[36]] FP64)
 void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, const FrameDev* fs,
                     const double* births_dev, int grid, cudaStream_t s);
+// detections: fs->Z ([M][dz] floats on the device)
 void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, const float* Z, int grid, cudaStream_t s);
+                        const FrameDev* fs, int grid, cudaStream_t s);
 void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, const float* Z, unsigned* n_fp64, unsigned* err,
-                        int grid, cudaStream_t s);
-void launch_check_finite(const float* Z, const FrameDev* fs, int dz, unsigned* err, cudaStream_t s);
+                        const FrameDev* fs, unsigned* n_fp64, unsigned* err, int grid, cudaStream_t s);
+void launch_check_finite(const FrameDev* fs, int dz, unsigned* err, cudaStream_t s);
 void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
                          unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s);
 

@@ -645,6 +645,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 // SMEM: staged in shared memory and copied to the image (16-byte words).
 template <int DZ, bool SMEM>
 __global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H;
@@ -880,6 +881,7 @@ int expand_draw_smem(int threads) { return threads * (2 * kDrawDead + 8 * kDrawD
 // synchronisation: every thread draws its own child from the parent's image.
 template <int DZ>
 __global__ void __launch_bounds__(256) draw_kernel(const ExpandArgs a) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const int stride = blockDim.x;
   uint32_t* s_dv = reinterpret_cast<uint32_t*>(sm) + threadIdx.x;
@@ -1138,6 +1140,7 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
 // every child of every parent (a.warp_all), or the draw kernel's overflow.
 template <int DZ, bool MAT>
 __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const WLay WL = make_wlay(DZ, MAT, a.T_max);
@@ -1184,6 +1187,7 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
 // requested once per parent (one warp per first survivor of a parent).
 template <int DZ>
 __global__ void __launch_bounds__(256) mat_prep_kernel(const ExpandArgs a) {
+  pdl_enter();
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int lane = threadIdx.x & 31;
   const int HU = a.md.h_up;
@@ -1223,6 +1227,7 @@ __device__ __forceinline__ int dedup_table_size(int HU) {
 
 __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long* child_key,
                              const unsigned long long* __restrict__ child_hash, int8_t* child_status) {
+  pdl_enter();
   extern __shared__ unsigned long long s_k[];   // [ts] keys, 0 = empty
   const int ts = dedup_table_size(HU);
   uint32_t* s_n = reinterpret_cast<uint32_t*>(s_k + ts);   // [ts] lowest draw
@@ -1278,8 +1283,7 @@ void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsign
   while (ts < 2 * HU) ts <<= 1;
   const int smem = ts * 12;
   if (smem > 48 * 1024) cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  dedup_kernel<<<grid, 128, smem, s>>>(fs, HU, child_key, child_hash, child_status);
-  ++g_launches;
+  launch_k(dedup_kernel, grid, 128, smem, s, fs, HU, child_key, child_hash, child_status);
 }
 
 // ---- host side ----
@@ -1323,8 +1327,7 @@ int expand_occupancy(const ExpandArgs& a, ExpandKernel k, int threads, int smem)
 void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int threads, int smem,
                           cudaStream_t s) {
   if (grid <= 0) return;
-  kernel_of(a, k)<<<grid, threads, smem, s>>>(a);
-  ++g_launches;
+  launch_k(kernel_of(a, k), grid, threads, smem, s, a);
 }
 
 }  // namespace glmb

@@ -75,6 +75,7 @@ __device__ Lse block_lse(Lse v) {
 // fixed-point threshold log(tau) + LSE.
 __global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* __restrict__ fs,
                            int h_up, PruneWork w, double log_tau, int h_max) {
+  pdl_enter();
   __shared__ bool last;
   const long long n = (long long)fs->H * h_up;
   // per thread: running maximum and a compensated FP32 sum of exp(key - max)
@@ -152,7 +153,7 @@ __global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* _
 
 void launch_lse(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
                 int h_max, int nblk, cudaStream_t s) {
-  lse_kernel<<<nblk, kRedThreads, 0, s>>>(keys, fs, h_up, w, log_tau, h_max); ++g_launches;
+  launch_k(lse_kernel, nblk, kRedThreads, 0, s, keys, fs, h_up, w, log_tau, h_max);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,6 +165,7 @@ constexpr int kDigit = 12, kBins = 1 << kDigit;
 
 __global__ void radix_hist_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w, int shift) {
+  pdl_enter();
   __shared__ unsigned hist[kBins];
   const long long n = (long long)fs->H * h_up;
   if (w.sel[3] != 0) return;
@@ -185,6 +187,7 @@ __global__ void radix_hist_kernel(const long long* __restrict__ keys,
 }
 
 __global__ void radix_find_kernel(PruneWork w, int shift, int first) {
+  pdl_enter();
   // thread t owns bins [4t, 4t + 4) (blockDim.x == kBins / 4 == 1024);
   // the count of bins above a thread's range is total - inclusive prefix
   __shared__ unsigned wsum[32];
@@ -248,8 +251,8 @@ void launch_select(const long long* keys, const FrameDev* fs, int h_up, int nbit
   const int passes = (nbits + kDigit - 1) / kDigit;
   for (int p = 0; p < passes; ++p) {
     const int shift = (passes - 1 - p) * kDigit;
-    radix_hist_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w, shift); ++g_launches;
-    radix_find_kernel<<<1, kBins / 4, 0, s>>>(w, shift, p == 0); ++g_launches;
+    launch_k(radix_hist_kernel, nblk, 256, 0, s, keys, fs, h_up, w, shift);
+    launch_k(radix_find_kernel, 1, kBins / 4, 0, s, w, shift, p == 0);
   }
 }
 
@@ -268,6 +271,7 @@ __device__ __forceinline__ unsigned long long keep_bits(long long k, long long t
 
 __global__ void keep_flags_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w) {
+  pdl_enter();
   const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -277,6 +281,7 @@ __global__ void keep_flags_kernel(const long long* __restrict__ keys,
 
 __global__ void keep_write_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w, int h_max) {
+  pdl_enter();
   const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -293,10 +298,10 @@ __global__ void keep_write_kernel(const long long* __restrict__ keys,
 
 void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long long cap, PruneWork w,
                     int h_max, int nblk, cudaStream_t s) {
-  keep_flags_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w); ++g_launches;
+  launch_k(keep_flags_kernel, nblk, 256, 0, s, keys, fs, h_up, w);
   scan_u64(w.flags, w.flags, &fs->H, h_up, cap, (unsigned long long*)(w.counts + 4), false,
            w.flags_tmp, w.flags_tmp_cap, w.err, s);
-  keep_write_kernel<<<nblk, 256, 0, s>>>(keys, fs, h_up, w, h_max); ++g_launches;
+  launch_k(keep_write_kernel, nblk, 256, 0, s, keys, fs, h_up, w, h_max);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,6 +312,7 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
                                 const uint16_t* __restrict__ child_alive, HypTable parents,
                                 int h_up, HypTable out, int h_max, unsigned* err,
                                 long long cap_entries) {
+  pdl_enter();
   __shared__ long long s_n;
   __shared__ double s_lse;
   __shared__ uint32_t carry;
@@ -386,8 +392,8 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
                      const HypTable& parents, int h_up, HypTable out, int h_max, unsigned* err,
                      long long cap_entries, cudaStream_t s) {
-  finalize_kernel<<<1, 1024, 0, s>>>(w, keys, child_alive, parents, h_up, out, h_max, err,
-                                     cap_entries); ++g_launches;
+  launch_k(finalize_kernel, 1, 1024, 0, s, w, keys, child_alive, parents, h_up, out, h_max, err,
+                                     cap_entries);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,6 +403,7 @@ void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_a
 __global__ void mark_old_kernel(const uint32_t* __restrict__ out_comp,
                                 const unsigned* __restrict__ n_entries, long long cap,
                                 const unsigned* err, uint32_t* flag) {
+  pdl_enter();
   if (*(volatile const unsigned*)err & kErrFatal) return;
   const long long n = min((long long)*n_entries, cap);
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -409,7 +416,7 @@ __global__ void mark_old_kernel(const uint32_t* __restrict__ out_comp,
 void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
                      const unsigned* err, uint32_t* flag, cudaStream_t s) {
   const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
-  mark_old_kernel<<<nb, 256, 0, s>>>(out_comp, n_entries_dev, cap, err, flag); ++g_launches;
+  launch_k(mark_old_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, err, flag);
 }
 
 template <int DZ>
@@ -575,6 +582,7 @@ __global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t
                           const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,
                           int cap_upd, const unsigned* __restrict__ n_upd_dev,
                           const unsigned* __restrict__ n_surv_dev, unsigned* err) {
+  pdl_enter();
   if (*n_surv_dev == 0u || (*(volatile unsigned*)err & kErrFatal)) return;
   const int n_src = fs->T;
   const unsigned n_keep = *n_keep_dev;
@@ -607,19 +615,19 @@ void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTabl
                            const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
                            int grid, cudaStream_t s) {
   if (md.dz == 2) {
-    gc_kernel<2><<<grid, 128, 0, s>>>(md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+    launch_k(gc_kernel<2>, grid, 128, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
                                       upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
   } else {
-    gc_kernel<3><<<grid, 128, 0, s>>>(md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+    launch_k(gc_kernel<3>, grid, 128, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
                                       upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
   }
-  ++g_launches;
 }
 
 __global__ void remap_kernel(uint32_t* out_comp, const unsigned* __restrict__ n_entries,
                              long long cap, const uint32_t* __restrict__ newpos,
                              const uint32_t* __restrict__ hvals,
                              const unsigned* __restrict__ n_keep_dev, const unsigned* err) {
+  pdl_enter();
   if (*(volatile const unsigned*)err & kErrFatal) return;
   const long long n = min((long long)*n_entries, cap);
   const uint32_t n_keep = *n_keep_dev;
@@ -634,7 +642,7 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
                   const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
                   const unsigned* err, cudaStream_t s) {
   const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
-  remap_kernel<<<nb, 256, 0, s>>>(out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err); ++g_launches;
+  launch_k(remap_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -655,6 +663,7 @@ __device__ __forceinline__ unsigned long long w_fx(double logw) {
 // block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
 __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap,
                                 int* nb, unsigned long long* r_fx) {
+  pdl_enter();
   extern __shared__ unsigned long long s_pmf[];   // [pcap]
   __shared__ unsigned long long bw[32];
   __shared__ int bi[32];
@@ -732,6 +741,7 @@ __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
 __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev, CompTable ct, int dx,
                                  const int* __restrict__ nb, unsigned long long* r_fx, glmb_track* out,
                                  int cap, unsigned* done) {
+  pdl_enter();
   extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
   unsigned long long* s_r = s_key + cap;
   __shared__ bool last;
@@ -798,14 +808,14 @@ void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const Co
     cudaFuncSetAttribute(est_exist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
   }
   unsigned long long* r_fx = reinterpret_cast<unsigned long long*>(r);
-  est_card_kernel<<<1, 1024, (size_t)pcap * 8, s>>>(hp, H, H_dev, pmf, pcap, nb, r_fx); ++g_launches;
+  launch_k(est_card_kernel, 1, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_fx);
   const int blocks = H_dev ? 2 * n_sm : std::max(1, std::min((H + 7) / 8, 2 * n_sm));
-  est_exist_kernel<<<blocks, 256, (size_t)pcap * 16, s>>>(hp, H, H_dev, ct, dx, nb, r_fx, (glmb_track*)tracks,
+  launch_k(est_exist_kernel, blocks, 256, (size_t)pcap * 16, s, hp, H, H_dev, ct, dx, nb, r_fx, (glmb_track*)tracks,
                                                          pcap, done);
-  ++g_launches;
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   unsigned long long s = 0ull;
@@ -816,7 +826,7 @@ __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
 
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s) {
   if (M <= 0) return;
-  meas_assoc_kernel<<<(M + 127) / 128, 128, 0, s>>>(hp, H, M, r_u); ++g_launches;
+  launch_k(meas_assoc_kernel, (M + 127) / 128, 128, 0, s, hp, H, M, r_u);
 }
 
 }  // namespace glmb

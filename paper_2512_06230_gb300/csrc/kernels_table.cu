@@ -27,6 +27,7 @@ __device__ void predict_comp(const Model& md, const CompTable& src, const CompTa
 template <int DZ>
 __global__ void predict_kernel(Model md, CompTable src, CompTable ct, const FrameDev* __restrict__ fs,
                                const double* __restrict__ births) {
+  pdl_enter();
   const int n = fs->n_comp, nb = fs->nb, frame = fs->frame;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n + nb; c += gridDim.x * blockDim.x) {
     if (c < n) predict_comp<DZ>(md, src, ct, c);
@@ -113,11 +114,10 @@ __device__ void birth_comp(const Model& md, const CompTable& ct, int c, const do
 void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, const FrameDev* fs,
                     const double* births_dev, int grid, cudaStream_t s) {
   if (md.dz == 2) {
-    predict_kernel<2><<<grid, 128, 0, s>>>(md, src, dst, fs, births_dev);
+    launch_k(predict_kernel<2>, grid, 128, 0, s, md, src, dst, fs, births_dev);
   } else {
-    predict_kernel<3><<<grid, 128, 0, s>>>(md, src, dst, fs, births_dev);
+    launch_k(predict_kernel<3>, grid, 128, 0, s, md, src, dst, fs, births_dev);
   }
-  ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,9 +184,10 @@ __device__ __forceinline__ bool pair_eval(const Model& md, const CompGeom<DZ>& g
 }
 
 template <int DZ>
-__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt,
-                                   const FrameDev* __restrict__ fs, const float* __restrict__ Z) {
+__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const FrameDev* __restrict__ fs) {
+  pdl_enter();
   const int T = fs->T, M = fs->M;
+  const float* __restrict__ Z = fs->Z;
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps) {
@@ -224,10 +225,11 @@ __device__ void table_write_comp(const Model& md, const CompTable& ct, const Pai
                                  unsigned* err);
 
 template <int DZ>
-__global__ void table_write_kernel(Model md, CompTable ct, PairTable pt,
-                                   const FrameDev* __restrict__ fs, const float* __restrict__ Z,
+__global__ void table_write_kernel(Model md, CompTable ct, PairTable pt, const FrameDev* __restrict__ fs,
                                    unsigned* n_fp64, unsigned* err) {
+  pdl_enter();
   const int T = fs->T, M = fs->M;
+  const float* __restrict__ Z = fs->Z;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps)
     table_write_comp<DZ>(md, ct, pt, c, Z, M, n_fp64, err);
@@ -320,22 +322,20 @@ __device__ void table_write_comp(const Model& md, const CompTable& ct, const Pai
 }
 
 void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, const float* Z, int grid, cudaStream_t s) {
-  if (md.dz == 2) { table_count_kernel<2><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z); }
-  else { table_count_kernel<3><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z); }
-  ++g_launches;
+                        const FrameDev* fs, int grid, cudaStream_t s) {
+  if (md.dz == 2) { launch_k(table_count_kernel<2>, grid, 256, 0, s, md, ct, pt, fs); }
+  else { launch_k(table_count_kernel<3>, grid, 256, 0, s, md, ct, pt, fs); }
 }
 
 void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, const float* Z, unsigned* n_fp64, unsigned* err,
-                        int grid, cudaStream_t s) {
-  if (md.dz == 2) { table_write_kernel<2><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z, n_fp64, err); }
-  else { table_write_kernel<3><<<grid, 256, 0, s>>>(md, ct, pt, fs, Z, n_fp64, err); }
-  ++g_launches;
+                        const FrameDev* fs, unsigned* n_fp64, unsigned* err, int grid, cudaStream_t s) {
+  if (md.dz == 2) { launch_k(table_write_kernel<2>, grid, 256, 0, s, md, ct, pt, fs, n_fp64, err); }
+  else { launch_k(table_write_kernel<3>, grid, 256, 0, s, md, ct, pt, fs, n_fp64, err); }
 }
 
-__global__ void check_finite_kernel(const float* __restrict__ Z, const FrameDev* __restrict__ fs,
-                                    int dz, unsigned* err) {
+__global__ void check_finite_kernel(const FrameDev* __restrict__ fs, int dz, unsigned* err) {
+  pdl_enter();
+  const float* __restrict__ Z = fs->Z;
   const long long n = (long long)fs->M * dz;
   bool bad = false;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -344,13 +344,14 @@ __global__ void check_finite_kernel(const float* __restrict__ Z, const FrameDev*
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrInput);
 }
 
-void launch_check_finite(const float* Z, const FrameDev* fs, int dz, unsigned* err, cudaStream_t s) {
-  check_finite_kernel<<<16, 256, 0, s>>>(Z, fs, dz, err); ++g_launches;
+void launch_check_finite(const FrameDev* fs, int dz, unsigned* err, cudaStream_t s) {
+  launch_k(check_finite_kernel, 16, 256, 0, s, fs, dz, err);
 }
 
 // per-parent slot and table sizes (max over parents), births included
 __global__ void parent_stats_kernel(HypTable hp, const FrameDev* __restrict__ fs, PairTable pt,
                                     unsigned* max_T, unsigned* max_K) {
+  pdl_enter();
   __shared__ unsigned kb;
   const int H = fs->H, nb = fs->nb, birth_base = fs->n_comp;
   if (threadIdx.x == 0) {
@@ -370,7 +371,7 @@ __global__ void parent_stats_kernel(HypTable hp, const FrameDev* __restrict__ fs
 
 void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
                          unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s) {
-  parent_stats_kernel<<<grid, 128, 0, s>>>(hp, fs, pt, max_T, max_K); ++g_launches;
+  launch_k(parent_stats_kernel, grid, 128, 0, s, hp, fs, pt, max_T, max_K);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,6 +428,7 @@ constexpr long long kScanSpin = 1LL << 22;   // look-back wait limit (iterations
 template <typename T>
 __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T* total, int total_at_end,
                              T* work, int nw, unsigned* err) {
+  pdl_enter();
   __shared__ int s_tile;
   __shared__ T s_excl;
   T* ctr = work;
@@ -512,6 +514,7 @@ constexpr long long kScanSmall = (long long)kScanThreads * 64;
 template <typename T>
 __global__ void scan_small(const T* in, T* out, const int* n_dev, int mult, T* total,
                            int total_at_end) {
+  pdl_enter();
   const long long n = scan_len(n_dev, mult);
   const int per = (int)((n + kScanThreads - 1) / kScanThreads);
   const long long b = (long long)threadIdx.x * per;
@@ -540,8 +543,7 @@ template <typename T>
 static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long cap, T* total,
                       bool total_at_end, T* tmp, long long tmp_cap, unsigned* err, cudaStream_t s) {
   if (cap <= kScanSmall) {
-    scan_small<T><<<1, kScanThreads, 0, s>>>(in, out, n_dev, mult, total, total_at_end ? 1 : 0);
-    ++g_launches;
+    launch_k(scan_small<T>, 1, kScanThreads, 0, s, in, out, n_dev, mult, total, total_at_end ? 1 : 0);
     return;
   }
   const int nt = scan_tiles(cap), nw = scan_tiles(tmp_cap);
@@ -549,8 +551,7 @@ static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long
     cudaMemsetAsync(err, (int)kErrNumeric, 1, s);
     return;
   }
-  scan_onepass<T><<<nt, kScanThreads, 0, s>>>(in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err);
-  ++g_launches;
+  launch_k(scan_onepass<T>, nt, kScanThreads, 0, s, in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err);
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
