@@ -123,7 +123,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=100,
+                    help="untimed steps (the default, one pass of the scene, fills the graph cache)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scene", default="mid")
     ap.add_argument("--seed", type=int, default=None)
@@ -181,13 +182,11 @@ def main():
 
     host_times = []
 
-    def run(n_steps, start, host, profile=False, record=None):
+    def run(n_steps, start, host):
         """Runs n_steps frames starting at global step index `start`; returns
         per-step event times (ms) and per-step work counters."""
         times, work = [], []
         host_times.clear()
-        if profile:
-            f.set_profiling(["expand"])
         for s in range(start, start + n_steps):
             fi = s % F
             fr = sc.frames[fi]
@@ -221,7 +220,9 @@ def main():
                              d2h=est["n"] * 352 + 64 * 8))
         return times, work
 
-    # warm-up, then the timed steps
+    # warm-up, then the timed steps; the expansion is timed with events in
+    # every run (the same mask throughout, so the warm-up's graphs are reused)
+    f.set_profiling(["expand"])
     run(args.warmup, 0, host=False)
     torch.cuda.synchronize()
     if world > 1:
@@ -230,9 +231,11 @@ def main():
     th = threading.Thread(target=sample_clocks, args=(stop, clk_lines), daemon=True)
     th.start()
     time.sleep(0.3)
-    launches0 = f.info()["n_launches"]
+    info_t0 = f.info()
+    launches0 = info_t0["n_launches"]
     torch.cuda.synchronize()
-    times, work = run(args.steps, args.warmup, host=False, profile=True)
+    f.set_profiling(["expand"])   # clears the totals
+    times, work = run(args.steps, args.warmup, host=False)
     torch.cuda.synchronize()
     host_step_ms = 1e3 * sum(t[0] for t in host_times) / max(1, len(host_times))
     host_est_ms = 1e3 * sum(t[1] for t in host_times) / max(1, len(host_times))
@@ -241,7 +244,6 @@ def main():
     tim = f.timing()
     stop.set()
     th.join(timeout=10)
-    f.set_profiling([])
     total_ms = float(sum(times))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -295,6 +297,7 @@ def main():
         "gpu_launches": int(launches),
         "host_ms_per_step": {"step_call": round(host_step_ms, 4), "estimates_call": round(host_est_ms, 4)},
         "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
+                   "captured_in_timed_steps": info1["n_graph_captures"] - info_t0["n_graph_captures"],
                    "redone_frames": info1["n_redo"],
                    "capture_ms_total": round(info1["graph_capture_ms"], 3)},
         "expand_plan": {"smem_bytes": info1["expand_smem_bytes"],
@@ -302,7 +305,7 @@ def main():
                         "threads": info1["expand_threads"],
                         "T": info1["expand_plan_T"], "K": info1["expand_plan_K"],
                         "M": info1["expand_plan_M"]},
-        "roofline": {"bound": "alu", "kernel": "expand_kernel (child expansion + scoring)",
+        "roofline": {"bound": "alu", "kernel": "child expansion and scoring (stage_kernel, draw_kernel, warp_kernel, dedup_kernel of one frame)",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",
                      "frac": achieved / peak_ops if achieved else None, "traffic": None,

@@ -1077,7 +1077,7 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
       const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (ie != cudaSuccess) return fail(h, GLMB_E_CUDA, "step: graph instantiation: %s", cudaGetErrorString(ie));
-      if (h->graphs.size() >= 16) {
+      if (h->graphs.size() >= 32) {
         // evict the least recently replayed graph
         int lru = 0;
         for (int gi = 1; gi < (int)h->graphs.size(); ++gi)
