@@ -678,9 +678,23 @@ __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
     r_fx[n] = 0ull;   // existence sums of the next kernel
   }
   __syncthreads();
-  for (int h = tid; h < H; h += nthr) {
-    const int n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
-    if (n < pcap) atomicAdd(&s_pmf[n], w_fx(hp.logw[h]));
+  // one shared-memory atomic per distinct cardinality in a warp (most
+  // hypotheses share a few cardinalities)
+  for (int base = 0; base < H; base += nthr) {
+    const int h = base + tid;
+    int n = -1;
+    unsigned long long w = 0ull;
+    if (h < H) {
+      n = (int)(hp.ptr[h + 1] - hp.ptr[h]);
+      if (n < pcap) w = w_fx(hp.logw[h]);
+      else n = -1;
+    }
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, n);
+    // w < 2^41: the two 21-bit halves of 32 weights sum without overflow
+    const unsigned lo = __reduce_add_sync(grp, (unsigned)(w & 0x1FFFFFull));
+    const unsigned hi = __reduce_add_sync(grp, (unsigned)(w >> 21));
+    if (n >= 0 && lane == __ffs(grp) - 1)
+      atomicAdd(&s_pmf[n], ((unsigned long long)hi << 21) + lo);
   }
   __syncthreads();
   // argmax over bins (exact integer sums)

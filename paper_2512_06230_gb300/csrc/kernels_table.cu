@@ -452,36 +452,53 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
     }
     T tile_sum;
     T run = block_exclusive_scan<T>(sum, tile_sum);
-    if (threadIdx.x == 0) {
+    // warp 0 publishes the tile's sum and looks back 32 predecessors at a
+    // time: it adds published sums until it meets a published prefix
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
       T excl = 0;
       if (tile > 0) {
-        ((volatile T*)agg)[tile] = tile_sum;
-        __threadfence();
-        ((volatile T*)st)[tile] = (T)kStAgg;
-        for (int p = tile - 1; p >= 0;) {
-          T f = ((volatile T*)st)[p];
+        if (lane == 0) {
+          ((volatile T*)agg)[tile] = tile_sum;
+          __threadfence();
+          ((volatile T*)st)[tile] = (T)kStAgg;
+        }
+        int top = tile - 1;   // highest predecessor not yet added
+        bool done = false, gave_up = false;
+        while (!done && top >= 0) {
+          const int p = top - lane;
+          T f = p >= 0 ? ((volatile T*)st)[p] : (T)kStInc;
           long long spin = 0;
-          while (f == 0 && ++spin < kScanSpin) f = ((volatile T*)st)[p];
-          if (f == 0) {   // a predecessor never published: give up on this scan
-            atomicOr(err, kErrNumeric);
+          while (__any_sync(0xFFFFFFFFu, f == 0) && ++spin < kScanSpin)
+            if (f == 0) f = ((volatile T*)st)[p];
+          if (__any_sync(0xFFFFFFFFu, f == 0)) {   // a predecessor never published
+            gave_up = true;
             break;
           }
           __threadfence();
-          if (f == (T)kStInc) {
-            excl += ((volatile T*)inc)[p];
-            break;
-          }
-          excl += ((volatile T*)agg)[p];
-          --p;
+          // the nearest predecessor with a published prefix (lowest lane)
+          const unsigned inc_mask = __ballot_sync(0xFFFFFFFFu, p >= 0 && f == (T)kStInc);
+          const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+          T v = 0;
+          if (p >= 0 && lane <= stop)
+            v = (lane == stop && f == (T)kStInc) ? ((volatile T*)inc)[p] : ((volatile T*)agg)[p];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+          excl += v;
+          done = inc_mask != 0u;
+          top -= 32;
         }
+        if (gave_up && lane == 0) atomicOr(err, kErrNumeric);
       }
-      ((volatile T*)inc)[tile] = excl + tile_sum;
-      __threadfence();
-      ((volatile T*)st)[tile] = (T)kStInc;
-      s_excl = excl;
-      if (tile == ntiles - 1) {
-        if (total) *total = excl + tile_sum;
-        if (total_at_end) out[n] = excl + tile_sum;
+      if (lane == 0) {
+        ((volatile T*)inc)[tile] = excl + tile_sum;
+        __threadfence();
+        ((volatile T*)st)[tile] = (T)kStInc;
+        s_excl = excl;
+        if (tile == ntiles - 1) {
+          if (total) *total = excl + tile_sum;
+          if (total_at_end) out[n] = excl + tile_sum;
+        }
       }
     }
     __syncthreads();
