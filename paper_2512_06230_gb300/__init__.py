@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libglmb.so")
 HEADER = os.path.join(_ROOT, "include", "glmb.h")
 SOURCES = ["kernels_table.cu", "kernels_expand.cu", "kernels_prune.cu", "glmb_api.cu",
-           "select_static.cu"]
+           "select_static.cu", "select_cluster.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 

@@ -751,11 +751,14 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   CompTable& A = h->comps[h->cur];
   CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
   prof_begin(h, kStageSelect);
-  launch_lse(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nblk, s);
-  launch_select(h->child_key, h->d_fs, h_up, nbits, h->pw, nblk, s);
-  launch_compact(h->child_key, h->d_fs, h_up, n, h->pw, h->cap_h, nblk, s);
-  launch_finalize(h->pw, h->child_key, h->child_alive, P, h_up, O, h->cap_h, h->d_scal + S_ERR,
-                  h->cap_entries, s);
+  if (!launch_select_cluster(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nbits, h->child_alive, P, O,
+                             h->d_scal + S_ERR, h->cap_entries, s)) {
+    launch_lse(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nblk, s);
+    launch_select(h->child_key, h->d_fs, h_up, nbits, h->pw, nblk, s);
+    launch_compact(h->child_key, h->d_fs, h_up, n, h->pw, h->cap_h, nblk, s);
+    launch_finalize(h->pw, h->child_key, h->child_alive, P, h_up, O, h->cap_h, h->d_scal + S_ERR,
+                    h->cap_entries, s);
+  }
   prof_end(h, kStageSelect);
   CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), s));
   CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));

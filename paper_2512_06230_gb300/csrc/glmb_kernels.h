@@ -143,6 +143,14 @@ void launch_select(const long long* keys, const FrameDev* fs, int h_up, int nbit
                    int nblk, cudaStream_t s);
 void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long long cap, PruneWork w,
                     int h_max, int nblk, cudaStream_t s);
+// the whole of launch_lse + launch_select + launch_compact + launch_finalize
+// in one launch of a thread-block cluster (select_cluster.cu); false when
+// the device cannot run the cluster (the caller then launches the chain)
+bool launch_select_cluster(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
+                           int h_max, int nbits, const uint16_t* child_alive, const HypTable& parents,
+                           const HypTable& out, unsigned* err, long long cap_entries, cudaStream_t s);
+// cluster size the fused selection runs with (0: cannot run)
+int select_cluster_size();
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
                      const HypTable& parents, int h_up, HypTable out, int h_max,
                      unsigned* err, long long cap_entries, cudaStream_t s);
