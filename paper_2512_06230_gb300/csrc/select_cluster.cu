@@ -144,44 +144,42 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
     }
   }
   cl.sync();
-  if (tid == 0) {
-    // the CTAs' partials in rank order: the same result in every CTA
-    long long M = kKeyInvalid;
-    double sum = 0.0;
+  if (wp == 0) {
+    // lane r holds CTA r's partial; maximum, rescale, sum over a fixed tree:
+    // the same result in every CTA
+    long long bm = kKeyInvalid;
+    double bs = 0.0;
     unsigned cnt = 0;
-    for (int r = 0; r < C; ++r) {
-      const SelShared* R = cl.map_shared_rank(&S, r);
-      cnt += R->pc;
-      const long long bm = R->pm;
-      const double bs = R->ps;
-      if (bm == kKeyInvalid || !(bs > 0.0)) continue;
-      if (M == kKeyInvalid) {
-        M = bm;
-        sum = bs;
-      } else if (bm > M) {
-        sum = bs + sum * (double)expf(fx_to_f(M - bm));
-        M = bm;
+    if (lane < C) {
+      const SelShared* R = cl.map_shared_rank(&S, lane);
+      bm = R->pm;
+      bs = R->ps;
+      cnt = R->pc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    const long long M = warp_max_k((bm == kKeyInvalid || !(bs > 0.0)) ? kKeyInvalid : bm);
+    double r = (bm == kKeyInvalid || !(bs > 0.0) || M == kKeyInvalid) ? 0.0 : bs * (double)expf(fx_to_f(bm - M));
+    const double sum = warp_sum_dd(r);
+    if (lane == 0) {
+      S.prefix = 0;
+      S.need = h_max;
+      S.bnd = 0;
+      if (M == kKeyInvalid || !(sum > 0.0)) {
+        S.lse = -INFINITY;
+        S.thr = LLONG_MAX;
+        S.mode = 2;
       } else {
-        sum += bs * (double)expf(fx_to_f(bm - M));
+        const double lse = (double)M * kFxInv + log(sum);
+        S.lse = lse;
+        S.thr = (long long)ceil((lse + log_tau) * 4294967296.0);
+        S.mode = 0;
       }
-    }
-    S.prefix = 0;
-    S.need = h_max;
-    S.bnd = 0;
-    if (M == kKeyInvalid || !(sum > 0.0)) {
-      S.lse = -INFINITY;
-      S.thr = LLONG_MAX;
-      S.mode = 2;
-    } else {
-      const double lse = (double)M * kFxInv + log(sum);
-      S.lse = lse;
-      S.thr = (long long)ceil((lse + log_tau) * 4294967296.0);
-      S.mode = 0;
-    }
-    if (rank == 0) {
-      w.lse[0] = S.lse;
-      w.thr[0] = S.thr;
-      w.counts[2] = cnt;
+      if (rank == 0) {
+        w.lse[0] = S.lse;
+        w.thr[0] = S.thr;
+        w.counts[2] = cnt;
+      }
     }
   }
   __syncthreads();
@@ -198,12 +196,20 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
     for (int b = tid; b < kSelBins; b += nthr) S.hist[b] = 0u;
     __syncthreads();
     const unsigned long long prefix = (unsigned long long)S.prefix;
-    for (long long j = lo + tid; j < hi; j += nthr) {
-      const long long k = keys[j];
-      if (k == kKeyInvalid || k < thr) continue;
-      const unsigned long long v = (unsigned long long)(k - thr);
-      if ((v >> (shift + kSelDigit)) != prefix) continue;
-      atomicAdd(&S.hist[(v >> shift) & (kSelBins - 1)], 1u);
+    // one shared-memory atomic per distinct bin of a warp (the keys near the
+    // top crowd a few bins)
+    for (long long base = lo; base < hi; base += nthr) {
+      const long long j = base + tid;
+      int bin = -1;
+      if (j < hi) {
+        const long long k = keys[j];
+        if (k != kKeyInvalid && k >= thr) {
+          const unsigned long long v = (unsigned long long)(k - thr);
+          if ((v >> (shift + kSelDigit)) == prefix) bin = (int)((v >> shift) & (kSelBins - 1));
+        }
+      }
+      const unsigned grp = __match_any_sync(0xFFFFFFFFu, bin);
+      if (bin >= 0 && lane == __ffs(grp) - 1) atomicAdd(&S.hist[bin], (unsigned)__popc(grp));
     }
     cl.sync();
     // this CTA's slice of the summed histogram
@@ -303,15 +309,18 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
   const unsigned long long excl_blk = (wp > 0 ? S.part[wp - 1] : 0ull) + x - mine;
   if (tid == 0) S.cnt = S.part[nw - 1];
   cl.sync();
-  if (tid == 0) {
-    unsigned long long before = 0ull, total = 0ull;
-    for (int r = 0; r < C; ++r) {
-      const unsigned long long c = cl.map_shared_rank(&S, r)->cnt;
-      if (r < rank) before += c;
-      total += c;
+  if (wp == 0) {
+    const unsigned long long c = lane < C ? cl.map_shared_rank(&S, lane)->cnt : 0ull;
+    unsigned long long before = lane < rank ? c : 0ull, total = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      before += __shfl_xor_sync(0xFFFFFFFFu, before, o);
+      total += __shfl_xor_sync(0xFFFFFFFFu, total, o);
     }
-    S.before = before;
-    S.total = total;
+    if (lane == 0) {
+      S.before = before;
+      S.total = total;
+    }
   }
   __syncthreads();
   {
@@ -326,8 +335,7 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
       if (pos < h_max) w.surv_idx[pos] = j;
     }
   }
-  __threadfence();
-  cl.sync();   // every survivor index is written
+  cl.sync();   // every survivor index is written (the cluster barrier orders them)
   if (rank != 0) return;
 
   // ---- 4: the retained set ----
@@ -350,11 +358,39 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
   __syncthreads();
   const long long ns = s_n;
   const double lse_all = S.lse;
+  // each thread's survivors (one per thread when ns <= blockDim.x): every
+  // load issued together
+  constexpr int kPer = 4;
+  long long sj[kPer], sk[kPer];
+  uint32_t sna[kPer];
+  unsigned long long suid[kPer];
+  const int rounds = (int)((ns + nthr - 1) / nthr);
+  const bool held = rounds <= kPer;
   {
     long long m = kKeyInvalid;
     double s = 0.0;
-    for (long long t = tid; t < ns; t += nthr) {
-      const long long k = keys[w.surv_idx[t]];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      sj[r] = 0;
+      sk[r] = 0;
+      sna[r] = 0;
+      suid[r] = 0;
+    }
+    for (int r = 0; r < rounds; ++r) {
+      const long long t = (long long)r * nthr + tid;
+      if (t >= ns) break;
+      const long long j = w.surv_idx[t];
+      const long long k = keys[j];
+      if (held) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q)
+          if (q == r) {
+            sj[q] = j;
+            sk[q] = k;
+            sna[q] = child_alive[j];
+            suid[q] = parents.uid[j / h_up];
+          }
+      }
       if (m == kKeyInvalid) { m = k; s = 1.0; }
       else if (k > m) { s = 1.0 + s * (double)expf(fx_to_f(m - k)); m = k; }
       else s += (double)expf(fx_to_f(k - m));
@@ -373,24 +409,45 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
     r = warp_sum_dd(r);
     if (lane == 0) S.dpart[wp] = r;
     __syncthreads();
-    if (tid == 0) {
-      double q2 = 0.0;
-      for (int k = 0; k < nw; ++k) q2 += S.dpart[k];
-      s_lse = (double)M * kFxInv - lse_all + log(q2);
-      w.lse[1] = s_lse;
+    if (wp == 0) {
+      double q2 = lane < nw ? S.dpart[lane] : 0.0;
+      q2 = warp_sum_dd(q2);
+      if (lane == 0) {
+        s_lse = (double)M * kFxInv - lse_all + log(q2);
+        w.lse[1] = s_lse;
+      }
     }
     __syncthreads();
   }
-  for (long long base = 0; base < ns; base += nthr) {
-    const long long t = base + tid;
+  uint32_t amax = 0;
+  for (int r = 0; r < rounds; ++r) {
+    const long long t = (long long)r * nthr + tid;
     uint32_t na = 0;
     if (t < ns) {
-      const long long j = w.surv_idx[t];
-      out.logw[t] = (double)keys[j] * kFxInv - lse_all - s_lse;
-      const long long hpar = j / h_up, nd = j % h_up;
-      out.uid[t] = mix64(parents.uid[hpar] + 0x9E3779B97F4A7C15ULL * (unsigned long long)(nd + 1));
-      na = child_alive[j];
-      atomicMax(&w.counts[3], na);
+      long long j, k;
+      unsigned long long pu;
+      if (held) {
+        j = sj[0];
+        k = sk[0];
+        na = sna[0];
+        pu = suid[0];
+#pragma unroll
+        for (int q = 1; q < kPer; ++q)
+          if (q == r) {
+            j = sj[q];
+            k = sk[q];
+            na = sna[q];
+            pu = suid[q];
+          }
+      } else {
+        j = w.surv_idx[t];
+        k = keys[j];
+        na = child_alive[j];
+        pu = parents.uid[j / h_up];
+      }
+      out.logw[t] = (double)k * kFxInv - lse_all - s_lse;
+      out.uid[t] = mix64(pu + 0x9E3779B97F4A7C15ULL * (unsigned long long)(j % h_up + 1));
+      amax = max(amax, na);
     }
     uint32_t y = na;
 #pragma unroll
@@ -416,6 +473,9 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
     if (tid == 0) carry += S.hist[nw - 1];
     __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, o));
+  if (lane == 0 && amax) atomicMax(&w.counts[3], amax);
   if (tid == 0) {
     out.ptr[ns] = carry;
     w.counts[1] = carry;
