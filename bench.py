@@ -43,6 +43,26 @@ UNIT = "frames/s"
 INT_PEAK_NOTE = "152 SMs x 128 lanes x 2070 MHz"
 
 
+def expansion_traffic():
+    """DRAM bytes per frame of the expansion kernels from the committed ncu
+    summary, or None when the kernels changed since it was captured."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        txt = open(os.path.join(here, "profiles", "expansion_traffic_mid.md")).read()
+        src = open(os.path.join(here, "paper_2512_06230_gb300", "csrc", "kernels_expand.cu"), "rb").read()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(("#", " ", "`")))
+    want = vals.get("kernels_expand.cu sha256 (first 16 hex)", "").strip()
+    if want != hashlib.sha256(src).hexdigest()[:16]:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_frame"])
+    except (KeyError, ValueError):
+        return None
+
+
 def scene_for_rank(args, rank):
     p = scenes.preset(args.scene)
     return scenes.make_scene(p, 1000 * 2 + rank if args.seed is None else args.seed + rank)
@@ -131,6 +151,8 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
+    ap.add_argument("--profile-frames", type=int, default=0,
+                    help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -176,6 +198,16 @@ def main():
     Zdev = [torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
             for fr in sc.frames]
     Bhost = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+    if args.profile_frames:
+        for k in range(args.profile_frames):
+            fr = sc.frames[k % F]
+            if k % F == 0:
+                f.reset()
+            f.step(Bhost[k % F], Zdev[k % F], device=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_frames": args.profile_frames, "info": {
+            k: v for k, v in f.info().items() if isinstance(v, (int, float))}}))
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     h_up = cfg["h_up"]
@@ -308,7 +340,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "child expansion and scoring (stage_kernel, draw_kernel, warp_kernel, dedup_kernel of one frame)",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",
-                     "frac": achieved / peak_ops if achieved else None, "traffic": None,
+                     "frac": achieved / peak_ops if achieved else None, "traffic": expansion_traffic(),
                      "peak_source": INT_PEAK_NOTE,
                      "kernel_ms_per_step": exp_ms / max(exp_calls, 1),
                      "kernel_share_of_step": exp_ms / total_ms if total_ms else None},
