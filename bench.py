@@ -139,6 +139,67 @@ def run_oracle(args, sc, cfg, budget_s):
         f"from the initial GLMB ({dt:.1f} s, {threads} threads)"
 
 
+def batch_cfg(p, sc):
+    return sc.filter_config(max_meas=int(p.n_objects * 0.9 * 6 + 4 * p.clutter_rate + 64),
+                            max_births=64, max_tracks=p.n_objects + 48,
+                            max_components=40 * (p.n_objects + 48), max_pairs=1 << 20)
+
+
+def run_batch(args, glmb, torch, dev):
+    """The batched form: --scenes independent scenes per frame (N ~ U{5..300},
+    H ~ U{100..5000}, clutter ~ U(5, 40)), --steps frames each, stepped together
+    by glmb_step_batch (each filter on its own stream), against the plain
+    path stepping the same scenes one after another.  One untimed pass fills
+    the graph caches; the filters are then reset and the second pass timed
+    (host wall clock, every scene's results synchronised each frame)."""
+    F = args.steps
+    specs = scenes.batch_scenes(args.scenes, 4000 if args.seed is None else args.seed, frames=F)
+    scs = [scenes.make_scene(p, s) for p, s in specs]
+    cfgs = [batch_cfg(p, sc) for (p, _), sc in zip(specs, scs)]
+    Z = [[torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, 2), device=dev)
+          for fr in sc.frames] for sc in scs]
+    B = [[glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames] for sc in scs]
+    torch.cuda.synchronize()
+
+    def run_pass(filters, batched):
+        t = 0.0
+        for k in range(F):
+            t0 = time.perf_counter()
+            if batched:
+                glmb.step_batch(filters, [(B[i][k], Z[i][k]) for i in range(len(filters))], device=True)
+            else:
+                for i, f in enumerate(filters):
+                    f.step(B[i][k], Z[i][k], device=True)
+            for f in filters:
+                f.estimates(cap=f.cfg["max_tracks"], pmf_cap=64)
+            t += time.perf_counter() - t0
+        return t
+
+    out = {}
+    for name, batched in (("sequential", False), ("batched", True)):
+        filters = [glmb.Filter(c) for c in cfgs]
+        run_pass(filters, batched)               # warm-up pass (graph captures)
+        for f in filters:
+            f.reset()
+        t = run_pass(filters, batched)
+        work = sum(f.info()["n_children"] for f in filters)   # the last frame's
+        out[name] = dict(seconds=t, scene_frames_per_s=len(filters) * F / t,
+                         children_per_frame=work)
+        for f in filters:
+            f.close()
+        torch.cuda.synchronize()
+    line = {"metric": "scene-frames/s, batched multi-scene GLMB (1 GB300)",
+            "value": out["batched"]["scene_frames_per_s"], "unit": "scene-frames/s", "n_gpus": 1,
+            "steps": F, "warmup": F, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.scenes} scenes x {F} frames, N~U{{5..300}}, H~U{{100..5000}}, "
+                                   "clutter~U(5,40), 2-D CV",
+                       "h_max": [p.h_max for p, _ in specs], "n_objects": [p.n_objects for p, _ in specs]},
+            "sequential": out["sequential"], "batched": out["batched"],
+            "speedup_vs_sequential": out["batched"]["scene_frames_per_s"] / out["sequential"]["scene_frames_per_s"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,6 +212,8 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
+    ap.add_argument("--scenes", type=int, default=64,
+                    help="--scene batch: independent scenes per frame")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
@@ -188,6 +251,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     glmb.load()
+
+    if args.scene == "batch":
+        return run_batch(args, glmb, torch, dev)
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)

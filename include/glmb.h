@@ -82,6 +82,9 @@ typedef struct {
   int64_t max_pairs;        /* capacity: gated (component, detection) pairs per frame;
                                0 selects 16 per component */
   void* stream;             /* cudaStream_t, or NULL */
+  int64_t max_components;   /* capacity: distinct Gaussian components (tracks are
+                               shared between hypotheses); 0 selects
+                               h_max * max_tracks + max_births */
 } glmb_config;
 
 /* An LMB birth component (Section 3): existence r, Gaussian density. */
@@ -259,6 +262,49 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
  * and the number of timed calls (n entries each; either pointer may be
  * NULL); it synchronises. */
 glmb_status glmb_set_profiling(glmb_handle* h, unsigned stage_mask);
+
+/* glmb_step in two halves, so that frames of several handles (each on its
+ * own stream) run on the GPU at the same time: glmb_step_enqueue launches
+ * the frame and returns; glmb_step_finish waits for it and commits it (or
+ * redoes or abandons it, as glmb_step would).  No other call on the handle
+ * is allowed in between.  Errors: as glmb_step; GLMB_E_STATE from finish
+ * without an enqueued frame. */
+glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z,
+                              int M, int z_is_device);
+glmb_status glmb_step_finish(glmb_handle* h);
+
+/* One frame of n independent filters (scenes): every frame is enqueued,
+ * then every frame finished.  Handles created with their own streams (the
+ * default when glmb_config.stream is NULL) run concurrently.  status[i]
+ * (nullable) receives scene i's result; the return value is the first
+ * error, or GLMB_OK.  Not part of the paper's method: the batched form. */
+typedef struct {
+  const glmb_birth* births;
+  int32_t n_births;
+  int32_t z_is_device;
+  const float* Z;
+  int32_t M;
+  int32_t pad;
+} glmb_frame_in;
+glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* frames, glmb_status* status);
+
+/* Launch shapes (not part of the method; results do not depend on them):
+ *   thread_warps_per_sm  draw one thread per child once the children give
+ *                        every SM this many warps (default 4);
+ *   draw_threads         threads per draw CTA (32..256, multiple of 32; 0:
+ *                        h_up rounded up to a warp, at most 256);
+ *   warp_cta_warps       most warps per CTA of the one-warp-per-child kernel
+ *                        (1..16, default 16);
+ *   stage_threads        threads per staging CTA (32..256, default 128).
+ * Setting them drops the captured graphs. */
+typedef struct {
+  int32_t thread_warps_per_sm;
+  int32_t draw_threads;
+  int32_t warp_cta_warps;
+  int32_t stage_threads;
+} glmb_tuning;
+glmb_status glmb_set_tuning(glmb_handle* h, const glmb_tuning* t);
+glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
 
 /* Launch-path overrides, for tests and tuning (not part of the paper's
  * method).  The paths compute the same arithmetic, so children's keys,

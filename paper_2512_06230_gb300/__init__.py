@@ -81,7 +81,7 @@ class GlmbConfig(C.Structure):
                 ("gate", C.c_double), ("h_max", C.c_int32), ("h_up", C.c_int32), ("tau", C.c_double),
                 ("seed", C.c_uint64), ("score_mode", C.c_int32), ("max_tracks", C.c_int32),
                 ("max_meas", C.c_int32), ("max_births", C.c_int32), ("max_pairs", C.c_int64),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("max_components", C.c_int64)]
 
 
 class GlmbBirth(C.Structure):
@@ -103,6 +103,18 @@ class GlmbInfo(C.Structure):
                 ("expand_ctas_per_sm", C.c_int32), ("expand_plan_T", C.c_int32),
                 ("expand_plan_K", C.c_int32), ("expand_plan_M", C.c_int32),
                 ("expand_threads", C.c_int32), ("graph_capture_ms", C.c_double)]
+
+
+class GlmbTuning(C.Structure):
+    """Launch shapes (glmb_tuning); results do not depend on them."""
+    _fields_ = [("thread_warps_per_sm", C.c_int32), ("draw_threads", C.c_int32),
+                ("warp_cta_warps", C.c_int32), ("stage_threads", C.c_int32)]
+
+
+class GlmbFrameIn(C.Structure):
+    """One scene's frame for glmb_step_batch."""
+    _fields_ = [("births", C.c_void_p), ("n_births", C.c_int32), ("z_is_device", C.c_int32),
+                ("Z", C.c_void_p), ("M", C.c_int32), ("pad", C.c_int32)]
 
 
 # NumPy views of the ABI records (same layout as the C structs)
@@ -145,6 +157,8 @@ def load() -> C.CDLL:
         "glmb_set_profiling": [P, C.c_uint], "glmb_get_timing": [P, P, P, I],
         "glmb_get_retained": [P, P, P, I, P],
         "glmb_step": [P, P, I, P, I, I], "glmb_set_step_estimates": [P, I], "glmb_set_launch_options": [P, C.c_uint],
+        "glmb_step_enqueue": [P, P, I, P, I, I], "glmb_step_finish": [P],
+        "glmb_step_batch": [P, I, P, P], "glmb_set_tuning": [P, P], "glmb_get_tuning": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -183,6 +197,7 @@ def make_config(cfg: dict, stream: Optional[int] = None) -> GlmbConfig:
     c.max_meas = int(cfg.get("max_meas", 0))
     c.max_births = int(cfg.get("max_births", 0))
     c.max_pairs = int(cfg.get("max_pairs", 0))
+    c.max_components = int(cfg.get("max_components", 0))
     c.stream = stream
     return c
 
@@ -294,6 +309,37 @@ class Filter:
 
     def prune(self):
         self._check(self.lib.glmb_prune(self.h))
+
+    def _frame_args(self, births, Z, device):
+        arr = self._births(births)
+        if device:
+            M = int(Z.shape[0])
+            return arr, len(births), C.c_void_p(Z.data_ptr()), M, 1, None
+        Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
+        return arr, len(births), _ptr(Zf), len(Zf), 0, Zf
+
+    def step_enqueue(self, births, Z, device: bool = False):
+        """Launches one frame (glmb_step_enqueue); step_finish completes it.
+        Host arrays are kept alive until then."""
+        arr, nb, zp, M, dev, keep = self._frame_args(births, Z, device)
+        self.M = M
+        self._inflight = (arr, keep, Z)
+        self._check(self.lib.glmb_step_enqueue(self.h, _ptr(arr), nb, zp, M, dev))
+
+    def step_finish(self):
+        self._check(self.lib.glmb_step_finish(self.h))
+        self._inflight = None
+
+    def tuning(self) -> dict:
+        t = GlmbTuning()
+        self._check(self.lib.glmb_get_tuning(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in GlmbTuning._fields_}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = GlmbTuning(**cur)
+        self._check(self.lib.glmb_set_tuning(self.h, C.byref(t)))
 
     def step(self, births, Z, device: bool = False):
         """One frame in one call (glmb_step: a replayed CUDA graph)."""
@@ -445,3 +491,26 @@ class Filter:
         self._check(self.lib.glmb_get_children(self.h, _ptr(logw), _ptr(st), _ptr(na), max(k, 1),
                                                C.byref(n)))
         return dict(logw=logw[:k], status=st[:k], n_alive=na[:k])
+
+
+def step_batch(filters, frames, device: bool = False):
+    """One frame of several independent filters (glmb_step_batch): all are
+    launched, then all completed, so that their graphs overlap on the GPU.
+    frames: a list of (births, Z) per filter.  Raises on the first error."""
+    n = len(filters)
+    if n == 0:
+        return
+    lib = filters[0].lib
+    hs = (C.c_void_p * n)(*[f.h for f in filters])
+    ins = (GlmbFrameIn * n)()
+    keep = []
+    for i, (f, (births, Z)) in enumerate(zip(filters, frames)):
+        arr, nb, zp, M, dev, zf = f._frame_args(births, Z, device)
+        keep.append((arr, zf, Z))
+        f.M = M
+        ins[i] = GlmbFrameIn(arr.ctypes.data if len(arr) else None, nb, dev, zp, M, 0)
+    st = (C.c_int * n)()
+    rc = lib.glmb_step_batch(hs, n, ins, st)
+    if rc != 0:
+        bad = next(i for i in range(n) if st[i] != 0)
+        raise GlmbError(st[bad], f"scene {bad}: " + lib.glmb_last_error(filters[bad].h).decode())

@@ -64,7 +64,7 @@ struct glmb_handle {
   int H = 1;
   long long n_entries = 0;
   int frame = 0;
-  int stage = 0;            // 0 ready for predict, 1 predicted, 2 updated
+  int stage = 0;            // 0 ready for predict, 1 predicted, 2 updated, 3 step in flight
   // last frame
   int nb = 0, T_work = 0, M = 0, H_par = 0, par_buf = 0, birth_base = 0;
   bool have_update = false, theta_M_valid = false, retained_valid = false;
@@ -107,6 +107,7 @@ struct glmb_handle {
   long long gen = 0, est_gen = -1;
   bool step_estimates = true;
   unsigned launch_opts = 0;   // GLMB_OPT_* overrides
+  glmb_tuning tune{4, 0, 16, 128};   // launch shapes (glmb_set_tuning)
   unsigned* h_cnt = nullptr;   // pinned copy of the prune counters
   double* d_ru = nullptr;
   // stage timing
@@ -402,10 +403,10 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
     return GLMB_E_INVALID;
   }
   h->cap_entries = (long long)h->cap_h * h->max_tracks;
-  h->cap_comp = h->cap_entries + h->cap_births;
+  h->cap_comp = c.max_components > 0 ? c.max_components : h->cap_entries + h->cap_births;
   h->cap_pairs = c.max_pairs > 0 ? c.max_pairs : 16 * h->cap_comp;
   h->cap_children = (long long)h->cap_h * c.h_up;
-  h->cap_upd = h->cap_entries;
+  h->cap_upd = std::min(h->cap_entries, h->cap_comp);
   const long long hcap = next_pow2(2 * h->cap_entries);
   h->hmask = (uint32_t)(hcap - 1);
   if (h->cap_comp >= (1LL << 31) || hcap > (1LL << 31) || h->cap_pairs >= (1LL << 32)) {
@@ -704,10 +705,11 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   const int img = (int)a.img_stride;
   // stage: one 128-thread CTA per parent
   const int st_smem = p.smem ? img : 0;
-  const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, 128, st_smem));
+  const int st_thr = h->tune.stage_threads;
+  const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
   // draws: one thread per child, blocks of up to 256 draws of one parent
-  const int d_thr = std::min(256, round_up(h_up, 32));
+  const int d_thr = h->tune.draw_threads > 0 ? h->tune.draw_threads : std::min(256, round_up(h_up, 32));
   const int nsl = (h_up + d_thr - 1) / d_thr;
   const int d_smem = expand_draw_smem(d_thr);
   const int d_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kDraw, d_thr, d_smem));
@@ -728,7 +730,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   h->exp_plan[3] = p.thread ? d_thr : w_thr;
   prof_begin(h, kStageExpand);
   CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, sizeof(unsigned), s));
-  launch_expand_kernel(a, ExpandKernel::kStage, st_grid, 128, st_smem, s);
+  launch_expand_kernel(a, ExpandKernel::kStage, st_grid, st_thr, st_smem, s);
   if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
   launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
   launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status,
@@ -819,13 +821,13 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   const int dz = h->md.dz;
   // one thread per child once the children give every SM four warps (the
   // register lists address pairs with 16 bits); else one warp per child
-  p.thread = (long long)h->H * h->cfg.h_up >= 4LL * 32 * h->n_sm;
+  p.thread = (long long)h->H * h->cfg.h_up >= (long long)h->tune.thread_warps_per_sm * 32 * h->n_sm;
   if (h->launch_opts & GLMB_OPT_DRAW_THREAD) p.thread = true;
   if (h->launch_opts & GLMB_OPT_DRAW_WARP) p.thread = false;
   p.thread = p.thread && p.K <= 65536;
   p.smem = expand_image_bytes(dz, p.T, p.K, p.M) <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL);
   p.Gw = p.Gm = 0;
-  for (int g = 16; g >= 1 && !p.Gw; --g)
+  for (int g = h->tune.warp_cta_warps; g >= 1 && !p.Gw; --g)
     if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
   for (int g = 8; g >= 1 && !p.Gm; --g)
     if (expand_warp_smem(dz, 1, p.T, g) <= h->smem_limit) p.Gm = g;
@@ -991,8 +993,8 @@ glmb_status glmb_prune(glmb_handle* h) {
   return finish_frame(h);
 }
 
-glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
-                      int z_is_device) {
+glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
+                              int z_is_device) {
   if (!h) return GLMB_E_INVALID;
   if (h->stage != 0) return fail(h, GLMB_E_STATE, "step: a frame is in progress");
   glmb_status st = stage_births(h, births, n_births);
@@ -1116,8 +1118,59 @@ glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, co
   h->par_buf = h->hcur;
   h->birth_base = h->n_comp;
   h->have_update = true;
+  h->stage = 3;   // in flight: glmb_step_finish
+  return GLMB_OK;
+}
+
+glmb_status glmb_step_finish(glmb_handle* h) {
+  if (!h) return GLMB_E_INVALID;
+  if (h->stage != 3) return fail(h, GLMB_E_STATE, "step_finish: no frame in flight");
   h->stage = 2;
   return finish_frame(h, true, h->step_estimates);
+}
+
+glmb_status glmb_step(glmb_handle* h, const glmb_birth* births, int n_births, const float* Z, int M,
+                      int z_is_device) {
+  glmb_status st = glmb_step_enqueue(h, births, n_births, Z, M, z_is_device);
+  if (st != GLMB_OK) return st;
+  return glmb_step_finish(h);
+}
+
+glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* frames, glmb_status* status) {
+  if (n < 0 || (n > 0 && (!hs || !frames))) return GLMB_E_INVALID;
+  glmb_status first = GLMB_OK;
+  for (int i = 0; i < n; ++i) {
+    const glmb_frame_in& f = frames[i];
+    const glmb_status st = glmb_step_enqueue(hs[i], f.births, f.n_births, f.Z, f.M, f.z_is_device);
+    if (status) status[i] = st;
+    if (st != GLMB_OK && first == GLMB_OK) first = st;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || hs[i]->stage != 3) continue;
+    const glmb_status st = glmb_step_finish(hs[i]);
+    if (status) status[i] = st;
+    if (st != GLMB_OK && first == GLMB_OK) first = st;
+  }
+  return first;
+}
+
+glmb_status glmb_set_tuning(glmb_handle* h, const glmb_tuning* t) {
+  if (!h || !t) return GLMB_E_INVALID;
+  if (t->thread_warps_per_sm < 0 || t->warp_cta_warps < 1 || t->warp_cta_warps > 16 ||
+      (t->draw_threads != 0 && (t->draw_threads < 32 || t->draw_threads > 256 || t->draw_threads % 32)) ||
+      t->stage_threads < 32 || t->stage_threads > 256 || t->stage_threads % 32)
+    return fail(h, GLMB_E_INVALID, "set_tuning: a launch shape out of range");
+  cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  h->tune = *t;
+  return GLMB_OK;
+}
+
+glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t) {
+  if (!h || !t) return GLMB_E_INVALID;
+  *t = h->tune;
+  return GLMB_OK;
 }
 
 glmb_status glmb_get_retained(glmb_handle* h, int64_t* child_idx, double* logw, int cap, int* n) {
@@ -1169,7 +1222,7 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
 glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out, double* card_pmf,
                            int pmf_cap) {
   if (!h || !n_out || (cap > 0 && !out)) return GLMB_E_INVALID;
-  if (h->stage == 2) return fail(h, GLMB_E_STATE, "estimates: call glmb_prune first");
+  if (h->stage >= 2) return fail(h, GLMB_E_STATE, "estimates: call glmb_prune (or glmb_step_finish) first");
   cudaStream_t s = h->stream;
   const int pcap = h->max_tracks + 1;
   if (h->est_gen != h->gen) {   // not computed with this state's step
@@ -1193,7 +1246,7 @@ glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out,
 
 glmb_status glmb_meas_assoc(glmb_handle* h, double* r_u, int cap) {
   if (!h || (cap > 0 && !r_u)) return GLMB_E_INVALID;
-  if (!h->theta_M_valid || h->stage == 2) return fail(h, GLMB_E_STATE, "meas_assoc: no pruned frame");
+  if (!h->theta_M_valid || h->stage >= 2) return fail(h, GLMB_E_STATE, "meas_assoc: no pruned frame");
   if (h->theta_M > cap) return fail(h, GLMB_E_CAPACITY, "meas_assoc: cap < M");
   launch_meas_assoc(h->hyps[h->hcur], h->H, h->theta_M, h->d_ru, h->stream);
   CU(cudaGetLastError());

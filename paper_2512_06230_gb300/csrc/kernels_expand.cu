@@ -1149,6 +1149,10 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
   const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
   // a frame already abandoned (e.g. entries beyond capacity) writes nothing
   if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) return;
+  const long long count = MAT ? (long long)*a.n_surv
+                              : (a.warp_all ? (long long)a.fs->H * HU : (long long)*a.redo_count);
+  // an empty list (the usual overflow case) costs no work-area set-up
+  if ((long long)blockIdx.x * (blockDim.x >> 5) >= count) return;
   unsigned char* gb = sm + g * WL.total;
   {
     // the sums are indexed d * T + t with each parent's own T <= T_max
@@ -1171,8 +1175,6 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
     if (lane == 0) *at<int>(gb, WL.nt) = 0;
     __syncwarp();
   }
-  const long long count = MAT ? (long long)*a.n_surv
-                              : (a.warp_all ? (long long)a.fs->H * HU : (long long)*a.redo_count);
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + g; c < count; c += nw) {
     const long long ci = MAT ? a.surv_idx[c] : (a.warp_all ? c : (long long)a.redo_list[c]);

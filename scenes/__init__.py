@@ -36,7 +36,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-__all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene",
+__all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene", "batch_scenes",
            "random_state", "chi2_gate"]
 
 
@@ -81,6 +81,26 @@ for _n in (50, 200, 500, 1000):
         name=f"sweep_N{_n}", dim=3, n_objects=_n, frames=50, extent=5000.0,
         p_d=0.85, lambda_d=2.0, clutter_rate=50.0, birth_window=None,
         births_per_frame=0.01 * _n, h_max=1000)
+
+
+def batch_scenes(n_scenes: int, seed: int, frames: int = 100, h_range=(100, 5000),
+                 n_range=(5, 300), clutter_range=(5.0, 40.0)):
+    """The batched workload: n_scenes independent 2-D scenes shaped like the
+    mid scene (P_D 0.9, 1 + Poisson(1.5) detections, births over frames
+    0-49) with N ~ U{n_range}, clutter rate ~ U(clutter_range) and a
+    hypothesis cap H ~ U{h_range} per scene.  Returns (params, seed) pairs;
+    the cap is params.h_max."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_scenes):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        h = int(rng.integers(h_range[0], h_range[1] + 1))
+        lam = float(rng.uniform(*clutter_range))
+        p = SceneParams(name=f"batch_{k}", dim=2, n_objects=n, frames=frames, extent=1000.0,
+                        lambda_d=1.5, clutter_rate=lam, birth_window=(0, min(49, frames - 1)),
+                        h_max=h)
+        out.append((p, seed * 1000 + k))
+    return out
 
 
 def preset(name: str, **overrides) -> SceneParams:

@@ -19,7 +19,8 @@ def test_struct_layouts_match_header(tmp_path):
     """ctypes mirrors of the ABI structs have the C compiler's sizes and offsets."""
     import subprocess
     structs = {"glmb_config": glmb.GlmbConfig, "glmb_birth": glmb.GlmbBirth,
-               "glmb_track": glmb.GlmbTrack, "glmb_info": glmb.GlmbInfo}
+               "glmb_track": glmb.GlmbTrack, "glmb_info": glmb.GlmbInfo,
+               "glmb_tuning": glmb.GlmbTuning, "glmb_frame_in": glmb.GlmbFrameIn}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{glmb.HEADER}"',
              'int main(void) {']
     for cname, py in structs.items():

@@ -1,0 +1,61 @@
+"""The batched form (glmb_step_batch: frames of several independent scenes
+launched together, each filter on its own stream) gives every scene exactly
+the results it gets alone: retained sets, hypothesis weights and estimates.
+Launch shapes (glmb_set_tuning) do not change results either."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def glmb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_06230_gb300 as g
+    g.build()
+    return g
+
+
+def _cfg(p, sc):
+    return sc.filter_config(max_meas=int(p.n_objects * 0.9 * 6 + 4 * p.clutter_rate + 64),
+                            max_births=64, max_tracks=p.n_objects + 48,
+                            max_components=40 * (p.n_objects + 48), max_pairs=1 << 18)
+
+
+def test_batch_equals_scenes_alone(glmb):
+    specs = scenes.batch_scenes(6, seed=7, frames=8, h_range=(50, 400), n_range=(5, 40))
+    scs = [scenes.make_scene(p, s) for p, s in specs]
+    alone = [glmb.Filter(_cfg(p, sc)) for (p, _), sc in zip(specs, scs)]
+    batch = [glmb.Filter(_cfg(p, sc)) for (p, _), sc in zip(specs, scs)]
+    for k in range(8):
+        for f, sc in zip(alone, scs):
+            f.step(sc.frames[k].births, sc.frames[k].Z)
+        glmb.step_batch(batch, [(sc.frames[k].births, sc.frames[k].Z) for sc in scs])
+        for a, b in zip(alone, batch):
+            ia, la = a.retained()
+            ib, lb = b.retained()
+            assert np.array_equal(ia, ib) and np.array_equal(la, lb), k
+            ea, eb = a.estimates(), b.estimates()
+            assert ea["n"] == eb["n"] and np.array_equal(ea["labels"], eb["labels"])
+            assert np.array_equal(ea["r"], eb["r"]) and np.array_equal(ea["mean"], eb["mean"])
+
+
+def test_tuning_does_not_change_results(glmb):
+    sc = scenes.make_scene(scenes.preset("mid"), 21)
+    cfg = sc.filter_config(max_meas=400, max_births=16, max_tracks=300)
+    fa, fb = glmb.Filter(cfg), glmb.Filter(cfg)
+    fb.set_tuning(thread_warps_per_sm=1, draw_threads=64, warp_cta_warps=4, stage_threads=256)
+    assert fb.tuning() == dict(thread_warps_per_sm=1, draw_threads=64, warp_cta_warps=4, stage_threads=256)
+    for k in range(12):
+        fr = sc.frames[k]
+        fa.step(fr.births, fr.Z)
+        fb.step(fr.births, fr.Z)
+        ia, la = fa.retained()
+        ib, lb = fb.retained()
+        assert np.array_equal(ia, ib) and np.array_equal(la, lb), k
