@@ -200,6 +200,76 @@ def run_batch(args, glmb, torch, dev):
     print(json.dumps(line))
 
 
+def _ints(text):
+    return [int(v) for v in str(text).split(",") if v]
+
+
+def run_convoy(args, glmb, torch):
+    """Section 4.1's scalability grid on the convoy workload: N copies of one
+    closed track (offset delta = 2 steps), five detections per object, no
+    clutter, 548 steps of 0.1 s; N x H_max over --convoy-n x --convoy-h,
+    for each score mode in --convoy-modes (0 the joint multi-detection
+    likelihood, 1 the product of C entries), --runs seeds each.  One update
+    is glmb_step with the frame's detections in host memory plus the
+    estimates read back (host wall clock, as the paper times an update);
+    one untimed pass per filter first fills its graph cache.  Accuracy is
+    the paper's: relative cardinality error and the Hungarian-matched mean
+    distance, averaged over the steps of a run.  --convoy-oracle-steps
+    steps of the FP64 oracle (single thread) are timed per (N, H_max) of
+    mode 0 beside it."""
+    from scenes.metrics import RunAccuracy
+    import oracle
+    steps = args.convoy_steps
+    grid = []
+    for N in _ints(args.convoy_n):
+        for H in _ints(args.convoy_h):
+            for mode in _ints(args.convoy_modes):
+                upd, acc_runs = [], []
+                for r in range(args.runs):
+                    seed = (0 if args.seed is None else args.seed) + 1000 * r + N
+                    sc = scenes.convoy_scene(N, seed, steps=steps, h_max=H)
+                    cfg = sc.filter_config(score_mode=mode)
+                    f = glmb.Filter(cfg)
+                    B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+                    for k, fr in enumerate(sc.frames):            # untimed: graph captures
+                        f.step(B[k], fr.Z)
+                    f.reset()
+                    acc = RunAccuracy()
+                    t_run = []
+                    for k, fr in enumerate(sc.frames):
+                        t0 = time.perf_counter()
+                        f.step(B[k], fr.Z)
+                        e = f.estimates(cap=256, pmf_cap=64)
+                        t_run.append(time.perf_counter() - t0)
+                        acc.add(e["mean"][:, :2], fr.truth[:, :2])
+                    f.close()
+                    upd.append(1000.0 * statistics.fmean(t_run))
+                    acc_runs.append(acc.summary())
+                row = dict(N=N, H_max=H, mode=mode, runs=args.runs, steps=steps,
+                           update_ms=statistics.fmean(upd),
+                           update_ms_sem=(statistics.stdev(upd) / math.sqrt(len(upd)) if len(upd) > 1 else 0.0),
+                           rel_card_error=statistics.fmean(a["rel_card_error"] for a in acc_runs),
+                           tracking_error_m=statistics.fmean(a["tracking_error_m"] for a in acc_runs))
+                if mode == 0 and args.convoy_oracle_steps > 0:
+                    sc = scenes.convoy_scene(N, 0 if args.seed is None else args.seed, steps=args.convoy_oracle_steps,
+                                             h_max=H)
+                    o = oracle.Oracle(sc.filter_config())
+                    t0 = time.perf_counter()
+                    for fr in sc.frames:
+                        o.step(fr.births, fr.Z)
+                        o.estimates()
+                    row["oracle_ms"] = 1000.0 * (time.perf_counter() - t0) / len(sc.frames)
+                    row["oracle_steps"] = len(sc.frames)
+                grid.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "convoy update time and accuracy (Section 4.1 grid, 1 GB300)",
+                      "unit": "ms/update", "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"convoy, D=5, lambda=0, sigma=0.25, delta=2, H_up=100, "
+                                             f"tau=1e-5, {steps} steps of 0.1 s",
+                                 "update": "glmb_step, host detections + estimates read back"},
+                      "grid": grid}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +284,12 @@ def main():
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
     ap.add_argument("--scenes", type=int, default=64,
                     help="--scene batch: independent scenes per frame")
+    ap.add_argument("--convoy-n", default="1,2,5,10,20", help="--scene convoy: object counts")
+    ap.add_argument("--convoy-h", default="5,10,25,50,100", help="--scene convoy: H_max values")
+    ap.add_argument("--convoy-modes", default="0,1", help="--scene convoy: score modes")
+    ap.add_argument("--convoy-steps", type=int, default=548)
+    ap.add_argument("--convoy-oracle-steps", type=int, default=20)
+    ap.add_argument("--runs", type=int, default=3, help="--scene convoy: seeds per configuration")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
@@ -254,6 +330,8 @@ def main():
 
     if args.scene == "batch":
         return run_batch(args, glmb, torch, dev)
+    if args.scene == "convoy":
+        return run_convoy(args, glmb, torch)
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)

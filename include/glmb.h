@@ -75,7 +75,9 @@ typedef struct {
   int32_t h_up;             /* children sampled per hypothesis (<= 65535) */
   double tau;               /* children with normalised weight < tau are dropped */
   uint64_t seed;            /* key of the counter-based random numbers */
-  int32_t score_mode;       /* 0: joint likelihood of each track's detections */
+  int32_t score_mode;       /* 0: joint likelihood of each track's detections (R3);
+                               1: product of the Eq. 2 entries C[i, t] of the chosen
+                               associations (the paper's factorised weighting) */
   int32_t max_tracks;       /* capacity: tracks per hypothesis incl. this frame's births */
   int32_t max_meas;         /* capacity: detections per frame (<= 65535) */
   int32_t max_births;       /* capacity: births per frame */
@@ -295,7 +297,7 @@ glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* 
  *                        h_up rounded up to a warp, at most 256);
  *   warp_cta_warps       most warps per CTA of the one-warp-per-child kernel
  *                        (1..16, default 16);
- *   stage_threads        threads per staging CTA (32..256, default 128).
+ *   stage_threads        threads per staging CTA (32..256, default 256).
  * Setting them drops the captured graphs. */
 typedef struct {
   int32_t thread_warps_per_sm;

@@ -107,7 +107,7 @@ struct glmb_handle {
   long long gen = 0, est_gen = -1;
   bool step_estimates = true;
   unsigned launch_opts = 0;   // GLMB_OPT_* overrides
-  glmb_tuning tune{4, 0, 16, 128};   // launch shapes (glmb_set_tuning)
+  glmb_tuning tune{4, 0, 16, 256};   // launch shapes (glmb_set_tuning)
   unsigned* h_cnt = nullptr;   // pinned copy of the prune counters
   double* d_ru = nullptr;
   // stage timing
@@ -389,7 +389,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   if (!((c.dim_x == 4 && c.dim_z == 2) || (c.dim_x == 6 && c.dim_z == 3))) return GLMB_E_INVALID;
   if (!(c.dt > 0) || !(c.q >= 0) || !(c.p_s >= 0 && c.p_s <= 1) || !(c.p_d >= 0 && c.p_d <= 1) ||
       !(c.lambda_d >= 0) || !(c.clutter_rate >= 0) || !(c.volume > 0) || !(c.gate > 0) ||
-      c.h_max < 1 || c.h_up < 1 || c.h_up > 65535 || !(c.tau > 0) || c.score_mode != 0)
+      c.h_max < 1 || c.h_up < 1 || c.h_up > 65535 || !(c.tau > 0) || c.score_mode < 0 || c.score_mode > 1)
     return GLMB_E_INVALID;
   glmb_handle* h = new glmb_handle();
   h->cfg = c;
@@ -447,6 +447,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   md.log_lambda_d = c.lambda_d > 0 ? (float)std::log(c.lambda_d) : -INFINITY;
   const double kappa = c.clutter_rate / c.volume;
   md.kappa_zero = !(kappa > 0);
+  md.score_mode = c.score_mode;
   md.log_kappa = md.kappa_zero ? -INFINITY : (float)std::log(kappa);
   md.fx_log_kappa = md.kappa_zero ? 0 : (long long)std::llrint((double)md.log_kappa * 4294967296.0);
   md.gate = std::isinf(c.gate) ? INFINITY : (float)c.gate;

@@ -50,6 +50,7 @@ struct Model {
   float lambda_d, log_lambda_d;
   float log_kappa;        // -inf when kappa == 0
   int kappa_zero;
+  int score_mode;         // 0 joint likelihood of a track's detections, 1 product of C entries
   float gate;
   float log_ps, log_1mps;
   long long fx_log_kappa; // fixed-point log kappa (0 when kappa == 0)
@@ -349,10 +350,26 @@ __device__ __forceinline__ long long term_from(const Model& md, const SlotM<DZ>&
   return fx_of(s.c - 0.5f * spread - 0.5f * d2);
 }
 
+// Factorised mode (score_mode 1): a track alive with detection set W
+// contributes log p + sum_{i in W} log C[i, t] (Eq. 2 entries, P_D included),
+// or log p + log(1 - P_D) when W is empty; sq then carries the fixed-point
+// sum of log C over W.
+__device__ __forceinline__ long long factor_term(const Model& md, float logp, int m, long long sq, int& ninf) {
+  ninf = 0;
+  float t = 0.f;
+  if (isinf(logp)) ++ninf; else t += logp;
+  if (m == 0) {
+    if (isinf(md.log_1mpd)) ++ninf; else t += md.log_1mpd;
+    return fx_of(t);
+  }
+  return fx_of(t) + sq;
+}
+
 template <int DZ>
 __device__ __forceinline__ long long alive_term(const Model& md, const float (&HPH)[DZ][DZ],
                                                 float logp, int m, const long long* se,
                                                 long long sq, int& ninf) {
+  if (md.score_mode == 1) return factor_term(md, logp, m, sq, ninf);
   if (m == 0) {
     ninf = 0;
     float t = 0.f;

@@ -277,6 +277,7 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) 
 template <int DZ>
 __device__ __forceinline__ long long slot_term(const Model& md, const View& v, int T, int t, int m, int dcnt,
                                                const long long (&se)[DZ], long long sq, int& ninf) {
+  if (md.score_mode == 1) return factor_term(md, v.logp[t], m, sq, ninf);
   if (m >= 1 && dcnt >= -2 && dcnt <= 2 && v.sln[(dcnt + 2) * T + t] != kNoSlm)
     return term_from<DZ>(md, load_slm<DZ>(v.slm, v.sln, T, dcnt + 2, t), m, se, sq, ninf);
   return slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, se, sq, ninf);
@@ -476,7 +477,8 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         smax = fmaxf(smax, pt.logC[ei]);
 #pragma unroll
         for (int d = 0; d < DZ; ++d) s_ce[d * Kp + off + j] = pt.e[d * capp + ei];
-        s_cq[off + j] = pt.q[ei];
+        // e^T R^-1 e of the pair; the factorised mode sums log C instead
+        s_cq[off + j] = md.score_mode == 1 ? pt.logC[ei] : pt.q[ei];
       }
       const float w0 = md.kappa_zero ? 0.f : expf(md.log_kappa - smax);
       float sum = w0;
@@ -529,7 +531,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   for (int x = tid; x < kSlmN * T; x += nthr) {
     const int t = x % T, v = x / T;
     const int m = s_mref[t] - 2 + v;
-    if (m < 1) {
+    if (m < 1 || md.score_mode == 1) {
       s_sln[v * T + t] = kNoSlm;
       continue;
     }

@@ -36,7 +36,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-__all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene", "batch_scenes",
+__all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene", "batch_scenes", "convoy_scene",
            "random_state", "chi2_gate"]
 
 
@@ -64,6 +64,8 @@ class SceneParams:
     h_max: int = 100
     h_up: int = 100
     tau: float = 1e-5
+    gate_tail: float = 1e-4     # chi-square tail outside the Mahalanobis gate
+    filter_clutter_rate: Optional[float] = None   # the filter's clutter rate, if not the world's
 
 
 # Scene presets.  "tiny" and "mid" are the 2-D constant-velocity scenes with
@@ -107,6 +109,80 @@ def preset(name: str, **overrides) -> SceneParams:
     return dataclasses.replace(PRESETS[name], **overrides)
 
 
+def convoy_path(steps: int, seed: int, dt: float = 0.1, extent: float = 80.0, laps: int = 3) -> np.ndarray:
+    """A smooth closed ground track inside [0, extent]^2 standing in for the
+    paper's GPS track (which is not public): a random ellipse with small
+    2nd and 3rd harmonics, scaled to 80 % of the area and walked `laps`
+    times, at constant speed, in `steps` samples dt apart, so that sample
+    `steps` would be sample 0 again (about 10 m/s for 548 samples and 3
+    laps).  Returns (steps, 4) states [x, y, vx, vy]."""
+    rng = np.random.default_rng(seed)
+    u = 2 * np.pi * np.linspace(0.0, 1.0, 16 * steps, endpoint=False)
+    # an ellipse plus 2nd and 3rd harmonics whose derivatives stay below half
+    # the ellipse's: the tangent never vanishes, so the track has no cusp
+    A, B = 1.0, rng.uniform(0.6, 1.0)
+    xy = np.stack([A * np.cos(u), B * np.sin(u)], 1)
+    for h, amp in ((2, 0.15), (3, 0.05)):
+        for a in range(2):
+            xy[:, a] += amp * rng.uniform(0.3, 1.0) * B / h * np.sin(h * u + rng.uniform(0, 2 * np.pi))
+    xy -= xy.min(0)
+    xy *= 0.8 * extent / xy.max()
+    xy += 0.1 * extent
+    seg = np.linalg.norm(np.roll(xy, -1, axis=0) - xy, axis=1)
+    arc = np.concatenate([[0.0], np.cumsum(seg)[:-1]])
+    total = arc[-1] + seg[-1]
+    s_t = (laps * total * np.arange(steps) / steps) % total
+    x = np.interp(s_t, arc, xy[:, 0], period=total)
+    y = np.interp(s_t, arc, xy[:, 1], period=total)
+    pos = np.stack([x, y], 1)
+    vel = (np.roll(pos, -1, axis=0) - np.roll(pos, 1, axis=0)) / (2 * dt)
+    return np.concatenate([pos, vel], 1)
+
+
+def convoy_scene(n_objects: int, seed: int, steps: int = 548, detections: int = 5,
+                 sigma: float = 0.25, delta: int = 2, dt: float = 0.1, h_max: int = 100,
+                 extent: float = 80.0, track_len: int = 548) -> "Scene":
+    """The paper's benchmark shape (Section 4.1): n_objects copies of one
+    closed ground track of track_len samples, copy n at step k at sample
+    (k + n * delta) mod track_len; the first `steps` steps.  Every object gives exactly `detections` detections per step,
+    N(x, sigma^2 I), left in sorted order (object, then draw); no clutter.
+    All objects exist from the first step: one birth component per object
+    there (position + N(0, (2 sigma)^2), velocity + N(0, 1 m^2/s^2),
+    r = 0.5), plus Poisson(1) spurious births anywhere (zero velocity,
+    r = 0.05) every step.  The filter model
+    reads D detections as 1 + Poisson(D - 1) and P_D = 0.999.  The world
+    has no clutter, but the filter assumes a little (0.5 per step over the
+    area): with none, one detection outside every gate would leave no
+    hypothesis with a finite weight."""
+    rng = np.random.default_rng(seed)
+    track = convoy_path(track_len, seed ^ 0xC0, dt=dt, extent=extent)
+    K = len(track)
+    p = SceneParams(name=f"convoy_N{n_objects}", dim=2, n_objects=n_objects, frames=steps, extent=extent,
+                    dt=dt, q=10.0, sigma=sigma, p_s=0.999, p_d=0.999, lambda_d=float(detections - 1),
+                    clutter_rate=0.0, birth_window=None, h_max=h_max, r_birth=0.5, r_false=0.05,
+                    false_births=1.0, birth_vel_std=6.0, h_up=100, tau=1e-5, gate_tail=1e-12,
+                    filter_clutter_rate=0.5)
+    sb = 2.0 * sigma
+    birth_cov = np.diag([sb ** 2] * 2 + [p.birth_vel_std ** 2] * 2)
+    sv = 1.0
+    track_cov = np.diag([sb ** 2] * 2 + [sv ** 2] * 2)
+    frames = []
+    for k in range(steps):
+        truth = np.stack([track[(k + n * delta) % K] for n in range(n_objects)])
+        Z = np.concatenate([truth[n, :2] + sigma * rng.normal(size=(detections, 2))
+                            for n in range(n_objects)]).astype(np.float32)
+        births = []
+        if k == 0:
+            for n in range(n_objects):
+                mean = truth[n] + rng.normal(size=4) * np.array([sb, sb, sv, sv])
+                births.append((p.r_birth, mean, track_cov.copy()))
+        for _ in range(int(rng.poisson(p.false_births))):
+            mean = np.concatenate([rng.uniform(0.0, extent, size=2), np.zeros(2)])
+            births.append((p.r_false, mean, birth_cov.copy()))
+        frames.append(Frame(Z=Z, births=births, truth=truth, truth_ids=np.arange(n_objects)))
+    return Scene(params=p, seed=seed, frames=frames)
+
+
 def chi2_gate(dim_z: int, tail: float = 1e-4) -> float:
     """Mahalanobis gate G: the chi-square(dim_z) quantile at 1 - tail."""
     from scipy.stats import chi2
@@ -140,8 +216,9 @@ class Scene:
         p = self.params
         cfg = dict(dim_x=2 * p.dim, dim_z=p.dim, dt=float(np.float32(p.dt)), q=p.q,
                    R=(p.sigma ** 2 * np.eye(p.dim)).tolist(), p_s=p.p_s, p_d=p.p_d,
-                   lambda_d=p.lambda_d, clutter_rate=p.clutter_rate,
-                   volume=p.extent ** p.dim, gate=chi2_gate(p.dim),
+                   lambda_d=p.lambda_d,
+                   clutter_rate=p.clutter_rate if p.filter_clutter_rate is None else p.filter_clutter_rate,
+                   volume=p.extent ** p.dim, gate=chi2_gate(p.dim, p.gate_tail),
                    h_max=p.h_max, h_up=p.h_up, tau=p.tau,
                    seed=(self.seed ^ 0x5EED) & ((1 << 64) - 1), score_mode=0)
         cfg.update(overrides)

@@ -175,3 +175,24 @@ def test_multi_frame_run_tracks_the_oracle(oracle_mod, glmb):
           f"equal MAP cardinality: {card}/{len(sc.frames)}")
     assert same >= len(sc.frames) // 2
     assert card >= 0.9 * len(sc.frames)
+
+
+@pytest.mark.parametrize("k", [1, 6, 20])
+def test_factorised_mode_tiny_frame(oracle_mod, glmb, k):
+    """Section 4: the factorised score (product of C entries of Eq. 2)."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1004)
+    _frame(oracle_mod, glmb, sc.filter_config(score_mode=1), sc, k)
+
+
+def test_factorised_mode_mid_frame(oracle_mod, glmb):
+    sc = scenes.make_scene(scenes.preset("mid"), 2001)
+    rep = _frame(oracle_mod, glmb, sc.filter_config(score_mode=1), sc, 12)
+    assert rep.checks["children"] >= 1000
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k", [0, 3, 15])
+def test_convoy_frame(oracle_mod, glmb, mode, k):
+    """Section 4.1's workload shape: five detections per object, no clutter."""
+    sc = scenes.convoy_scene(5, 77, steps=16, h_max=50)
+    _frame(oracle_mod, glmb, sc.filter_config(score_mode=mode), sc, k)

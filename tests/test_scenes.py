@@ -1,0 +1,80 @@
+"""Synthetic workloads and the accuracy metrics (CPU)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import scenes
+from scenes.metrics import RunAccuracy, matched_distance
+
+
+def test_convoy_shape_follows_section_4_1():
+    N, D, delta = 4, 5, 2
+    sc = scenes.convoy_scene(N, 3, steps=40, detections=D, delta=delta)
+    track = scenes.convoy_path(548, 3 ^ 0xC0)
+    for k, fr in enumerate(sc.frames):
+        assert fr.Z.shape == (N * D, 2)
+        # copy n is the base track offset by n * delta steps
+        for n in range(N):
+            np.testing.assert_allclose(fr.truth[n], track[(k + n * delta) % 548])
+        # detections in sorted order (object by object), spread sigma
+        for n in range(N):
+            err = fr.Z[n * D:(n + 1) * D] - fr.truth[n, :2]
+            assert np.all(np.abs(err) < 6 * sc.params.sigma)
+    assert len([b for b in sc.frames[0].births if b[0] == sc.params.r_birth]) == N
+    cfg = sc.filter_config()
+    assert sc.params.clutter_rate == 0.0 and cfg["lambda_d"] == D - 1
+    assert cfg["h_up"] == 100 and cfg["tau"] == 1e-5
+
+
+def test_convoy_path_is_smooth_closed_and_inside_the_area():
+    tr = scenes.convoy_path(548, 9)
+    assert tr[:, :2].min() >= 0 and tr[:, :2].max() <= 80
+    # constant speed, and the wrap from the last sample to the first is an
+    # ordinary step: copies offset modulo the track length never jump
+    step = np.linalg.norm(np.roll(tr[:, :2], -1, axis=0) - tr[:, :2], axis=1)
+    assert step.max() / step.min() < 1.01
+    assert 5.0 < step.mean() / 0.1 < 15.0
+    acc = np.linalg.norm(np.roll(tr[:, 2:], -1, axis=0) - tr[:, 2:], axis=1) / 0.1
+    assert acc.max() < 15.0
+
+
+def test_detection_noise_has_the_stated_spread():
+    sc = scenes.convoy_scene(5, 4, steps=200)
+    err = np.concatenate([fr.Z - np.repeat(fr.truth[:, :2], 5, axis=0) for fr in sc.frames])
+    assert abs(err.std() - 0.25) < 0.01
+    assert np.all(np.abs(err.mean(0)) < 0.01)
+
+
+def test_matched_distance_brute_force():
+    rng = np.random.default_rng(0)
+    from itertools import permutations
+    for _ in range(5):
+        a, b = rng.normal(size=(3, 2)), rng.normal(size=(4, 2))
+        best = min(np.mean([np.linalg.norm(a[i] - b[p[i]]) for i in range(3)])
+                   for p in permutations(range(4), 3))
+        assert abs(matched_distance(a, b) - best) < 1e-12
+
+
+def test_run_accuracy_cardinality():
+    acc = RunAccuracy()
+    acc.add(np.zeros((3, 2)), np.zeros((4, 2)))
+    acc.add(np.zeros((4, 2)), np.zeros((4, 2)))
+    s = acc.summary()
+    assert s["rel_card_error"] == pytest.approx(0.125) and s["tracking_error_m"] == 0.0
+
+
+def test_oracle_tracks_a_short_convoy(oracle_mod):
+    """The FP64 filter on the convoy workload: after a short settling time the
+    cardinality is right and the estimates sit within the detection spread."""
+    sc = scenes.convoy_scene(3, 5, steps=25, h_max=25)
+    o = oracle_mod.Oracle(sc.filter_config())
+    acc = RunAccuracy()
+    for k, fr in enumerate(sc.frames):
+        o.step(fr.births, fr.Z)
+        e = o.estimates()
+        if k >= 5:
+            acc.add(e["mean"][:, :2], fr.truth[:, :2])
+    s = acc.summary()
+    assert s["rel_card_error"] < 0.05, s
+    assert s["tracking_error_m"] < 0.25, s
