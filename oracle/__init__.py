@@ -77,6 +77,12 @@ def _load():
         lib.orc_estimates.argtypes = [P, C.c_int, P, P, P, P, P, P, P, C.c_int, P]
         lib.orc_meas_assoc.argtypes = [P, P]
         lib.orc_bruteforce.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        lib.orc_set_gate.argtypes = [P, P, C.c_double]
+        lib.orc_mlp_margin.argtypes = [P, C.c_int]
+        lib.orc_mlp_margin.restype = C.c_double
+        lib.orc_gate_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P]
+        lib.orc_mlp_logit.argtypes = [P, P, C.c_int]
+        lib.orc_mlp_logit.restype = C.c_double
         lib.orc_philox.argtypes = [P, P, P]
         lib.orc_mix64.argtypes = [C.c_uint64]
         lib.orc_mix64.restype = C.c_uint64
@@ -95,6 +101,17 @@ class OracleError(RuntimeError):
 def _check(rc: int, what: str):
     if rc != 0:
         raise OracleError(f"{what}: {ERRORS.get(rc, rc)}")
+
+
+GATE_NPARAM = 8779
+
+
+def mlp_logit(params, feat, round_act: bool = True) -> float:
+    """The C oracle's MLP forward pass on one raw feature row."""
+    p = np.ascontiguousarray(params, np.float32).reshape(-1)
+    f = np.ascontiguousarray(feat, np.float64).reshape(-1)
+    assert p.size == GATE_NPARAM and f.size == 5
+    return _load().orc_mlp_logit(_ptr(p), _ptr(f), int(round_act))
 
 
 def philox(ctr, key) -> np.ndarray:
@@ -250,6 +267,28 @@ class Oracle:
 
     def gate_margin(self, h):
         return self.lib.orc_gate_margin(self.h, h)
+
+    # -- learned gate ----------------------------------------------------------
+    def set_gate(self, params, threshold: float = 0.0):
+        """Switch the learned gate on (params: GATE_NPARAM float32 values) or
+        off (None); applies from the next update."""
+        if params is None:
+            self._gate = None
+            _check(self.lib.orc_set_gate(self.h, None, 0.0), "set_gate")
+            return
+        self._gate = np.ascontiguousarray(params, np.float32).reshape(-1)
+        assert self._gate.size == GATE_NPARAM
+        _check(self.lib.orc_set_gate(self.h, _ptr(self._gate), float(threshold)), "set_gate")
+
+    def mlp_margin(self, h):
+        return self.lib.orc_mlp_margin(self.h, h)
+
+    def gate_eval(self, h, t, i):
+        feat = np.zeros(5)
+        lg = C.c_double()
+        if self.lib.orc_gate_eval(self.h, h, t, i, _ptr(feat), C.byref(lg)) != 0:
+            raise OracleError("gate_eval index")
+        return feat, lg.value
 
     def children(self):
         n = self.num_parents() * self._c.h_up

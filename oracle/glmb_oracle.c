@@ -52,6 +52,12 @@
  *   R9  estimates: MAP cardinality, then the heaviest hypothesis of that
  *       cardinality; existence of a label = total weight of hypotheses that
  *       contain it.
+ *   R10 learned gate (an extension, off unless orc_set_gate is called): a
+ *       pair that passes the Mahalanobis test enters the table only when a
+ *       5-64-64-64-1 GELU MLP on (d^2, |e|, p, age, log det S) scores it at
+ *       or above a threshold.  The decision is taken on the forward pass
+ *       with bf16 weights and bf16-rounded inputs and activations (the
+ *       precision the library decides in), accumulated in double.
  *
  * Parity unpinned: R2 (death probability) and R9 (estimator) are readings
  * with no value in the paper to check them against; the tests only hold the
@@ -183,6 +189,7 @@ typedef struct {
   int *ptr, *meas;
   double *d2, *logC, *q, *e;
   double gate_margin;
+  double mlp_margin;          /* smallest |logit - threshold| judged */
   int *rptr, *rslot, *rpair;  /* same pairs re-indexed by detection row */
   /* children */
   int8_t* status;             /* 0 zero weight, 1 unique, 2 duplicate */
@@ -195,6 +202,9 @@ typedef struct {
 
 struct orc_filter {
   orc_config c;
+  int mlp_on;                 /* learned gate (see orc_set_gate) */
+  float mlp[8779];
+  double mlp_thr;
   int dx, dz;
   int frame;
   double F[36], Q[36], Rinv[9], logdetR, kappa, log_kappa;
@@ -454,6 +464,89 @@ static double quad_Rinv(const orc_filter* f, const double* e) {
   return s;
 }
 
+/* ------------------------------------------------------------------ */
+/* Learned gate (an extension beyond the paper's gate g_ijk): an MLP on   */
+/* five features of a pair, applied after the Mahalanobis test.           */
+/* ------------------------------------------------------------------ */
+enum { G_W1 = 0, G_B1 = 320, G_W2 = 384, G_B2 = 4480, G_W3 = 4544, G_B3 = 8640, G_W4 = 8704,
+       G_B4 = 8768, G_MU = 8769, G_SD = 8774 };
+
+/* round to the nearest bf16 (ties to even) through float */
+static double to_bf16(double x) {
+  float v = (float)x;
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+  }
+  memcpy(&v, &u, 4);
+  return v;
+}
+
+/* GELU(x) = x * Phi(x), Phi the standard normal distribution function */
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+
+double orc_mlp_logit(const float* p, const double* feat, int round_act) {
+  double x[5], h[64], g[64];
+  for (int j = 0; j < 5; ++j) {
+    x[j] = (feat[j] - (double)p[G_MU + j]) / (double)p[G_SD + j];
+    if (round_act) x[j] = to_bf16(x[j]);
+  }
+  for (int o = 0; o < 64; ++o) {
+    double z = p[G_B1 + o];
+    for (int j = 0; j < 5; ++j) z += to_bf16(p[G_W1 + o * 5 + j]) * x[j];
+    h[o] = round_act ? to_bf16(gelu(z)) : gelu(z);
+  }
+  for (int o = 0; o < 64; ++o) {
+    double z = p[G_B2 + o];
+    for (int j = 0; j < 64; ++j) z += to_bf16(p[G_W2 + o * 64 + j]) * h[j];
+    g[o] = round_act ? to_bf16(gelu(z)) : gelu(z);
+  }
+  for (int o = 0; o < 64; ++o) {
+    double z = p[G_B3 + o];
+    for (int j = 0; j < 64; ++j) z += to_bf16(p[G_W3 + o * 64 + j]) * g[j];
+    h[o] = round_act ? to_bf16(gelu(z)) : gelu(z);
+  }
+  double z = p[G_B4];
+  for (int j = 0; j < 64; ++j) z += to_bf16(p[G_W4 + j]) * h[j];
+  return z;
+}
+
+/* the gate's five features of slot t and a detection with innovation e */
+static void gate_features(const orc_filter* f, const par_t* P, int t, const double* e, double d2,
+                          double* feat) {
+  double n2 = 0.0;
+  for (int a = 0; a < f->dz; ++a) n2 += e[a] * e[a];
+  feat[0] = d2;
+  feat[1] = sqrt(n2);
+  feat[2] = P->p[t];
+  feat[3] = (double)((uint32_t)f->frame - P->lk[t]);
+  feat[4] = P->logdetS[t];
+}
+
+int orc_set_gate(orc_filter* f, const float* params, double threshold) {
+  if (!f) return 1;
+  f->mlp_on = params != NULL;
+  if (params) memcpy(f->mlp, params, sizeof f->mlp);
+  f->mlp_thr = threshold;
+  return 0;
+}
+
+/* whether the pair enters the table: the Mahalanobis test (R1), then, when
+ * the learned gate is on, its logit against the threshold (decided on the
+ * bf16-rounded forward pass) */
+static int pair_gated(const orc_filter* f, const par_t* P, int t, const double* e, double d2,
+                      double* margin) {
+  if (!(d2 <= f->c.gate)) return 0;
+  if (!f->mlp_on) return 1;
+  double feat[5];
+  gate_features(f, P, t, e, d2, feat);
+  double lg = orc_mlp_logit(f->mlp, feat, 1);
+  if (margin && fabs(lg - f->mlp_thr) < *margin) *margin = fabs(lg - f->mlp_thr);
+  return lg >= f->mlp_thr;
+}
+
 static int build_table(const orc_filter* f, par_t* P) {
   int dx = f->dx, dz = f->dz, T = P->T, M = f->M;
   P->S = (double*)calloc(T * dz * dz + 1, sizeof(double));
@@ -462,6 +555,7 @@ static int build_table(const orc_filter* f, par_t* P) {
   P->dprob = (double*)calloc(T + 1, sizeof(double));
   P->ptr = (int*)calloc(T + 1, sizeof(int));
   P->gate_margin = INFINITY;
+  P->mlp_margin = INFINITY;
   for (int t = 0; t < T; ++t) {
     double* S = P->S + t * dz * dz;
     for (int a = 0; a < dz; ++a)
@@ -481,7 +575,7 @@ static int build_table(const orc_filter* f, par_t* P) {
         double mg = fabs(d2 - f->c.gate) / f->c.gate;
         if (mg < P->gate_margin) P->gate_margin = mg;
       }
-      if (d2 <= f->c.gate) ++K;
+      if (pair_gated(f, P, t, e, d2, &P->mlp_margin)) ++K;
     }
   }
   P->ptr[T] = K;
@@ -496,7 +590,7 @@ static int build_table(const orc_filter* f, par_t* P) {
     for (int i = 0; i < M; ++i) {
       innovation(f, P->m + t * dx, f->Z + i * dz, e);
       double d2 = mahal(dz, P->L + t * dz * dz, e);
-      if (!(d2 <= f->c.gate)) continue;
+      if (!pair_gated(f, P, t, e, d2, NULL)) continue;
       P->meas[k] = i;
       P->d2[k] = d2;
       P->logC[k] = log(f->c.p_d) - 0.5 * (d2 + P->logdetS[t] + dz * LOG2PI);
@@ -937,7 +1031,24 @@ int orc_pair(const orc_filter* f, int h, int t, int i, double* d2, double* logC,
   *d2 = mahal(dz, P->L + t * dz * dz, e);
   *logC = log(f->c.p_d) - 0.5 * (*d2 + P->logdetS[t] + dz * LOG2PI);
   *q = quad_Rinv(f, e);
-  return *d2 <= f->c.gate ? 1 : 0;
+  return pair_gated(f, P, t, e, *d2, NULL);
+}
+
+double orc_mlp_margin(const orc_filter* f, int h) {
+  if (!f->par || h < 0 || h >= f->Hold) return NAN;
+  return f->par[h].mlp_margin;
+}
+
+int orc_gate_eval(const orc_filter* f, int h, int t, int i, double* feat, double* logit) {
+  if (!f->par || h < 0 || h >= f->Hold || t < 0 || t >= f->par[h].T || i < 0 || i >= f->M)
+    return -1;
+  const par_t* P = &f->par[h];
+  double e[3];
+  innovation(f, P->m + t * f->dx, f->Z + i * f->dz, e);
+  double d2 = mahal(f->dz, P->L + t * f->dz * f->dz, e);
+  gate_features(f, P, t, e, d2, feat);
+  *logit = f->mlp_on ? orc_mlp_logit(f->mlp, feat, 1) : NAN;
+  return 0;
 }
 
 double orc_gate_margin(const orc_filter* f, int h) {

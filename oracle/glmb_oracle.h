@@ -71,6 +71,24 @@ int orc_estimates(const orc_filter* f, int cap, int* n_out, uint32_t* lk, uint32
 int orc_meas_assoc(const orc_filter* f, double* r_u);
 int orc_bruteforce(const orc_filter* f, int h, int cap, uint8_t* dead, uint16_t* theta,
                    double* logw);
+/* Learned gate: a 5-64-64-64-1 MLP with GELU activations on five features
+ * of a gated (slot, detection) pair (Mahalanobis d^2, innovation norm,
+ * prior existence, track age in frames, log det S).  A pair that passes the
+ * Mahalanobis gate is kept only when its logit >= threshold.  params holds
+ * ORC_GATE_NPARAM floats: W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64]
+ * b3[64] w4[64] b4 mu[5] sd[5] (weights used rounded to bf16; features
+ * standardised as (f - mu) / sd).  NULL switches the gate off. */
+#define ORC_GATE_NPARAM 8779
+int orc_set_gate(orc_filter* f, const float* params, double threshold);
+/* smallest |logit - threshold| over the pairs the gate judged for parent h
+ * (INFINITY when the gate is off or judged none) */
+double orc_mlp_margin(const orc_filter* f, int h);
+/* features and logit of (parent h, slot t, detection i) */
+int orc_gate_eval(const orc_filter* f, int h, int t, int i, double* feat, double* logit);
+/* the MLP on one raw feature row; round_act = 1 rounds the standardised
+ * features and every hidden activation to bf16 (the precision the library's
+ * decision is taken in), 0 keeps them in double */
+double orc_mlp_logit(const float* params, const double* feat, int round_act);
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 uint64_t orc_mix64(uint64_t x);
 

@@ -37,6 +37,7 @@ from typing import List, Optional, Tuple
 import numpy as np
 
 __all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene", "batch_scenes", "convoy_scene",
+           "gate_params", "GATE_NPARAM",
            "random_state", "chi2_gate"]
 
 
@@ -333,3 +334,25 @@ def random_state(rng: np.random.Generator, dim: int, H: int, n_labels: int,
             tr.append((labels[j][0], labels[j][1], mean, P))
         hyps.append(tr)
     return logw, uids, hyps
+
+
+GATE_NPARAM = 8779
+
+
+def gate_params(seed: int, mu=None, sd=None, scale: float = 1.0, bias: float = 0.0) -> np.ndarray:
+    """Seeded parameters of the gate's 5-64-64-64-1 MLP (float32, layout
+    W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] w4[64] b4 mu[5]
+    sd[5]): each matrix N(0, scale^2 / fan_in), biases N(0, 0.1^2), the
+    output bias `bias`, standardisation mu (default 0) and sd (default 1)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, n_out in ((5, 64), (64, 64), (64, 64)):
+        parts.append(rng.normal(scale=scale / np.sqrt(fan_in), size=(n_out, fan_in)).ravel())
+        parts.append(rng.normal(scale=0.1, size=n_out))
+    parts.append(rng.normal(scale=scale / 8.0, size=64))
+    parts.append(np.array([bias]))
+    parts.append(np.zeros(5) if mu is None else np.asarray(mu, np.float64))
+    parts.append(np.ones(5) if sd is None else np.asarray(sd, np.float64))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == GATE_NPARAM
+    return p
