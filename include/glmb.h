@@ -127,6 +127,7 @@ typedef struct {
   int32_t expand_plan_M;       /* detection rows it was planned for */
   int32_t expand_threads;      /* threads per CTA of the last expansion */
   double graph_capture_ms;     /* host time spent capturing and instantiating frame graphs */
+  int64_t n_pairs_pregate;     /* pairs that passed the Mahalanobis test (before the learned gate) */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks
@@ -329,6 +330,81 @@ glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts);
  * of the paper's method: a launch option. */
 glmb_status glmb_set_step_estimates(glmb_handle* h, int on);
 glmb_status glmb_get_timing(glmb_handle* h, double* ms, long long* calls, int n);
+
+/* ------------------------------------------------------------------------
+ * Learned pair gate (an extension beyond the paper).  The paper gates the
+ * compatibility matrix of Eq. 2 with a fixed test g_ijk (Section 3); this
+ * library's test is d^2 <= cfg.gate.  The learned gate adds a 5-64-64-64-1
+ * multilayer perceptron with GELU activations that scores every pair passing
+ * that test from five features:
+ *   d^2 (Mahalanobis), |e| (innovation norm), p (the slot's prior existence),
+ *   age = frame - label_k, log det S.
+ * In GLMB_GATE_PRUNE mode a pair enters the table only when its logit is at
+ * or above the threshold, so the expansion draws over fewer candidates; the
+ * death probability (reading R2) sums over the pairs that remain.
+ *
+ * Parameters: GLMB_GATE_NPARAM floats,
+ *   W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] w4[64] b4 mu[5] sd[5]
+ * (row-major, output index first).  Features enter as (f - mu) / sd.  The
+ * matrices W1, W2, W3 and w4 are used rounded to bf16; the standardised
+ * features and the hidden activations are rounded to bf16 before each
+ * matrix product; products accumulate in fp32.  The first GLMB_GATE_NTRAIN
+ * values are the trained ones (mu and sd are fixed).
+ * ---------------------------------------------------------------------- */
+#define GLMB_GATE_NPARAM 8779
+#define GLMB_GATE_NTRAIN 8769
+#define GLMB_GATE_OFF 0     /* no learned gate (the default) */
+#define GLMB_GATE_PRUNE 1   /* drop pairs whose logit < threshold */
+#define GLMB_GATE_SCORE 2   /* score every pair, prune nothing (for evaluation) */
+
+/* Sets the gate for the following updates.  params: host memory, copied
+ * (ignored, and may be NULL, for GLMB_GATE_OFF).  Errors: GLMB_E_INVALID for
+ * an unknown mode, missing params, a non-finite parameter or sd <= 0;
+ * GLMB_E_OOM when the gate's buffers (two byte/float arrays of max_pairs
+ * entries and, for PRUNE, a second pair table) cannot be allocated. */
+glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, int mode);
+
+/* Raw features (before standardisation) of the pairs of the last update's
+ * table as it was before the learned gate, in table order (component, then
+ * detection): X[n][5] floats, host memory.  *n receives the pair count;
+ * GLMB_E_CAPACITY when it exceeds cap rows (nothing copied).  Valid from the
+ * update until the next prediction.  GLMB_E_STATE without an update. */
+glmb_status glmb_gate_features(glmb_handle* h, float* X, int64_t cap, int64_t* n);
+
+/* Logits of those pairs (modes PRUNE and SCORE), host memory, same order. */
+glmb_status glmb_gate_logits(glmb_handle* h, float* logit, int64_t cap, int64_t* n);
+
+/* After a pruned frame with the gate OFF or in SCORE mode: used[k] = 1 when
+ * a retained hypothesis assigns a detection to the track of pair k (the
+ * gate's training label), else 0 (cap_pairs entries at least the pair
+ * count); hyp_flag[j] = 1 when retained hypothesis j uses a pair whose logit
+ * is below the threshold (SCORE mode; 0 otherwise; cap_h >= hypotheses).
+ * Either array may be NULL.  Host memory.  Errors: GLMB_E_STATE without a
+ * pruned frame or in PRUNE mode; GLMB_E_CAPACITY for short arrays. */
+glmb_status glmb_gate_usage(glmb_handle* h, uint8_t* used, int64_t cap_pairs, uint8_t* hyp_flag, int cap_h,
+                            int64_t* n_pairs, int* n_hyp);
+
+/* Stateless MLP calls (no filter handle), device memory throughout, all
+ * work enqueued on `stream` (a cudaStream_t, NULL for the default stream);
+ * the caller owns every buffer.  err: one device uint32 to which a kernel
+ * ORs 256 when a tensor-core wait ran out of time (its results are then
+ * invalid); the caller zeroes and reads it.  GLMB_E_INVALID for n < 0 or a
+ * NULL pointer (n = 0 launches nothing).
+ *
+ * glmb_mlp_forward: logit[i] for the raw feature rows X[n][5].
+ * glmb_mlp_backward: zeroes grad[GLMB_GATE_NPARAM] and *loss (a double),
+ *   then accumulates the loss sum_i wt[i] (softplus(z_i) - y[i] z_i) and its
+ *   gradient with respect to the bf16-rounded weights (rounding passed
+ *   straight through; zero for mu and sd).  y[i] in {0, 1}.
+ * glmb_mlp_adam: one Adam step (Kingma and Ba 2015, bias-corrected,
+ *   step = 1, 2, ...) of the first GLMB_GATE_NTRAIN parameters, moments m
+ *   and v (GLMB_GATE_NTRAIN floats each, zero before the first step). */
+glmb_status glmb_mlp_forward(const float* params, const float* X, int64_t n, float* logit, uint32_t* err,
+                             void* stream);
+glmb_status glmb_mlp_backward(const float* params, const float* X, const float* y, const float* wt, int64_t n,
+                              float* grad, double* loss, uint32_t* err, void* stream);
+glmb_status glmb_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                          float beta2, float eps, void* stream);
 
 /* Top-H selection without device allocation.  The paper has no counterpart:
  * this is the normalisation and truncation step of glmb_prune offered on

@@ -1043,7 +1043,7 @@ int orc_gate_eval(const orc_filter* f, int h, int t, int i, double* feat, double
   if (!f->par || h < 0 || h >= f->Hold || t < 0 || t >= f->par[h].T || i < 0 || i >= f->M)
     return -1;
   const par_t* P = &f->par[h];
-  double e[3];
+  double e[3] = {0.0, 0.0, 0.0};
   innovation(f, P->m + t * f->dx, f->Z + i * f->dz, e);
   double d2 = mahal(f->dz, P->L + t * f->dz * f->dz, e);
   gate_features(f, P, t, e, d2, feat);

@@ -24,7 +24,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libglmb.so")
 HEADER = os.path.join(_ROOT, "include", "glmb.h")
-SOURCES = ["kernels_table.cu", "kernels_expand.cu", "kernels_prune.cu", "glmb_api.cu",
+SOURCES = ["kernels_table.cu", "kernels_expand.cu", "kernels_prune.cu", "glmb_api.cu", "gate_mlp.cu",
            "select_static.cu", "select_cluster.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
@@ -102,7 +102,8 @@ class GlmbInfo(C.Structure):
                 ("n_redo", C.c_int64), ("expand_smem_bytes", C.c_int32),
                 ("expand_ctas_per_sm", C.c_int32), ("expand_plan_T", C.c_int32),
                 ("expand_plan_K", C.c_int32), ("expand_plan_M", C.c_int32),
-                ("expand_threads", C.c_int32), ("graph_capture_ms", C.c_double)]
+                ("expand_threads", C.c_int32), ("graph_capture_ms", C.c_double),
+                ("n_pairs_pregate", C.c_int64)]
 
 
 class GlmbTuning(C.Structure):
@@ -159,6 +160,10 @@ def load() -> C.CDLL:
         "glmb_step": [P, P, I, P, I, I], "glmb_set_step_estimates": [P, I], "glmb_set_launch_options": [P, C.c_uint],
         "glmb_step_enqueue": [P, P, I, P, I, I], "glmb_step_finish": [P],
         "glmb_step_batch": [P, I, P, P], "glmb_set_tuning": [P, P], "glmb_get_tuning": [P, P],
+        "glmb_set_gate": [P, P, C.c_float, I], "glmb_gate_features": [P, P, L, P],
+        "glmb_gate_logits": [P, P, L, P], "glmb_gate_usage": [P, P, L, P, I, P, P],
+        "glmb_mlp_forward": [P, P, L, P, P, P], "glmb_mlp_backward": [P, P, P, P, L, P, P, P, P],
+        "glmb_mlp_adam": [P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -376,6 +381,46 @@ class Filter:
 
     OPT_STAGE_GLOBAL, OPT_DRAW_WARP, OPT_DRAW_THREAD = 1, 2, 4
 
+    # ---- learned pair gate ----
+    GATE_OFF, GATE_PRUNE, GATE_SCORE = 0, 1, 2
+
+    def set_gate(self, params=None, threshold: float = 0.0, mode: int = 1):
+        """Learned gate for the following updates (params: GATE_NPARAM
+        float32 values; mode GATE_PRUNE drops pairs whose logit < threshold,
+        GATE_SCORE only scores them; None switches it off)."""
+        if params is None:
+            self._check(self.lib.glmb_set_gate(self.h, None, C.c_float(0.0), self.GATE_OFF))
+            return
+        p = np.ascontiguousarray(params, np.float32).reshape(-1)
+        if p.size != GATE_NPARAM:
+            raise ValueError(f"gate parameters: {p.size} values, need {GATE_NPARAM}")
+        self._check(self.lib.glmb_set_gate(self.h, _ptr(p), C.c_float(threshold), int(mode)))
+
+    def gate_features(self) -> np.ndarray:
+        """Raw features (K x 5) of the last update's pairs before the gate."""
+        n = C.c_int64()
+        self.lib.glmb_gate_features(self.h, None, 0, C.byref(n))
+        X = np.zeros((max(n.value, 1), 5), np.float32)
+        self._check(self.lib.glmb_gate_features(self.h, _ptr(X), X.shape[0], C.byref(n)))
+        return X[: n.value]
+
+    def gate_logits(self) -> np.ndarray:
+        n = C.c_int64()
+        self.lib.glmb_gate_logits(self.h, None, 0, C.byref(n))
+        z = np.zeros(max(n.value, 1), np.float32)
+        self._check(self.lib.glmb_gate_logits(self.h, _ptr(z), z.size, C.byref(n)))
+        return z[: n.value]
+
+    def gate_usage(self):
+        """(used[K] uint8, hyp_flag[H] uint8) of the last pruned frame."""
+        K, H = C.c_int64(), C.c_int()
+        self.lib.glmb_gate_usage(self.h, None, 0, None, 0, C.byref(K), C.byref(H))
+        used = np.zeros(max(K.value, 1), np.uint8)
+        flag = np.zeros(max(H.value, 1), np.uint8)
+        self._check(self.lib.glmb_gate_usage(self.h, _ptr(used), used.size, _ptr(flag), flag.size,
+                                             C.byref(K), C.byref(H)))
+        return used[: K.value], flag[: H.value]
+
     def set_launch_options(self, opts: int = 0):
         self._check(self.lib.glmb_set_launch_options(self.h, int(opts)))
 
@@ -491,6 +536,47 @@ class Filter:
         self._check(self.lib.glmb_get_children(self.h, _ptr(logw), _ptr(st), _ptr(na), max(k, 1),
                                                C.byref(n)))
         return dict(logw=logw[:k], status=st[:k], n_alive=na[:k])
+
+
+GATE_NPARAM = 8779
+GATE_NTRAIN = 8769
+
+
+def _tptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    return C.c_void_p(stream) if stream is not None else None
+
+
+def mlp_forward(params, X, err, stream=None):
+    """Logits of the raw feature rows X (torch float32 (n, 5), CUDA) through
+    glmb_mlp_forward; err: a zeroed CUDA uint32/int32 tensor of one element
+    that receives 256 if a tensor-core wait ran out of time."""
+    import torch
+    n = int(X.shape[0])
+    out = torch.empty(n, dtype=torch.float32, device=X.device)
+    st = load().glmb_mlp_forward(_tptr(params), _tptr(X), n, _tptr(out), _tptr(err), _stream(stream))
+    if st:
+        raise GlmbError(st, "mlp_forward")
+    return out
+
+
+def mlp_backward(params, X, y, wt, grad, loss, err, stream=None):
+    """Fills grad (GATE_NPARAM float32) and loss (one float64) on the device."""
+    n = int(X.shape[0])
+    st = load().glmb_mlp_backward(_tptr(params), _tptr(X), _tptr(y), _tptr(wt), n, _tptr(grad), _tptr(loss),
+                                  _tptr(err), _stream(stream))
+    if st:
+        raise GlmbError(st, "mlp_backward")
+
+
+def mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    st = load().glmb_mlp_adam(_tptr(params), _tptr(grad), _tptr(m), _tptr(v), int(step), C.c_float(lr),
+                              C.c_float(beta1), C.c_float(beta2), C.c_float(eps), _stream(stream))
+    if st:
+        raise GlmbError(st, "mlp_adam")
 
 
 def step_batch(filters, frames, device: bool = False):

@@ -26,7 +26,8 @@ enum { kStagePredict = 0, kStageTable, kStageExpand, kStageSelect, kStageMat, kS
        kStageEstimates, kNumStages };
 
 // device scalar slots
-enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_REDO = 7, S_N = 16 };
+enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_REDO = 7, S_KFULL = 8,
+       S_N = 16 };
 
 }  // namespace
 
@@ -75,6 +76,19 @@ struct glmb_handle {
   const float* z_dev = nullptr;   // detections the kernels read: d_Z or the caller's device buffer
   float* h_Z = nullptr;
   PairTable pt{};
+  // learned pair gate (glmb_set_gate): parameters on the device, the table
+  // before the gate (PRUNE mode; shares logdetS with pt), per-pair keep flags
+  // and logits of the last update, scratch of the training-data calls
+  int gate_mode = 0, gate_mode_frame = 0;
+  float gate_thr = 0.f;
+  float* gate_params = nullptr;
+  PairTable pt_full{};
+  uint8_t* gate_keep = nullptr;
+  float* gate_logit = nullptr;
+  float* gate_X = nullptr;
+  uint8_t* gate_used = nullptr;
+  uint8_t* gate_hflag = nullptr;
+  long long n_pairs_pregate = 0;
   uint32_t* scan_tmp32 = nullptr;
   long long scan_cap32 = 0;   // capacity scan_tmp32 was sized for
   long long* child_key = nullptr;
@@ -270,6 +284,7 @@ const char* err_text(unsigned e) {
   if (e & kErrUpdates) return "distinct track updates exceed capacity";
   if (e & kErrHash) return "update table full";
   if (e & kErrNumeric) return "covariance not positive definite";
+  if (e & kErrGate) return "learned gate: a tensor-core wait ran out of time";
   return "device error";
 }
 
@@ -640,11 +655,26 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
   prof_begin(h, kStageTable);
   launch_check_finite(h->d_fs, dz, h->d_scal + S_ERR, h->stream);
   const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
-  launch_table_count(h->md, B, h->pt, h->d_fs, gt, h->stream);
-  scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR,
-           h->stream);
-  launch_table_write(h->md, B, h->pt, h->d_fs, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
+  // with the gate pruning, the Mahalanobis-gated table goes to pt_full and
+  // the gate compacts the pairs it keeps into pt
+  const bool prune = h->gate_mode == GLMB_GATE_PRUNE;
+  const PairTable& P0 = prune ? h->pt_full : h->pt;
+  launch_table_count(h->md, B, P0, h->d_fs, gt, h->stream);
+  scan_u32(P0.cnt, P0.ptr, &h->d_fs->T, 1, cap, h->d_scal + (prune ? S_KFULL : S_K), true, h->scan_tmp32,
+           h->scan_cap32, h->d_scal + S_ERR, h->stream);
+  launch_table_write(h->md, B, P0, h->d_fs, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
                      h->stream);
+  if (h->gate_mode != GLMB_GATE_OFF) {
+    launch_gate_forward_table(h->gate_params, h->gate_thr, h->md, B, P0, h->d_fs, h->gate_logit,
+                              prune ? h->gate_keep : nullptr, h->d_scal + S_ERR, 2 * h->n_sm, h->stream);
+    if (prune) {
+      launch_gate_compact(h->md, B, P0, h->gate_keep, h->pt, h->d_fs, true, gt, h->stream);
+      scan_u32(h->pt.cnt, h->pt.ptr, &h->d_fs->T, 1, cap, h->d_scal + S_K, true, h->scan_tmp32, h->scan_cap32,
+               h->d_scal + S_ERR, h->stream);
+      launch_gate_compact(h->md, B, P0, h->gate_keep, h->pt, h->d_fs, false, gt, h->stream);
+    }
+  }
+  h->gate_mode_frame = h->gate_mode;
   const int gs = p.fixed ? 4 * h->n_sm : std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm));
   launch_parent_stats(h->hyps[h->hcur], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
                       gs, h->stream);
@@ -893,8 +923,10 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
     est_enqueued = false;   // the estimates copied with the first pass are stale
   }
   if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
+  if (e & kErrGate) return abandon(GLMB_E_CUDA, err_text(e));
   if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
   h->n_pairs = h->h_scal[S_K];
+  h->n_pairs_pregate = h->gate_mode_frame == GLMB_GATE_PRUNE ? (long long)h->h_scal[S_KFULL] : h->n_pairs;
   h->n_fp64 = (int)h->h_scal[S_FP64];
   const unsigned n_surv = cnt[0];
   if (n_surv == 0) return abandon(GLMB_E_NUMERIC, "no child has a finite weight above tau");
@@ -1202,6 +1234,7 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
     CU(cudaMemcpy(&K32, h->pt.ptr + h->T_work, sizeof K32, cudaMemcpyDeviceToHost));
     info->n_pairs = K32;
   }
+  info->n_pairs_pregate = h->gate_mode_frame == GLMB_GATE_PRUNE ? h->n_pairs_pregate : info->n_pairs;
   info->n_children = h->have_update ? (long long)h->H_par * h->cfg.h_up : 0;
   info->n_unique = h->n_unique;
   info->n_updates = h->n_upd;
@@ -1580,6 +1613,153 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
   if (status) CU(cudaMemcpy(status, h->child_status, (size_t)n, cudaMemcpyDeviceToHost));
   if (n_alive) CU(cudaMemcpy(n_alive, h->child_alive, (size_t)n * 2, cudaMemcpyDeviceToHost));
   return GLMB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned pair gate
+// ---------------------------------------------------------------------------
+glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, int mode) {
+  if (!h) return GLMB_E_INVALID;
+  if (mode != GLMB_GATE_OFF && mode != GLMB_GATE_PRUNE && mode != GLMB_GATE_SCORE)
+    return fail(h, GLMB_E_INVALID, "set_gate: unknown mode %d", mode);
+  if (mode != GLMB_GATE_OFF) {
+    if (!params) return fail(h, GLMB_E_INVALID, "set_gate: no parameters");
+    for (int i = 0; i < GLMB_GATE_NPARAM; ++i)
+      if (!std::isfinite(params[i])) return fail(h, GLMB_E_INVALID, "set_gate: parameter %d is not finite", i);
+    for (int j = 0; j < 5; ++j)
+      if (!(params[kGateSd + j] > 0.f)) return fail(h, GLMB_E_INVALID, "set_gate: sd[%d] <= 0", j);
+    if (std::isnan(threshold)) return fail(h, GLMB_E_INVALID, "set_gate: threshold is NaN");
+  }
+  CU(cudaStreamSynchronize(h->stream));
+  const int dz = h->md.dz;
+  if (mode != GLMB_GATE_OFF && !h->gate_params) {
+    if (!(dalloc(h, &h->gate_params, GLMB_GATE_NPARAM) && dalloc(h, &h->gate_keep, h->cap_pairs) &&
+          dalloc(h, &h->gate_logit, h->cap_pairs)))
+      return fail(h, GLMB_E_OOM, "set_gate: gate buffers");
+  }
+  if (mode == GLMB_GATE_PRUNE && !h->pt_full.ptr) {
+    PairTable& F = h->pt_full;
+    if (!(dalloc(h, &F.cnt, h->cap_comp + 1) && dalloc(h, &F.ptr, h->cap_comp + 1) &&
+          dalloc(h, &F.meas, h->cap_pairs) && dalloc(h, &F.logC, h->cap_pairs) && dalloc(h, &F.q, h->cap_pairs) &&
+          dalloc(h, &F.e, h->cap_pairs * dz) && dalloc(h, &F.dthr, h->cap_comp) &&
+          dalloc(h, &F.dprob, h->cap_comp))) {
+      F.ptr = nullptr;
+      return fail(h, GLMB_E_OOM, "set_gate: second pair table");
+    }
+    F.logdetS = h->pt.logdetS;
+    F.cap_pairs = h->cap_pairs;
+  }
+  if (mode != GLMB_GATE_OFF)
+    CU(cudaMemcpy(h->gate_params, params, GLMB_GATE_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+  if (mode != h->gate_mode) {
+    // captured frame graphs were built for the other table path
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+  }
+  h->gate_mode = mode;
+  h->gate_thr = threshold;
+  return GLMB_OK;
+}
+
+namespace {
+// the table of the last update before the learned gate
+const PairTable& pregate_table(const glmb_handle* h) {
+  return h->gate_mode_frame == GLMB_GATE_PRUNE ? h->pt_full : h->pt;
+}
+}  // namespace
+
+glmb_status glmb_gate_features(glmb_handle* h, float* X, int64_t cap, int64_t* n) {
+  if (!h || !n || (cap > 0 && !X)) return GLMB_E_INVALID;
+  if (!h->have_update) return fail(h, GLMB_E_STATE, "gate_features: no update");
+  CU(cudaStreamSynchronize(h->stream));
+  const PairTable& P0 = pregate_table(h);
+  uint32_t K32 = 0;
+  CU(cudaMemcpy(&K32, P0.ptr + h->T_work, sizeof K32, cudaMemcpyDeviceToHost));
+  *n = K32;
+  if ((int64_t)K32 > cap) return fail(h, GLMB_E_CAPACITY, "gate_features: %u pairs, cap %lld", K32, (long long)cap);
+  if (K32 == 0) return GLMB_OK;
+  if (!h->gate_X && !dalloc(h, &h->gate_X, h->cap_pairs * 5)) return fail(h, GLMB_E_OOM, "gate_features: scratch");
+  launch_gate_features(h->md, h->comps[1 - h->cur], P0, h->d_fs, h->gate_X, h->cap_pairs, 2 * h->n_sm, h->stream);
+  CU(cudaMemcpyAsync(X, h->gate_X, (size_t)K32 * 5 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GLMB_OK;
+}
+
+glmb_status glmb_gate_logits(glmb_handle* h, float* logit, int64_t cap, int64_t* n) {
+  if (!h || !n || (cap > 0 && !logit)) return GLMB_E_INVALID;
+  if (!h->have_update || h->gate_mode_frame == GLMB_GATE_OFF)
+    return fail(h, GLMB_E_STATE, "gate_logits: no update with the gate on");
+  CU(cudaStreamSynchronize(h->stream));
+  uint32_t K32 = 0;
+  CU(cudaMemcpy(&K32, pregate_table(h).ptr + h->T_work, sizeof K32, cudaMemcpyDeviceToHost));
+  *n = K32;
+  if ((int64_t)K32 > cap) return fail(h, GLMB_E_CAPACITY, "gate_logits: cap");
+  if (K32) CU(cudaMemcpy(logit, h->gate_logit, (size_t)K32 * sizeof(float), cudaMemcpyDeviceToHost));
+  return GLMB_OK;
+}
+
+glmb_status glmb_gate_usage(glmb_handle* h, uint8_t* used, int64_t cap_pairs, uint8_t* hyp_flag, int cap_h,
+                            int64_t* n_pairs, int* n_hyp) {
+  if (!h || !n_pairs || !n_hyp) return GLMB_E_INVALID;
+  if (!h->retained_valid || !h->theta_M_valid || !h->have_update)
+    return fail(h, GLMB_E_STATE, "gate_usage: no pruned frame");
+  if (h->gate_mode_frame == GLMB_GATE_PRUNE) return fail(h, GLMB_E_STATE, "gate_usage: the gate pruned the table");
+  CU(cudaStreamSynchronize(h->stream));
+  uint32_t K32 = 0;
+  CU(cudaMemcpy(&K32, h->pt.ptr + h->T_work, sizeof K32, cudaMemcpyDeviceToHost));
+  *n_pairs = K32;
+  *n_hyp = h->H;
+  if ((used && (int64_t)K32 > cap_pairs) || (hyp_flag && h->H > cap_h))
+    return fail(h, GLMB_E_CAPACITY, "gate_usage: arrays too short");
+  if (!h->gate_used && !(dalloc(h, &h->gate_used, h->cap_pairs) && dalloc(h, &h->gate_hflag, h->cap_h)))
+    return fail(h, GLMB_E_OOM, "gate_usage: scratch");
+  CU(cudaMemsetAsync(h->gate_used, 0, std::max<size_t>(K32, 1), h->stream));
+  CU(cudaMemsetAsync(h->gate_hflag, 0, std::max(h->H, 1), h->stream));
+  const int capT = std::max(1, (int)h->h_scal[S_MAXT]);
+  const bool score = h->gate_mode_frame == GLMB_GATE_SCORE;
+  launch_gate_usage(h->hyps[h->par_buf], h->hyps[h->hcur], h->comps[h->cur], h->comps[1 - h->cur], h->pw.surv_idx,
+                    h->H, h->cfg.h_up, h->theta_M, h->pt, h->d_fs, score ? h->gate_logit : nullptr, h->gate_thr,
+                    h->gate_used, h->gate_hflag, capT, std::max(1, std::min(h->H, 8 * h->n_sm)), h->stream);
+  if (used && K32) CU(cudaMemcpyAsync(used, h->gate_used, K32, cudaMemcpyDeviceToHost, h->stream));
+  if (hyp_flag && h->H) CU(cudaMemcpyAsync(hyp_flag, h->gate_hflag, (size_t)h->H, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return GLMB_OK;
+}
+
+glmb_status glmb_mlp_forward(const float* params, const float* X, int64_t n, float* logit, uint32_t* err,
+                             void* stream) {
+  if (n < 0 || !params || !err || (n > 0 && (!X || !logit))) return GLMB_E_INVALID;
+  if (n == 0) return GLMB_OK;
+  int dev = 0, n_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (n + 127) / 128;
+  const int grid = (int)std::max(1LL, std::min(tiles, 4LL * n_sm));
+  launch_gate_forward_rows(params, X, n, logit, err, grid, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? GLMB_OK : GLMB_E_CUDA;
+}
+
+glmb_status glmb_mlp_backward(const float* params, const float* X, const float* y, const float* wt, int64_t n,
+                              float* grad, double* loss, uint32_t* err, void* stream) {
+  if (n < 0 || !params || !grad || !loss || !err || (n > 0 && (!X || !y || !wt))) return GLMB_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(grad, 0, GLMB_GATE_NPARAM * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(loss, 0, sizeof(double), s) != cudaSuccess)
+    return GLMB_E_CUDA;
+  if (n == 0) return GLMB_OK;
+  int dev = 0, n_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (n + 127) / 128;
+  launch_gate_train(params, X, y, wt, n, grad, loss, err, (int)std::max(1LL, std::min(tiles, (long long)n_sm)), s);
+  return cudaGetLastError() == cudaSuccess ? GLMB_OK : GLMB_E_CUDA;
+}
+
+glmb_status glmb_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                          float beta2, float eps, void* stream) {
+  if (!params || !grad || !m || !v || step < 1) return GLMB_E_INVALID;
+  launch_gate_adam(params, grad, m, v, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? GLMB_OK : GLMB_E_CUDA;
 }
 
 }  // extern "C"

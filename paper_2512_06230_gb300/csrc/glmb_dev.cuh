@@ -30,6 +30,7 @@ enum : uint32_t {
   kErrEntries = 32u,    // hypothesis entries beyond capacity
   kErrSlots = 64u,      // per-hypothesis staging beyond the planned size
   kErrInput = 128u,     // a detection is NaN or infinite
+  kErrGate = 256u,      // a tensor-core wait of the learned gate ran out of time
 };
 
 constexpr float kFxScale = 4294967296.0f;          // 2^32
@@ -408,6 +409,54 @@ __device__ __forceinline__ unsigned long long dead_key(int t) {
 }
 __device__ __forceinline__ unsigned long long wset_key(int i) {
   return mix64(0x5A5A5A5A00000000ULL ^ (unsigned long long)(uint32_t)i);
+}
+
+// ---- log-sum-exp and the posterior death probability (reading R2) ----
+__device__ __forceinline__ void lse_push(float& m, float& s, float x) {
+  if (x == -INFINITY) return;
+  if (x > m) {
+    s = (m == -INFINITY ? 0.f : s * __expf(m - x)) + 1.f;
+    m = x;
+  } else {
+    s += __expf(x - m);
+  }
+}
+
+// combines the (max, scaled sum) pairs of the 32 lanes of a warp
+__device__ __forceinline__ void lse_warp(float& lm, float& ls) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float m2 = __shfl_xor_sync(0xFFFFFFFFu, lm, o);
+    const float s2 = __shfl_xor_sync(0xFFFFFFFFu, ls, o);
+    const float m = fmaxf(lm, m2);
+    if (m != -INFINITY) {
+      ls = (lm == -INFINITY ? 0.f : ls * __expf(lm - m)) + (m2 == -INFINITY ? 0.f : s2 * __expf(m2 - m));
+      lm = m;
+    }
+  }
+}
+
+// d_prob = (1 - p) / ((1 - p) + p psi), psi = (1 - P_D) + sum C / kappa,
+// from the LSE (lm, ls) of log C - log kappa over the component's gated
+// pairs (any: at least one pair), and its threshold on 24-bit uniforms
+__device__ __forceinline__ void death_prob(const Model& md, float logp, float log1mp, float lm, float ls,
+                                           bool any, float& d_out, uint32_t& thr_out) {
+  float logpsi;
+  if (md.kappa_zero && any) {
+    logpsi = INFINITY;
+  } else {
+    float m = lm, s = ls;
+    lse_push(m, s, md.log_1mpd);
+    logpsi = (m == -INFINITY) ? -INFINITY : m + logf(s);
+  }
+  float d;
+  if (logp == -INFINITY) d = 1.f;
+  else if (log1mp == -INFINITY) d = 0.f;
+  else if (logpsi == INFINITY) d = 0.f;
+  else if (logpsi == -INFINITY) d = 1.f;
+  else d = 1.f / (1.f + expf(logp + logpsi - log1mp));
+  d_out = d;
+  thr_out = d >= 1.f ? kOne24 : (d <= 0.f ? 0u : (uint32_t)ceilf(d * 16777216.f));
 }
 
 }  // namespace glmb

@@ -167,7 +167,43 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
                   const unsigned* err, cudaStream_t s);
 // device error flags that abandon a frame (state left untouched)
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
-                               kErrEntries | kErrSlots | kErrInput;
+                               kErrEntries | kErrSlots | kErrInput | kErrGate;
+
+// ---- learned pair gate (gate_mlp.cu) ----
+// parameter vector (floats): W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64]
+// b3[64] w4[64] b4 mu[5] sd[5]; the first kGateNTrain are trained
+constexpr int kGateW1 = 0, kGateB1 = 320, kGateW2 = 384, kGateB2 = 4480, kGateW3 = 4544,
+              kGateB3 = 8640, kGateW4 = 8704, kGateB4 = 8768, kGateMu = 8769, kGateSd = 8774;
+constexpr int kGateNParam = 8779, kGateNTrain = 8769;
+int gate_forward_smem();
+int gate_train_smem();
+// logits of n raw feature rows X[n][5] (persistent grid, 128 rows per tile)
+void launch_gate_forward_rows(const float* P, const float* X, long long n, float* logit, unsigned* err,
+                              int grid, cudaStream_t s);
+// logits and keep flags (logit >= thr) of every pair of the table `full`
+void launch_gate_forward_table(const float* P, float thr, const Model& md, const CompTable& ct,
+                               const PairTable& full, const FrameDev* fs, float* logit, uint8_t* keep,
+                               unsigned* err, int grid, cudaStream_t s);
+// adds the gradient of sum wt (softplus(z) - y z) to grad and the loss to *loss
+void launch_gate_train(const float* P, const float* X, const float* y, const float* wt, long long n,
+                       float* grad, double* loss, unsigned* err, int grid, cudaStream_t s);
+void launch_gate_adam(float* P, const float* G, float* m, float* v, int t, float lr, float b1, float b2,
+                      float eps, cudaStream_t s);
+// raw features of the pairs of table pt into X (at most cap rows)
+void launch_gate_features(const Model& md, const CompTable& ct, const PairTable& pt, const FrameDev* fs,
+                          float* X, long long cap, int grid, cudaStream_t s);
+// count = true: kept pairs per component into gated.cnt; false: stable
+// compaction into gated (whose ptr is the scan of cnt) and death probabilities
+void launch_gate_compact(const Model& md, const CompTable& ct, const PairTable& full, const uint8_t* keep,
+                         const PairTable& gated, const FrameDev* fs, bool count, int grid, cudaStream_t s);
+// pairs of table pt used by the H_new retained hypotheses `out` (children
+// surv[j] of parents `par`; A the new state's components, B the predicted
+// ones; capT >= the largest retained track count), and per retained
+// hypothesis whether it uses a pair with logit < thr (logit nullable)
+void launch_gate_usage(const HypTable& par, const HypTable& out, const CompTable& A, const CompTable& B,
+                       const long long* surv, int H_new, int h_up, int M, const PairTable& pt, const FrameDev* fs,
+                       const float* logit, float thr, uint8_t* used, uint8_t* hflag, int capT, int grid,
+                       cudaStream_t s);
 
 // estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, r[pcap] (existence
 // sums, zeroed by the first kernel), tracks = glmb_track[pcap]; done is a

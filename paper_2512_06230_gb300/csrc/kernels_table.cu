@@ -209,16 +209,6 @@ __global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const F
   }
 }
 
-__device__ __forceinline__ void lse_push(float& m, float& s, float x) {
-  if (x == -INFINITY) return;
-  if (x > m) {
-    s = (m == -INFINITY ? 0.f : s * __expf(m - x)) + 1.f;
-    m = x;
-  } else {
-    s += __expf(x - m);
-  }
-}
-
 template <int DZ>
 __device__ void table_write_comp(const Model& md, const CompTable& ct, const PairTable& pt, int c,
                                  const float* __restrict__ Z, int M, unsigned* n_fp64,
@@ -286,37 +276,10 @@ __device__ void table_write_comp(const Model& md, const CompTable& ct, const Pai
     }
     off += __popc(bal);
   }
-  // warp-combine the log-sum-exp
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float m2 = __shfl_xor_sync(0xFFFFFFFFu, lm, o);
-    const float s2 = __shfl_xor_sync(0xFFFFFFFFu, ls, o);
-    const float m = fmaxf(lm, m2);
-    if (m != -INFINITY) {
-      ls = (lm == -INFINITY ? 0.f : ls * __expf(lm - m)) + (m2 == -INFINITY ? 0.f : s2 * __expf(m2 - m));
-      lm = m;
-    }
-  }
+  lse_warp(lm, ls);
   const bool any_w = __any_sync(0xFFFFFFFFu, any);
   if (lane == 0) {
-    // log psi = log((1 - P_D) + sum C / kappa)
-    float logpsi;
-    if (md.kappa_zero && any_w) {
-      logpsi = INFINITY;
-    } else {
-      float m = lm, s = ls;
-      lse_push(m, s, md.log_1mpd);
-      logpsi = (m == -INFINITY) ? -INFINITY : m + logf(s);
-    }
-    const float logp = ct.logp[c], log1mp = ct.log1mp[c];
-    float d;
-    if (logp == -INFINITY) d = 1.f;
-    else if (log1mp == -INFINITY) d = 0.f;
-    else if (logpsi == INFINITY) d = 0.f;
-    else if (logpsi == -INFINITY) d = 1.f;
-    else d = 1.f / (1.f + expf(logp + logpsi - log1mp));
-    pt.dprob[c] = d;
-    pt.dthr[c] = d >= 1.f ? kOne24 : (d <= 0.f ? 0u : (uint32_t)ceilf(d * 16777216.f));
+    death_prob(md, ct.logp[c], ct.log1mp[c], lm, ls, any_w, pt.dprob[c], pt.dthr[c]);
     pt.logdetS[c] = g.logdet;
   }
 }

@@ -23,6 +23,11 @@ REL_TOL = 1e-5
 DECISION_MARGIN = 1e-5
 BOUNDARY_TOL = 2 * LOGW_TOL
 GATE_MARGIN = 1e-5
+# learned gate: a pair whose oracle logit is within MLP_MARGIN of the
+# threshold may be decided either way (the kernel standardises fp32 features,
+# so an input can round to the neighbouring bf16 value; a one-ulp change of
+# an input moves the logit by about 1e-2 for unit-scale weights)
+MLP_MARGIN = 0.05
 
 
 @dataclass
@@ -49,15 +54,20 @@ def oracle_state(oracle_mod, cfg, scene, n_frames, n_threads=8):
     return o.export_state()
 
 
-def run_frame(oracle_mod, glmb, cfg, state, births, Z, n_threads=8):
+def run_frame(oracle_mod, glmb, cfg, state, births, Z, n_threads=8, gate=None):
     """Both implementations from the same state through one frame; returns
-    (oracle, filter, data) with every intermediate needed by compare()."""
+    (oracle, filter, data) with every intermediate needed by compare().
+    gate: (params, threshold) of a learned gate that prunes pairs on both sides."""
     frame, logw, uid, tracks = state
     o = oracle_mod.Oracle(cfg, n_threads=n_threads)
     o.import_state(frame, logw, uid, tracks)
+    if gate is not None:
+        o.set_gate(gate[0], gate[1])
     o.predict(births)
     o.update(Z)
     g = glmb.Filter(cfg)
+    if gate is not None:
+        g.set_gate(gate[0], gate[1], glmb.Filter.GATE_PRUNE)
     g.import_state(glmb.pack_state(frame, logw, uid, tracks, g.dx))
     g.predict(births)
     g.update(Z)
@@ -88,7 +98,9 @@ def compare(o, g, d, cfg, Z, report: Report | None = None) -> Report:
     G = cfg["gate"]
     # ---- a1 prediction, a2 table, a3 death probability, per (parent, slot)
     n_slots = 0
-    near_gate_parents = set()
+    # parents with a pair close to either gate's decision: their tables may
+    # legitimately differ by that pair
+    near_gate_parents = {h for h in range(H) if o.mlp_margin(h) < MLP_MARGIN}
     for h in range(H):
         T = o.parent_slots(h)
         if gptr[h + 1] - gptr[h] != T:
