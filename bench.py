@@ -270,6 +270,234 @@ def run_convoy(args, glmb, torch):
                       "grid": grid}))
 
 
+def run_sweep(args, glmb, torch, dev):
+    """The 3-D scalability grid: N objects alive from frame 0 (held near N by
+    Poisson(0.01 N) births per frame), clutter Poisson(50), P_D 0.85,
+    1 + Poisson(2) detections, 50 frames, for N in --sweep-n and H_max in
+    --sweep-h.  Per cell: one untimed pass fills the graph cache, then every
+    frame is timed with CUDA events (detections resident, L2 flushed between
+    frames, estimates read back inside the frame).  Reports frames/s over
+    all frames and over frames 10-49 (after the birth transient) and
+    hypothesis-track updates/s.  The FP64 oracle (all host threads) is timed
+    on the first --sweep-oracle-frames frames of the cells with N * H_max up
+    to --sweep-oracle-max, the rest are "not run"."""
+    import oracle
+    grid = []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for N in _ints(args.sweep_n):
+        for H in _ints(args.sweep_h):
+            sc = scenes.make_scene(scenes.preset(f"sweep_N{N}", h_max=H),
+                                   3000 + N if args.seed is None else args.seed)
+            cfg = filter_cfg(sc)
+            try:
+                row = _sweep_cell(args, glmb, torch, dev, flush, sc, cfg)
+            except glmb.GlmbError as e:
+                row = dict(error=str(e))
+            row = dict(N=N, H_max=H, **row)
+            if N * H <= args.sweep_oracle_max and args.sweep_oracle_frames > 0:
+                threads = os.cpu_count() or 1
+                o = oracle.Oracle(cfg, n_threads=threads)
+                per = []
+                for fr in sc.frames[:args.sweep_oracle_frames]:
+                    t0 = time.perf_counter()
+                    o.step(fr.births, fr.Z)
+                    o.estimates()
+                    per.append(time.perf_counter() - t0)
+                row["oracle_ms_last_frame"] = 1e3 * per[-1]
+                row["oracle"] = f"frames 0..{len(per) - 1}, {threads} threads"
+                if "frame_ms" in row:
+                    row["gpu_ms_same_frame"] = row["frame_ms"][len(per) - 1]
+            else:
+                row["oracle"] = "not run"
+            row.pop("frame_ms", None)
+            grid.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "3-D sweep: GLMB update frames/s and hypothesis-track updates/s vs N, H_max (1 GB300)",
+                      "unit": "frames/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "3-D CV in [0,5000]^3, N alive from frame 0, clutter Poisson(50), "
+                                             "P_D 0.85, 1+Poisson(2) detections, 50 frames, H_up=100",
+                                 "l2": "flushed between frames (256 MiB write, outside the timed events)"},
+                      "grid": grid}))
+
+
+def _sweep_cell(args, glmb, torch, dev, flush, sc, cfg):
+    """One (N, H_max) cell of the sweep: per-frame CUDA-event times."""
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    f = glmb.Filter(cfg, stream=stream.cuda_stream)
+    try:
+        Zdev = [torch.from_numpy(fr.Z).to(dev) for fr in sc.frames]
+        B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+        for k in range(len(sc.frames)):                    # untimed: graph captures
+            f.step(B[k], Zdev[k], device=True)
+        f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+        f.reset()
+        torch.cuda.synchronize()
+        times, entries, hyps = [], [], []
+        for k in range(len(sc.frames)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.step(B[k], Zdev[k], device=True)
+            f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            info = f.info()
+            entries.append(info["n_entries"])
+            hyps.append(info["n_hyp"])
+    finally:
+        f.close()
+        torch.cuda.synchronize()
+    steady = slice(10, len(times))
+    return dict(frames=len(times),
+                frames_per_s=len(times) / (sum(times) / 1e3),
+                frames_per_s_steady=len(times[steady]) / (sum(times[steady]) / 1e3),
+                ms_per_frame_steady=statistics.fmean(times[steady]),
+                hypothesis_track_updates_per_s=sum(entries) / (sum(times) / 1e3),
+                hypothesis_track_updates_per_s_steady=sum(entries[steady]) / (sum(times[steady]) / 1e3),
+                mean_M=statistics.fmean(len(fr.Z) for fr in sc.frames),
+                mean_hypotheses_steady=statistics.fmean(hyps[steady]), frame_ms=times)
+
+
+def _timed_run(f, frames, B, Zdev, torch, stream, flush, truth_dim, lost=False):
+    """One pass of the scene through glmb_step with per-frame CUDA-event
+    times (after an untimed pass that fills the graph cache); returns
+    times, OSPA per frame, pairs after / before the gate, lost mass."""
+    from scenes.metrics import ospa
+    f.set_profiling(["table", "expand", "select", "materialize"])
+    for k in range(len(frames)):
+        f.step(B[k], Zdev[k], device=True)
+    f.reset()
+    torch.cuda.synchronize()
+    f.set_profiling(["table", "expand", "select", "materialize"])   # clears the totals
+    times, osp, pairs, pre, lm = [], [], [], [], []
+    for k, fr in enumerate(frames):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.step(B[k], Zdev[k], device=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        est = f.estimates(cap=f.cfg["max_tracks"], pmf_cap=64)
+        osp.append(ospa(est["mean"][:, :truth_dim], fr.truth[:, :truth_dim], c=100.0))
+        info = f.info()
+        pairs.append(info["n_pairs"])
+        pre.append(info["n_pairs_pregate"])
+        if lost:
+            _, flag = f.gate_usage()
+            w = np.exp(f.hypotheses()["logw"])
+            lm.append(float(np.sum(w * flag) / np.sum(w)))
+    stages = {k: v[0] / max(v[1], 1) for k, v in f.timing().items() if v[1]}
+    return times, osp, pairs, pre, lm, stages
+
+
+def run_gate(args, glmb, torch, dev):
+    """The learned pair gate on the 3-D workload (N objects alive from frame
+    0, clutter Poisson(50), P_D 0.85, 1 + Poisson(2) detections, H_max):
+    training data (features and usage labels) from the ungated filter on
+    --gate-train scenes, training by the library's kernels, a threshold that
+    keeps --gate-keep of the used training pairs, then --gate-eval held-out
+    scenes run three ways: without the gate (frame time, OSPA), with the gate
+    scoring only (lost mass: the weight of retained hypotheses that use a
+    pair the gate would prune) and with the gate pruning (frame time, OSPA,
+    pairs).  Repeated for each base Mahalanobis gate tail in --gate-tails."""
+    from paper_2512_06230_gb300 import gate as G
+    N, H, F = args.gate_n, args.gate_h, args.gate_frames
+    base = scenes.preset("sweep_N200", n_objects=N, births_per_frame=0.01 * N, h_max=H, frames=F)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = []
+    for tail in [float(t) for t in args.gate_tails.split(",")]:
+        def cfg_for(sc):
+            c = filter_cfg(sc)
+            c["gate"] = scenes.chi2_gate(3, tail)
+            c["max_pairs"] = 1 << 22
+            return c
+        t0 = time.perf_counter()
+        Xs, ys = [], []
+        for s in range(args.gate_train):
+            sc = scenes.make_scene(base, 50000 + s)
+            X, y = G.collect(cfg_for(sc), [(glmb.births_array(fr.births, sc.dim_x), fr.Z) for fr in sc.frames],
+                             skip=2)
+            Xs.append(X)
+            ys.append(y)
+        X, y = np.concatenate(Xs), np.concatenate(ys)
+        t_collect = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        params, hist = G.train(X, y, steps=args.gate_steps, batch=32768, lr=2e-3, seed=1, log_every=500)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        thr = G.threshold(params, X, y, keep_used=args.gate_keep)
+        z = G.logits(params, X)
+        keep = z >= thr
+        ev = dict(plain_ms=[], gated_ms=[], plain_ospa=[], gated_ospa=[], plain_pairs=[], gated_pairs=[],
+                  lost=[], plain_stages=[], gated_stages=[])
+        for s in range(args.gate_eval):
+            sc = scenes.make_scene(base, 60000 + s)
+            cfg = cfg_for(sc)
+            Zdev = [torch.from_numpy(fr.Z).to(dev) for fr in sc.frames]
+            B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+            for mode in ("plain", "score", "gated"):
+                f = glmb.Filter(cfg, stream=stream.cuda_stream)
+                if mode == "score":
+                    f.set_gate(params, thr, glmb.Filter.GATE_SCORE)
+                elif mode == "gated":
+                    f.set_gate(params, thr, glmb.Filter.GATE_PRUNE)
+                try:
+                    tm, osp, pairs, pre, lm, stg = _timed_run(f, sc.frames, B, Zdev, torch, stream, flush, 3,
+                                                              lost=(mode == "score"))
+                finally:
+                    f.close()
+                if mode != "score":
+                    ev[mode + "_stages"].append(stg)
+                if mode == "plain":
+                    ev["plain_ms"] += tm[2:]
+                    ev["plain_ospa"] += osp
+                    ev["plain_pairs"] += pairs[2:]
+                elif mode == "score":
+                    ev["lost"] += lm[2:]
+                else:
+                    ev["gated_ms"] += tm[2:]
+                    ev["gated_ospa"] += osp
+                    ev["gated_pairs"] += pairs[2:]
+            del Zdev
+        row = {"gate_tail": tail, "gate_G": scenes.chi2_gate(3, tail), "threshold": thr,
+               "train": {"scenes": args.gate_train, "frames_per_scene": F - 2, "pairs": int(len(y)),
+                         "used_fraction": float(y.mean()), "collect_s": round(t_collect, 2),
+                         "train_s": round(t_train, 2), "steps": args.gate_steps,
+                         "loss_history": hist, "used_kept": float(keep[y > 0].mean()),
+                         "pairs_kept": float(keep.mean())},
+               "held_out": {"scenes": args.gate_eval,
+                            "plain_ms_per_frame": statistics.fmean(ev["plain_ms"]),
+                            "gated_ms_per_frame": statistics.fmean(ev["gated_ms"]),
+                            "speedup": statistics.fmean(ev["plain_ms"]) / statistics.fmean(ev["gated_ms"]),
+                            "plain_pairs_per_frame": statistics.fmean(ev["plain_pairs"]),
+                            "gated_pairs_per_frame": statistics.fmean(ev["gated_pairs"]),
+                            "lost_mass_mean": statistics.fmean(ev["lost"]),
+                            "lost_mass_max": max(ev["lost"]),
+                            "ospa_plain": statistics.fmean(ev["plain_ospa"]),
+                            "ospa_gated": statistics.fmean(ev["gated_ospa"]),
+                            "stage_ms_plain": {k: statistics.fmean(d[k] for d in ev["plain_stages"])
+                                               for k in ev["plain_stages"][0]},
+                            "stage_ms_gated": {k: statistics.fmean(d[k] for d in ev["gated_stages"])
+                                               for k in ev["gated_stages"][0]}}}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "learned pair gate: frame time, lost mass and OSPA, gated vs plain (1 GB300)",
+                      "unit": "ms/frame", "higher_is_better": False, "dtype": "bf16 (gate MLP) / f32",
+                      "data": "synthetic",
+                      "config": {"workload": f"3-D CV in [0,5000]^3, N={N}, H_max={H}, H_up=100, clutter Poisson(50), "
+                                             f"P_D 0.85, 1+Poisson(2) detections, {F} frames per scene (first 2 "
+                                             "not scored)", "ospa": "c = 100 m, p = 1, MAP estimates",
+                                 "l2": "flushed between frames"},
+                      "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,6 +518,19 @@ def main():
     ap.add_argument("--convoy-steps", type=int, default=548)
     ap.add_argument("--convoy-oracle-steps", type=int, default=20)
     ap.add_argument("--runs", type=int, default=3, help="--scene convoy: seeds per configuration")
+    ap.add_argument("--sweep-n", default="50,200,500,1000", help="--scene sweep: object counts")
+    ap.add_argument("--sweep-h", default="1000,5000,20000", help="--scene sweep: H_max values")
+    ap.add_argument("--sweep-oracle-frames", type=int, default=4)
+    ap.add_argument("--sweep-oracle-max", type=int, default=200 * 1000,
+                    help="--scene sweep: largest N * H_max the oracle is timed on")
+    ap.add_argument("--gate-n", type=int, default=300, help="--scene gate: objects")
+    ap.add_argument("--gate-h", type=int, default=5000, help="--scene gate: H_max")
+    ap.add_argument("--gate-frames", type=int, default=30)
+    ap.add_argument("--gate-train", type=int, default=40, help="--scene gate: training scenes")
+    ap.add_argument("--gate-eval", type=int, default=8, help="--scene gate: held-out scenes")
+    ap.add_argument("--gate-steps", type=int, default=3000)
+    ap.add_argument("--gate-keep", type=float, default=0.99999, help="fraction of used training pairs kept")
+    ap.add_argument("--gate-tails", default="1e-4,1e-12,1e-30", help="chi-square tails of the base gate")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
@@ -332,6 +573,10 @@ def main():
         return run_batch(args, glmb, torch, dev)
     if args.scene == "convoy":
         return run_convoy(args, glmb, torch)
+    if args.scene == "sweep":
+        return run_sweep(args, glmb, torch, dev)
+    if args.scene == "gate":
+        return run_gate(args, glmb, torch, dev)
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)

@@ -546,8 +546,14 @@ def _tptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _stream(stream):
-    return C.c_void_p(stream) if stream is not None else None
+def _stream(stream, t):
+    """The CUDA stream to enqueue on: the given one, else torch's current
+    stream on the device of tensor t (so the call orders with torch's own
+    work on its tensors)."""
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
 def mlp_forward(params, X, err, stream=None):
@@ -557,7 +563,7 @@ def mlp_forward(params, X, err, stream=None):
     import torch
     n = int(X.shape[0])
     out = torch.empty(n, dtype=torch.float32, device=X.device)
-    st = load().glmb_mlp_forward(_tptr(params), _tptr(X), n, _tptr(out), _tptr(err), _stream(stream))
+    st = load().glmb_mlp_forward(_tptr(params), _tptr(X), n, _tptr(out), _tptr(err), _stream(stream, X))
     if st:
         raise GlmbError(st, "mlp_forward")
     return out
@@ -567,14 +573,14 @@ def mlp_backward(params, X, y, wt, grad, loss, err, stream=None):
     """Fills grad (GATE_NPARAM float32) and loss (one float64) on the device."""
     n = int(X.shape[0])
     st = load().glmb_mlp_backward(_tptr(params), _tptr(X), _tptr(y), _tptr(wt), n, _tptr(grad), _tptr(loss),
-                                  _tptr(err), _stream(stream))
+                                  _tptr(err), _stream(stream, X))
     if st:
         raise GlmbError(st, "mlp_backward")
 
 
 def mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     st = load().glmb_mlp_adam(_tptr(params), _tptr(grad), _tptr(m), _tptr(v), int(step), C.c_float(lr),
-                              C.c_float(beta1), C.c_float(beta2), C.c_float(eps), _stream(stream))
+                              C.c_float(beta1), C.c_float(beta2), C.c_float(eps), _stream(stream, params))
     if st:
         raise GlmbError(st, "mlp_adam")
 

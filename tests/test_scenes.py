@@ -78,3 +78,17 @@ def test_oracle_tracks_a_short_convoy(oracle_mod):
     s = acc.summary()
     assert s["rel_card_error"] < 0.05, s
     assert s["tracking_error_m"] < 0.25, s
+
+
+def test_ospa_closed_forms():
+    from scenes.metrics import ospa
+    a = np.array([[0.0, 0.0], [10.0, 0.0]])
+    assert ospa(a, a) == 0.0
+    assert ospa(np.zeros((0, 2)), a, c=50) == 50.0
+    # one missed object out of two: (0 + c) / 2
+    assert ospa(a[:1], a, c=40.0) == pytest.approx(20.0)
+    # shifted by 3 and the cut-off not reached: mean distance
+    assert ospa(a + [0.0, 3.0], a, c=100.0) == pytest.approx(3.0)
+    # order 2 with one far pair: sqrt((d1^2 + c^2) / 2)
+    b = np.array([[0.0, 4.0], [500.0, 0.0]])
+    assert ospa(b, a, c=30.0, p=2) == pytest.approx(np.sqrt((16 + 900) / 2))
