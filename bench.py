@@ -498,6 +498,63 @@ def run_gate(args, glmb, torch, dev):
                       "rows": rows}))
 
 
+def run_mlp(args, glmb, torch, dev):
+    """The learned gate's MLP kernels alone on --mlp-rows synthetic feature
+    rows (features resident in device memory): forward (glmb_mlp_forward)
+    and forward + backward (glmb_mlp_backward), --steps timed launches each
+    after --warmup, CUDA events on the launching stream.  Dense work per row:
+    forward 2 (5*64 + 64*64 + 64*64 + 64) flops, the backward's two
+    activation-gradient products and three weight-gradient products add
+    2 (2*64*64 + 5*64 + 2*64*64 + 64) more after its own forward."""
+    rng = np.random.default_rng(0 if args.seed is None else args.seed)
+    n = args.mlp_rows
+    X = np.stack([rng.chisquare(2, n) * 3, rng.gamma(2.0, 4.0, n), rng.uniform(0, 1, n),
+                  rng.integers(0, 40, n).astype(float), rng.normal(5.0, 1.5, n)], 1).astype(np.float32)
+    mu, sd = X.mean(0), X.std(0)
+    from paper_2512_06230_gb300 import gate as G
+    P = torch.from_numpy(G.init_params(1, mu, sd)).to(dev)
+    Xd = torch.from_numpy(X).to(dev)
+    y = torch.from_numpy((rng.uniform(size=n) < 0.3).astype(np.float32)).to(dev)
+    wt = torch.full((n,), 1.0 / n, device=dev)
+    grad = torch.zeros(glmb.GATE_NPARAM, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+    f_fwd = 2.0 * (5 * 64 + 64 * 64 + 64 * 64 + 64)
+    f_bwd = f_fwd + 2.0 * (2 * 64 * 64 + 5 * 64 + 2 * 64 * 64 + 64)
+    for name, call, flops in (("forward", lambda: glmb.mlp_forward(P, Xd, err), f_fwd),
+                              ("forward+backward", lambda: glmb.mlp_backward(P, Xd, y, wt, grad, loss, err), f_bwd)):
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            call()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = dict(ms=ms, rows_per_s=n / (ms / 1e3), tflops=n * flops / (ms * 1e-3) / 1e12)
+    assert int(err.item()) == 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops", 1900.0)
+    fw = out["forward"]
+    print(json.dumps({"metric": "learned-gate MLP rows/s (5-64-64-64-1 GELU, bf16 tcgen05)", "value": fw["rows_per_s"],
+                      "unit": "rows/s", "higher_is_better": True, "dtype": "bf16 x bf16 -> f32", "data": "synthetic",
+                      "config": {"workload": f"{n} feature rows resident in device memory", "rows": n},
+                      "kernels": out,
+                      "roofline": {"bound": "tensor", "achieved": fw["tflops"], "peak": peak, "unit": "TFLOP/s",
+                                   "frac": fw["tflops"] / peak,
+                                   "peak_source": "MEASURED_PEAKS.json bf16_tflops" if "bf16_tflops" in peaks
+                                   else "fallback 1900"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,6 +588,7 @@ def main():
     ap.add_argument("--gate-steps", type=int, default=3000)
     ap.add_argument("--gate-keep", type=float, default=0.99999, help="fraction of used training pairs kept")
     ap.add_argument("--gate-tails", default="1e-4,1e-12,1e-30", help="chi-square tails of the base gate")
+    ap.add_argument("--mlp-rows", type=int, default=1 << 22, help="--scene mlp: feature rows")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
@@ -577,6 +635,8 @@ def main():
         return run_sweep(args, glmb, torch, dev)
     if args.scene == "gate":
         return run_gate(args, glmb, torch, dev)
+    if args.scene == "mlp":
+        return run_mlp(args, glmb, torch, dev)
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)
