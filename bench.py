@@ -142,7 +142,7 @@ def run_oracle(args, sc, cfg, budget_s):
 def batch_cfg(p, sc):
     return sc.filter_config(max_meas=int(p.n_objects * 0.9 * 6 + 4 * p.clutter_rate + 64),
                             max_births=64, max_tracks=p.n_objects + 48,
-                            max_components=40 * (p.n_objects + 48), max_pairs=1 << 20)
+                            max_components=400 * (p.n_objects + 48), max_pairs=1 << 20)
 
 
 def run_batch(args, glmb, torch, dev):

@@ -888,7 +888,8 @@ void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, co
   prof_begin(h, kStageEstimates);
   launch_estimates(Y, H, H_dev, A, h->md.dx, (double*)(h->d_est + h->est_off_pmf), pcap, (int*)h->d_est,
                    (double*)(h->d_est + h->est_off_r), h->d_est + h->est_off_tr,
-                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, h->stream);
+                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, H_dev ? h->d_scal + S_ERR : nullptr,
+                   h->stream);
   prof_end(h, kStageEstimates);
 }
 

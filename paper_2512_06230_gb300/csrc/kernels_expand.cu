@@ -651,6 +651,9 @@ __global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H;
+  // a table that failed (e.g. pairs beyond capacity, whose offsets then run
+  // past the pair arrays) is not staged; the frame is abandoned
+  if (*(volatile const unsigned*)a.err & kErrFatal) return;
   for (int h = blockIdx.x; h < H; h += gridDim.x) {
     unsigned char* img = a.img + (size_t)h * a.img_stride;
     __syncthreads();   // the previous parent's copy-out has read shared memory
@@ -893,6 +896,9 @@ __global__ void __launch_bounds__(256) draw_kernel(const ExpandArgs a) {
   const int H = a.fs->H, HU = a.md.h_up;
   const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
   const int nsl = (HU + (int)blockDim.x - 1) / (int)blockDim.x;
+  // a failed table or staging (the frame is redone or abandoned): the
+  // images may be stale, so nothing is drawn
+  if (*(volatile const unsigned*)a.err & kErrFatal) return;
   for (int job = blockIdx.x; job < H * nsl; job += gridDim.x) {
     const int h = job / nsl;
     const int n = (job % nsl) * (int)blockDim.x + (int)threadIdx.x;
@@ -1149,8 +1155,10 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int HU = a.md.h_up, M = a.fs->M;
   const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
-  // a frame already abandoned (e.g. entries beyond capacity) writes nothing
+  // a frame already abandoned (e.g. entries beyond capacity) writes
+  // nothing; a failed table or staging leaves the images stale
   if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) return;
+  if (!MAT && (*(volatile const unsigned*)a.err & kErrFatal)) return;
   const long long count = MAT ? (long long)*a.n_surv
                               : (a.warp_all ? (long long)a.fs->H * HU : (long long)*a.redo_count);
   // an empty list (the usual overflow case) costs no work-area set-up

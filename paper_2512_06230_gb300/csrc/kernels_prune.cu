@@ -662,8 +662,10 @@ __device__ __forceinline__ unsigned long long w_fx(double logw) {
 // heaviest hypothesis of that cardinality (ties to the lower index); one
 // block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
 __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap,
-                                int* nb, unsigned long long* r_fx) {
+                                int* nb, unsigned long long* r_fx, const unsigned* err) {
   pdl_enter();
+  // a frame that failed left the new table incomplete: nothing to read
+  if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
   extern __shared__ unsigned long long s_pmf[];   // [pcap]
   __shared__ unsigned long long bw[32];
   __shared__ int bi[32];
@@ -754,8 +756,9 @@ __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
 // records (mean hi + lo in FP64, full covariance).
 __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev, CompTable ct, int dx,
                                  const int* __restrict__ nb, unsigned long long* r_fx, glmb_track* out,
-                                 int cap, unsigned* done) {
+                                 int cap, unsigned* done, const unsigned* err) {
   pdl_enter();
+  if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
   extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
   unsigned long long* s_r = s_key + cap;
   __shared__ bool last;
@@ -765,8 +768,9 @@ __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev,
   const int wpb = blockDim.x >> 5;
   const uint32_t b0 = best >= 0 ? hp.ptr[best] : 0u;
   const int nmap = best >= 0 ? min((int)(hp.ptr[best + 1] - b0), cap) : 0;
+  const uint32_t ccap = (uint32_t)ct.cap;
   for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
-    const uint32_t cm = hp.comp[b0 + j];
+    const uint32_t cm = min(hp.comp[b0 + j], ccap - 1u);
     s_key[j] = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
     s_r[j] = 0ull;
   }
@@ -775,7 +779,7 @@ __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev,
     const uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
     const unsigned long long wgt = w_fx(hp.logw[h]);
     for (uint32_t e = lo + lane; e < hi; e += 32) {
-      const uint32_t c = hp.comp[e];
+      const uint32_t c = min(hp.comp[e], ccap - 1u);
       const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
       int l = 0, u = nmap;
       while (l < u) {
@@ -796,7 +800,7 @@ __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev,
   __threadfence();
   const size_t cc = ct.cap;
   for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
-    const uint32_t c = hp.comp[b0 + j];
+    const uint32_t c = min(hp.comp[b0 + j], ccap - 1u);
     glmb_track& t = out[j];
     t.label_k = ct.lk[c];
     t.label_b = ct.lb[c];
@@ -816,16 +820,16 @@ __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev,
 
 void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
                       double* pmf, int pcap, int* nb, double* r, void* tracks, unsigned* done, int n_sm,
-                      cudaStream_t s) {
+                      const unsigned* err, cudaStream_t s) {
   if (pcap * 16 > 48 * 1024) {
     cudaFuncSetAttribute(est_card_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
     cudaFuncSetAttribute(est_exist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
   }
   unsigned long long* r_fx = reinterpret_cast<unsigned long long*>(r);
-  launch_k(est_card_kernel, 1, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_fx);
+  launch_k(est_card_kernel, 1, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_fx, err);
   const int blocks = H_dev ? 2 * n_sm : std::max(1, std::min((H + 7) / 8, 2 * n_sm));
   launch_k(est_exist_kernel, blocks, 256, (size_t)pcap * 16, s, hp, H, H_dev, ct, dx, nb, r_fx, (glmb_track*)tracks,
-                                                         pcap, done);
+                                                         pcap, done, err);
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {

@@ -70,3 +70,47 @@ def test_paths_agree_mid(glmb):
 def test_paths_agree_3d(glmb):
     F = glmb.Filter
     _run_lockstep(glmb, "sweep_N50", 13, 6, [0, F.OPT_DRAW_WARP | F.OPT_STAGE_GLOBAL, F.OPT_DRAW_THREAD])
+
+
+def _burst_frames(seed, k_burst, n_extra):
+    """The tiny scene with a burst of extra detections at frame k_burst,
+    all near existing detections: a parent's gated pairs jump past the
+    estimate from earlier frames, so the frame's expansion is redone with
+    the exact maxima."""
+    sc = scenes.make_scene(scenes.preset("tiny"), seed)
+    rng = np.random.default_rng(seed)
+    frames = []
+    for k, fr in enumerate(sc.frames[:k_burst + 3]):
+        Z = fr.Z
+        if k == k_burst and len(fr.truth):
+            # around one object's true position: every extra detection gates
+            # with its track, so the pair count of every parent holding the
+            # track jumps by n_extra
+            extra = fr.truth[0, :2] + rng.normal(scale=2.0, size=(n_extra, 2))
+            Z = np.concatenate([Z, extra.astype(np.float32)])
+        frames.append((fr.births, Z))
+    return sc, frames
+
+
+def test_redone_frame_in_the_graph_path_matches_separate_calls(glmb):
+    """A frame whose expansion plan is exceeded is redone.  Through
+    glmb_step (frame graph, estimates inside the graph) it must give the same
+    hypotheses and estimates as predict / update / prune, and every later
+    frame must run."""
+    sc, frames = _burst_frames(1011, 8, 400)
+    cfg = sc.filter_config()
+    a, b = glmb.Filter(cfg), glmb.Filter(cfg)
+    redo = 0
+    for k, (births, Z) in enumerate(frames):
+        a.step(births, Z)
+        b.predict(births)
+        b.update(Z)
+        b.prune()
+        ha, hb = a.hypotheses(), b.hypotheses()
+        np.testing.assert_array_equal(ha["uid"], hb["uid"])
+        np.testing.assert_array_equal(ha["logw"], hb["logw"])
+        ea, eb = a.estimates(), b.estimates()
+        np.testing.assert_array_equal(ea["labels"], eb["labels"])
+        np.testing.assert_array_equal(ea["pmf"], eb["pmf"])
+        redo = a.info()["n_redo"]
+    assert redo >= 1, "the burst did not exceed the plan"
