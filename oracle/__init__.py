@@ -77,6 +77,7 @@ def _load():
         lib.orc_estimates.argtypes = [P, C.c_int, P, P, P, P, P, P, P, C.c_int, P]
         lib.orc_meas_assoc.argtypes = [P, P]
         lib.orc_bruteforce.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        lib.orc_parent_pairs.argtypes = [P, C.c_int, P, P, P, P, P]
         lib.orc_set_gate.argtypes = [P, P, C.c_double]
         lib.orc_mlp_margin.argtypes = [P, C.c_int]
         lib.orc_mlp_margin.restype = C.c_double
@@ -267,6 +268,20 @@ class Oracle:
 
     def gate_margin(self, h):
         return self.lib.orc_gate_margin(self.h, h)
+
+    def parent_pairs(self, h):
+        """Parent h's gated-pair table: dict(ptr, meas, logC, q, e)."""
+        K = self.lib.orc_parent_pairs(self.h, h, None, None, None, None, None)
+        if K < 0:
+            raise OracleError("parent index")
+        T = self.parent_slots(h)
+        ptr = np.zeros(T + 1, np.int32)
+        meas = np.zeros(max(K, 1), np.int32)
+        lc = np.zeros(max(K, 1))
+        q = np.zeros(max(K, 1))
+        e = np.zeros((max(K, 1), self.dz))
+        self.lib.orc_parent_pairs(self.h, h, _ptr(ptr), _ptr(meas), _ptr(lc), _ptr(q), _ptr(e))
+        return dict(ptr=ptr, meas=meas[:K], logC=lc[:K], q=q[:K], e=e[:K])
 
     # -- learned gate ----------------------------------------------------------
     def set_gate(self, params, threshold: float = 0.0):

@@ -1034,6 +1034,22 @@ int orc_pair(const orc_filter* f, int h, int t, int i, double* d2, double* logC,
   return pair_gated(f, P, t, e, *d2, NULL);
 }
 
+int orc_parent_pairs(const orc_filter* f, int h, int32_t* ptr, int32_t* meas, double* logC, double* q,
+                     double* e) {
+  if (!f->par || h < 0 || h >= f->Hold) return -1;
+  const par_t* P = &f->par[h];
+  if (meas) {
+    for (int t = 0; t <= P->T; ++t) ptr[t] = P->ptr[t];
+    for (int k = 0; k < P->K; ++k) {
+      meas[k] = P->meas[k];
+      logC[k] = P->logC[k];
+      q[k] = P->q[k];
+      for (int a = 0; a < f->dz; ++a) e[k * f->dz + a] = P->e[k * f->dz + a];
+    }
+  }
+  return P->K;
+}
+
 double orc_mlp_margin(const orc_filter* f, int h) {
   if (!f->par || h < 0 || h >= f->Hold) return NAN;
   return f->par[h].mlp_margin;

@@ -60,6 +60,11 @@ int orc_slot(const orc_filter* f, int h, int t, uint32_t* lk, uint32_t* lb, doub
 int orc_pair(const orc_filter* f, int h, int t, int i, double* d2, double* logC, double* e,
              double* q);
 double orc_gate_margin(const orc_filter* f, int h);
+/* parent h's gated-pair table (CSR by slot, detections ascending within a
+ * slot): ptr[T+1], meas[K], logC[K], q[K], e[K][dim_z]; returns K (-1 on a
+ * bad index); with meas NULL only K is returned */
+int orc_parent_pairs(const orc_filter* f, int h, int32_t* ptr, int32_t* meas, double* logC, double* q,
+                     double* e);
 int orc_children(const orc_filter* f, int8_t* status, double* logw, double* margin,
                  int32_t* n_alive, uint64_t* uid);
 int orc_child(const orc_filter* f, int h, int n, uint8_t* dead, uint16_t* theta);

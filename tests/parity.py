@@ -99,13 +99,16 @@ def compare(o, g, d, cfg, Z, report: Report | None = None) -> Report:
     # ---- a1 prediction, a2 table, a3 death probability, per (parent, slot)
     n_slots = 0
     # parents with a pair close to either gate's decision: their tables may
-    # legitimately differ by that pair
-    near_gate_parents = {h for h in range(H) if o.mlp_margin(h) < MLP_MARGIN}
+    # legitimately differ by that pair (the oracle records both margins
+    # while it builds each parent's table)
+    near_gate_parents = {h for h in range(H)
+                         if o.mlp_margin(h) < MLP_MARGIN or o.gate_margin(h) < GATE_MARGIN}
     for h in range(H):
         T = o.parent_slots(h)
         if gptr[h + 1] - gptr[h] != T:
             r.fail(f"parent {h}: {gptr[h + 1] - gptr[h]} slots on GPU, {T} in oracle")
             continue
+        op = o.parent_pairs(h)
         for t in range(T):
             n_slots += 1
             s = o.slot(h, t)
@@ -118,21 +121,19 @@ def compare(o, g, d, cfg, Z, report: Report | None = None) -> Report:
             r.err("dprob_abs", abs(gc["dprob"][c] - s["dprob"]))
             lo, hi = gp["ptr"][c], gp["ptr"][c + 1]
             gm = gp["meas"][lo:hi]
-            om = []
-            for i in range(len(Z)):
-                pr = o.pair(h, t, i)
-                if math.isfinite(G) and abs(pr["d2"] - G) / G < GATE_MARGIN:
-                    near_gate_parents.add(h)
-                if pr["gated"]:
-                    om.append(i)
-                    k = np.searchsorted(gm, i)
-                    if k < len(gm) and gm[k] == i:
-                        j = lo + k
-                        r.err("logC_abs", abs(gp["logC"][j] - pr["logC"]))
-                        r.err("q_rel", abs(gp["q"][j] - pr["q"]) / max(1.0, abs(pr["q"])))
-                        r.err("e_rel", _rel(gp["e"][j], pr["e"]))
-            if h not in near_gate_parents and list(gm) != om:
-                r.fail(f"gate set ({h},{t}): gpu {list(gm)} oracle {om}")
+            a, b = op["ptr"][t], op["ptr"][t + 1]
+            om = op["meas"][a:b]
+            # values of the pairs both sides hold
+            both, gi, oi = np.intersect1d(gm, om, assume_unique=True, return_indices=True)
+            if len(both):
+                j = lo + gi
+                k = a + oi
+                r.err("logC_abs", np.max(np.abs(gp["logC"][j] - op["logC"][k])))
+                r.err("q_rel", np.max(np.abs(gp["q"][j] - op["q"][k]) / np.maximum(1.0, np.abs(op["q"][k]))))
+                r.err("e_rel", float(np.max(np.max(np.abs(gp["e"][j] - op["e"][k]), axis=1)
+                                            / np.maximum(1.0, np.max(np.abs(op["e"][k]), axis=1)))))
+            if h not in near_gate_parents and not np.array_equal(gm, om):
+                r.fail(f"gate set ({h},{t}): gpu {list(gm)} oracle {list(om)}")
     r.checks["slots"] = n_slots
     for key, tol in (("mean_rel", REL_TOL), ("cov_rel", REL_TOL), ("p_abs", 1e-6),
                      ("dprob_abs", 2e-6), ("logC_abs", 5e-5), ("q_rel", 2e-5), ("e_rel", 2e-5)):

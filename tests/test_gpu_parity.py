@@ -196,3 +196,16 @@ def test_convoy_frame(oracle_mod, glmb, mode, k):
     """Section 4.1's workload shape: five detections per object, no clutter."""
     sc = scenes.convoy_scene(5, 77, steps=16, h_max=50)
     _frame(oracle_mod, glmb, sc.filter_config(score_mode=mode), sc, k)
+
+
+@pytest.mark.parametrize("N,k", [(200, 4), (1000, 3)])
+def test_sweep_full_size_frame(oracle_mod, glmb, N, k):
+    """The 3-D sweep at full size, H_max = 20000: N = 200 (the cap binds as
+    hypotheses grow) and N = 1000 (the largest configuration, about 2600
+    detections and 1000 tracks per hypothesis)."""
+    sc = scenes.make_scene(scenes.preset(f"sweep_N{N}", h_max=20000, frames=k + 1), 3000 + N)
+    nb = max(len(f.births) for f in sc.frames)
+    cfg = sc.filter_config(max_meas=max(len(f.Z) for f in sc.frames) + 16, max_births=max(8, nb),
+                           max_tracks=2 * N + nb + 64)
+    rep = _frame(oracle_mod, glmb, cfg, sc, k)
+    assert rep.checks["slots"] > 10000
