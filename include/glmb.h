@@ -21,9 +21,10 @@
  *    glmb_create, from the capacities in glmb_config; no call allocates
  *    device memory afterwards.
  *  - Work is issued on glmb_config.stream (a cudaStream_t; NULL means a
- *    stream owned by the handle).  glmb_predict and glmb_update only enqueue
- *    work (their host inputs are copied before they return); glmb_prune and
- *    every call that returns sizes or host data synchronise that stream.
+ *    stream owned by the handle).  glmb_predict only enqueues work (its host
+ *    inputs are copied before it returns); glmb_update waits once, for its
+ *    expansion, to check the expansion's plan (see glmb_update); glmb_prune
+ *    and every call that returns sizes or host data synchronise that stream.
  *  - Call order per frame: glmb_predict -> glmb_update -> glmb_prune ->
  *    any number of glmb_estimates / glmb_meas_assoc / glmb_get_* calls.
  *    A call out of order returns GLMB_E_STATE and changes nothing.
@@ -155,8 +156,10 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
  * the handle's stream must be ordered after its writes).  Builds the gated
  * compatibility table, the posterior death probabilities, and the h_up
  * children of each hypothesis with their exact log-weights; unique children
- * stay on the device for glmb_prune.  The call only enqueues work: it does
- * not wait for the GPU.
+ * stay on the device for glmb_prune.  The call waits once for the GPU, after
+ * the expansion: a hypothesis with more gated pairs than the expansion was
+ * planned for (from earlier frames) makes it redo the expansion with the
+ * frame's exact maxima before it returns, so the children are final.
  * Errors: GLMB_E_STATE (no predict), GLMB_E_INVALID (M < 0, NaN/Inf in a
  * host Z), GLMB_E_CAPACITY (M beyond max_meas, or a per-hypothesis table
  * that cannot fit in shared memory).  Errors found on the device (NaN/Inf in

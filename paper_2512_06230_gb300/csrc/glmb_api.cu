@@ -653,13 +653,12 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
   const long long cap = p.fixed ? h->cap_comp : std::max(T, 1);
   CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
   prof_begin(h, kStageTable);
-  launch_check_finite(h->d_fs, dz, h->d_scal + S_ERR, h->stream);
   const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
   // with the gate pruning, the Mahalanobis-gated table goes to pt_full and
   // the gate compacts the pairs it keeps into pt
   const bool prune = h->gate_mode == GLMB_GATE_PRUNE;
   const PairTable& P0 = prune ? h->pt_full : h->pt;
-  launch_table_count(h->md, B, P0, h->d_fs, gt, h->stream);
+  launch_table_count(h->md, B, P0, h->d_fs, h->d_scal + S_ERR, gt, h->stream);   // also checks Z is finite
   scan_u32(P0.cnt, P0.ptr, &h->d_fs->T, 1, cap, h->d_scal + (prune ? S_KFULL : S_K), true, h->scan_tmp32,
            h->scan_cap32, h->d_scal + S_ERR, h->stream);
   launch_table_write(h->md, B, P0, h->d_fs, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
@@ -675,9 +674,8 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
     }
   }
   h->gate_mode_frame = h->gate_mode;
-  const int gs = p.fixed ? 4 * h->n_sm : std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm));
-  launch_parent_stats(h->hyps[h->hcur], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
-                      gs, h->stream);
+  // the largest slot and pair counts per parent are recorded by the
+  // staging kernel (ExpandArgs::max_T / max_K)
   prof_end(h, kStageTable);
   return GLMB_OK;
 }
@@ -700,6 +698,9 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
   a.redo_count = h->d_scal + S_REDO;
   a.materialize = mat ? 1 : 0;
   a.err = h->d_scal + S_ERR;
+  a.gc_flag = h->gc_flag;
+  a.max_T = h->d_scal + S_MAXT;
+  a.max_K = h->d_scal + S_MAXK;
   return a;
 }
 
@@ -795,6 +796,8 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   prof_end(h, kStageSelect);
   CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), s));
   CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));
+  const long long capT = p.fixed ? h->cap_comp : std::max(h->T_work, 1);
+  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));   // set by the materialisation
   ExpandArgs a = expand_args(h, p, true);
   a.surv_idx = h->pw.surv_idx;
   a.n_surv = h->pw.counts;
@@ -820,10 +823,7 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   launch_expand_kernel(a, ExpandKernel::kWarp, m_grid, m_thr, m_smem, s);
   prof_end(h, kStageMat);
   const int T = h->T_work;
-  const long long capT = p.fixed ? h->cap_comp : std::max(T, 1);
   prof_begin(h, kStageGc);
-  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));
-  launch_mark_old(O.comp, h->pw.counts + 1, h->cap_entries, h->d_scal + S_ERR, h->gc_flag, s);
   scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
            h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR, s);
   const int ggc = p.fixed ? 8 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
@@ -996,6 +996,8 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
     Plan q{};
     q.fixed = false;
     enqueue_table(h, q);
+    launch_parent_stats(h->hyps[h->hcur], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
+                        std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm)), h->stream);
     CU(cudaStreamSynchronize(h->stream));
     unsigned mk = 0;
     CU(cudaMemcpy(&mk, h->d_scal + S_MAXK, sizeof mk, cudaMemcpyDeviceToHost));
@@ -1010,6 +1012,23 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
   h->plan = p;
   enqueue_expand(h, p);
   CU(cudaGetLastError());
+  // a parent with more gated pairs than the plan's estimate: redo the
+  // expansion now with the frame's exact maxima, so that the children are
+  // final when update returns (glmb_step redoes in its completion instead)
+  CU(cudaStreamSynchronize(h->stream));
+  unsigned sc[4] = {0, 0, 0, 0};
+  CU(cudaMemcpy(sc, h->d_scal, sizeof sc, cudaMemcpyDeviceToHost));
+  if ((sc[S_ERR] & kErrSlots) && !(sc[S_ERR] & (kErrFatal & ~kErrSlots))) {
+    Plan q;
+    if (make_plan(h, false, std::max(1u, sc[S_MAXT]), std::max(1u, sc[S_MAXK]), h->M, q) &&
+        ensure_img(h, q) == GLMB_OK) {
+      ++h->redo_count;
+      CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
+      enqueue_expand(h, q);
+      CU(cudaGetLastError());
+      h->plan = q;
+    }
+  }
   h->H_par = h->H;
   h->par_buf = h->hcur;
   h->birth_base = h->n_comp;

@@ -37,12 +37,12 @@ inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
 // appended at dst[n_comp..) (births_dev: per birth [r, mean[6], cov[36]] FP64)
 void launch_predict(const Model& md, const CompTable& src, const CompTable& dst, const FrameDev* fs,
                     const double* births_dev, int grid, cudaStream_t s);
-// detections: fs->Z ([M][dz] floats on the device)
+// detections: fs->Z ([M][dz] floats on the device); the count kernel also
+// sets kErrInput in *err when a detection coordinate is not finite
 void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, int grid, cudaStream_t s);
+                        const FrameDev* fs, unsigned* err, int grid, cudaStream_t s);
 void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
                         const FrameDev* fs, unsigned* n_fp64, unsigned* err, int grid, cudaStream_t s);
-void launch_check_finite(const FrameDev* fs, int dz, unsigned* err, cudaStream_t s);
 void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable& pt,
                          unsigned* max_T, unsigned* max_K, int grid, cudaStream_t s);
 
@@ -97,7 +97,12 @@ struct ExpandArgs {
   long long* upd_se;           // [dz][cap_upd] fixed-point sum of innovations
   uint32_t* upd_count;
   int cap_upd;
+  uint32_t* gc_flag;           // [T] set for old components the new hypotheses keep
   unsigned* err;
+  // largest slot and gated-pair counts over the staged parents (staging
+  // records them for the next frame's plan and for a redo)
+  unsigned* max_T;
+  unsigned* max_K;
 };
 // bytes of one parent's image (the staging kernel's shared memory when it
 // stages there)
@@ -154,8 +159,6 @@ int select_cluster_size();
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
                      const HypTable& parents, int h_up, HypTable out, int h_max,
                      unsigned* err, long long cap_entries, cudaStream_t s);
-void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
-                     const unsigned* err, uint32_t* flag, cudaStream_t s);
 void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
                            const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
                            const unsigned* n_keep_dev, const uint32_t* upd_src,

@@ -374,12 +374,28 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
     sc.K = 0;
     sc.uid = a.parents.uid[h];
     sc.logw = a.parents.logw[h];
-    if (sc.T > a.T_max || M > a.M_plan) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+  }
+  __syncthreads();
+  const int T = sc.T, Town = sc.Town;
+  const uint32_t plo = a.parents.ptr[h];
+  // the parent's gated pairs, counted for every parent (also one beyond the
+  // plan): the frame's maxima plan the next frame, or this frame's redo
+  {
+    unsigned kp = 0;
+    for (int t = tid; t < T; t += nthr)
+      kp += pt.cnt[t < Town ? a.parents.comp[plo + t] : (uint32_t)(birth_base + (t - Town))];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xFFFFFFFFu, kp, o);
+    if ((tid & 31) == 0 && kp) atomicAdd(&sc.K, (int)kp);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (a.max_T) atomicMax(a.max_T, (unsigned)T);
+    if (a.max_K) atomicMax(a.max_K, (unsigned)sc.K);
+    if (T > a.T_max || M > a.M_plan || sc.K > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
   }
   __syncthreads();
   if (sc.bad) return;
-  const int T = sc.T, Town = sc.Town;
-  const uint32_t plo = a.parents.ptr[h];
 
   // ---- slots ----
   for (int t = tid; t < T; t += nthr) {
@@ -1123,7 +1139,9 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
     for (int t = lane; t < T; t += 32) {
       if (bit_of(dmask, t)) continue;
       const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
-      a.out_comp[base + (uint32_t)t - below] = bit_of(tmask, t) ? newval[t] : v.refnew[t];
+      const uint32_t val = bit_of(tmask, t) ? newval[t] : v.refnew[t];
+      a.out_comp[base + (uint32_t)t - below] = val;
+      if (!(val & kNewTag)) a.gc_flag[val] = 1u;   // an old component stays
     }
     __syncwarp();
   }

@@ -400,24 +400,6 @@ void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_a
 // Garbage collection of components and the batched track update (Kalman
 // with the mean detection and R/m, Joseph form).
 // ---------------------------------------------------------------------------
-__global__ void mark_old_kernel(const uint32_t* __restrict__ out_comp,
-                                const unsigned* __restrict__ n_entries, long long cap,
-                                const unsigned* err, uint32_t* flag) {
-  pdl_enter();
-  if (*(volatile const unsigned*)err & kErrFatal) return;
-  const long long n = min((long long)*n_entries, cap);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const uint32_t v = out_comp[e];
-    if (!(v & kNewTag)) flag[v] = 1u;
-  }
-}
-
-void launch_mark_old(const uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
-                     const unsigned* err, uint32_t* flag, cudaStream_t s) {
-  const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
-  launch_k(mark_old_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, err, flag);
-}
 
 template <int DZ>
 __device__ void copy_comp(const Model& md, const CompTable& src, int c, const CompTable& dst, int d) {

@@ -184,10 +184,19 @@ __device__ __forceinline__ bool pair_eval(const Model& md, const CompGeom<DZ>& g
 }
 
 template <int DZ>
-__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const FrameDev* __restrict__ fs) {
+__global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const FrameDev* __restrict__ fs,
+                                   unsigned* err) {
   pdl_enter();
   const int T = fs->T, M = fs->M;
   const float* __restrict__ Z = fs->Z;
+  {
+    // every detection coordinate finite, else the frame is rejected
+    bool bad = false;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)M * DZ;
+         k += (long long)gridDim.x * blockDim.x)
+      bad |= !isfinite(Z[k]);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrInput);
+  }
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps) {
@@ -285,9 +294,9 @@ __device__ void table_write_comp(const Model& md, const CompTable& ct, const Pai
 }
 
 void launch_table_count(const Model& md, const CompTable& ct, const PairTable& pt,
-                        const FrameDev* fs, int grid, cudaStream_t s) {
-  if (md.dz == 2) { launch_k(table_count_kernel<2>, grid, 256, 0, s, md, ct, pt, fs); }
-  else { launch_k(table_count_kernel<3>, grid, 256, 0, s, md, ct, pt, fs); }
+                        const FrameDev* fs, unsigned* err, int grid, cudaStream_t s) {
+  if (md.dz == 2) { launch_k(table_count_kernel<2>, grid, 256, 0, s, md, ct, pt, fs, err); }
+  else { launch_k(table_count_kernel<3>, grid, 256, 0, s, md, ct, pt, fs, err); }
 }
 
 void launch_table_write(const Model& md, const CompTable& ct, const PairTable& pt,
@@ -296,20 +305,6 @@ void launch_table_write(const Model& md, const CompTable& ct, const PairTable& p
   else { launch_k(table_write_kernel<3>, grid, 256, 0, s, md, ct, pt, fs, n_fp64, err); }
 }
 
-__global__ void check_finite_kernel(const FrameDev* __restrict__ fs, int dz, unsigned* err) {
-  pdl_enter();
-  const float* __restrict__ Z = fs->Z;
-  const long long n = (long long)fs->M * dz;
-  bool bad = false;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    bad |= !isfinite(Z[k]);
-  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrInput);
-}
-
-void launch_check_finite(const FrameDev* fs, int dz, unsigned* err, cudaStream_t s) {
-  launch_k(check_finite_kernel, 16, 256, 0, s, fs, dz, err);
-}
 
 // per-parent slot and table sizes (max over parents), births included
 __global__ void parent_stats_kernel(HypTable hp, const FrameDev* __restrict__ fs, PairTable pt,
