@@ -17,9 +17,12 @@
  *  - All pointers are host pointers unless the argument name says "device".
  *    The caller owns every buffer it passes; the library copies inputs
  *    before the call returns and writes outputs only on GLMB_OK.
- *  - The handle owns all device memory.  It is allocated once, in
- *    glmb_create, from the capacities in glmb_config; no call allocates
- *    device memory afterwards.
+ *  - The handle owns all device memory, from cudaMalloc or the allocation
+ *    hook of glmb_config.  glmb_create allocates it from the capacities in
+ *    glmb_config, with two exceptions: the per-hypothesis expansion images,
+ *    grown by glmb_update / glmb_step when a frame needs more, and the
+ *    learned gate's buffers, allocated by glmb_set_gate and the gate's data
+ *    calls on first use.  Growth waits for the handle's stream first.
  *  - Work is issued on glmb_config.stream (a cudaStream_t; NULL means a
  *    stream owned by the handle).  glmb_predict only enqueues work (its host
  *    inputs are copied before it returns); glmb_update waits once, for its
@@ -88,6 +91,15 @@ typedef struct {
   int64_t max_components;   /* capacity: distinct Gaussian components (tracks are
                                shared between hypotheses); 0 selects
                                h_max * max_tracks + max_births */
+  /* Device allocation hook (both NULL: cudaMalloc / cudaFree).  With it set,
+   * every device buffer of the handle comes from dev_alloc(bytes, alloc_ctx),
+   * which returns NULL on failure, and is returned through
+   * dev_free(ptr, alloc_ctx) when the buffer is replaced or the handle is
+   * destroyed (after the handle's stream has finished with it): for example
+   * a framework's caching allocator.  Set both or neither. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } glmb_config;
 
 /* An LMB birth component (Section 3): existence r, Gaussian density. */

@@ -74,6 +74,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 # --------------------------------------------------------------------------
 # C structs (layouts of include/glmb.h)
 # --------------------------------------------------------------------------
+# device allocation hook of glmb_config
+DEV_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class GlmbConfig(C.Structure):
     _fields_ = [("dim_x", C.c_int32), ("dim_z", C.c_int32), ("dt", C.c_float), ("q", C.c_double),
                 ("R", C.c_double * 9), ("p_s", C.c_double), ("p_d", C.c_double),
@@ -81,7 +86,8 @@ class GlmbConfig(C.Structure):
                 ("gate", C.c_double), ("h_max", C.c_int32), ("h_up", C.c_int32), ("tau", C.c_double),
                 ("seed", C.c_uint64), ("score_mode", C.c_int32), ("max_tracks", C.c_int32),
                 ("max_meas", C.c_int32), ("max_births", C.c_int32), ("max_pairs", C.c_int64),
-                ("stream", C.c_void_p), ("max_components", C.c_int64)]
+                ("stream", C.c_void_p), ("max_components", C.c_int64),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class GlmbBirth(C.Structure):
@@ -175,6 +181,26 @@ def load() -> C.CDLL:
     return lib
 
 
+def torch_allocator_hooks(device=None):
+    """(dev_alloc, dev_free) callbacks over torch.cuda's caching allocator.
+    The blocks are taken on torch's current stream of `device`; the library
+    returns a block only after its own stream has finished with it."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev)
+        except RuntimeError:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return DEV_ALLOC_FN(_alloc), DEV_FREE_FN(_free)
+
+
 class GlmbError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -261,10 +287,17 @@ def unpack_state(buf: bytes):
 class Filter:
     """One GLMB filter on the current CUDA device (see include/glmb.h)."""
 
-    def __init__(self, cfg: dict, stream: Optional[int] = None):
+    def __init__(self, cfg: dict, stream: Optional[int] = None, allocator: Optional[str] = None):
+        """allocator="torch": the handle's device memory comes from PyTorch's
+        caching allocator (glmb_config.dev_alloc / dev_free)."""
         self.lib = load()
         self.cfg = dict(cfg)
         self._c = make_config(cfg, stream)
+        if allocator == "torch":
+            self._hooks = torch_allocator_hooks()
+            self._c.dev_alloc, self._c.dev_free = self._hooks
+        elif allocator is not None:
+            raise ValueError(f"unknown allocator {allocator!r}")
         self.dx, self.dz = self._c.dim_x, self._c.dim_z
         h = C.c_void_p()
         st = self.lib.glmb_create(C.byref(self._c), C.byref(h))

@@ -185,11 +185,28 @@ glmb_status fail(glmb_handle* h, glmb_status st, const char* fmt, ...) {
       return fail(h, GLMB_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));         \
   } while (0)
 
+// device memory through the configured hook, else cudaMalloc / cudaFree
+void* dev_alloc_raw(glmb_handle* h, size_t bytes) {
+  if (h->cfg.dev_alloc) return h->cfg.dev_alloc(bytes, h->cfg.alloc_ctx);
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return q;
+}
+
+void dev_free_raw(glmb_handle* h, void* p) {
+  if (!p) return;
+  if (h->cfg.dev_alloc) h->cfg.dev_free(p, h->cfg.alloc_ctx);
+  else cudaFree(p);
+}
+
 template <typename T>
 bool dalloc(glmb_handle* h, T** p, long long n) {
-  void* q = nullptr;
   if (n <= 0) n = 1;
-  if (cudaMalloc(&q, (size_t)n * sizeof(T)) != cudaSuccess) return false;
+  void* q = dev_alloc_raw(h, (size_t)n * sizeof(T));
+  if (!q) return false;
   h->allocs.push_back(q);
   *p = (T*)q;
   return true;
@@ -220,7 +237,7 @@ bool alloc_hyps(glmb_handle* h, HypTable& y) {
 }
 
 void free_all(glmb_handle* h) {
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) dev_free_raw(h, p);
   for (void* p : h->host_allocs) cudaFreeHost(p);
   h->allocs.clear();
   h->host_allocs.clear();
@@ -285,6 +302,7 @@ const char* err_text(unsigned e) {
   if (e & kErrHash) return "update table full";
   if (e & kErrNumeric) return "covariance not positive definite";
   if (e & kErrGate) return "learned gate: a tensor-core wait ran out of time";
+  if (e & kErrTimeout) return "a scan's look-back waited past its limit";
   return "device error";
 }
 
@@ -406,6 +424,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
       !(c.lambda_d >= 0) || !(c.clutter_rate >= 0) || !(c.volume > 0) || !(c.gate > 0) ||
       c.h_max < 1 || c.h_up < 1 || c.h_up > 65535 || !(c.tau > 0) || c.score_mode < 0 || c.score_mode > 1)
     return GLMB_E_INVALID;
+  if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr)) return GLMB_E_INVALID;
   glmb_handle* h = new glmb_handle();
   h->cfg = c;
   const int dx = c.dim_x, dz = c.dim_z;
@@ -550,7 +569,7 @@ glmb_status glmb_destroy(glmb_handle* h) {
   if (!h) return GLMB_OK;
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
-  if (h->img) cudaFree(h->img);
+  dev_free_raw(h, h->img);
   for (int st = 0; st < kNumStages; ++st)
     if (h->ev[st][0]) {
       cudaEventDestroy(h->ev[st][0]);
@@ -712,15 +731,12 @@ glmb_status ensure_img(glmb_handle* h, const Plan& p) {
   CU(cudaStreamSynchronize(h->stream));
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
-  if (h->img) cudaFree(h->img);
+  dev_free_raw(h, h->img);
   h->img = nullptr;
   h->img_alloc = 0;
   const size_t want = need + need / 4;
-  void* q = nullptr;
-  if (cudaMalloc(&q, want) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(h, GLMB_E_CAPACITY, "expansion images: %zu bytes not available", want);
-  }
+  void* q = dev_alloc_raw(h, want);
+  if (!q) return fail(h, GLMB_E_CAPACITY, "expansion images: %zu bytes not available", want);
   h->img = (unsigned char*)q;
   h->img_alloc = want;
   return GLMB_OK;
@@ -924,7 +940,7 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
     est_enqueued = false;   // the estimates copied with the first pass are stale
   }
   if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
-  if (e & kErrGate) return abandon(GLMB_E_CUDA, err_text(e));
+  if (e & (kErrGate | kErrTimeout)) return abandon(GLMB_E_TIMEOUT, err_text(e));
   if (e & kErrFatal) return abandon(e & kErrNumeric ? GLMB_E_NUMERIC : GLMB_E_CAPACITY, err_text(e));
   h->n_pairs = h->h_scal[S_K];
   h->n_pairs_pregate = h->gate_mode_frame == GLMB_GATE_PRUNE ? (long long)h->h_scal[S_KFULL] : h->n_pairs;

@@ -31,6 +31,7 @@ enum : uint32_t {
   kErrSlots = 64u,      // per-hypothesis staging beyond the planned size
   kErrInput = 128u,     // a detection is NaN or infinite
   kErrGate = 256u,      // a tensor-core wait of the learned gate ran out of time
+  kErrTimeout = 512u,   // a scan's look-back waited past its limit
 };
 
 constexpr float kFxScale = 4294967296.0f;          // 2^32

@@ -51,7 +51,7 @@ void launch_parent_stats(const HypTable& hp, const FrameDev* fs, const PairTable
 // may serve scans of different capacities), zero before the first scan (each
 // scan leaves it zero); total (nullable) receives the sum, and with
 // total_at_end the sum is also written to out[n]; a look-back that waits too
-// long sets kErrNumeric in *err
+// long sets kErrTimeout in *err
 long long scan_tmp_elems(long long cap);
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
               uint32_t* total, bool total_at_end, uint32_t* tmp, long long tmp_cap, unsigned* err,
@@ -170,7 +170,7 @@ void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long c
                   const unsigned* err, cudaStream_t s);
 // device error flags that abandon a frame (state left untouched)
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
-                               kErrEntries | kErrSlots | kErrInput | kErrGate;
+                               kErrEntries | kErrSlots | kErrInput | kErrGate | kErrTimeout;
 
 // ---- learned pair gate (gate_mlp.cu) ----
 // parameter vector (floats): W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64]

@@ -446,7 +446,7 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
           done = inc_mask != 0u;
           top -= 32;
         }
-        if (gave_up && lane == 0) atomicOr(err, kErrNumeric);
+        if (gave_up && lane == 0) atomicOr(err, kErrTimeout);
       }
       if (lane == 0) {
         ((volatile T*)inc)[tile] = excl + tile_sum;

@@ -114,3 +114,27 @@ def test_redone_frame_in_the_graph_path_matches_separate_calls(glmb):
         np.testing.assert_array_equal(ea["pmf"], eb["pmf"])
         redo = a.info()["n_redo"]
     assert redo >= 1, "the burst did not exceed the plan"
+
+
+def test_torch_allocator_hook_gives_the_same_results(glmb):
+    """glmb_config's allocation hook: every device buffer from PyTorch's
+    caching allocator (the images grown mid-run included), identical results,
+    and the memory back in torch's cache after destroy."""
+    import torch
+    sc = scenes.make_scene(scenes.preset("tiny"), 1012)
+    cfg = sc.filter_config()
+    base = torch.cuda.memory_allocated()
+    a = glmb.Filter(cfg)
+    b = glmb.Filter(cfg, allocator="torch")
+    held = torch.cuda.memory_allocated() - base
+    assert held > 0
+    for fr in sc.frames[:15]:
+        a.step(fr.births, fr.Z)
+        b.step(fr.births, fr.Z)
+        ha, hb = a.hypotheses(), b.hypotheses()
+        np.testing.assert_array_equal(ha["uid"], hb["uid"])
+        np.testing.assert_array_equal(ha["logw"], hb["logw"])
+    assert torch.cuda.memory_allocated() - base >= held
+    a.close()
+    b.close()
+    assert torch.cuda.memory_allocated() == base
