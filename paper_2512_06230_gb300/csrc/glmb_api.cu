@@ -207,6 +207,12 @@ bool dalloc(glmb_handle* h, T** p, long long n) {
   if (n <= 0) n = 1;
   void* q = dev_alloc_raw(h, (size_t)n * sizeof(T));
   if (!q) return false;
+  // zero-filled: no kernel ever reads uninitialised memory, even a stale
+  // region of a frame that is being redone
+  if (cudaMemset(q, 0, (size_t)n * sizeof(T)) != cudaSuccess) {
+    dev_free_raw(h, q);
+    return false;
+  }
   h->allocs.push_back(q);
   *p = (T*)q;
   return true;
@@ -781,7 +787,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   launch_expand_kernel(a, ExpandKernel::kStage, st_grid, st_thr, st_smem, s);
   if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
   launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
-  launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status,
+  launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status, h->d_scal + S_ERR,
                p.fixed ? 8 * n_sm : std::max(1, std::min(h->H, 8 * n_sm)), s);
   prof_end(h, kStageExpand);
   return GLMB_OK;

@@ -123,7 +123,7 @@ void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int thr
                           cudaStream_t s);
 // marks duplicate children (status 2, key dropped), one block per parent
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
-                  int8_t* child_status, int grid, cudaStream_t s);
+                  int8_t* child_status, const unsigned* err, int grid, cudaStream_t s);
 
 // ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
 struct PruneWork {

@@ -1256,8 +1256,10 @@ __device__ __forceinline__ int dedup_table_size(int HU) {
 }
 
 __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long* child_key,
-                             const unsigned long long* __restrict__ child_hash, int8_t* child_status) {
+                             const unsigned long long* __restrict__ child_hash, int8_t* child_status,
+                             const unsigned* err) {
   pdl_enter();
+  if (*(volatile const unsigned*)err & kErrFatal) return;   // the draws were skipped
   extern __shared__ unsigned long long s_k[];   // [ts] keys, 0 = empty
   const int ts = dedup_table_size(HU);
   uint32_t* s_n = reinterpret_cast<uint32_t*>(s_k + ts);   // [ts] lowest draw
@@ -1308,12 +1310,12 @@ __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long*
 }
 
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
-                  int8_t* child_status, int grid, cudaStream_t s) {
+                  int8_t* child_status, const unsigned* err, int grid, cudaStream_t s) {
   int ts = 64;
   while (ts < 2 * HU) ts <<= 1;
   const int smem = ts * 12;
   if (smem > 48 * 1024) cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  launch_k(dedup_kernel, grid, 128, smem, s, fs, HU, child_key, child_hash, child_status);
+  launch_k(dedup_kernel, grid, 128, smem, s, fs, HU, child_key, child_hash, child_status, err);
 }
 
 // ---- host side ----

@@ -76,6 +76,7 @@ __device__ Lse block_lse(Lse v) {
 __global__ void lse_kernel(const long long* __restrict__ keys, const FrameDev* __restrict__ fs,
                            int h_up, PruneWork w, double log_tau, int h_max) {
   pdl_enter();
+  if (*(volatile const unsigned*)w.err & kErrFatal) return;   // children stale: frame redone or abandoned
   __shared__ bool last;
   const long long n = (long long)fs->H * h_up;
   // per thread: running maximum and a compensated FP32 sum of exp(key - max)
@@ -166,6 +167,7 @@ constexpr int kDigit = 12, kBins = 1 << kDigit;
 __global__ void radix_hist_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w, int shift) {
   pdl_enter();
+  if (*(volatile const unsigned*)w.err & kErrFatal) return;   // children stale: frame redone or abandoned
   __shared__ unsigned hist[kBins];
   const long long n = (long long)fs->H * h_up;
   if (w.sel[3] != 0) return;
@@ -188,6 +190,7 @@ __global__ void radix_hist_kernel(const long long* __restrict__ keys,
 
 __global__ void radix_find_kernel(PruneWork w, int shift, int first) {
   pdl_enter();
+  if (*(volatile const unsigned*)w.err & kErrFatal) return;   // children stale: frame redone or abandoned
   // thread t owns bins [4t, 4t + 4) (blockDim.x == kBins / 4 == 1024);
   // the count of bins above a thread's range is total - inclusive prefix
   __shared__ unsigned wsum[32];
@@ -272,6 +275,7 @@ __device__ __forceinline__ unsigned long long keep_bits(long long k, long long t
 __global__ void keep_flags_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w) {
   pdl_enter();
+  if (*(volatile const unsigned*)w.err & kErrFatal) return;   // children stale: frame redone or abandoned
   const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -282,6 +286,7 @@ __global__ void keep_flags_kernel(const long long* __restrict__ keys,
 __global__ void keep_write_kernel(const long long* __restrict__ keys,
                                   const FrameDev* __restrict__ fs, int h_up, PruneWork w, int h_max) {
   pdl_enter();
+  if (*(volatile const unsigned*)w.err & kErrFatal) return;   // children stale: frame redone or abandoned
   const long long n = (long long)fs->H * h_up;
   const long long thr = w.thr[0], bnd = w.sel[2], need = w.sel[1], mode = w.sel[3];
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -313,6 +318,7 @@ __global__ void finalize_kernel(PruneWork w, const long long* __restrict__ keys,
                                 int h_up, HypTable out, int h_max, unsigned* err,
                                 long long cap_entries) {
   pdl_enter();
+  if (*(volatile const unsigned*)err & kErrFatal) return;
   __shared__ long long s_n;
   __shared__ double s_lse;
   __shared__ uint32_t carry;

@@ -76,6 +76,10 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
                       double log_tau, int h_max, int nbits, const uint16_t* __restrict__ child_alive,
                       HypTable parents, HypTable out, unsigned* err, long long cap_entries) {
   pdl_enter();
+  // a frame whose expansion was skipped (the staging flagged it, or the
+  // table failed) holds stale children: nothing to select; every CTA of the
+  // cluster reads the same flag and returns before any cluster barrier
+  if (*(volatile const unsigned*)err & kErrFatal) return;
   extern __shared__ __align__(16) unsigned char sel_sm[];
   SelShared& S = *reinterpret_cast<SelShared*>(sel_sm);
   cg::cluster_group cl = cg::this_cluster();
