@@ -207,9 +207,9 @@ bool dalloc(glmb_handle* h, T** p, long long n) {
   if (n <= 0) n = 1;
   void* q = dev_alloc_raw(h, (size_t)n * sizeof(T));
   if (!q) return false;
-  // zero-filled: no kernel ever reads uninitialised memory, even a stale
-  // region of a frame that is being redone
-  if (cudaMemset(q, 0, (size_t)n * sizeof(T)) != cudaSuccess) {
+  // zero-filled, in the handle's stream order: no kernel ever reads
+  // uninitialised memory, even a stale region of a frame being redone
+  if (cudaMemsetAsync(q, 0, (size_t)n * sizeof(T), h->stream) != cudaSuccess) {
     dev_free_raw(h, q);
     return false;
   }
@@ -256,8 +256,7 @@ bool alloc_est(glmb_handle* h) {
   h->est_off_r = h->est_off_tr + sizeof(glmb_track) * pcap;
   h->est_off_done = h->est_off_r + 8 * pcap;
   const size_t bytes = h->est_off_done + 16;
-  return dalloc(h, &h->d_est, (long long)bytes) && halloc(h, &h->h_est, (long long)h->est_off_r) &&
-         cudaMemset(h->d_est, 0, bytes) == cudaSuccess;
+  return dalloc(h, &h->d_est, (long long)bytes) && halloc(h, &h->h_est, (long long)h->est_off_r);
 }
 
 long long next_pow2(long long x) {
@@ -309,6 +308,9 @@ const char* err_text(unsigned e) {
   if (e & kErrNumeric) return "covariance not positive definite";
   if (e & kErrGate) return "learned gate: a tensor-core wait ran out of time";
   if (e & kErrTimeout) return "a scan's look-back waited past its limit";
+  if (e & kErrChkSurv) return "internal check: a survivor index outside the frame's children";
+  if (e & kErrChkComp) return "internal check: a component index outside the working table";
+  if (e & kErrChkRemap) return "internal check: a new-hypothesis entry outside its tables";
   return "device error";
 }
 
@@ -547,10 +549,9 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
     h->pw.err = h->d_scal + S_ERR;
     h->pw.flags_tmp_cap = h->cap_children;
     h->scan_cap32 = scan_n;
-    // scan work areas start zeroed (each scan leaves its own zeroed)
-    ok = cudaMemset(h->scan_tmp32, 0, sizeof(uint32_t) * scan_tmp_elems(scan_n)) == cudaSuccess &&
-         cudaMemset(h->pw.flags_tmp, 0, sizeof(unsigned long long) * scan_tmp_elems(h->cap_children)) ==
-             cudaSuccess;
+    // scan work areas start zeroed (dalloc zero-fills them; each scan
+    // leaves its own zeroed); every fill is ordered before the handle's work
+    ok = cudaStreamSynchronize(h->stream) == cudaSuccess;
   }
   if (!ok) {
     free_all(h);
@@ -665,7 +666,7 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 glmb_status enqueue_predict(glmb_handle* h, const Plan& p) {
   const CompTable& A = h->comps[h->cur];
   const CompTable& B = h->comps[1 - h->cur];
-  const int gp = p.fixed ? 8 * h->n_sm : std::max(1, std::min((h->T_work + 127) / 128, 8 * h->n_sm));
+  const int gp = p.fixed ? 2 * h->n_sm : std::max(1, std::min((h->T_work + 127) / 128, 8 * h->n_sm));
   prof_begin(h, kStagePredict);
   launch_predict(h->md, A, B, h->d_fs, h->d_births, gp, h->stream);
   prof_end(h, kStagePredict);
@@ -678,7 +679,7 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
   const long long cap = p.fixed ? h->cap_comp : std::max(T, 1);
   CU(cudaMemsetAsync(h->d_scal, 0, S_N * sizeof(unsigned), h->stream));
   prof_begin(h, kStageTable);
-  const int gt = p.fixed ? 16 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
+  const int gt = p.fixed ? 4 * h->n_sm : std::max(1, std::min((T * 32 + 255) / 256, 16 * h->n_sm));
   // with the gate pruning, the Mahalanobis-gated table goes to pt_full and
   // the gate compacts the pairs it keeps into pt
   const bool prune = h->gate_mode == GLMB_GATE_PRUNE;
@@ -848,12 +849,12 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   prof_begin(h, kStageGc);
   scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
            h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR, s);
-  const int ggc = p.fixed ? 8 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
+  const int ggc = p.fixed ? 4 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
   launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP,
                         h->upd_src, h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD,
                         h->pw.counts, h->d_scal + S_ERR, ggc, s);
   launch_remap(O.comp, h->pw.counts + 1, h->cap_entries, h->gc_newpos, h->hvals,
-               h->d_scal + S_NKEEP, h->d_scal + S_ERR, s);
+               h->d_scal + S_NKEEP, h->d_scal + S_ERR, h->hmask, h->d_fs, s);
   prof_end(h, kStageGc);
   CU(cudaGetLastError());
   return GLMB_OK;
@@ -1478,22 +1479,24 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
     std::vector<float> col(nc);
     for (int a = 0; a < dx; ++a) {
       for (int c = 0; c < nc; ++c) col[c] = mh[(size_t)c * dx + a];
-      CU(cudaMemcpy(A.mhi + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpyAsync(A.mhi + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
       for (int c = 0; c < nc; ++c) col[c] = ml[(size_t)c * dx + a];
-      CU(cudaMemcpy(A.mlo + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpyAsync(A.mlo + (size_t)a * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
     }
     for (int k = 0; k < ncov; ++k) {
       for (int c = 0; c < nc; ++c) col[c] = cv[(size_t)c * ncov + k];
-      CU(cudaMemcpy(A.cov + (size_t)k * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpyAsync(A.cov + (size_t)k * A.cap, col.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
     }
-    CU(cudaMemcpy(A.lk, lk.data(), nc * 4, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(A.lb, lb.data(), nc * 4, cudaMemcpyHostToDevice));
+    CU(cudaMemcpyAsync(A.lk, lk.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(A.lb, lb.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
   }
   const HypTable& Y = h->hyps[h->hcur];
-  CU(cudaMemcpy(Y.ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
-  if (hd.n_tracks > 0) CU(cudaMemcpy(Y.comp, comp.data(), (size_t)hd.n_tracks * 4, cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(Y.logw, logw.data(), logw.size() * 8, cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(Y.uid, uid.data(), uid.size() * 8, cudaMemcpyHostToDevice));
+  CU(cudaMemcpyAsync(Y.ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  if (hd.n_tracks > 0) CU(cudaMemcpyAsync(Y.comp, comp.data(), (size_t)hd.n_tracks * 4, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(Y.logw, logw.data(), logw.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(Y.uid, uid.data(), uid.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  // the copies read host vectors of this call: complete before returning
+  CU(cudaStreamSynchronize(h->stream));
   h->n_comp = nc;
   h->H = hd.n_hyp;
   h->n_entries = hd.n_tracks;
@@ -1691,8 +1694,11 @@ glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, 
     F.logdetS = h->pt.logdetS;
     F.cap_pairs = h->cap_pairs;
   }
-  if (mode != GLMB_GATE_OFF)
-    CU(cudaMemcpy(h->gate_params, params, GLMB_GATE_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+  if (mode != GLMB_GATE_OFF) {
+    CU(cudaMemcpyAsync(h->gate_params, params, GLMB_GATE_NPARAM * sizeof(float), cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
   if (mode != h->gate_mode) {
     // captured frame graphs were built for the other table path
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);

@@ -32,6 +32,10 @@ enum : uint32_t {
   kErrInput = 128u,     // a detection is NaN or infinite
   kErrGate = 256u,      // a tensor-core wait of the learned gate ran out of time
   kErrTimeout = 512u,   // a scan's look-back waited past its limit
+  // internal index checks (a violated invariant; the access is skipped)
+  kErrChkSurv = 1024u,  // a survivor index outside the frame's children
+  kErrChkComp = 2048u,  // a component index outside the working table
+  kErrChkRemap = 4096u, // a new-hypothesis entry outside the tables it names
 };
 
 constexpr float kFxScale = 4294967296.0f;          // 2^32

@@ -167,10 +167,11 @@ void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTabl
                            int grid, cudaStream_t s);
 void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
                   const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
-                  const unsigned* err, cudaStream_t s);
+                  const unsigned* err, uint32_t hmask, const FrameDev* fs, cudaStream_t s);
 // device error flags that abandon a frame (state left untouched)
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
-                               kErrEntries | kErrSlots | kErrInput | kErrGate | kErrTimeout;
+                               kErrEntries | kErrSlots | kErrInput | kErrGate | kErrTimeout | kErrChkSurv |
+                               kErrChkComp | kErrChkRemap;
 
 // ---- learned pair gate (gate_mlp.cu) ----
 // parameter vector (floats): W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64]

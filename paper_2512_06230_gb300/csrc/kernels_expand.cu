@@ -382,13 +382,20 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   // plan): the frame's maxima plan the next frame, or this frame's redo
   {
     unsigned kp = 0;
-    for (int t = tid; t < T; t += nthr)
-      kp += pt.cnt[t < Town ? a.parents.comp[plo + t] : (uint32_t)(birth_base + (t - Town))];
+    for (int t = tid; t < T; t += nthr) {
+      const uint32_t c = t < Town ? a.parents.comp[plo + t] : (uint32_t)(birth_base + (t - Town));
+      if (c >= (uint32_t)(birth_base + nb)) {   // invariant: slots name the working table
+        atomicOr(a.err, kErrChkComp);
+        continue;
+      }
+      kp += pt.cnt[c];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xFFFFFFFFu, kp, o);
     if ((tid & 31) == 0 && kp) atomicAdd(&sc.K, (int)kp);
   }
   __syncthreads();
+  if (tid == 0 && (*(volatile const unsigned*)a.err & kErrChkComp)) sc.bad = 1;
   if (tid == 0) {
     if (a.max_T) atomicMax(a.max_T, (unsigned)T);
     if (a.max_K) atomicMax(a.max_K, (unsigned)sc.K);
@@ -1141,7 +1148,10 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
       const uint32_t val = bit_of(tmask, t) ? newval[t] : v.refnew[t];
       a.out_comp[base + (uint32_t)t - below] = val;
-      if (!(val & kNewTag)) a.gc_flag[val] = 1u;   // an old component stays
+      if (!(val & kNewTag)) {   // an old component stays
+        if (val < (uint32_t)a.fs->T) a.gc_flag[val] = 1u;
+        else atomicOr(a.err, kErrChkRemap);
+      }
     }
     __syncwarp();
   }

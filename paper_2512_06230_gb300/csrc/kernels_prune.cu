@@ -584,9 +584,16 @@ __global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t
        x += (long long)gridDim.x * blockDim.x) {
     if (x < n_src) {
       const int c = (int)x;
-      if (flag[c]) copy_comp<DZ>(md, src, c, dst, (int)newpos[c]);
+      if (flag[c]) {
+        if (newpos[c] >= n_keep) atomicOr(err, kErrChkComp);
+        else copy_comp<DZ>(md, src, c, dst, (int)newpos[c]);
+      }
     } else {
       const int u = (int)(x - n_src);
+      if (upd_src[u] >= (uint32_t)n_src) {
+        atomicOr(err, kErrChkComp);
+        continue;
+      }
       long long se[DZ];
 #pragma unroll
       for (int a = 0; a < DZ; ++a) se[a] = upd_se[(size_t)a * cap_upd + u];
@@ -614,23 +621,28 @@ void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTabl
 __global__ void remap_kernel(uint32_t* out_comp, const unsigned* __restrict__ n_entries,
                              long long cap, const uint32_t* __restrict__ newpos,
                              const uint32_t* __restrict__ hvals,
-                             const unsigned* __restrict__ n_keep_dev, const unsigned* err) {
+                             const unsigned* __restrict__ n_keep_dev, const unsigned* err, uint32_t hmask,
+                             const FrameDev* __restrict__ fs) {
   pdl_enter();
   if (*(volatile const unsigned*)err & kErrFatal) return;
   const long long n = min((long long)*n_entries, cap);
-  const uint32_t n_keep = *n_keep_dev;
+  const uint32_t n_keep = *n_keep_dev, n_src = (uint32_t)fs->T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const uint32_t v = out_comp[e];
+    if ((v & kNewTag) ? (v & ~kNewTag) > hmask : v >= n_src) {
+      atomicOr((unsigned*)err, kErrChkRemap);
+      continue;
+    }
     out_comp[e] = (v & kNewTag) ? n_keep + hvals[v & ~kNewTag] : newpos[v];
   }
 }
 
 void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
                   const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
-                  const unsigned* err, cudaStream_t s) {
+                  const unsigned* err, uint32_t hmask, const FrameDev* fs, cudaStream_t s) {
   const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
-  launch_k(remap_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err);
+  launch_k(remap_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err, hmask, fs);
 }
 
 // ---------------------------------------------------------------------------

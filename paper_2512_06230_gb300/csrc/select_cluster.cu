@@ -384,6 +384,10 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
       const long long t = (long long)r * nthr + tid;
       if (t >= ns) break;
       const long long j = w.surv_idx[t];
+      if (j < 0 || j >= n) {   // invariant: every survivor index was written this frame
+        atomicOr(err, kErrChkSurv);
+        continue;
+      }
       const long long k = keys[j];
       if (held) {
 #pragma unroll
@@ -445,6 +449,10 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
           }
       } else {
         j = w.surv_idx[t];
+        if (j < 0 || j >= n) {
+          atomicOr(err, kErrChkSurv);
+          j = 0;
+        }
         k = keys[j];
         na = child_alive[j];
         pu = parents.uid[j / h_up];
