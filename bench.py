@@ -6,7 +6,9 @@ track update, estimates) on a seeded synthetic scene: 2-D constant velocity,
 100 objects appearing over the first 50 frames, 100 frames, clutter
 Poisson(20), 1 + Poisson(1.5) detections per detected object, H_max = 1000,
 H_up = 100.  Steps walk through the scene's frames in order; the filter is
-reset when the scene restarts.
+reset when the scene restarts.  Before the warm-up steps, one untimed set-up
+pass over the scene captures the frame graphs its plans need (reported as
+config.graph_precapture_frames; --no-precapture skips it).
 
 value  frames/s with each frame's detections already in device memory.
 e2e    frames/s through the same C ABI with host buffers: detections copied
@@ -559,12 +561,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=100,
-                    help="untimed steps (the default, one pass of the scene, fills the graph cache)")
+    ap.add_argument("--warmup", type=int, default=10,
+                    help="untimed warm-up steps (after the set-up pass that captures the frame graphs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scene", default="mid")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-precapture", action="store_true",
+                    help="skip the untimed set-up pass that captures the scene's frame graphs")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
     ap.add_argument("--scenes", type=int, default=64,
@@ -701,9 +705,15 @@ def main():
                              d2h=est["n"] * 352 + 64 * 8))
         return times, work
 
-    # warm-up, then the timed steps; the expansion is timed with events in
-    # every run (the same mask throughout, so the warm-up's graphs are reused)
+    # set-up: one untimed pass over the scene captures the frame graphs of
+    # every plan the scene needs (a reset restarts the planning state, so a
+    # later pass replays the same plans); then the warm-up, then the timed
+    # steps.  The expansion is timed with events in every run (the same mask
+    # throughout, so the set-up pass's graphs are reused).
     f.set_profiling(["expand"])
+    precapture = 0 if args.no_precapture else F
+    if precapture:
+        run(precapture, 0, host=False)
     run(args.warmup, 0, host=False)
     torch.cuda.synchronize()
     if world > 1:
@@ -770,7 +780,8 @@ def main():
                    "scene": args.scene, "h_max": cfg["h_max"], "h_up": h_up,
                    "frames_per_scene": F, "l2": "flushed between steps (256 MiB write, outside "
                    "the timed events)" if not args.no_flush else "not flushed",
-                   "inputs": "detections resident in device memory; births (<1 KB) copied in predict"},
+                   "inputs": "detections resident in device memory; births (<1 KB) copied in predict",
+                   "graph_precapture_frames": precapture},
         "hypothesis_track_updates_per_s": entries * world / (total_ms / 1000.0),
         "e2e": {"value": frames / (total_h / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": sum(w["h2d"] for w in work_h) / len(work_h),

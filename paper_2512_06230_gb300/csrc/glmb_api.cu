@@ -329,6 +329,7 @@ glmb_status set_initial(glmb_handle* h) {
   h->frame = 0;
   h->stage = 0;
   h->alive_max = 0;
+  h->K_est = 256;   // the planning state starts over with the filter
   h->have_update = false;
   h->theta_M_valid = false;
   return GLMB_OK;
