@@ -126,7 +126,7 @@ def run_oracle(args, sc, cfg, budget_s):
     """FP64 oracle over the scene's frames from the initial GLMB, all host
     threads, until the scene ends or the time budget is spent."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
     o = oracle.Oracle(cfg, n_threads=threads)
     t0 = time.perf_counter()
     n = 0
@@ -570,6 +570,8 @@ def main():
     ap.add_argument("--no-precapture", action="store_true",
                     help="skip the untimed set-up pass that captures the scene's frame graphs")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the oracle leg (0: all cores)")
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
     ap.add_argument("--scenes", type=int, default=64,
                     help="--scene batch: independent scenes per frame")
