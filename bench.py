@@ -65,6 +65,24 @@ def expansion_traffic():
         return None
 
 
+def max_over_ranks(value: float, device, world: int) -> float:
+    """The largest of the ranks' values (every rank gets it): the job's time
+    is its slowest rank's.  One rank: the value itself."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the frames of all ranks over the slowest rank's
+    time (ms)."""
+    return steps_per_rank * world / (max_ms / 1000.0)
+
+
 def scene_for_rank(args, rank):
     p = scenes.preset(args.scene)
     return scenes.make_scene(p, 1000 * 2 + rank if args.seed is None else args.seed + rank)
@@ -737,19 +755,12 @@ def main():
     tim = f.timing()
     stop.set()
     th.join(timeout=10)
-    total_ms = float(sum(times))
+    total_ms = max_over_ranks(float(sum(times)), dev, world)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     # end to end through the host-buffer path
     times_h, work_h = run(args.steps, args.warmup, host=True)
-    total_h = float(sum(times_h))
-    if world > 1:
-        t = torch.tensor([total_h], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_h = float(t.item())
+    total_h = max_over_ranks(float(sum(times_h)), dev, world)
     stage = None
     if args.stages:
         f.set_profiling(list(glmb.Filter.STAGES))
@@ -760,7 +771,7 @@ def main():
     if rank != 0:
         return
     frames = args.steps * world
-    value = frames / (total_ms / 1000.0)
+    value = job_rate(args.steps, world, total_ms)
     entries = sum(w["entries"] for w in work)
     # roofline of the dominant kernel (child expansion): integer ALU work of
     # the counter-based sampler, 100 32-bit operations per Philox4x32-10
