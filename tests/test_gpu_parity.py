@@ -209,3 +209,13 @@ def test_sweep_full_size_frame(oracle_mod, glmb, N, k):
                            max_tracks=2 * N + nb + 64)
     rep = _frame(oracle_mod, glmb, cfg, sc, k)
     assert rep.checks["slots"] > 10000
+
+
+@pytest.mark.parametrize("h_up,h_max,k", [(1, 50, 12), (300, 200, 8), (1000, 400, 10)])
+def test_draw_counts_and_caps(oracle_mod, glmb, h_up, h_max, k):
+    """H_up = 1 (one child per parent: every frame keeps the reference-most
+    draw or nothing), and H_up of 300 and 1000, whose draws span several
+    ragged 256-child slices of a parent in the thread-per-child kernel."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1021)
+    rep = _frame(oracle_mod, glmb, sc.filter_config(h_up=h_up, h_max=h_max), sc, k)
+    assert rep.checks["children"] % h_up == 0
