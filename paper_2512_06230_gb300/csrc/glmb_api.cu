@@ -298,20 +298,32 @@ bool spd_inverse(int n, const double* A, double* Ainv, double* logdet) {
 }
 
 
+// every condition flagged in e, joined (a static buffer: the caller copies it)
 const char* err_text(unsigned e) {
-  if (e & kErrPairs) return "gated pairs exceed max_pairs";
-  if (e & kErrSlots) return "per-hypothesis staging exceeded its plan";
-  if (e & kErrEntries) return "hypothesis entries exceed h_max * max_tracks";
-  if (e & kErrComps) return "components exceed capacity";
-  if (e & kErrUpdates) return "distinct track updates exceed capacity";
-  if (e & kErrHash) return "update table full";
-  if (e & kErrNumeric) return "covariance not positive definite";
-  if (e & kErrGate) return "learned gate: a tensor-core wait ran out of time";
-  if (e & kErrTimeout) return "a scan's look-back waited past its limit";
-  if (e & kErrChkSurv) return "internal check: a survivor index outside the frame's children";
-  if (e & kErrChkComp) return "internal check: a component index outside the working table";
-  if (e & kErrChkRemap) return "internal check: a new-hypothesis entry outside its tables";
-  return "device error";
+  static const struct { unsigned bit; const char* text; } kText[] = {
+      {kErrPairs, "gated pairs exceed max_pairs"},
+      {kErrSlots, "per-hypothesis staging exceeded its plan"},
+      {kErrEntries, "hypothesis entries exceed h_max * max_tracks"},
+      {kErrComps, "components exceed capacity"},
+      {kErrUpdates, "distinct track updates exceed capacity"},
+      {kErrHash, "update table full"},
+      {kErrNumeric, "covariance not positive definite"},
+      {kErrInput, "a detection is not finite"},
+      {kErrGate, "learned gate: a tensor-core wait ran out of time"},
+      {kErrTimeout, "a scan's look-back waited past its limit"},
+      {kErrChkSurv, "internal check: a survivor index outside the frame's children"},
+      {kErrChkComp, "internal check: a component index outside the working table"},
+      {kErrChkRemap, "internal check: a new-hypothesis entry outside its tables"},
+  };
+  thread_local static char buf[512];
+  buf[0] = 0;
+  for (const auto& t : kText)
+    if (e & t.bit) {
+      if (buf[0]) std::strncat(buf, "; ", sizeof buf - std::strlen(buf) - 1);
+      std::strncat(buf, t.text, sizeof buf - std::strlen(buf) - 1);
+    }
+  if (!buf[0]) std::snprintf(buf, sizeof buf, "device error 0x%x", e);
+  return buf;
 }
 
 glmb_status set_initial(glmb_handle* h) {
@@ -894,6 +906,20 @@ int plan_smem(const glmb_handle* h, const Plan& p) {
   return expand_image_bytes(h->md.dz, p.T, p.K, p.M);
 }
 
+// the largest slot and pair counts over the frame's parents, computed from
+// the table alone (a redo plans from these, whatever the failed pass staged)
+glmb_status exact_maxima(glmb_handle* h, unsigned& max_T, unsigned& max_K) {
+  CU(cudaMemsetAsync(h->d_scal + S_MAXT, 0, 2 * sizeof(unsigned), h->stream));
+  launch_parent_stats(h->hyps[h->par_buf], h->d_fs, h->pt, h->d_scal + S_MAXT, h->d_scal + S_MAXK,
+                      std::max(1, std::min((h->H + 127) / 128, 4 * h->n_sm)), h->stream);
+  unsigned m[2] = {0, 0};
+  CU(cudaMemcpyAsync(m, h->d_scal + S_MAXT, sizeof m, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  max_T = m[0];
+  max_K = m[1];
+  return GLMB_OK;
+}
+
 // frame result: commit, abandon, or redo with exact maxima; `done` on return
 // the frame's counters (and, with estimates, the estimate block) to pinned
 // host memory, on the stream
@@ -935,8 +961,10 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
     // a parent had more gated pairs than planned: redo the expansion and
     // the pruning with the exact maxima of this frame
     ++h->redo_count;
+    unsigned mt = 0, mk = 0;
+    if ((st = exact_maxima(h, mt, mk)) != GLMB_OK) return st;
     Plan p;
-    if (!make_plan(h, false, std::max(1, (int)h->h_scal[S_MAXT]), std::max(1, (int)h->h_scal[S_MAXK]), h->M, p))
+    if (!make_plan(h, false, std::max(1u, mt), std::max(1u, mk), h->M, p))
       return abandon(GLMB_E_CAPACITY, "per-hypothesis table exceeds the supported sizes");
     if ((st = ensure_img(h, p)) != GLMB_OK) return abandon(st, "expansion images do not fit");
     CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
@@ -1044,7 +1072,10 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
   CU(cudaMemcpy(sc, h->d_scal, sizeof sc, cudaMemcpyDeviceToHost));
   if ((sc[S_ERR] & kErrSlots) && !(sc[S_ERR] & (kErrFatal & ~kErrSlots))) {
     Plan q;
-    if (make_plan(h, false, std::max(1u, sc[S_MAXT]), std::max(1u, sc[S_MAXK]), h->M, q) &&
+    unsigned mt = 0, mk = 0;
+    h->par_buf = h->hcur;   // exact_maxima reads the parents of this update
+    if ((st = exact_maxima(h, mt, mk)) != GLMB_OK) return st;
+    if (make_plan(h, false, std::max(1u, mt), std::max(1u, mk), h->M, q) &&
         ensure_img(h, q) == GLMB_OK) {
       ++h->redo_count;
       CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));

@@ -675,8 +675,11 @@ __global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H;
   // a table that failed (e.g. pairs beyond capacity, whose offsets then run
-  // past the pair arrays) is not staged; the frame is abandoned
-  if (*(volatile const unsigned*)a.err & kErrFatal) return;
+  // past the pair arrays) is not staged; the frame is abandoned.  The flags
+  // this kernel raises itself (a parent beyond the plan, a bad slot index)
+  // are set by its CTAs while others start, so they must not stop a CTA:
+  // every parent's counts are recorded
+  if (*(volatile const unsigned*)a.err & (kErrFatal & ~(kErrSlots | kErrChkComp))) return;
   for (int h = blockIdx.x; h < H; h += gridDim.x) {
     unsigned char* img = a.img + (size_t)h * a.img_stride;
     __syncthreads();   // the previous parent's copy-out has read shared memory
