@@ -5,6 +5,21 @@ step of the filter runs in the library's CUDA kernels.  The library is
 built in-tree by :func:`build` (sm_103a only).  Importing this module never
 falls back to another implementation: if ``libglmb.so`` is missing,
 :class:`Filter` raises.
+
+Use::
+
+    import paper_2512_06230_gb300 as glmb
+    glmb.build()
+    f = glmb.Filter(cfg)                   # cfg: dict of glmb_config fields
+    for births, Z in frames:               # births: [(r, mean, cov)], Z: (M, dim_z)
+        f.step(births, Z)                  # predict + update + prune (one graph)
+        est = f.estimates()                # labels, existence, means, covariances
+    f.close()
+
+Several independent scenes step together with :func:`step_batch`; the
+learned pair gate is set with :meth:`Filter.set_gate` and trained with
+:mod:`paper_2512_06230_gb300.gate`; launch shapes are tuned with
+:mod:`paper_2512_06230_gb300.tune`.
 """
 from __future__ import annotations
 
