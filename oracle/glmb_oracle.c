@@ -59,10 +59,14 @@
  *       with bf16 weights and bf16-rounded inputs and activations (the
  *       precision the library decides in), accumulated in double.
  *
- * Parity unpinned: R2 (death probability) and R9 (estimator) are readings
- * with no value in the paper to check them against; the tests only hold the
- * code to the stated formulas.  Everything else is pinned by closed forms,
- * brute force and independent restatements (tests/test_oracle_pins.py).
+ * R2 is pinned where the model reduces to the single-detection Bernoulli
+ * filter (one track, lambda_d = 0): the death probability equals the exact
+ * marginal over every enumerated child.  R9's sums (cardinality pmf, label
+ * existence) are pinned against the brute-force posterior.  Parity
+ * unpinned: R9's choice of the MAP cardinality, then the heaviest
+ * hypothesis of that cardinality, is a reading with nothing in the paper to
+ * check it against.  Everything else is pinned by closed forms, brute force
+ * and independent restatements (tests/test_oracle_pins.py).
  */
 #include "glmb_oracle.h"
 

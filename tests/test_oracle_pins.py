@@ -493,3 +493,48 @@ def test_death_probability_follows_reading(oracle_mod):
         psi = (1 - cfg["p_d"]) + sum(cfg["p_d"] * multivariate_normal(m[:2], S).pdf(z)
                                      for z in g) / kappa
         assert abs(o.slot(0, t)["dprob"] - (1 - p) / ((1 - p) + p * psi)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# R2 and R9 against the exact posterior, where the model reduces to the
+# textbook single-detection Bernoulli / GLMB filter
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,M", [(40, 3), (41, 4), (42, 2)])
+def test_death_probability_is_the_exact_marginal_of_a_single_track(oracle_mod, seed, M):
+    """With one track and exactly one detection per detected object
+    (lambda_d = 0), the posterior over (death, associations) is the
+    single-detection Bernoulli filter's.  The marginal probability that the
+    track is dead, summed over every enumerated child, is then what reading
+    R2 computes from the compatibility row alone."""
+    rng = np.random.default_rng(seed)
+    o, cfg, Z, slots = _tiny(oracle_mod, rng, n_tracks=1, M=M, births=0, lambda_d=0.0, p_s=0.9)
+    dead, theta, lw = o.bruteforce(0)
+    w = np.exp(lw - lw.max())
+    finite = np.isfinite(lw)
+    p_dead = w[finite & (dead[:, 0] == 1)].sum() / w[finite].sum()
+    assert o.slot(0, 0)["dprob"] == pytest.approx(p_dead, rel=1e-10, abs=1e-14)
+
+
+def test_cardinality_and_existence_are_sums_over_the_exact_posterior(oracle_mod):
+    """With every child of the parent retained (H_max above the association
+    space, tau below every weight, H_up large enough to sample them all),
+    the cardinality distribution and the label existences of the estimates
+    equal the sums over the brute-force posterior."""
+    rng = np.random.default_rng(31)
+    o, cfg, Z, slots = _tiny(oracle_mod, rng, n_tracks=2, M=2, births=1, h_up=60000, h_max=100000, p_s=1.0,
+                             tau=1e-300)
+    dead, theta, lw = o.bruteforce(0)
+    finite = np.isfinite(lw)
+    dead, lw = dead[finite], lw[finite]
+    w = np.exp(lw - np.logaddexp.reduce(lw))
+    card = (dead == 0).sum(axis=1)
+    pmf_exact = np.bincount(card, weights=w, minlength=5)
+    labels = [o.slot(0, t)["label"] for t in range(o.parent_slots(0))]
+    exist_exact = {labels[t]: w[dead[:, t] == 0].sum() for t in range(len(labels))}
+    o.prune()
+    idx, klw, _ = o.kept()
+    assert len(idx) == len(lw), "not every child of the association space was sampled"
+    e = o.estimates()
+    np.testing.assert_allclose(e["pmf"][:len(pmf_exact)], pmf_exact, atol=1e-12)
+    for lab, r in zip(e["labels"], e["r"]):
+        assert r == pytest.approx(exist_exact[tuple(lab)], abs=1e-12)
