@@ -410,19 +410,21 @@ class Filter:
     # ---- outputs ----
     def estimates(self, cap: int = 4096, pmf_cap: int = 4096):
         """MAP tracks (labels, existence, mean, cov) and the cardinality pmf."""
+        # the output buffers and their pointers are kept between calls (this
+        # runs once per frame; building ctypes pointers costs microseconds)
         buf = getattr(self, "_est_buf", None)
         if buf is None or len(buf[0]) < cap or len(buf[1]) < pmf_cap:
-            buf = (np.zeros(cap, TRACK_DTYPE), np.zeros(pmf_cap))
+            o, q, n = np.zeros(cap, TRACK_DTYPE), np.zeros(pmf_cap), C.c_int()
+            buf = (o, q, _ptr(o), _ptr(q), n, C.byref(n))
             self._est_buf = buf
-        out, pmf = buf
-        n = C.c_int()
-        self._check(self.lib.glmb_estimates(self.h, _ptr(out), cap, C.byref(n), _ptr(pmf), pmf_cap))
+        out, pmf, p_out, p_pmf, n, n_ref = buf
+        self._check(self.lib.glmb_estimates(self.h, p_out, cap, n_ref, p_pmf, pmf_cap))
         k, dx = n.value, self.dx
         t = out[:k].copy()
-        # labels: (k, 2) array of (label_k, label_b); the rest are views of
-        # this call's own copy of the records
-        return dict(n=k, labels=np.stack((t["label_k"], t["label_b"]), axis=1),
-                    r=t["r"], mean=t["mean"][:, :dx],
+        # every field is a view of this call's own copy of the records;
+        # labels: (k, 2) of (label_k, label_b), the records' first two words
+        words = t.view(np.uint32).reshape(k, TRACK_DTYPE.itemsize // 4)
+        return dict(n=k, labels=words[:, :2], r=t["r"], mean=t["mean"][:, :dx],
                     cov=t["cov"][:, : dx * dx].reshape(k, dx, dx), pmf=pmf[:pmf_cap].copy())
 
     STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")

@@ -108,10 +108,13 @@ struct glmb_handle {
   long long* upd_se = nullptr;
   uint32_t* gc_flag = nullptr;
   uint32_t* gc_newpos = nullptr;
+  // frame results, one device block copied back in one piece:
+  // [scalars (S_N)][prune counters (8)][estimates], mirrored in pinned host
+  // memory up to the estimates' r array
   unsigned* d_scal = nullptr;
   unsigned* h_scal = nullptr;
-  // estimates: one device block [nb (16 B)][pmf][tracks][r][done], mirrored on
-  // the host up to r
+  size_t res_off_cnt = 0, res_off_est = 0;
+  // estimates: [nb (16 B)][pmf][tracks][r][done], mirrored on the host up to r
   unsigned char* d_est = nullptr;
   unsigned char* h_est = nullptr;
   size_t est_off_pmf = 0, est_off_tr = 0, est_off_r = 0, est_off_done = 0;
@@ -130,7 +133,11 @@ struct glmb_handle {
   bool ev_pending[kNumStages] = {};
   double stage_ms[kNumStages] = {};
   long long stage_calls[kNumStages] = {};
-  // frame sizes on the device (two pinned host slots: predict, update)
+  // frame inputs, one device block [sizes][births][detections] that a frame
+  // graph fills with one copy from its pinned image; the host block is
+  // [sizes slot 0][the device block's image, whose sizes are slot 1]
+  // (slot 0: glmb_predict, slot 1: glmb_update and glmb_step)
+  size_t in_off_births = 0, in_off_Z = 0;
   FrameDev* d_fs = nullptr;
   FrameDev* h_fs = nullptr;
   // shared-memory plan of the expansion: exact slot maximum (from the last
@@ -249,14 +256,41 @@ void free_all(glmb_handle* h) {
   h->host_allocs.clear();
 }
 
-bool alloc_est(glmb_handle* h) {
+size_t round_up64(size_t x) { return (x + 63) / 64 * 64; }
+
+// The frame's input and result blocks (layouts at their handle fields).
+bool alloc_io(glmb_handle* h) {
+  const size_t fs = sizeof(FrameDev);
+  h->in_off_births = round_up64(fs);
+  h->in_off_Z = h->in_off_births + round_up64((size_t)h->cap_births * kBirthRec * sizeof(double));
+  const size_t in_bytes = h->in_off_Z + (size_t)h->cap_meas * h->md.dz * sizeof(float);
+  unsigned char *din = nullptr, *hin = nullptr;
+  if (!dalloc(h, &din, (long long)in_bytes) || !halloc(h, &hin, (long long)(fs + in_bytes))) return false;
+  h->d_fs = reinterpret_cast<FrameDev*>(din);
+  h->d_births = reinterpret_cast<double*>(din + h->in_off_births);
+  h->d_Z = reinterpret_cast<float*>(din + h->in_off_Z);
+  h->h_fs = reinterpret_cast<FrameDev*>(hin);
+  h->h_births = reinterpret_cast<double*>(hin + fs + h->in_off_births);
+  h->h_Z = reinterpret_cast<float*>(hin + fs + h->in_off_Z);
+
   const size_t pcap = (size_t)h->max_tracks + 1;
   h->est_off_pmf = 16;
   h->est_off_tr = h->est_off_pmf + 8 * pcap;
   h->est_off_r = h->est_off_tr + sizeof(glmb_track) * pcap;
   h->est_off_done = h->est_off_r + 8 * pcap;
-  const size_t bytes = h->est_off_done + 16;
-  return dalloc(h, &h->d_est, (long long)bytes) && halloc(h, &h->h_est, (long long)h->est_off_r);
+  h->res_off_cnt = round_up64(S_N * sizeof(unsigned));
+  h->res_off_est = h->res_off_cnt + 64;
+  unsigned char *dres = nullptr, *hres = nullptr;
+  if (!dalloc(h, &dres, (long long)(h->res_off_est + h->est_off_done + 16)) ||
+      !halloc(h, &hres, (long long)(h->res_off_est + h->est_off_r)))
+    return false;
+  h->d_scal = reinterpret_cast<unsigned*>(dres);
+  h->pw.counts = reinterpret_cast<unsigned*>(dres + h->res_off_cnt);
+  h->d_est = dres + h->res_off_est;
+  h->h_scal = reinterpret_cast<unsigned*>(hres);
+  h->h_cnt = reinterpret_cast<unsigned*>(hres + h->res_off_cnt);
+  h->h_est = hres + h->res_off_est;
+  return true;
 }
 
 long long next_pow2(long long x) {
@@ -531,11 +565,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   const long long scan_n = std::max(h->cap_comp, h->cap_children);
   bool ok = alloc_comps(h, h->comps[0], h->cap_comp, dx) && alloc_comps(h, h->comps[1], h->cap_comp, dx) &&
             alloc_hyps(h, h->hyps[0]) && alloc_hyps(h, h->hyps[1]) &&
-            dalloc(h, &h->d_births, (long long)h->cap_births * kBirthRec) &&
-            halloc(h, &h->h_births, (long long)h->cap_births * kBirthRec) &&
-            alloc_est(h) &&
-            dalloc(h, &h->d_Z, (long long)h->cap_meas * dz) &&
-            halloc(h, &h->h_Z, (long long)h->cap_meas * dz) &&
+            alloc_io(h) &&
             dalloc(h, &h->pt.cnt, h->cap_comp + 1) && dalloc(h, &h->pt.ptr, h->cap_comp + 1) &&
             dalloc(h, &h->pt.meas, h->cap_pairs) && dalloc(h, &h->pt.logC, h->cap_pairs) &&
             dalloc(h, &h->pt.q, h->cap_pairs) && dalloc(h, &h->pt.e, h->cap_pairs * dz) &&
@@ -551,13 +581,11 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->pw.hist, 4096) && dalloc(h, &h->pw.sel, 4) &&
             dalloc(h, &h->pw.flags, h->cap_children) &&
             dalloc(h, &h->pw.flags_tmp, scan_tmp_elems(h->cap_children)) &&
-            dalloc(h, &h->pw.surv_idx, h->cap_h) && dalloc(h, &h->pw.counts, 8) &&
+            dalloc(h, &h->pw.surv_idx, h->cap_h) &&
             dalloc(h, &h->hkeys, hcap) && dalloc(h, &h->hvals, hcap) &&
             dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
             dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
-            dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_scal, S_N) &&
-            halloc(h, &h->h_scal, S_N) && halloc(h, &h->h_cnt, 8) && dalloc(h, &h->d_ru, h->cap_meas) &&
-            dalloc(h, &h->d_fs, 1) && halloc(h, &h->h_fs, 2);
+            dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_ru, h->cap_meas);
   if (ok) {
     h->pw.err = h->d_scal + S_ERR;
     h->pw.flags_tmp_cap = h->cap_children;
@@ -924,10 +952,9 @@ glmb_status exact_maxima(glmb_handle* h, unsigned& max_T, unsigned& max_K) {
 // the frame's counters (and, with estimates, the estimate block) to pinned
 // host memory, on the stream
 glmb_status enqueue_results(glmb_handle* h, bool with_est) {
-  CU(cudaMemcpyAsync(h->h_cnt, h->pw.counts, 8 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaMemcpyAsync(h->h_scal, h->d_scal, S_N * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
-  if (with_est)
-    CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, h->stream));
+  // scalars and counters (and the estimates) in one copy of the result block
+  const size_t bytes = with_est ? h->res_off_est + h->est_off_r : h->res_off_cnt + 8 * sizeof(unsigned);
+  CU(cudaMemcpyAsync(h->h_scal, h->d_scal, bytes, cudaMemcpyDeviceToHost, h->stream));
   return GLMB_OK;
 }
 
@@ -1163,10 +1190,9 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
       const auto t_cap = std::chrono::steady_clock::now();
       CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
-      cudaMemcpyAsync(h->d_fs, &h->h_fs[1], sizeof(FrameDev), cudaMemcpyHostToDevice, h->stream);
-      cudaMemcpyAsync(h->d_births, h->h_births, (size_t)h->cap_births * kBirthRec * sizeof(double),
-                      cudaMemcpyHostToDevice, h->stream);
-      cudaMemcpyAsync(h->d_Z, h->h_Z, (size_t)std::min(q.M, h->cap_meas) * h->md.dz * sizeof(float),
+      // sizes, births and host detections in one copy of the input block
+      cudaMemcpyAsync(h->d_fs, &h->h_fs[1],
+                      h->in_off_Z + (size_t)std::min(q.M, h->cap_meas) * h->md.dz * sizeof(float),
                       cudaMemcpyHostToDevice, h->stream);
       enqueue_predict(h, q);
       enqueue_table(h, q);
