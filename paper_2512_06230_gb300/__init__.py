@@ -349,12 +349,25 @@ class Filter:
         arr = self._births(births)
         self._check(self.lib.glmb_predict(self.h, _ptr(arr), len(births)))
 
+    def _dev_z(self, Z):
+        """Pointer and row count of detections in device memory: a CUDA
+        tensor (torch) of shape (M, dim_z), float32, contiguous.  Anything
+        else is refused here, before the kernels could read it as such."""
+        if not getattr(Z, "is_cuda", False):
+            raise TypeError("device detections: a CUDA tensor is required")
+        if not Z.is_floating_point() or Z.element_size() != 4 or Z.is_complex():
+            raise TypeError(f"device detections: float32 required, got {Z.dtype}")
+        if Z.dim() != 2 or (Z.shape[1] != self.dz and Z.shape[0] > 0):
+            raise ValueError(f"device detections: shape (M, {self.dz}) required, got {tuple(Z.shape)}")
+        if not Z.is_contiguous():
+            raise ValueError("device detections: a contiguous tensor is required")
+        return C.c_void_p(Z.data_ptr()), int(Z.shape[0])
+
     def update(self, Z, device: bool = False):
         if device:
-            # a CUDA tensor (torch) of shape (M, dim_z), float32, contiguous
-            M = int(Z.shape[0])
+            zp, M = self._dev_z(Z)
             self.M = M
-            self._check(self.lib.glmb_update(self.h, C.c_void_p(Z.data_ptr()), M, 1))
+            self._check(self.lib.glmb_update(self.h, zp, M, 1))
             return
         Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
         self.M = len(Zf)
@@ -366,8 +379,8 @@ class Filter:
     def _frame_args(self, births, Z, device):
         arr = self._births(births)
         if device:
-            M = int(Z.shape[0])
-            return arr, len(births), C.c_void_p(Z.data_ptr()), M, 1, None
+            zp, M = self._dev_z(Z)
+            return arr, len(births), zp, M, 1, None
         Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
         return arr, len(births), _ptr(Zf), len(Zf), 0, Zf
 
@@ -398,10 +411,9 @@ class Filter:
         """One frame in one call (glmb_step: a replayed CUDA graph)."""
         arr = self._births(births)
         if device:
-            M = int(Z.shape[0])
+            zp, M = self._dev_z(Z)
             self.M = M
-            self._check(self.lib.glmb_step(self.h, _ptr(arr), len(births),
-                                           C.c_void_p(Z.data_ptr()), M, 1))
+            self._check(self.lib.glmb_step(self.h, _ptr(arr), len(births), zp, M, 1))
             return
         Zf = np.ascontiguousarray(Z, dtype=np.float32).reshape(-1, self.dz)
         self.M = len(Zf)

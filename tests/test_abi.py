@@ -3,6 +3,8 @@ every entry point declared in include/glmb.h (no compute calls here)."""
 import ctypes
 import re
 
+import pytest
+
 import paper_2512_06230_gb300 as glmb
 
 
@@ -58,3 +60,33 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
         assert "no fallback" in str(e)
     else:
         raise AssertionError("load() must raise without the CUDA library")
+
+
+def test_device_detections_are_checked_before_the_call():
+    """Detections passed as device memory must be a contiguous float32 CUDA
+    tensor of shape (M, dim_z); the binding refuses anything else before a
+    kernel could read it (host logic, checked with stand-in tensors)."""
+    import types
+
+    import paper_2512_06230_gb300 as g
+
+    def fake(**kw):
+        a = dict(is_cuda=True, dtype="float32", shape=(3, 2), data_ptr=lambda: 4096,
+                 is_floating_point=lambda: True, is_complex=lambda: False, element_size=lambda: 4,
+                 dim=lambda: len(a["shape"]), is_contiguous=lambda: True)
+        a.update(kw)
+        return types.SimpleNamespace(**a)
+
+    f = types.SimpleNamespace(dz=2)
+    ptr, M = g.Filter._dev_z(f, fake())
+    assert M == 3 and ptr.value == 4096
+    assert g.Filter._dev_z(f, fake(shape=(0, 3)))[1] == 0      # empty: any width
+    bad = [(fake(is_cuda=False), TypeError), (fake(element_size=lambda: 8), TypeError),
+           (fake(is_floating_point=lambda: False), TypeError), (fake(shape=(3, 3)), ValueError),
+           (fake(shape=(6,)), ValueError), (fake(is_contiguous=lambda: False), ValueError)]
+    for z, err in bad:
+        with pytest.raises(err):
+            g.Filter._dev_z(f, z)
+    import numpy as np
+    with pytest.raises(TypeError):
+        g.Filter._dev_z(f, np.zeros((3, 2), np.float32))
