@@ -82,7 +82,8 @@
 
 /* ------------------------------------------------------------------ */
 /* Counter-based generator: Philox4x32-10 from Salmon, Moraes, Dror and  */
-/* Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).         */
+/* Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11); pinned   */
+/* to the known-answer vectors published with that definition.          */
 /* ------------------------------------------------------------------ */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
   uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];

@@ -32,6 +32,25 @@ def philox_np(ctr, key):
     return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
 
 
+def _golden_philox():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [[int(w, 16) for w in line.split()] for line in open(path)
+            if line.strip() and not line.startswith("#")]
+    a = np.array(rows, dtype=np.uint64).astype(np.uint32)
+    return a[:, :4], a[:, 4:6], a[:, 6:10]
+
+
+def test_philox_matches_published_known_answers(oracle_mod):
+    """The generator both sides implement, against the known-answer vectors
+    published with its definition (Salmon et al., SC'11)."""
+    ctr, key, out = _golden_philox()
+    assert len(ctr) == 3
+    np.testing.assert_array_equal(philox_np(ctr, key), out)
+    for j in range(len(ctr)):
+        np.testing.assert_array_equal(oracle_mod.philox(ctr[j], key[j]), out[j])
+
+
 def test_philox_two_implementations_agree(oracle_mod):
     rng = np.random.default_rng(7)
     ctr = rng.integers(0, 2 ** 32, size=(500, 4), dtype=np.uint64).astype(np.uint32)
