@@ -89,6 +89,19 @@ def test_philox_is_uniform_and_mixes():
     assert 60 < flips.mean() < 68 and flips.min() > 56
 
 
+def test_mix64_matches_the_published_sequence(oracle_mod):
+    """The mix behind hypothesis identifiers is SplitMix64's output function:
+    stepping its state from 0 reproduces the generator's reference outputs."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.txt")
+    want = [int(line, 16) for line in open(path) if line.strip() and not line.startswith("#")]
+    state, got = 0, []
+    for _ in want:
+        state = (state + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+        got.append(oracle_mod.mix64(state))
+    assert got == want
+
+
 def test_mix64_distinct(oracle_mod):
     vals = {oracle_mod.mix64(x) for x in range(20000)}
     assert len(vals) == 20000
