@@ -138,3 +138,33 @@ def test_torch_allocator_hook_gives_the_same_results(glmb):
     a.close()
     b.close()
     assert torch.cuda.memory_allocated() == base
+
+
+def test_step_graphs_with_device_detections_match_separate_calls(glmb):
+    """The configuration the benchmark times: the mid scene stepped through
+    replayed frame graphs with detections resident in device memory.  Every
+    frame must equal predict / update / prune with host detections (the path
+    the oracle parity tests check) bit for bit: retained hypotheses, their
+    weights, and the estimates."""
+    import torch
+    sc = scenes.make_scene(scenes.preset("mid"), 1015)
+    import bench
+    cfg = bench.filter_cfg(sc)
+    a, b = glmb.Filter(cfg), glmb.Filter(cfg)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for k, fr in enumerate(sc.frames[:40]):
+        Zd = torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
+        a.step(fr.births, Zd, device=True)
+        b.predict(fr.births)
+        b.update(fr.Z)
+        b.prune()
+        ha, hb = a.hypotheses(), b.hypotheses()
+        np.testing.assert_array_equal(ha["uid"], hb["uid"], err_msg=f"frame {k}")
+        np.testing.assert_array_equal(ha["logw"], hb["logw"], err_msg=f"frame {k}")
+        ea = a.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+        eb = b.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+        assert ea["n"] == eb["n"], k
+        for key in ("labels", "r", "mean", "cov", "pmf"):
+            np.testing.assert_array_equal(ea[key], eb[key], err_msg=f"frame {k}: {key}")
+    info = a.info()
+    assert info["n_graph_launches"] >= 30 and info["n_graph_captures"] < info["n_graph_launches"]
