@@ -799,7 +799,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   a.child_status = h->child_status;
   a.child_alive = h->child_alive;
   const int img = (int)a.img_stride;
-  // stage: one 128-thread CTA per parent
+  // stage: one CTA of stage_threads threads per parent (persistent grid)
   const int st_smem = p.smem ? img : 0;
   const int st_thr = h->tune.stage_threads;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
