@@ -219,3 +219,31 @@ def test_draw_counts_and_caps(oracle_mod, glmb, h_up, h_max, k):
     sc = scenes.make_scene(scenes.preset("tiny"), 1021)
     rep = _frame(oracle_mod, glmb, sc.filter_config(h_up=h_up, h_max=h_max), sc, k)
     assert rep.checks["children"] % h_up == 0
+
+
+@pytest.mark.parametrize("h_max,tau,k,kept", [(1, 1e-5, 9, "one"), (100000, 1e-300, 4, "all"),
+                                               (5000, 1e-300, 5, "cap")])
+def test_truncation_extremes(oracle_mod, glmb, h_max, tau, k, kept):
+    """H_max = 1 keeps only the heaviest child (ties to the lower child
+    index).  With tau ~ 0: a frame of 573 parents whose ~3200 unique
+    children all fit under H_max = 100 000 keeps every one (no radix round
+    decides anything), and a frame of 3231 parents with ~17 000 unique
+    children fills H_max = 5000 exactly."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1022)
+    rep = _frame(oracle_mod, glmb, sc.filter_config(h_max=h_max, tau=tau), sc, k)
+    if kept == "one":
+        assert rep.checks["retained"] == 1
+    elif kept == "all":
+        assert rep.checks["retained"] == rep.checks["unique_children"] > 10000
+    else:
+        assert rep.checks["retained"] == h_max
+
+
+def test_detections_at_capacity(oracle_mod, glmb):
+    """A frame whose detection count equals max_meas exactly (the detection
+    buffers and per-hypothesis association rows full to the last entry)."""
+    sc = scenes.make_scene(scenes.preset("tiny"), 1023)
+    k = 8
+    cfg = sc.filter_config(max_meas=len(sc.frames[k].Z))
+    assert cfg["max_meas"] > 0
+    _frame(oracle_mod, glmb, cfg, sc, k)
