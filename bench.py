@@ -176,8 +176,12 @@ def run_batch(args, glmb, torch, dev):
     specs = scenes.batch_scenes(args.scenes, 4000 if args.seed is None else args.seed, frames=F)
     scs = [scenes.make_scene(p, s) for p, s in specs]
     cfgs = [batch_cfg(p, sc) for (p, _), sc in zip(specs, scs)]
-    Z = [[torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, 2), device=dev)
-          for fr in sc.frames] for sc in scs]
+    on_dev = args.batch_detections == "device"
+    if on_dev:
+        Z = [[torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, 2), device=dev)
+              for fr in sc.frames] for sc in scs]
+    else:
+        Z = [[fr.Z for fr in sc.frames] for sc in scs]
     B = [[glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames] for sc in scs]
     torch.cuda.synchronize()
 
@@ -186,10 +190,10 @@ def run_batch(args, glmb, torch, dev):
         for k in range(F):
             t0 = time.perf_counter()
             if batched:
-                glmb.step_batch(filters, [(B[i][k], Z[i][k]) for i in range(len(filters))], device=True)
+                glmb.step_batch(filters, [(B[i][k], Z[i][k]) for i in range(len(filters))], device=on_dev)
             else:
                 for i, f in enumerate(filters):
-                    f.step(B[i][k], Z[i][k], device=True)
+                    f.step(B[i][k], Z[i][k], device=on_dev)
             for f in filters:
                 f.estimates(cap=f.cfg["max_tracks"], pmf_cap=64)
             t += time.perf_counter() - t0
@@ -214,6 +218,7 @@ def run_batch(args, glmb, torch, dev):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.scenes} scenes x {F} frames, N~U{{5..300}}, H~U{{100..5000}}, "
                                    "clutter~U(5,40), 2-D CV",
+                       "detections": args.batch_detections,
                        "h_max": [p.h_max for p, _ in specs], "n_objects": [p.n_objects for p, _ in specs]},
             "sequential": out["sequential"], "batched": out["batched"],
             "speedup_vs_sequential": out["batched"]["scene_frames_per_s"] / out["sequential"]["scene_frames_per_s"]}
@@ -591,6 +596,8 @@ def main():
     ap.add_argument("--cpu-threads", type=int, default=0,
                     help="host threads of the oracle leg (0: all cores)")
     ap.add_argument("--stages", action="store_true", help="also report per-stage times")
+    ap.add_argument("--batch-detections", default="device", choices=["device", "host"],
+                    help="--scene batch: detections resident in device memory or copied from the host")
     ap.add_argument("--scenes", type=int, default=64,
                     help="--scene batch: independent scenes per frame")
     ap.add_argument("--convoy-n", default="1,2,5,10,20", help="--scene convoy: object counts")
