@@ -159,6 +159,14 @@ def run_oracle(args, sc, cfg, budget_s):
         f"from the initial GLMB ({dt:.1f} s, {threads} threads)"
 
 
+def workload_config(args, sc, cfg) -> dict:
+    """The workload of the default run, named the same in both arms."""
+    F = len(sc.frames)
+    return {"workload": f"{args.scene} scene: 2-D CV, {sc.params.n_objects} objects, "
+                        f"{F} frames, H_max={cfg['h_max']}, H_up={cfg['h_up']}",
+            "scene": args.scene, "h_max": cfg["h_max"], "h_up": cfg["h_up"], "frames_per_scene": F}
+
+
 def batch_cfg(p, sc):
     return sc.filter_config(max_meas=int(p.n_objects * 0.9 * 6 + 4 * p.clutter_rate + 64),
                             max_births=64, max_tracks=p.n_objects + 48,
@@ -638,7 +646,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": f"{args.scene} scene", "scene": args.scene},
+                "data": "synthetic", "config": workload_config(args, sc, cfg),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -795,10 +803,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.scene} scene: 2-D CV, {sc.params.n_objects} objects, "
-                               f"{F} frames, H_max={cfg['h_max']}, H_up={h_up}",
-                   "scene": args.scene, "h_max": cfg["h_max"], "h_up": h_up,
-                   "frames_per_scene": F, "l2": "flushed between steps (256 MiB write, outside "
+        "config": {**workload_config(args, sc, cfg),
+                   "l2": "flushed between steps (256 MiB write, outside "
                    "the timed events)" if not args.no_flush else "not flushed",
                    "inputs": "detections resident in device memory; births (<1 KB) copied in predict",
                    "graph_precapture_frames": precapture},
