@@ -110,14 +110,18 @@ struct glmb_handle {
   uint32_t* gc_newpos = nullptr;
   // frame results, one device block copied back in one piece:
   // [scalars (S_N)][prune counters (8)][estimates], mirrored in pinned host
-  // memory up to the estimates' r array
+  // memory up to the end of the estimate records
   unsigned* d_scal = nullptr;
   unsigned* h_scal = nullptr;
   size_t res_off_cnt = 0, res_off_est = 0;
-  // estimates: [nb (16 B)][pmf][tracks][r][done], mirrored on the host up to r
+  // estimates: [nb (16 B)][pmf][tracks][done], mirrored on the host up to
+  // est_off_end (the start of done); `done` holds the component bound of the
+  // existence sums and est_rcomp their per-component sums (both left zeroed
+  // by the kernels)
   unsigned char* d_est = nullptr;
+  unsigned long long* est_rcomp = nullptr;
   unsigned char* h_est = nullptr;
-  size_t est_off_pmf = 0, est_off_tr = 0, est_off_r = 0, est_off_done = 0;
+  size_t est_off_pmf = 0, est_off_tr = 0, est_off_end = 0, est_off_done = 0;
   // state generation (bumped by every change of the filter state) and the
   // generation whose estimates h_est holds; glmb_step computes them in its
   // graph unless step_estimates is off
@@ -276,13 +280,13 @@ bool alloc_io(glmb_handle* h) {
   const size_t pcap = (size_t)h->max_tracks + 1;
   h->est_off_pmf = 16;
   h->est_off_tr = h->est_off_pmf + 8 * pcap;
-  h->est_off_r = h->est_off_tr + sizeof(glmb_track) * pcap;
-  h->est_off_done = h->est_off_r + 8 * pcap;
+  h->est_off_end = h->est_off_tr + sizeof(glmb_track) * pcap;
+  h->est_off_done = h->est_off_end;
   h->res_off_cnt = round_up64(S_N * sizeof(unsigned));
   h->res_off_est = h->res_off_cnt + 64;
   unsigned char *dres = nullptr, *hres = nullptr;
   if (!dalloc(h, &dres, (long long)(h->res_off_est + h->est_off_done + 16)) ||
-      !halloc(h, &hres, (long long)(h->res_off_est + h->est_off_r)))
+      !halloc(h, &hres, (long long)(h->res_off_est + h->est_off_end)))
     return false;
   h->d_scal = reinterpret_cast<unsigned*>(dres);
   h->pw.counts = reinterpret_cast<unsigned*>(dres + h->res_off_cnt);
@@ -565,7 +569,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   const long long scan_n = std::max(h->cap_comp, h->cap_children);
   bool ok = alloc_comps(h, h->comps[0], h->cap_comp, dx) && alloc_comps(h, h->comps[1], h->cap_comp, dx) &&
             alloc_hyps(h, h->hyps[0]) && alloc_hyps(h, h->hyps[1]) &&
-            alloc_io(h) &&
+            alloc_io(h) && dalloc(h, &h->est_rcomp, h->cap_comp) &&
             dalloc(h, &h->pt.cnt, h->cap_comp + 1) && dalloc(h, &h->pt.ptr, h->cap_comp + 1) &&
             dalloc(h, &h->pt.meas, h->cap_pairs) && dalloc(h, &h->pt.logC, h->cap_pairs) &&
             dalloc(h, &h->pt.q, h->cap_pairs) && dalloc(h, &h->pt.e, h->cap_pairs * dz) &&
@@ -953,7 +957,7 @@ glmb_status exact_maxima(glmb_handle* h, unsigned& max_T, unsigned& max_K) {
 // host memory, on the stream
 glmb_status enqueue_results(glmb_handle* h, bool with_est) {
   // scalars and counters (and the estimates) in one copy of the result block
-  const size_t bytes = with_est ? h->res_off_est + h->est_off_r : h->res_off_cnt + 8 * sizeof(unsigned);
+  const size_t bytes = with_est ? h->res_off_est + h->est_off_end : h->res_off_cnt + 8 * sizeof(unsigned);
   CU(cudaMemcpyAsync(h->h_scal, h->d_scal, bytes, cudaMemcpyDeviceToHost, h->stream));
   return GLMB_OK;
 }
@@ -964,9 +968,8 @@ void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, co
   const int pcap = h->max_tracks + 1;
   prof_begin(h, kStageEstimates);
   launch_estimates(Y, H, H_dev, A, h->md.dx, (double*)(h->d_est + h->est_off_pmf), pcap, (int*)h->d_est,
-                   (double*)(h->d_est + h->est_off_r), h->d_est + h->est_off_tr,
-                   (unsigned*)(h->d_est + h->est_off_done), h->n_sm, H_dev ? h->d_scal + S_ERR : nullptr,
-                   h->stream);
+                   h->est_rcomp, h->d_est + h->est_off_tr, (unsigned*)(h->d_est + h->est_off_done), h->n_sm,
+                   H_dev ? h->d_scal + S_ERR : nullptr, h->stream);
   prof_end(h, kStageEstimates);
 }
 
@@ -1363,7 +1366,7 @@ glmb_status glmb_estimates(glmb_handle* h, glmb_track* out, int cap, int* n_out,
   if (h->est_gen != h->gen) {   // not computed with this state's step
     enqueue_estimates(h, h->hyps[h->hcur], h->comps[h->cur], nullptr, h->H);
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_r, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h->h_est, h->d_est, h->est_off_end, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     h->est_gen = h->gen;
   }

@@ -209,13 +209,13 @@ void launch_gate_usage(const HypTable& par, const HypTable& out, const CompTable
                        const float* logit, float thr, uint8_t* used, uint8_t* hflag, int capT, int grid,
                        cudaStream_t s);
 
-// estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, r[pcap] (existence
-// sums, zeroed by the first kernel), tracks = glmb_track[pcap]; done is a
-// zeroed counter (left zeroed); H_dev (nullable) gives H on the device;
+// estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, tracks =
+// glmb_track[pcap]; r_comp[ct.cap] (per-component weight sums) and cmax are
+// zeroed work areas, left zeroed; H_dev (nullable) gives H on the device;
 // err (nullable): the frame's error flags, on which the kernels do nothing
 void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
-                      double* pmf, int pcap, int* nb, double* r, void* tracks, unsigned* done, int n_sm,
-                      const unsigned* err, cudaStream_t s);
+                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, void* tracks, unsigned* cmax,
+                      int n_sm, const unsigned* err, cudaStream_t s);
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s);
 
 }  // namespace glmb

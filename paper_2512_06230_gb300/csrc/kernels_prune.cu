@@ -659,13 +659,9 @@ __device__ __forceinline__ unsigned long long w_fx(double logw) {
 }
 
 // Cardinality distribution, MAP cardinality (ties to the smaller n) and the
-// heaviest hypothesis of that cardinality (ties to the lower index); one
-// block.  nb[0] = n_hat, nb[1] = MAP hypothesis.
-__global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap,
-                                int* nb, unsigned long long* r_fx, const unsigned* err) {
-  pdl_enter();
-  // a frame that failed left the new table incomplete: nothing to read
-  if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
+// heaviest hypothesis of that cardinality (ties to the lower index), by one
+// block: nb[0] = n_hat, nb[1] = MAP hypothesis.
+__device__ __forceinline__ void est_card_block(const HypTable& hp, const int H, double* pmf, int pcap, int* nb) {
   extern __shared__ unsigned long long s_pmf[];   // [pcap]
   __shared__ unsigned long long bw[32];
   __shared__ int bi[32];
@@ -674,11 +670,7 @@ __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
   __shared__ int s_nhat;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5;
   const int nw = (nthr + 31) >> 5;
-  const int H = H_dev ? (int)*H_dev : H_host;
-  for (int n = tid; n < pcap; n += nthr) {
-    s_pmf[n] = 0ull;
-    r_fx[n] = 0ull;   // existence sums of the next kernel
-  }
+  for (int n = tid; n < pcap; n += nthr) s_pmf[n] = 0ull;
   __syncthreads();
   // one shared-memory atomic per distinct cardinality in a warp (most
   // hypotheses share a few cardinalities)
@@ -749,62 +741,85 @@ __global__ void est_card_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
   }
 }
 
-// r[j] = total weight of hypotheses holding the label of MAP track j (one
-// warp per hypothesis; the MAP track list, in label order, is binary searched
-// in shared memory and the weights summed per block there, then once per
-// block into r_fx); the last block writes the MAP tracks as glmb_track
-// records (mean hi + lo in FP64, full covariance).
-__global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev, CompTable ct, int dx,
-                                 const int* __restrict__ nb, unsigned long long* r_fx, glmb_track* out,
-                                 int cap, unsigned* done, const unsigned* err) {
+// Existence of the MAP tracks, first half, beside the cardinality block:
+// every hypothesis adds its weight onto each of its components,
+// r_comp[c] += w_h (one warp per hypothesis), and cmax records one past the
+// largest component index met.  A label occurs at most once in a
+// hypothesis, so the sum over the components of one label is the total
+// weight of the hypotheses that hold it (the existence of Section 3's
+// labelled tracks), reached without waiting for the MAP hypothesis.
+__global__ void est_sums_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap, int* nb,
+                                unsigned long long* r_comp, int ccap, unsigned* cmax, const unsigned* err) {
+  pdl_enter();
+  // a frame that failed left the new table incomplete: nothing to read
+  if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
+  const int H = H_dev ? (int)*H_dev : H_host;
+  if (blockIdx.x == 0) {
+    est_card_block(hp, H, pmf, pcap, nb);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  unsigned top = 0u;
+  for (int h = (blockIdx.x - 1) * wpb + (threadIdx.x >> 5); h < H; h += (gridDim.x - 1) * wpb) {
+    const uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
+    const unsigned long long wgt = w_fx(hp.logw[h]);
+    for (uint32_t e = lo + lane; e < hi; e += 32) {
+      const uint32_t c = min(hp.comp[e], (uint32_t)ccap - 1u);
+      if (wgt) atomicAdd(&r_comp[c], wgt);
+      top = max(top, c + 1u);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xFFFFFFFFu, top, o));
+  if (lane == 0 && top) atomicMax(cmax, top);
+}
+
+// Existence of the MAP tracks, second half (one block): the labels of the
+// MAP hypothesis (in label order) go to shared memory; every component
+// with a nonzero sum adds it to its label's entry (binary search), and its
+// sum is cleared, so r_comp and cmax are left zeroed; then the MAP tracks
+// are written as glmb_track records (mean hi + lo in FP64, full
+// covariance).
+__global__ void est_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* __restrict__ nb,
+                                  unsigned long long* r_comp, unsigned* cmax, glmb_track* out, int cap,
+                                  const unsigned* err) {
   pdl_enter();
   if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
   extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
   unsigned long long* s_r = s_key + cap;
-  __shared__ bool last;
-  const int H = H_dev ? (int)*H_dev : H_host;
   const int best = nb[1];
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
   const uint32_t b0 = best >= 0 ? hp.ptr[best] : 0u;
   const int nmap = best >= 0 ? min((int)(hp.ptr[best + 1] - b0), cap) : 0;
   const uint32_t ccap = (uint32_t)ct.cap;
+  const uint32_t nc = min(*(volatile unsigned*)cmax, ccap);
   for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
     const uint32_t cm = min(hp.comp[b0 + j], ccap - 1u);
     s_key[j] = ((unsigned long long)ct.lk[cm] << 32) | ct.lb[cm];
     s_r[j] = 0ull;
   }
   __syncthreads();
-  for (int h = blockIdx.x * wpb + (threadIdx.x >> 5); h < H && nmap > 0; h += gridDim.x * wpb) {
-    const uint32_t lo = hp.ptr[h], hi = hp.ptr[h + 1];
-    const unsigned long long wgt = w_fx(hp.logw[h]);
-    for (uint32_t e = lo + lane; e < hi; e += 32) {
-      const uint32_t c = min(hp.comp[e], ccap - 1u);
-      const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
-      int l = 0, u = nmap;
-      while (l < u) {
-        const int mid = (l + u) >> 1;
-        if (s_key[mid] < key) l = mid + 1; else u = mid;
-      }
-      if (l < nmap && s_key[l] == key) atomicAdd(&s_r[l], wgt);
+  for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+    const unsigned long long v = r_comp[c];
+    if (!v) continue;
+    r_comp[c] = 0ull;
+    const unsigned long long key = ((unsigned long long)ct.lk[c] << 32) | ct.lb[c];
+    int l = 0, u = nmap;
+    while (l < u) {
+      const int mid = (l + u) >> 1;
+      if (s_key[mid] < key) l = mid + 1; else u = mid;
     }
+    if (l < nmap && s_key[l] == key) atomicAdd(&s_r[l], v);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < nmap; j += blockDim.x)
-    if (s_r[j]) atomicAdd(&r_fx[j], s_r[j]);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
+  if (threadIdx.x == 0) *cmax = 0u;
   const size_t cc = ct.cap;
   for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
     const uint32_t c = min(hp.comp[b0 + j], ccap - 1u);
     glmb_track& t = out[j];
     t.label_k = ct.lk[c];
     t.label_b = ct.lb[c];
-    t.r = (double)((volatile unsigned long long*)r_fx)[j] * kWfxInv;
+    t.r = (double)s_r[j] * kWfxInv;
     for (int a = 0; a < 6; ++a)
       t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
     for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
@@ -815,21 +830,23 @@ __global__ void est_exist_kernel(HypTable hp, int H_host, const unsigned* H_dev,
         t.cov[k * dx + i] = v;
       }
   }
-  if (threadIdx.x == 0) *done = 0u;
 }
 
 void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
-                      double* pmf, int pcap, int* nb, double* r, void* tracks, unsigned* done, int n_sm,
-                      const unsigned* err, cudaStream_t s) {
-  if (pcap * 16 > 48 * 1024) {
-    cudaFuncSetAttribute(est_card_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
-    cudaFuncSetAttribute(est_exist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
+                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, void* tracks, unsigned* cmax,
+                      int n_sm, const unsigned* err, cudaStream_t s) {
+  static int attr_pcap = 0;   // the limits only grow (graphs of larger filters stay valid)
+  if (pcap * 16 > 48 * 1024 && pcap > attr_pcap) {
+    cudaFuncSetAttribute(est_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
+    cudaFuncSetAttribute(est_tracks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
+    attr_pcap = pcap;
   }
-  unsigned long long* r_fx = reinterpret_cast<unsigned long long*>(r);
-  launch_k(est_card_kernel, 1, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_fx, err);
-  const int blocks = H_dev ? 2 * n_sm : std::max(1, std::min((H + 7) / 8, 2 * n_sm));
-  launch_k(est_exist_kernel, blocks, 256, (size_t)pcap * 16, s, hp, H, H_dev, ct, dx, nb, r_fx, (glmb_track*)tracks,
-                                                         pcap, done, err);
+  // block 0: the cardinality; blocks 1..: one warp per hypothesis
+  const int sum_blocks = H_dev ? n_sm : std::max(1, std::min((H + 31) / 32, n_sm));
+  launch_k(est_sums_kernel, 1 + sum_blocks, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_comp,
+           ct.cap, cmax, err);
+  launch_k(est_tracks_kernel, 1, 1024, (size_t)pcap * 16, s, hp, ct, dx, nb, r_comp, cmax, (glmb_track*)tracks,
+           pcap, err);
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
