@@ -895,11 +895,9 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
            h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR, s);
   const int ggc = p.fixed ? 4 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
-  launch_gc_copy_update(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP,
-                        h->upd_src, h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD,
-                        h->pw.counts, h->d_scal + S_ERR, ggc, s);
-  launch_remap(O.comp, h->pw.counts + 1, h->cap_entries, h->gc_newpos, h->hvals,
-               h->d_scal + S_NKEEP, h->d_scal + S_ERR, h->hmask, h->d_fs, s);
+  launch_gc_remap(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP, h->upd_src, h->upd_m,
+                  h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts, h->d_scal + S_ERR, O.comp,
+                  h->pw.counts + 1, h->cap_entries, h->hvals, h->hmask, ggc, s);
   prof_end(h, kStageGc);
   CU(cudaGetLastError());
   return GLMB_OK;

@@ -159,15 +159,16 @@ int select_cluster_size();
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,
                      const HypTable& parents, int h_up, HypTable out, int h_max,
                      unsigned* err, long long cap_entries, cudaStream_t s);
-void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
-                           const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
-                           const unsigned* n_keep_dev, const uint32_t* upd_src,
-                           const uint32_t* upd_m, const long long* upd_se, int cap_upd,
-                           const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
-                           int grid, cudaStream_t s);
-void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
-                  const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
-                  const unsigned* err, uint32_t hmask, const FrameDev* fs, cudaStream_t s);
+// components of the new state into dst: every flagged old component c
+// copied to newpos[c], then the distinct track updates (Kalman) after the
+// n_keep kept ones; in the same launch the new hypothesis table's component
+// indices out_comp[0 .. *n_entries_dev) are remapped, an old component c
+// to newpos[c] and a new one (kNewTag | hash slot) to n_keep + hvals[slot]
+void launch_gc_remap(const Model& md, const CompTable& src, const CompTable& dst, const uint32_t* newpos,
+                     const uint32_t* flag, const FrameDev* fs, const unsigned* n_keep_dev, const uint32_t* upd_src,
+                     const uint32_t* upd_m, const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
+                     const unsigned* n_surv_dev, unsigned* err, uint32_t* out_comp, const unsigned* n_entries_dev,
+                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, int grid, cudaStream_t s);
 // device error flags that abandon a frame (state left untouched)
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
                                kErrEntries | kErrSlots | kErrInput | kErrGate | kErrTimeout | kErrChkSurv |

@@ -404,7 +404,8 @@ void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_a
 
 // ---------------------------------------------------------------------------
 // Garbage collection of components and the batched track update (Kalman
-// with the mean detection and R/m, Joseph form).
+// with the mean detection and R/m, Joseph form), in one launch with the
+// remapping of the new hypothesis table's component indices.
 // ---------------------------------------------------------------------------
 
 template <int DZ>
@@ -564,12 +565,14 @@ __device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
 }
 
 template <int DZ>
-__global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
-                          const uint32_t* __restrict__ flag, const FrameDev* __restrict__ fs,
-                          const unsigned* __restrict__ n_keep_dev, const uint32_t* __restrict__ upd_src,
-                          const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,
-                          int cap_upd, const unsigned* __restrict__ n_upd_dev,
-                          const unsigned* __restrict__ n_surv_dev, unsigned* err) {
+__global__ void gc_remap_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
+                                const uint32_t* __restrict__ flag, const FrameDev* __restrict__ fs,
+                                const unsigned* __restrict__ n_keep_dev, const uint32_t* __restrict__ upd_src,
+                                const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,
+                                int cap_upd, const unsigned* __restrict__ n_upd_dev,
+                                const unsigned* __restrict__ n_surv_dev, unsigned* err, uint32_t* out_comp,
+                                const unsigned* __restrict__ n_entries, long long cap_entries,
+                                const uint32_t* __restrict__ hvals, uint32_t hmask) {
   pdl_enter();
   if (*n_surv_dev == 0u || (*(volatile unsigned*)err & kErrFatal)) return;
   const int n_src = fs->T;
@@ -601,48 +604,33 @@ __global__ void gc_kernel(Model md, CompTable src, CompTable dst, const uint32_t
         atomicOr(err, kErrNumeric);
     }
   }
-}
-
-void launch_gc_copy_update(const Model& md, const CompTable& src, const CompTable& dst,
-                           const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
-                           const unsigned* n_keep_dev, const uint32_t* upd_src,
-                           const uint32_t* upd_m, const long long* upd_se, int cap_upd,
-                           const unsigned* n_upd_dev, const unsigned* n_surv_dev, unsigned* err,
-                           int grid, cudaStream_t s) {
-  if (md.dz == 2) {
-    launch_k(gc_kernel<2>, grid, 128, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
-                                      upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
-  } else {
-    launch_k(gc_kernel<3>, grid, 128, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
-                                      upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
-  }
-}
-
-__global__ void remap_kernel(uint32_t* out_comp, const unsigned* __restrict__ n_entries,
-                             long long cap, const uint32_t* __restrict__ newpos,
-                             const uint32_t* __restrict__ hvals,
-                             const unsigned* __restrict__ n_keep_dev, const unsigned* err, uint32_t hmask,
-                             const FrameDev* __restrict__ fs) {
-  pdl_enter();
-  if (*(volatile const unsigned*)err & kErrFatal) return;
-  const long long n = min((long long)*n_entries, cap);
-  const uint32_t n_keep = *n_keep_dev, n_src = (uint32_t)fs->T;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+  // the new hypothesis table's component indices: an old component to its
+  // compacted position, a new one (tagged hash slot) to its update's
+  // position after the kept components (independent of the copies above)
+  const long long n_e = min((long long)*n_entries, cap_entries);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_e;
        e += (long long)gridDim.x * blockDim.x) {
     const uint32_t v = out_comp[e];
-    if ((v & kNewTag) ? (v & ~kNewTag) > hmask : v >= n_src) {
-      atomicOr((unsigned*)err, kErrChkRemap);
+    if ((v & kNewTag) ? (v & ~kNewTag) > hmask : v >= (uint32_t)n_src) {
+      atomicOr(err, kErrChkRemap);
       continue;
     }
     out_comp[e] = (v & kNewTag) ? n_keep + hvals[v & ~kNewTag] : newpos[v];
   }
 }
 
-void launch_remap(uint32_t* out_comp, const unsigned* n_entries_dev, long long cap,
-                  const uint32_t* newpos, const uint32_t* hvals, const unsigned* n_keep_dev,
-                  const unsigned* err, uint32_t hmask, const FrameDev* fs, cudaStream_t s) {
-  const int nb = (int)max(1LL, min((cap + 255) / 256, 2048LL));
-  launch_k(remap_kernel, nb, 256, 0, s, out_comp, n_entries_dev, cap, newpos, hvals, n_keep_dev, err, hmask, fs);
+void launch_gc_remap(const Model& md, const CompTable& src, const CompTable& dst, const uint32_t* newpos,
+                     const uint32_t* flag, const FrameDev* fs, const unsigned* n_keep_dev, const uint32_t* upd_src,
+                     const uint32_t* upd_m, const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
+                     const unsigned* n_surv_dev, unsigned* err, uint32_t* out_comp, const unsigned* n_entries_dev,
+                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, int grid, cudaStream_t s) {
+  if (md.dz == 2) {
+    launch_k(gc_remap_kernel<2>, grid, 256, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask);
+  } else {
+    launch_k(gc_remap_kernel<3>, grid, 256, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
+             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask);
+  }
 }
 
 // ---------------------------------------------------------------------------
