@@ -115,9 +115,9 @@ struct glmb_handle {
   unsigned* h_scal = nullptr;
   size_t res_off_cnt = 0, res_off_est = 0;
   // estimates: [nb (16 B)][pmf][tracks][done], mirrored on the host up to
-  // est_off_end (the start of done); `done` holds the component bound of the
-  // existence sums and est_rcomp their per-component sums (both left zeroed
-  // by the kernels)
+  // est_off_end (the start of done); `done` holds the component bound and
+  // the block counter of the existence sums, est_rcomp their per-component
+  // sums followed by the per-track sums (all left zeroed by the kernels)
   unsigned char* d_est = nullptr;
   unsigned long long* est_rcomp = nullptr;
   unsigned char* h_est = nullptr;
@@ -569,7 +569,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   const long long scan_n = std::max(h->cap_comp, h->cap_children);
   bool ok = alloc_comps(h, h->comps[0], h->cap_comp, dx) && alloc_comps(h, h->comps[1], h->cap_comp, dx) &&
             alloc_hyps(h, h->hyps[0]) && alloc_hyps(h, h->hyps[1]) &&
-            alloc_io(h) && dalloc(h, &h->est_rcomp, h->cap_comp) &&
+            alloc_io(h) && dalloc(h, &h->est_rcomp, h->cap_comp + h->max_tracks + 1) &&
             dalloc(h, &h->pt.cnt, h->cap_comp + 1) && dalloc(h, &h->pt.ptr, h->cap_comp + 1) &&
             dalloc(h, &h->pt.meas, h->cap_pairs) && dalloc(h, &h->pt.logC, h->cap_pairs) &&
             dalloc(h, &h->pt.q, h->cap_pairs) && dalloc(h, &h->pt.e, h->cap_pairs * dz) &&
@@ -965,9 +965,10 @@ glmb_status enqueue_results(glmb_handle* h, bool with_est) {
 void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, const unsigned* H_dev, int H) {
   const int pcap = h->max_tracks + 1;
   prof_begin(h, kStageEstimates);
-  launch_estimates(Y, H, H_dev, A, h->md.dx, (double*)(h->d_est + h->est_off_pmf), pcap, (int*)h->d_est,
-                   h->est_rcomp, h->d_est + h->est_off_tr, (unsigned*)(h->d_est + h->est_off_done), h->n_sm,
-                   H_dev ? h->d_scal + S_ERR : nullptr, h->stream);
+  unsigned* work = reinterpret_cast<unsigned*>(h->d_est + h->est_off_done);   // [cmax, done]
+  launch_estimates(Y, H, H_dev, H_dev ? h->cap_h : H, A, h->md.dx, (double*)(h->d_est + h->est_off_pmf), pcap,
+                   (int*)h->d_est, h->est_rcomp, h->est_rcomp + h->cap_comp, h->d_est + h->est_off_tr, work,
+                   work + 1, h->n_sm, H_dev ? h->d_scal + S_ERR : nullptr, h->stream);
   prof_end(h, kStageEstimates);
 }
 

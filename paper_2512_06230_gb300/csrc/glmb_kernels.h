@@ -211,12 +211,14 @@ void launch_gate_usage(const HypTable& par, const HypTable& out, const CompTable
                        cudaStream_t s);
 
 // estimates: pmf[pcap], nb = {n_hat, MAP hypothesis}, tracks =
-// glmb_track[pcap]; r_comp[ct.cap] (per-component weight sums) and cmax are
-// zeroed work areas, left zeroed; H_dev (nullable) gives H on the device;
-// err (nullable): the frame's error flags, on which the kernels do nothing
-void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
-                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, void* tracks, unsigned* cmax,
-                      int n_sm, const unsigned* err, cudaStream_t s);
+// glmb_track[pcap]; r_comp[ct.cap] (per-component weight sums), r_map[pcap]
+// (per-track sums), cmax and done are zeroed work areas, left zeroed;
+// H_dev (nullable) gives H on the device, H_bound an upper bound of H (the
+// launch shape follows it); err (nullable): the frame's error flags, on
+// which the kernels do nothing
+void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, int H_bound, const CompTable& ct, int dx,
+                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, unsigned long long* r_map,
+                      void* tracks, unsigned* cmax, unsigned* done, int n_sm, const unsigned* err, cudaStream_t s);
 void launch_meas_assoc(const HypTable& hp, int H, int M, double* r_u, cudaStream_t s);
 
 }  // namespace glmb

@@ -763,19 +763,22 @@ __global__ void est_sums_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
   if (lane == 0 && top) atomicMax(cmax, top);
 }
 
-// Existence of the MAP tracks, second half (one block): the labels of the
-// MAP hypothesis (in label order) go to shared memory; every component
-// with a nonzero sum adds it to its label's entry (binary search), and its
-// sum is cleared, so r_comp and cmax are left zeroed; then the MAP tracks
-// are written as glmb_track records (mean hi + lo in FP64, full
-// covariance).
+// Existence of the MAP tracks, second half: the labels of the MAP
+// hypothesis (in label order) go to each block's shared memory; every
+// component with a nonzero sum adds it to its label's entry (binary search)
+// and its sum is cleared, so r_comp is left zeroed.  One block writes the
+// MAP tracks (glmb_track records: mean hi + lo in FP64, full covariance)
+// from its own sums; with several blocks (large tables) each adds its sums
+// into r_map once and the last block to finish writes the tracks.  cmax,
+// done and r_map are left zeroed.
 __global__ void est_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* __restrict__ nb,
-                                  unsigned long long* r_comp, unsigned* cmax, glmb_track* out, int cap,
-                                  const unsigned* err) {
+                                  unsigned long long* r_comp, unsigned* cmax, unsigned* done,
+                                  unsigned long long* r_map, glmb_track* out, int cap, const unsigned* err) {
   pdl_enter();
   if (err && (*(volatile const unsigned*)err & kErrFatal)) return;
   extern __shared__ unsigned long long s_key[];   // [cap] MAP labels, then [cap] sums
   unsigned long long* s_r = s_key + cap;
+  __shared__ bool last;
   const int best = nb[1];
   const uint32_t b0 = best >= 0 ? hp.ptr[best] : 0u;
   const int nmap = best >= 0 ? min((int)(hp.ptr[best + 1] - b0), cap) : 0;
@@ -787,7 +790,7 @@ __global__ void est_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* 
     s_r[j] = 0ull;
   }
   __syncthreads();
-  for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     const unsigned long long v = r_comp[c];
     if (!v) continue;
     r_comp[c] = 0ull;
@@ -800,14 +803,34 @@ __global__ void est_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* 
     if (l < nmap && s_key[l] == key) atomicAdd(&s_r[l], v);
   }
   __syncthreads();
-  if (threadIdx.x == 0) *cmax = 0u;
+  const bool multi = gridDim.x > 1;
+  if (multi) {
+    for (int j = threadIdx.x; j < nmap; j += blockDim.x)
+      if (s_r[j]) atomicAdd(&r_map[j], s_r[j]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+  }
+  if (threadIdx.x == 0) {
+    // every block has read cmax by now (the last block, or the only one)
+    *cmax = 0u;
+    if (multi) *done = 0u;
+  }
   const size_t cc = ct.cap;
   for (int j = threadIdx.x; j < nmap; j += blockDim.x) {
+    unsigned long long rs = s_r[j];
+    if (multi) {
+      rs = ((volatile unsigned long long*)r_map)[j];
+      r_map[j] = 0ull;
+    }
     const uint32_t c = min(hp.comp[b0 + j], ccap - 1u);
     glmb_track& t = out[j];
     t.label_k = ct.lk[c];
     t.label_b = ct.lb[c];
-    t.r = (double)s_r[j] * kWfxInv;
+    t.r = (double)rs * kWfxInv;
     for (int a = 0; a < 6; ++a)
       t.mean[a] = a < dx ? (double)ct.mhi[a * cc + c] + (double)ct.mlo[a * cc + c] : 0.0;
     for (int k = 0; k < 36; ++k) t.cov[k] = 0.0;
@@ -820,9 +843,9 @@ __global__ void est_tracks_kernel(HypTable hp, CompTable ct, int dx, const int* 
   }
 }
 
-void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const CompTable& ct, int dx,
-                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, void* tracks, unsigned* cmax,
-                      int n_sm, const unsigned* err, cudaStream_t s) {
+void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, int H_bound, const CompTable& ct, int dx,
+                      double* pmf, int pcap, int* nb, unsigned long long* r_comp, unsigned long long* r_map,
+                      void* tracks, unsigned* cmax, unsigned* done, int n_sm, const unsigned* err, cudaStream_t s) {
   static int attr_pcap = 0;   // the limits only grow (graphs of larger filters stay valid)
   if (pcap * 16 > 48 * 1024 && pcap > attr_pcap) {
     cudaFuncSetAttribute(est_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
@@ -833,8 +856,11 @@ void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, const Co
   const int sum_blocks = H_dev ? n_sm : std::max(1, std::min((H + 31) / 32, n_sm));
   launch_k(est_sums_kernel, 1 + sum_blocks, 1024, (size_t)pcap * 8, s, hp, H, H_dev, pmf, pcap, nb, r_comp,
            ct.cap, cmax, err);
-  launch_k(est_tracks_kernel, 1, 1024, (size_t)pcap * 16, s, hp, ct, dx, nb, r_comp, cmax, (glmb_track*)tracks,
-           pcap, err);
+  // the components in use grow with the hypotheses: one block while the
+  // table holds at most 4096 hypotheses, else two blocks per SM
+  const int track_blocks = H_bound <= 4096 ? 1 : 2 * n_sm;
+  launch_k(est_tracks_kernel, track_blocks, 1024, (size_t)pcap * 16, s, hp, ct, dx, nb, r_comp, cmax, done, r_map,
+           (glmb_track*)tracks, pcap, err);
 }
 
 __global__ void meas_assoc_kernel(HypTable hp, int H, int M, double* r_u) {
