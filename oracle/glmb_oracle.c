@@ -62,11 +62,11 @@
  * R2 is pinned where the model reduces to the single-detection Bernoulli
  * filter (one track, lambda_d = 0): the death probability equals the exact
  * marginal over every enumerated child.  R9's sums (cardinality pmf, label
- * existence) are pinned against the brute-force posterior.  Parity
- * unpinned: R9's choice of the MAP cardinality, then the heaviest
- * hypothesis of that cardinality, is a reading with nothing in the paper to
- * check it against.  Everything else is pinned by closed forms, brute force
- * and independent restatements (tests/test_oracle_pins.py).
+ * existence) and its choice (the MAP cardinality, then the heaviest
+ * hypothesis of that cardinality) are pinned against the brute-force
+ * posterior; the choice rule itself is a reading, which the paper does not
+ * state.  Everything else is pinned by closed forms, brute force and
+ * independent restatements (tests/test_oracle_pins.py).
  */
 #include "glmb_oracle.h"
 

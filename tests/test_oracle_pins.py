@@ -547,6 +547,38 @@ def test_death_probability_is_the_exact_marginal_of_a_single_track(oracle_mod, s
     assert o.slot(0, 0)["dprob"] == pytest.approx(p_dead, rel=1e-10, abs=1e-14)
 
 
+def test_estimate_choice_rule_against_the_exact_posterior(oracle_mod):
+    """The estimator's choice (reading R9: the most probable cardinality,
+    then the heaviest hypothesis of that cardinality) computed from the
+    brute-force posterior.  In this case the heaviest hypothesis overall has
+    a different cardinality, so taking it instead fails here."""
+    rng = np.random.default_rng(101)
+    o, cfg, Z, slots = _tiny(oracle_mod, rng, n_tracks=1, M=3, births=2, h_up=60000, h_max=100000,
+                             tau=1e-300)
+    dead, theta, lw = o.bruteforce(0)
+    finite = np.isfinite(lw)
+    dead, lw = dead[finite], lw[finite]
+    w = np.exp(lw - np.logaddexp.reduce(lw))
+    card = (dead == 0).sum(axis=1)
+    pmf = np.bincount(card, weights=w)
+    n_hat = int(np.argmax(pmf))
+    assert card[int(np.argmax(w))] != n_hat            # the case discriminates
+    cand = np.nonzero(card == n_hat)[0]
+    best = cand[int(np.argmax(w[cand]))]
+    labels = [o.slot(0, t)["label"] for t in range(o.parent_slots(0))]
+    want = sorted(labels[t] for t in range(len(labels)) if not dead[best, t])
+    # the draws miss only children of negligible weight (here ~0.3 % of the
+    # mass, against a 17 % margin between the two likeliest cardinalities)
+    ch = o.children()
+    got = ch["logw"][ch["status"] == 1]
+    assert np.exp(np.logaddexp.reduce(got) - np.logaddexp.reduce(lw)) > 0.99
+    assert np.sort(pmf)[-1] - np.sort(pmf)[-2] > 0.1
+    o.prune()
+    e = o.estimates()
+    assert e["n"] == n_hat
+    assert [tuple(l) for l in e["labels"]] == want
+
+
 def test_cardinality_and_existence_are_sums_over_the_exact_posterior(oracle_mod):
     """With every child of the parent retained (H_max above the association
     space, tau below every weight, H_up large enough to sample them all),
