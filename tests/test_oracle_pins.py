@@ -511,9 +511,10 @@ def test_sampler_frequencies_follow_the_proposal(oracle_mod):
 
 
 def test_death_probability_follows_reading(oracle_mod):
-    """Parity unpinned by the paper (Section 3 names d_prob without a
-    formula): this only checks the oracle against the stated reading
-    psi = (1-P_D) + sum_gated C/kappa, d = (1-p)/((1-p) + p psi)."""
+    """The oracle's d_prob against the formula of reading R2 (Section 3
+    names d_prob without giving one): psi = (1-P_D) + sum_gated C/kappa,
+    d = (1-p)/((1-p) + p psi).  The reading itself is pinned to the exact
+    posterior by test_death_probability_is_the_exact_marginal_of_a_single_track."""
     rng = np.random.default_rng(70)
     cfg, tracks, births, Z = _scenario(rng, M=5, births=2, gate=9.0)
     o, slots = _run(oracle_mod, cfg, tracks, births, Z)
