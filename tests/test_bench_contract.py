@@ -43,3 +43,19 @@ def test_reference_line_has_the_contract_keys():
 
 def test_reference_arm_prints_only_on_rank_0():
     assert _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"}) == []
+
+
+def test_clock_summary_reads_reasons_for_its_own_gpu():
+    """The clock record beside every number: median SM clock under load,
+    the maximum, and any throttle reason seen while the timed steps ran."""
+    import bench
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2010, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "1, 900, 2070, 300.0, 0x40, Active, Not Active, Active, Not Active",
+             "garbage line"]
+    c = bench.summarize_clocks(lines, 0)
+    assert c == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c1 = bench.summarize_clocks(lines, 1)
+    assert c1["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and c1["sm_mhz"] == 900.0
+    assert bench.summarize_clocks([], 0)["reasons"] == ["unavailable"]
