@@ -28,6 +28,11 @@
  *    inputs are copied before it returns); glmb_update waits once, for its
  *    expansion, to check the expansion's plan (see glmb_update); glmb_prune
  *    and every call that returns sizes or host data synchronise that stream.
+ *  - Host threads: the calls on one handle must not overlap.  The library
+ *    also keeps a few process-wide launch settings (kernel shared-memory
+ *    limits, the selection's cluster size), set on first use, so handles
+ *    are created and stepped from one host thread at a time (the batched
+ *    calls run many handles from one thread).
  *  - Call order per frame: glmb_predict -> glmb_update -> glmb_prune ->
  *    any number of glmb_estimates / glmb_meas_assoc / glmb_get_* calls.
  *    A call out of order returns GLMB_E_STATE and changes nothing.
