@@ -92,3 +92,24 @@ def test_ospa_closed_forms():
     # order 2 with one far pair: sqrt((d1^2 + c^2) / 2)
     b = np.array([[0.0, 4.0], [500.0, 0.0]])
     assert ospa(b, a, c=30.0, p=2) == pytest.approx(np.sqrt((16 + 900) / 2))
+
+
+def test_batch_workload_draws_the_stated_ranges():
+    """The batched workload: N ~ U{5..300}, H_max ~ U{100..5000}, clutter
+    ~ U(5, 40), every scene with its own seed, the same list for the same
+    seed."""
+    specs = scenes.batch_scenes(256, 4000, frames=100)
+    n = np.array([p.n_objects for p, _ in specs])
+    h = np.array([p.h_max for p, _ in specs])
+    lam = np.array([p.clutter_rate for p, _ in specs])
+    assert n.min() >= 5 and n.max() <= 300 and h.min() >= 100 and h.max() <= 5000
+    assert lam.min() >= 5.0 and lam.max() <= 40.0
+    # roughly uniform: each half of each range holds a fair share of 256
+    for v, lo, hi in ((n, 5, 300), (h, 100, 5000), (lam, 5.0, 40.0)):
+        assert 0.35 < np.mean(v < (lo + hi) / 2) < 0.65
+    assert len({s for _, s in specs}) == 256
+    assert [(p.n_objects, p.h_max, s) for p, s in scenes.batch_scenes(256, 4000)] == \
+        [(p.n_objects, p.h_max, s) for p, s in specs]
+    p0, s0 = specs[0]
+    sc = scenes.make_scene(p0, s0)
+    assert len(sc.frames) == 100 and sc.dim_z == 2
