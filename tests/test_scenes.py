@@ -113,3 +113,26 @@ def test_batch_workload_draws_the_stated_ranges():
     p0, s0 = specs[0]
     sc = scenes.make_scene(p0, s0)
     assert len(sc.frames) == 100 and sc.dim_z == 2
+
+
+def test_presets_follow_the_stated_recipes():
+    """Tiny, mid and the 3-D sweep scenes carry the parameters of the input
+    recipes, and a generated mid scene's detection counts match them:
+    alive objects x P_D x (1 + lambda_d) + clutter per frame."""
+    t, m = scenes.preset("tiny"), scenes.preset("mid")
+    assert (t.dim, t.n_objects, t.frames, t.extent, t.birth_window, t.lambda_d, t.clutter_rate, t.h_max) == \
+        (2, 10, 50, 1000.0, (0, 24), 1.0, 5.0, 100)
+    assert (m.dim, m.n_objects, m.frames, m.extent, m.birth_window, m.lambda_d, m.clutter_rate, m.h_max) == \
+        (2, 100, 100, 1000.0, (0, 49), 1.5, 20.0, 1000)
+    for p in (t, m):
+        assert (p.p_s, p.p_d, p.sigma, p.speed_max, p.h_up, p.tau) == (0.99, 0.9, 5.0, 10.0, 100, 1e-5)
+    for n in (50, 200, 500, 1000):
+        s = scenes.preset(f"sweep_N{n}")
+        assert (s.dim, s.n_objects, s.frames, s.extent, s.p_d, s.lambda_d, s.clutter_rate, s.sigma) == \
+            (3, n, 50, 5000.0, 0.85, 2.0, 50.0, 5.0)
+        assert s.births_per_frame == pytest.approx(0.01 * n) and s.birth_window is None
+    sc = scenes.make_scene(m, 2024)
+    alive = np.array([len(fr.truth) for fr in sc.frames[50:]])
+    M = np.array([len(fr.Z) for fr in sc.frames[50:]])
+    want = alive * m.p_d * (1 + m.lambda_d) + m.clutter_rate
+    assert abs(M.mean() / want.mean() - 1) < 0.05
