@@ -136,3 +136,25 @@ def test_presets_follow_the_stated_recipes():
     M = np.array([len(fr.Z) for fr in sc.frames[50:]])
     want = alive * m.p_d * (1 + m.lambda_d) + m.clutter_rate
     assert abs(M.mean() / want.mean() - 1) < 0.05
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_ospa_equals_brute_force_over_assignments(p):
+    """OSPA from its definition, every injection of the smaller set into the
+    larger enumerated, on small random sets (both orders, cut-off binding
+    for some pairs)."""
+    import itertools
+
+    from scenes.metrics import ospa
+    rng = np.random.default_rng(5 + int(p))
+    c = 30.0
+    for _ in range(25):
+        m, n = rng.integers(1, 5, size=2)
+        X = rng.uniform(0, 60, size=(m, 2))
+        Y = rng.uniform(0, 60, size=(n, 2))
+        A, B = (X, Y) if m <= n else (Y, X)
+        best = min(sum(min(np.linalg.norm(A[i] - B[j]), c) ** p for i, j in enumerate(perm))
+                   for perm in itertools.permutations(range(len(B)), len(A)))
+        want = ((best + c ** p * (len(B) - len(A))) / len(B)) ** (1 / p)
+        assert ospa(X, Y, c=c, p=p) == pytest.approx(want, rel=1e-12)
+        assert ospa(Y, X, c=c, p=p) == pytest.approx(want, rel=1e-12)
