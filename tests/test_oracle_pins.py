@@ -603,3 +603,34 @@ def test_cardinality_and_existence_are_sums_over_the_exact_posterior(oracle_mod)
     np.testing.assert_allclose(e["pmf"][:len(pmf_exact)], pmf_exact, atol=1e-12)
     for lab, r in zip(e["labels"], e["r"]):
         assert r == pytest.approx(exist_exact[tuple(lab)], abs=1e-12)
+
+
+@pytest.mark.parametrize("h_max", [100000, 7])
+def test_clutter_probability_of_each_detection_is_a_sum_over_the_exact_posterior(oracle_mod, h_max):
+    """Reading R9: r_U,i is the total weight of the retained hypotheses that
+    assign detection i to clutter.  Against the brute-force posterior: with
+    every child retained, the sum over the whole normalised posterior; with
+    H_max = 7, the sum over the exact top 7 renormalised among themselves
+    (so summing weights before the renormalisation, or over the children
+    before the cut, fails)."""
+    rng = np.random.default_rng(35)
+    o, cfg, Z, slots = _tiny(oracle_mod, rng, n_tracks=2, M=3, births=1, h_up=60000, h_max=h_max, p_s=1.0,
+                             tau=1e-300, clutter_rate=60.0)
+    dead, theta, lw = o.bruteforce(0)
+    finite = np.isfinite(lw)
+    theta, lw = theta[finite], lw[finite]
+    order = np.lexsort((np.arange(len(lw)), -lw))[:h_max]
+    assert len(lw) > 7
+    w_all = np.exp(lw - np.logaddexp.reduce(lw))
+    w = np.exp(lw[order] - np.logaddexp.reduce(lw[order]))
+    ru_exact = np.array([w[theta[order, i] == 0].sum() for i in range(len(Z))])
+    assert ((ru_exact > 1e-3) & (ru_exact < 1 - 1e-3)).all()   # every detection discriminates
+    if h_max < len(lw):
+        # the two plausible slips give results far outside the tolerance
+        ru_raw = np.array([w_all[order][theta[order, i] == 0].sum() for i in range(len(Z))])
+        ru_all = np.array([w_all[theta[:, i] == 0].sum() for i in range(len(Z))])
+        assert np.abs(ru_raw - ru_exact).max() > 1e-6 and np.abs(ru_all - ru_exact).max() > 1e-6
+    o.prune()
+    idx, klw, _ = o.kept()
+    assert len(idx) == min(h_max, len(lw))
+    np.testing.assert_allclose(o.meas_assoc(), ru_exact, atol=1e-12)
