@@ -2,24 +2,32 @@
 
 A step is one frame of the whole update (predict, compatibility table,
 death probabilities, child expansion and scoring, normalisation and top-H,
-track update, estimates) on a seeded synthetic scene: 2-D constant velocity,
-100 objects appearing over the first 50 frames, 100 frames, clutter
-Poisson(20), 1 + Poisson(1.5) detections per detected object, H_max = 1000,
-H_up = 100.  Steps walk through the scene's frames in order; the filter is
-reset when the scene restarts.  Before the warm-up steps, one untimed set-up
-pass over the scene captures the frame graphs its plans need (reported as
-config.graph_precapture_frames; --no-precapture skips it).
+track update, estimates).  The default workload is the largest cell of the
+3-D scalability sweep whose hypothesis cap binds: N = 200 objects held near
+N (deaths at P_S 0.99, Poisson(0.01 N) births per frame) in [0, 5000]^3,
+clutter Poisson(50), P_D 0.85, 1 + Poisson(2) detections per detected
+object, H_max = 20000, H_up = 100, 50 frames.  Steps walk the steady frames
+10-49 in order and wrap; the filter reaches a window frame by a reset and an
+untimed replay of the frames before it, so the timed frames do not depend
+on --steps.  Before the warm-up steps, one untimed set-up pass over the
+scene captures the frame graphs its plans need.  Further cells (N = 1000 and
+N = 50 of the sweep, and the 2-D mid scene) are measured the same way and
+reported under "cells".
 
 value  frames/s with each frame's detections already in device memory.
-e2e    frames/s through the same C ABI with host buffers: detections copied
-       host->device and the estimates read back inside every step.
-Between steps a 256 MiB buffer is written to flush L2 (outside the timed
-events).  Under torchrun every rank runs its own independent scene (no
-collective on the data path); value is the frames of all ranks over the
-slowest rank's time.
+e2e    frames/s of the same frames through the same C ABI with host
+       buffers: detections copied host->device and the estimates read back
+       inside every step.
+Every step is timed alone with CUDA events on the filter's stream; a 256 MiB
+buffer is written before it to flush L2 (outside the events).  Under
+torchrun every rank runs its own independent scene (no collective on the
+data path); value is the frames of all ranks over the slowest rank's time.
 
---impl reference times the FP64 CPU oracle (the reference implementation of
-this method in this repository) on the host cores.
+cpu_baseline times the FP64 CPU oracle on the host cores on a bounded sample
+of the workload (the last frame it reaches from the initial GLMB within
+--cpu-budget seconds); oracle_error re-runs one frame of the workload from
+the oracle's own state and reports the library's largest error against the
+oracle for every output.  --impl reference prints the oracle's line alone.
 """
 from __future__ import annotations
 
@@ -44,15 +52,25 @@ METRIC = "GLMB update frames/sec & hypothesis-track updates/s vs N objects, H ca
 UNIT = "frames/s"
 INT_PEAK_NOTE = "152 SMs x 128 lanes x 2070 MHz"
 
+# The default workload: the largest cell of the 3-D scalability sweep whose
+# hypothesis cap binds (N = 200 objects, H_max = 20000: about 10^4 retained
+# hypotheses of about 200 tracks each, 580 detections per frame), timed on
+# its steady-state frames 10-49 (frames 0-9 are the transient in which the
+# hypothesis count grows to the cap).  Extra cells of the same sweep are
+# measured with the same protocol and reported in the same line.
+DEFAULT_SCENE = "sweep_N200"
+DEFAULT_H_MAX = 20000
+DEFAULT_EXTRA = "sweep_N1000:20000,sweep_N50:1000,mid"
 
-def expansion_traffic():
-    """DRAM bytes per frame of the expansion kernels from the committed ncu
-    summary, or None when the kernels changed since it was captured."""
+
+def expansion_traffic(workload=DEFAULT_SCENE):
+    """DRAM bytes per frame of the expansion kernels on a workload, from the
+    committed ncu summary profiles/expansion_traffic_<workload>.md, or None
+    when there is none or the kernels changed since it was captured."""
     import hashlib
-    here = os.path.dirname(os.path.abspath(__file__))
     try:
-        txt = open(os.path.join(here, "profiles", "expansion_traffic_mid.md")).read()
-        src = open(os.path.join(here, "paper_2512_06230_gb300", "csrc", "kernels_expand.cu"), "rb").read()
+        txt = open(os.path.join(ROOT, "profiles", f"expansion_traffic_{workload}.md")).read()
+        src = open(os.path.join(ROOT, "paper_2512_06230_gb300", "csrc", "kernels_expand.cu"), "rb").read()
     except OSError:
         return None
     vals = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith(("#", " ", "`")))
@@ -83,9 +101,28 @@ def job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
     return steps_per_rank * world / (max_ms / 1000.0)
 
 
-def scene_for_rank(args, rank):
-    p = scenes.preset(args.scene)
-    return scenes.make_scene(p, 1000 * 2 + rank if args.seed is None else args.seed + rank)
+def scene_params(name: str, h_max=None):
+    """Scene parameters and the seed base of a named workload: "sweep_N<n>"
+    (3-D sweep, seed 3000 + n), "mid" (2-D, seed 2000), "tiny" (seed 1000)."""
+    if name.startswith("sweep_N"):
+        p = scenes.preset(name, h_max=DEFAULT_H_MAX if h_max is None else h_max)
+        return p, 3000 + p.n_objects
+    p = scenes.preset(name) if h_max is None else scenes.preset(name, h_max=h_max)
+    return p, {"tiny": 1000, "mid": 2000}.get(name, 2000)
+
+
+def window_start(name: str) -> int:
+    """First frame of the steady window: after the birth transient."""
+    if name.startswith("sweep_N"):
+        return 10
+    return {"tiny": 25, "mid": 50}.get(name, 0)
+
+
+def scene_for_rank(args, rank, name=None, h_max=None):
+    """The scene a rank runs: every rank its own seed (independent scenes)."""
+    name = args.scene if name is None else name
+    p, base = scene_params(name, getattr(args, "h_max", None) if h_max is None else h_max)
+    return scenes.make_scene(p, base + 7919 * rank if args.seed is None else args.seed + rank)
 
 
 def filter_cfg(sc):
@@ -140,31 +177,195 @@ def summarize_clocks(lines, dev):
             "samples": len(sm)}
 
 
-def run_oracle(args, sc, cfg, budget_s):
-    """FP64 oracle over the scene's frames from the initial GLMB, all host
-    threads, until the scene ends or the time budget is spent."""
+def run_oracle(args, sc, cfg, budget_s, state_frame=None):
+    """The FP64 oracle on the host cores over a bounded sample of the
+    workload: from the initial GLMB it steps the scene's frames in order
+    until budget_s is spent (the frame in progress is finished); the rate is
+    that of the last frame it completed, the largest of the sample (the
+    hypothesis count grows over the first frames), whose predecessors only
+    build its state.  With state_frame set, the oracle's own state before
+    that frame is also returned (for an error report against the GPU).
+    Returns (frames/s, threads, sample text, details, state)."""
     import oracle
     threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
     o = oracle.Oracle(cfg, n_threads=threads)
-    t0 = time.perf_counter()
-    n = 0
-    for fr in sc.frames:
+    t_start = time.perf_counter()
+    per, state = [], None
+    for k, fr in enumerate(sc.frames):
+        if state_frame is not None and k == state_frame:
+            state = o.export_state()
+        t0 = time.perf_counter()
         o.step(fr.births, fr.Z)
         o.estimates()
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
+        per.append((k, time.perf_counter() - t0, o.num_parents()))
+        if time.perf_counter() - t_start > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return n / dt, threads, f"{args.scene} scene frames 0..{n - 1} of {len(sc.frames)} " \
-        f"from the initial GLMB ({dt:.1f} s, {threads} threads)"
+    if state_frame is not None and state is None and len(per) > state_frame:
+        state = o.export_state()
+    k, dt, parents = per[-1]
+    total = time.perf_counter() - t_start
+    sample = (f"frame {k} of the {sc.params.name} scene (seed {sc.seed}; {parents} parent hypotheses, "
+              f"{len(sc.frames[k].Z)} detections), reached by the oracle itself from the initial GLMB through "
+              f"frames 0..{k - 1} untimed; {dt:.2f} s for the frame, {total:.1f} s in all, {threads} threads")
+    details = {"frames": [{"frame": a, "s": round(b, 4), "parents": c} for a, b, c in per]}
+    return 1.0 / dt, threads, sample, details, state
 
 
-def workload_config(args, sc, cfg) -> dict:
+def workload_config(args, sc, cfg, w0=None) -> dict:
     """The workload of the default run, named the same in both arms."""
     F = len(sc.frames)
-    return {"workload": f"{args.scene} scene: 2-D CV, {sc.params.n_objects} objects, "
-                        f"{F} frames, H_max={cfg['h_max']}, H_up={cfg['h_up']}",
-            "scene": args.scene, "h_max": cfg["h_max"], "h_up": cfg["h_up"], "frames_per_scene": F}
+    w0 = window_start(sc.params.name) if w0 is None else w0
+    p = sc.params
+    if p.dim == 3:
+        shape = (f"3-D sweep cell N={p.n_objects}, H_max={cfg['h_max']}: CV in [0,{p.extent:g}]^3, "
+                 f"clutter Poisson({p.clutter_rate:g}), P_D {p.p_d:g}, 1+Poisson({p.lambda_d:g}) detections")
+    else:
+        shape = (f"{p.name} scene: 2-D CV, {p.n_objects} objects, clutter Poisson({p.clutter_rate:g}), "
+                 f"H_max={cfg['h_max']}")
+    return {"workload": f"{shape}, H_up={cfg['h_up']}; steady frames {w0}-{F - 1} of a {F}-frame scene, cycled",
+            "scene": p.name, "n_objects": p.n_objects, "h_max": cfg["h_max"], "h_up": cfg["h_up"],
+            "frames_per_scene": F, "timed_frames": [w0, F - 1], "seed": sc.seed}
+
+
+class Cell:
+    """One workload stepped by the library: steps walk the steady window
+    [w0, F) in order and wrap; the filter is brought to a window frame by a
+    reset and an untimed replay of the frames before it (the filter is
+    deterministic, so a replay reproduces the state exactly).  Every step
+    is timed alone with CUDA events on the filter's stream; L2 is flushed
+    before it, outside the events."""
+
+    def __init__(self, glmb, torch, dev, sc, cfg, w0, stages=("expand", "select"), flush=None):
+        self.glmb, self.torch, self.sc, self.cfg, self.w0 = glmb, torch, sc, cfg, w0
+        self.F = len(sc.frames)
+        self.stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(self.stream)
+        self.f = glmb.Filter(cfg, stream=self.stream.cuda_stream)
+        self.Zdev = [torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
+                     for fr in sc.frames]
+        self.B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+        self.flush = flush
+        self.stages = list(stages)
+        self.f.set_profiling(self.stages)
+        self.pos = 0
+        torch.cuda.synchronize()
+
+    def close(self):
+        self.f.close()
+        self.torch.cuda.synchronize()
+
+    def goto(self, k):
+        """Reset, then step frames 0..k-1 untimed."""
+        self.f.reset()
+        for j in range(k):
+            self.f.step(self.B[j], self.Zdev[j], device=True)
+        self.pos = k
+
+    def precapture(self):
+        """One untimed pass over the whole scene: captures the frame graph of
+        every plan the scene needs (a later pass replays them)."""
+        self.goto(self.F)
+        self.f.estimates(cap=self.cfg["max_tracks"], pmf_cap=64)
+        self.torch.cuda.synchronize()
+
+    def run(self, n_steps, start, host=False):
+        """Steps start .. start + n_steps - 1 of the window cycle; returns per
+        step: event time (ms), stage times, launches and work counters."""
+        torch, f, cfg = self.torch, self.f, self.cfg
+        W = self.F - self.w0
+        out = []
+        for s in range(start, start + n_steps):
+            fi = self.w0 + s % W
+            if self.pos != fi:
+                self.goto(fi)
+            fr = self.sc.frames[fi]
+            info0 = f.info()
+            tim0 = f.timing()
+            if self.flush is not None:
+                self.flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            if host:
+                f.step(self.B[fi], fr.Z)
+            else:
+                f.step(self.B[fi], self.Zdev[fi], device=True)
+            est = f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
+            e1.record(self.stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            info = f.info()
+            tim = f.timing()
+            self.pos = fi + 1
+            M = len(fr.Z)
+            out.append(dict(
+                ms=ms, frame=fi, M=M, parents=info0["n_hyp"], retained=info["n_hyp"],
+                entries=info["n_entries"], children=info["n_children"], unique=info["n_unique"],
+                n_est=est["n"], launches=info["n_launches"] - info0["n_launches"],
+                captures=info["n_graph_captures"] - info0["n_graph_captures"],
+                redo=info["n_redo"] - info0["n_redo"],
+                draws=cfg["h_up"] * (info0["n_entries"] + info0["n_hyp"] * (len(fr.births) + M)),
+                stage_ms={k: tim[k][0] - tim0.get(k, (0.0, 0))[0] for k in tim},
+                h2d=(fr.Z.nbytes + len(fr.births) * 43 * 8) if host else 0,
+                d2h=est["n"] * 352 + 64 * 8))
+        return out
+
+
+def summarize(steps, world=1):
+    """Rates of a list of step records (one rank)."""
+    ms = sum(s["ms"] for s in steps)
+    n = len(steps)
+    return dict(frames_per_s=n / (ms / 1e3), ms_per_step=ms / n,
+                hypothesis_track_updates_per_s=sum(s["entries"] for s in steps) / (ms / 1e3),
+                mean_parents=statistics.fmean(s["parents"] for s in steps),
+                mean_retained=statistics.fmean(s["retained"] for s in steps),
+                mean_M=statistics.fmean(s["M"] for s in steps),
+                children_per_step=statistics.fmean(s["children"] for s in steps),
+                launches=sum(s["launches"] for s in steps),
+                captures_in_timed_steps=sum(s["captures"] for s in steps),
+                redone_frames=sum(s["redo"] for s in steps),
+                stage_ms_per_step={k: sum(s["stage_ms"].get(k, 0.0) for s in steps) / n
+                                   for k in steps[0]["stage_ms"]})
+
+
+def rooflines(steps, peaks, workload=DEFAULT_SCENE):
+    """Roofline objects of the expansion (int32 issue, the dominant kernel
+    group) and of the selection (HBM), from the timed steps' stage events.
+
+    Expansion: 25 int32 lane operations per uniform (one Philox4x32-10 call
+    of about 100 operations gives four uniforms), one uniform per slot and
+    per detection row of every child drawn, against 152 SMs x 128 lanes x
+    2070 MHz.  Selection: the algorithmic bytes of the survey's a6+a7 row,
+    8 B per child key per pass over two passes plus 16 B per retained
+    hypothesis written, against the measured HBM copy bandwidth."""
+    peak_ops = 152 * 128 * 2070e6
+    exp_ms = sum(s["stage_ms"].get("expand", 0.0) for s in steps)
+    sel_ms = sum(s["stage_ms"].get("select", 0.0) for s in steps)
+    total_ms = sum(s["ms"] for s in steps)
+    ops = 25.0 * sum(s["draws"] for s in steps)
+    n = len(steps)
+    exp = None
+    if exp_ms > 0:
+        a = ops / (exp_ms / 1e3)
+        exp = {"bound": "alu", "kernel": "child expansion and scoring (stage_kernel, draw_kernel, warp_kernel, "
+                                         "dedup_kernel of one frame)",
+               "achieved": a / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",
+               "frac": a / peak_ops, "traffic": expansion_traffic(workload), "peak_source": INT_PEAK_NOTE,
+               "algorithmic_per_step": ops / n, "kernel_ms_per_step": exp_ms / n,
+               "kernel_share_of_step": exp_ms / total_ms}
+    sel = None
+    hbm = peaks.get("hbm_gbs")
+    if sel_ms > 0:
+        byts = sum(16.0 * s["children"] + 16.0 * s["retained"] for s in steps)
+        a = byts / (sel_ms / 1e3) / 1e9
+        p = hbm if hbm else 6800.0
+        sel = {"bound": "hbm", "kernel": "normalisation and top-H selection (select_cluster_kernel, or the "
+                                         "lse/radix/compact chain)",
+               "achieved": a, "peak": p, "unit": "GB/s", "frac": a / p, "traffic": None,
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6800 GB/s",
+               "algorithmic_per_step": byts / n, "kernel_ms_per_step": sel_ms / n,
+               "kernel_share_of_step": sel_ms / total_ms}
+    return exp, sel
 
 
 def batch_cfg(p, sc):
@@ -588,22 +789,55 @@ def run_mlp(args, glmb, torch, dev):
                                    else "fallback 1900"}}))
 
 
+def peaks_file():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def oracle_error(oracle_state, glmb, sc, cfg, k):
+    """Error of the library against the FP64 oracle for every output of one
+    frame of the timed workload (the benchmark spec's per-output error report): both
+    import the oracle's own state before frame k and run frame k; the
+    step-by-step comparison of the parity tests gives the largest error of
+    each output and the decisions it excused."""
+    import oracle
+    from tests import parity
+    oracle.build()
+    fr = sc.frames[k]
+    o, g, d = parity.run_frame(oracle, glmb, cfg, oracle_state, fr.births, fr.Z,
+                               n_threads=os.cpu_count() or 1)
+    rep = parity.compare(o, g, d, cfg, fr.Z)
+    g.close()
+    return {"frame": k, "max_err": {a: float(f"{b:.3g}") for a, b in sorted(rep.max_err.items())},
+            "checks": rep.checks, "excused": rep.excused, "failures": len(rep.failures),
+            "tolerances": {"logw_abs": parity.LOGW_TOL, "mean_cov_rel": parity.REL_TOL}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10,
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5,
                     help="untimed warm-up steps (after the set-up pass that captures the frame graphs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--scene", default="mid")
+    ap.add_argument("--scene", default=DEFAULT_SCENE,
+                    help="sweep_N<n> (3-D sweep cell, H_max from --h-max), mid, tiny, or one of the "
+                         "workload modes batch, convoy, sweep, gate, mlp")
+    ap.add_argument("--h-max", type=int, default=None, help="H_max of the scene (sweep cells: 20000)")
+    ap.add_argument("--extra-cells", default=DEFAULT_EXTRA,
+                    help="further workloads measured the same way in the same line: name[:H_max],...")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-flush", action="store_true")
-    ap.add_argument("--no-precapture", action="store_true",
-                    help="skip the untimed set-up pass that captures the scene's frame graphs")
-    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work after which its sample ends (the frame in progress finishes)")
     ap.add_argument("--cpu-threads", type=int, default=0,
                     help="host threads of the oracle leg (0: all cores)")
-    ap.add_argument("--stages", action="store_true", help="also report per-stage times")
+    ap.add_argument("--error-frame", type=int, default=4,
+                    help="frame of the default workload re-run against the oracle for the error report "
+                         "(-1: none)")
+    ap.add_argument("--stages", action="store_true", help="time every stage of the frame, not only two")
     ap.add_argument("--batch-detections", default="device", choices=["device", "host"],
                     help="--scene batch: detections resident in device memory or copied from the host")
     ap.add_argument("--scenes", type=int, default=64,
@@ -642,14 +876,15 @@ def main():
             return
         sc = scene_for_rank(args, 0)
         cfg = filter_cfg(sc)
-        v, threads, sample = run_oracle(args, sc, cfg, min(args.cpu_budget, 20.0 + 2 * args.steps))
+        v, threads, sample, details, _ = run_oracle(args, sc, cfg, args.cpu_budget)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": workload_config(args, sc, cfg),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": sample},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "oracle_frames": details["frames"]}
         print(json.dumps(line))
         return
 
@@ -679,77 +914,30 @@ def main():
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)
-    F = len(sc.frames)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    f = glmb.Filter(cfg, stream=stream.cuda_stream)
-    Zdev = [torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, sc.dim_z), device=dev)
-            for fr in sc.frames]
-    Bhost = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
+    w0 = window_start(sc.params.name)
     if args.profile_frames:
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        f = glmb.Filter(cfg, stream=stream.cuda_stream)
+        F = len(sc.frames)
+        Zdev = [torch.from_numpy(fr.Z).to(dev) for fr in sc.frames]
+        B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
         for k in range(args.profile_frames):
-            fr = sc.frames[k % F]
             if k % F == 0:
                 f.reset()
-            f.step(Bhost[k % F], Zdev[k % F], device=True)
+            f.step(B[k % F], Zdev[k % F], device=True)
         torch.cuda.synchronize()
         print(json.dumps({"profile_frames": args.profile_frames, "info": {
             k: v for k, v in f.info().items() if isinstance(v, (int, float))}}))
         return
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
-    h_up = cfg["h_up"]
-
-    host_times = []
-
-    def run(n_steps, start, host):
-        """Runs n_steps frames starting at global step index `start`; returns
-        per-step event times (ms) and per-step work counters."""
-        times, work = [], []
-        host_times.clear()
-        for s in range(start, start + n_steps):
-            fi = s % F
-            fr = sc.frames[fi]
-            if not args.no_flush:
-                flush.zero_()
-            info0 = f.info() if fi != 0 else None
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if fi == 0:
-                f.reset()
-            t0 = time.perf_counter()
-            if host:
-                f.step(Bhost[fi], fr.Z)
-            else:
-                f.step(Bhost[fi], Zdev[fi], device=True)
-            t1 = time.perf_counter()
-            est = f.estimates(cap=cfg["max_tracks"], pmf_cap=64)
-            t2 = time.perf_counter()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            host_times.append((t1 - t0, t2 - t1))
-            info = f.info()
-            H_par = 1 if info0 is None else info0["n_hyp"]
-            E_par = 0 if info0 is None else info0["n_entries"]
-            M = len(fr.Z)
-            work.append(dict(entries=info["n_entries"], n_est=est["n"], M=M,
-                             draws=h_up * (E_par + H_par * (len(fr.births) + M)),
-                             h2d=fr.Z.nbytes + len(fr.births) * 43 * 8,
-                             d2h=est["n"] * 352 + 64 * 8))
-        return times, work
-
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stages = list(glmb.Filter.STAGES) if args.stages else ["expand", "select"]
+    cell = Cell(glmb, torch, dev, sc, cfg, w0, stages=stages, flush=flush)
     # set-up: one untimed pass over the scene captures the frame graphs of
-    # every plan the scene needs (a reset restarts the planning state, so a
-    # later pass replays the same plans); then the warm-up, then the timed
-    # steps.  The expansion is timed with events in every run (the same mask
-    # throughout, so the set-up pass's graphs are reused).
-    f.set_profiling(["expand"])
-    precapture = 0 if args.no_precapture else F
-    if precapture:
-        run(precapture, 0, host=False)
-    run(args.warmup, 0, host=False)
+    # every plan it needs; then the warm-up steps, then the timed steps (the
+    # same window frames, replayed from a reset)
+    cell.precapture()
+    cell.run(args.warmup, 0)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -757,85 +945,79 @@ def main():
     th = threading.Thread(target=sample_clocks, args=(stop, clk_lines), daemon=True)
     th.start()
     time.sleep(0.3)
-    info_t0 = f.info()
-    launches0 = info_t0["n_launches"]
     torch.cuda.synchronize()
-    f.set_profiling(["expand"])   # clears the totals
-    times, work = run(args.steps, args.warmup, host=False)
+    steps = cell.run(args.steps, args.warmup)
     torch.cuda.synchronize()
-    host_step_ms = 1e3 * sum(t[0] for t in host_times) / max(1, len(host_times))
-    host_est_ms = 1e3 * sum(t[1] for t in host_times) / max(1, len(host_times))
-    info1 = f.info()
-    launches = info1["n_launches"] - launches0
-    tim = f.timing()
     stop.set()
     th.join(timeout=10)
-    total_ms = max_over_ranks(float(sum(times)), dev, world)
+    total_ms = max_over_ranks(float(sum(s["ms"] for s in steps)), dev, world)
     if world > 1:
         torch.distributed.barrier()
-    # end to end through the host-buffer path
-    times_h, work_h = run(args.steps, args.warmup, host=True)
-    total_h = max_over_ranks(float(sum(times_h)), dev, world)
-    stage = None
-    if args.stages:
-        f.set_profiling(list(glmb.Filter.STAGES))
-        run(args.steps, args.warmup, host=False)
-        stage = {k: {"ms_per_step": v[0] / max(v[1], 1), "calls": v[1]} for k, v in f.timing().items()}
-        f.set_profiling([])
-
+    # end to end through the host-buffer path: the same frames, from the same state
+    steps_h = cell.run(args.steps, args.warmup, host=True)
+    total_h = max_over_ranks(float(sum(s["ms"] for s in steps_h)), dev, world)
+    cell.close()
+    # further cells of the sweep, the same protocol
+    extra = {}
+    for spec in [s for s in args.extra_cells.split(",") if s]:
+        name, _, hm = spec.partition(":")
+        sc2 = scene_for_rank(args, rank, name=name, h_max=int(hm) if hm else None)
+        cfg2 = filter_cfg(sc2)
+        c2 = Cell(glmb, torch, dev, sc2, cfg2, window_start(name), flush=flush)
+        try:
+            c2.precapture()
+            c2.run(args.warmup, 0)
+            st2 = c2.run(args.steps, args.warmup)
+            sh2 = c2.run(args.steps, args.warmup, host=True)
+        finally:
+            c2.close()
+        s2 = summarize(st2)
+        ex2, sel2 = rooflines(st2, peaks_file(), name)
+        extra[f"{name}:{cfg2['h_max']}"] = {
+            "workload": workload_config(args, sc2, cfg2)["workload"], "value": s2["frames_per_s"],
+            "ms_per_step": s2["ms_per_step"],
+            "hypothesis_track_updates_per_s": s2["hypothesis_track_updates_per_s"],
+            "e2e": summarize(sh2)["frames_per_s"], "mean_parents": s2["mean_parents"],
+            "mean_M": s2["mean_M"], "stage_ms_per_step": s2["stage_ms_per_step"],
+            "roofline_frac": {"expansion_alu": ex2["frac"] if ex2 else None,
+                              "selection_hbm": sel2["frac"] if sel2 else None}}
     if rank != 0:
         return
-    frames = args.steps * world
+    summ = summarize(steps)
+    summ_h = summarize(steps_h)
     value = job_rate(args.steps, world, total_ms)
-    entries = sum(w["entries"] for w in work)
-    # roofline of the dominant kernel (child expansion): integer ALU work of
-    # the counter-based sampler, 100 32-bit operations per Philox4x32-10
-    # call and one call per four uniforms, one uniform per slot and per
-    # detection row of every child drawn
-    exp_ms, exp_calls = tim["expand"]
-    draws = sum(w["draws"] for w in work)
-    ops = 25.0 * draws
     clocks = summarize_clocks(clk_lines, local)
-    peak_ops = 152 * 128 * 2070e6
-    achieved = ops / (exp_ms / 1000.0) if exp_ms > 0 else None
-    cpu_v, cpu_threads, cpu_sample = run_oracle(args, sc, cfg, args.cpu_budget)
+    peaks = peaks_file()
+    exp, sel = rooflines(steps, peaks, sc.params.name)
+    ef = args.error_frame if 0 <= args.error_frame < w0 else None
+    cpu_v, cpu_threads, cpu_sample, cpu_det, ostate = run_oracle(args, sc, cfg, args.cpu_budget, state_frame=ef)
+    err = oracle_error(ostate, glmb, sc, cfg, ef) if ostate is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**workload_config(args, sc, cfg),
-                   "l2": "flushed between steps (256 MiB write, outside "
-                   "the timed events)" if not args.no_flush else "not flushed",
-                   "inputs": "detections resident in device memory; births (<1 KB) copied in predict",
-                   "graph_precapture_frames": precapture},
-        "hypothesis_track_updates_per_s": entries * world / (total_ms / 1000.0),
-        "e2e": {"value": frames / (total_h / 1000.0), "unit": UNIT,
-                "h2d_bytes_per_step": sum(w["h2d"] for w in work_h) / len(work_h),
-                "d2h_bytes_per_step": sum(w["d2h"] for w in work_h) / len(work_h)},
-        "gpu_launches": int(launches),
-        "host_ms_per_step": {"step_call": round(host_step_ms, 4), "estimates_call": round(host_est_ms, 4)},
-        "graphs": {"captured": info1["n_graph_captures"], "replayed": info1["n_graph_launches"],
-                   "captured_in_timed_steps": info1["n_graph_captures"] - info_t0["n_graph_captures"],
-                   "redone_frames": info1["n_redo"],
-                   "capture_ms_total": round(info1["graph_capture_ms"], 3)},
-        "expand_plan": {"smem_bytes": info1["expand_smem_bytes"],
-                        "ctas_per_sm": info1["expand_ctas_per_sm"],
-                        "threads": info1["expand_threads"],
-                        "T": info1["expand_plan_T"], "K": info1["expand_plan_K"],
-                        "M": info1["expand_plan_M"]},
-        "roofline": {"bound": "alu", "kernel": "child expansion and scoring (stage_kernel, draw_kernel, warp_kernel, dedup_kernel of one frame)",
-                     "achieved": achieved / 1e12 if achieved else None,
-                     "peak": peak_ops / 1e12, "unit": "Tops/s (int32 lane ops)",
-                     "frac": achieved / peak_ops if achieved else None, "traffic": expansion_traffic(),
-                     "peak_source": INT_PEAK_NOTE,
-                     "kernel_ms_per_step": exp_ms / max(exp_calls, 1),
-                     "kernel_share_of_step": exp_ms / total_ms if total_ms else None},
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)" if flush is not None
+                   else "not flushed",
+                   "inputs": "detections resident in device memory; births (<4 KB) copied in the frame graph",
+                   "graph_precapture": "one untimed pass over the scene before the warm-up"},
+        "hypothesis_track_updates_per_s": summ["hypothesis_track_updates_per_s"] * world,
+        "e2e": {"value": job_rate(args.steps, world, total_h), "unit": UNIT,
+                "h2d_bytes_per_step": statistics.fmean(s["h2d"] for s in steps_h),
+                "d2h_bytes_per_step": statistics.fmean(s["d2h"] for s in steps_h),
+                "ms_per_step": total_h / args.steps},
+        "gpu_launches": int(summ["launches"]),
+        "work": {k: summ[k] for k in ("mean_parents", "mean_retained", "mean_M", "children_per_step",
+                                      "captures_in_timed_steps", "redone_frames")},
+        "stage_ms_per_step": summ["stage_ms_per_step"],
+        "roofline": exp,
+        "roofline_selection": sel,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": cpu_sample},
+        "oracle_error": err,
+        "cells": extra,
         "clocks": clocks,
     }
-    if stage:
-        line["stages"] = stage
     print(json.dumps(line))
 
 

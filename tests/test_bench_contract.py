@@ -36,9 +36,11 @@ def test_reference_line_has_the_contract_keys():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     # the GPU arm's workload object, built by the same function
     import bench
-    sc = bench.scene_for_rank(type("A", (), {"scene": "mid", "seed": None})(), 0)
-    want = bench.workload_config(type("A", (), {"scene": "mid"})(), sc, bench.filter_cfg(sc))
+    args = type("A", (), {"scene": bench.DEFAULT_SCENE, "seed": None, "h_max": None})()
+    sc = bench.scene_for_rank(args, 0)
+    want = bench.workload_config(args, sc, bench.filter_cfg(sc))
     assert d["config"] == want
+    assert want["scene"] == "sweep_N200" and want["h_max"] == 20000 and want["timed_frames"] == [10, 49]
 
 
 def test_reference_arm_prints_only_on_rank_0():
