@@ -432,19 +432,23 @@ glmb_status glmb_mlp_adam(float* params, const float* grad, float* m, float* v, 
  * (a tracking loop with a fixed memory budget and a frame deadline, where
  * cudaMalloc can synchronise the device and stall; a host application
  * whose memory policy forbids raw cudaMalloc).  It needs no handle and
- * allocates nothing: its scratch is a 64 KiB array in the library's device
- * image, which every GPU that loads the library holds until the process
- * exits.
+ * allocates nothing: its scratch is a 41,216-byte array in the library's
+ * device image, which every GPU that loads the library holds until the
+ * process exits.
  *
  * Inputs (device memory, caller-owned): logw_dev[n] child log-weights in
- * FP64, -INFINITY (or NaN) for children without weight.  Computation, as in
- * glmb_prune: weights are rounded to 2^-32, normalised by their FP64
- * log-sum-exp, those below tau dropped, the h_max largest kept (ties to the
- * lower index).  Outputs (device memory, caller-owned): idx_out_dev[h_max]
- * the kept indices in ascending order, logw_out_dev[h_max] their
- * renormalised log-weights, *n_out_dev their number.  Work is queued on
- * stream (a cudaStream_t; NULL is the default stream) and the call returns
- * without waiting.
+ * FP64.  Valid log-weights lie in (-2^30, 2^30); anything else (-INFINITY,
+ * +INFINITY, NaN, or a finite value outside that range) marks a child
+ * without weight.  Computation, with the steps of glmb_prune's selection:
+ * weights are rounded to 2^-32, normalised by their log-sum-exp (summed in
+ * FP64), those below tau dropped, the h_max largest kept (ties to the lower
+ * index).  glmb_prune sums its log-sum-exp in another order, so the two
+ * agree up to its rounding: a child within that rounding of tau may be
+ * decided either way.  Outputs (device memory, caller-owned):
+ * idx_out_dev[h_max] the kept indices in ascending order,
+ * logw_out_dev[h_max] their renormalised log-weights, *n_out_dev their
+ * number.  Work is queued on stream (a cudaStream_t; NULL is the default
+ * stream) and the call returns without waiting.
  *
  * The first call on a device looks up the scratch array's address for that
  * device (make it before any stream capture).  Every call uses the same

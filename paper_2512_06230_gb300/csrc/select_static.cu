@@ -1,7 +1,7 @@
 // glmb_select_top_static: top-H selection of child log-weights that makes no
-// device allocation.  Its scratch is the file-scope array below, sized for
-// at most kMaxBlocks blocks; every GPU that loads the library holds it until
-// the process exits.
+// device allocation.  Its scratch is the file-scope array below (41,216
+// bytes, sized for at most kMaxBlocks blocks); every GPU that loads the
+// library holds it until the process exits.
 //
 // Who needs it: callers that may not allocate device memory while they run,
 // such as a tracking loop with a fixed memory budget and a hard frame
@@ -9,11 +9,14 @@
 // milliseconds), or code embedded in a host application whose memory policy
 // forbids raw cudaMalloc.  The caller still passes the inputs and outputs.
 //
-// The computation matches the selection inside glmb_prune: log-weights are
-// converted to int64 with 2^-32 resolution, normalised by their FP64
-// log-sum-exp, children below tau are dropped, the h_max largest are kept
-// (ties by index), the kept ones are listed in index order and their
-// log-weights renormalised.
+// The steps are those of the selection inside glmb_prune: log-weights are
+// converted to int64 with 2^-32 resolution, normalised by their log-sum-exp,
+// children below tau are dropped, the h_max largest are kept (ties by
+// index), the kept ones are listed in index order and their log-weights
+// renormalised.  The log-sum-exp is summed differently (FP64 exponentials
+// here, FP32 exponentials with compensated sums there), so the two agree up
+// to its rounding: a child whose normalised weight lies within that rounding
+// of tau may land on either side of the cut.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -38,6 +41,8 @@ constexpr size_t kOffBlkEq = kOffBlkGt + 4 * kMaxBlocks;         // uint32[kMaxB
 constexpr size_t kOffHist = kOffBlkEq + 4 * kMaxBlocks;          // uint32[kBinsS]
 constexpr size_t kOffScal = kOffHist + 4 * kBinsS;               // Scal
 constexpr size_t kScratchBytes = kOffScal + 256;
+// the size glmb.h states for the scratch array
+static_assert(kScratchBytes == 41216, "scratch size changed: update glmb.h");
 
 struct SelScal {
   unsigned done;        // last-block counter
@@ -68,8 +73,10 @@ __host__ __device__ inline Ptrs ptrs_of(unsigned char* base) {
 }
 
 __device__ __forceinline__ long long key_of(double lw) {
-  // -inf (and NaN) mark children without weight
-  if (!(lw > -INFINITY)) return kKeyInvalid;
+  // log-weights outside (-2^30, 2^30) -- -inf, +inf and NaN among them --
+  // mark children without weight; inside, every key is below 2^62 in
+  // magnitude, so the difference of two keys cannot overflow
+  if (!(lw > -1073741824.0 && lw < 1073741824.0)) return kKeyInvalid;
   return __double2ll_rn(lw * 4294967296.0);
 }
 

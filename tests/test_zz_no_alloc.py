@@ -85,6 +85,26 @@ def test_static_selection_edge_cases(api):
     # h_max smaller than the candidates, equal weights at the boundary
     idx, lw = _select(f, np.zeros(7), 3, 1e-5)
     assert list(idx) == [0, 1, 2]
+    # +inf, NaN and values beyond 2^30 in magnitude mark children without weight
+    logw = np.array([0.0, np.inf, -1.0, 3.0e9, np.nan, -2.0e9, -2.0])
+    idx, lw = _select(f, logw, 10, 1e-5)
+    assert list(idx) == [0, 2, 6]
+    w = np.exp(logw[[0, 2, 6]])
+    assert np.allclose(lw, np.log(w / w.sum()), atol=1e-12)
+
+
+def test_static_selection_child_at_the_tau_cut(api):
+    """A child whose normalised weight is tau itself: the log-sum-exp is
+    rounded differently here and in glmb_prune, so either decision is
+    correct; the other children and all renormalised weights are exact."""
+    glmb, f = api
+    tau = 1e-5
+    x = np.log(tau / (1.0 - tau))          # w1 / (w0 + w1) = tau with w0 = 1
+    logw = np.array([0.0, x])
+    idx, lw = _select(f, logw, 10, tau)
+    assert list(idx) in ([0], [0, 1])
+    w = np.exp(logw[idx])
+    assert np.allclose(lw, np.log(w / w.sum()), atol=1e-12)
 
 
 def test_static_selection_rejects_sizes_beyond_the_limit(api):
