@@ -425,11 +425,133 @@ __device__ void copy_comp(const Model& md, const CompTable& src, int c, const Co
   dst.log1mp[d] = src.log1mp[c];
 }
 
+// Gain, mean and Joseph-form covariance of one track update in arithmetic F,
+// from P, S^-1 = Si, R/m and the mean innovation; writes component d.
+template <typename F, int DZ>
+__device__ __forceinline__ void kalman_tail(const F (&P)[2 * DZ][2 * DZ], const F (&Si)[DZ][DZ],
+                                            const F (&Rm)[DZ][DZ], const F (&ebar)[DZ], const CompTable& src,
+                                            int c, const CompTable& dst, int d) {
+  constexpr int DX = 2 * DZ;
+  const size_t cs = src.cap, cd = dst.cap;
+  F K[DX][DZ];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      F t = 0;
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t += P[i][a] * Si[a][b];
+      K[i][b] = t;
+    }
+#pragma unroll
+  for (int i = 0; i < DX; ++i) {
+    F delta = 0;
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) delta += K[i][b] * ebar[b];
+    float hi = src.mhi[i * cs + c], lo = src.mlo[i * cs + c];
+    if (sizeof(F) == sizeof(float)) {
+      df_add(hi, lo, (float)delta);
+    } else {
+      const double v = ((double)hi + (double)lo) + (double)delta;
+      hi = (float)v;
+      lo = (float)(v - (double)hi);
+    }
+    dst.mhi[i * cd + d] = hi;
+    dst.mlo[i * cd + d] = lo;
+  }
+  // Joseph form: (I - K H) P (I - K H)^T + K (R/m) K^T
+  F AP[DX][DX];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = 0; j < DX; ++j) {
+      F t = P[i][j];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t -= K[i][a] * P[a][j];
+      AP[i][j] = t;
+    }
+  F KR[DX][DZ];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      F t = 0;
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) t += K[i][a] * Rm[a][b];
+      KR[i][b] = t;
+    }
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = i; j < DX; ++j) {
+      F t = AP[i][j], t2 = AP[j][i];
+#pragma unroll
+      for (int a = 0; a < DZ; ++a) {
+        t -= AP[i][a] * K[j][a];
+        t2 -= AP[j][a] * K[i][a];
+      }
+      F r = 0;
+#pragma unroll
+      for (int b = 0; b < DZ; ++b) r += KR[i][b] * K[j][b];
+      dst.cov[(size_t)pidx(DX, i, j) * cd + d] = (float)(F(0.5) * (t + t2) + r);
+    }
+}
+
+// The FP64 update of an ill-conditioned innovation covariance (rare; kept
+// out of line so that its registers do not limit the kernel's occupancy).
+template <int DZ>
+__device__ __noinline__ bool kalman_fp64(const Model& md, const float (&P)[2 * DZ][2 * DZ], const long long (&se)[DZ],
+                                         int m, const CompTable& src, int c, const CompTable& dst, int d) {
+  constexpr int DX = 2 * DZ;
+  double Pd[DX][DX], Sd[DZ][DZ], Ld[DZ][DZ], ldd, Li[DZ][DZ], Si[DZ][DZ], Rd[DZ][DZ], ed[DZ];
+#pragma unroll
+  for (int i = 0; i < DX; ++i)
+#pragma unroll
+    for (int j = 0; j < DX; ++j) Pd[i][j] = P[i][j];
+#pragma unroll
+  for (int a = 0; a < DZ; ++a) {
+    ed[a] = (double)se[a] * kFxInv / (double)m;
+#pragma unroll
+    for (int b = 0; b < DZ; ++b) {
+      Rd[a][b] = (double)md.R[a * DZ + b] / (double)m;
+      Sd[a][b] = Pd[a][b] + Rd[a][b];
+    }
+  }
+  if (!chol_n<double, DZ>(Sd, Ld, ldd, 2.220446049250313e-16)) return false;
+#pragma unroll
+  for (int j = 0; j < DZ; ++j)
+#pragma unroll
+    for (int i = 0; i < DZ; ++i) {
+      double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k) t -= Ld[i][k] * Li[k][j];
+      Li[i][j] = (i < j) ? 0.0 : t / Ld[i][i];
+    }
+#pragma unroll
+  for (int i = 0; i < DZ; ++i)
+#pragma unroll
+    for (int j = 0; j < DZ; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
+      Si[i][j] = t;
+    }
+  kalman_tail<double, DZ>(Pd, Si, Rd, ed, src, c, dst, d);
+  return true;
+}
+
+// Kalman update of component c with m detections whose innovations sum to
+// se (fixed point), into component d.  An innovation covariance whose FP32
+// Cholesky factor fails the pivot test (a pivot at or below 16 eps32
+// trace S) is factorised in FP64, and the gain, the mean and the Joseph
+// form are then computed in FP64 too: with S that ill-conditioned the gain
+// P H^T S^-1 cancels in FP32 (the posterior covariance is the difference of
+// nearly equal O(|P|) terms).
 template <int DZ>
 __device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
                             const long long (&se)[DZ], const CompTable& dst, int d) {
   constexpr int DX = 2 * DZ;
-  const size_t cs = src.cap, cd = dst.cap;
+  const size_t cs = src.cap;
   float P[DX][DX];
 #pragma unroll
   for (int i = 0; i < DX; ++i)
@@ -450,113 +572,32 @@ __device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
       S[a][b] = P[a][b] + Rm[a][b];
     }
   }
-  // S^-1 from the Cholesky factor (FP64 when ill-conditioned)
-  float Si[DZ][DZ];
-  {
-    float L[DZ][DZ], ld;
-    if (chol_n<float, DZ>(S, L, ld, 1.1920929e-7f)) {
-      float Li[DZ][DZ];
+  float L[DZ][DZ], ld;
+  if (chol_n<float, DZ>(S, L, ld, 1.1920929e-7f)) {
+    // S^-1 from the FP32 Cholesky factor
+    float Li[DZ][DZ], Si[DZ][DZ];
 #pragma unroll
-      for (int j = 0; j < DZ; ++j)
+    for (int j = 0; j < DZ; ++j)
 #pragma unroll
-        for (int i = 0; i < DZ; ++i) {
-          float t = (i == j) ? 1.f : 0.f;
+      for (int i = 0; i < DZ; ++i) {
+        float t = (i == j) ? 1.f : 0.f;
 #pragma unroll
-          for (int k = 0; k < i; ++k) t -= L[i][k] * Li[k][j];
-          Li[i][j] = (i < j) ? 0.f : t / L[i][i];
-        }
-#pragma unroll
-      for (int i = 0; i < DZ; ++i)
-#pragma unroll
-        for (int j = 0; j < DZ; ++j) {
-          float t = 0.f;
-#pragma unroll
-          for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
-          Si[i][j] = t;
-        }
-    } else {
-      double Sd[DZ][DZ], Ld[DZ][DZ], ldd, Li[DZ][DZ];
-#pragma unroll
-      for (int a = 0; a < DZ; ++a)
-#pragma unroll
-        for (int b = 0; b < DZ; ++b) Sd[a][b] = S[a][b];
-      if (!chol_n<double, DZ>(Sd, Ld, ldd, 2.220446049250313e-16)) return false;
-#pragma unroll
-      for (int j = 0; j < DZ; ++j)
-#pragma unroll
-        for (int i = 0; i < DZ; ++i) {
-          double t = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-          for (int k = 0; k < i; ++k) t -= Ld[i][k] * Li[k][j];
-          Li[i][j] = (i < j) ? 0.0 : t / Ld[i][i];
-        }
-#pragma unroll
-      for (int i = 0; i < DZ; ++i)
-#pragma unroll
-        for (int j = 0; j < DZ; ++j) {
-          double t = 0.0;
-#pragma unroll
-          for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
-          Si[i][j] = (float)t;
-        }
-    }
-  }
-  float K[DX][DZ];
-#pragma unroll
-  for (int i = 0; i < DX; ++i)
-#pragma unroll
-    for (int b = 0; b < DZ; ++b) {
-      float t = 0.f;
-#pragma unroll
-      for (int a = 0; a < DZ; ++a) t += P[i][a] * Si[a][b];
-      K[i][b] = t;
-    }
-#pragma unroll
-  for (int i = 0; i < DX; ++i) {
-    float delta = 0.f;
-#pragma unroll
-    for (int b = 0; b < DZ; ++b) delta += K[i][b] * ebar[b];
-    float hi = src.mhi[i * cs + c], lo = src.mlo[i * cs + c];
-    df_add(hi, lo, delta);
-    dst.mhi[i * cd + d] = hi;
-    dst.mlo[i * cd + d] = lo;
-  }
-  // Joseph form: (I - K H) P (I - K H)^T + K (R/m) K^T
-  float AP[DX][DX];
-#pragma unroll
-  for (int i = 0; i < DX; ++i)
-#pragma unroll
-    for (int j = 0; j < DX; ++j) {
-      float t = P[i][j];
-#pragma unroll
-      for (int a = 0; a < DZ; ++a) t -= K[i][a] * P[a][j];
-      AP[i][j] = t;
-    }
-  float KR[DX][DZ];
-#pragma unroll
-  for (int i = 0; i < DX; ++i)
-#pragma unroll
-    for (int b = 0; b < DZ; ++b) {
-      float t = 0.f;
-#pragma unroll
-      for (int a = 0; a < DZ; ++a) t += K[i][a] * Rm[a][b];
-      KR[i][b] = t;
-    }
-#pragma unroll
-  for (int i = 0; i < DX; ++i)
-#pragma unroll
-    for (int j = i; j < DX; ++j) {
-      float t = AP[i][j], t2 = AP[j][i];
-#pragma unroll
-      for (int a = 0; a < DZ; ++a) {
-        t -= AP[i][a] * K[j][a];
-        t2 -= AP[j][a] * K[i][a];
+        for (int k = 0; k < i; ++k) t -= L[i][k] * Li[k][j];
+        Li[i][j] = (i < j) ? 0.f : t / L[i][i];
       }
-      float r = 0.f;
 #pragma unroll
-      for (int b = 0; b < DZ; ++b) r += KR[i][b] * K[j][b];
-      dst.cov[(size_t)pidx(DX, i, j) * cd + d] = 0.5f * (t + t2) + r;
-    }
+    for (int i = 0; i < DZ; ++i)
+#pragma unroll
+      for (int j = 0; j < DZ; ++j) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < DZ; ++k) t += Li[k][i] * Li[k][j];
+        Si[i][j] = t;
+      }
+    kalman_tail<float, DZ>(P, Si, Rm, ebar, src, c, dst, d);
+  } else if (!kalman_fp64<DZ>(md, P, se, m, src, c, dst, d)) {
+    return false;
+  }
   dst.lk[d] = src.lk[c];
   dst.lb[d] = src.lb[c];
   dst.logp[d] = src.logp[c];
@@ -565,7 +606,7 @@ __device__ bool kalman_comp(const Model& md, const CompTable& src, int c, int m,
 }
 
 template <int DZ>
-__global__ void gc_remap_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
+__global__ void __launch_bounds__(256, DZ == 2 ? 3 : 2) gc_remap_kernel(Model md, CompTable src, CompTable dst, const uint32_t* __restrict__ newpos,
                                 const uint32_t* __restrict__ flag, const FrameDev* __restrict__ fs,
                                 const unsigned* __restrict__ n_keep_dev, const uint32_t* __restrict__ upd_src,
                                 const uint32_t* __restrict__ upd_m, const long long* __restrict__ upd_se,

@@ -48,6 +48,8 @@ def test_mid_scene_frame(oracle_mod, glmb, k):
     sc = scenes.make_scene(scenes.preset("mid"), 2001)
     rep = _frame(oracle_mod, glmb, sc.filter_config(), sc, k)
     assert rep.checks["children"] >= 1000
+    assert rep.excused["children"] <= parity.excused_children_bound(rep, sc.filter_config(), len(sc.frames[k].Z))
+    assert rep.excused["boundary"] <= 2 + 0.001 * rep.checks["retained"]
 
 
 def test_3d_scene_frame(oracle_mod, glmb):
@@ -209,6 +211,10 @@ def test_sweep_full_size_frame(oracle_mod, glmb, N, k):
                            max_tracks=2 * N + nb + 64)
     rep = _frame(oracle_mod, glmb, cfg, sc, k)
     assert rep.checks["slots"] > 10000
+    # what the excuses admitted: few decisions near a boundary of a row or of
+    # the death probability, and few retained hypotheses near the cut
+    assert rep.excused["children"] <= parity.excused_children_bound(rep, cfg, len(sc.frames[k].Z))
+    assert rep.excused["boundary"] <= 2 + 0.001 * rep.checks["retained"]
 
 
 @pytest.mark.parametrize("h_up,h_max,k", [(1, 50, 12), (300, 200, 8), (1000, 400, 10)])
@@ -249,3 +255,20 @@ def test_detections_at_capacity(oracle_mod, glmb):
     cfg = sc.filter_config(max_meas=len(sc.frames[k].Z))
     assert cfg["max_meas"] > 0
     _frame(oracle_mod, glmb, cfg, sc, k)
+
+
+@pytest.mark.parametrize("shape", ["diagonal", "correlated"])
+def test_ill_conditioned_innovation_takes_the_fp64_factorisation(oracle_mod, glmb, shape):
+    """Precision management: the Cholesky factor of an ill-conditioned
+    innovation covariance is computed in FP64 on the GPU (counted in
+    glmb_info.n_fp64_chol); the frame then matches the FP64 oracle at the
+    usual tolerances."""
+    cfg, state, Z, _ = parity.ill_conditioned_case(shape)
+    o, g, d = parity.run_frame(oracle_mod, glmb, cfg, state, [], Z)
+    rep = parity.compare(o, g, d, cfg, Z)
+    n64 = g.info()["n_fp64_chol"]
+    print(f"\n{shape}: n_fp64_chol {n64} checks {rep.checks} max_err "
+          + " ".join(f"{k}={v:.2e}" for k, v in sorted(rep.max_err.items())))
+    assert rep.ok(), rep.failures[:10]
+    assert n64 >= 4
+    assert rep.checks["unique_children"] >= 10 and rep.checks["retained"] >= 10

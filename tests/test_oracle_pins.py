@@ -634,3 +634,37 @@ def test_clutter_probability_of_each_detection_is_a_sum_over_the_exact_posterior
     idx, klw, _ = o.kept()
     assert len(idx) == min(h_max, len(lw))
     np.testing.assert_allclose(o.meas_assoc(), ru_exact, atol=1e-12)
+
+
+def test_ill_conditioned_case_needs_the_fp64_factorisation(oracle_mod):
+    """The ill-conditioned cases of the GPU parity tests: FP32 Cholesky's
+    pivot test (a pivot at or below 16 eps32 trace S) rejects both innovation
+    covariances, and for the correlated one an FP32 factorisation (numpy
+    float32) misses log det S by far more than the log-weight tolerance, so
+    only an FP64 factorisation can meet it.  The oracle's log det S and
+    log C of the first pair equal the closed forms in FP64."""
+    from tests import parity
+    for shape in ("diagonal", "correlated"):
+        cfg, state, Z, S = parity.ill_conditioned_case(shape)
+        S32 = S.astype(np.float32)
+        piv1 = np.float32(S32[1, 1]) - np.float32(S32[1, 0] / np.sqrt(S32[0, 0])) ** 2
+        assert piv1 <= np.float32(16 * 1.1920929e-7) * (S32[0, 0] + S32[1, 1])
+        o = oracle_mod.Oracle(cfg)
+        o.import_state(*state)
+        o.predict([])
+        o.update(Z)
+        Sp = S + 2.0 ** -40 * np.eye(2)            # the velocity variance reaches the position block
+        sl = o.slot(0, 0)
+        assert sl["logdetS"] == pytest.approx(np.linalg.slogdet(Sp)[1], abs=1e-9)
+        e = Z[0].astype(np.float64) - state[3][0][0][2][:2]
+        d2 = e @ np.linalg.solve(Sp, e)
+        pr = o.pair(0, 0, 0)
+        assert pr["d2"] == pytest.approx(d2, rel=1e-8)
+        lc = np.log(cfg["p_d"]) - 0.5 * (d2 + np.linalg.slogdet(Sp)[1] + 2 * np.log(2 * np.pi))
+        assert pr["logC"] == pytest.approx(lc, abs=1e-9)
+        o.prune()
+        if shape == "correlated":
+            l00 = np.sqrt(S32[0, 0])
+            l10 = S32[1, 0] / l00
+            ld32 = 2 * np.log(l00) + np.log(float(S32[1, 1] - l10 * l10))
+            assert abs(ld32 - np.linalg.slogdet(S)[1]) > 100 * parity.LOGW_TOL
