@@ -146,6 +146,8 @@ typedef struct {
   int32_t expand_threads;      /* threads per CTA of the last expansion */
   double graph_capture_ms;     /* host time spent capturing and instantiating frame graphs */
   int64_t n_pairs_pregate;     /* pairs that passed the Mahalanobis test (before the learned gate) */
+  int64_t n_draw_overflow;     /* children of the last update that the one-thread-per-child draw
+                                  handed to the one-warp-per-child kernel (a slot met twice) */
 } glmb_info;
 
 /* Creates a filter holding the initial GLMB: one hypothesis with no tracks
@@ -315,7 +317,8 @@ glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* 
  *   thread_warps_per_sm  draw one thread per child once the children give
  *                        every SM this many warps (default 4);
  *   draw_threads         threads per draw CTA (32..256, multiple of 32; 0:
- *                        h_up rounded up to a warp, at most 256);
+ *                        256; the draw kernel takes the frame's children in
+ *                        order, one per thread, whatever the CTA size);
  *   warp_cta_warps       most warps per CTA of the one-warp-per-child kernel
  *                        (1..16, default 16);
  *   stage_threads        threads per staging CTA (32..256, default 256).
@@ -461,6 +464,31 @@ glmb_status glmb_mlp_adam(float* params, const float* grad, float* m, float* v, 
 glmb_status glmb_select_top_static(const double* logw_dev, int64_t n, int32_t h_max, double tau,
                                    int64_t* idx_out_dev, double* logw_out_dev, int32_t* n_out_dev,
                                    void* stream);
+
+/* Failure-detection test hook (not part of the paper's method: it tests the
+ * library's own error handling).  Every device-side wait of the library is
+ * bounded; when a wait runs out, the kernel records the error, leaves its
+ * work unfinished and returns, and the frame fails with GLMB_E_TIMEOUT,
+ * leaving the previous frame's state intact.  This call makes one such
+ * wait run out on purpose, without any GPU fault:
+ *   GLMB_WAIT_TEST_SCAN  the first tile of every one-pass scan (used for
+ *                        the pair-count scan of frames with more than 16384
+ *                        components) withholds its prefix, so the look-back
+ *                        waits of the later tiles give up after `limit`
+ *                        polls;
+ *   GLMB_WAIT_TEST_GATE  CTA 0 of the learned gate's forward pass issues no
+ *                        tensor-core work for its first tile (nothing is in
+ *                        flight), so its completion wait gives up after
+ *                        `limit` SM clock cycles and the CTA frees its
+ *                        tensor memory and returns;
+ *   GLMB_WAIT_TEST_OFF   normal limits (`limit` ignored).
+ * The setting is process-wide and applies to kernels launched after the
+ * call; while it is set, glmb_step runs its frames without capturing a
+ * graph.  Errors: GLMB_E_INVALID (unknown mode, limit < 1). */
+#define GLMB_WAIT_TEST_OFF 0
+#define GLMB_WAIT_TEST_SCAN 1
+#define GLMB_WAIT_TEST_GATE 2
+glmb_status glmb_set_wait_test(int mode, long long limit);
 
 /* Message of the last error on this handle ("" if none). */
 const char* glmb_last_error(glmb_handle* h);

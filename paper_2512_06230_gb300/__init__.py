@@ -124,7 +124,7 @@ class GlmbInfo(C.Structure):
                 ("expand_ctas_per_sm", C.c_int32), ("expand_plan_T", C.c_int32),
                 ("expand_plan_K", C.c_int32), ("expand_plan_M", C.c_int32),
                 ("expand_threads", C.c_int32), ("graph_capture_ms", C.c_double),
-                ("n_pairs_pregate", C.c_int64)]
+                ("n_pairs_pregate", C.c_int64), ("n_draw_overflow", C.c_int64)]
 
 
 class GlmbTuning(C.Structure):
@@ -185,6 +185,7 @@ def load() -> C.CDLL:
         "glmb_gate_logits": [P, P, L, P], "glmb_gate_usage": [P, P, L, P, I, P, P],
         "glmb_mlp_forward": [P, P, L, P, P, P], "glmb_mlp_backward": [P, P, P, P, L, P, P, P, P],
         "glmb_mlp_adam": [P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float, P],
+        "glmb_set_wait_test": [I, C.c_longlong],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -214,6 +215,18 @@ def torch_allocator_hooks(device=None):
         torch.cuda.caching_allocator_delete(ptr)
 
     return DEV_ALLOC_FN(_alloc), DEV_FREE_FN(_free)
+
+
+WAIT_TEST_OFF, WAIT_TEST_SCAN, WAIT_TEST_GATE = 0, 1, 2
+
+
+def set_wait_test(mode: int, limit: int = 0) -> None:
+    """Failure-detection test hook (glmb_set_wait_test): make one bounded
+    device wait run out (WAIT_TEST_SCAN, WAIT_TEST_GATE) after `limit`, or
+    restore the normal limits (WAIT_TEST_OFF)."""
+    st = load().glmb_set_wait_test(int(mode), int(limit))
+    if st != 0:
+        raise GlmbError(st, "glmb_set_wait_test rejected its arguments")
 
 
 class GlmbError(RuntimeError):
@@ -302,14 +315,21 @@ def unpack_state(buf: bytes):
 class Filter:
     """One GLMB filter on the current CUDA device (see include/glmb.h)."""
 
-    def __init__(self, cfg: dict, stream: Optional[int] = None, allocator: Optional[str] = None):
+    def __init__(self, cfg: dict, stream: Optional[int] = None, allocator=None):
         """allocator="torch": the handle's device memory comes from PyTorch's
-        caching allocator (glmb_config.dev_alloc / dev_free)."""
+        caching allocator (glmb_config.dev_alloc / dev_free); a pair of
+        callables (alloc(nbytes) -> device address or None, free(address))
+        routes it through the caller's own functions."""
         self.lib = load()
         self.cfg = dict(cfg)
         self._c = make_config(cfg, stream)
         if allocator == "torch":
             self._hooks = torch_allocator_hooks()
+            self._c.dev_alloc, self._c.dev_free = self._hooks
+        elif isinstance(allocator, tuple) and len(allocator) == 2:
+            fa, ff = allocator
+            self._hooks = (DEV_ALLOC_FN(lambda nbytes, ctx: fa(int(nbytes))),
+                           DEV_FREE_FN(lambda ptr, ctx: ff(ptr)))
             self._c.dev_alloc, self._c.dev_free = self._hooks
         elif allocator is not None:
             raise ValueError(f"unknown allocator {allocator!r}")

@@ -169,6 +169,7 @@ struct glmb_handle {
   // stats
   long long n_pairs = 0, n_unique = 0;
   int n_upd = 0, n_fp64 = 0;
+  long long n_draw_overflow = 0;
   int T_max = 0, K_max = 0;
 };
 
@@ -433,6 +434,13 @@ glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
     h->graphs.clear();
   }
   h->launch_opts = opts;
+  return GLMB_OK;
+}
+
+glmb_status glmb_set_wait_test(int mode, long long limit) {
+  if (mode != 0 && mode != GLMB_WAIT_TEST_SCAN && mode != GLMB_WAIT_TEST_GATE) return GLMB_E_INVALID;
+  if (mode != 0 && limit < 1) return GLMB_E_INVALID;
+  set_wait_test(WaitTest{mode, mode ? limit : 0});
   return GLMB_OK;
 }
 
@@ -808,12 +816,13 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   const int st_thr = h->tune.stage_threads;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
-  // draws: one thread per child, blocks of up to 256 draws of one parent
-  const int d_thr = h->tune.draw_threads > 0 ? h->tune.draw_threads : std::min(256, round_up(h_up, 32));
-  const int nsl = (h_up + d_thr - 1) / d_thr;
+  // draws: one thread per child over the frame's children in order
+  // (persistent grid)
+  const int d_thr = h->tune.draw_threads > 0 ? h->tune.draw_threads : 256;
   const int d_smem = expand_draw_smem(d_thr);
   const int d_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kDraw, d_thr, d_smem));
-  const int d_grid = p.fixed ? d_ctas * n_sm : (int)std::max(1LL, std::min((long long)h->H * nsl, (long long)d_ctas * n_sm));
+  const long long d_need = ((long long)h->H * h_up + d_thr - 1) / d_thr;
+  const int d_grid = p.fixed ? d_ctas * n_sm : (int)std::max(1LL, std::min(d_need, (long long)d_ctas * n_sm));
   // warp kernel: the overflow list, or every child
   const int w_thr = 32 * p.Gw;
   const int w_smem = expand_warp_smem(dz, 0, p.T, p.Gw);
@@ -1010,6 +1019,7 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
   h->n_pairs = h->h_scal[S_K];
   h->n_pairs_pregate = h->gate_mode_frame == GLMB_GATE_PRUNE ? (long long)h->h_scal[S_KFULL] : h->n_pairs;
   h->n_fp64 = (int)h->h_scal[S_FP64];
+  h->n_draw_overflow = h->plan.thread ? (long long)h->h_scal[S_REDO] : 0;
   const unsigned n_surv = cnt[0];
   if (n_surv == 0) return abandon(GLMB_E_NUMERIC, "no child has a finite weight above tau");
   const unsigned n_keep = h->h_scal[S_NKEEP], n_upd = h->h_scal[S_NUPD];
@@ -1143,7 +1153,10 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
   h->T_work = h->n_comp + n_births;
   h->M = M;
   Plan p;
-  if (!make_plan(h, true, h->alive_max + h->nb, h->K_est, h->M, p) &&
+  // while a wait test is set, frames run eagerly (no graph is captured with
+  // the test's launch settings)
+  const bool graphs_ok = wait_test().mode == 0;
+  if (!(graphs_ok && make_plan(h, true, h->alive_max + h->nb, h->K_est, h->M, p)) &&
       !make_plan(h, false, h->alive_max + h->nb, h->K_est, h->M, p)) {
     h->frame -= 1;
     return fail(h, GLMB_E_CAPACITY, "step: per-hypothesis table does not fit in shared memory");
@@ -1353,6 +1366,7 @@ glmb_status glmb_get_info(glmb_handle* h, glmb_info* info) {
   info->expand_plan_M = h->exp_plan[2];
   info->expand_threads = h->exp_plan[3];
   info->graph_capture_ms = h->capture_ms;
+  info->n_draw_overflow = h->n_draw_overflow;
   return GLMB_OK;
 }
 

@@ -42,11 +42,23 @@ constexpr int kSlmN = 5;   // cached m-only term parts per slot (m_ref - 2 .. m_
 struct Lay {
   int scal;
   int row, rowbl, seref, sqref, termref, hwref, gaind, lossd, deadd;
-  int rowrk, rca, rowoff, rowfill, roww0, rowthr0;
+  int rowrk, rch, rowoff, rowfill, roww0, rowthr0;
   int comp, dthr, logp, log1mp, mref, refnew, hph, slm, dpc;
   int cthr, ceidx, cw, ce, cq, cslot;
-  int ninfref, sln, gninf, lninf, dninf;
+  int ninfref, sln, gninf, lninf, dninf, srow;
   int total;
+};
+
+// Chunk of four detection rows with candidates, as the thread-per-child
+// draw reads it: head = (chunk index, bit b set when row 4 cc + b has a
+// candidate slot that can die, low and high words of the bloom of those
+// slots over the four rows), then the four rows' reference intervals
+// [lo, hi) of the 24-bit uniform (rows without candidates, or beyond the
+// detections: [0, 2^24)).
+struct RowChunk {
+  uint4 head;
+  uint4 lo;
+  uint4 hi;
 };
 
 struct Bump {
@@ -87,7 +99,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.lossd = b.take(8LL * M);
   L.deadd = b.take(8LL * T);
   L.rowrk = b.take(4LL * M);                // reference option's slot and pair
-  L.rca = b.take(4LL * ((M + 3) / 4 + 1));  // chunks of 4 rows with candidates
+  L.rch = b.take(48LL * ((M + 3) / 4 + 1)); // chunks of 4 rows with candidates (RowChunk)
   L.rowoff = b.take(4LL * (M + 1));
   L.rowfill = b.take(4LL * (M + 1));
   L.roww0 = b.take(4LL * M);
@@ -112,6 +124,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.gninf = b.take(K);
   L.lninf = b.take(M);
   L.dninf = b.take(T);
+  L.srow = b.take(T);                       // slot can die and is a candidate of some row
   L.total = b.off;
   return L;
 }
@@ -226,12 +239,14 @@ struct View {
   const unsigned long long* rowbl;
   const long long *seref, *sqref, *termref, *gaind, *lossd, *deadd;
   const unsigned long long* hwref;
-  const uint32_t *rowrk, *rca, *rowthr0, *comp, *dthr, *refnew, *dpc, *cthr;
+  const RowChunk* rch;
+  const uint32_t *rowrk, *rowthr0, *comp, *dthr, *refnew, *dpc, *cthr;
   const float *roww0, *logp, *log1mp, *hph, *slm, *cw, *ce, *cq;
   const int* mref;
   const uint16_t* cslot;
   const uint8_t* ninfref;
   const int8_t *sln, *gninf, *lninf, *dninf;
+  const uint8_t* srow;
 };
 
 __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) {
@@ -250,7 +265,8 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) 
   v.dninf = at<int8_t>(b, L.dninf);
   v.hwref = at<unsigned long long>(b, L.hwref);
   v.rowrk = at<uint32_t>(b, L.rowrk);
-  v.rca = at<uint32_t>(b, L.rca);
+  v.rch = at<RowChunk>(b, L.rch);
+  v.srow = at<uint8_t>(b, L.srow);
   v.rowthr0 = at<uint32_t>(b, L.rowthr0);
   v.comp = at<uint32_t>(b, L.comp);
   v.dthr = at<uint32_t>(b, L.dthr);
@@ -333,7 +349,8 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   long long* s_termref = at<long long>(sm, L.termref);
   unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
   uint32_t* s_rowrk = at<uint32_t>(sm, L.rowrk);
-  uint32_t* s_rca = at<uint32_t>(sm, L.rca);
+  RowChunk* s_rch = at<RowChunk>(sm, L.rch);
+  uint8_t* s_srow = at<uint8_t>(sm, L.srow);
   uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
   uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
   uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
@@ -429,6 +446,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   for (int t = tid; t < T; t += nthr) {
     const uint32_t c = s_comp[t];
     for (uint32_t j = pt.ptr[c], je = pt.ptr[c + 1]; j < je; ++j) atomicAdd(&s_rowfill[pt.meas[j]], 1u);
+    s_srow[t] = (pt.ptr[c + 1] > pt.ptr[c] && s_dthr[t] > 0u) ? 1 : 0;
   }
   __syncthreads();
   // exclusive scan of the row counts (single warp, serial carry over chunks)
@@ -517,11 +535,12 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       unsigned long long bl = 0ull;
       for (int j = 0; j < nc; ++j) {
         const float w = s_cw[off + j];
-        bl |= 1ull << (s_cslot[off + j] & 63);
+        const bool can_die = s_dthr[s_cslot[off + j]] > 0u;
+        if (can_die) bl |= 1ull << (s_cslot[off + j] & 63);
         cum += w;
         s_cthr[off + j] = (j == nc - 1) ? kOne24 : thr_of(cum / sum);
         if (w > best) { best = w; ref = j + 1; }
-        flag |= s_dthr[s_cslot[off + j]] > 0u;
+        flag |= can_die;
       }
       // row i: x = first candidate, y = count | may-die flag << 15 |
       // reference option << 16, [z, w) = the uniforms that pick the reference
@@ -574,13 +593,32 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       if (mask) s_dpc[atomicAdd(&sc.ndpc, 1)] = ((uint32_t)cc << 4) | mask;
     }
     for (int cc = tid; cc < ((M + 3) >> 2); cc += nthr) {
-      uint32_t mask = 0;
+      uint32_t mask = 0, dmask = 0;
+      unsigned long long bl = 0ull;
+      uint32_t lo[4], hi[4];
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int i = 4 * cc + b;
-        if (i < M && s_rowoff[i + 1] > s_rowoff[i]) mask |= 1u << b;
+        lo[b] = 0u;
+        hi[b] = kOne24;
+        if (i < M && s_rowoff[i + 1] > s_rowoff[i]) {
+          const uint4 R = s_row[i];
+          mask |= 1u << b;
+          lo[b] = R.z;
+          hi[b] = R.w;
+          if (R.y & 0x8000u) {
+            dmask |= 1u << b;
+            bl |= s_rowbl[i];
+          }
+        }
       }
-      if (mask) s_rca[atomicAdd(&sc.nrca, 1)] = ((uint32_t)cc << 4) | mask;
+      if (mask) {
+        RowChunk rc;
+        rc.head = make_uint4((uint32_t)cc, dmask, (uint32_t)bl, (uint32_t)(bl >> 32));
+        rc.lo = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        rc.hi = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        s_rch[atomicAdd(&sc.nrca, 1)] = rc;
+      }
     }
   }
   __syncthreads();
@@ -696,203 +734,204 @@ __global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
 }
 
 // ====================== draw: one thread per child ======================
-constexpr int kDrawDead = 16, kDrawDev = 24;   // per-thread list capacities (shared memory)
+// A child's deaths come first: one Philox4x32-10 call per chunk of four
+// slots that can die.  Then one categorical draw per detection row with
+// candidates, one call per chunk of four rows.  A row keeps its reference
+// option when its 24-bit uniform falls in the reference interval and none
+// of its candidates died -- nearly always -- so the common path reads one
+// 48-byte chunk record and tests four intervals per call.  The rest is out
+// of line: a row with a candidate that may have died is drawn among the
+// living, and a row that leaves the reference adds the staged change of a
+// single deviation.  Whether a slot died is answered by its bloom bit and,
+// when that is set, by regenerating the slot's death draw, so a thread
+// keeps no lists.  A child that meets a slot twice (two deviations moving
+// detections of one slot) needs that slot rescored exactly: such a child,
+// or one with more than kDrawMet met slots, goes to the warp kernel.
+constexpr int kDrawMet = 8;
 
-// Returns false when the child's deaths or deviations overflow its lists
-// (the child is then queued for the warp kernel).  s_dl / s_dv / s_ds: this
-// thread's lists of dead slots, deviations (row << 16 | option) and their
-// (reference slot + 1, new slot + 1), entry j at [j * stride].
-template <int DZ>
-__device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v, const int T, const int Kp,
-                                             const int h, const int n, const uint2 key, uint16_t* s_dl,
-                                             uint32_t* s_dv, uint32_t* s_ds, const int stride) {
+// Whether slot t of the child whose death stream is pd died.
+__device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, const PhiloxRun& pd, uint2 key,
+                                          uint32_t t) {
+  const uint4 r = philox_at(pd, t >> 2, key);
+  return (word_of(r, (int)(t & 3u)) >> 8) < dthr[t];
+}
+
+// Option of row i when its bloom meets the child's dead slots: -1 when no
+// candidate died (the row is drawn as usual), -2 when no option is left,
+// else the option drawn in proportion to the living candidates' weights
+// (clutter first), in the FP32 arithmetic of the warp kernel.
+__device__ __noinline__ int row_among_living(const uint4 R, const uint16_t* __restrict__ cslot,
+                                             const float* __restrict__ cw, float w0,
+                                             const uint32_t* __restrict__ dthr, const PhiloxRun pd, const uint2 key,
+                                             const unsigned long long bloom, const uint32_t k) {
+  const uint32_t off = R.x;
+  const int nc = (int)(R.y & 0x7FFFu);
+  auto is_dead = [&](int j) -> bool {
+    const uint32_t t = cslot[off + j];
+    return ((bloom >> (t & 63u)) & 1ull) && slot_died(dthr, pd, key, t);
+  };
+  uint32_t dm = 0u;
+  bool any = false;
+  for (int j = 0; j < nc; ++j)
+    if (is_dead(j)) {
+      any = true;
+      if (j < 32) dm |= 1u << j;
+    }
+  if (!any) return -1;
+  auto dead_j = [&](int j) -> bool { return j < 32 ? ((dm >> j) & 1u) != 0u : is_dead(j); };
+  float sum = w0;
+  for (int j = 0; j < nc; ++j)
+    if (!dead_j(j)) sum += cw[off + j];
+  if (!(sum > 0.f)) return -2;
+  const float xk = (float)k * 5.9604644775390625e-8f * sum;
+  float cum = w0;
+  int last = w0 > 0.f ? 0 : -1;
+  int opt = -1;
+  if (w0 > 0.f && xk < cum) opt = 0;
+  for (int j = 0; j < nc; ++j) {
+    if (dead_j(j)) continue;
+    const float w = cw[off + j];
+    if (!(w > 0.f)) continue;
+    cum += w;
+    last = j + 1;
+    if (opt < 0 && xk < cum) opt = j + 1;
+  }
+  if (opt < 0) opt = last < 0 ? 0 : last;
+  return opt;
+}
+
+// Score change of row i moving from its reference option to opt: the
+// staged single-deviation changes of the slots it leaves and joins (a dead
+// reference slot is not met: its change is the death's).  met = (slot left
+// + 1) << 16 | (slot joined + 1), 0 for clutter or a dead slot.
+struct RowMove {
+  long long d;
+  unsigned long long hw;
+  int ninf, clut;
+  uint32_t met;
+};
+
+__device__ __noinline__ RowMove row_move(const uint4 R, const int i, const int opt, const uint16_t* __restrict__ cslot,
+                                         const long long* __restrict__ lossd, const long long* __restrict__ gaind,
+                                         const int8_t* __restrict__ lninf, const int8_t* __restrict__ gninf,
+                                         const uint32_t* __restrict__ dthr, const PhiloxRun pd, const uint2 key,
+                                         const unsigned long long bloom) {
+  const int ref = (int)(R.y >> 16);
+  uint32_t rs1 = ref > 0 ? (uint32_t)cslot[R.x + ref - 1] + 1u : 0u;
+  const uint32_t ns1 = opt > 0 ? (uint32_t)cslot[R.x + opt - 1] + 1u : 0u;
+  RowMove m;
+  m.hw = row_key(i, (int)ns1) - row_key(i, (int)rs1);
+  m.clut = (opt == 0) - (ref == 0);
+  m.d = 0;
+  m.ninf = 0;
+  if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(dthr, pd, key, rs1 - 1u)) rs1 = 0u;
+  if (rs1) {
+    m.d += lossd[i];
+    m.ninf += lninf[i];
+  }
+  if (ns1) {
+    m.d += gaind[R.x + opt - 1];
+    m.ninf += gninf[R.x + opt - 1];
+  }
+  m.met = (rs1 << 16) | ns1;
+  return m;
+}
+
+// Option of row i for uniform k when every candidate is alive: clutter
+// below the clutter threshold, else the first candidate whose cumulative
+// threshold exceeds k.
+__device__ __forceinline__ int row_option(const uint4 R, const uint32_t* __restrict__ cthr, uint32_t thr0,
+                                          uint32_t k) {
+  if (k < thr0) return 0;
+  const int nc = (int)(R.y & 0x7FFFu);
+  int j = 0;
+  while (j < nc - 1 && k >= cthr[R.x + j]) ++j;
+  return j + 1;
+}
+
+// Draws child n of the parent staged in v.  Returns false when the child
+// must be drawn by the warp kernel (a slot met twice, or more met slots
+// than the register list holds).
+__device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v, const int T, const int h,
+                                             const int n, const uint2 key) {
   const Model& md = a.md;
   const Scal& sc = *v.sc;
   const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
-  const int ndpc = sc.ndpc, nrca = sc.nrca;
+  const PhiloxRun pd = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n, key);
   unsigned long long bloom = 0ull, hsh = 0ull;
   long long delta = 0;
-  int nd = 0, ndv = 0, dclut = 0, dninf = 0;
+  int nd = 0, dclut = 0, dninf = 0;
   bool bad_row = false;
   // stage 1: deaths (a dead slot's change is its dead term)
+  const int ndpc = sc.ndpc;
   for (int x = 0; x < ndpc; ++x) {
     const uint32_t ent = v.dpc[x];
     const uint32_t cc = ent >> 4, mask = ent & 15u;
-    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
+    const uint4 r = philox_at(pd, cc, key);
     const uint4 th = *reinterpret_cast<const uint4*>(v.dthr + 4 * cc);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const uint32_t thb = b == 0 ? th.x : b == 1 ? th.y : b == 2 ? th.z : th.w;
       if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < thb) {
         const uint32_t t = 4u * cc + (uint32_t)b;
-        if (nd < kDrawDead) s_dl[nd * stride] = (uint16_t)t;
         ++nd;
-        bloom |= 1ull << (t & 63u);
         hsh += dead_key((int)t);
         delta += v.deadd[t];
         dninf += v.dninf[t];
+        if (v.srow[t]) bloom |= 1ull << (t & 63u);
       }
     }
   }
-  const int ndc = min(nd, kDrawDead);
-  auto dead = [&](uint32_t t) -> bool {
-    if (!((bloom >> (t & 63u)) & 1ull)) return false;
-    for (int j = 0; j < ndc; ++j)
-      if (s_dl[j * stride] == t) return true;
-    return false;
+  // stage 2: one categorical draw per detection row with candidates; a row
+  // that leaves the reference option adds its change at once
+  const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, key);
+  uint32_t met[kDrawMet / 2] = {0u, 0u, 0u, 0u};
+  int nmet = 0;
+  bool twice = false;
+  auto meet = [&](uint32_t t1) {
+#pragma unroll
+    for (int q = 0; q < kDrawMet; ++q)
+      if (q < nmet && ((met[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) == t1) twice = true;
+#pragma unroll
+    for (int q = 0; q < kDrawMet; ++q)
+      if (q == nmet) met[q >> 1] |= t1 << (16 * (q & 1));
+    ++nmet;
   };
-  // stage 2: one categorical draw per detection row with candidates; rows
-  // that leave the reference option are only recorded here
+  const int nrca = sc.nrca;
   for (int x = 0; x < nrca; ++x) {
-    const uint32_t ent = v.rca[x];
-    const uint32_t cc = ent >> 4, mask = ent & 15u;
-    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, cc), key);
+    const RowChunk& rc = v.rch[x];
+    const uint4 hd = rc.head, lo = rc.lo, hi = rc.hi;
+    const uint4 r = philox_at(pr, hd.x, key);
+    const uint32_t hit = ((((unsigned long long)hd.w << 32) | hd.z) & bloom) ? hd.y : 0u;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      if (!((mask >> b) & 1u)) continue;
-      const int i = 4 * (int)cc + b;
-      const uint4 R = v.row[i];
       const uint32_t k = word_of(r, b) >> 8;
-      const uint32_t off = R.x;
-      const int nc = (int)(R.y & 0x7FFFu);
-      int opt;
-      // dead candidates of this row, bit j (rows beyond 32 candidates test
-      // the rest one by one)
-      uint32_t dm = 0u;
-      if (nd > 0 && (R.y & 0x8000u) && (v.rowbl[i] & bloom))
-        for (int j = 0; j < nc; ++j)
-          if (dead(v.cslot[off + j])) dm |= 1u << min(j, 31);
-      if (dm) {
-        // some candidates are dead: draw among the living in proportion to
-        // their weights (clutter first)
-        auto is_dead = [&](int j) -> bool {
-          return j < 31 ? ((dm >> j) & 1u) != 0u : dead(v.cslot[off + j]);
-        };
-        const float w0 = md.kappa_zero ? 0.f : v.roww0[i];
-        float sum = w0;
-        for (int j = 0; j < nc; ++j)
-          if (!is_dead(j)) sum += v.cw[off + j];
-        if (!(sum > 0.f)) {
+      const uint32_t l = word_of(lo, b), u = word_of(hi, b);
+      const bool in_ref = k - l < u - l;
+      if (in_ref && !((hit >> b) & 1u)) continue;   // the reference option
+      const int i = 4 * (int)hd.x + b;
+      const uint4 R = v.row[i];
+      int opt = -1;
+      if (((hit >> b) & 1u) && (v.rowbl[i] & bloom)) {
+        opt = row_among_living(R, v.cslot, v.cw, md.kappa_zero ? 0.f : v.roww0[i], v.dthr, pd, key, bloom, k);
+        if (opt == -2) {
           bad_row = true;
           opt = 0;
-        } else {
-          const float xk = (float)k * 5.9604644775390625e-8f * sum;
-          float cum = w0;
-          int last = w0 > 0.f ? 0 : -1;
-          opt = -1;
-          if (w0 > 0.f && xk < cum) opt = 0;
-          for (int j = 0; j < nc; ++j) {
-            if (is_dead(j)) continue;
-            const float w = v.cw[off + j];
-            if (!(w > 0.f)) continue;
-            cum += w;
-            last = j + 1;
-            if (opt < 0 && xk < cum) opt = j + 1;
-          }
-          if (opt < 0) opt = last < 0 ? 0 : last;
         }
-      } else if (k - R.z < R.w - R.z) {
-        continue;   // the reference option
-      } else if (k < v.rowthr0[i]) {
-        opt = 0;
-      } else {
-        int j = 0;
-        while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
-        opt = j + 1;
       }
-      if (opt != (int)(R.y >> 16)) {
-        if (ndv < kDrawDev) s_dv[ndv * stride] = ((uint32_t)i << 16) | (uint32_t)opt;
-        ++ndv;
+      if (opt == -1) {
+        if (in_ref) continue;
+        opt = row_option(R, v.cthr, v.rowthr0[i], k);
       }
-    }
-  }
-  if (nd > kDrawDead || ndv > kDrawDev) return false;
-  // stage 3: each deviation moves one detection from its reference slot to
-  // its new slot; a slot met once changes by the staged single-deviation
-  // change (a dead reference slot is not met: its change is the death's)
-  unsigned long long tb0 = 0ull, tb1 = 0ull;   // slots met (bit slot mod 128)
-  bool twice = false;
-  auto meet = [&](uint32_t t) {
-    const unsigned long long bit = 1ull << (t & 63u);
-    unsigned long long& w = (t & 64u) ? tb1 : tb0;
-    twice |= (w & bit) != 0ull;
-    w |= bit;
-  };
-  for (int q = 0; q < ndv; ++q) {
-    const uint32_t e = s_dv[q * stride];
-    const int i = (int)(e >> 16), opt = (int)(e & 0xFFFFu);
-    const uint4 R = v.row[i];
-    const int ref = (int)(R.y >> 16);
-    uint32_t rs1 = ref > 0 ? (uint32_t)v.cslot[R.x + ref - 1] + 1u : 0u;
-    const uint32_t ns1 = opt > 0 ? (uint32_t)v.cslot[R.x + opt - 1] + 1u : 0u;
-    hsh += row_key(i, (int)ns1) - row_key(i, (int)rs1);
-    dclut += (opt == 0) - (ref == 0);
-    if (rs1 && dead(rs1 - 1u)) rs1 = 0u;
-    if (rs1) {
-      meet(rs1 - 1u);
-      delta += v.lossd[i];
-      dninf += v.lninf[i];
-    }
-    if (ns1) {
-      meet(ns1 - 1u);
-      delta += v.gaind[R.x + opt - 1];
-      dninf += v.gninf[R.x + opt - 1];
-    }
-    s_ds[q * stride] = (rs1 << 16) | ns1;
-  }
-  if (twice) {
-    // a slot met more than once (or two sharing a bit): its change is the
-    // exact rescoring with all deviations that move it, in place of the sum
-    // of their single changes
-    for (int w = 0; w < 2 * ndv; ++w) {
-      const uint32_t sw = s_ds[(w >> 1) * stride];
-      const uint32_t sp = (w & 1) ? (sw & 0xFFFFu) : (sw >> 16);
-      if (sp == 0u) continue;
-      int cnt = 0;
-      bool first = true;
-      for (int w2 = 0; w2 < 2 * ndv; ++w2) {
-        const uint32_t s2 = s_ds[(w2 >> 1) * stride];
-        if (((w2 & 1) ? (s2 & 0xFFFFu) : (s2 >> 16)) != sp) continue;
-        ++cnt;
-        if (w2 < w) first = false;
-      }
-      if (cnt < 2 || !first) continue;
-      int dcnt = 0, sninf = 0;
-      long long dse[DZ], dsq = 0, single = 0;
-#pragma unroll
-      for (int d = 0; d < DZ; ++d) dse[d] = 0;
-      for (int w2 = w; w2 < 2 * ndv; ++w2) {
-        const uint32_t s2 = s_ds[(w2 >> 1) * stride];
-        if (((w2 & 1) ? (s2 & 0xFFFFu) : (s2 >> 16)) != sp) continue;
-        const uint32_t e2 = s_dv[(w2 >> 1) * stride];
-        const int i2 = (int)(e2 >> 16);
-        const uint4 R2 = v.row[i2];
-        uint32_t pos;
-        int sg;
-        if (w2 & 1) {
-          pos = R2.x + (e2 & 0xFFFFu) - 1u;
-          sg = 1;
-          single += v.gaind[pos];
-          sninf += v.gninf[pos];
-        } else {
-          pos = R2.x + (R2.y >> 16) - 1u;
-          sg = -1;
-          single += v.lossd[i2];
-          sninf += v.lninf[i2];
-        }
-        dcnt += sg;
-#pragma unroll
-        for (int d = 0; d < DZ; ++d) dse[d] += sg * fx_of(v.ce[d * Kp + pos]);
-        dsq += sg * fx_of(v.cq[pos]);
-      }
-      const int t = (int)sp - 1;
-      long long se[DZ];
-#pragma unroll
-      for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + dse[d];
-      int ninf;
-      const long long term = slot_term<DZ>(md, v, T, t, v.mref[t] + dcnt, dcnt, se, v.sqref[t] + dsq, ninf);
-      delta += term - v.termref[t] - single;
-      dninf += ninf - (int)v.ninfref[t] - sninf;
+      if (opt == (int)(R.y >> 16)) continue;
+      const RowMove m = row_move(R, i, opt, v.cslot, v.lossd, v.gaind, v.lninf, v.gninf, v.dthr, pd, key, bloom);
+      hsh += m.hw;
+      dclut += m.clut;
+      delta += m.d;
+      dninf += m.ninf;
+      if (m.met >> 16) meet(m.met >> 16);
+      if (m.met & 0xFFFFu) meet(m.met & 0xFFFFu);
+      if (twice || nmet > kDrawMet) return false;
     }
   }
   const long long score = sc.ref_score + delta + (md.kappa_zero ? 0LL : (long long)dclut * md.fx_log_kappa);
@@ -906,33 +945,28 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v,
   return true;
 }
 
-int expand_draw_smem(int threads) { return threads * (2 * kDrawDead + 8 * kDrawDev); }
+int expand_draw_smem(int) { return 0; }
 
-// Persistent over jobs (parent, slice of blockDim.x draws); no block-level
-// synchronisation: every thread draws its own child from the parent's image.
+// Persistent over the children of the frame, one thread per child in the
+// order parent * h_up + draw (a warp holds 32 consecutive children, of at
+// most two parents when h_up >= 32); no block-level synchronisation.
 template <int DZ>
-__global__ void __launch_bounds__(256) draw_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256, 4) draw_kernel(const ExpandArgs a) {
   pdl_enter();
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int stride = blockDim.x;
-  uint32_t* s_dv = reinterpret_cast<uint32_t*>(sm) + threadIdx.x;
-  uint32_t* s_ds = reinterpret_cast<uint32_t*>(sm + 4 * kDrawDev * stride) + threadIdx.x;
-  uint16_t* s_dl = reinterpret_cast<uint16_t*>(sm + 8 * kDrawDev * stride) + threadIdx.x;
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H, HU = a.md.h_up;
   const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
-  const int nsl = (HU + (int)blockDim.x - 1) / (int)blockDim.x;
   // a failed table or staging (the frame is redone or abandoned): the
   // images may be stale, so nothing is drawn
   if (*(volatile const unsigned*)a.err & kErrFatal) return;
-  for (int job = blockIdx.x; job < H * nsl; job += gridDim.x) {
-    const int h = job / nsl;
-    const int n = (job % nsl) * (int)blockDim.x + (int)threadIdx.x;
-    const unsigned char* img = a.img + (size_t)h * a.img_stride;
-    const View v = make_view(img, L);
-    if (n >= HU || v.sc->bad) continue;
-    if (!thread_child<DZ>(a, v, v.sc->T, a.K_max, h, n, key, s_dl, s_dv, s_ds, stride))
-      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)(h * HU + n);
+  const long long total = (long long)H * HU;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(j / HU);
+    const int n = (int)(j - (long long)h * HU);
+    const View v = make_view(a.img + (size_t)h * a.img_stride, L);
+    if (v.sc->bad) continue;
+    if (!thread_child(a, v, v.sc->T, h, n, key)) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)j;
   }
 }
 
