@@ -180,7 +180,8 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
  * planned for (from earlier frames) makes it redo the expansion with the
  * frame's exact maxima before it returns, so the children are final.
  * Errors: GLMB_E_STATE (no predict), GLMB_E_INVALID (M < 0, NaN/Inf in a
- * host Z), GLMB_E_CAPACITY (M beyond max_meas, or a per-hypothesis table
+ * host Z, a device Z that is not device or managed memory of the handle's
+ * GPU or not 4-byte aligned), GLMB_E_CAPACITY (M beyond max_meas, or a per-hypothesis table
  * that cannot fit in shared memory).  Errors found on the device (NaN/Inf in
  * a device Z, gated pairs beyond max_pairs) are returned by glmb_prune. */
 glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device);

@@ -79,8 +79,8 @@ __device__ __forceinline__ void fence_async_smem() {
 }
 
 // waits for the mbarrier phase with the given parity; gives up after
-// about a second of SM clock (returns false)
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// `limit` SM clock cycles, about a second by default (returns false)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kGateWaitLimit) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -91,7 +91,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 2000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -226,8 +226,9 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t a, uint32_t b,
 }
 
 // every thread waits for the layer; a time-out anywhere aborts the CTA
-__device__ __forceinline__ bool layer_wait(uint32_t mbar, uint32_t& parity, int* flag) {
-  const bool ok = mbar_wait(mbar, parity);
+__device__ __forceinline__ bool layer_wait(uint32_t mbar, uint32_t& parity, int* flag,
+                                           long long limit = kGateWaitLimit) {
+  const bool ok = mbar_wait(mbar, parity, limit);
   parity ^= 1u;
   if (!ok) atomicOr(flag, 1);
   fence_after();
@@ -314,6 +315,8 @@ struct GateFwdArgs {
   uint8_t* keep;
   float* logit;
   unsigned* err;
+  long long wait_limit;   // SM clock cycles a completion wait may take
+  int skip_first_mma;     // failure-detection test: CTA 0 issues no MMA for its first tile
 };
 
 template <bool kTable>
@@ -366,21 +369,22 @@ __global__ void __launch_bounds__(kTile) gate_forward_kernel(GateFwdArgs g) {
     write_input(sm + FLay::A0, m, f, valid, cst);
     fence_async_smem();
     __syncthreads();
-    layer_mma(tmem, a0, smem_u32(sm + FLay::W1), 1, mbar);
-    if (!(ok = layer_wait(mbar, parity, flag))) break;
+    if (!(g.skip_first_mma && blockIdx.x == 0 && tile == blockIdx.x))
+      layer_mma(tmem, a0, smem_u32(sm + FLay::W1), 1, mbar);
+    if (!(ok = layer_wait(mbar, parity, flag, g.wait_limit))) break;
     hidden_epilogue(trow, cst + kCB1, nullptr, sm + FLay::H1, m);
     fence_before();
     fence_async_smem();
     __syncthreads();
     layer_mma(tmem, h1, smem_u32(sm + FLay::W2), 4, mbar);
-    if (!(ok = layer_wait(mbar, parity, flag))) break;
+    if (!(ok = layer_wait(mbar, parity, flag, g.wait_limit))) break;
     // layer 2's activations overwrite its own operand once the MMA is done
     hidden_epilogue(trow, cst + kCB2, nullptr, sm + FLay::H1, m);
     fence_before();
     fence_async_smem();
     __syncthreads();
     layer_mma(tmem, h1, smem_u32(sm + FLay::W3), 4, mbar);
-    if (!(ok = layer_wait(mbar, parity, flag))) break;
+    if (!(ok = layer_wait(mbar, parity, flag, g.wait_limit))) break;
     float z = cst[kCB4];
 #pragma unroll 1
     for (int c0 = 0; c0 < kHid; c0 += 16) {
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(kTile) gate_forward_kernel(GateFwdArgs g) {
   }
   if (!ok) {
     // an MMA may still be in flight: give it one more bounded wait
-    mbar_wait(mbar, parity ^ 1u);
+    mbar_wait(mbar, parity ^ 1u, g.wait_limit);
     if (m == 0) atomicOr(g.err, kErrGate);
   }
   fence_before();
@@ -786,6 +790,9 @@ void launch_gate_forward_rows(const float* P, const float* X, long long n, float
   g.n = n;
   g.logit = logit;
   g.err = err;
+  const WaitTest wt = wait_test();
+  g.wait_limit = wt.mode == kWaitTestGate ? wt.limit : kGateWaitLimit;
+  g.skip_first_mma = wt.mode == kWaitTestGate ? 1 : 0;
   launch_k(gate_forward_kernel<false>, grid, kTile, FLay::TOTAL, s, g);
 }
 
@@ -803,6 +810,9 @@ void launch_gate_forward_table(const float* P, float thr, const Model& md, const
   g.keep = keep;
   g.logit = logit;
   g.err = err;
+  const WaitTest wt = wait_test();
+  g.wait_limit = wt.mode == kWaitTestGate ? wt.limit : kGateWaitLimit;
+  g.skip_first_mma = wt.mode == kWaitTestGate ? 1 : 0;
   launch_k(gate_forward_kernel<true>, grid, kTile, FLay::TOTAL, s, g);
 }
 

@@ -688,6 +688,20 @@ glmb_status stage_detections(glmb_handle* h, const float* Z, int M, int z_is_dev
       if (!std::isfinite(Z[k])) return fail(h, GLMB_E_INVALID, "update: non-finite detection");
   if (M > 0) {
     if (z_is_device) {
+      // the kernels read device detections with global-memory loads: the
+      // buffer must be device (or managed) memory of this handle's GPU,
+      // 4-byte aligned
+      cudaPointerAttributes pa{};
+      int dev = -1;
+      if (cudaPointerGetAttributes(&pa, Z) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, GLMB_E_INVALID, "update: detections are not device memory");
+      }
+      CU(cudaGetDevice(&dev));
+      if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+        return fail(h, GLMB_E_INVALID, "update: detections are not device memory of the handle's GPU");
+      if ((reinterpret_cast<uintptr_t>(Z) & 3u) != 0u)
+        return fail(h, GLMB_E_INVALID, "update: device detections not 4-byte aligned");
       h->z_dev = Z;
     } else {
       std::memcpy(h->h_Z, Z, (size_t)M * dz * sizeof(float));

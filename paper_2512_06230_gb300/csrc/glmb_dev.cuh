@@ -174,6 +174,9 @@ __device__ __forceinline__ uint4 philox_at(const PhiloxRun& p, uint32_t cc, uint
   const uint32_t y0 = hiD ^ p.y0;
   const uint32_t hiE = __umulhi(M0, y0), loE = M0 * y0;     // round 3, first product
   uint4 c = make_uint4(loD ^ p.z0, p.z1, hiE ^ p.z2, loE);
+  // the round keys are formed here, per call: held across a caller's loop
+  // they would take 14 registers
+  asm volatile("" : "+r"(k.x), "+r"(k.y));
   k.x += 3u * 0x9E3779B9u;
   k.y += 3u * 0xBB67AE85u;
 #pragma unroll

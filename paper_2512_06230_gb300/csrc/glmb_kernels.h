@@ -61,6 +61,22 @@ void scan_u64(const unsigned long long* in, unsigned long long* out, const int* 
               unsigned long long* tmp, long long tmp_cap, unsigned* err, cudaStream_t s);
 
 // ---- expansion / materialisation (kernels_expand.cu) ----
+// Test hook of the bounded device-side waits (glmb_set_wait_test): mode 0
+// runs with the normal limits; kWaitTestScan makes the first tile of every
+// one-pass scan withhold its prefix, kWaitTestGate makes the gate's forward
+// pass issue no tensor-core work for the first tile of its CTA 0, and in
+// both the wait gives up after `limit` (polls for the scan, SM clock cycles
+// for the gate).
+struct WaitTest {
+  int mode;
+  long long limit;
+};
+constexpr int kWaitTestScan = 1, kWaitTestGate = 2;
+constexpr long long kScanSpinLimit = 1LL << 22;        // look-back polls
+constexpr long long kGateWaitLimit = 2000000000LL;     // SM clock cycles (about a second)
+WaitTest wait_test();
+void set_wait_test(WaitTest w);
+
 struct ExpandArgs {
   Model md;
   CompTable ct;           // working (predicted) table

@@ -739,15 +739,17 @@ __global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
 // candidates, one call per chunk of four rows.  A row keeps its reference
 // option when its 24-bit uniform falls in the reference interval and none
 // of its candidates died -- nearly always -- so the common path reads one
-// 48-byte chunk record and tests four intervals per call.  The rest is out
-// of line: a row with a candidate that may have died is drawn among the
-// living, and a row that leaves the reference adds the staged change of a
-// single deviation.  Whether a slot died is answered by its bloom bit and,
-// when that is set, by regenerating the slot's death draw, so a thread
-// keeps no lists.  A child that meets a slot twice (two deviations moving
-// detections of one slot) needs that slot rescored exactly: such a child,
-// or one with more than kDrawMet met slots, goes to the warp kernel.
-constexpr int kDrawMet = 8;
+// 48-byte chunk record and tests four intervals per call, and holds only
+// the chunk loop's state in registers.  Everything else about a row is out
+// of line (row_slow): a row with a candidate that may have died is drawn
+// among the living, and a row that leaves the reference adds the staged
+// change of a single deviation.  Whether a slot died is answered by its
+// bloom bit and, when that is set, by regenerating the slot's death draw,
+// so a thread keeps no lists.  The slots a child's deviations meet are
+// kept as a 64-bit mask (bit slot mod 64): a child whose deviations meet a
+// slot twice needs that slot rescored exactly, so a child whose mask bit is
+// already set (a slot met twice, or two slots sharing a bit) goes to the
+// warp kernel.
 
 // Whether slot t of the child whose death stream is pd died.
 __device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, const PhiloxRun& pd, uint2 key,
@@ -756,182 +758,234 @@ __device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, con
   return (word_of(r, (int)(t & 3u)) >> 8) < dthr[t];
 }
 
-// Option of row i when its bloom meets the child's dead slots: -1 when no
-// candidate died (the row is drawn as usual), -2 when no option is left,
-// else the option drawn in proportion to the living candidates' weights
-// (clutter first), in the FP32 arithmetic of the warp kernel.
-__device__ __noinline__ int row_among_living(const uint4 R, const uint16_t* __restrict__ cslot,
-                                             const float* __restrict__ cw, float w0,
-                                             const uint32_t* __restrict__ dthr, const PhiloxRun pd, const uint2 key,
-                                             const unsigned long long bloom, const uint32_t k) {
-  const uint32_t off = R.x;
-  const int nc = (int)(R.y & 0x7FFFu);
-  auto is_dead = [&](int j) -> bool {
-    const uint32_t t = cslot[off + j];
-    return ((bloom >> (t & 63u)) & 1ull) && slot_died(dthr, pd, key, t);
-  };
-  uint32_t dm = 0u;
-  bool any = false;
-  for (int j = 0; j < nc; ++j)
-    if (is_dead(j)) {
-      any = true;
-      if (j < 32) dm |= 1u << j;
-    }
-  if (!any) return -1;
-  auto dead_j = [&](int j) -> bool { return j < 32 ? ((dm >> j) & 1u) != 0u : is_dead(j); };
-  float sum = w0;
-  for (int j = 0; j < nc; ++j)
-    if (!dead_j(j)) sum += cw[off + j];
-  if (!(sum > 0.f)) return -2;
-  const float xk = (float)k * 5.9604644775390625e-8f * sum;
-  float cum = w0;
-  int last = w0 > 0.f ? 0 : -1;
-  int opt = -1;
-  if (w0 > 0.f && xk < cum) opt = 0;
-  for (int j = 0; j < nc; ++j) {
-    if (dead_j(j)) continue;
-    const float w = cw[off + j];
-    if (!(w > 0.f)) continue;
-    cum += w;
-    last = j + 1;
-    if (opt < 0 && xk < cum) opt = j + 1;
-  }
-  if (opt < 0) opt = last < 0 ? 0 : last;
-  return opt;
-}
-
-// Score change of row i moving from its reference option to opt: the
-// staged single-deviation changes of the slots it leaves and joins (a dead
-// reference slot is not met: its change is the death's).  met = (slot left
-// + 1) << 16 | (slot joined + 1), 0 for clutter or a dead slot.
-struct RowMove {
+// The outcome of one detection row that needs more than the interval test:
+// moved = the row left its reference option (d, hw, ninf, clut: its score,
+// key, infinite-term and clutter-count changes; met = (slot left + 1) << 16
+// | (slot joined + 1), 0 for clutter or a dead slot), bad = no option left.
+struct RowOut {
   long long d;
   unsigned long long hw;
   int ninf, clut;
   uint32_t met;
+  int moved, bad;
 };
 
-__device__ __noinline__ RowMove row_move(const uint4 R, const int i, const int opt, const uint16_t* __restrict__ cslot,
-                                         const long long* __restrict__ lossd, const long long* __restrict__ gaind,
-                                         const int8_t* __restrict__ lninf, const int8_t* __restrict__ gninf,
-                                         const uint32_t* __restrict__ dthr, const PhiloxRun pd, const uint2 key,
-                                         const unsigned long long bloom) {
-  const int ref = (int)(R.y >> 16);
-  uint32_t rs1 = ref > 0 ? (uint32_t)cslot[R.x + ref - 1] + 1u : 0u;
-  const uint32_t ns1 = opt > 0 ? (uint32_t)cslot[R.x + opt - 1] + 1u : 0u;
-  RowMove m;
-  m.hw = row_key(i, (int)ns1) - row_key(i, (int)rs1);
-  m.clut = (opt == 0) - (ref == 0);
-  m.d = 0;
-  m.ninf = 0;
-  if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(dthr, pd, key, rs1 - 1u)) rs1 = 0u;
-  if (rs1) {
-    m.d += lossd[i];
-    m.ninf += lninf[i];
-  }
-  if (ns1) {
-    m.d += gaind[R.x + opt - 1];
-    m.ninf += gninf[R.x + opt - 1];
-  }
-  m.met = (rs1 << 16) | ns1;
-  return m;
-}
-
-// Option of row i for uniform k when every candidate is alive: clutter
-// below the clutter threshold, else the first candidate whose cumulative
-// threshold exceeds k.
-__device__ __forceinline__ int row_option(const uint4 R, const uint32_t* __restrict__ cthr, uint32_t thr0,
-                                          uint32_t k) {
-  if (k < thr0) return 0;
-  const int nc = (int)(R.y & 0x7FFFu);
-  int j = 0;
-  while (j < nc - 1 && k >= cthr[R.x + j]) ++j;
-  return j + 1;
-}
-
-// Draws child n of the parent staged in v.  Returns false when the child
-// must be drawn by the warp kernel (a slot met twice, or more met slots
-// than the register list holds).
-__device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v, const int T, const int h,
-                                             const int n, const uint2 key) {
-  const Model& md = a.md;
+// Row i of the parent staged at img (plan sizes Tp, Kp, Mp) for child n and
+// uniform k.  A row whose bloom meets the child's dead slots is drawn among
+// the living candidates in proportion to their weights (clutter first), in
+// the FP32 arithmetic of the warp kernel; otherwise its option is the first
+// whose cumulative threshold exceeds k.
+template <int DZ>
+__device__ __noinline__ RowOut row_slow(const unsigned char* img, const int Tp, const int Kp, const int Mp,
+                                        const int i, const uint32_t k, const bool may_hit,
+                                        const unsigned long long bloom, const uint32_t n, const uint2 key,
+                                        const int kappa_zero) {
+  const Lay L = make_lay(DZ, Tp, Kp, Mp);
+  const View v = make_view(img, L);
   const Scal& sc = *v.sc;
-  const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
-  const PhiloxRun pd = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n, key);
-  unsigned long long bloom = 0ull, hsh = 0ull;
-  long long delta = 0;
-  int nd = 0, dclut = 0, dninf = 0;
-  bool bad_row = false;
-  // stage 1: deaths (a dead slot's change is its dead term)
-  const int ndpc = sc.ndpc;
-  for (int x = 0; x < ndpc; ++x) {
-    const uint32_t ent = v.dpc[x];
-    const uint32_t cc = ent >> 4, mask = ent & 15u;
-    const uint4 r = philox_at(pd, cc, key);
-    const uint4 th = *reinterpret_cast<const uint4*>(v.dthr + 4 * cc);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const uint32_t thb = b == 0 ? th.x : b == 1 ? th.y : b == 2 ? th.z : th.w;
-      if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < thb) {
-        const uint32_t t = 4u * cc + (uint32_t)b;
-        ++nd;
-        hsh += dead_key((int)t);
-        delta += v.deadd[t];
-        dninf += v.dninf[t];
-        if (v.srow[t]) bloom |= 1ull << (t & 63u);
+  const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * n, key);
+  const uint4 R = v.row[i];
+  const uint32_t off = R.x;
+  const int nc = (int)(R.y & 0x7FFFu);
+  const int ref = (int)(R.y >> 16);
+  RowOut o;
+  o.d = 0;
+  o.hw = 0ull;
+  o.ninf = o.clut = 0;
+  o.met = 0u;
+  o.moved = o.bad = 0;
+  int opt = -1;
+  if (may_hit && (v.rowbl[i] & bloom)) {
+    auto is_dead = [&](int j) -> bool {
+      const uint32_t t = v.cslot[off + j];
+      return ((bloom >> (t & 63u)) & 1ull) && slot_died(v.dthr, pd, key, t);
+    };
+    uint32_t dm = 0u;
+    bool any = false;
+    for (int j = 0; j < nc; ++j)
+      if (is_dead(j)) {
+        any = true;
+        if (j < 32) dm |= 1u << j;
+      }
+    if (any) {
+      auto dead_j = [&](int j) -> bool { return j < 32 ? ((dm >> j) & 1u) != 0u : is_dead(j); };
+      const float w0 = kappa_zero ? 0.f : v.roww0[i];
+      float sum = w0;
+      for (int j = 0; j < nc; ++j)
+        if (!dead_j(j)) sum += v.cw[off + j];
+      if (!(sum > 0.f)) {
+        o.bad = 1;
+        opt = 0;
+      } else {
+        const float xk = (float)k * 5.9604644775390625e-8f * sum;
+        float cum = w0;
+        int last = w0 > 0.f ? 0 : -1;
+        if (w0 > 0.f && xk < cum) opt = 0;
+        for (int j = 0; j < nc; ++j) {
+          if (dead_j(j)) continue;
+          const float w = v.cw[off + j];
+          if (!(w > 0.f)) continue;
+          cum += w;
+          last = j + 1;
+          if (opt < 0 && xk < cum) opt = j + 1;
+        }
+        if (opt < 0) opt = last < 0 ? 0 : last;
       }
     }
   }
-  // stage 2: one categorical draw per detection row with candidates; a row
-  // that leaves the reference option adds its change at once
-  const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, key);
-  uint32_t met[kDrawMet / 2] = {0u, 0u, 0u, 0u};
-  int nmet = 0;
-  bool twice = false;
-  auto meet = [&](uint32_t t1) {
+  if (opt < 0) {
+    if (k - R.z < R.w - R.z) return o;   // the reference option
+    if (k < v.rowthr0[i]) {
+      opt = 0;
+    } else {
+      int j = 0;
+      while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
+      opt = j + 1;
+    }
+  }
+  if (opt == ref) return o;
+  // the row moves from its reference option to opt: the staged changes of
+  // the slots it leaves and joins (a dead reference slot is not met: its
+  // change is the death's)
+  uint32_t rs1 = ref > 0 ? (uint32_t)v.cslot[off + ref - 1] + 1u : 0u;
+  const uint32_t ns1 = opt > 0 ? (uint32_t)v.cslot[off + opt - 1] + 1u : 0u;
+  o.moved = 1;
+  o.hw = row_key(i, (int)ns1) - row_key(i, (int)rs1);
+  o.clut = (opt == 0) - (ref == 0);
+  if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(v.dthr, pd, key, rs1 - 1u)) rs1 = 0u;
+  if (rs1) {
+    o.d += v.lossd[i];
+    o.ninf += v.lninf[i];
+  }
+  if (ns1) {
+    o.d += v.gaind[off + opt - 1];
+    o.ninf += v.gninf[off + opt - 1];
+  }
+  o.met = (rs1 << 16) | ns1;
+  return o;
+}
+
+// Rows a child's chunk loop sets aside for row_slow (per-thread list in
+// shared memory, entry q at [q * blockDim.x]); a child with more goes to
+// the warp kernel.
+constexpr int kDrawSlow = 16;
+
+// Draws child n of the parent staged at img.  The chunk loop only tests the
+// reference intervals and notes the rows that need more (their uniform is
+// regenerated afterwards), so it holds nothing but its own state in
+// registers.  Returns false when the child must be drawn by the warp kernel
+// (more noted rows than the list holds, its deviations meet a slot twice,
+// or two met slots share a mask bit).
+template <int DZ>
+__device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned char* img, const Lay& L,
+                                             const int h, const int n, const uint2 key, uint16_t* s_slow) {
+  const Model& md = a.md;
+  const Scal& sc = *at<Scal>(img, L.scal);
+  unsigned long long bloom = 0ull;
+  int nd = 0;
+  {
+    // stage 1: deaths; only their bloom (slots with candidate rows) is kept
+    // through the chunk loop, their score and key changes are summed after
+    const uint32_t* dpc = at<uint32_t>(img, L.dpc);
+    const uint32_t* dthr = at<uint32_t>(img, L.dthr);
+    const uint8_t* srow = at<uint8_t>(img, L.srow);
+    const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n, key);
+    const int ndpc = sc.ndpc;
+    // the next chunk's entry is loaded one iteration ahead, so its Philox
+    // call does not wait for the load
+    uint32_t ent_next = ndpc > 0 ? dpc[0] : 0u;
+    for (int x = 0; x < ndpc; ++x) {
+      const uint32_t ent = ent_next;
+      if (x + 1 < ndpc) ent_next = dpc[x + 1];
+      const uint32_t cc = ent >> 4, mask = ent & 15u;
+      const uint4 r = philox_at(pd, cc, key);
+      const uint4 th = *reinterpret_cast<const uint4*>(dthr + 4 * cc);
 #pragma unroll
-    for (int q = 0; q < kDrawMet; ++q)
-      if (q < nmet && ((met[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) == t1) twice = true;
-#pragma unroll
-    for (int q = 0; q < kDrawMet; ++q)
-      if (q == nmet) met[q >> 1] |= t1 << (16 * (q & 1));
-    ++nmet;
-  };
-  const int nrca = sc.nrca;
-  for (int x = 0; x < nrca; ++x) {
-    const RowChunk& rc = v.rch[x];
-    const uint4 hd = rc.head, lo = rc.lo, hi = rc.hi;
-    const uint4 r = philox_at(pr, hd.x, key);
-    const uint32_t hit = ((((unsigned long long)hd.w << 32) | hd.z) & bloom) ? hd.y : 0u;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const uint32_t k = word_of(r, b) >> 8;
-      const uint32_t l = word_of(lo, b), u = word_of(hi, b);
-      const bool in_ref = k - l < u - l;
-      if (in_ref && !((hit >> b) & 1u)) continue;   // the reference option
-      const int i = 4 * (int)hd.x + b;
-      const uint4 R = v.row[i];
-      int opt = -1;
-      if (((hit >> b) & 1u) && (v.rowbl[i] & bloom)) {
-        opt = row_among_living(R, v.cslot, v.cw, md.kappa_zero ? 0.f : v.roww0[i], v.dthr, pd, key, bloom, k);
-        if (opt == -2) {
-          bad_row = true;
-          opt = 0;
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t thb = b == 0 ? th.x : b == 1 ? th.y : b == 2 ? th.z : th.w;
+        if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < thb) {
+          const uint32_t t = 4u * cc + (uint32_t)b;
+          ++nd;
+          if (srow[t]) bloom |= 1ull << (t & 63u);
         }
       }
-      if (opt == -1) {
-        if (in_ref) continue;
-        opt = row_option(R, v.cthr, v.rowthr0[i], k);
+    }
+  }
+  // stage 2: one categorical draw per detection row with candidates; rows
+  // outside their reference interval, or whose candidates' bloom meets the
+  // dead slots', are noted
+  int nslow = 0;
+  {
+    const PhiloxRun pr = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n + 1u, key);
+    const RowChunk* rch = at<RowChunk>(img, L.rch);
+    const int nrca = sc.nrca;
+    uint32_t cc_next = nrca > 0 ? rch[0].head.x : 0u;   // one iteration ahead
+    for (int x = 0; x < nrca; ++x) {
+      const uint32_t cc = cc_next;
+      if (x + 1 < nrca) cc_next = rch[x + 1].head.x;
+      const uint4 r = philox_at(pr, cc, key);
+      const uint4 hd = rch[x].head, lo = rch[x].lo, hi = rch[x].hi;
+      const uint32_t hit = ((((unsigned long long)hd.w << 32) | hd.z) & bloom) ? hd.y : 0u;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t k = word_of(r, b) >> 8;
+        const uint32_t l = word_of(lo, b), u = word_of(hi, b);
+        if (k - l < u - l && !((hit >> b) & 1u)) continue;   // the reference option
+        if (nslow < kDrawSlow) s_slow[nslow * (int)blockDim.x] = (uint16_t)(4u * hd.x + (uint32_t)b);
+        ++nslow;
       }
-      if (opt == (int)(R.y >> 16)) continue;
-      const RowMove m = row_move(R, i, opt, v.cslot, v.lossd, v.gaind, v.lninf, v.gninf, v.dthr, pd, key, bloom);
-      hsh += m.hw;
-      dclut += m.clut;
-      delta += m.d;
-      dninf += m.ninf;
-      if (m.met >> 16) meet(m.met >> 16);
-      if (m.met & 0xFFFFu) meet(m.met & 0xFFFFu);
-      if (twice || nmet > kDrawMet) return false;
+    }
+  }
+  if (nslow > kDrawSlow) return false;
+  // the deaths' score and key changes (a dead slot's change is its dead term)
+  unsigned long long hsh = 0ull;
+  long long delta = 0;
+  int dclut = 0, dninf = 0;
+  bool bad_row = false;
+  if (nd) {
+    const uint32_t* dpc = at<uint32_t>(img, L.dpc);
+    const uint32_t* dthr = at<uint32_t>(img, L.dthr);
+    const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n, key);
+    const int ndpc = sc.ndpc;
+    int left = nd;
+    for (int x = 0; x < ndpc && left; ++x) {
+      const uint32_t ent = dpc[x];
+      const uint32_t cc = ent >> 4, mask = ent & 15u;
+      const uint4 r = philox_at(pd, cc, key);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t t = 4u * cc + (uint32_t)b;
+        if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < dthr[t]) {
+          --left;
+          hsh += dead_key((int)t);
+          delta += at<long long>(img, L.deadd)[t];
+          dninf += at<int8_t>(img, L.dninf)[t];
+        }
+      }
+    }
+  }
+  // the noted rows: drawn among the living when a candidate may have died,
+  // else from the thresholds; a row that leaves the reference option adds
+  // its change
+  if (nslow) {
+    const PhiloxRun pr = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n + 1u, key);
+    unsigned long long metm = 0ull;
+    for (int q = 0; q < nslow; ++q) {
+      const int i = s_slow[q * (int)blockDim.x];
+      const uint4 r = philox_at(pr, (uint32_t)i >> 2, key);
+      const uint32_t k = word_of(r, i & 3) >> 8;
+      const RowOut o = row_slow<DZ>(img, a.T_max, a.K_max, a.M_plan, i, k, true, bloom, (uint32_t)n, key,
+                                    md.kappa_zero);
+      bad_row |= o.bad != 0;
+      if (!o.moved) continue;
+      hsh += o.hw;
+      dclut += o.clut;
+      delta += o.d;
+      dninf += o.ninf;
+      const unsigned long long m1 = (o.met >> 16) ? 1ull << (((o.met >> 16) - 1u) & 63u) : 0ull;
+      const unsigned long long m2 = (o.met & 0xFFFFu) ? 1ull << (((o.met & 0xFFFFu) - 1u) & 63u) : 0ull;
+      if ((metm & (m1 | m2)) || (m1 & m2)) return false;
+      metm |= m1 | m2;
     }
   }
   const long long score = sc.ref_score + delta + (md.kappa_zero ? 0LL : (long long)dclut * md.fx_log_kappa);
@@ -941,18 +995,20 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const View& v,
   a.child_key[j] = valid ? score : kKeyInvalid;
   a.child_hash[j] = hsh;
   a.child_status[j] = valid ? 1 : 0;
-  a.child_alive[j] = (uint16_t)(T - nd);
+  a.child_alive[j] = (uint16_t)(sc.T - nd);
   return true;
 }
 
-int expand_draw_smem(int) { return 0; }
+int expand_draw_smem(int threads) { return threads * kDrawSlow * (int)sizeof(uint16_t); }
 
 // Persistent over the children of the frame, one thread per child in the
 // order parent * h_up + draw (a warp holds 32 consecutive children, of at
 // most two parents when h_up >= 32); no block-level synchronisation.
 template <int DZ>
-__global__ void __launch_bounds__(256, 4) draw_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256, 3) draw_kernel(const ExpandArgs a) {
   pdl_enter();
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint16_t* s_slow = reinterpret_cast<uint16_t*>(sm) + threadIdx.x;
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H, HU = a.md.h_up;
   const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
@@ -964,9 +1020,9 @@ __global__ void __launch_bounds__(256, 4) draw_kernel(const ExpandArgs a) {
        j += (long long)gridDim.x * blockDim.x) {
     const int h = (int)(j / HU);
     const int n = (int)(j - (long long)h * HU);
-    const View v = make_view(a.img + (size_t)h * a.img_stride, L);
-    if (v.sc->bad) continue;
-    if (!thread_child(a, v, v.sc->T, h, n, key)) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)j;
+    const unsigned char* img = a.img + (size_t)h * a.img_stride;
+    if (at<Scal>(img, L.scal)->bad) continue;
+    if (!thread_child<DZ>(a, img, L, h, n, key, s_slow)) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)j;
   }
 }
 

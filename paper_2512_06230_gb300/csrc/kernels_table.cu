@@ -10,6 +10,12 @@ namespace glmb {
 
 long long g_launches = 0;
 
+namespace {
+WaitTest g_wait_test{0, 0};
+}
+WaitTest wait_test() { return g_wait_test; }
+void set_wait_test(WaitTest w) { g_wait_test = w; }
+
 // ---------------------------------------------------------------------------
 // Prediction: m <- F m, P <- F P F^T + Q for the constant-velocity model,
 // F = [[I, dt I], [0, I]], from the state table into the working table
@@ -189,6 +195,12 @@ __global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const F
   pdl_enter();
   const int T = fs->T, M = fs->M;
   const float* __restrict__ Z = fs->Z;
+  // detections are read with global-memory loads: an address outside
+  // global memory rejects the frame instead of being loaded
+  if (M > 0 && !__isGlobal(Z)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrInput);
+    return;
+  }
   {
     // every detection coordinate finite, else the frame is rejected
     bool bad = false;
@@ -229,6 +241,7 @@ __global__ void table_write_kernel(Model md, CompTable ct, PairTable pt, const F
   pdl_enter();
   const int T = fs->T, M = fs->M;
   const float* __restrict__ Z = fs->Z;
+  if (M > 0 && !__isGlobal(Z)) return;   // flagged by the count kernel
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps)
     table_write_comp<DZ>(md, ct, pt, c, Z, M, n_fp64, err);
@@ -381,11 +394,10 @@ __device__ __forceinline__ long long scan_len(const int* n_dev, int mult) {
 // prefixes [nw]; counters and status are zero before the first use and left
 // zero by the last block to finish.
 constexpr unsigned kStAgg = 1u, kStInc = 2u;
-constexpr long long kScanSpin = 1LL << 22;   // look-back wait limit (iterations)
 
 template <typename T>
 __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T* total, int total_at_end,
-                             T* work, int nw, unsigned* err) {
+                             T* work, int nw, unsigned* err, long long spin_limit, int withhold_first) {
   pdl_enter();
   __shared__ int s_tile;
   __shared__ T s_excl;
@@ -427,7 +439,7 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
           const int p = top - lane;
           T f = p >= 0 ? ((volatile T*)st)[p] : (T)kStInc;
           long long spin = 0;
-          while (__any_sync(0xFFFFFFFFu, f == 0) && ++spin < kScanSpin)
+          while (__any_sync(0xFFFFFFFFu, f == 0) && ++spin < spin_limit)
             if (f == 0) f = ((volatile T*)st)[p];
           if (__any_sync(0xFFFFFFFFu, f == 0)) {   // a predecessor never published
             gave_up = true;
@@ -451,7 +463,9 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
       if (lane == 0) {
         ((volatile T*)inc)[tile] = excl + tile_sum;
         __threadfence();
-        ((volatile T*)st)[tile] = (T)kStInc;
+        // (a failure-detection test withholds the first tile's prefix, so
+        // that the later tiles' bounded waits run out)
+        if (!(withhold_first && tile == 0)) ((volatile T*)st)[tile] = (T)kStInc;
         s_excl = excl;
         if (tile == ntiles - 1) {
           if (total) *total = excl + tile_sum;
@@ -526,7 +540,10 @@ static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long
     cudaMemsetAsync(err, (int)kErrNumeric, 1, s);
     return;
   }
-  launch_k(scan_onepass<T>, nt, kScanThreads, 0, s, in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err);
+  const WaitTest wt = wait_test();
+  const bool test = wt.mode == kWaitTestScan;
+  launch_k(scan_onepass<T>, nt, kScanThreads, 0, s, in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err,
+           test ? wt.limit : kScanSpinLimit, test ? 1 : 0);
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,

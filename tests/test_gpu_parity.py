@@ -272,3 +272,31 @@ def test_ill_conditioned_innovation_takes_the_fp64_factorisation(oracle_mod, glm
     assert rep.ok(), rep.failures[:10]
     assert n64 >= 4
     assert rep.checks["unique_children"] >= 10 and rep.checks["retained"] >= 10
+
+
+def _ospa_run(filt_step, filt_est, scene, dim):
+    from scenes.metrics import ospa
+    out = []
+    for fr in scene.frames:
+        filt_step(fr)
+        out.append(ospa(filt_est()[:, :dim], fr.truth[:, :dim], c=50.0, p=1.0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("preset,seed", [("tiny", 1001), ("tiny", 1002), ("mid", 2001)])
+def test_multi_frame_ospa_within_one_percent_of_the_oracle(oracle_mod, glmb, preset, seed):
+    """Multi-frame runs are compared by OSPA (order 1, cut-off 50 m, MAP
+    estimates against the scene's truth): the GPU filter and the oracle,
+    each from the initial GLMB over the whole scene, give mean OSPA within
+    1 % of each other."""
+    sc = scenes.make_scene(scenes.preset(preset), seed)
+    cfg = sc.filter_config()
+    o = oracle_mod.Oracle(cfg, n_threads=8)
+    g = glmb.Filter(cfg)
+    d = sc.dim_z
+    oo = _ospa_run(lambda fr: o.step(fr.births, fr.Z), lambda: o.estimates()["mean"], sc, d)
+    og = _ospa_run(lambda fr: g.step(fr.births, fr.Z), lambda: g.estimates()["mean"], sc, d)
+    g.close()
+    print(f"\n{preset}/{seed}: mean OSPA oracle {oo.mean():.4f} m, GPU {og.mean():.4f} m, "
+          f"frames equal {np.sum(np.abs(oo - og) < 1e-6)}/{len(oo)}")
+    assert abs(og.mean() - oo.mean()) <= 0.01 * oo.mean()
