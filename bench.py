@@ -434,6 +434,128 @@ def run_batch(args, glmb, torch, dev):
     print(json.dumps(line))
 
 
+def run_target(args, glmb, torch, dev):
+    """The benchmark spec's comparison: the batched form with the learned gate
+    against the plain single-scene form, on the same scenes and GPU.
+    Scenes: --scenes held-out scenes of the batched workload's distribution
+    (2-D, N ~ U{5..--target-nmax}, H ~ U{100..5000}, clutter ~ U(5, 40)),
+    --steps frames each.  The gate is trained on --gate-train other scenes
+    of the same distribution (features and usage labels from the ungated
+    filter, the library's training kernels), its threshold keeping
+    --gate-keep of the used training pairs.  Plain: each scene alone, frame
+    after frame (glmb_step, gate off).  Batched + gate: every scene's frame
+    at once (glmb_step_batch), gate pruning.  Both with device-resident
+    detections and the estimates read every frame, timed on the host wall
+    clock over a second pass (the first fills the graph caches).  Accuracy:
+    OSPA (order 1, cut-off 50 m) of the MAP estimates against the scene's
+    truth, per frame; the FP64 oracle runs the plain method on the scenes
+    it finishes within --cpu-budget seconds in all, and each GPU form's
+    mean OSPA over those scenes is compared with the oracle's."""
+    from paper_2512_06230_gb300 import gate as G
+    from scenes.metrics import ospa
+    import oracle
+    F = args.steps
+    seed0 = 7000 if args.seed is None else args.seed
+    specs = scenes.batch_scenes(args.scenes, seed0, frames=F, n_range=(5, args.target_nmax))
+    train_specs = scenes.batch_scenes(args.gate_train, seed0 + 1, frames=F, n_range=(5, args.target_nmax))
+    scs = [scenes.make_scene(p, s) for p, s in specs]
+    cfgs = [batch_cfg(p, sc) for (p, _), sc in zip(specs, scs)]
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for p, s in train_specs:
+        sc = scenes.make_scene(p, s)
+        X, y = G.collect(batch_cfg(p, sc), [(glmb.births_array(fr.births, sc.dim_x), fr.Z) for fr in sc.frames],
+                         skip=2)
+        Xs.append(X)
+        ys.append(y)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    params, hist = G.train(X, y, steps=args.gate_steps, batch=32768, lr=2e-3, seed=1)
+    thr = G.threshold(params, X, y, keep_used=args.gate_keep)
+    t_train = time.perf_counter() - t0
+    Z = [[torch.from_numpy(fr.Z).to(dev) if len(fr.Z) else torch.zeros((0, 2), device=dev) for fr in sc.frames]
+         for sc in scs]
+    B = [[glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames] for sc in scs]
+    torch.cuda.synchronize()
+
+    def arm(batched):
+        filters = [glmb.Filter(c) for c in cfgs]
+        if batched:
+            for f in filters:
+                f.set_gate(params, thr, glmb.Filter.GATE_PRUNE)
+        res = {}
+        for pass_ in range(2):
+            if pass_:
+                for f in filters:
+                    f.reset()
+            est = [[None] * F for _ in filters]
+            t_s = time.perf_counter()
+            if batched:
+                for k in range(F):
+                    glmb.step_batch(filters, [(B[i][k], Z[i][k]) for i in range(len(filters))], device=True)
+                    for i, f in enumerate(filters):
+                        est[i][k] = f.estimates(cap=f.cfg["max_tracks"], pmf_cap=64)["mean"][:, :2].copy()
+            else:
+                for i, f in enumerate(filters):
+                    for k in range(F):
+                        f.step(B[i][k], Z[i][k], device=True)
+                        est[i][k] = f.estimates(cap=f.cfg["max_tracks"], pmf_cap=64)["mean"][:, :2].copy()
+            torch.cuda.synchronize()
+            seconds = time.perf_counter() - t_s
+            osp = [[ospa(est[i][k], scs[i].frames[k].truth[:, :2], c=50.0) for k in range(F)]
+                   for i in range(len(filters))]
+            res = dict(seconds=seconds, ospa=osp, pairs=sum(f.info()["n_pairs"] for f in filters) / len(filters))
+        for f in filters:
+            f.close()
+        return res
+
+    plain = arm(False)
+    bat = arm(True)
+    # the oracle (plain method, FP64) on the smallest scenes within the budget
+    order = sorted(range(len(scs)), key=lambda i: (specs[i][0].n_objects, specs[i][0].h_max))
+    threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
+    o_osp, o_idx, t_o = {}, [], time.perf_counter()
+    for i in order:
+        if time.perf_counter() - t_o > args.cpu_budget:
+            break
+        o = oracle.Oracle(cfgs[i], n_threads=threads)
+        vals = []
+        for k, fr in enumerate(scs[i].frames):
+            o.step(fr.births, fr.Z)
+            vals.append(ospa(o.estimates()["mean"][:, :2], fr.truth[:, :2], c=50.0))
+        o_osp[i] = vals
+        o_idx.append(i)
+
+    def mean_over(osp, idx):
+        v = [x for i in idx for x in osp[i]]
+        return float(np.mean(v)) if v else None
+
+    all_idx = list(range(len(scs)))
+    n_sf = len(scs) * F
+    line = {"metric": "batched + learned-gate GLMB vs plain single-scene GLMB: scene-frames/s at equal OSPA (1 GB300)",
+            "value": n_sf / bat["seconds"], "unit": "scene-frames/s", "higher_is_better": True,
+            "dtype": "f32 (bf16 gate MLP)", "data": "synthetic", "n_gpus": 1, "steps": F,
+            "config": {"workload": f"{len(scs)} scenes x {F} frames, 2-D CV, N~U{{5..{args.target_nmax}}}, "
+                                   "H~U{100..5000}, clutter~U(5,40), device detections, estimates read every frame",
+                       "gate": {"train_scenes": args.gate_train, "pairs": int(len(y)), "used_fraction": float(y.mean()),
+                                "steps": args.gate_steps, "keep_used": args.gate_keep, "threshold": thr,
+                                "train_s": round(t_train, 1)},
+                       "ospa": "order 1, cut-off 50 m, MAP estimates vs truth"},
+            "plain": {"scene_frames_per_s": n_sf / plain["seconds"], "ospa_mean": mean_over(plain["ospa"], all_idx),
+                      "pairs_last_frame_per_scene": plain["pairs"]},
+            "batched_gate": {"scene_frames_per_s": n_sf / bat["seconds"], "ospa_mean": mean_over(bat["ospa"], all_idx),
+                             "pairs_last_frame_per_scene": bat["pairs"]},
+            "speedup": plain["seconds"] / bat["seconds"],
+            "oracle": {"scenes": len(o_idx), "n_objects": [specs[i][0].n_objects for i in o_idx],
+                       "ospa_mean": mean_over(o_osp, o_idx), "threads": threads,
+                       "plain_ospa_mean_same_scenes": mean_over(plain["ospa"], o_idx),
+                       "batched_gate_ospa_mean_same_scenes": mean_over(bat["ospa"], o_idx)}}
+    om = line["oracle"]["ospa_mean"]
+    if om:
+        line["oracle"]["plain_rel_diff"] = line["oracle"]["plain_ospa_mean_same_scenes"] / om - 1.0
+        line["oracle"]["batched_gate_rel_diff"] = line["oracle"]["batched_gate_ospa_mean_same_scenes"] / om - 1.0
+    print(json.dumps(line))
+
+
 def _ints(text):
     return [int(v) for v in str(text).split(",") if v]
 
@@ -862,6 +984,7 @@ def main():
     ap.add_argument("--gate-keep", type=float, default=0.99999, help="fraction of used training pairs kept")
     ap.add_argument("--gate-tails", default="1e-4,1e-12,1e-30", help="chi-square tails of the base gate")
     ap.add_argument("--mlp-rows", type=int, default=1 << 22, help="--scene mlp: feature rows")
+    ap.add_argument("--target-nmax", type=int, default=300, help="--scene target: largest object count")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="only run this many frames of the scene through glmb_step (for ncu captures) and exit")
     args = ap.parse_args()
@@ -911,6 +1034,8 @@ def main():
         return run_gate(args, glmb, torch, dev)
     if args.scene == "mlp":
         return run_mlp(args, glmb, torch, dev)
+    if args.scene == "target":
+        return run_target(args, glmb, torch, dev)
 
     sc = scene_for_rank(args, rank)
     cfg = filter_cfg(sc)
