@@ -322,7 +322,9 @@ glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* 
  *                        order, one per thread, whatever the CTA size);
  *   warp_cta_warps       most warps per CTA of the one-warp-per-child kernel
  *                        (1..16, default 16);
- *   stage_threads        threads per staging CTA (32..256, default 256).
+ *   stage_threads        threads per staging CTA (32..256, multiple of 32; 0,
+ *                        the default: 256 when parents are staged in shared
+ *                        memory or are fewer than two per SM, else 64).
  * Setting them drops the captured graphs. */
 typedef struct {
   int32_t thread_warps_per_sm;
@@ -342,11 +344,16 @@ glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
  *   GLMB_OPT_DRAW_THREAD   draw children one per thread whatever the number
  *                          of parents (children whose lists overflow still
  *                          go to the warp path).
- * Default 0: shared-memory staging when it fits, one thread per child once
- * the children give every SM four warps. */
+ *   GLMB_OPT_STAGE_SHARED  build them in shared memory whenever a parent's
+ *                          tables fit (GLMB_OPT_STAGE_GLOBAL wins if both
+ *                          are set).
+ * Default 0: shared-memory staging when eight staging CTAs fit on an SM
+ * (else in global memory), one thread per child once the children give
+ * every SM four warps. */
 #define GLMB_OPT_STAGE_GLOBAL 1u
 #define GLMB_OPT_DRAW_WARP 2u
 #define GLMB_OPT_DRAW_THREAD 4u
+#define GLMB_OPT_STAGE_SHARED 8u
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts);
 
 /* Whether glmb_step computes the frame's estimates in its graph (on by

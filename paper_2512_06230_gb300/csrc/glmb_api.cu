@@ -39,6 +39,7 @@ struct Plan {
   int T, K, M;     // per-parent image plan: slots, gated pairs, detection rows
   bool thread;     // draws: one thread per child (many parents) or one warp per child
   bool smem;       // parents staged in shared memory (else in the image)
+  int st_thr;      // threads per staging CTA
   int Gw, Gm;      // warps per CTA of the warp kernel: expansion, regeneration
 };
 }  // namespace
@@ -55,7 +56,7 @@ struct glmb_handle {
   int cap_h = 0, cap_meas = 0, cap_births = 0, max_tracks = 0;
   long long cap_entries = 0, cap_comp = 0, cap_pairs = 0, cap_children = 0, cap_upd = 0;
   uint32_t hmask = 0;
-  int smem_limit = 0, n_sm = 0;
+  int smem_limit = 0, n_sm = 0, smem_per_sm = 0;
   // state (table A = comps[cur]) and working table (B)
   CompTable comps[2];
   int cur = 0;
@@ -128,7 +129,7 @@ struct glmb_handle {
   long long gen = 0, est_gen = -1;
   bool step_estimates = true;
   unsigned launch_opts = 0;   // GLMB_OPT_* overrides
-  glmb_tuning tune{4, 0, 16, 256};   // launch shapes (glmb_set_tuning)
+  glmb_tuning tune{4, 0, 16, 0};     // launch shapes (glmb_set_tuning)
   unsigned* h_cnt = nullptr;   // pinned copy of the prune counters
   double* d_ru = nullptr;
   // stage timing
@@ -426,7 +427,7 @@ extern "C" {
 
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
   if (!h) return GLMB_E_INVALID;
-  if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD))
+  if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD | GLMB_OPT_STAGE_SHARED))
     return fail(h, GLMB_E_INVALID, "set_launch_options: unknown option bits 0x%x", opts);
   if (opts != h->launch_opts) {
     cudaStreamSynchronize(h->stream);
@@ -563,6 +564,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
     return GLMB_E_CUDA;
   }
   cudaDeviceGetAttribute(&h->smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
   expand_init(h->smem_limit);
   if (c.stream) {
@@ -825,9 +827,9 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   a.child_status = h->child_status;
   a.child_alive = h->child_alive;
   const int img = (int)a.img_stride;
-  // stage: one CTA of stage_threads threads per parent (persistent grid)
+  // stage: one CTA of p.st_thr threads per parent (persistent grid)
   const int st_smem = p.smem ? img : 0;
-  const int st_thr = h->tune.stage_threads;
+  const int st_thr = p.st_thr;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
   // draws: one thread per child over the frame's children in order
@@ -945,7 +947,21 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   if (h->launch_opts & GLMB_OPT_DRAW_THREAD) p.thread = true;
   if (h->launch_opts & GLMB_OPT_DRAW_WARP) p.thread = false;
   p.thread = p.thread && p.K <= 65536;
-  p.smem = expand_image_bytes(dz, p.T, p.K, p.M) <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL);
+  // parents are staged in shared memory (then copied out to their image)
+  // when eight staging CTAs fit on an SM; larger images are built in place
+  // in global memory, where many CTAs per SM keep more parents in flight
+  // (measured: on the 3-D sweep's N = 200 cell, 123 KB images, staging in
+  // global memory with 64-thread CTAs ran the expansion in 2.41 ms against
+  // 3.51 ms in shared memory at one CTA per SM; on the 2-D mid scene, 19 KB
+  // images, shared memory stayed faster)
+  const int img_bytes = expand_image_bytes(dz, p.T, p.K, p.M);
+  p.smem = img_bytes <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
+           (8LL * img_bytes <= (long long)h->smem_per_sm || (h->launch_opts & GLMB_OPT_STAGE_SHARED));
+  // staging threads: 256 in shared memory, or for few parents (each parent's
+  // work spread over more threads); else 64, so that more parents are in
+  // flight per SM
+  p.st_thr = h->tune.stage_threads > 0 ? h->tune.stage_threads
+             : (p.smem || (long long)h->H < 2LL * h->n_sm) ? 256 : 64;
   p.Gw = p.Gm = 0;
   for (int g = h->tune.warp_cta_warps; g >= 1 && !p.Gw; --g)
     if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
@@ -1198,7 +1214,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
     int best = -1;
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
       const glmb_handle::CachedGraph& g = h->graphs[gi];
-      if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread ||
+      if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread || g.plan.st_thr != p.st_thr ||
           g.plan.T < p.T || g.plan.K < p.K || g.plan.M < p.M)
         continue;
       if (best < 0 || g.smem < h->graphs[best].smem) best = gi;
@@ -1321,7 +1337,7 @@ glmb_status glmb_set_tuning(glmb_handle* h, const glmb_tuning* t) {
   if (!h || !t) return GLMB_E_INVALID;
   if (t->thread_warps_per_sm < 0 || t->warp_cta_warps < 1 || t->warp_cta_warps > 16 ||
       (t->draw_threads != 0 && (t->draw_threads < 32 || t->draw_threads > 256 || t->draw_threads % 32)) ||
-      t->stage_threads < 32 || t->stage_threads > 256 || t->stage_threads % 32)
+      (t->stage_threads != 0 && (t->stage_threads < 32 || t->stage_threads > 256 || t->stage_threads % 32)))
     return fail(h, GLMB_E_INVALID, "set_tuning: a launch shape out of range");
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);

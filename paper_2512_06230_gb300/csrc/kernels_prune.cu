@@ -777,6 +777,8 @@ __device__ __forceinline__ void est_card_block(const HypTable& hp, const int H, 
 // hypothesis, so the sum over the components of one label is the total
 // weight of the hypotheses that hold it (the existence of Section 3's
 // labelled tracks), reached without waiting for the MAP hypothesis.
+constexpr int kEstPriv = 4096;   // components summed in shared memory per block
+
 __global__ void est_sums_kernel(HypTable hp, int H_host, const unsigned* H_dev, double* pmf, int pcap, int* nb,
                                 unsigned long long* r_comp, int ccap, unsigned* cmax, const unsigned* err) {
   pdl_enter();
@@ -787,6 +789,14 @@ __global__ void est_sums_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
     est_card_block(hp, H, pmf, pcap, nb);
     return;
   }
+  // hypotheses share most of their components, so the block sums the
+  // first kEstPriv components in shared memory and adds each nonzero sum
+  // to global memory once (fixed point: the sums do not depend on order)
+  __shared__ unsigned long long s_acc[kEstPriv];
+  __shared__ unsigned s_top;
+  for (int c = threadIdx.x; c < kEstPriv; c += blockDim.x) s_acc[c] = 0ull;
+  if (threadIdx.x == 0) s_top = 0u;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   unsigned top = 0u;
@@ -795,13 +805,21 @@ __global__ void est_sums_kernel(HypTable hp, int H_host, const unsigned* H_dev, 
     const unsigned long long wgt = w_fx(hp.logw[h]);
     for (uint32_t e = lo + lane; e < hi; e += 32) {
       const uint32_t c = min(hp.comp[e], (uint32_t)ccap - 1u);
-      if (wgt) atomicAdd(&r_comp[c], wgt);
+      if (wgt) {
+        if (c < (uint32_t)kEstPriv) atomicAdd(&s_acc[c], wgt);
+        else atomicAdd(&r_comp[c], wgt);
+      }
       top = max(top, c + 1u);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xFFFFFFFFu, top, o));
-  if (lane == 0 && top) atomicMax(cmax, top);
+  if (lane == 0 && top) atomicMax(&s_top, top);
+  __syncthreads();
+  const unsigned nt = min(s_top, (unsigned)kEstPriv);
+  for (unsigned c = threadIdx.x; c < nt; c += blockDim.x)
+    if (s_acc[c]) atomicAdd(&r_comp[c], s_acc[c]);
+  if (threadIdx.x == 0 && s_top) atomicMax(cmax, s_top);
 }
 
 // Existence of the MAP tracks, second half: the labels of the MAP
@@ -888,7 +906,9 @@ void launch_estimates(const HypTable& hp, int H, const unsigned* H_dev, int H_bo
                       double* pmf, int pcap, int* nb, unsigned long long* r_comp, unsigned long long* r_map,
                       void* tracks, unsigned* cmax, unsigned* done, int n_sm, const unsigned* err, cudaStream_t s) {
   static int attr_pcap = 0;   // the limits only grow (graphs of larger filters stay valid)
-  if (pcap * 16 > 48 * 1024 && pcap > attr_pcap) {
+  // (est_sums_kernel also holds kEstPriv sums in static shared memory, so
+  // the opt-in is made whatever the dynamic size)
+  if (pcap > attr_pcap) {
     cudaFuncSetAttribute(est_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 8);
     cudaFuncSetAttribute(est_tracks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pcap * 16);
     attr_pcap = pcap;

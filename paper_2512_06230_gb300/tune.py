@@ -14,7 +14,7 @@ DEFAULT_SPACE = {
     "thread_warps_per_sm": (1, 2, 4, 8),
     "draw_threads": (0, 128, 256),
     "warp_cta_warps": (8, 16),
-    "stage_threads": (128, 256),
+    "stage_threads": (0, 64, 128, 256),
 }
 
 

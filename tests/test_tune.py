@@ -61,5 +61,5 @@ def test_candidates_enumerate_the_product_in_order():
     c = tune.candidates({"a": (1, 2), "b": (3,), "c": (4, 5)})
     assert c == [{"a": 1, "b": 3, "c": 4}, {"a": 1, "b": 3, "c": 5},
                  {"a": 2, "b": 3, "c": 4}, {"a": 2, "b": 3, "c": 5}]
-    assert len(tune.candidates()) == 4 * 3 * 2 * 2
+    assert len(tune.candidates()) == 4 * 3 * 2 * 4
     assert tune.candidates(limit=3) == tune.candidates()[:3]
