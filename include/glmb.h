@@ -318,8 +318,10 @@ glmb_status glmb_step_batch(glmb_handle* const* hs, int n, const glmb_frame_in* 
  *   thread_warps_per_sm  draw one thread per child once the children give
  *                        every SM this many warps (default 4);
  *   draw_threads         threads per draw CTA (32..256, multiple of 32; 0:
- *                        256; the draw kernel takes the frame's children in
- *                        order, one per thread, whatever the CTA size);
+ *                        256, halved down to 64 while the frame's children
+ *                        would give an SM fewer than two CTAs; the draw
+ *                        kernel takes the children in order, one per
+ *                        thread, whatever the CTA size);
  *   warp_cta_warps       most warps per CTA of the one-warp-per-child kernel
  *                        (1..16, default 16);
  *   stage_threads        threads per staging CTA (32..256, multiple of 32; 0,

@@ -834,7 +834,15 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
   // draws: one thread per child over the frame's children in order
   // (persistent grid)
-  const int d_thr = h->tune.draw_threads > 0 ? h->tune.draw_threads : 256;
+  // CTAs of 256 threads, or smaller ones when the frame's children would
+  // not give every SM two of them (the mid scene's 32 000 children fill
+  // only 125 CTAs of 256)
+  int d_thr = h->tune.draw_threads;
+  if (d_thr <= 0) {
+    const long long kids = (long long)h->H * h_up;
+    d_thr = 256;
+    while (d_thr > 64 && kids < 2LL * n_sm * d_thr) d_thr >>= 1;
+  }
   const int d_smem = expand_draw_smem(d_thr);
   const int d_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kDraw, d_thr, d_smem));
   const long long d_need = ((long long)h->H * h_up + d_thr - 1) / d_thr;

@@ -707,7 +707,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 // Persistent: each CTA stages parents blockIdx.x, blockIdx.x + gridDim.x, ...
 // SMEM: staged in shared memory and copied to the image (16-byte words).
 template <int DZ, bool SMEM>
-__global__ void __launch_bounds__(256) stage_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
@@ -868,7 +868,7 @@ __device__ __noinline__ RowOut row_slow(const unsigned char* img, const int Tp, 
 // Rows a child's chunk loop sets aside for row_slow (per-thread list in
 // shared memory, entry q at [q * blockDim.x]); a child with more goes to
 // the warp kernel.
-constexpr int kDrawSlow = 16;
+constexpr int kDrawSlow = 24;
 
 // Draws child n of the parent staged at img.  The chunk loop only tests the
 // reference intervals and notes the rows that need more (their uniform is
@@ -930,8 +930,13 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
       for (int b = 0; b < 4; ++b) {
         const uint32_t k = word_of(r, b) >> 8;
         const uint32_t l = word_of(lo, b), u = word_of(hi, b);
-        if (k - l < u - l && !((hit >> b) & 1u)) continue;   // the reference option
-        if (nslow < kDrawSlow) s_slow[nslow * (int)blockDim.x] = (uint16_t)(4u * hd.x + (uint32_t)b);
+        const bool in_ref = k - l < u - l;
+        if (in_ref && !((hit >> b) & 1u)) continue;   // the reference option
+        const uint32_t i = 4u * cc + (uint32_t)b;
+        // a row of a chunk whose bloom meets the dead slots', still in its
+        // reference interval: noted only if its own candidates' bloom does
+        if (in_ref && !(at<unsigned long long>(img, L.rowbl)[i] & bloom)) continue;
+        if (nslow < kDrawSlow) s_slow[nslow * (int)blockDim.x] = (uint16_t)i;
         ++nslow;
       }
     }
