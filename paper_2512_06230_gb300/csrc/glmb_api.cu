@@ -632,6 +632,8 @@ glmb_status glmb_destroy(glmb_handle* h) {
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   dev_free_raw(h, h->img);
+  dev_free_raw(h, h->pt.slm);
+  dev_free_raw(h, h->pt.sln);
   for (int st = 0; st < kNumStages; ++st)
     if (h->ev[st][0]) {
       cudaEventDestroy(h->ev[st][0]);
@@ -815,6 +817,34 @@ glmb_status ensure_img(glmb_handle* h, const Plan& p) {
   if (!q) return fail(h, GLMB_E_CAPACITY, "expansion images: %zu bytes not available", want);
   h->img = (unsigned char*)q;
   h->img_alloc = want;
+  return GLMB_OK;
+}
+
+// the per-component table of m-only term parts holds the frame's working
+// components (grown on demand, which drops the captured graphs: they hold
+// its address).  Without room the terms are built per slot instead (the
+// same values), so a failed allocation only costs time.
+glmb_status ensure_slm(glmb_handle* h, long long need) {
+  if (need <= h->pt.slm_cap || h->pt.slm_cap >= h->cap_comp) return GLMB_OK;
+  const long long cap = std::min<long long>(h->cap_comp, ((need + need / 2 + 255) / 256) * 256);
+  const int NP = h->md.dz * (h->md.dz + 1) / 2;
+  CU(cudaStreamSynchronize(h->stream));
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  dev_free_raw(h, h->pt.slm);
+  dev_free_raw(h, h->pt.sln);
+  h->pt.slm = (float*)dev_alloc_raw(h, (size_t)cap * kSlmM * (NP + 1) * sizeof(float));
+  h->pt.sln = (int8_t*)dev_alloc_raw(h, (size_t)cap * kSlmM);
+  h->pt.slm_cap = (h->pt.slm && h->pt.sln) ? (int)cap : 0;
+  if (!h->pt.slm_cap) {
+    dev_free_raw(h, h->pt.slm);
+    dev_free_raw(h, h->pt.sln);
+    h->pt.slm = nullptr;
+    h->pt.sln = nullptr;
+  }
+  h->pt_full.slm = h->pt.slm;
+  h->pt_full.sln = h->pt.sln;
+  h->pt_full.slm_cap = h->pt.slm_cap;
   return GLMB_OK;
 }
 
@@ -1088,6 +1118,7 @@ glmb_status glmb_predict(glmb_handle* h, const glmb_birth* births, int n_births)
   if (h->stage != 0) return fail(h, GLMB_E_STATE, "predict: previous frame not pruned");
   glmb_status st = stage_births(h, births, n_births);
   if (st != GLMB_OK) return st;
+  if ((st = ensure_slm(h, (long long)h->n_comp + n_births)) != GLMB_OK) return st;
   h->frame += 1;
   h->nb = n_births;
   h->T_work = h->n_comp + n_births;
@@ -1186,6 +1217,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
   if (st != GLMB_OK) return st;
   st = stage_detections(h, Z, M, z_is_device, false);
   if (st != GLMB_OK) return st;
+  if ((st = ensure_slm(h, (long long)h->n_comp + n_births)) != GLMB_OK) return st;
   h->frame += 1;
   h->nb = n_births;
   h->T_work = h->n_comp + n_births;
@@ -1805,6 +1837,9 @@ glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, 
     }
     F.logdetS = h->pt.logdetS;
     F.cap_pairs = h->cap_pairs;
+    F.slm = h->pt.slm;
+    F.sln = h->pt.sln;
+    F.slm_cap = h->pt.slm_cap;
   }
   if (mode != GLMB_GATE_OFF) {
     CU(cudaMemcpyAsync(h->gate_params, params, GLMB_GATE_NPARAM * sizeof(float), cudaMemcpyHostToDevice,

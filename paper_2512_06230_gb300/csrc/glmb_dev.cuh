@@ -98,7 +98,16 @@ struct PairTable {
   float* dprob;           // [comp]
   float* logdetS;         // [comp]
   long long cap_pairs;
+  // the parts of a component's alive term that depend only on (component,
+  // m): S_m^-1 (packed) and the m-only constants, for m = 1 .. kSlmM, built
+  // once per frame for the first slm_cap components (every parent holding
+  // the component reads them): slm[((m - 1) * (NP + 1) + k) * slm_cap + c],
+  // sln[(m - 1) * slm_cap + c] the infinite-term count
+  float* slm;
+  int8_t* sln;
+  int slm_cap;
 };
+constexpr int kSlmM = 8;
 
 struct HypTable {
   uint32_t* ptr;          // [cap_h + 1]

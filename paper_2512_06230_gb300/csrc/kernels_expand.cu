@@ -37,15 +37,14 @@
 namespace glmb {
 
 // ---- per-parent image ----
-constexpr int kSlmN = 5;   // cached m-only term parts per slot (m_ref - 2 .. m_ref + 2)
 
 struct Lay {
   int scal;
   int row, rowbl, seref, sqref, termref, hwref, gaind, lossd, deadd;
   int rowrk, rch, rowoff, rowfill, roww0, rowthr0;
-  int comp, dthr, logp, log1mp, mref, refnew, hph, slm, dpc;
+  int comp, dthr, logp, log1mp, mref, refnew, hph, dpc;
   int cthr, ceidx, cw, ce, cq, cslot;
-  int ninfref, sln, gninf, lninf, dninf, srow;
+  int ninfref, gninf, lninf, dninf, srow;
   int total;
 };
 
@@ -111,7 +110,6 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.mref = b.take(4LL * T);
   L.refnew = b.take(4LL * T);
   L.hph = b.take(4LL * NP * T);             // H P H^T of each slot (packed)
-  L.slm = b.take(4LL * kSlmN * (NP + 1) * T);   // m-only term parts, m = m_ref - 2 .. m_ref + 2
   L.dpc = b.take(4LL * (T / 4 + 2));        // chunks of 4 slots that can die
   L.cthr = b.take(4LL * K);
   L.ceidx = b.take(4LL * K);
@@ -120,7 +118,6 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.cq = b.take(4LL * K);                   // e^T R^-1 e of each candidate pair
   L.cslot = b.take(2LL * K);
   L.ninfref = b.take(T);
-  L.sln = b.take((long long)kSlmN * T);
   L.gninf = b.take(K);
   L.lninf = b.take(M);
   L.dninf = b.take(T);
@@ -195,29 +192,17 @@ __device__ __forceinline__ void slot_HPH(const float* s_hph, int T, int t, float
     }
 }
 
-// Cached m-only parts of slot t's term, v = m - m_ref + 2 in {0 .. 4};
-// kNoSlm marks an entry that was not built (m < 1).
-constexpr int8_t kNoSlm = 127;
-
+// The m-only parts of component c's alive term with m detections, from the
+// frame's per-component table (built by the table's count kernel).
 template <int DZ>
-__device__ __forceinline__ void store_slm(float* s_slm, int8_t* s_sln, int T, int v, int t,
-                                          const SlotM<DZ>& s) {
-  constexpr int NP = DZ * (DZ + 1) / 2;
-#pragma unroll
-  for (int k = 0; k < NP; ++k) s_slm[(v * (NP + 1) + k) * T + t] = s.Sinv[k];
-  s_slm[(v * (NP + 1) + NP) * T + t] = s.c;
-  s_sln[v * T + t] = (int8_t)s.ninf;
-}
-
-template <int DZ>
-__device__ __forceinline__ SlotM<DZ> load_slm(const float* s_slm, const int8_t* s_sln, int T, int v,
-                                              int t) {
+__device__ __forceinline__ SlotM<DZ> load_cslm(const float* slm, const int8_t* sln, int cap, int m, uint32_t c) {
   constexpr int NP = DZ * (DZ + 1) / 2;
   SlotM<DZ> s;
+  const size_t base = (size_t)(m - 1) * (NP + 1);
 #pragma unroll
-  for (int k = 0; k < NP; ++k) s.Sinv[k] = s_slm[(v * (NP + 1) + k) * T + t];
-  s.c = s_slm[(v * (NP + 1) + NP) * T + t];
-  s.ninf = s_sln[v * T + t];
+  for (int k = 0; k < NP; ++k) s.Sinv[k] = slm[(base + k) * cap + c];
+  s.c = slm[(base + NP) * cap + c];
+  s.ninf = sln[(size_t)(m - 1) * cap + c];
   return s;
 }
 
@@ -241,15 +226,18 @@ struct View {
   const unsigned long long* hwref;
   const RowChunk* rch;
   const uint32_t *rowrk, *rowthr0, *comp, *dthr, *refnew, *dpc, *cthr;
-  const float *roww0, *logp, *log1mp, *hph, *slm, *cw, *ce, *cq;
+  const float *roww0, *logp, *log1mp, *hph, *cw, *ce, *cq;
+  const float* cslm;      // per-component m-only term parts (PairTable::slm)
+  const int8_t* csln;
+  int slm_cap;
   const int* mref;
   const uint16_t* cslot;
   const uint8_t* ninfref;
-  const int8_t *sln, *gninf, *lninf, *dninf;
+  const int8_t *gninf, *lninf, *dninf;
   const uint8_t* srow;
 };
 
-__device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) {
+__device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L, const PairTable& pt) {
   View v;
   v.sc = at<Scal>(b, L.scal);
   v.row = at<uint4>(b, L.row);
@@ -277,25 +265,35 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) 
   v.logp = at<float>(b, L.logp);
   v.log1mp = at<float>(b, L.log1mp);
   v.hph = at<float>(b, L.hph);
-  v.slm = at<float>(b, L.slm);
+  v.cslm = pt.slm;
+  v.csln = pt.sln;
+  v.slm_cap = pt.slm_cap;
   v.cw = at<float>(b, L.cw);
   v.ce = at<float>(b, L.ce);
   v.cq = at<float>(b, L.cq);
   v.mref = at<int>(b, L.mref);
   v.cslot = at<uint16_t>(b, L.cslot);
   v.ninfref = at<uint8_t>(b, L.ninfref);
-  v.sln = at<int8_t>(b, L.sln);
   return v;
 }
 
-// Term of slot t alive with m = m_ref + dcnt detections whose sums are
-// (se, sq): from the cache when it holds m, else built from H P H^T.
+// a view for code that evaluates no track term (no per-component table)
+__device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L) {
+  PairTable none{};
+  return make_view(b, L, none);
+}
+
+// Term of slot t alive with m detections whose sums are (se, sq): the m-only
+// parts from the per-component table when it holds (component, m), else
+// built from H P H^T (the same function, so the same values).
 template <int DZ>
-__device__ __forceinline__ long long slot_term(const Model& md, const View& v, int T, int t, int m, int dcnt,
+__device__ __forceinline__ long long slot_term(const Model& md, const View& v, int T, int t, int m,
                                                const long long (&se)[DZ], long long sq, int& ninf) {
   if (md.score_mode == 1) return factor_term(md, v.logp[t], m, sq, ninf);
-  if (m >= 1 && dcnt >= -2 && dcnt <= 2 && v.sln[(dcnt + 2) * T + t] != kNoSlm)
-    return term_from<DZ>(md, load_slm<DZ>(v.slm, v.sln, T, dcnt + 2, t), m, se, sq, ninf);
+  if (m >= 1 && m <= kSlmM) {
+    const uint32_t c = v.comp[t];
+    if (c < (uint32_t)v.slm_cap) return term_from<DZ>(md, load_cslm<DZ>(v.cslm, v.csln, v.slm_cap, m, c), m, se, sq, ninf);
+  }
   return slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, se, sq, ninf);
 }
 
@@ -361,7 +359,6 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   float* s_log1mp = at<float>(sm, L.log1mp);
   int* s_mref = at<int>(sm, L.mref);
   float* s_hph = at<float>(sm, L.hph);
-  float* s_slm = at<float>(sm, L.slm);
   uint32_t* s_dpc = at<uint32_t>(sm, L.dpc);
   uint32_t* s_cthr = at<uint32_t>(sm, L.cthr);
   uint32_t* s_ceidx = at<uint32_t>(sm, L.ceidx);
@@ -370,7 +367,6 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   float* s_cq = at<float>(sm, L.cq);
   uint16_t* s_cslot = at<uint16_t>(sm, L.cslot);
   uint8_t* s_ninfref = at<uint8_t>(sm, L.ninfref);
-  int8_t* s_sln = at<int8_t>(sm, L.sln);
   const int Kp = a.K_max;                   // stride of the candidate arrays
   const CompTable& ct = a.ct;
   const PairTable& pt = a.pt;
@@ -569,18 +565,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   }
   __syncthreads();
 
-  // ---- m-only term parts (slot x {m_ref - 2 .. m_ref + 2}), chunk lists ----
-  for (int x = tid; x < kSlmN * T; x += nthr) {
-    const int t = x % T, v = x / T;
-    const int m = s_mref[t] - 2 + v;
-    if (m < 1 || md.score_mode == 1) {
-      s_sln[v * T + t] = kNoSlm;
-      continue;
-    }
-    float HPH[DZ][DZ];
-    slot_HPH<DZ>(s_hph, T, t, HPH);
-    store_slm<DZ>(s_slm, s_sln, T, v, t, make_slot_m<DZ>(md, HPH, s_logp[t], m));
-  }
+  // ---- chunk lists ----
   {
     const int nch = (T + 3) >> 2;
     for (int cc = tid; cc < nch; cc += nthr) {
@@ -634,8 +619,9 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       const int mr = s_mref[t];
       int ninf;
       long long term;
-      if (mr >= 1 && s_sln[2 * T + t] != kNoSlm) {
-        term = term_from<DZ>(md, load_slm<DZ>(s_slm, s_sln, T, 2, t), mr, se, s_sqref[t], ninf);
+      if (md.score_mode == 0 && mr >= 1 && mr <= kSlmM && s_comp[t] < (uint32_t)a.pt.slm_cap) {
+        term = term_from<DZ>(md, load_cslm<DZ>(a.pt.slm, a.pt.sln, a.pt.slm_cap, mr, s_comp[t]), mr, se, s_sqref[t],
+                             ninf);
       } else {
         float HPH[DZ][DZ];
         slot_HPH<DZ>(s_hph, T, t, HPH);
@@ -654,7 +640,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   // ---- single-deviation deltas (same functions and inputs as a child's
   // rescoring of a slot touched once, so the sums are bit-identical) ----
   {
-    const View v = make_view(sm, L);
+    const View v = make_view(sm, L, a.pt);
     long long* s_gaind = at<long long>(sm, L.gaind);
     long long* s_lossd = at<long long>(sm, L.lossd);
     long long* s_deadd = at<long long>(sm, L.deadd);
@@ -668,7 +654,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 #pragma unroll
       for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + fx_of(s_ce[d * Kp + pos]);
       int ninf;
-      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] + 1, 1, se, s_sqref[t] + fx_of(s_cq[pos]), ninf);
+      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] + 1, se, s_sqref[t] + fx_of(s_cq[pos]), ninf);
       s_gaind[pos] = term - s_termref[t];
       s_gninf[pos] = (int8_t)(ninf - (int)s_ninfref[t]);
     }
@@ -686,7 +672,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 #pragma unroll
       for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] - fx_of(s_ce[d * Kp + pos]);
       int ninf;
-      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] - 1, -1, se, s_sqref[t] - fx_of(s_cq[pos]), ninf);
+      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] - 1, se, s_sqref[t] - fx_of(s_cq[pos]), ninf);
       s_lossd[i] = term - s_termref[t];
       s_lninf[i] = (int8_t)(ninf - (int)s_ninfref[t]);
     }
@@ -741,15 +727,14 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
 // of its candidates died -- nearly always -- so the common path reads one
 // 48-byte chunk record and tests four intervals per call, and holds only
 // the chunk loop's state in registers.  Everything else about a row is out
-// of line (row_slow): a row with a candidate that may have died is drawn
+// of line (slow_rows): a row with a candidate that may have died is drawn
 // among the living, and a row that leaves the reference adds the staged
 // change of a single deviation.  Whether a slot died is answered by its
 // bloom bit and, when that is set, by regenerating the slot's death draw,
 // so a thread keeps no lists.  The slots a child's deviations meet are
-// kept as a 64-bit mask (bit slot mod 64): a child whose deviations meet a
-// slot twice needs that slot rescored exactly, so a child whose mask bit is
-// already set (a slot met twice, or two slots sharing a bit) goes to the
-// warp kernel.
+// kept as a 64-bit mask (bit slot mod 64): when a bit is met again (a slot
+// met twice, or two slots sharing a bit), the slots met more than once are
+// rescored exactly after the rows (slow_rows).
 
 // Whether slot t of the child whose death stream is pd died.
 __device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, const PhiloxRun& pd, uint2 key,
@@ -758,124 +743,194 @@ __device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, con
   return (word_of(r, (int)(t & 3u)) >> 8) < dthr[t];
 }
 
-// The outcome of one detection row that needs more than the interval test:
-// moved = the row left its reference option (d, hw, ninf, clut: its score,
-// key, infinite-term and clutter-count changes; met = (slot left + 1) << 16
-// | (slot joined + 1), 0 for clutter or a dead slot), bad = no option left.
-struct RowOut {
+// The rows a child's chunk loop noted, in one out-of-line call (the
+// parent's layout, view and generators are built once per child): each
+// row's uniform is regenerated; a row whose candidates' bloom meets the
+// child's dead slots is drawn among the living candidates in proportion to
+// their weights (clutter first), in the FP32 arithmetic of the warp kernel;
+// otherwise its option is the first whose cumulative threshold exceeds the
+// uniform.  A row that leaves its reference option adds the staged changes
+// of the slots it leaves and joins (a dead reference slot is not met: its
+// change is the death's).  When the deviations meet a slot more than once,
+// that slot's change is not the sum of the single changes but the exact
+// rescoring of the slot with every detection that joins and leaves it: the
+// slots met more than once are rescored with the warp kernel's functions
+// and inputs, so the keys are bit-identical.
+struct SlowSum {
   long long d;
   unsigned long long hw;
-  int ninf, clut;
-  uint32_t met;
-  int moved, bad;
+  int ninf, clut, bad;
 };
 
-// Row i of the parent staged at img (plan sizes Tp, Kp, Mp) for child n and
-// uniform k.  A row whose bloom meets the child's dead slots is drawn among
-// the living candidates in proportion to their weights (clutter first), in
-// the FP32 arithmetic of the warp kernel; otherwise its option is the first
-// whose cumulative threshold exceeds k.
 template <int DZ>
-__device__ __noinline__ RowOut row_slow(const unsigned char* img, const int Tp, const int Kp, const int Mp,
-                                        const int i, const uint32_t k, const bool may_hit,
-                                        const unsigned long long bloom, const uint32_t n, const uint2 key,
-                                        const int kappa_zero) {
+__device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, const unsigned char* img,
+                                          const int Tp, const int Kp, const int Mp, const uint16_t* s_slow,
+                                          const int nslow, const int stride, const unsigned long long bloom,
+                                          const uint32_t n, const uint2 key) {
+  constexpr int kE = 2 * 24;
   const Lay L = make_lay(DZ, Tp, Kp, Mp);
-  const View v = make_view(img, L);
+  const View v = make_view(img, L, *pt);
   const Scal& sc = *v.sc;
-  const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * n, key);
-  const uint4 R = v.row[i];
-  const uint32_t off = R.x;
-  const int nc = (int)(R.y & 0x7FFFu);
-  const int ref = (int)(R.y >> 16);
-  RowOut o;
-  o.d = 0;
-  o.hw = 0ull;
-  o.ninf = o.clut = 0;
-  o.met = 0u;
-  o.moved = o.bad = 0;
-  int opt = -1;
-  if (may_hit && (v.rowbl[i] & bloom)) {
-    auto is_dead = [&](int j) -> bool {
-      const uint32_t t = v.cslot[off + j];
-      return ((bloom >> (t & 63u)) & 1ull) && slot_died(v.dthr, pd, key, t);
-    };
-    uint32_t dm = 0u;
-    bool any = false;
-    for (int j = 0; j < nc; ++j)
-      if (is_dead(j)) {
-        any = true;
-        if (j < 32) dm |= 1u << j;
-      }
-    if (any) {
-      auto dead_j = [&](int j) -> bool { return j < 32 ? ((dm >> j) & 1u) != 0u : is_dead(j); };
-      const float w0 = kappa_zero ? 0.f : v.roww0[i];
-      float sum = w0;
+  const int T = sc.T;
+  const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
+  const PhiloxRun pd = philox_run(uid_lo, uid_hi, 2u * n, key);
+  const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * n + 1u, key);
+  SlowSum o{0, 0ull, 0, 0, 0};
+  uint16_t ep_slot[kE], ep_row[kE];
+  uint32_t ep_pos[kE];
+  int8_t ep_sg[kE];
+  int ne = 0;
+  unsigned long long metm = 0ull;
+  bool twice = false;
+  for (int q = 0; q < nslow; ++q) {
+    const int i = s_slow[q * stride];
+    const uint4 rr = philox_at(pr, (uint32_t)i >> 2, key);
+    const uint32_t k = word_of(rr, i & 3) >> 8;
+    const uint4 R = v.row[i];
+    const uint32_t off = R.x;
+    const int nc = (int)(R.y & 0x7FFFu);
+    const int ref = (int)(R.y >> 16);
+    int opt = -1;
+    if (v.rowbl[i] & bloom) {
+      auto is_dead = [&](int j) -> bool {
+        const uint32_t t = v.cslot[off + j];
+        return ((bloom >> (t & 63u)) & 1ull) && slot_died(v.dthr, pd, key, t);
+      };
+      uint32_t dm = 0u;
+      bool any = false;
       for (int j = 0; j < nc; ++j)
-        if (!dead_j(j)) sum += v.cw[off + j];
-      if (!(sum > 0.f)) {
-        o.bad = 1;
+        if (is_dead(j)) {
+          any = true;
+          if (j < 32) dm |= 1u << j;
+        }
+      if (any) {
+        auto dead_j = [&](int j) -> bool { return j < 32 ? ((dm >> j) & 1u) != 0u : is_dead(j); };
+        const float w0 = md->kappa_zero ? 0.f : v.roww0[i];
+        float sum = w0;
+        for (int j = 0; j < nc; ++j)
+          if (!dead_j(j)) sum += v.cw[off + j];
+        if (!(sum > 0.f)) {
+          o.bad = 1;
+          opt = 0;
+        } else {
+          const float xk = (float)k * 5.9604644775390625e-8f * sum;
+          float cum = w0;
+          int last = w0 > 0.f ? 0 : -1;
+          if (w0 > 0.f && xk < cum) opt = 0;
+          for (int j = 0; j < nc; ++j) {
+            if (dead_j(j)) continue;
+            const float w = v.cw[off + j];
+            if (!(w > 0.f)) continue;
+            cum += w;
+            last = j + 1;
+            if (opt < 0 && xk < cum) opt = j + 1;
+          }
+          if (opt < 0) opt = last < 0 ? 0 : last;
+        }
+      }
+    }
+    if (opt < 0) {
+      if (k - R.z < R.w - R.z) continue;   // the reference option
+      if (k < v.rowthr0[i]) {
         opt = 0;
       } else {
-        const float xk = (float)k * 5.9604644775390625e-8f * sum;
-        float cum = w0;
-        int last = w0 > 0.f ? 0 : -1;
-        if (w0 > 0.f && xk < cum) opt = 0;
-        for (int j = 0; j < nc; ++j) {
-          if (dead_j(j)) continue;
-          const float w = v.cw[off + j];
-          if (!(w > 0.f)) continue;
-          cum += w;
-          last = j + 1;
-          if (opt < 0 && xk < cum) opt = j + 1;
-        }
-        if (opt < 0) opt = last < 0 ? 0 : last;
+        int j = 0;
+        while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
+        opt = j + 1;
       }
     }
-  }
-  if (opt < 0) {
-    if (k - R.z < R.w - R.z) return o;   // the reference option
-    if (k < v.rowthr0[i]) {
-      opt = 0;
-    } else {
-      int j = 0;
-      while (j < nc - 1 && k >= v.cthr[off + j]) ++j;
-      opt = j + 1;
+    if (opt == ref) continue;
+    uint32_t rs1 = ref > 0 ? (uint32_t)v.cslot[off + ref - 1] + 1u : 0u;
+    const uint32_t ns1 = opt > 0 ? (uint32_t)v.cslot[off + opt - 1] + 1u : 0u;
+    o.hw += row_key(i, (int)ns1) - row_key(i, (int)rs1);
+    o.clut += (opt == 0) - (ref == 0);
+    if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(v.dthr, pd, key, rs1 - 1u)) rs1 = 0u;
+    unsigned long long m1 = 0ull, m2 = 0ull;
+    if (rs1) {
+      o.d += v.lossd[i];
+      o.ninf += v.lninf[i];
+      m1 = 1ull << ((rs1 - 1u) & 63u);
+      if (ne < kE) {
+        ep_slot[ne] = (uint16_t)rs1;
+        ep_sg[ne] = -1;
+        ep_pos[ne] = off + (uint32_t)ref - 1u;
+        ep_row[ne] = (uint16_t)i;
+        ++ne;
+      }
     }
+    if (ns1) {
+      o.d += v.gaind[off + opt - 1];
+      o.ninf += v.gninf[off + opt - 1];
+      m2 = 1ull << ((ns1 - 1u) & 63u);
+      if (ne < kE) {
+        ep_slot[ne] = (uint16_t)ns1;
+        ep_sg[ne] = 1;
+        ep_pos[ne] = off + (uint32_t)opt - 1u;
+        ep_row[ne] = (uint16_t)i;
+        ++ne;
+      }
+    }
+    twice |= (metm & (m1 | m2)) || (m1 & m2);
+    metm |= m1 | m2;
   }
-  if (opt == ref) return o;
-  // the row moves from its reference option to opt: the staged changes of
-  // the slots it leaves and joins (a dead reference slot is not met: its
-  // change is the death's)
-  uint32_t rs1 = ref > 0 ? (uint32_t)v.cslot[off + ref - 1] + 1u : 0u;
-  const uint32_t ns1 = opt > 0 ? (uint32_t)v.cslot[off + opt - 1] + 1u : 0u;
-  o.moved = 1;
-  o.hw = row_key(i, (int)ns1) - row_key(i, (int)rs1);
-  o.clut = (opt == 0) - (ref == 0);
-  if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(v.dthr, pd, key, rs1 - 1u)) rs1 = 0u;
-  if (rs1) {
-    o.d += v.lossd[i];
-    o.ninf += v.lninf[i];
+  if (!twice) return o;
+  // slots met more than once: exact term minus reference term minus the
+  // single changes added above
+  for (int w = 0; w < ne; ++w) {
+    const uint16_t sp = ep_slot[w];
+    int cnt = 0;
+    bool first = true;
+    for (int w2 = 0; w2 < ne; ++w2)
+      if (ep_slot[w2] == sp) {
+        ++cnt;
+        if (w2 < w) first = false;
+      }
+    if (cnt < 2 || !first) continue;
+    int dcnt = 0, sninf = 0;
+    long long dse[DZ], dsq = 0, single = 0;
+#pragma unroll
+    for (int d = 0; d < DZ; ++d) dse[d] = 0;
+    for (int w2 = w; w2 < ne; ++w2) {
+      if (ep_slot[w2] != sp) continue;
+      const uint32_t pos = ep_pos[w2];
+      const int sg = ep_sg[w2];
+      if (sg > 0) {
+        single += v.gaind[pos];
+        sninf += v.gninf[pos];
+      } else {
+        single += v.lossd[ep_row[w2]];
+        sninf += v.lninf[ep_row[w2]];
+      }
+      dcnt += sg;
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) dse[d] += sg * fx_of(v.ce[d * Kp + pos]);
+      dsq += sg * fx_of(v.cq[pos]);
+    }
+    const int t = (int)sp - 1;
+    long long se[DZ];
+#pragma unroll
+    for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + dse[d];
+    int ninf;
+    const long long term = slot_term<DZ>(*md, v, T, t, v.mref[t] + dcnt, se, v.sqref[t] + dsq, ninf);
+    o.d += term - v.termref[t] - single;
+    o.ninf += ninf - (int)v.ninfref[t] - sninf;
   }
-  if (ns1) {
-    o.d += v.gaind[off + opt - 1];
-    o.ninf += v.gninf[off + opt - 1];
-  }
-  o.met = (rs1 << 16) | ns1;
   return o;
 }
 
-// Rows a child's chunk loop sets aside for row_slow (per-thread list in
+// Rows a child's chunk loop sets aside for slow_rows (per-thread list in
 // shared memory, entry q at [q * blockDim.x]); a child with more goes to
 // the warp kernel.
 constexpr int kDrawSlow = 24;
+// chunks per iteration of the draw loop: two (1) or one (0)
+constexpr int kDrawPairs = 1;
 
 // Draws child n of the parent staged at img.  The chunk loop only tests the
 // reference intervals and notes the rows that need more (their uniform is
 // regenerated afterwards), so it holds nothing but its own state in
-// registers.  Returns false when the child must be drawn by the warp kernel
-// (more noted rows than the list holds, its deviations meet a slot twice,
-// or two met slots share a mask bit).
+// registers.  Slots its deviations meet more than once are rescored exactly
+// (slow_rows).  Returns false when the child must be drawn by the warp
+// kernel: more noted rows than the list holds.
 template <int DZ>
 __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned char* img, const Lay& L,
                                              const int h, const int n, const uint2 key, uint16_t* s_slow) {
@@ -919,11 +974,8 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
     const PhiloxRun pr = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n + 1u, key);
     const RowChunk* rch = at<RowChunk>(img, L.rch);
     const int nrca = sc.nrca;
-    uint32_t cc_next = nrca > 0 ? rch[0].head.x : 0u;   // one iteration ahead
-    for (int x = 0; x < nrca; ++x) {
-      const uint32_t cc = cc_next;
-      if (x + 1 < nrca) cc_next = rch[x + 1].head.x;
-      const uint4 r = philox_at(pr, cc, key);
+    // the interval tests of chunk x with its four words r
+    auto test_chunk = [&](int x, uint32_t cc, const uint4& r) {
       const uint4 hd = rch[x].head, lo = rch[x].lo, hi = rch[x].hi;
       const uint32_t hit = ((((unsigned long long)hd.w << 32) | hd.z) & bloom) ? hd.y : 0u;
 #pragma unroll
@@ -939,6 +991,23 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
         if (nslow < kDrawSlow) s_slow[nslow * (int)blockDim.x] = (uint16_t)i;
         ++nslow;
       }
+    };
+    int x = 0;
+    if (kDrawPairs) {
+      // two chunks per iteration: two independent Philox chains in flight
+      for (; x + 1 < nrca; x += 2) {
+        const uint32_t c0 = rch[x].head.x, c1 = rch[x + 1].head.x;
+        const uint4 r0 = philox_at(pr, c0, key);
+        const uint4 r1 = philox_at(pr, c1, key);
+        test_chunk(x, c0, r0);
+        test_chunk(x + 1, c1, r1);
+      }
+    }
+    uint32_t cc_next = x < nrca ? rch[x].head.x : 0u;   // one iteration ahead
+    for (; x < nrca; ++x) {
+      const uint32_t cc = cc_next;
+      if (x + 1 < nrca) cc_next = rch[x + 1].head.x;
+      test_chunk(x, cc, philox_at(pr, cc, key));
     }
   }
   if (nslow > kDrawSlow) return false;
@@ -969,29 +1038,15 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
       }
     }
   }
-  // the noted rows: drawn among the living when a candidate may have died,
-  // else from the thresholds; a row that leaves the reference option adds
-  // its change
+  // the noted rows (out of line, once per child)
   if (nslow) {
-    const PhiloxRun pr = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n + 1u, key);
-    unsigned long long metm = 0ull;
-    for (int q = 0; q < nslow; ++q) {
-      const int i = s_slow[q * (int)blockDim.x];
-      const uint4 r = philox_at(pr, (uint32_t)i >> 2, key);
-      const uint32_t k = word_of(r, i & 3) >> 8;
-      const RowOut o = row_slow<DZ>(img, a.T_max, a.K_max, a.M_plan, i, k, true, bloom, (uint32_t)n, key,
-                                    md.kappa_zero);
-      bad_row |= o.bad != 0;
-      if (!o.moved) continue;
-      hsh += o.hw;
-      dclut += o.clut;
-      delta += o.d;
-      dninf += o.ninf;
-      const unsigned long long m1 = (o.met >> 16) ? 1ull << (((o.met >> 16) - 1u) & 63u) : 0ull;
-      const unsigned long long m2 = (o.met & 0xFFFFu) ? 1ull << (((o.met & 0xFFFFu) - 1u) & 63u) : 0ull;
-      if ((metm & (m1 | m2)) || (m1 & m2)) return false;
-      metm |= m1 | m2;
-    }
+    const SlowSum o = slow_rows<DZ>(&md, &a.pt, img, a.T_max, a.K_max, a.M_plan, s_slow, nslow, (int)blockDim.x, bloom,
+                                    (uint32_t)n, key);
+    hsh += o.hw;
+    dclut += o.clut;
+    delta += o.d;
+    dninf += o.ninf;
+    bad_row |= o.bad != 0;
   }
   const long long score = sc.ref_score + delta + (md.kappa_zero ? 0LL : (long long)dclut * md.fx_log_kappa);
   const int ninf = sc.ninf_ref + dninf + (md.kappa_zero ? dclut : 0);
@@ -1010,7 +1065,7 @@ int expand_draw_smem(int threads) { return threads * kDrawSlow * (int)sizeof(uin
 // order parent * h_up + draw (a warp holds 32 consecutive children, of at
 // most two parents when h_up >= 32); no block-level synchronisation.
 template <int DZ>
-__global__ void __launch_bounds__(256, 3) draw_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256, 3) draw_kernel(const __grid_constant__ ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* s_slow = reinterpret_cast<uint16_t*>(sm) + threadIdx.x;
@@ -1217,7 +1272,7 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       m = v.mref[t] + acc_cnt[t];
 #pragma unroll
       for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + acc_se[d * T + t];
-      term = slot_term<DZ>(md, v, T, t, m, acc_cnt[t], se, v.sqref[t] + acc_sq[t], ninf);
+      term = slot_term<DZ>(md, v, T, t, m, se, v.sqref[t] + acc_sq[t], ninf);
     }
     my_delta += term - v.termref[t];
     my_dninf += ninf - (int)v.ninfref[t];
@@ -1315,7 +1370,7 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
   for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + g; c < count; c += nw) {
     const long long ci = MAT ? a.surv_idx[c] : (a.warp_all ? c : (long long)a.redo_list[c]);
     const int h = (int)(ci / HU), n = (int)(ci % HU);
-    const View v = make_view(a.img + (size_t)h * a.img_stride, L);
+    const View v = make_view(a.img + (size_t)h * a.img_stride, L, a.pt);
     if (v.sc->bad) continue;
     warp_child<DZ, MAT>(a, v, v.sc->T, a.K_max, M, h, n, (int)c, key, gb, WL);
   }

@@ -227,6 +227,25 @@ __global__ void table_count_kernel(Model md, CompTable ct, PairTable pt, const F
     }
   }
   if (lane == 0) pt.cnt[c] = cnt;
+  // the m-only parts of the component's alive term, m = lane + 1
+  if (md.score_mode == 0 && (uint32_t)c < (uint32_t)pt.slm_cap && lane < kSlmM) {
+    constexpr int NP = DZ * (DZ + 1) / 2;
+    float HPH[DZ][DZ];
+#pragma unroll
+    for (int x = 0; x < DZ; ++x)
+#pragma unroll
+      for (int y = x; y < DZ; ++y) {
+        const float v = ct.cov[(size_t)pidx(md.dx, x, y) * ct.cap + c];
+        HPH[x][y] = v;
+        HPH[y][x] = v;
+      }
+    const SlotM<DZ> sm = make_slot_m<DZ>(md, HPH, ct.logp[c], lane + 1);
+    const size_t cap = (size_t)pt.slm_cap;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pt.slm[((size_t)lane * (NP + 1) + k) * cap + c] = sm.Sinv[k];
+    pt.slm[((size_t)lane * (NP + 1) + NP) * cap + c] = sm.c;
+    pt.sln[(size_t)lane * cap + c] = (int8_t)sm.ninf;
+  }
   }
 }
 
