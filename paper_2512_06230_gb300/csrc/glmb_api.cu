@@ -26,7 +26,7 @@ enum { kStagePredict = 0, kStageTable, kStageExpand, kStageSelect, kStageMat, kS
        kStageEstimates, kNumStages };
 
 // device scalar slots
-enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_REDO = 7, S_KFULL = 8,
+enum { S_ERR = 0, S_FP64 = 1, S_MAXT = 2, S_MAXK = 3, S_NUPD = 4, S_NKEEP = 5, S_K = 6, S_REDO = 7, S_STAGE = 8, S_KFULL = 9,
        S_N = 16 };
 
 }  // namespace
@@ -152,8 +152,16 @@ struct glmb_handle {
   int exp_smem = 0, exp_ctas = 0;
   int exp_plan[4] = {0, 0, 0, 0};   // T, K, M, threads of the last expansion
   int redo_count = 0;
+  int lse_parts = 1;    // log-sum-exp partials the last expansion wrote
   // launch plan of the frame in progress, and captured frame graphs
   Plan plan{};
+  // a kernel node of a captured graph that takes the frame's Philox key,
+  // with the arguments it was captured with
+  struct KeyNode {
+    cudaGraphNode_t node;
+    cudaKernelNodeParams p;
+    ExpandArgs a;
+  };
   struct CachedGraph {
     int hcur;
     unsigned prof;
@@ -162,6 +170,8 @@ struct glmb_handle {
     long long n_kernels;
     int smem;              // shared memory per CTA of its expansion
     long long last_use;
+    cudaGraph_t graph;     // kept while exec lives: its key nodes are set per replay
+    std::vector<KeyNode> key_nodes;
   };
   std::vector<CachedGraph> graphs;
   bool capturing = false;
@@ -189,6 +199,13 @@ glmb_status fail(glmb_handle* h, glmb_status st, const char* fmt, ...) {
   va_end(ap);
   if (h) h->err = buf;
   return st;
+}
+
+void drop_graph(glmb_handle::CachedGraph& g) {
+  cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g.exec = nullptr;
+  g.graph = nullptr;
 }
 
 #define CU(call)                                                                    \
@@ -431,7 +448,7 @@ glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
     return fail(h, GLMB_E_INVALID, "set_launch_options: unknown option bits 0x%x", opts);
   if (opts != h->launch_opts) {
     cudaStreamSynchronize(h->stream);
-    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : h->graphs) drop_graph(g);
     h->graphs.clear();
   }
   h->launch_opts = opts;
@@ -450,7 +467,7 @@ glmb_status glmb_set_step_estimates(glmb_handle* h, int on) {
   if (h->step_estimates != (on != 0)) {
     // captured graphs were built with the other setting
     cudaStreamSynchronize(h->stream);
-    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : h->graphs) drop_graph(g);
     h->graphs.clear();
   }
   h->step_estimates = on != 0;
@@ -592,6 +609,8 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->redo_list, h->cap_children) &&
             dalloc(h, &h->pw.blk_max, 4097) && dalloc(h, &h->pw.blk_sum, 4097) &&
             dalloc(h, &h->pw.blk_done, 4) && dalloc(h, &h->pw.lse, 2) && dalloc(h, &h->pw.thr, 1) &&
+            dalloc(h, &h->pw.part_max, kMaxLseParts) && dalloc(h, &h->pw.part_sum, kMaxLseParts) &&
+            dalloc(h, &h->pw.part_cnt, kMaxLseParts) &&
             dalloc(h, &h->pw.hist, 4096) && dalloc(h, &h->pw.sel, 4) &&
             dalloc(h, &h->pw.flags, h->cap_children) &&
             dalloc(h, &h->pw.flags_tmp, scan_tmp_elems(h->cap_children)) &&
@@ -630,7 +649,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
 glmb_status glmb_destroy(glmb_handle* h) {
   if (!h) return GLMB_OK;
   cudaStreamSynchronize(h->stream);
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->graphs) drop_graph(g);
   dev_free_raw(h, h->img);
   dev_free_raw(h, h->pt.slm);
   dev_free_raw(h, h->pt.sln);
@@ -793,11 +812,14 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
   a.warp_all = p.thread ? 0 : 1;
   a.redo_list = h->redo_list;
   a.redo_count = h->d_scal + S_REDO;
+  a.stage_next = h->d_scal + S_STAGE;
   a.materialize = mat ? 1 : 0;
   a.err = h->d_scal + S_ERR;
   a.gc_flag = h->gc_flag;
   a.max_T = h->d_scal + S_MAXT;
   a.max_K = h->d_scal + S_MAXK;
+  a.key_x = h->md.seed_lo;
+  a.key_y = h->md.seed_hi ^ (uint32_t)h->frame;
   return a;
 }
 
@@ -807,7 +829,7 @@ glmb_status ensure_img(glmb_handle* h, const Plan& p) {
   const size_t need = (size_t)h->cap_h * (size_t)expand_image_bytes(h->md.dz, p.T, p.K, p.M);
   if (need <= h->img_alloc) return GLMB_OK;
   CU(cudaStreamSynchronize(h->stream));
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->graphs) drop_graph(g);
   h->graphs.clear();
   dev_free_raw(h, h->img);
   h->img = nullptr;
@@ -829,7 +851,7 @@ glmb_status ensure_slm(glmb_handle* h, long long need) {
   const long long cap = std::min<long long>(h->cap_comp, ((need + need / 2 + 255) / 256) * 256);
   const int NP = h->md.dz * (h->md.dz + 1) / 2;
   CU(cudaStreamSynchronize(h->stream));
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->graphs) drop_graph(g);
   h->graphs.clear();
   dev_free_raw(h, h->pt.slm);
   dev_free_raw(h, h->pt.sln);
@@ -857,8 +879,9 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   a.child_status = h->child_status;
   a.child_alive = h->child_alive;
   const int img = (int)a.img_stride;
-  // stage: one CTA of p.st_thr threads per parent (persistent grid)
-  const int st_smem = p.smem ? img : 0;
+  // stage: CTAs of p.st_thr threads, each taking the next parent from a
+  // counter (persistent grid)
+  const int st_smem = (p.smem ? img : 0) + 16;   // the image, and the next-parent word
   const int st_thr = p.st_thr;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
@@ -892,12 +915,13 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   h->exp_plan[2] = p.M;
   h->exp_plan[3] = p.thread ? d_thr : w_thr;
   prof_begin(h, kStageExpand);
-  CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, sizeof(unsigned), s));
+  CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, 2 * sizeof(unsigned), s));   // S_REDO, S_STAGE
   launch_expand_kernel(a, ExpandKernel::kStage, st_grid, st_thr, st_smem, s);
   if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
   launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
-  launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status, h->d_scal + S_ERR,
-               p.fixed ? 8 * n_sm : std::max(1, std::min(h->H, 8 * n_sm)), s);
+  h->lse_parts = std::min(kMaxLseParts, p.fixed ? 8 * n_sm : std::max(1, std::min(h->H, 8 * n_sm)));
+  launch_dedup(h->d_fs, h_up, h->child_key, h->child_hash, h->child_status, h->d_scal + S_ERR, h->pw,
+               h->lse_parts, s);
   prof_end(h, kStageExpand);
   return GLMB_OK;
 }
@@ -916,7 +940,8 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   CompTable& A = h->comps[h->cur];
   CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
   prof_begin(h, kStageSelect);
-  if (!launch_select_cluster(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nbits, h->child_alive, P, O,
+  if (!launch_select_cluster(h->child_key, h->d_fs, h_up, h->pw, h->lse_parts, log_tau, h->cap_h, nbits,
+                             h->child_alive, P, O,
                              h->d_scal + S_ERR, h->cap_entries, s)) {
     launch_lse(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nblk, s);
     launch_select(h->child_key, h->d_fs, h_up, nbits, h->pw, nblk, s);
@@ -993,7 +1018,7 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   // 3.51 ms in shared memory at one CTA per SM; on the 2-D mid scene, 19 KB
   // images, shared memory stayed faster)
   const int img_bytes = expand_image_bytes(dz, p.T, p.K, p.M);
-  p.smem = img_bytes <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
+  p.smem = img_bytes + 16 <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
            (8LL * img_bytes <= (long long)h->smem_per_sm || (h->launch_opts & GLMB_OPT_STAGE_SHARED));
   // staging threads: 256 in shared memory, or for few parents (each parent's
   // work spread over more threads); else 64, so that more parents are in
@@ -1003,8 +1028,10 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   p.Gw = p.Gm = 0;
   for (int g = h->tune.warp_cta_warps; g >= 1 && !p.Gw; --g)
     if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
-  for (int g = 8; g >= 1 && !p.Gm; --g)
-    if (expand_warp_smem(dz, 1, p.T, g) <= h->smem_limit) p.Gm = g;
+  // materialisation: the CTA size that keeps the most warps resident (its
+  // per-warp work area is large, so eight-warp CTAs would leave an SM with
+  // one CTA and shared memory unused)
+  p.Gm = expand_warp_best_cta(dz, 1, p.T, 8, h->smem_limit);
   return p.T <= 32767 && p.Gw > 0 && p.Gm > 0;
 }
 
@@ -1298,25 +1325,53 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
           if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_kernels;
         }
       g_launches -= n_kernels;   // counted once per replay below, not at capture
+      std::vector<glmb_handle::KeyNode> key_nodes;
+      for (size_t ni = 0; ni < n_nodes; ++ni) {
+        cudaGraphNodeType ty;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphNodeGetType(nodes[ni], &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel ||
+            cudaGraphKernelNodeGetParams(nodes[ni], &kp) != cudaSuccess || !expand_kernel_takes_key(kp.func))
+          continue;
+        glmb_handle::KeyNode kn;
+        kn.node = nodes[ni];
+        kn.p = kp;
+        kn.p.kernelParams = nullptr;
+        kn.p.extra = nullptr;
+        std::memcpy(&kn.a, kp.kernelParams[0], sizeof(ExpandArgs));
+        key_nodes.push_back(kn);
+      }
       const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ie != cudaSuccess) return fail(h, GLMB_E_CUDA, "step: graph instantiation: %s", cudaGetErrorString(ie));
+      if (ie != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(h, GLMB_E_CUDA, "step: graph instantiation: %s", cudaGetErrorString(ie));
+      }
       if (h->graphs.size() >= 32) {
         // evict the least recently replayed graph
         int lru = 0;
         for (int gi = 1; gi < (int)h->graphs.size(); ++gi)
           if (h->graphs[gi].last_use < h->graphs[lru].last_use) lru = gi;
-        cudaGraphExecDestroy(h->graphs[lru].exec);
+        drop_graph(h->graphs[lru]);
         h->graphs.erase(h->graphs.begin() + lru);
       }
-      h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels, plan_smem(h, q), 0});
+      h->graphs.push_back(glmb_handle::CachedGraph{h->hcur, h->prof_mask, q, exec, n_kernels, plan_smem(h, q), 0,
+                                                   graph, std::move(key_nodes)});
       ++h->n_captures;
       h->capture_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_cap).count();
       best = (int)h->graphs.size() - 1;
     }
     h->graphs[best].last_use = h->frame;
-    const glmb_handle::CachedGraph& g = h->graphs[best];
+    glmb_handle::CachedGraph& g = h->graphs[best];
     h->plan = g.plan;
+    // this frame's Philox key in the nodes that draw
+    const uint32_t key_y = h->md.seed_hi ^ (uint32_t)h->frame;
+    for (auto& kn : g.key_nodes) {
+      if (kn.a.key_y == key_y) continue;
+      kn.a.key_y = key_y;
+      void* args[1] = {&kn.a};
+      cudaKernelNodeParams q = kn.p;
+      q.kernelParams = args;
+      CU(cudaGraphExecKernelNodeSetParams(g.exec, kn.node, &q));
+    }
     g_launches += g.n_kernels;
     CU(cudaGraphLaunch(g.exec, h->stream));
     ++h->n_graph_launches;
@@ -1380,7 +1435,7 @@ glmb_status glmb_set_tuning(glmb_handle* h, const glmb_tuning* t) {
       (t->stage_threads != 0 && (t->stage_threads < 32 || t->stage_threads > 256 || t->stage_threads % 32)))
     return fail(h, GLMB_E_INVALID, "set_tuning: a launch shape out of range");
   cudaStreamSynchronize(h->stream);
-  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->graphs) drop_graph(g);
   h->graphs.clear();
   h->tune = *t;
   return GLMB_OK;
@@ -1848,7 +1903,7 @@ glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, 
   }
   if (mode != h->gate_mode) {
     // captured frame graphs were built for the other table path
-    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : h->graphs) drop_graph(g);
     h->graphs.clear();
   }
   h->gate_mode = mode;

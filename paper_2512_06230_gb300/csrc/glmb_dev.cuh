@@ -176,6 +176,11 @@ __device__ __forceinline__ PhiloxRun philox_run(uint32_t c0, uint32_t c1, uint32
   return p;
 }
 
+// The round keys k + r (W0, W1) are loop-invariant: with a key that is a
+// launch parameter they are formed once per thread in uniform registers.
+// Where the key is a per-thread value (an out-of-line function's argument),
+// philox_at_rk forms them per call instead, so they take no registers
+// across the caller's loop.
 __device__ __forceinline__ uint4 philox_at(const PhiloxRun& p, uint32_t cc, uint2 k) {
   constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
   const uint32_t w2 = p.w2 ^ cc;
@@ -183,9 +188,6 @@ __device__ __forceinline__ uint4 philox_at(const PhiloxRun& p, uint32_t cc, uint
   const uint32_t y0 = hiD ^ p.y0;
   const uint32_t hiE = __umulhi(M0, y0), loE = M0 * y0;     // round 3, first product
   uint4 c = make_uint4(loD ^ p.z0, p.z1, hiE ^ p.z2, loE);
-  // the round keys are formed here, per call: held across a caller's loop
-  // they would take 14 registers
-  asm volatile("" : "+r"(k.x), "+r"(k.y));
   k.x += 3u * 0x9E3779B9u;
   k.y += 3u * 0xBB67AE85u;
 #pragma unroll
@@ -197,6 +199,11 @@ __device__ __forceinline__ uint4 philox_at(const PhiloxRun& p, uint32_t cc, uint
     k.y += 0xBB67AE85u;
   }
   return c;
+}
+
+__device__ __forceinline__ uint4 philox_at_rk(const PhiloxRun& p, uint32_t cc, uint2 k) {
+  asm volatile("" : "+r"(k.x), "+r"(k.y));
+  return philox_at(p, cc, k);
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4& r, int b) {
@@ -216,6 +223,40 @@ __device__ __forceinline__ long long fx_of(float x) { return __float2ll_rn(x * k
 // which runs at a small fraction of the FP32 rate on this part)
 __device__ __forceinline__ float fx_to_f(long long v) {
   return (float)(int)(v >> 32) + (float)(uint32_t)v * 2.3283064365386963e-10f;
+}
+
+// One thread's running log-sum-exp of fixed-point keys: the largest key m
+// and a compensated (Kahan) FP32 sum of exp(key - m), rescaled when m grows;
+// n counts the keys.  Partials are combined in FP64 (lse_merge).
+struct LseAcc {
+  long long m;
+  float s, c;
+  unsigned n;
+  __device__ __forceinline__ LseAcc() : m(kKeyInvalid), s(0.f), c(0.f), n(0u) {}
+  __device__ __forceinline__ void add(long long k) {
+    ++n;
+    float term = 1.f;
+    if (m == kKeyInvalid) {
+      m = k;
+    } else if (k > m) {
+      const float sc = expf(fx_to_f(m - k));
+      s *= sc;
+      c *= sc;
+      m = k;
+    } else {
+      term = expf(fx_to_f(k - m));
+    }
+    const float y = term - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double sum() const { return (double)s - (double)c; }
+};
+
+// sum * exp(m - M): a partial (m, sum) rescaled to the overall maximum M
+__device__ __forceinline__ double lse_rescale(long long m, double sum, long long M) {
+  return (m == kKeyInvalid || !(sum > 0.0) || M == kKeyInvalid) ? 0.0 : sum * (double)expf(fx_to_f(m - M));
 }
 
 // a + b for hi/lo float pairs (Knuth two-sum, then renormalise)

@@ -93,6 +93,7 @@ struct ExpandArgs {
   int warp_all;           // warp kernel: every child of every parent (else the overflow list)
   uint32_t* redo_list;    // children the draw kernel could not take
   unsigned* redo_count;
+  unsigned* stage_next;   // staging: next parent to take (zero at the launch)
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
   unsigned long long* child_hash;   // [H * h_up] order-free key of (deaths, associations)
@@ -119,6 +120,10 @@ struct ExpandArgs {
   // records them for the next frame's plan and for a redo)
   unsigned* max_T;
   unsigned* max_K;
+  // Philox key of the frame, (seed_lo, seed_hi ^ frame): a launch parameter,
+  // so that the round keys are the same for every thread and stay out of
+  // the per-thread registers (a replayed frame graph has it set per frame)
+  uint32_t key_x, key_y;
 };
 // bytes of one parent's image (the staging kernel's shared memory when it
 // stages there)
@@ -137,9 +142,18 @@ void expand_init(int smem_limit);
 // mat_prep: one warp per retained parent
 void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int threads, int smem,
                           cudaStream_t s);
+// warps per CTA of the warp kernel (at most max_warps) that keep the most
+// warps resident on an SM, for per-parent slot counts up to T (0: none fits)
+int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem_limit);
+// whether a kernel of a captured graph takes the frame's Philox key in its
+// ExpandArgs (the draw and warp kernels)
+bool expand_kernel_takes_key(const void* fn);
+struct PruneWork;
 // marks duplicate children (status 2, key dropped), one block per parent
+// and writes the log-sum-exp partial of its unique children per block
+// (w.part_*; grid <= kMaxLseParts)
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
-                  int8_t* child_status, const unsigned* err, int grid, cudaStream_t s);
+                  int8_t* child_status, const unsigned* err, const PruneWork& w, int grid, cudaStream_t s);
 
 // ---- normalisation, truncation, track update, estimates (kernels_prune.cu) ----
 struct PruneWork {
@@ -156,7 +170,14 @@ struct PruneWork {
   long long* surv_idx;          // [cap_h]
   unsigned* counts;             // [8]: n_surv, n_entries, n_unique, max alive, [4..5] scan total
   unsigned* err;                // device error flags
+  // log-sum-exp partials of the unique children, one per block of the
+  // duplicate-marking kernel (kMaxLseParts at most): maximum key, sum of
+  // exp(key - maximum), count
+  long long* part_max;
+  double* part_sum;
+  unsigned* part_cnt;
 };
+constexpr int kMaxLseParts = 4096;
 // the children are the fs->H * h_up entries of keys
 void launch_lse(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
                 int h_max, int nblk, cudaStream_t s);
@@ -167,9 +188,11 @@ void launch_compact(const long long* keys, const FrameDev* fs, int h_up, long lo
 // the whole of launch_lse + launch_select + launch_compact + launch_finalize
 // in one launch of a thread-block cluster (select_cluster.cu); false when
 // the device cannot run the cluster (the caller then launches the chain)
-bool launch_select_cluster(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, double log_tau,
-                           int h_max, int nbits, const uint16_t* child_alive, const HypTable& parents,
-                           const HypTable& out, unsigned* err, long long cap_entries, cudaStream_t s);
+// (n_part: the duplicate-marking kernel's log-sum-exp partials)
+bool launch_select_cluster(const long long* keys, const FrameDev* fs, int h_up, PruneWork w, int n_part,
+                           double log_tau, int h_max, int nbits, const uint16_t* child_alive,
+                           const HypTable& parents, const HypTable& out, unsigned* err, long long cap_entries,
+                           cudaStream_t s);
 // cluster size the fused selection runs with (0: cannot run)
 int select_cluster_size();
 void launch_finalize(PruneWork w, const long long* keys, const uint16_t* child_alive,

@@ -32,6 +32,11 @@
 //             association, requested once per parent.
 // The duplicate test keys a child by the order-free sum of mix64 keys of its
 // deviations and deaths.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "glmb_kernels.h"
 
 namespace glmb {
@@ -52,12 +57,14 @@ struct Lay {
 // draw reads it: head = (chunk index, bit b set when row 4 cc + b has a
 // candidate slot that can die, low and high words of the bloom of those
 // slots over the four rows), then the four rows' reference intervals
-// [lo, hi) of the 24-bit uniform (rows without candidates, or beyond the
-// detections: [0, 2^24)).
+// [lo, hi) of the 24-bit uniform u = word >> 8 (rows without candidates, or
+// beyond the detections: [0, 2^24)), held as base = lo << 8 and
+// span = ((hi - lo) << 8) - 1 (mod 2^32): u is in [lo, hi) exactly when
+// word - base <= span, as unsigned 32-bit arithmetic (hi - lo >= 1).
 struct RowChunk {
   uint4 head;
-  uint4 lo;
-  uint4 hi;
+  uint4 base;
+  uint4 span;
 };
 
 struct Bump {
@@ -600,8 +607,9 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       if (mask) {
         RowChunk rc;
         rc.head = make_uint4((uint32_t)cc, dmask, (uint32_t)bl, (uint32_t)(bl >> 32));
-        rc.lo = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        rc.hi = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        rc.base = make_uint4(lo[0] << 8, lo[1] << 8, lo[2] << 8, lo[3] << 8);
+        rc.span = make_uint4(((hi[0] - lo[0]) << 8) - 1u, ((hi[1] - lo[1]) << 8) - 1u, ((hi[2] - lo[2]) << 8) - 1u,
+                             ((hi[3] - lo[3]) << 8) - 1u);
         s_rch[atomicAdd(&sc.nrca, 1)] = rc;
       }
     }
@@ -690,13 +698,17 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   }
 }
 
-// Persistent: each CTA stages parents blockIdx.x, blockIdx.x + gridDim.x, ...
+// Persistent: CTA b stages parent b first (the launch spreads CTAs over the
+// SMs, so a frame with few parents gets one SM each), then takes the next
+// parent from a counter until none is left (parents differ in slots and
+// pairs, so a fixed share per CTA would leave SMs idle at the end).
 // SMEM: staged in shared memory and copied to the image (16-byte words).
 template <int DZ, bool SMEM>
 __global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
+  int& s_next = *reinterpret_cast<int*>(sm + (SMEM ? L.total : 0));   // after the staged image
   const int H = a.fs->H;
   // a table that failed (e.g. pairs beyond capacity, whose offsets then run
   // past the pair arrays) is not staged; the frame is abandoned.  The flags
@@ -704,9 +716,8 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
   // are set by its CTAs while others start, so they must not stop a CTA:
   // every parent's counts are recorded
   if (*(volatile const unsigned*)a.err & (kErrFatal & ~(kErrSlots | kErrChkComp))) return;
-  for (int h = blockIdx.x; h < H; h += gridDim.x) {
+  for (int h = blockIdx.x; h < H;) {
     unsigned char* img = a.img + (size_t)h * a.img_stride;
-    __syncthreads();   // the previous parent's copy-out has read shared memory
     stage_parent<DZ>(a, h, L, SMEM ? sm : img);
     __syncthreads();
     if (SMEM) {
@@ -716,6 +727,10 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
       uint4* dst = reinterpret_cast<uint4*>(img);
       for (int w = threadIdx.x; w < (bytes + 15) / 16; w += blockDim.x) dst[w] = src[w];
     }
+    __syncthreads();   // the copy-out has read shared memory, s_next is free
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + (int)atomicAdd(a.stage_next, 1u);
+    __syncthreads();
+    h = s_next;
   }
 }
 
@@ -739,7 +754,7 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
 // Whether slot t of the child whose death stream is pd died.
 __device__ __forceinline__ bool slot_died(const uint32_t* __restrict__ dthr, const PhiloxRun& pd, uint2 key,
                                           uint32_t t) {
-  const uint4 r = philox_at(pd, t >> 2, key);
+  const uint4 r = philox_at_rk(pd, t >> 2, key);
   return (word_of(r, (int)(t & 3u)) >> 8) < dthr[t];
 }
 
@@ -784,7 +799,7 @@ __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, 
   bool twice = false;
   for (int q = 0; q < nslow; ++q) {
     const int i = s_slow[q * stride];
-    const uint4 rr = philox_at(pr, (uint32_t)i >> 2, key);
+    const uint4 rr = philox_at_rk(pr, (uint32_t)i >> 2, key);
     const uint32_t k = word_of(rr, i & 3) >> 8;
     const uint4 R = v.row[i];
     const uint32_t off = R.x;
@@ -922,6 +937,10 @@ __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, 
 // shared memory, entry q at [q * blockDim.x]); a child with more goes to
 // the warp kernel.
 constexpr int kDrawSlow = 24;
+// Dead slots the first death pass records for the score pass (the same
+// kind of per-thread list, after the noted rows); a child with more
+// regenerates its death draws instead.
+constexpr int kDrawDead = 8;
 // chunks per iteration of the draw loop: two (1) or one (0)
 constexpr int kDrawPairs = 1;
 
@@ -933,7 +952,8 @@ constexpr int kDrawPairs = 1;
 // kernel: more noted rows than the list holds.
 template <int DZ>
 __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned char* img, const Lay& L,
-                                             const int h, const int n, const uint2 key, uint16_t* s_slow) {
+                                             const int h, const int n, const uint2 key, uint16_t* s_slow,
+                                             uint16_t* s_dead) {
   const Model& md = a.md;
   const Scal& sc = *at<Scal>(img, L.scal);
   unsigned long long bloom = 0ull;
@@ -960,6 +980,7 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
         const uint32_t thb = b == 0 ? th.x : b == 1 ? th.y : b == 2 ? th.z : th.w;
         if (((mask >> b) & 1u) && (word_of(r, b) >> 8) < thb) {
           const uint32_t t = 4u * cc + (uint32_t)b;
+          if (nd < kDrawDead) s_dead[nd * (int)blockDim.x] = (uint16_t)t;
           ++nd;
           if (srow[t]) bloom |= 1ull << (t & 63u);
         }
@@ -976,18 +997,21 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
     const int nrca = sc.nrca;
     // the interval tests of chunk x with its four words r
     auto test_chunk = [&](int x, uint32_t cc, const uint4& r) {
-      const uint4 hd = rch[x].head, lo = rch[x].lo, hi = rch[x].hi;
+      const uint4 hd = rch[x].head, base = rch[x].base, span = rch[x].span;
       const uint32_t hit = ((((unsigned long long)hd.w << 32) | hd.z) & bloom) ? hd.y : 0u;
+      // bit b: row 4 cc + b left its reference interval
+      uint32_t out = 0u;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint32_t k = word_of(r, b) >> 8;
-        const uint32_t l = word_of(lo, b), u = word_of(hi, b);
-        const bool in_ref = k - l < u - l;
-        if (in_ref && !((hit >> b) & 1u)) continue;   // the reference option
+      for (int b = 0; b < 4; ++b)
+        if (word_of(r, b) - word_of(base, b) > word_of(span, b)) out |= 1u << b;
+      uint32_t look = out | hit;   // nearly always 0: all four keep the reference
+      while (look) {
+        const int b = __ffs(look) - 1;
+        look &= look - 1u;
         const uint32_t i = 4u * cc + (uint32_t)b;
         // a row of a chunk whose bloom meets the dead slots', still in its
         // reference interval: noted only if its own candidates' bloom does
-        if (in_ref && !(at<unsigned long long>(img, L.rowbl)[i] & bloom)) continue;
+        if (!((out >> b) & 1u) && !(at<unsigned long long>(img, L.rowbl)[i] & bloom)) continue;
         if (nslow < kDrawSlow) s_slow[nslow * (int)blockDim.x] = (uint16_t)i;
         ++nslow;
       }
@@ -1016,7 +1040,17 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
   long long delta = 0;
   int dclut = 0, dninf = 0;
   bool bad_row = false;
-  if (nd) {
+  if (nd && nd <= kDrawDead) {
+    const long long* deadd = at<long long>(img, L.deadd);
+    const int8_t* dninf8 = at<int8_t>(img, L.dninf);
+    for (int q = 0; q < nd; ++q) {
+      const int t = s_dead[q * (int)blockDim.x];
+      hsh += dead_key(t);
+      delta += deadd[t];
+      dninf += dninf8[t];
+    }
+  } else if (nd) {
+    // more deaths than the list holds: their draws again
     const uint32_t* dpc = at<uint32_t>(img, L.dpc);
     const uint32_t* dthr = at<uint32_t>(img, L.dthr);
     const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n, key);
@@ -1059,7 +1093,7 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
   return true;
 }
 
-int expand_draw_smem(int threads) { return threads * kDrawSlow * (int)sizeof(uint16_t); }
+int expand_draw_smem(int threads) { return threads * (kDrawSlow + kDrawDead) * (int)sizeof(uint16_t); }
 
 // Persistent over the children of the frame, one thread per child in the
 // order parent * h_up + draw (a warp holds 32 consecutive children, of at
@@ -1069,9 +1103,10 @@ __global__ void __launch_bounds__(256, 3) draw_kernel(const __grid_constant__ Ex
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* s_slow = reinterpret_cast<uint16_t*>(sm) + threadIdx.x;
+  uint16_t* s_dead = s_slow + kDrawSlow * blockDim.x;
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int H = a.fs->H, HU = a.md.h_up;
-  const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
+  const uint2 key = make_uint2(a.key_x, a.key_y);
   // a failed table or staging (the frame is redone or abandoned): the
   // images may be stale, so nothing is drawn
   if (*(volatile const unsigned*)a.err & kErrFatal) return;
@@ -1082,7 +1117,8 @@ __global__ void __launch_bounds__(256, 3) draw_kernel(const __grid_constant__ Ex
     const int n = (int)(j - (long long)h * HU);
     const unsigned char* img = a.img + (size_t)h * a.img_stride;
     if (at<Scal>(img, L.scal)->bad) continue;
-    if (!thread_child<DZ>(a, img, L, h, n, key, s_slow)) a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)j;
+    if (!thread_child<DZ>(a, img, L, h, n, key, s_slow, s_dead))
+      a.redo_list[atomicAdd(a.redo_count, 1u)] = (uint32_t)j;
   }
 }
 
@@ -1335,7 +1371,7 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
   const WLay WL = make_wlay(DZ, MAT, a.T_max);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int HU = a.md.h_up, M = a.fs->M;
-  const uint2 key = make_uint2(a.md.seed_lo, a.md.seed_hi ^ (uint32_t)a.fs->frame);
+  const uint2 key = make_uint2(a.key_x, a.key_y);
   // a frame already abandoned (e.g. entries beyond capacity) writes
   // nothing; a failed table or staging leaves the images stale
   if (MAT && (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs))) return;
@@ -1418,16 +1454,25 @@ __device__ __forceinline__ int dedup_table_size(int HU) {
   return ts;
 }
 
-__global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long* child_key,
-                             const unsigned long long* __restrict__ child_hash, int8_t* child_status,
-                             const unsigned* err) {
+__global__ void __launch_bounds__(128) dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long* child_key,
+                                                   const unsigned long long* __restrict__ child_hash,
+                                                   int8_t* child_status, const unsigned* err, long long* part_max,
+                                                   double* part_sum, unsigned* part_cnt) {
   pdl_enter();
   if (*(volatile const unsigned*)err & kErrFatal) return;   // the draws were skipped
   extern __shared__ unsigned long long s_k[];   // [ts] keys, 0 = empty
   const int ts = dedup_table_size(HU);
   uint32_t* s_n = reinterpret_cast<uint32_t*>(s_k + ts);   // [ts] lowest draw
   __shared__ uint32_t s_zero;                                // lowest draw whose key is 0
+  __shared__ long long s_pm[4];
+  __shared__ double s_ps[4];
+  __shared__ unsigned s_pc[4];
   const int H = fs->H;
+  // a block beyond the parents (fixed launches are sized for the most
+  // parents a frame can have) holds an empty partial; the selection reads
+  // only the first H partials
+  if (blockIdx.x >= H) return;
+  LseAcc acc;   // this thread's unique children
   for (int h = blockIdx.x; h < H; h += gridDim.x) {
     const size_t base = (size_t)h * HU;
     __syncthreads();
@@ -1467,18 +1512,53 @@ __global__ void dedup_kernel(const FrameDev* __restrict__ fs, int HU, long long*
       if (low < (uint32_t)n) {
         child_status[base + n] = 2;
         child_key[base + n] = kKeyInvalid;
+      } else {
+        acc.add(child_key[base + n]);
       }
     }
+  }
+  // the block's partial: maximum, sum rescaled to it (FP64), count
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long M = acc.m;
+  unsigned c = acc.n;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    M = max(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+    c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  }
+  if (lane == 0) {
+    s_pm[wp] = M;
+    s_pc[wp] = c;
+  }
+  __syncthreads();
+  M = s_pm[0];
+  c = s_pc[0];
+  for (int w = 1; w < nw; ++w) {
+    M = max(M, s_pm[w]);
+    c += s_pc[w];
+  }
+  double r = lse_rescale(acc.m, acc.sum(), M);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+  if (lane == 0) s_ps[wp] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += s_ps[w];
+    part_max[blockIdx.x] = M;
+    part_sum[blockIdx.x] = t;
+    part_cnt[blockIdx.x] = c;
   }
 }
 
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,
-                  int8_t* child_status, const unsigned* err, int grid, cudaStream_t s) {
+                  int8_t* child_status, const unsigned* err, const PruneWork& w, int grid, cudaStream_t s) {
   int ts = 64;
   while (ts < 2 * HU) ts <<= 1;
   const int smem = ts * 12;
   if (smem > 48 * 1024) cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  launch_k(dedup_kernel, grid, 128, smem, s, fs, HU, child_key, child_hash, child_status, err);
+  launch_k(dedup_kernel, std::min(grid, kMaxLseParts), 128, smem, s, fs, HU, child_key, child_hash, child_status,
+           err, w.part_max, w.part_sum, w.part_cnt);
 }
 
 // ---- host side ----
@@ -1523,6 +1603,38 @@ void launch_expand_kernel(const ExpandArgs& a, ExpandKernel k, int grid, int thr
                           cudaStream_t s) {
   if (grid <= 0) return;
   launch_k(kernel_of(a, k), grid, threads, smem, s, a);
+}
+
+int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem_limit) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, int> memo;
+  const auto key = std::make_tuple(dz, materialize, T, max_warps, smem_limit);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  int best = 0, best_res = 0;
+  for (int g = 1; g <= max_warps; ++g) {
+    const int smem = expand_warp_smem(dz, materialize, T, g);
+    if (smem > smem_limit) break;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_fn(dz, materialize != 0), 32 * g, smem) !=
+        cudaSuccess)
+      per_sm = 0;
+    if (per_sm * g >= best_res && per_sm > 0) {   // ties: the larger CTA
+      best_res = per_sm * g;
+      best = g;
+    }
+  }
+  cudaGetLastError();
+  memo[key] = best;
+  return best;
+}
+
+bool expand_kernel_takes_key(const void* fn) {
+  for (int dz = 2; dz <= 3; ++dz)
+    if (fn == (const void*)draw_fn(dz) || fn == (const void*)warp_fn(dz, false) || fn == (const void*)warp_fn(dz, true))
+      return true;
+  return false;
 }
 
 }  // namespace glmb
