@@ -105,6 +105,9 @@ struct glmb_handle {
   unsigned long long* hkeys = nullptr;
   uint32_t* hvals = nullptr;
   uint32_t* upd_src = nullptr;
+  uint32_t* upd_slot = nullptr;   // update id -> hash slot
+  unsigned* d_hprev = nullptr;     // updates the last materialisation inserted
+  bool hash_dirty = false;         // a frame overflowed the update table: clear all of it
   uint32_t* upd_m = nullptr;
   long long* upd_se = nullptr;
   uint32_t* gc_flag = nullptr;
@@ -617,6 +620,7 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
             dalloc(h, &h->pw.surv_idx, h->cap_h) &&
             dalloc(h, &h->hkeys, hcap) && dalloc(h, &h->hvals, hcap) &&
             dalloc(h, &h->upd_src, h->cap_upd) && dalloc(h, &h->upd_m, h->cap_upd) &&
+            dalloc(h, &h->upd_slot, h->cap_upd) && dalloc(h, &h->d_hprev, 1) &&
             dalloc(h, &h->upd_se, h->cap_upd * dz) && dalloc(h, &h->gc_flag, h->cap_comp) &&
             dalloc(h, &h->gc_newpos, h->cap_comp) && dalloc(h, &h->d_ru, h->cap_meas);
   if (ok) {
@@ -950,7 +954,9 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
                     h->cap_entries, s);
   }
   prof_end(h, kStageSelect);
-  CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), s));
+  // the update hash table: only the slots the last materialisation filled
+  // are cleared (the whole table is cleared after a frame that failed)
+  launch_hash_reset(h->hkeys, h->upd_slot, h->d_hprev, (int)h->cap_upd, 2 * h->n_sm, s);
   CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));
   const long long capT = p.fixed ? h->cap_comp : std::max(h->T_work, 1);
   CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));   // set by the materialisation
@@ -967,6 +973,7 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   a.upd_m = h->upd_m;
   a.upd_se = h->upd_se;
   a.upd_count = h->d_scal + S_NUPD;
+  a.upd_slot = h->upd_slot;
   a.cap_upd = (int)h->cap_upd;
   const int m_thr = 32 * p.Gm;
   const int m_smem = expand_warp_smem(h->md.dz, 1, p.T, p.Gm);
@@ -985,7 +992,7 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   const int ggc = p.fixed ? 4 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
   launch_gc_remap(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP, h->upd_src, h->upd_m,
                   h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts, h->d_scal + S_ERR, O.comp,
-                  h->pw.counts + 1, h->cap_entries, h->hvals, h->hmask, ggc, s);
+                  h->pw.counts + 1, h->cap_entries, h->hvals, h->hmask, h->d_hprev, ggc, s);
   prof_end(h, kStageGc);
   CU(cudaGetLastError());
   return GLMB_OK;
@@ -1076,6 +1083,16 @@ void enqueue_estimates(glmb_handle* h, const HypTable& Y, const CompTable& A, co
   prof_end(h, kStageEstimates);
 }
 
+// the whole update hash table cleared (and the reset list emptied) after a
+// frame whose updates overflowed it; stream-ordered before the next frame
+glmb_status clear_hash_if_dirty(glmb_handle* h) {
+  if (!h->hash_dirty) return GLMB_OK;
+  CU(cudaMemsetAsync(h->hkeys, 0, ((size_t)h->hmask + 1) * sizeof(unsigned long long), h->stream));
+  CU(cudaMemsetAsync(h->d_hprev, 0, sizeof(unsigned), h->stream));
+  h->hash_dirty = false;
+  return GLMB_OK;
+}
+
 // results: the counters were copied by the frame's launches when
 // copies_enqueued (with the estimates when est_enqueued); redo, abandon or
 // commit
@@ -1090,6 +1107,8 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
   CU(cudaStreamSynchronize(h->stream));
   const unsigned* cnt = h->h_cnt;
   unsigned e = h->h_scal[S_ERR];
+  // updates beyond the table's capacity are not in the reset list
+  if (e & (kErrUpdates | kErrHash)) h->hash_dirty = true;
   if ((e & kErrSlots) && !(e & (kErrFatal & ~kErrSlots))) {
     // a parent had more gated pairs than planned: redo the expansion and
     // the pruning with the exact maxima of this frame
@@ -1101,11 +1120,13 @@ glmb_status finish_frame(glmb_handle* h, bool copies_enqueued = false, bool est_
       return abandon(GLMB_E_CAPACITY, "per-hypothesis table exceeds the supported sizes");
     if ((st = ensure_img(h, p)) != GLMB_OK) return abandon(st, "expansion images do not fit");
     CU(cudaMemsetAsync(h->d_scal + S_ERR, 0, sizeof(unsigned), h->stream));
+    if ((st = clear_hash_if_dirty(h)) != GLMB_OK) return st;
     if ((st = enqueue_expand(h, p)) != GLMB_OK) return st;
     if ((st = enqueue_prune(h, p)) != GLMB_OK) return st;
     if ((st = enqueue_results(h, false)) != GLMB_OK) return st;
     CU(cudaStreamSynchronize(h->stream));
     e = h->h_scal[S_ERR];
+    if (e & (kErrUpdates | kErrHash)) h->hash_dirty = true;
     est_enqueued = false;   // the estimates copied with the first pass are stale
   }
   if (e & kErrInput) return abandon(GLMB_E_INVALID, "non-finite detection");
@@ -1231,7 +1252,9 @@ glmb_status glmb_prune(glmb_handle* h) {
   if (!h) return GLMB_E_INVALID;
   if (h->stage != 2) return fail(h, GLMB_E_STATE, "prune: call glmb_update first");
   h->retained_valid = false;
-  glmb_status st = enqueue_prune(h, h->plan);
+  glmb_status st = clear_hash_if_dirty(h);
+  if (st != GLMB_OK) return st;
+  st = enqueue_prune(h, h->plan);
   if (st != GLMB_OK) return st;
   return finish_frame(h);
 }
@@ -1258,6 +1281,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
     h->frame -= 1;
     return fail(h, GLMB_E_CAPACITY, "step: per-hypothesis table does not fit in shared memory");
   }
+  if ((st = clear_hash_if_dirty(h)) != GLMB_OK) return st;
   // the frame's sizes, births and host detections go up with the frame: as
   // copy nodes of the graph when one is replayed, else as separate copies
   if ((st = upload_sizes(h, 1, !p.fixed)) != GLMB_OK) return st;

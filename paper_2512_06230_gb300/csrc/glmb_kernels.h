@@ -113,6 +113,7 @@ struct ExpandArgs {
   uint32_t* upd_m;             // update id -> |W|
   long long* upd_se;           // [dz][cap_upd] fixed-point sum of innovations
   uint32_t* upd_count;
+  uint32_t* upd_slot;          // update id -> its hash slot (cleared by the next frame's reset)
   int cap_upd;
   uint32_t* gc_flag;           // [T] set for old components the new hypotheses keep
   unsigned* err;
@@ -148,6 +149,10 @@ int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem
 // whether a kernel of a captured graph takes the frame's Philox key in its
 // ExpandArgs (the draw and warp kernels)
 bool expand_kernel_takes_key(const void* fn);
+// clears the hash slots of the n_prev updates recorded in upd_slot (the
+// previous materialisation's), instead of clearing the whole table
+void launch_hash_reset(unsigned long long* hkeys, const uint32_t* upd_slot, const unsigned* n_prev, int cap_upd,
+                       int grid, cudaStream_t s);
 struct PruneWork;
 // marks duplicate children (status 2, key dropped), one block per parent
 // and writes the log-sum-exp partial of its unique children per block
@@ -207,7 +212,8 @@ void launch_gc_remap(const Model& md, const CompTable& src, const CompTable& dst
                      const uint32_t* flag, const FrameDev* fs, const unsigned* n_keep_dev, const uint32_t* upd_src,
                      const uint32_t* upd_m, const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
                      const unsigned* n_surv_dev, unsigned* err, uint32_t* out_comp, const unsigned* n_entries_dev,
-                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, int grid, cudaStream_t s);
+                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, unsigned* n_upd_prev, int grid,
+                     cudaStream_t s);
 // device error flags that abandon a frame (state left untouched)
 constexpr unsigned kErrFatal = kErrPairs | kErrHash | kErrUpdates | kErrComps | kErrNumeric |
                                kErrEntries | kErrSlots | kErrInput | kErrGate | kErrTimeout | kErrChkSurv |

@@ -215,13 +215,25 @@ __device__ __forceinline__ SlotM<DZ> load_cslm(const float* slm, const int8_t* s
 
 // Term of slot t alive with m detections, built from H P H^T (kept out of
 // line: it is rare and needs many registers)
+struct TermOut {
+  long long term;
+  int ninf;
+};
 template <int DZ>
-__device__ __noinline__ long long slot_term_full(const Model& md, const float* s_hph, const float* s_logp,
-                                                 int T, int t, int m, const long long (&se)[DZ], long long sq,
-                                                 int& ninf) {
+struct SeVec {
+  long long v[DZ];
+};
+
+template <int DZ>
+__device__ __noinline__ TermOut slot_term_full(const Model& md, const float* s_hph, const float* s_logp, int T,
+                                               int t, int m, const SeVec<DZ> se, long long sq) {
+  // the sums come and the result goes by value, so a caller keeps them in
+  // registers (an array passed by reference would live in local memory)
   float HPH[DZ][DZ];
   slot_HPH<DZ>(s_hph, T, t, HPH);
-  return alive_term<DZ>(md, HPH, s_logp[t], m, se, sq, ninf);
+  TermOut o;
+  o.term = alive_term<DZ>(md, HPH, s_logp[t], m, se.v, sq, o.ninf);
+  return o;
 }
 
 // read-only view of a staged parent
@@ -301,7 +313,12 @@ __device__ __forceinline__ long long slot_term(const Model& md, const View& v, i
     const uint32_t c = v.comp[t];
     if (c < (uint32_t)v.slm_cap) return term_from<DZ>(md, load_cslm<DZ>(v.cslm, v.csln, v.slm_cap, m, c), m, se, sq, ninf);
   }
-  return slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, se, sq, ninf);
+  SeVec<DZ> sv;
+#pragma unroll
+  for (int d = 0; d < DZ; ++d) sv.v[d] = se[d];
+  const TermOut o = slot_term_full<DZ>(md, v.hph, v.logp, T, t, m, sv, sq);
+  ninf = o.ninf;
+  return o.term;
 }
 
 __device__ __forceinline__ bool bit_of(const uint32_t* m, int t) {
@@ -326,6 +343,7 @@ __device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long
 #pragma unroll
         for (int d = 0; d < DZ; ++d) a.upd_se[(size_t)d * a.cap_upd + id] = se[d];
         a.hvals[slot] = id;
+        a.upd_slot[id] = slot;
       } else {
         atomicOr(a.err, kErrUpdates);
         a.hvals[slot] = 0u;
@@ -340,6 +358,14 @@ __device__ uint32_t upd_insert(const ExpandArgs& a, uint32_t comp, unsigned long
 }
 
 // ====================== stage: one CTA per parent ======================
+// Detection rows with at most this many candidate slots are sorted and
+// weighed in registers (nearly all rows: a detection gates to one track or
+// a few).
+constexpr int kRowReg = 4;
+template <int N>
+struct FVec {
+  float v[N];
+};
 // Builds parent h's image at `sm` (shared memory, or the image itself).
 template <int DZ>
 __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm) {
@@ -494,6 +520,117 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
     for (int i = tid; i < M; i += nthr) {
       const uint32_t off = s_rowoff[i];
       const int nc = (int)(s_rowoff[i + 1] - off);
+      if (nc == 0) {
+        s_row[i] = make_uint4(off, 0u, 0u, kOne24);
+        s_rowthr0[i] = kOne24;
+        s_rowbl[i] = 0ull;
+        s_rowrk[i] = 0u;
+        s_roww0[i] = 1.f;
+        ++my_clut;
+        continue;
+      }
+      // row i: x = first candidate, y = count | may-die flag << 15 |
+      // reference option << 16, [z, w) = the uniforms that pick the reference
+      // option when every candidate is alive; the reference slot's sums
+      auto finish_row = [&](int ref, bool flag, uint32_t thr0, uint32_t lo, uint32_t hi, unsigned long long bl,
+                            float w0, int r, const FVec<DZ> e_ref, float q_ref) {
+        s_row[i] = make_uint4(off, (uint32_t)nc | (flag ? 0x8000u : 0u) | ((uint32_t)ref << 16), lo, hi);
+        s_rowthr0[i] = thr0;
+        s_rowbl[i] = bl;
+        s_rowrk[i] = ref > 0 ? (((uint32_t)r + 1u) << 16) | (off + ref - 1) : 0u;
+        s_roww0[i] = w0;
+        if (ref == 0) {
+          ++my_clut;
+        } else {
+          atomicAdd(&s_mref[r], 1);
+#pragma unroll
+          for (int d = 0; d < DZ; ++d)
+            atomicAdd((unsigned long long*)&s_seref[d * T + r], (unsigned long long)fx_of(e_ref.v[d]));
+          atomicAdd((unsigned long long*)&s_sqref[r], (unsigned long long)fx_of(q_ref));
+          atomicAdd(&s_hwref[r], wset_key(i));
+        }
+      };
+      if (nc <= kRowReg) {
+        // the candidates in registers: sorted, weighed and thresholded with
+        // the same operations in the same order as the general path below
+        uint32_t cs[kRowReg], ce[kRowReg];
+#pragma unroll
+        for (int x = 0; x < kRowReg; ++x) {
+          cs[x] = x < nc ? s_cslot[off + x] : 0xFFFFu;
+          ce[x] = x < nc ? s_ceidx[off + x] : 0u;
+        }
+#pragma unroll
+        for (int x = 1; x < kRowReg; ++x)
+#pragma unroll
+          for (int y = x; y > 0; --y)
+            if (cs[y - 1] > cs[y]) {   // unused entries (0xFFFF) stay last
+              const uint32_t ts = cs[y - 1], te = ce[y - 1];
+              cs[y - 1] = cs[y];
+              ce[y - 1] = ce[y];
+              cs[y] = ts;
+              ce[y] = te;
+            }
+        float lc[kRowReg];
+        float smax = md.kappa_zero ? -INFINITY : md.log_kappa;
+#pragma unroll
+        for (int x = 0; x < kRowReg; ++x) {
+          if (x >= nc) break;
+          s_cslot[off + x] = (uint16_t)cs[x];
+          s_ceidx[off + x] = ce[x];
+          lc[x] = pt.logC[ce[x]];
+          smax = fmaxf(smax, lc[x]);
+#pragma unroll
+          for (int d = 0; d < DZ; ++d) s_ce[d * Kp + off + x] = pt.e[d * capp + ce[x]];
+          s_cq[off + x] = md.score_mode == 1 ? lc[x] : pt.q[ce[x]];
+        }
+        const float w0 = md.kappa_zero ? 0.f : expf(md.log_kappa - smax);
+        float wv[kRowReg];
+        float sum = w0;
+#pragma unroll
+        for (int x = 0; x < kRowReg; ++x) {
+          if (x >= nc) break;
+          wv[x] = expf(lc[x] - smax);
+          s_cw[off + x] = wv[x];
+          sum += wv[x];
+        }
+        float cum = w0, best = w0;
+        int ref = 0;
+        bool flag = false;
+        const uint32_t thr0 = thr_of(cum / sum);
+        uint32_t lo = 0u, hi = thr0, prev = thr0;
+        unsigned long long bl = 0ull;
+        int r = 0;
+        uint32_t rce = 0u;
+        float rlc = 0.f;
+#pragma unroll
+        for (int x = 0; x < kRowReg; ++x) {
+          if (x >= nc) break;
+          const bool can_die = s_dthr[cs[x]] > 0u;
+          if (can_die) bl |= 1ull << (cs[x] & 63);
+          cum += wv[x];
+          const uint32_t th = (x == nc - 1) ? kOne24 : thr_of(cum / sum);
+          s_cthr[off + x] = th;
+          if (wv[x] > best) {
+            best = wv[x];
+            ref = x + 1;
+            lo = prev;
+            hi = th;
+            r = (int)cs[x];
+            rce = ce[x];
+            rlc = lc[x];
+          }
+          prev = th;
+          flag |= can_die;
+        }
+        // the reference pair's innovation and q, read again (L1)
+        FVec<DZ> e_ref;
+        float q_ref = 0.f;
+#pragma unroll
+        for (int d = 0; d < DZ; ++d) e_ref.v[d] = ref > 0 ? pt.e[d * capp + rce] : 0.f;
+        if (ref > 0) q_ref = md.score_mode == 1 ? rlc : pt.q[rce];
+        finish_row(ref, flag, thr0, lo, hi, bl, w0, r, e_ref, q_ref);
+        continue;
+      }
       for (int x = 1; x < nc; ++x) {   // insertion sort by slot
         const uint16_t ks = s_cslot[off + x];
         const uint32_t ke = s_ceidx[off + x];
@@ -505,15 +642,6 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         }
         s_cslot[off + y + 1] = ks;
         s_ceidx[off + y + 1] = ke;
-      }
-      if (nc == 0) {
-        s_row[i] = make_uint4(off, 0u, 0u, kOne24);
-        s_rowthr0[i] = kOne24;
-        s_rowbl[i] = 0ull;
-        s_rowrk[i] = 0u;
-        s_roww0[i] = 1.f;
-        ++my_clut;
-        continue;
       }
       float smax = md.kappa_zero ? -INFINITY : md.log_kappa;
       for (int j = 0; j < nc; ++j) {
@@ -545,28 +673,21 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         if (w > best) { best = w; ref = j + 1; }
         flag |= can_die;
       }
-      // row i: x = first candidate, y = count | may-die flag << 15 |
-      // reference option << 16, [z, w) = the uniforms that pick the reference
-      // option when every candidate is alive
       const uint32_t lo = ref == 0 ? 0u : (ref == 1 ? thr0 : s_cthr[off + ref - 2]);
       const uint32_t hi = ref == 0 ? thr0 : s_cthr[off + ref - 1];
-      s_row[i] = make_uint4(off, (uint32_t)nc | (flag ? 0x8000u : 0u) | ((uint32_t)ref << 16), lo, hi);
-      s_rowthr0[i] = thr0;
-      s_rowbl[i] = bl;
-      s_rowrk[i] = ref > 0 ? (((uint32_t)s_cslot[off + ref - 1] + 1u) << 16) | (off + ref - 1) : 0u;
-      s_roww0[i] = w0;
-      if (ref == 0) {
-        ++my_clut;
-      } else {
-        const int r = s_cslot[off + ref - 1];
-        const uint32_t pos = off + ref - 1;
-        atomicAdd(&s_mref[r], 1);
+      FVec<DZ> e_ref;
+      float q_ref = 0.f;
+      int r = 0;
 #pragma unroll
-        for (int d = 0; d < DZ; ++d)
-          atomicAdd((unsigned long long*)&s_seref[d * T + r], (unsigned long long)fx_of(s_ce[d * Kp + pos]));
-        atomicAdd((unsigned long long*)&s_sqref[r], (unsigned long long)fx_of(s_cq[pos]));
-        atomicAdd(&s_hwref[r], wset_key(i));
+      for (int d = 0; d < DZ; ++d) e_ref.v[d] = 0.f;
+      if (ref > 0) {
+        const uint32_t pos = off + ref - 1;
+        r = s_cslot[pos];
+#pragma unroll
+        for (int d = 0; d < DZ; ++d) e_ref.v[d] = s_ce[d * Kp + pos];
+        q_ref = s_cq[pos];
       }
+      finish_row(ref, flag, thr0, lo, hi, bl, w0, r, e_ref, q_ref);
     }
     if (my_clut) atomicAdd(&sc.nclut_ref, my_clut);
   }
@@ -704,7 +825,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 // pairs, so a fixed share per CTA would leave SMs idle at the end).
 // SMEM: staged in shared memory and copied to the image (16-byte words).
 template <int DZ, bool SMEM>
-__global__ void __launch_bounds__(256, 3) stage_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256, 3) stage_kernel(const __grid_constant__ ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
@@ -1364,7 +1485,7 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
 // Persistent over a list of children, one warp each: the survivors (MAT),
 // every child of every parent (a.warp_all), or the draw kernel's overflow.
 template <int DZ, bool MAT>
-__global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(512) warp_kernel(const __grid_constant__ ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
@@ -1415,7 +1536,7 @@ __global__ void __launch_bounds__(512) warp_kernel(const ExpandArgs a) {
 // The reference association's updated components of every retained parent,
 // requested once per parent (one warp per first survivor of a parent).
 template <int DZ>
-__global__ void __launch_bounds__(256) mat_prep_kernel(const ExpandArgs a) {
+__global__ void __launch_bounds__(256) mat_prep_kernel(const __grid_constant__ ExpandArgs a) {
   pdl_enter();
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int lane = threadIdx.x & 31;
@@ -1549,6 +1670,19 @@ __global__ void __launch_bounds__(128) dedup_kernel(const FrameDev* __restrict__
     part_sum[blockIdx.x] = t;
     part_cnt[blockIdx.x] = c;
   }
+}
+
+__global__ void hash_reset_kernel(unsigned long long* hkeys, const uint32_t* __restrict__ upd_slot,
+                                  const unsigned* __restrict__ n_prev, int cap_upd) {
+  pdl_enter();
+  const unsigned n = min(*n_prev, (unsigned)cap_upd);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    hkeys[upd_slot[i]] = 0ull;
+}
+
+void launch_hash_reset(unsigned long long* hkeys, const uint32_t* upd_slot, const unsigned* n_prev, int cap_upd,
+                       int grid, cudaStream_t s) {
+  launch_k(hash_reset_kernel, grid, 256, 0, s, hkeys, upd_slot, n_prev, cap_upd);
 }
 
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,

@@ -613,8 +613,11 @@ __global__ void __launch_bounds__(256, DZ == 2 ? 3 : 2) gc_remap_kernel(Model md
                                 int cap_upd, const unsigned* __restrict__ n_upd_dev,
                                 const unsigned* __restrict__ n_surv_dev, unsigned* err, uint32_t* out_comp,
                                 const unsigned* __restrict__ n_entries, long long cap_entries,
-                                const uint32_t* __restrict__ hvals, uint32_t hmask) {
+                                const uint32_t* __restrict__ hvals, uint32_t hmask, unsigned* n_upd_prev) {
   pdl_enter();
+  // the updates this frame inserted into the hash table, for the next
+  // frame's reset (whatever happens below)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_upd_prev = *n_upd_dev;
   if (*n_surv_dev == 0u || (*(volatile unsigned*)err & kErrFatal)) return;
   const int n_src = fs->T;
   const unsigned n_keep = *n_keep_dev;
@@ -664,13 +667,16 @@ void launch_gc_remap(const Model& md, const CompTable& src, const CompTable& dst
                      const uint32_t* flag, const FrameDev* fs, const unsigned* n_keep_dev, const uint32_t* upd_src,
                      const uint32_t* upd_m, const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
                      const unsigned* n_surv_dev, unsigned* err, uint32_t* out_comp, const unsigned* n_entries_dev,
-                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, int grid, cudaStream_t s) {
+                     long long cap_entries, const uint32_t* hvals, uint32_t hmask, unsigned* n_upd_prev, int grid,
+                     cudaStream_t s) {
   if (md.dz == 2) {
     launch_k(gc_remap_kernel<2>, grid, 256, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
-             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask);
+             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask,
+             n_upd_prev);
   } else {
     launch_k(gc_remap_kernel<3>, grid, 256, 0, s, md, src, dst, newpos, flag, fs, n_keep_dev, upd_src, upd_m,
-             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask);
+             upd_se, cap_upd, n_upd_dev, n_surv_dev, err, out_comp, n_entries_dev, cap_entries, hvals, hmask,
+             n_upd_prev);
   }
 }
 

@@ -194,3 +194,65 @@ def test_device_detections_must_be_device_memory(glmb):
     assert f.lib.glmb_update(f.h, C.c_void_p(dev.data_ptr()), M, 1) == 0
     assert f.lib.glmb_prune(f.h) == 0
     f.close()
+
+
+def test_update_table_overflow_fails_the_frame_and_the_next_frames_are_exact(glmb):
+    """A frame whose distinct track updates exceed the component capacity
+    fails with GLMB_E_CAPACITY and leaves the state as it was.  The update
+    hash table is cleared frame to frame only where the last frame filled
+    it; after an overflow (updates that found no room are not on that list)
+    the whole table is cleared, so the frames that follow equal those of a
+    filter that never saw the failing frame."""
+    import numpy as np
+    sc = scenes.make_scene(scenes.preset("tiny"), 1001)
+    big = sc.filter_config(max_components=20000, max_meas=1024)
+    k_spike, k_end = 12, 18
+    fr = sc.frames[k_spike]
+    rng = np.random.default_rng(3)
+    # seven more detections about every detection of the frame, ~28 m out
+    # (near the gate's edge, where a track and clutter are about equally
+    # likely), so the hypotheses take many distinct detection sets and the
+    # frame's updates spike (the FP64 oracle on this frame: 109 distinct
+    # tracks after it against at most 55 after any earlier frame)
+    extra = []
+    for _ in range(7):
+        ang = rng.uniform(0.0, 2.0 * np.pi, len(fr.Z))
+        extra.append(fr.Z + 28.0 * np.stack([np.cos(ang), np.sin(ang)], axis=1) + rng.normal(0.0, 1.0, fr.Z.shape))
+    Zs = np.concatenate([fr.Z] + extra).astype(np.float32)
+    ref = glmb.Filter(big)
+    need = 0
+    for k in range(k_spike):
+        ref.step(sc.frames[k].births, sc.frames[k].Z)
+        need = max(need, ref.info()["n_components"] + len(sc.frames[k + 1].births))
+    probe = glmb.Filter(big)
+    probe.import_state(ref.export_state())
+    probe.step(fr.births, Zs)
+    spike_updates = probe.info()["n_updates"]
+    probe.close()
+    for k in range(k_spike + 1, k_end):
+        ref.step(sc.frames[k].births, sc.frames[k].Z)
+        need = max(need, ref.info()["n_components"] + len(sc.frames[k + 1].births))
+    ref.close()
+    cap = need
+    assert spike_updates > cap, (spike_updates, cap)
+    a = glmb.Filter(sc.filter_config(max_components=cap, max_meas=1024))
+    b = glmb.Filter(big)
+    for k in range(k_spike):
+        a.step(sc.frames[k].births, sc.frames[k].Z)
+        b.step(sc.frames[k].births, sc.frames[k].Z)
+    before = a.export_state()
+    with pytest.raises(glmb.GlmbError) as ei:
+        a.step(fr.births, Zs)
+    assert ei.value.status == 3              # GLMB_E_CAPACITY
+    assert "distinct track updates exceed capacity" in str(ei.value), str(ei.value)
+    assert a.export_state() == before
+    for k in range(k_spike + 1, k_end):
+        a.step(sc.frames[k].births, sc.frames[k].Z)
+        b.step(sc.frames[k].births, sc.frames[k].Z)
+        ia, la = a.retained()
+        ib, lb = b.retained()
+        assert np.array_equal(ia, ib) and np.array_equal(la, lb), k
+        ea, eb = a.estimates(), b.estimates()
+        assert ea["n"] == eb["n"] and np.array_equal(ea["mean"], eb["mean"]), k
+    a.close()
+    b.close()
