@@ -885,7 +885,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   const int img = (int)a.img_stride;
   // stage: CTAs of p.st_thr threads, each taking the next parent from a
   // counter (persistent grid)
-  const int st_smem = (p.smem ? img : 0) + 16;   // the image, and the next-parent word
+  const int st_smem = (p.smem ? img : 0) + expand_stage_tail_bytes(p.M, p.smem);
   const int st_thr = p.st_thr;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
@@ -1025,7 +1025,8 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   // 3.51 ms in shared memory at one CTA per SM; on the 2-D mid scene, 19 KB
   // images, shared memory stayed faster)
   const int img_bytes = expand_image_bytes(dz, p.T, p.K, p.M);
-  p.smem = img_bytes + 16 <= h->smem_limit && !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
+  p.smem = img_bytes + expand_stage_tail_bytes(p.M, true) <= h->smem_limit &&
+           !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
            (8LL * img_bytes <= (long long)h->smem_per_sm || (h->launch_opts & GLMB_OPT_STAGE_SHARED));
   // staging threads: 256 in shared memory, or for few parents (each parent's
   // work spread over more threads); else 64, so that more parents are in

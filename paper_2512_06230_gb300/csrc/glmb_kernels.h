@@ -129,6 +129,10 @@ struct ExpandArgs {
 // bytes of one parent's image (the staging kernel's shared memory when it
 // stages there)
 int expand_image_bytes(int dz, int T_max, int K_max, int M);
+// shared memory the staging kernel needs beside (or, with the image in
+// global memory, instead of) the image: next-parent word, scan sums, and
+// the row offsets and fill cursors when the image is in global memory
+int expand_stage_tail_bytes(int M_plan, bool image_in_smem);
 // shared memory of a draw-kernel CTA of `threads` threads
 int expand_draw_smem(int threads);
 // shared memory of a warp-kernel CTA of `warps` warps

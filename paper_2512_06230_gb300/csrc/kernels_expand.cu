@@ -367,8 +367,12 @@ struct FVec {
   float v[N];
 };
 // Builds parent h's image at `sm` (shared memory, or the image itself).
+// `tail`: shared memory beside the image: 8 words for the row-count scan,
+// then (when the image itself is in global memory) the row offsets and
+// fill cursors, 2 (M + 1) words, so that their atomics stay on chip.
 template <int DZ>
-__device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm) {
+__device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm, uint32_t* tail,
+                             bool rows_in_tail) {
   const Model& md = a.md;
   const int M = a.fs->M;
   const int birth_base = a.fs->n_comp, nb = a.fs->nb;
@@ -383,8 +387,9 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   RowChunk* s_rch = at<RowChunk>(sm, L.rch);
   uint8_t* s_srow = at<uint8_t>(sm, L.srow);
   uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
-  uint32_t* s_rowoff = at<uint32_t>(sm, L.rowoff);
-  uint32_t* s_rowfill = at<uint32_t>(sm, L.rowfill);
+  uint32_t* s_wsum = tail;
+  uint32_t* s_rowoff = rows_in_tail ? tail + 8 : at<uint32_t>(sm, L.rowoff);
+  uint32_t* s_rowfill = rows_in_tail ? tail + 8 + (a.M_plan + 1) : at<uint32_t>(sm, L.rowfill);
   float* s_roww0 = at<float>(sm, L.roww0);
   uint32_t* s_comp = at<uint32_t>(sm, L.comp);
   uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
@@ -478,36 +483,45 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
     s_srow[t] = (pt.ptr[c + 1] > pt.ptr[c] && s_dthr[t] > 0u) ? 1 : 0;
   }
   __syncthreads();
-  // exclusive scan of the row counts (single warp, serial carry over chunks)
-  if (tid < 32) {
-    uint32_t carry = 0;
-    for (int base = 0; base < M; base += 32) {
-      const int i = base + tid;
-      const uint32_t v = i < M ? s_rowfill[i] : 0u;
-      uint32_t x = v;
+  // exclusive scan of the row counts over the block: each thread a
+  // contiguous run of rows, a scan of the runs' totals across the warps;
+  // the offsets are also the fill cursors
+  {
+    const int per = (M + nthr - 1) / nthr;
+    const int b0 = min(M, tid * per), b1 = min(M, b0 + per);
+    uint32_t run = 0;
+    for (int i = b0; i < b1; ++i) run += s_rowfill[i];
+    const int lane = tid & 31, wp = tid >> 5;
+    uint32_t x = run;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (tid >= o) x += y;
-      }
-      if (i < M) s_rowoff[i] = carry + x - v;
-      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
     }
-    if (tid == 0) {
-      s_rowoff[M] = carry;
-      sc.K = (int)carry;
-      if ((int)carry > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+    if (lane == 31) s_wsum[wp] = x;
+    __syncthreads();
+    uint32_t base = x - run;
+    for (int w = 0; w < wp; ++w) base += s_wsum[w];
+    for (int i = b0; i < b1; ++i) {
+      const uint32_t v = s_rowfill[i];
+      s_rowoff[i] = base;
+      s_rowfill[i] = base;
+      base += v;
+    }
+    if (tid == nthr - 1) {
+      // the last thread's run ends at M (or is empty, with base the total)
+      s_rowoff[M] = base;
+      sc.K = (int)base;
+      if ((int)base > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
     }
   }
   __syncthreads();
   if (sc.bad) return;
-  for (int i = tid; i < M; i += nthr) s_rowfill[i] = 0;
-  __syncthreads();
   for (int t = tid; t < T; t += nthr) {
     const uint32_t c = s_comp[t];
     for (uint32_t j = pt.ptr[c], je = pt.ptr[c + 1]; j < je; ++j) {
       const uint32_t i = pt.meas[j];
-      const uint32_t pos = s_rowoff[i] + atomicAdd(&s_rowfill[i], 1u);
+      const uint32_t pos = atomicAdd(&s_rowfill[i], 1u);
       s_cslot[pos] = (uint16_t)t;
       s_ceidx[pos] = j;
     }
@@ -829,7 +843,10 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const __grid_constant__ E
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
-  int& s_next = *reinterpret_cast<int*>(sm + (SMEM ? L.total : 0));   // after the staged image
+  // after the staged image (SMEM) or alone: the next-parent word, then the
+  // staging's shared scratch (expand_stage_tail_bytes)
+  int& s_next = *reinterpret_cast<int*>(sm + (SMEM ? L.total : 0));
+  uint32_t* tail = reinterpret_cast<uint32_t*>(sm + (SMEM ? L.total : 0) + 16);
   const int H = a.fs->H;
   // a table that failed (e.g. pairs beyond capacity, whose offsets then run
   // past the pair arrays) is not staged; the frame is abandoned.  The flags
@@ -839,7 +856,7 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const __grid_constant__ E
   if (*(volatile const unsigned*)a.err & (kErrFatal & ~(kErrSlots | kErrChkComp))) return;
   for (int h = blockIdx.x; h < H;) {
     unsigned char* img = a.img + (size_t)h * a.img_stride;
-    stage_parent<DZ>(a, h, L, SMEM ? sm : img);
+    stage_parent<DZ>(a, h, L, SMEM ? sm : img, tail, !SMEM);
     __syncthreads();
     if (SMEM) {
       // a parent whose staging failed copies only its header
@@ -1212,6 +1229,10 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
   a.child_status[j] = valid ? 1 : 0;
   a.child_alive[j] = (uint16_t)(sc.T - nd);
   return true;
+}
+
+int expand_stage_tail_bytes(int M_plan, bool image_in_smem) {
+  return 16 + 32 + (image_in_smem ? 0 : ((8 * (M_plan + 1) + 15) & ~15));
 }
 
 int expand_draw_smem(int threads) { return threads * (kDrawSlow + kDrawDead) * (int)sizeof(uint16_t); }
