@@ -885,7 +885,12 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   const int img = (int)a.img_stride;
   // stage: CTAs of p.st_thr threads, each taking the next parent from a
   // counter (persistent grid)
-  const int st_smem = (p.smem ? img : 0) + expand_stage_tail_bytes(p.M, p.smem);
+  // staged in global memory: as much of its scratch in shared memory as fits
+  a.stage_tail = 0;
+  if (!p.smem)
+    for (int m = 2; m >= 1 && !a.stage_tail; --m)
+      if (expand_stage_tail_bytes(dz, p.T, p.K, p.M, m) <= h->smem_limit) a.stage_tail = m;
+  const int st_smem = (p.smem ? img : 0) + expand_stage_tail_bytes(dz, p.T, p.K, p.M, a.stage_tail);
   const int st_thr = p.st_thr;
   const int st_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kStage, st_thr, st_smem));
   const int st_grid = p.fixed ? st_ctas * n_sm : std::max(1, std::min(h->H, st_ctas * n_sm));
@@ -1025,14 +1030,17 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   // 3.51 ms in shared memory at one CTA per SM; on the 2-D mid scene, 19 KB
   // images, shared memory stayed faster)
   const int img_bytes = expand_image_bytes(dz, p.T, p.K, p.M);
-  p.smem = img_bytes + expand_stage_tail_bytes(p.M, true) <= h->smem_limit &&
+  p.smem = img_bytes + expand_stage_tail_bytes(dz, p.T, p.K, p.M, 0) <= h->smem_limit &&
            !(h->launch_opts & GLMB_OPT_STAGE_GLOBAL) &&
            (8LL * img_bytes <= (long long)h->smem_per_sm || (h->launch_opts & GLMB_OPT_STAGE_SHARED));
   // staging threads: 256 in shared memory, or for few parents (each parent's
-  // work spread over more threads); else 64, so that more parents are in
-  // flight per SM
+  // work spread over more threads); else 128: with its scratch in shared
+  // memory (about 29 KB for the 3-D sweep's plans) six such CTAs per SM keep
+  // 24 warps in flight, where 64-thread CTAs would be limited to seven by
+  // shared memory (measured on the N = 200, H_max = 20000 cell: expansion
+  // 1.56 ms with 128, 1.87 ms with 64)
   p.st_thr = h->tune.stage_threads > 0 ? h->tune.stage_threads
-             : (p.smem || (long long)h->H < 2LL * h->n_sm) ? 256 : 64;
+             : (p.smem || (long long)h->H < 2LL * h->n_sm) ? 256 : 128;
   p.Gw = p.Gm = 0;
   for (int g = h->tune.warp_cta_warps; g >= 1 && !p.Gw; --g)
     if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;

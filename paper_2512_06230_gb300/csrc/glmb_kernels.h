@@ -94,6 +94,7 @@ struct ExpandArgs {
   uint32_t* redo_list;    // children the draw kernel could not take
   unsigned* redo_count;
   unsigned* stage_next;   // staging: next parent to take (zero at the launch)
+  int stage_tail;         // staging in global memory: what it keeps in shared memory (expand_stage_tail_bytes)
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
   unsigned long long* child_hash;   // [H * h_up] order-free key of (deaths, associations)
@@ -131,8 +132,10 @@ struct ExpandArgs {
 int expand_image_bytes(int dz, int T_max, int K_max, int M);
 // shared memory the staging kernel needs beside (or, with the image in
 // global memory, instead of) the image: next-parent word, scan sums, and
-// the row offsets and fill cursors when the image is in global memory
-int expand_stage_tail_bytes(int M_plan, bool image_in_smem);
+// the arrays it reads back many times when the image is in global memory
+// (mode: 0 the two words only, 1 with the row offsets, 2 with every listed
+// array; the image in shared memory takes mode 0)
+int expand_stage_tail_bytes(int dz, int T_plan, int K_plan, int M_plan, int mode);
 // shared memory of a draw-kernel CTA of `threads` threads
 int expand_draw_smem(int threads);
 // shared memory of a warp-kernel CTA of `warps` warps

@@ -133,6 +133,39 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   return L;
 }
 
+// The staging kernel's shared scratch beside the image: the next-parent
+// word (16 B) and the scan's warp sums (32 B); then, when the image is
+// built in global memory, the arrays the staging reads back many times:
+// mode >= 1 the row offsets and fill cursors, mode 2 also the candidates'
+// slots and pair indices and the per-slot reference counts, sums, terms
+// and infinite-term counts (copied to the image at the end of the parent).
+// Offsets from its base.
+struct StageTail {
+  int rowoff, rowfill, cslot, ceidx, mref, seref, sqref, hwref, termref, ninfref, total;
+};
+__host__ __device__ inline StageTail make_stage_tail(int dz, int T, int K, int M, int mode) {
+  StageTail S{};
+  Bump b;
+  b.take(16);   // next-parent word
+  b.take(32);   // warp sums of the row-count scan
+  if (mode >= 1) {
+    S.rowoff = b.take(4LL * (M + 1));
+    S.rowfill = b.take(4LL * (M + 1));
+  }
+  if (mode >= 2) {
+    S.cslot = b.take(2LL * K);
+    S.ceidx = b.take(4LL * K);
+    S.mref = b.take(4LL * T);
+    S.seref = b.take(8LL * dz * T);
+    S.sqref = b.take(8LL * T);
+    S.hwref = b.take(8LL * T);
+    S.termref = b.take(8LL * T);
+    S.ninfref = b.take(T);
+  }
+  S.total = b.off;
+  return S;
+}
+
 int expand_image_bytes(int dz, int T, int K, int M) {
   return (make_lay(dz, T, K, M).total + 127) & ~127;
 }
@@ -367,44 +400,47 @@ struct FVec {
   float v[N];
 };
 // Builds parent h's image at `sm` (shared memory, or the image itself).
-// `tail`: shared memory beside the image: 8 words for the row-count scan,
-// then (when the image itself is in global memory) the row offsets and
-// fill cursors, 2 (M + 1) words, so that their atomics stay on chip.
+// `tb`: the shared scratch beside the image (StageTail).  With the image in
+// global memory (in_tail) the arrays it lists live there while the parent
+// is staged, so that their atomics and read-backs stay on chip, and are
+// copied to the image at the end.
 template <int DZ>
-__device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm, uint32_t* tail,
-                             bool rows_in_tail) {
+__device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, unsigned char* sm, unsigned char* tb,
+                             int mode) {
+  const StageTail TS = make_stage_tail(DZ, a.T_max, a.K_max, a.M_plan, mode);
+  const bool in_tail = mode >= 2;
   const Model& md = a.md;
   const int M = a.fs->M;
   const int birth_base = a.fs->n_comp, nb = a.fs->nb;
   Scal& sc = *at<Scal>(sm, L.scal);
   uint4* s_row = at<uint4>(sm, L.row);
   unsigned long long* s_rowbl = at<unsigned long long>(sm, L.rowbl);
-  long long* s_seref = at<long long>(sm, L.seref);
-  long long* s_sqref = at<long long>(sm, L.sqref);
-  long long* s_termref = at<long long>(sm, L.termref);
-  unsigned long long* s_hwref = at<unsigned long long>(sm, L.hwref);
+  long long* s_seref = in_tail ? at<long long>(tb, TS.seref) : at<long long>(sm, L.seref);
+  long long* s_sqref = in_tail ? at<long long>(tb, TS.sqref) : at<long long>(sm, L.sqref);
+  long long* s_termref = in_tail ? at<long long>(tb, TS.termref) : at<long long>(sm, L.termref);
+  unsigned long long* s_hwref = in_tail ? at<unsigned long long>(tb, TS.hwref) : at<unsigned long long>(sm, L.hwref);
   uint32_t* s_rowrk = at<uint32_t>(sm, L.rowrk);
   RowChunk* s_rch = at<RowChunk>(sm, L.rch);
   uint8_t* s_srow = at<uint8_t>(sm, L.srow);
   uint32_t* s_rowthr0 = at<uint32_t>(sm, L.rowthr0);
-  uint32_t* s_wsum = tail;
-  uint32_t* s_rowoff = rows_in_tail ? tail + 8 : at<uint32_t>(sm, L.rowoff);
-  uint32_t* s_rowfill = rows_in_tail ? tail + 8 + (a.M_plan + 1) : at<uint32_t>(sm, L.rowfill);
+  uint32_t* s_wsum = at<uint32_t>(tb, 16);
+  uint32_t* s_rowoff = mode >= 1 ? at<uint32_t>(tb, TS.rowoff) : at<uint32_t>(sm, L.rowoff);
+  uint32_t* s_rowfill = mode >= 1 ? at<uint32_t>(tb, TS.rowfill) : at<uint32_t>(sm, L.rowfill);
   float* s_roww0 = at<float>(sm, L.roww0);
   uint32_t* s_comp = at<uint32_t>(sm, L.comp);
   uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
   float* s_logp = at<float>(sm, L.logp);
   float* s_log1mp = at<float>(sm, L.log1mp);
-  int* s_mref = at<int>(sm, L.mref);
+  int* s_mref = in_tail ? at<int>(tb, TS.mref) : at<int>(sm, L.mref);
   float* s_hph = at<float>(sm, L.hph);
   uint32_t* s_dpc = at<uint32_t>(sm, L.dpc);
   uint32_t* s_cthr = at<uint32_t>(sm, L.cthr);
-  uint32_t* s_ceidx = at<uint32_t>(sm, L.ceidx);
+  uint32_t* s_ceidx = in_tail ? at<uint32_t>(tb, TS.ceidx) : at<uint32_t>(sm, L.ceidx);
   float* s_cw = at<float>(sm, L.cw);
   float* s_ce = at<float>(sm, L.ce);
   float* s_cq = at<float>(sm, L.cq);
-  uint16_t* s_cslot = at<uint16_t>(sm, L.cslot);
-  uint8_t* s_ninfref = at<uint8_t>(sm, L.ninfref);
+  uint16_t* s_cslot = in_tail ? at<uint16_t>(tb, TS.cslot) : at<uint16_t>(sm, L.cslot);
+  uint8_t* s_ninfref = in_tail ? at<uint8_t>(tb, TS.ninfref) : at<uint8_t>(sm, L.ninfref);
   const int Kp = a.K_max;                   // stride of the candidate arrays
   const CompTable& ct = a.ct;
   const PairTable& pt = a.pt;
@@ -826,6 +862,32 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       s_dninf[t] = (int8_t)(ninf - (int)s_ninfref[t]);
     }
   }
+  if (in_tail) {
+    // the arrays staged on chip go to the image
+    __syncthreads();
+    const int K = sc.K;
+    uint16_t* g_cslot = at<uint16_t>(sm, L.cslot);
+    uint32_t* g_ceidx = at<uint32_t>(sm, L.ceidx);
+    for (int i = tid; i < K; i += nthr) {
+      g_cslot[i] = s_cslot[i];
+      g_ceidx[i] = s_ceidx[i];
+    }
+    int* g_mref = at<int>(sm, L.mref);
+    long long* g_seref = at<long long>(sm, L.seref);
+    long long* g_sqref = at<long long>(sm, L.sqref);
+    unsigned long long* g_hwref = at<unsigned long long>(sm, L.hwref);
+    long long* g_termref = at<long long>(sm, L.termref);
+    uint8_t* g_ninfref = at<uint8_t>(sm, L.ninfref);
+    for (int t = tid; t < T; t += nthr) {
+      g_mref[t] = s_mref[t];
+#pragma unroll
+      for (int d = 0; d < DZ; ++d) g_seref[d * T + t] = s_seref[d * T + t];
+      g_sqref[t] = s_sqref[t];
+      g_hwref[t] = s_hwref[t];
+      g_termref[t] = s_termref[t];
+      g_ninfref[t] = s_ninfref[t];
+    }
+  }
   if (tid == 0) {
     sc.ref_score += __double2ll_rn(sc.logw * 4294967296.0);
     if (md.kappa_zero) sc.ninf_ref += sc.nclut_ref;
@@ -845,8 +907,8 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const __grid_constant__ E
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   // after the staged image (SMEM) or alone: the next-parent word, then the
   // staging's shared scratch (expand_stage_tail_bytes)
-  int& s_next = *reinterpret_cast<int*>(sm + (SMEM ? L.total : 0));
-  uint32_t* tail = reinterpret_cast<uint32_t*>(sm + (SMEM ? L.total : 0) + 16);
+  unsigned char* tb = sm + (SMEM ? L.total : 0);
+  int& s_next = *reinterpret_cast<int*>(tb);
   const int H = a.fs->H;
   // a table that failed (e.g. pairs beyond capacity, whose offsets then run
   // past the pair arrays) is not staged; the frame is abandoned.  The flags
@@ -856,7 +918,7 @@ __global__ void __launch_bounds__(256, 3) stage_kernel(const __grid_constant__ E
   if (*(volatile const unsigned*)a.err & (kErrFatal & ~(kErrSlots | kErrChkComp))) return;
   for (int h = blockIdx.x; h < H;) {
     unsigned char* img = a.img + (size_t)h * a.img_stride;
-    stage_parent<DZ>(a, h, L, SMEM ? sm : img, tail, !SMEM);
+    stage_parent<DZ>(a, h, L, SMEM ? sm : img, tb, SMEM ? 0 : a.stage_tail);
     __syncthreads();
     if (SMEM) {
       // a parent whose staging failed copies only its header
@@ -1231,8 +1293,8 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
   return true;
 }
 
-int expand_stage_tail_bytes(int M_plan, bool image_in_smem) {
-  return 16 + 32 + (image_in_smem ? 0 : ((8 * (M_plan + 1) + 15) & ~15));
+int expand_stage_tail_bytes(int dz, int T_plan, int K_plan, int M_plan, int mode) {
+  return make_stage_tail(dz, T_plan, K_plan, M_plan, mode).total;
 }
 
 int expand_draw_smem(int threads) { return threads * (kDrawSlow + kDrawDead) * (int)sizeof(uint16_t); }
@@ -1733,6 +1795,7 @@ static KernelFn prep_fn(int dz) { return dz == 2 ? mat_prep_kernel<2> : mat_prep
 void expand_init(int smem_limit) {
   for (int dz = 2; dz <= 3; ++dz) {
     cudaFuncSetAttribute(stage_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    cudaFuncSetAttribute(stage_fn(dz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
     cudaFuncSetAttribute(draw_fn(dz), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
     cudaFuncSetAttribute(warp_fn(dz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
     cudaFuncSetAttribute(warp_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
