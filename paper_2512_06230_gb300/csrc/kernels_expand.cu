@@ -1166,14 +1166,8 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
     const uint8_t* srow = at<uint8_t>(img, L.srow);
     const PhiloxRun pd = philox_run((uint32_t)sc.uid, (uint32_t)(sc.uid >> 32), 2u * (uint32_t)n, key);
     const int ndpc = sc.ndpc;
-    // the next chunk's entry is loaded one iteration ahead, so its Philox
-    // call does not wait for the load
-    uint32_t ent_next = ndpc > 0 ? dpc[0] : 0u;
-    for (int x = 0; x < ndpc; ++x) {
-      const uint32_t ent = ent_next;
-      if (x + 1 < ndpc) ent_next = dpc[x + 1];
+    auto test_deaths = [&](uint32_t ent, const uint4& r) {
       const uint32_t cc = ent >> 4, mask = ent & 15u;
-      const uint4 r = philox_at(pd, cc, key);
       const uint4 th = *reinterpret_cast<const uint4*>(dthr + 4 * cc);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -1185,6 +1179,19 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
           if (srow[t]) bloom |= 1ull << (t & 63u);
         }
       }
+    };
+    // two chunks per iteration: two independent Philox chains in flight
+    int x = 0;
+    for (; x + 1 < ndpc; x += 2) {
+      const uint32_t e0 = dpc[x], e1 = dpc[x + 1];
+      const uint4 r0 = philox_at(pd, e0 >> 4, key);
+      const uint4 r1 = philox_at(pd, e1 >> 4, key);
+      test_deaths(e0, r0);
+      test_deaths(e1, r1);
+    }
+    if (x < ndpc) {
+      const uint32_t e = dpc[x];
+      test_deaths(e, philox_at(pd, e >> 4, key));
     }
   }
   // stage 2: one categorical draw per detection row with candidates; rows
