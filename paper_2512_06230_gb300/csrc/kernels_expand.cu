@@ -1141,7 +1141,7 @@ constexpr int kDrawSlow = 24;
 // kind of per-thread list, after the noted rows); a child with more
 // regenerates its death draws instead.
 constexpr int kDrawDead = 8;
-// chunks per iteration of the draw loop: two (1) or one (0)
+// chunks per iteration of the draw loop's rows: three (1) or one (0)
 constexpr int kDrawPairs = 1;
 
 // Draws child n of the parent staged at img.  The chunk loop only tests the
@@ -1225,13 +1225,15 @@ __device__ __forceinline__ bool thread_child(const ExpandArgs& a, const unsigned
     };
     int x = 0;
     if (kDrawPairs) {
-      // two chunks per iteration: two independent Philox chains in flight
-      for (; x + 1 < nrca; x += 2) {
-        const uint32_t c0 = rch[x].head.x, c1 = rch[x + 1].head.x;
+      // three chunks per iteration: three independent Philox chains in flight
+      for (; x + 2 < nrca; x += 3) {
+        const uint32_t c0 = rch[x].head.x, c1 = rch[x + 1].head.x, c2 = rch[x + 2].head.x;
         const uint4 r0 = philox_at(pr, c0, key);
         const uint4 r1 = philox_at(pr, c1, key);
+        const uint4 r2 = philox_at(pr, c2, key);
         test_chunk(x, c0, r0);
         test_chunk(x + 1, c1, r1);
+        test_chunk(x + 2, c2, r2);
       }
     }
     uint32_t cc_next = x < nrca ? rch[x].head.x : 0u;   // one iteration ahead
