@@ -45,11 +45,11 @@ namespace glmb {
 
 struct Lay {
   int scal;
-  int row, rowbl, seref, sqref, termref, hwref, gaind, lossd, deadd;
+  int row, rowbl, seref, sqref, termref, hwref, deadd;
   int rowrk, rch, rowoff, rowfill, roww0, rowthr0;
   int comp, dthr, logp, log1mp, mref, refnew, hph, dpc;
   int cthr, ceidx, cw, ce, cq, cslot;
-  int ninfref, gninf, lninf, dninf, srow;
+  int ninfref, dninf, srow;
   int total;
 };
 
@@ -97,12 +97,8 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.sqref = b.take(8LL * T);                // reference sums of e^T R^-1 e
   L.termref = b.take(8LL * T);              // reference track terms
   L.hwref = b.take(8LL * T);                // reference detection-set keys
-  // exact score change of one deviation from the reference: a row's
-  // detection joining candidate pair p's slot (gaind[p]), leaving its
-  // reference slot (lossd[i]), a slot dying (deadd[t]); with the changes of
-  // the infinite-term counts (gninf, lninf, dninf)
-  L.gaind = b.take(8LL * K);
-  L.lossd = b.take(8LL * M);
+  // exact score change of a slot dying (deadd[t]) and of its infinite-term
+  // count (dninf); a row's deviations are scored by the child that makes them
   L.deadd = b.take(8LL * T);
   L.rowrk = b.take(4LL * M);                // reference option's slot and pair
   L.rch = b.take(48LL * ((M + 3) / 4 + 1)); // chunks of 4 rows with candidates (RowChunk)
@@ -125,8 +121,6 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
   L.cq = b.take(4LL * K);                   // e^T R^-1 e of each candidate pair
   L.cslot = b.take(2LL * K);
   L.ninfref = b.take(T);
-  L.gninf = b.take(K);
-  L.lninf = b.take(M);
   L.dninf = b.take(T);
   L.srow = b.take(T);                       // slot can die and is a candidate of some row
   L.total = b.off;
@@ -274,7 +268,7 @@ struct View {
   const Scal* sc;
   const uint4* row;
   const unsigned long long* rowbl;
-  const long long *seref, *sqref, *termref, *gaind, *lossd, *deadd;
+  const long long *seref, *sqref, *termref, *deadd;
   const unsigned long long* hwref;
   const RowChunk* rch;
   const uint32_t *rowrk, *rowthr0, *comp, *dthr, *refnew, *dpc, *cthr;
@@ -285,7 +279,7 @@ struct View {
   const int* mref;
   const uint16_t* cslot;
   const uint8_t* ninfref;
-  const int8_t *gninf, *lninf, *dninf;
+  const int8_t* dninf;
   const uint8_t* srow;
 };
 
@@ -297,11 +291,7 @@ __device__ __forceinline__ View make_view(const unsigned char* b, const Lay& L, 
   v.seref = at<long long>(b, L.seref);
   v.sqref = at<long long>(b, L.sqref);
   v.termref = at<long long>(b, L.termref);
-  v.gaind = at<long long>(b, L.gaind);
-  v.lossd = at<long long>(b, L.lossd);
   v.deadd = at<long long>(b, L.deadd);
-  v.gninf = at<int8_t>(b, L.gninf);
-  v.lninf = at<int8_t>(b, L.lninf);
   v.dninf = at<int8_t>(b, L.dninf);
   v.hwref = at<unsigned long long>(b, L.hwref);
   v.rowrk = at<uint32_t>(b, L.rowrk);
@@ -816,45 +806,11 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   }
   __syncthreads();
 
-  // ---- single-deviation deltas (same functions and inputs as a child's
-  // rescoring of a slot touched once, so the sums are bit-identical) ----
+  // ---- death deltas: a slot dying changes its term to the dead term (the
+  // rows' single deviations are scored by the children that make them) ----
   {
-    const View v = make_view(sm, L, a.pt);
-    long long* s_gaind = at<long long>(sm, L.gaind);
-    long long* s_lossd = at<long long>(sm, L.lossd);
     long long* s_deadd = at<long long>(sm, L.deadd);
-    int8_t* s_gninf = at<int8_t>(sm, L.gninf);
-    int8_t* s_lninf = at<int8_t>(sm, L.lninf);
     int8_t* s_dninf = at<int8_t>(sm, L.dninf);
-    const int K = sc.K;
-    for (int pos = tid; pos < K; pos += nthr) {
-      const int t = s_cslot[pos];
-      long long se[DZ];
-#pragma unroll
-      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] + fx_of(s_ce[d * Kp + pos]);
-      int ninf;
-      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] + 1, se, s_sqref[t] + fx_of(s_cq[pos]), ninf);
-      s_gaind[pos] = term - s_termref[t];
-      s_gninf[pos] = (int8_t)(ninf - (int)s_ninfref[t]);
-    }
-    for (int i = tid; i < M; i += nthr) {
-      const uint4 R = s_row[i];
-      const int ref = (int)(R.y >> 16);
-      if (ref == 0) {
-        s_lossd[i] = 0;
-        s_lninf[i] = 0;
-        continue;
-      }
-      const uint32_t pos = R.x + (uint32_t)ref - 1u;
-      const int t = s_cslot[pos];
-      long long se[DZ];
-#pragma unroll
-      for (int d = 0; d < DZ; ++d) se[d] = s_seref[d * T + t] - fx_of(s_ce[d * Kp + pos]);
-      int ninf;
-      const long long term = slot_term<DZ>(md, v, T, t, s_mref[t] - 1, se, s_sqref[t] - fx_of(s_cq[pos]), ninf);
-      s_lossd[i] = term - s_termref[t];
-      s_lninf[i] = (int8_t)(ninf - (int)s_ninfref[t]);
-    }
     for (int t = tid; t < T; t += nthr) {
       int ninf;
       const long long term = dead_term(s_log1mp[t], ninf);
@@ -977,6 +933,26 @@ struct SlowSum {
   int ninf, clut, bad;
 };
 
+// The score change of one deviation, alone: candidate pair `pos` joining
+// (sg = 1) or leaving (sg = -1) slot t, from the slot's reference sums (the
+// same function and inputs as an exact rescoring of the slot, so the sums
+// are bit-identical); term = the change, ninf = the infinite-term count's.
+template <int DZ>
+__device__ __noinline__ TermOut single_deviation(const Model* md, const View* vp, int T, int Kp, int t, uint32_t pos,
+                                                 int sg) {
+  const View& v = *vp;
+  long long se[DZ];
+#pragma unroll
+  for (int d = 0; d < DZ; ++d) se[d] = v.seref[d * T + t] + (long long)sg * fx_of(v.ce[d * Kp + pos]);
+  int ninf;
+  const long long term =
+      slot_term<DZ>(*md, v, T, t, v.mref[t] + sg, se, v.sqref[t] + (long long)sg * fx_of(v.cq[pos]), ninf);
+  TermOut o;
+  o.term = term - v.termref[t];
+  o.ninf = ninf - (int)v.ninfref[t];
+  return o;
+}
+
 template <int DZ>
 __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, const unsigned char* img,
                                           const int Tp, const int Kp, const int Mp, const uint16_t* s_slow,
@@ -991,10 +967,16 @@ __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, 
   const PhiloxRun pd = philox_run(uid_lo, uid_hi, 2u * n, key);
   const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * n + 1u, key);
   SlowSum o{0, 0ull, 0, 0, 0};
-  uint16_t ep_slot[kE], ep_row[kE];
+  uint16_t ep_slot[kE];
   uint32_t ep_pos[kE];
-  int8_t ep_sg[kE];
+  int8_t ep_sg[kE], ep_dn[kE];
+  long long ep_d[kE];
   int ne = 0;
+  auto single_dev = [&](int t, uint32_t pos, int sg, long long& d, int& dn) {
+    const TermOut r = single_deviation<DZ>(md, &v, T, Kp, t, pos, sg);
+    d = r.term;
+    dn = r.ninf;
+  };
   unsigned long long metm = 0ull;
   bool twice = false;
   for (int q = 0; q < nslow; ++q) {
@@ -1062,26 +1044,34 @@ __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, 
     if (rs1 && ((bloom >> ((rs1 - 1u) & 63u)) & 1ull) && slot_died(v.dthr, pd, key, rs1 - 1u)) rs1 = 0u;
     unsigned long long m1 = 0ull, m2 = 0ull;
     if (rs1) {
-      o.d += v.lossd[i];
-      o.ninf += v.lninf[i];
+      long long d;
+      int dn;
+      single_dev((int)rs1 - 1, off + (uint32_t)ref - 1u, -1, d, dn);
+      o.d += d;
+      o.ninf += dn;
       m1 = 1ull << ((rs1 - 1u) & 63u);
       if (ne < kE) {
         ep_slot[ne] = (uint16_t)rs1;
         ep_sg[ne] = -1;
         ep_pos[ne] = off + (uint32_t)ref - 1u;
-        ep_row[ne] = (uint16_t)i;
+        ep_d[ne] = d;
+        ep_dn[ne] = (int8_t)dn;
         ++ne;
       }
     }
     if (ns1) {
-      o.d += v.gaind[off + opt - 1];
-      o.ninf += v.gninf[off + opt - 1];
+      long long d;
+      int dn;
+      single_dev((int)ns1 - 1, off + (uint32_t)opt - 1u, 1, d, dn);
+      o.d += d;
+      o.ninf += dn;
       m2 = 1ull << ((ns1 - 1u) & 63u);
       if (ne < kE) {
         ep_slot[ne] = (uint16_t)ns1;
         ep_sg[ne] = 1;
         ep_pos[ne] = off + (uint32_t)opt - 1u;
-        ep_row[ne] = (uint16_t)i;
+        ep_d[ne] = d;
+        ep_dn[ne] = (int8_t)dn;
         ++ne;
       }
     }
@@ -1109,13 +1099,8 @@ __device__ __noinline__ SlowSum slow_rows(const Model* md, const PairTable* pt, 
       if (ep_slot[w2] != sp) continue;
       const uint32_t pos = ep_pos[w2];
       const int sg = ep_sg[w2];
-      if (sg > 0) {
-        single += v.gaind[pos];
-        sninf += v.gninf[pos];
-      } else {
-        single += v.lossd[ep_row[w2]];
-        sninf += v.lninf[ep_row[w2]];
-      }
+      single += ep_d[w2];
+      sninf += ep_dn[w2];
       dcnt += sg;
 #pragma unroll
       for (int d = 0; d < DZ; ++d) dse[d] += sg * fx_of(v.ce[d * Kp + pos]);
