@@ -874,7 +874,9 @@ glmb_status ensure_slm(glmb_handle* h, long long need) {
   return GLMB_OK;
 }
 
-glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
+// scal_zeroed: the frame's table stage has just zeroed the scalar block
+// (the redo counter and the staging counter with it)
+glmb_status enqueue_expand(glmb_handle* h, const Plan& p, bool scal_zeroed = false) {
   cudaStream_t s = h->stream;
   const int n_sm = h->n_sm, h_up = h->cfg.h_up, dz = h->md.dz;
   ExpandArgs a = expand_args(h, p, false);
@@ -924,7 +926,7 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p) {
   h->exp_plan[2] = p.M;
   h->exp_plan[3] = p.thread ? d_thr : w_thr;
   prof_begin(h, kStageExpand);
-  CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, 2 * sizeof(unsigned), s));   // S_REDO, S_STAGE
+  if (!scal_zeroed) CU(cudaMemsetAsync(h->d_scal + S_REDO, 0, 2 * sizeof(unsigned), s));   // S_REDO, S_STAGE
   launch_expand_kernel(a, ExpandKernel::kStage, st_grid, st_thr, st_smem, s);
   if (p.thread) launch_expand_kernel(a, ExpandKernel::kDraw, d_grid, d_thr, d_smem, s);
   launch_expand_kernel(a, ExpandKernel::kWarp, w_grid, w_thr, w_smem, s);
@@ -947,11 +949,12 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   HypTable& O = h->hyps[1 - h->hcur];
   const CompTable& B = h->comps[1 - h->cur];
   CompTable& A = h->comps[h->cur];
-  CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
   prof_begin(h, kStageSelect);
+  // (the cluster kernel zeroes the prune counters itself)
   if (!launch_select_cluster(h->child_key, h->d_fs, h_up, h->pw, h->lse_parts, log_tau, h->cap_h, nbits,
                              h->child_alive, P, O,
                              h->d_scal + S_ERR, h->cap_entries, s)) {
+    CU(cudaMemsetAsync(h->pw.counts, 0, 8 * sizeof(unsigned), s));
     launch_lse(h->child_key, h->d_fs, h_up, h->pw, log_tau, h->cap_h, nblk, s);
     launch_select(h->child_key, h->d_fs, h_up, nbits, h->pw, nblk, s);
     launch_compact(h->child_key, h->d_fs, h_up, n, h->pw, h->cap_h, nblk, s);
@@ -961,10 +964,8 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   prof_end(h, kStageSelect);
   // the update hash table: only the slots the last materialisation filled
   // are cleared (the whole table is cleared after a frame that failed)
-  launch_hash_reset(h->hkeys, h->upd_slot, h->d_hprev, (int)h->cap_upd, 2 * h->n_sm, s);
-  CU(cudaMemsetAsync(h->d_scal + S_NUPD, 0, sizeof(unsigned), s));
+  launch_hash_reset(h->hkeys, h->upd_slot, h->d_hprev, (int)h->cap_upd, h->d_scal + S_NUPD, 2 * h->n_sm, s);
   const long long capT = p.fixed ? h->cap_comp : std::max(h->T_work, 1);
-  CU(cudaMemsetAsync(h->gc_flag, 0, (size_t)capT * sizeof(uint32_t), s));   // set by the materialisation
   ExpandArgs a = expand_args(h, p, true);
   a.surv_idx = h->pw.surv_idx;
   a.n_surv = h->pw.counts;
@@ -1227,7 +1228,7 @@ glmb_status glmb_update(glmb_handle* h, const float* Z, int M, int z_is_device) 
     enqueue_table(h, p);
   }
   h->plan = p;
-  enqueue_expand(h, p);
+  enqueue_expand(h, p, true);
   CU(cudaGetLastError());
   // a parent with more gated pairs than the plan's estimate: redo the
   // expansion now with the frame's exact maxima, so that the children are
@@ -1341,7 +1342,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
                       cudaMemcpyHostToDevice, h->stream);
       enqueue_predict(h, q);
       enqueue_table(h, q);
-      enqueue_expand(h, q);
+      enqueue_expand(h, q, true);
       enqueue_prune(h, q);
       if (h->step_estimates)
         enqueue_estimates(h, h->hyps[1 - h->hcur], h->comps[h->cur], h->pw.counts, 0);
@@ -1414,7 +1415,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
   } else {
     enqueue_predict(h, p);
     enqueue_table(h, p);
-    enqueue_expand(h, p);
+    enqueue_expand(h, p, true);
     enqueue_prune(h, p);
     if (h->step_estimates)
       enqueue_estimates(h, h->hyps[1 - h->hcur], h->comps[h->cur], h->pw.counts, 0);

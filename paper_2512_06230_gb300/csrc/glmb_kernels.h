@@ -157,9 +157,10 @@ int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem
 // ExpandArgs (the draw and warp kernels)
 bool expand_kernel_takes_key(const void* fn);
 // clears the hash slots of the n_prev updates recorded in upd_slot (the
-// previous materialisation's), instead of clearing the whole table
+// previous materialisation's), instead of clearing the whole table, and
+// zeroes the insert counter n_cur
 void launch_hash_reset(unsigned long long* hkeys, const uint32_t* upd_slot, const unsigned* n_prev, int cap_upd,
-                       int grid, cudaStream_t s);
+                       unsigned* n_cur, int grid, cudaStream_t s);
 struct PruneWork;
 // marks duplicate children (status 2, key dropped), one block per parent
 // and writes the log-sum-exp partial of its unique children per block

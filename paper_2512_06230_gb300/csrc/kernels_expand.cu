@@ -135,7 +135,7 @@ __host__ __device__ inline Lay make_lay(int dz, int T, int K, int M) {
 // and infinite-term counts (copied to the image at the end of the parent).
 // Offsets from its base.
 struct StageTail {
-  int rowoff, rowfill, cslot, ceidx, mref, seref, sqref, hwref, termref, ninfref, total;
+  int rowoff, rowfill, cslot, ceidx, mref, seref, sqref, hwref, termref, ninfref, dthr, total;
 };
 __host__ __device__ inline StageTail make_stage_tail(int dz, int T, int K, int M, int mode) {
   StageTail S{};
@@ -155,6 +155,7 @@ __host__ __device__ inline StageTail make_stage_tail(int dz, int T, int K, int M
     S.hwref = b.take(8LL * T);
     S.termref = b.take(8LL * T);
     S.ninfref = b.take(T);
+    S.dthr = b.take(4LL * T);
   }
   S.total = b.off;
   return S;
@@ -418,7 +419,9 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   uint32_t* s_rowfill = mode >= 1 ? at<uint32_t>(tb, TS.rowfill) : at<uint32_t>(sm, L.rowfill);
   float* s_roww0 = at<float>(sm, L.roww0);
   uint32_t* s_comp = at<uint32_t>(sm, L.comp);
-  uint32_t* s_dthr = at<uint32_t>(sm, L.dthr);
+  // death thresholds: written to the image, read back on chip
+  uint32_t* g_dthr = at<uint32_t>(sm, L.dthr);
+  uint32_t* s_dthr = in_tail ? at<uint32_t>(tb, TS.dthr) : g_dthr;
   float* s_logp = at<float>(sm, L.logp);
   float* s_log1mp = at<float>(sm, L.log1mp);
   int* s_mref = in_tail ? at<int>(tb, TS.mref) : at<int>(sm, L.mref);
@@ -451,9 +454,15 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
     sc.K = 0;
     sc.uid = a.parents.uid[h];
     sc.logw = a.parents.logw[h];
+    // the block reads its sizes and counts on chip (the scan's words are
+    // free until the scan)
+    s_wsum[2] = (uint32_t)sc.T;
+    s_wsum[3] = (uint32_t)sc.Town;
+    s_wsum[4] = 0u;   // gated pairs
+    s_wsum[5] = 0u;   // bad
   }
   __syncthreads();
-  const int T = sc.T, Town = sc.Town;
+  const int T = (int)s_wsum[2], Town = (int)s_wsum[3];
   const uint32_t plo = a.parents.ptr[h];
   // the parent's gated pairs, counted for every parent (also one beyond the
   // plan): the frame's maxima plan the next frame, or this frame's redo
@@ -469,17 +478,24 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xFFFFFFFFu, kp, o);
-    if ((tid & 31) == 0 && kp) atomicAdd(&sc.K, (int)kp);
+    if ((tid & 31) == 0 && kp) atomicAdd(&s_wsum[4], kp);
   }
   __syncthreads();
-  if (tid == 0 && (*(volatile const unsigned*)a.err & kErrChkComp)) sc.bad = 1;
   if (tid == 0) {
+    const int K = (int)s_wsum[4];
+    sc.K = K;
+    int bad = (*(volatile const unsigned*)a.err & kErrChkComp) ? 1 : 0;
     if (a.max_T) atomicMax(a.max_T, (unsigned)T);
-    if (a.max_K) atomicMax(a.max_K, (unsigned)sc.K);
-    if (T > a.T_max || M > a.M_plan || sc.K > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+    if (a.max_K) atomicMax(a.max_K, (unsigned)K);
+    if (T > a.T_max || M > a.M_plan || K > a.K_max) {
+      bad = 1;
+      atomicOr(a.err, kErrSlots);
+    }
+    sc.bad = bad;
+    s_wsum[5] = (uint32_t)bad;
   }
   __syncthreads();
-  if (sc.bad) return;
+  if (s_wsum[5]) return;
 
   // ---- slots ----
   for (int t = tid; t < T; t += nthr) {
@@ -492,7 +508,11 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
 #pragma unroll
         for (int y = x; y < DZ; ++y, ++k) s_hph[k * T + t] = ct.cov[(size_t)pidx(md.dx, x, y) * ct.cap + c];
     }
-    s_dthr[t] = pt.dthr[c];
+    {
+      const uint32_t dt = pt.dthr[c];
+      s_dthr[t] = dt;
+      if (in_tail) g_dthr[t] = dt;
+    }
     s_logp[t] = ct.logp[c];
     s_log1mp[t] = ct.log1mp[c];
     s_mref[t] = 0;
@@ -538,11 +558,16 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       // the last thread's run ends at M (or is empty, with base the total)
       s_rowoff[M] = base;
       sc.K = (int)base;
-      if ((int)base > a.K_max) { sc.bad = 1; atomicOr(a.err, kErrSlots); }
+      const bool over = (int)base > a.K_max;
+      if (over) {
+        sc.bad = 1;
+        atomicOr(a.err, kErrSlots);
+      }
+      s_wsum[7] = over ? 1u : 0u;   // no warp's scan reads the last word
     }
   }
   __syncthreads();
-  if (sc.bad) return;
+  if (s_wsum[7]) return;
   for (int t = tid; t < T; t += nthr) {
     const uint32_t c = s_comp[t];
     for (uint32_t j = pt.ptr[c], je = pt.ptr[c + 1]; j < je; ++j) {
@@ -555,6 +580,11 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   __syncthreads();
 
   // ---- rows: order, weights, thresholds, reference option ----
+  // (the scan's sums are read; their words count the chunk lists next)
+  if (tid == 0) {
+    s_wsum[0] = 0u;
+    s_wsum[1] = 0u;
+  }
   {
     int my_clut = 0;
     for (int i = tid; i < M; i += nthr) {
@@ -743,7 +773,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         const int t = 4 * cc + b;
         if (t < T && s_dthr[t] > 0u) mask |= 1u << b;
       }
-      if (mask) s_dpc[atomicAdd(&sc.ndpc, 1)] = ((uint32_t)cc << 4) | mask;
+      if (mask) s_dpc[atomicAdd(&s_wsum[0], 1u)] = ((uint32_t)cc << 4) | mask;
     }
     for (int cc = tid; cc < ((M + 3) >> 2); cc += nthr) {
       uint32_t mask = 0, dmask = 0;
@@ -771,11 +801,16 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         rc.base = make_uint4(lo[0] << 8, lo[1] << 8, lo[2] << 8, lo[3] << 8);
         rc.span = make_uint4(((hi[0] - lo[0]) << 8) - 1u, ((hi[1] - lo[1]) << 8) - 1u, ((hi[2] - lo[2]) << 8) - 1u,
                              ((hi[3] - lo[3]) << 8) - 1u);
-        s_rch[atomicAdd(&sc.nrca, 1)] = rc;
+        s_rch[atomicAdd(&s_wsum[1], 1u)] = rc;
       }
     }
   }
   __syncthreads();
+
+  if (tid == 0) {
+    sc.ndpc = (int)s_wsum[0];
+    sc.nrca = (int)s_wsum[1];
+  }
 
   // ---- reference terms ----
   {
@@ -1618,6 +1653,9 @@ __global__ void __launch_bounds__(256) mat_prep_kernel(const __grid_constant__ E
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
   const int lane = threadIdx.x & 31;
   const int HU = a.md.h_up;
+  // the kept-component flags the materialisation sets: cleared here over
+  // the working table only (the next kernel waits for this one)
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.fs->T; c += gridDim.x * blockDim.x) a.gc_flag[c] = 0u;
   if (*(volatile unsigned*)a.err & (kErrEntries | kErrSlots | kErrPairs)) return;
   const long long count = (long long)*a.n_surv;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -1750,16 +1788,17 @@ __global__ void __launch_bounds__(128) dedup_kernel(const FrameDev* __restrict__
 }
 
 __global__ void hash_reset_kernel(unsigned long long* hkeys, const uint32_t* __restrict__ upd_slot,
-                                  const unsigned* __restrict__ n_prev, int cap_upd) {
+                                  const unsigned* __restrict__ n_prev, int cap_upd, unsigned* n_cur) {
   pdl_enter();
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_cur = 0u;   // this frame's insert counter
   const unsigned n = min(*n_prev, (unsigned)cap_upd);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     hkeys[upd_slot[i]] = 0ull;
 }
 
 void launch_hash_reset(unsigned long long* hkeys, const uint32_t* upd_slot, const unsigned* n_prev, int cap_upd,
-                       int grid, cudaStream_t s) {
-  launch_k(hash_reset_kernel, grid, 256, 0, s, hkeys, upd_slot, n_prev, cap_upd);
+                       unsigned* n_cur, int grid, cudaStream_t s) {
+  launch_k(hash_reset_kernel, grid, 256, 0, s, hkeys, upd_slot, n_prev, cap_upd, n_cur);
 }
 
 void launch_dedup(const FrameDev* fs, int HU, long long* child_key, const unsigned long long* child_hash,

@@ -79,15 +79,19 @@ select_cluster_kernel(const long long* __restrict__ keys, const FrameDev* __rest
                       int n_part, double log_tau, int h_max, int nbits, const uint16_t* __restrict__ child_alive,
                       HypTable parents, HypTable out, unsigned* err, long long cap_entries) {
   pdl_enter();
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5, nw = nthr >> 5;
+  // the prune counters start at zero (this thread writes the first of them
+  // below; the others are written after cluster barriers)
+  if (rank == 0 && tid == 0)
+    for (int i = 0; i < 8; ++i) w.counts[i] = 0u;
   // a frame whose expansion was skipped (the staging flagged it, or the
   // table failed) holds stale children: nothing to select; every CTA of the
   // cluster reads the same flag and returns before any cluster barrier
   if (*(volatile const unsigned*)err & kErrFatal) return;
   extern __shared__ __align__(16) unsigned char sel_sm[];
   SelShared& S = *reinterpret_cast<SelShared*>(sel_sm);
-  cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wp = tid >> 5, nw = nthr >> 5;
   const long long n = (long long)fs->H * h_up;
   const long long per = (n + C - 1) / C;
   const long long lo = min(n, (long long)rank * per), hi = min(n, lo + per);
