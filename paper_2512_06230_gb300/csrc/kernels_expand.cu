@@ -587,7 +587,16 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
   }
   {
     int my_clut = 0;
-    for (int i = tid; i < M; i += nthr) {
+    // every thread runs the same rounds, so that the four rows of a chunk
+    // (four neighbouring lanes: nthr is a multiple of 32) can pass their
+    // parts of the chunk's record to its first lane
+    for (int rb = 0; rb < M; rb += nthr) {
+    const int i = rb + tid;
+    bool r_has = false, r_flag = false;
+    uint32_t r_lo = 0u, r_hi = kOne24;
+    unsigned long long r_bl = 0ull;
+    auto row_body = [&]() {
+      if (i >= M) return;
       const uint32_t off = s_rowoff[i];
       const int nc = (int)(s_rowoff[i + 1] - off);
       if (nc == 0) {
@@ -597,7 +606,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         s_rowrk[i] = 0u;
         s_roww0[i] = 1.f;
         ++my_clut;
-        continue;
+        return;
       }
       // row i: x = first candidate, y = count | may-die flag << 15 |
       // reference option << 16, [z, w) = the uniforms that pick the reference
@@ -609,6 +618,11 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         s_rowbl[i] = bl;
         s_rowrk[i] = ref > 0 ? (((uint32_t)r + 1u) << 16) | (off + ref - 1) : 0u;
         s_roww0[i] = w0;
+        r_has = true;
+        r_flag = flag;
+        r_lo = lo;
+        r_hi = hi;
+        r_bl = bl;
         if (ref == 0) {
           ++my_clut;
         } else {
@@ -699,7 +713,7 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         for (int d = 0; d < DZ; ++d) e_ref.v[d] = ref > 0 ? pt.e[d * capp + rce] : 0.f;
         if (ref > 0) q_ref = md.score_mode == 1 ? rlc : pt.q[rce];
         finish_row(ref, flag, thr0, lo, hi, bl, w0, r, e_ref, q_ref);
-        continue;
+        return;
       }
       for (int x = 1; x < nc; ++x) {   // insertion sort by slot
         const uint16_t ks = s_cslot[off + x];
@@ -758,6 +772,36 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
         q_ref = s_cq[pos];
       }
       finish_row(ref, flag, thr0, lo, hi, bl, w0, r, e_ref, q_ref);
+    };
+    row_body();
+    // the chunk's record, at its first lane
+    {
+      const int lane = tid & 31, lead = lane & ~3;
+      uint32_t cmask = 0u, cdmask = 0u, blo = 0u, bhi = 0u, lo4[4], hi4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t has = __shfl_sync(0xFFFFFFFFu, r_has ? 1u : 0u, lead + q);
+        const uint32_t fl = __shfl_sync(0xFFFFFFFFu, r_flag ? 1u : 0u, lead + q);
+        const uint32_t bl0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r_bl, lead + q);
+        const uint32_t bl1 = __shfl_sync(0xFFFFFFFFu, (uint32_t)(r_bl >> 32), lead + q);
+        lo4[q] = __shfl_sync(0xFFFFFFFFu, r_lo, lead + q);
+        hi4[q] = __shfl_sync(0xFFFFFFFFu, r_hi, lead + q);
+        cmask |= has << q;
+        if (fl) {
+          cdmask |= 1u << q;
+          blo |= bl0;
+          bhi |= bl1;
+        }
+      }
+      if (lane == lead && cmask) {
+        RowChunk rc;
+        rc.head = make_uint4((uint32_t)(i >> 2), cdmask, blo, bhi);
+        rc.base = make_uint4(lo4[0] << 8, lo4[1] << 8, lo4[2] << 8, lo4[3] << 8);
+        rc.span = make_uint4(((hi4[0] - lo4[0]) << 8) - 1u, ((hi4[1] - lo4[1]) << 8) - 1u,
+                             ((hi4[2] - lo4[2]) << 8) - 1u, ((hi4[3] - lo4[3]) << 8) - 1u);
+        s_rch[atomicAdd(&s_wsum[1], 1u)] = rc;
+      }
+    }
     }
     if (my_clut) atomicAdd(&sc.nclut_ref, my_clut);
   }
@@ -775,38 +819,8 @@ __device__ void stage_parent(const ExpandArgs& a, const int h, const Lay& L, uns
       }
       if (mask) s_dpc[atomicAdd(&s_wsum[0], 1u)] = ((uint32_t)cc << 4) | mask;
     }
-    for (int cc = tid; cc < ((M + 3) >> 2); cc += nthr) {
-      uint32_t mask = 0, dmask = 0;
-      unsigned long long bl = 0ull;
-      uint32_t lo[4], hi[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = 4 * cc + b;
-        lo[b] = 0u;
-        hi[b] = kOne24;
-        if (i < M && s_rowoff[i + 1] > s_rowoff[i]) {
-          const uint4 R = s_row[i];
-          mask |= 1u << b;
-          lo[b] = R.z;
-          hi[b] = R.w;
-          if (R.y & 0x8000u) {
-            dmask |= 1u << b;
-            bl |= s_rowbl[i];
-          }
-        }
-      }
-      if (mask) {
-        RowChunk rc;
-        rc.head = make_uint4((uint32_t)cc, dmask, (uint32_t)bl, (uint32_t)(bl >> 32));
-        rc.base = make_uint4(lo[0] << 8, lo[1] << 8, lo[2] << 8, lo[3] << 8);
-        rc.span = make_uint4(((hi[0] - lo[0]) << 8) - 1u, ((hi[1] - lo[1]) << 8) - 1u, ((hi[2] - lo[2]) << 8) - 1u,
-                             ((hi[3] - lo[3]) << 8) - 1u);
-        s_rch[atomicAdd(&s_wsum[1], 1u)] = rc;
-      }
-    }
   }
   __syncthreads();
-
   if (tid == 0) {
     sc.ndpc = (int)s_wsum[0];
     sc.nrca = (int)s_wsum[1];
