@@ -1431,9 +1431,18 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
     }
     __syncwarp();
   }
-  // phase 2: one categorical draw per detection row
+  // phase 2: one categorical draw per detection row.  The dead slots'
+  // bloom (slot mod 64) screens a row's candidates before the exact check;
+  // a row none of whose candidates died whose uniform is in its reference
+  // interval keeps its reference option without its thresholds
   int my_dclut = 0;
   bool bad_row = false;
+  unsigned long long dbl = 0ull;
+  for (int w = lane; w < W; w += 32)
+    for (uint32_t m = dmask[w]; m; m &= m - 1u) dbl |= 1ull << ((32 * w + __ffs(m) - 1) & 63);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dbl |= __shfl_xor_sync(0xFFFFFFFFu, dbl, o);
+  const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, key);
   for (int cc = lane; cc < nrc; cc += 32) {
     const int i0 = 4 * cc;
     const int i1 = min(i0 + 4, M);
@@ -1444,12 +1453,13 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
         for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
       continue;
     }
-    const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, (uint32_t)cc), key);
+    const uint4 r = philox_at(pr, (uint32_t)cc, key);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int i = i0 + b;
       if (i >= i1) break;
       const uint4 R = v.row[i];
+      const unsigned long long rbl = v.rowbl[i];
       const uint32_t off = R.x;
       const int nc = (int)(R.y & 0x7FFFu);
       if (nc == 0) {
@@ -1458,11 +1468,13 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       }
       const uint32_t k = word_of(r, b) >> 8;
       bool fast = true;
-      if (R.y & 0x8000u)
+      if ((R.y & 0x8000u) && (rbl & dbl))
         for (int j = 0; j < nc; ++j)
           if (bit_of(dmask, v.cslot[off + j])) { fast = false; break; }
       int opt;
-      if (fast) {
+      if (fast && k - R.z < R.w - R.z) {
+        opt = (int)(R.y >> 16);   // the reference option
+      } else if (fast) {
         if (k < v.rowthr0[i]) {
           opt = 0;
         } else {
