@@ -1446,13 +1446,6 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
   for (int cc = lane; cc < nrc; cc += 32) {
     const int i0 = 4 * cc;
     const int i1 = min(i0 + 4, M);
-    bool any = false;
-    for (int i = i0; i < i1; ++i) any |= (v.row[i].y & 0x7FFFu) != 0u;
-    if (!any) {
-      if (MAT)
-        for (int i = i0; i < i1; ++i) a.out_theta[(size_t)s_out * M + i] = 0;
-      continue;
-    }
     const uint4 r = philox_at(pr, (uint32_t)cc, key);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
