@@ -349,13 +349,21 @@ glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
  *   GLMB_OPT_STAGE_SHARED  build them in shared memory whenever a parent's
  *                          tables fit (GLMB_OPT_STAGE_GLOBAL wins if both
  *                          are set).
+ *   GLMB_OPT_STAGE_SCRATCH_ROWS  when the tables are built in global memory,
+ *                          keep only the row offsets in shared memory
+ *                          while a parent is staged;
+ *   GLMB_OPT_STAGE_SCRATCH_NONE  keep none of its scratch there (wins over
+ *                          GLMB_OPT_STAGE_SCRATCH_ROWS).
  * Default 0: shared-memory staging when eight staging CTAs fit on an SM
- * (else in global memory), one thread per child once the children give
- * every SM four warps. */
+ * (else in global memory, with as much of the staging's scratch in shared
+ * memory as fits), one thread per child once the children give every SM
+ * four warps. */
 #define GLMB_OPT_STAGE_GLOBAL 1u
 #define GLMB_OPT_DRAW_WARP 2u
 #define GLMB_OPT_DRAW_THREAD 4u
 #define GLMB_OPT_STAGE_SHARED 8u
+#define GLMB_OPT_STAGE_SCRATCH_ROWS 16u
+#define GLMB_OPT_STAGE_SCRATCH_NONE 32u
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts);
 
 /* Whether glmb_step computes the frame's estimates in its graph (on by

@@ -447,7 +447,8 @@ extern "C" {
 
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
   if (!h) return GLMB_E_INVALID;
-  if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD | GLMB_OPT_STAGE_SHARED))
+  if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD | GLMB_OPT_STAGE_SHARED |
+               GLMB_OPT_STAGE_SCRATCH_ROWS | GLMB_OPT_STAGE_SCRATCH_NONE))
     return fail(h, GLMB_E_INVALID, "set_launch_options: unknown option bits 0x%x", opts);
   if (opts != h->launch_opts) {
     cudaStreamSynchronize(h->stream);
@@ -889,8 +890,11 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p, bool scal_zeroed = fal
   // counter (persistent grid)
   // staged in global memory: as much of its scratch in shared memory as fits
   a.stage_tail = 0;
+  const int top = (h->launch_opts & GLMB_OPT_STAGE_SCRATCH_NONE)   ? 0
+                  : (h->launch_opts & GLMB_OPT_STAGE_SCRATCH_ROWS) ? 1
+                                                                   : 2;
   if (!p.smem)
-    for (int m = 2; m >= 1 && !a.stage_tail; --m)
+    for (int m = top; m >= 1 && !a.stage_tail; --m)
       if (expand_stage_tail_bytes(dz, p.T, p.K, p.M, m) <= h->smem_limit) a.stage_tail = m;
   const int st_smem = (p.smem ? img : 0) + expand_stage_tail_bytes(dz, p.T, p.K, p.M, a.stage_tail);
   const int st_thr = p.st_thr;

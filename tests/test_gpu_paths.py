@@ -70,7 +70,9 @@ def test_paths_agree_mid(glmb):
 def test_paths_agree_3d(glmb):
     F = glmb.Filter
     _run_lockstep(glmb, "sweep_N50", 13, 6, [0, F.OPT_DRAW_WARP | F.OPT_STAGE_GLOBAL, F.OPT_DRAW_THREAD,
-                                             F.OPT_STAGE_SHARED, F.OPT_STAGE_SHARED | F.OPT_DRAW_WARP])
+                                             F.OPT_STAGE_SHARED, F.OPT_STAGE_SHARED | F.OPT_DRAW_WARP,
+                                             F.OPT_STAGE_GLOBAL | F.OPT_STAGE_SCRATCH_ROWS,
+                                             F.OPT_STAGE_GLOBAL | F.OPT_STAGE_SCRATCH_NONE])
 
 
 def _burst_frames(seed, k_burst, n_extra):
