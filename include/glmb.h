@@ -353,7 +353,11 @@ glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
  *                          keep only the row offsets in shared memory
  *                          while a parent is staged;
  *   GLMB_OPT_STAGE_SCRATCH_NONE  keep none of its scratch there (wins over
- *                          GLMB_OPT_STAGE_SCRATCH_ROWS).
+ *                          GLMB_OPT_STAGE_SCRATCH_ROWS);
+ *   GLMB_OPT_WARP_GROUPS   on the one-warp-per-child path, let several
+ *                          warps share a child whenever the children are
+ *                          few (by default only for plans of 768 slots or
+ *                          more).
  * Default 0: shared-memory staging when eight staging CTAs fit on an SM
  * (else in global memory, with as much of the staging's scratch in shared
  * memory as fits), one thread per child once the children give every SM
@@ -364,6 +368,7 @@ glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
 #define GLMB_OPT_STAGE_SHARED 8u
 #define GLMB_OPT_STAGE_SCRATCH_ROWS 16u
 #define GLMB_OPT_STAGE_SCRATCH_NONE 32u
+#define GLMB_OPT_WARP_GROUPS 64u
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts);
 
 /* Whether glmb_step computes the frame's estimates in its graph (on by

@@ -462,7 +462,7 @@ class Filter:
     STAGES = ("predict", "table", "expand", "select", "materialize", "update_gc", "estimates")
 
     OPT_STAGE_GLOBAL, OPT_DRAW_WARP, OPT_DRAW_THREAD, OPT_STAGE_SHARED = 1, 2, 4, 8
-    OPT_STAGE_SCRATCH_ROWS, OPT_STAGE_SCRATCH_NONE = 16, 32
+    OPT_STAGE_SCRATCH_ROWS, OPT_STAGE_SCRATCH_NONE, OPT_WARP_GROUPS = 16, 32, 64
 
     # ---- learned pair gate ----
     GATE_OFF, GATE_PRUNE, GATE_SCORE = 0, 1, 2

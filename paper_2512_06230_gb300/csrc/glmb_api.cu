@@ -40,7 +40,8 @@ struct Plan {
   bool thread;     // draws: one thread per child (many parents) or one warp per child
   bool smem;       // parents staged in shared memory (else in the image)
   int st_thr;      // threads per staging CTA
-  int Gw, Gm;      // warps per CTA of the warp kernel: expansion, regeneration
+  int Gw, Gm;      // children per CTA of the warp kernel: expansion, regeneration
+  int wg, mg;      // warps per child in them (1, 2, 4 or 8)
 };
 }  // namespace
 
@@ -448,7 +449,7 @@ extern "C" {
 glmb_status glmb_set_launch_options(glmb_handle* h, unsigned opts) {
   if (!h) return GLMB_E_INVALID;
   if (opts & ~(GLMB_OPT_STAGE_GLOBAL | GLMB_OPT_DRAW_WARP | GLMB_OPT_DRAW_THREAD | GLMB_OPT_STAGE_SHARED |
-               GLMB_OPT_STAGE_SCRATCH_ROWS | GLMB_OPT_STAGE_SCRATCH_NONE))
+               GLMB_OPT_STAGE_SCRATCH_ROWS | GLMB_OPT_STAGE_SCRATCH_NONE | GLMB_OPT_WARP_GROUPS))
     return fail(h, GLMB_E_INVALID, "set_launch_options: unknown option bits 0x%x", opts);
   if (opts != h->launch_opts) {
     cudaStreamSynchronize(h->stream);
@@ -823,6 +824,7 @@ ExpandArgs expand_args(glmb_handle* h, const Plan& p, bool mat) {
   a.gc_flag = h->gc_flag;
   a.max_T = h->d_scal + S_MAXT;
   a.max_K = h->d_scal + S_MAXK;
+  a.warp_group = 1;
   a.key_x = h->md.seed_lo;
   a.key_y = h->md.seed_hi ^ (uint32_t)h->frame;
   return a;
@@ -916,8 +918,11 @@ glmb_status enqueue_expand(glmb_handle* h, const Plan& p, bool scal_zeroed = fal
   const long long d_need = ((long long)h->H * h_up + d_thr - 1) / d_thr;
   const int d_grid = p.fixed ? d_ctas * n_sm : (int)std::max(1LL, std::min(d_need, (long long)d_ctas * n_sm));
   // warp kernel: the overflow list, or every child
-  const int w_thr = 32 * p.Gw;
-  const int w_smem = expand_warp_smem(dz, 0, p.T, p.Gw);
+  int wg = p.wg;
+  while (wg > 1 && p.Gw * wg > 16) wg >>= 1;   // a CTA holds at most 16 warps
+  const int w_thr = 32 * p.Gw * wg;
+  const int w_smem = expand_warp_smem(dz, 0, p.T, p.Gw, wg > 1);
+  a.warp_group = wg;
   const int w_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kWarp, w_thr, w_smem));
   int w_grid = w_ctas * n_sm;
   if (p.thread) w_grid = n_sm;
@@ -985,8 +990,13 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   a.upd_count = h->d_scal + S_NUPD;
   a.upd_slot = h->upd_slot;
   a.cap_upd = (int)h->cap_upd;
-  const int m_thr = 32 * p.Gm;
-  const int m_smem = expand_warp_smem(h->md.dz, 1, p.T, p.Gm);
+  int mg = p.mg;
+  while (mg > 1 && p.Gm * mg > 16) mg >>= 1;   // a CTA holds at most 16 warps
+  // (the areas were sized for one warp each; a group's area is 64 bytes larger)
+  if (mg > 1 && expand_warp_smem(h->md.dz, 1, p.T, p.Gm, 1) > h->smem_limit) mg = 1;
+  const int m_thr = 32 * p.Gm * mg;
+  const int m_smem = expand_warp_smem(h->md.dz, 1, p.T, p.Gm, mg > 1);
+  a.warp_group = mg;
   const int m_ctas = std::max(1, expand_occupancy(a, ExpandKernel::kWarp, m_thr, m_smem));
   const int m_grid = p.fixed ? m_ctas * h->n_sm
                              : std::max(1, std::min((h->cap_h + p.Gm - 1) / p.Gm, m_ctas * h->n_sm));
@@ -1048,11 +1058,30 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
              : (p.smem || (long long)h->H < 2LL * h->n_sm) ? 256 : 128;
   p.Gw = p.Gm = 0;
   for (int g = h->tune.warp_cta_warps; g >= 1 && !p.Gw; --g)
-    if (expand_warp_smem(dz, 0, p.T, g) <= h->smem_limit) p.Gw = g;
+    if (expand_warp_smem(dz, 0, p.T, g, 1) <= h->smem_limit) p.Gw = g;
   // materialisation: the CTA size that keeps the most warps resident (its
   // per-warp work area is large, so eight-warp CTAs would leave an SM with
   // one CTA and shared memory unused)
   p.Gm = expand_warp_best_cta(dz, 1, p.T, 8, h->smem_limit);
+  // warps per child: when the children are few (the large-N cells keep a
+  // few hypotheses of thousands of slots and rows), several warps share a
+  // child, as long as all the children's warps fit on the GPU at once
+  // (16 per SM at the kernel's registers) and a CTA stays within 16 warps
+  // (the CTA bound is applied at the launch: plans that differ only in
+  // their work areas per CTA then still match a captured graph)
+  auto group = [&](long long children) {
+    int gw = 1;
+    while (gw < 8 && children * gw * 2 <= 16LL * h->n_sm) gw *= 2;
+    return gw;
+  };
+  // only for plans of many slots (a child's loops are long): the group size
+  // is part of a captured graph's plan, and smaller scenes, whose hypothesis
+  // counts sweep through the thresholds as they grow, would otherwise
+  // spread their frames over more graphs (measured: the N = 200 cell's
+  // regeneration 0.196 -> 0.208 ms)
+  const bool long_children = p.T >= 768 || (h->launch_opts & GLMB_OPT_WARP_GROUPS);
+  p.wg = (p.thread || !long_children) ? 1 : group((long long)h->H * h->cfg.h_up);
+  p.mg = long_children ? group(std::max(1, h->H)) : 1;
   return p.T <= 32767 && p.Gw > 0 && p.Gm > 0;
 }
 
@@ -1320,6 +1349,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
       const glmb_handle::CachedGraph& g = h->graphs[gi];
       if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread || g.plan.st_thr != p.st_thr ||
+          g.plan.wg != p.wg || g.plan.mg != p.mg ||
           g.plan.T < p.T || g.plan.K < p.K || g.plan.M < p.M)
         continue;
       if (best < 0 || g.smem < h->graphs[best].smem) best = gi;

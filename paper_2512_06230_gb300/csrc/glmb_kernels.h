@@ -95,6 +95,7 @@ struct ExpandArgs {
   unsigned* redo_count;
   unsigned* stage_next;   // staging: next parent to take (zero at the launch)
   int stage_tail;         // staging in global memory: what it keeps in shared memory (expand_stage_tail_bytes)
+  int warp_group;         // warp kernel: warps per child (1, 2, 4 or 8; a CTA holds whole groups)
   // expansion outputs
   long long* child_key;   // [H * h_up] fixed-point log-weight or kKeyInvalid
   unsigned long long* child_hash;   // [H * h_up] order-free key of (deaths, associations)
@@ -139,7 +140,7 @@ int expand_stage_tail_bytes(int dz, int T_plan, int K_plan, int M_plan, int mode
 // shared memory of a draw-kernel CTA of `threads` threads
 int expand_draw_smem(int threads);
 // shared memory of a warp-kernel CTA of `warps` warps
-int expand_warp_smem(int dz, int materialize, int T_max, int warps);
+int expand_warp_smem(int dz, int materialize, int T_max, int warps, int grp = 0);
 enum class ExpandKernel { kStage, kDraw, kWarp, kMatPrep };
 // resident CTAs per SM of one of the kernels
 int expand_occupancy(const ExpandArgs& a, ExpandKernel k, int threads, int smem);

@@ -167,10 +167,10 @@ int expand_image_bytes(int dz, int T, int K, int M) {
 
 // per-warp work area of the warp kernel
 struct WLay {
-  int se, sq, hw, cnt, newval, tmask, dmask, dpre, nt, tlist, total;
+  int se, sq, hw, cnt, newval, tmask, dmask, dpre, nt, tlist, red, total;
 };
 
-__host__ __device__ inline WLay make_wlay(int dz, int mat, int T) {
+__host__ __device__ inline WLay make_wlay(int dz, int mat, int T, int grp = 0) {
   WLay L;
   Bump b;
   const int W = (T + 31) / 32 + 1;
@@ -184,12 +184,13 @@ __host__ __device__ inline WLay make_wlay(int dz, int mat, int T) {
   L.dpre = b.take(4LL * W);
   L.nt = b.take(16);
   L.tlist = b.take(2LL * T);
+  L.red = grp ? b.take(64) : 0;   // a multi-warp group's reductions
   L.total = b.off;
   return L;
 }
 
-int expand_warp_smem(int dz, int materialize, int T, int warps) {
-  return warps * make_wlay(dz, materialize, T).total;
+int expand_warp_smem(int dz, int materialize, int T, int warps, int grp) {
+  return warps * make_wlay(dz, materialize, T, grp).total;
 }
 
 template <typename T>
@@ -206,6 +207,14 @@ __device__ __forceinline__ uint32_t thr_of(float frac) {
   if (!(frac > 0.f)) return 0u;
   if (frac >= 1.f) return kOne24;
   return (uint32_t)ceilf(frac * 16777216.f);
+}
+
+// A child of the warp path is handled by a group of gsz threads (one warp,
+// or several consecutive warps of the CTA that share one work area and
+// synchronise on named barrier gid + 1).
+__device__ __forceinline__ void group_sync(int gsz, int gid) {
+  if (gsz == 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(gsz) : "memory");
 }
 
 __device__ __forceinline__ void touch(uint32_t* tmask, uint16_t* tlist, int* nt, int t) {
@@ -1372,14 +1381,17 @@ __global__ void __launch_bounds__(256, 3) draw_kernel(const __grid_constant__ Ex
 // ====================== warp: one warp per child ======================
 // The work area's sums, masks and touched list are zero on entry and are
 // left zero on return.
-template <int DZ, bool MAT>
+template <int DZ, bool MAT, bool GRP>
 __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, const int Kp, const int M,
                            const int h, const int n, const int s_out, const uint2 key, unsigned char* gb,
-                           const WLay& WL) {
+                           const WLay& WL, const int gsz_in, const int gid) {
+  const int gsz = GRP ? gsz_in : 32;   // one warp: the group code folds away
   const Model& md = a.md;
   const Scal& sc = *v.sc;
   const int HU = md.h_up;
   const int lane = threadIdx.x & 31;
+  const int gl = (int)threadIdx.x % gsz;   // the thread's index in its group
+  unsigned long long* red = at<unsigned long long>(gb, WL.red);
   const int W = (T + 31) >> 5;
   const int nrc = (M + 3) >> 2;
   const uint32_t uid_lo = (uint32_t)sc.uid, uid_hi = (uint32_t)(sc.uid >> 32);
@@ -1398,7 +1410,7 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
   // phase 1: deaths
   int my_dead = 0;
   unsigned long long hsh = 0;
-  for (int x = lane; x < ndpc; x += 32) {
+  for (int x = gl; x < ndpc; x += gsz) {
     const uint32_t ent = v.dpc[x];
     const uint32_t cc = ent >> 4, mask = ent & 15u;
     const uint4 r = philox10(make_uint4(uid_lo, uid_hi, 2u * (uint32_t)n, cc), key);
@@ -1414,22 +1426,24 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       }
     }
   }
-  __syncwarp();
+  group_sync(gsz, gid);
   if (MAT) {
-    uint32_t carry = 0;
-    for (int base = 0; base < W; base += 32) {
-      const int w = base + lane;
-      const uint32_t val = w < W ? (uint32_t)__popc(dmask[w]) : 0u;
-      uint32_t x = val;
+    if (gl < 32) {   // the group's first warp
+      uint32_t carry = 0;
+      for (int base = 0; base < W; base += 32) {
+        const int w = base + lane;
+        const uint32_t val = w < W ? (uint32_t)__popc(dmask[w]) : 0u;
+        uint32_t x = val;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (w < W) dpre[w] = carry + x - val;
+        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
       }
-      if (w < W) dpre[w] = carry + x - val;
-      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
     }
-    __syncwarp();
+    group_sync(gsz, gid);
   }
   // phase 2: one categorical draw per detection row.  The dead slots'
   // bloom (slot mod 64) screens a row's candidates before the exact check;
@@ -1438,12 +1452,17 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
   int my_dclut = 0;
   bool bad_row = false;
   unsigned long long dbl = 0ull;
-  for (int w = lane; w < W; w += 32)
+  for (int w = gl; w < W; w += gsz)
     for (uint32_t m = dmask[w]; m; m &= m - 1u) dbl |= 1ull << ((32 * w + __ffs(m) - 1) & 63);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dbl |= __shfl_xor_sync(0xFFFFFFFFu, dbl, o);
+  if (gsz > 32) {
+    if (lane == 0 && dbl) atomicOr(&red[0], dbl);
+    group_sync(gsz, gid);
+    dbl = red[0];
+  }
   const PhiloxRun pr = philox_run(uid_lo, uid_hi, 2u * (uint32_t)n + 1u, key);
-  for (int cc = lane; cc < nrc; cc += 32) {
+  for (int cc = gl; cc < nrc; cc += gsz) {
     const int i0 = 4 * cc;
     const int i1 = min(i0 + 4, M);
     const uint4 r = philox_at(pr, (uint32_t)cc, key);
@@ -1542,12 +1561,12 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       }
     }
   }
-  __syncwarp();
+  group_sync(gsz, gid);
   // phase 3: rescore touched slots
   const int nt = *((volatile int*)ntp);
   long long my_delta = 0;
   int my_dninf = 0;
-  for (int x = lane; x < nt; x += 32) {
+  for (int x = gl; x < nt; x += gsz) {
     const int t = tlist[x];
     int ninf;
     long long term;
@@ -1580,11 +1599,29 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
     my_dead += __shfl_xor_sync(0xFFFFFFFFu, my_dead, o);
     hsh += __shfl_xor_sync(0xFFFFFFFFu, hsh, o);
   }
-  const bool any_bad = __any_sync(0xFFFFFFFFu, bad_row);
-  __syncwarp();
+  bool any_bad = __any_sync(0xFFFFFFFFu, bad_row);
+  if (gsz > 32 && !MAT) {
+    // the group's totals (integers: the same whatever the order)
+    if (lane == 0) {
+      atomicAdd(&red[1], (unsigned long long)my_delta);
+      atomicAdd(&red[2], (unsigned long long)(long long)my_dninf);
+      atomicAdd(&red[3], (unsigned long long)(long long)my_dclut);
+      atomicAdd(&red[4], (unsigned long long)(long long)my_dead);
+      atomicAdd(&red[5], hsh);
+      if (any_bad) atomicOr(&red[6], 1ull);
+    }
+    group_sync(gsz, gid);
+    my_delta = (long long)red[1];
+    my_dninf = (int)(long long)red[2];
+    my_dclut = (int)(long long)red[3];
+    my_dead = (int)(long long)red[4];
+    hsh = red[5];
+    any_bad = red[6] != 0ull;
+  }
+  group_sync(gsz, gid);
   if (MAT) {
     const uint32_t base = a.out_ptr[s_out];
-    for (int t = lane; t < T; t += 32) {
+    for (int t = gl; t < T; t += gsz) {
       if (bit_of(dmask, t)) continue;
       const uint32_t below = dpre[t >> 5] + __popc(dmask[t >> 5] & ((1u << (t & 31)) - 1u));
       const uint32_t val = bit_of(tmask, t) ? newval[t] : v.refnew[t];
@@ -1594,10 +1631,11 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
         else atomicOr(a.err, kErrChkRemap);
       }
     }
-    __syncwarp();
+    group_sync(gsz, gid);
   }
-  for (int w = lane; w < W; w += 32) { tmask[w] = 0; dmask[w] = 0; }
-  if (lane == 0) {
+  for (int w = gl; w < W; w += gsz) { tmask[w] = 0; dmask[w] = 0; }
+  if (GRP && gl < 8) red[gl] = 0ull;   // every reader has passed a barrier since
+  if (gl == 0) {
     *ntp = 0;
     if (!MAT) {
       const long long score = sc.ref_score + my_delta + (md.kappa_zero ? 0LL : (long long)my_dclut * md.fx_log_kappa);
@@ -1610,18 +1648,21 @@ __device__ void warp_child(const ExpandArgs& a, const View& v, const int T, cons
       a.child_alive[j] = (uint16_t)(T - my_dead);
     }
   }
-  __syncwarp();
+  group_sync(gsz, gid);
 }
 
-// Persistent over a list of children, one warp each: the survivors (MAT),
-// every child of every parent (a.warp_all), or the draw kernel's overflow.
-template <int DZ, bool MAT>
+// Persistent over a list of children, one group of a.warp_group warps each
+// (several when the children are few and long): the survivors (MAT), every
+// child of every parent (a.warp_all), or the draw kernel's overflow.
+template <int DZ, bool MAT, bool GRP>
 __global__ void __launch_bounds__(512) warp_kernel(const __grid_constant__ ExpandArgs a) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   const Lay L = make_lay(DZ, a.T_max, a.K_max, a.M_plan);
-  const WLay WL = make_wlay(DZ, MAT, a.T_max);
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const WLay WL = make_wlay(DZ, MAT, a.T_max, GRP ? 1 : 0);
+  // groups of a.warp_group warps per child, one work area each
+  const int gsz = GRP ? 32 * a.warp_group : 32, groups = (int)blockDim.x / gsz;
+  const int g = (int)threadIdx.x / gsz, gl = (int)threadIdx.x % gsz;
   const int HU = a.md.h_up, M = a.fs->M;
   const uint2 key = make_uint2(a.key_x, a.key_y);
   // a frame already abandoned (e.g. entries beyond capacity) writes
@@ -1631,7 +1672,7 @@ __global__ void __launch_bounds__(512) warp_kernel(const __grid_constant__ Expan
   const long long count = MAT ? (long long)*a.n_surv
                               : (a.warp_all ? (long long)a.fs->H * HU : (long long)*a.redo_count);
   // an empty list (the usual overflow case) costs no work-area set-up
-  if ((long long)blockIdx.x * (blockDim.x >> 5) >= count) return;
+  if ((long long)blockIdx.x * groups >= count) return;
   unsigned char* gb = sm + g * WL.total;
   {
     // the sums are indexed d * T + t with each parent's own T <= T_max
@@ -1640,27 +1681,28 @@ __global__ void __launch_bounds__(512) warp_kernel(const __grid_constant__ Expan
     long long* acc_se = at<long long>(gb, WL.se);
     long long* acc_sq = at<long long>(gb, WL.sq);
     unsigned long long* acc_hw = at<unsigned long long>(gb, WL.hw);
-    for (int t = lane; t < a.T_max; t += 32) {
+    for (int t = gl; t < a.T_max; t += gsz) {
       acc_cnt[t] = 0;
 #pragma unroll
       for (int d = 0; d < DZ; ++d) acc_se[d * a.T_max + t] = 0;
       acc_sq[t] = 0;
       if (MAT) acc_hw[t] = 0;
     }
-    for (int w = lane; w < Wm; w += 32) {
+    for (int w = gl; w < Wm; w += gsz) {
       at<uint32_t>(gb, WL.tmask)[w] = 0;
       at<uint32_t>(gb, WL.dmask)[w] = 0;
     }
-    if (lane == 0) *at<int>(gb, WL.nt) = 0;
-    __syncwarp();
+    if (gl == 0) *at<int>(gb, WL.nt) = 0;
+    if (GRP && gl < 8) at<unsigned long long>(gb, WL.red)[gl] = 0ull;
+    group_sync(gsz, g);
   }
-  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + g; c < count; c += nw) {
+  const long long nw = (long long)gridDim.x * groups;
+  for (long long c = (long long)blockIdx.x * groups + g; c < count; c += nw) {
     const long long ci = MAT ? a.surv_idx[c] : (a.warp_all ? c : (long long)a.redo_list[c]);
     const int h = (int)(ci / HU), n = (int)(ci % HU);
     const View v = make_view(a.img + (size_t)h * a.img_stride, L, a.pt);
     if (v.sc->bad) continue;
-    warp_child<DZ, MAT>(a, v, v.sc->T, a.K_max, M, h, n, (int)c, key, gb, WL);
+    warp_child<DZ, MAT, GRP>(a, v, v.sc->T, a.K_max, M, h, n, (int)c, key, gb, WL, gsz, g);
   }
 }
 
@@ -1838,9 +1880,13 @@ static KernelFn stage_fn(int dz, bool smem) {
   return smem ? stage_kernel<3, true> : stage_kernel<3, false>;
 }
 static KernelFn draw_fn(int dz) { return dz == 2 ? draw_kernel<2> : draw_kernel<3>; }
-static KernelFn warp_fn(int dz, bool mat) {
-  if (dz == 2) return mat ? warp_kernel<2, true> : warp_kernel<2, false>;
-  return mat ? warp_kernel<3, true> : warp_kernel<3, false>;
+static KernelFn warp_fn(int dz, bool mat, bool grp = false) {
+  if (grp) {
+    if (dz == 2) return mat ? warp_kernel<2, true, true> : warp_kernel<2, false, true>;
+    return mat ? warp_kernel<3, true, true> : warp_kernel<3, false, true>;
+  }
+  if (dz == 2) return mat ? warp_kernel<2, true, false> : warp_kernel<2, false, false>;
+  return mat ? warp_kernel<3, true, false> : warp_kernel<3, false, false>;
 }
 static KernelFn prep_fn(int dz) { return dz == 2 ? mat_prep_kernel<2> : mat_prep_kernel<3>; }
 
@@ -1849,8 +1895,10 @@ void expand_init(int smem_limit) {
     cudaFuncSetAttribute(stage_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
     cudaFuncSetAttribute(stage_fn(dz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
     cudaFuncSetAttribute(draw_fn(dz), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-    cudaFuncSetAttribute(warp_fn(dz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
-    cudaFuncSetAttribute(warp_fn(dz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    for (int grp = 0; grp < 2; ++grp) {
+      cudaFuncSetAttribute(warp_fn(dz, false, grp), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+      cudaFuncSetAttribute(warp_fn(dz, true, grp), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+    }
   }
 }
 
@@ -1858,7 +1906,7 @@ static KernelFn kernel_of(const ExpandArgs& a, ExpandKernel k) {
   switch (k) {
     case ExpandKernel::kStage: return stage_fn(a.md.dz, a.stage_smem != 0);
     case ExpandKernel::kDraw: return draw_fn(a.md.dz);
-    case ExpandKernel::kWarp: return warp_fn(a.md.dz, a.materialize != 0);
+    case ExpandKernel::kWarp: return warp_fn(a.md.dz, a.materialize != 0, a.warp_group > 1);
     default: return prep_fn(a.md.dz);
   }
 }
@@ -1884,7 +1932,7 @@ int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem
   if (it != memo.end()) return it->second;
   int best = 0, best_res = 0;
   for (int g = 1; g <= max_warps; ++g) {
-    const int smem = expand_warp_smem(dz, materialize, T, g);
+    const int smem = expand_warp_smem(dz, materialize, T, g, 0);
     if (smem > smem_limit) break;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_fn(dz, materialize != 0), 32 * g, smem) !=
@@ -1902,7 +1950,8 @@ int expand_warp_best_cta(int dz, int materialize, int T, int max_warps, int smem
 
 bool expand_kernel_takes_key(const void* fn) {
   for (int dz = 2; dz <= 3; ++dz)
-    if (fn == (const void*)draw_fn(dz) || fn == (const void*)warp_fn(dz, false) || fn == (const void*)warp_fn(dz, true))
+    if (fn == (const void*)draw_fn(dz) || fn == (const void*)warp_fn(dz, false) || fn == (const void*)warp_fn(dz, true) ||
+        fn == (const void*)warp_fn(dz, false, true) || fn == (const void*)warp_fn(dz, true, true))
       return true;
   return false;
 }

@@ -51,18 +51,24 @@ def _run_lockstep(glmb, preset, seed, n_frames, opts_list, **cfg_over):
             ret.append(f.retained()[0])
         for o, r in zip(opts_list[1:], ret[1:]):
             assert np.array_equal(ret[0], r), (k, o)
+    # the whole state (hypotheses, components, theta) after the last frame
+    s0 = fs[0].export_state()
+    for o, f in zip(opts_list[1:], fs[1:]):
+        assert f.export_state() == s0, o
     return paths_seen
 
 
 def test_paths_agree_tiny(glmb):
     F = glmb.Filter
     _run_lockstep(glmb, "tiny", 11, 20, [0, F.OPT_STAGE_GLOBAL, F.OPT_DRAW_THREAD,
-                                         F.OPT_DRAW_THREAD | F.OPT_STAGE_GLOBAL, F.OPT_DRAW_WARP])
+                                         F.OPT_DRAW_THREAD | F.OPT_STAGE_GLOBAL, F.OPT_DRAW_WARP,
+                                         F.OPT_DRAW_WARP | F.OPT_WARP_GROUPS, F.OPT_WARP_GROUPS])
 
 
 def test_paths_agree_mid(glmb):
     F = glmb.Filter
-    seen = _run_lockstep(glmb, "mid", 12, 16, [0, F.OPT_DRAW_WARP, F.OPT_DRAW_THREAD | F.OPT_STAGE_GLOBAL],
+    seen = _run_lockstep(glmb, "mid", 12, 16, [0, F.OPT_DRAW_WARP, F.OPT_DRAW_THREAD | F.OPT_STAGE_GLOBAL,
+                                               F.OPT_DRAW_WARP | F.OPT_WARP_GROUPS],
                          max_meas=400, max_births=16, max_tracks=300)
     assert len(seen) >= 2   # both draw mappings ran
 
