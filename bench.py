@@ -1088,7 +1088,7 @@ def main():
         name, _, hm = spec.partition(":")
         sc2 = scene_for_rank(args, rank, name=name, h_max=int(hm) if hm else None)
         cfg2 = filter_cfg(sc2)
-        c2 = Cell(glmb, torch, dev, sc2, cfg2, window_start(name), flush=flush)
+        c2 = Cell(glmb, torch, dev, sc2, cfg2, window_start(name), stages=stages, flush=flush)
         try:
             c2.precapture()
             c2.run(args.warmup, 0)

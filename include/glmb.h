@@ -354,10 +354,12 @@ glmb_status glmb_get_tuning(glmb_handle* h, glmb_tuning* t);
  *                          while a parent is staged;
  *   GLMB_OPT_STAGE_SCRATCH_NONE  keep none of its scratch there (wins over
  *                          GLMB_OPT_STAGE_SCRATCH_ROWS);
- *   GLMB_OPT_WARP_GROUPS   on the one-warp-per-child path, let several
- *                          warps share a child whenever the children are
- *                          few (by default only for plans of 768 slots or
- *                          more).
+ *   GLMB_OPT_WARP_GROUPS   on the one-warp-per-child path, let at least
+ *                          two warps share each child (by default groups
+ *                          form when the per-child work areas of a
+ *                          large plan leave an SM fewer than 16 warps, or
+ *                          when a plan of 768 slots or more has too few
+ *                          children to fill the GPU's warps).
  * Default 0: shared-memory staging when eight staging CTAs fit on an SM
  * (else in global memory, with as much of the staging's scratch in shared
  * memory as fits), one thread per child once the children give every SM

@@ -42,6 +42,7 @@ struct Plan {
   int st_thr;      // threads per staging CTA
   int Gw, Gm;      // children per CTA of the warp kernel: expansion, regeneration
   int wg, mg;      // warps per child in them (1, 2, 4 or 8)
+  int wc, mc;      // the part of wg, mg that follows the hypothesis count
 };
 }  // namespace
 
@@ -1020,6 +1021,29 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
 
 // expansion plan of this frame: slots exactly (largest survivor of the last
 // prune plus births), gated pairs from earlier frames (redone if exceeded)
+// Warps per child on the warp path (expansion wg, regeneration mg) from
+// the parts wc, mc that follow the hypothesis count: a child's work area in
+// shared memory bounds how many warps an SM holds (16 at the kernel's
+// registers); when the areas of a large plan leave fewer, a group of 2, 4
+// or 8 warps shares each area (a child), so that the SM still holds up to
+// 16 warps.  This part depends on the plan's slots alone, so a graph
+// captured with headroom serves the frames that need fewer slots.
+// GLMB_OPT_WARP_GROUPS forces groups of at least two (tests).
+void set_groups(glmb_handle* h, Plan& p, int wc, int mc) {
+  const int dz = h->md.dz;
+  auto by_area = [&](int mat) {
+    const int area = expand_warp_smem(dz, mat, p.T, 1, 1);
+    const int areas_sm = std::max(1, std::min(16, h->smem_per_sm / std::max(area, 1)));
+    int gw = 1;
+    while (gw < 8 && areas_sm * gw * 2 <= 16) gw *= 2;
+    return (h->launch_opts & GLMB_OPT_WARP_GROUPS) ? std::max(gw, 2) : gw;
+  };
+  p.wc = wc;
+  p.mc = mc;
+  p.wg = p.thread ? 1 : std::max(by_area(0), wc);
+  p.mg = std::max(by_area(1), mc);
+}
+
 bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, Plan& p) {
   p.fixed = fixed;
   p.T = std::max(1, T_plan);
@@ -1063,25 +1087,20 @@ bool make_plan(glmb_handle* h, bool fixed, int T_plan, int K_plan, int M_plan, P
   // per-warp work area is large, so eight-warp CTAs would leave an SM with
   // one CTA and shared memory unused)
   p.Gm = expand_warp_best_cta(dz, 1, p.T, 8, h->smem_limit);
-  // warps per child: when the children are few (the large-N cells keep a
-  // few hypotheses of thousands of slots and rows), several warps share a
-  // child, as long as all the children's warps fit on the GPU at once
-  // (16 per SM at the kernel's registers) and a CTA stays within 16 warps
-  // (the CTA bound is applied at the launch: plans that differ only in
-  // their work areas per CTA then still match a captured graph)
-  auto group = [&](long long children) {
+  // warps per child, in two parts.  When the children are few (a few
+  // hypotheses of many slots), several warps share a child, as long as all
+  // the children's warps fit on the GPU at once (16 per SM).  This part
+  // follows the hypothesis count, so it is kept to frames of 768 slots or
+  // more, whose scenes hold their counts (smaller scenes sweep through the
+  // thresholds as they grow and would spread their frames over more graphs:
+  // measured, the N = 200 cell's regeneration 0.196 -> 0.208 ms).
+  auto by_children = [&](long long children) {
     int gw = 1;
-    while (gw < 8 && children * gw * 2 <= 16LL * h->n_sm) gw *= 2;
+    if (p.T >= 768)
+      while (gw < 8 && children * gw * 2 <= 16LL * h->n_sm) gw *= 2;
     return gw;
   };
-  // only for plans of many slots (a child's loops are long): the group size
-  // is part of a captured graph's plan, and smaller scenes, whose hypothesis
-  // counts sweep through the thresholds as they grow, would otherwise
-  // spread their frames over more graphs (measured: the N = 200 cell's
-  // regeneration 0.196 -> 0.208 ms)
-  const bool long_children = p.T >= 768 || (h->launch_opts & GLMB_OPT_WARP_GROUPS);
-  p.wg = (p.thread || !long_children) ? 1 : group((long long)h->H * h->cfg.h_up);
-  p.mg = long_children ? group(std::max(1, h->H)) : 1;
+  set_groups(h, p, p.thread ? 1 : by_children((long long)h->H * h->cfg.h_up), by_children(std::max(1, h->H)));
   return p.T <= 32767 && p.Gw > 0 && p.Gm > 0;
 }
 
@@ -1349,7 +1368,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
     for (int gi = 0; gi < (int)h->graphs.size(); ++gi) {
       const glmb_handle::CachedGraph& g = h->graphs[gi];
       if (g.hcur != h->hcur || g.prof != h->prof_mask || g.plan.thread != p.thread || g.plan.st_thr != p.st_thr ||
-          g.plan.wg != p.wg || g.plan.mg != p.mg ||
+          g.plan.wc != p.wc || g.plan.mc != p.mc ||
           g.plan.T < p.T || g.plan.K < p.K || g.plan.M < p.M)
         continue;
       if (best < 0 || g.smem < h->graphs[best].smem) best = gi;
@@ -1361,6 +1380,7 @@ glmb_status glmb_step_enqueue(glmb_handle* h, const glmb_birth* births, int n_bi
           q.thread != p.thread ||
           (p.smem && !q.smem))
         q = p;
+      set_groups(h, q, p.wc, p.mc);   // this frame's parts (q.T decides the rest)
       if ((st = ensure_img(h, q)) != GLMB_OK) {
         h->frame -= 1;
         return st;

@@ -408,15 +408,18 @@ __device__ __forceinline__ long long scan_len(const int* n_dev, int mult) {
 // the order they start (an atomic counter), publish their tile's sum, and
 // add up their predecessors' published sums back to the nearest published
 // inclusive prefix.  A tile waits only on tiles taken before it, by blocks
-// already running.  Work area (elements of T), laid out for the largest scan
-// it serves (nw tiles): counters [2], status [nw], aggregates [nw], inclusive
-// prefixes [nw]; counters and status are zero before the first use and left
-// zero by the last block to finish.
+// already running.  The grid is persistent (at most the blocks the GPU holds
+// at once): a block takes tiles until none is left, so that a scan sized for
+// a large capacity but short at run time costs no idle blocks.  Work area
+// (elements of T), laid out for the largest scan it serves (nw tiles):
+// counters [2], status [nw], aggregates [nw], inclusive prefixes [nw];
+// counters and status are zero before the first use and left zero by the
+// last block to finish.
 constexpr unsigned kStAgg = 1u, kStInc = 2u;
 
 template <typename T>
 __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T* total, int total_at_end,
-                             T* work, int nw, unsigned* err, long long spin_limit, int withhold_first) {
+                             T* work, int nw, int nt, unsigned* err, long long spin_limit, int withhold_first) {
   pdl_enter();
   __shared__ int s_tile;
   __shared__ T s_excl;
@@ -424,13 +427,20 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
   T* st = work + 2;
   T* agg = work + 2 + nw;
   T* inc = work + 2 + 2 * nw;
-  const int nt = (int)gridDim.x;
   const long long n = scan_len(n_dev, mult);
   const int ntiles = (int)min((long long)nt, (n + kScanTile - 1) / kScanTile);
-  if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], T(1));
-  __syncthreads();
-  const int tile = s_tile;
-  if (tile < ntiles) {
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctr[0], T(1));
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();   // s_tile is read by all before the next take
+    if (tile >= ntiles) {
+      if (tile == 0 && threadIdx.x == 0) {   // empty input
+        if (total) *total = 0;
+        if (total_at_end) out[n] = 0;
+      }
+      break;
+    }
     const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
     T vals[kScanItems];
     T sum = 0;
@@ -500,9 +510,6 @@ __global__ void scan_onepass(const T* in, T* out, const int* n_dev, int mult, T*
         out[base + k] = run;
         run += vals[k];
       }
-  } else if (tile == 0 && threadIdx.x == 0) {   // empty input
-    if (total) *total = 0;
-    if (total_at_end) out[n] = 0;
   }
   // the last block to finish clears the work area for the next scan
   __syncthreads();
@@ -545,6 +552,19 @@ __global__ void scan_small(const T* in, T* out, const int* n_dev, int mult, T* t
 }
 
 static int scan_tiles(long long cap) { return (int)((cap + kScanTile - 1) / kScanTile + 1); }
+
+// blocks of scan_onepass the GPU holds at once (the persistent grid)
+template <typename T>
+static int scan_resident_blocks() {
+  static const int n = [] {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, scan_onepass<T>, kScanThreads, 0);
+    return std::max(1, sms) * std::max(1, per);
+  }();
+  return n;
+}
 long long scan_tmp_elems(long long cap) { return 3LL * scan_tiles(cap) + 2; }
 
 template <typename T>
@@ -561,8 +581,8 @@ static void scan_impl(const T* in, T* out, const int* n_dev, int mult, long long
   }
   const WaitTest wt = wait_test();
   const bool test = wt.mode == kWaitTestScan;
-  launch_k(scan_onepass<T>, nt, kScanThreads, 0, s, in, out, n_dev, mult, total, total_at_end ? 1 : 0, tmp, nw, err,
-           test ? wt.limit : kScanSpinLimit, test ? 1 : 0);
+  launch_k(scan_onepass<T>, std::min(nt, scan_resident_blocks<T>()), kScanThreads, 0, s, in, out, n_dev, mult,
+           total, total_at_end ? 1 : 0, tmp, nw, nt, err, test ? wt.limit : kScanSpinLimit, test ? 1 : 0);
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, const int* n_dev, int mult, long long cap,
