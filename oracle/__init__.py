@@ -38,7 +38,9 @@ class _Config(C.Structure):
                 ("p_d", C.c_double), ("lambda_d", C.c_double), ("clutter_rate", C.c_double),
                 ("volume", C.c_double), ("gate", C.c_double), ("h_max", C.c_int32),
                 ("h_up", C.c_int32), ("tau", C.c_double), ("seed", C.c_uint64),
-                ("score_mode", C.c_int32), ("n_threads", C.c_int32)]
+                ("score_mode", C.c_int32), ("n_threads", C.c_int32), ("model", C.c_int32),
+                ("n_particles", C.c_int32), ("sigma_a", C.c_double), ("sigma_w", C.c_double),
+                ("ess_frac", C.c_double)]
 
 
 class _Birth(C.Structure):
@@ -87,6 +89,14 @@ def _load():
         lib.orc_philox.argtypes = [P, P, P]
         lib.orc_mix64.argtypes = [C.c_uint64]
         lib.orc_mix64.restype = C.c_uint64
+        lib.orc_import_particles.argtypes = [P, P, P]
+        lib.orc_export_particles.argtypes = [P, P, P]
+        lib.orc_slot_particles.argtypes = [P, C.c_int, C.c_int, P, P]
+        lib.orc_resample_margin.argtypes = [P]
+        lib.orc_resample_margin.restype = C.c_double
+        lib.orc_ctrv.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
+        lib.orc_particle_normals.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                             C.c_uint32, P]
         _lib = lib
     return _lib
 
@@ -144,7 +154,20 @@ def make_config(cfg: dict, n_threads: int = 1) -> _Config:
     c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
     c.score_mode = int(cfg.get("score_mode", 0))
     c.n_threads = int(n_threads)
+    c.model = int(cfg.get("model", 0))
+    c.n_particles = int(cfg.get("n_particles", 0))
+    c.sigma_a = float(cfg.get("sigma_a", 0.0))
+    c.sigma_w = float(cfg.get("sigma_w", 0.0))
+    c.ess_frac = float(cfg.get("ess_frac", 0.0))
     return c
+
+
+def ctrv(x, dt, a=0.0, alpha=0.0) -> np.ndarray:
+    """The oracle's CTRV step of one state (px, py, v, heading, turn rate)."""
+    xi = np.ascontiguousarray(x, np.float64).reshape(5)
+    out = np.zeros(5)
+    _load().orc_ctrv(_ptr(xi), float(dt), float(a), float(alpha), _ptr(out))
+    return out
 
 
 def births_array(births, dim_x: int):
@@ -202,8 +225,14 @@ class Oracle:
         self.prune()
 
     # -- state -------------------------------------------------------------
+    @property
+    def particles(self) -> int:
+        return self._c.n_particles if self._c.model == 1 else 0
+
     def import_state(self, frame, logw, uid, tracks):
-        """tracks: list (per hypothesis) of (lk, lb, mean, cov)."""
+        """tracks: list (per hypothesis) of (lk, lb, mean, cov), or with the
+        particle model (lk, lb, mean, cov, x[P][5], logw[P]) (the mean and
+        covariance are then recomputed from the particles)."""
         H = len(logw)
         ntr = np.array([len(t) for t in tracks], dtype=np.int32)
         n = int(ntr.sum())
@@ -213,13 +242,23 @@ class Oracle:
         cov = np.zeros((max(n, 1), self.dx, self.dx))
         o = 0
         for tr in tracks:
-            for (a, b, m, P) in tr:
-                lk[o], lb[o], mean[o], cov[o] = a, b, m, P
+            for rec in tr:
+                lk[o], lb[o], mean[o], cov[o] = rec[:4]
                 o += 1
         lw = np.ascontiguousarray(logw, dtype=np.float64)
         ud = np.ascontiguousarray(uid, dtype=np.uint64)
         _check(self.lib.orc_import(self.h, int(frame), H, _ptr(lw), _ptr(ud), _ptr(ntr),
                                    _ptr(lk), _ptr(lb), _ptr(mean), _ptr(cov)), "import")
+        Np = self.particles
+        if Np:
+            x = np.zeros((max(n, 1), Np, 5))
+            pw = np.zeros((max(n, 1), Np))
+            o = 0
+            for tr in tracks:
+                for rec in tr:
+                    x[o], pw[o] = rec[4], rec[5]
+                    o += 1
+            _check(self.lib.orc_import_particles(self.h, _ptr(x), _ptr(pw)), "import_particles")
 
     def export_state(self):
         H, n, fr = C.c_int(), C.c_int(), C.c_int()
@@ -234,12 +273,36 @@ class Oracle:
         cov = np.zeros((max(n, 1), self.dx, self.dx))
         self.lib.orc_export(self.h, _ptr(logw), _ptr(uid), _ptr(ntr), _ptr(lk), _ptr(lb),
                             _ptr(mean), _ptr(cov))
+        Np = self.particles
+        if Np:
+            x = np.zeros((max(n, 1), Np, 5))
+            pw = np.zeros((max(n, 1), Np))
+            _check(self.lib.orc_export_particles(self.h, _ptr(x), _ptr(pw)), "export_particles")
         tracks, o = [], 0
         for h in range(H):
-            tracks.append([(int(lk[o + t]), int(lb[o + t]), mean[o + t].copy(), cov[o + t].copy())
-                           for t in range(ntr[h])])
+            if Np:
+                tracks.append([(int(lk[o + t]), int(lb[o + t]), mean[o + t].copy(), cov[o + t].copy(),
+                                x[o + t].copy(), pw[o + t].copy()) for t in range(ntr[h])])
+            else:
+                tracks.append([(int(lk[o + t]), int(lb[o + t]), mean[o + t].copy(), cov[o + t].copy())
+                               for t in range(ntr[h])])
             o += ntr[h]
         return fr.value, logw, uid, tracks
+
+    def slot_particles(self, h, t):
+        Np = self.particles
+        x = np.zeros((Np, 5))
+        pw = np.zeros(Np)
+        _check(self.lib.orc_slot_particles(self.h, h, t, _ptr(x), _ptr(pw)), "slot_particles")
+        return x, pw
+
+    def resample_margin(self) -> float:
+        return self.lib.orc_resample_margin(self.h)
+
+    def particle_normals(self, lk, lb, p, stream, call) -> np.ndarray:
+        out = np.zeros(2)
+        self.lib.orc_particle_normals(self.h, lk, lb, p, stream, call, _ptr(out))
+        return out
 
     # -- introspection -------------------------------------------------------
     def num_parents(self):

@@ -1,7 +1,8 @@
 /*
  * FP64 CPU oracle of the multi-detection GLMB filter update
  * (arXiv 2512.06230, "GPU-GLMB", Section 3), with Gaussian constant-velocity
- * track densities in place of the paper's particles.
+ * track densities (model 0) or the paper's weighted particles moved by
+ * constant-turn-rate-and-velocity kinematics (model 1, reading R15).
  *
  * TEST INFRASTRUCTURE ONLY.  Plain, slow and written to be read against the
  * paper: every step follows Section 3 in the paper's order, in double
@@ -181,13 +182,15 @@ typedef struct {
   uint64_t uid;
   int n;
   uint32_t *lk, *lb;
-  double *m, *P;              /* n*dx, n*dx*dx */
+  double *m, *P;              /* n*dx, n*dx*dx (model 1: the particles' moments) */
+  double *x, *pw;             /* model 1: particles n*Np*5, log-weights n*Np */
 } hyp_t;
 
 typedef struct {
   int T;                      /* slots: the parent's predicted tracks, then births */
   uint32_t *lk, *lb;
   double *m, *P, *p;          /* predicted mean, covariance, prior existence */
+  double *x, *pw;             /* model 1: predicted particles T*Np*5, log-weights T*Np */
   double *S, *L, *logdetS;    /* innovation covariance, its Cholesky factor */
   double *dprob;
   int K;                      /* gated (slot, detection) pairs, CSR by slot */
@@ -228,15 +231,16 @@ struct orc_filter {
   double* kept_logw;
   double lse_all;
   uint16_t* kept_theta;       /* theta of retained children, in their own track indices */
+  double resample_margin;     /* model 1: see orc_resample_margin */
 };
 
 static void free_hyp(hyp_t* h) {
-  free(h->lk); free(h->lb); free(h->m); free(h->P);
+  free(h->lk); free(h->lb); free(h->m); free(h->P); free(h->x); free(h->pw);
   memset(h, 0, sizeof(*h));
 }
 
 static void free_par(par_t* P) {
-  free(P->lk); free(P->lb); free(P->m); free(P->P); free(P->p);
+  free(P->lk); free(P->lb); free(P->m); free(P->P); free(P->p); free(P->x); free(P->pw);
   free(P->S); free(P->L); free(P->logdetS); free(P->dprob);
   free(P->ptr); free(P->meas); free(P->d2); free(P->logC); free(P->q); free(P->e);
   free(P->rptr); free(P->rslot); free(P->rpair);
@@ -290,15 +294,169 @@ static void cv_model(orc_filter* f) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* Particle track densities (model 1; Section 3: each labeled state is a */
+/* set of P weighted particles moved by constant-turn-rate-and-velocity */
+/* kinematics; births are sampled from the birth density; the retained */
+/* tracks get a particle update with resampling).  Reading R15:         */
+/*   a. state (px, py, v, psi, omega); over dt the heading turns by     */
+/*      omega dt and the position moves along the arc; the longitudinal */
+/*      acceleration a and yaw acceleration alpha (per particle, per    */
+/*      frame) add (dt^2/2)(cos psi, sin psi) a, dt a, dt^2/2 alpha and */
+/*      dt alpha to (px, py), v, psi and omega (psi the heading before  */
+/*      the step); a ~ N(0, sigma_a^2), alpha ~ N(0, sigma_w^2).        */
+/*   b. normals: Philox4x32-10 keyed by (seed_lo ^ 0x5851F42D,          */
+/*      seed_hi ^ frame), counter (label_k, label_b, particle,          */
+/*      stream << 24 | call); each call's words (w0..w3) give two       */
+/*      normals, sqrt(-2 ln u(w0)) cos(2 pi u(w1)) and the same of      */
+/*      (w2, w3), with u(w) = (w + 1/2) 2^-32.  Stream 1: the step's    */
+/*      (a, alpha); stream 2: a birth particle's five normals (calls 0  */
+/*      to 2), x = m_B + L xi with L L^T the birth covariance; stream   */
+/*      3: the resampling offset u(w0) of call 0 of particle 0.         */
+/*   c. C entry: P_D sum_p w_p N(z; (px, py)_p, R); gate: the           */
+/*      Mahalanobis test of R1 under the particles' weighted mean and   */
+/*      covariance.                                                     */
+/*   d. weights: the product of the chosen C entries (score_mode 1).    */
+/*   e. update with detections W: log w_p += sum_{z in W}               */
+/*      log N(z; (px, py)_p, R), normalised; when the effective sample  */
+/*      size 1 / sum w_p^2 falls below ess_frac * P, systematic         */
+/*      resampling: target r = (u + r) / P takes the first particle     */
+/*      whose cumulative weight exceeds it (the last when none does);   */
+/*      resampled weights 1/P.  W empty: unchanged.                     */
+/*   f. a track's mean and covariance are the particles' weighted       */
+/*      moments (the gate, the estimates).                              */
+/* ------------------------------------------------------------------ */
+#define PI_D 3.14159265358979323846
+static double quad_Rinv(const orc_filter* f, const double* e);
+#define PKEY_XOR 0x5851F42Du
+
+static double unit_open(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
+
+void orc_particle_normals(const orc_filter* f, uint32_t lk, uint32_t lb, uint32_t p, uint32_t s,
+                          uint32_t j, double out[2]) {
+  uint32_t key[2] = {(uint32_t)f->c.seed ^ PKEY_XOR, (uint32_t)(f->c.seed >> 32) ^ (uint32_t)f->frame};
+  uint32_t ctr[4] = {lk, lb, p, (s << 24) | j};
+  uint32_t w[4];
+  orc_philox(ctr, key, w);
+  out[0] = sqrt(-2.0 * log(unit_open(w[0]))) * cos(2.0 * PI_D * unit_open(w[1]));
+  out[1] = sqrt(-2.0 * log(unit_open(w[2]))) * cos(2.0 * PI_D * unit_open(w[3]));
+}
+
+/* The arc displacement (v / omega)(sin(psi + omega dt) - sin psi,
+ * cos psi - cos(psi + omega dt)) written with the sum-to-product identity,
+ * v dt sinc(omega dt / 2) (cos, sin)(psi + omega dt / 2), which holds at
+ * omega = 0 too (the straight line). */
+void orc_ctrv(const double x[5], double dt, double a, double alpha, double out[5]) {
+  double px = x[0], py = x[1], v = x[2], psi = x[3], om = x[4];
+  double half = 0.5 * om * dt;
+  double sinc = half != 0.0 ? sin(half) / half : 1.0;
+  out[0] = px + v * dt * sinc * cos(psi + half) + 0.5 * dt * dt * cos(psi) * a;
+  out[1] = py + v * dt * sinc * sin(psi + half) + 0.5 * dt * dt * sin(psi) * a;
+  out[2] = v + dt * a;
+  out[3] = psi + om * dt + 0.5 * dt * dt * alpha;
+  out[4] = om + dt * alpha;
+}
+
+/* weighted mean and covariance of Np particles (R15f) */
+static void particle_moments(int Np, const double* x, const double* lw, double* m, double* P) {
+  for (int a = 0; a < 5; ++a) m[a] = 0.0;
+  for (int p = 0; p < Np; ++p) {
+    double w = exp(lw[p]);
+    for (int a = 0; a < 5; ++a) m[a] += w * x[p * 5 + a];
+  }
+  for (int k = 0; k < 25; ++k) P[k] = 0.0;
+  for (int p = 0; p < Np; ++p) {
+    double w = exp(lw[p]);
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) P[a * 5 + b] += w * (x[p * 5 + a] - m[a]) * (x[p * 5 + b] - m[b]);
+  }
+}
+
+/* log N(z; (px, py), R) of a particle */
+static double particle_loglik(const orc_filter* f, const double* xp, const double* z) {
+  double e[2] = {z[0] - xp[0], z[1] - xp[1]};
+  return -0.5 * (quad_Rinv(f, e) + f->logdetR + 2.0 * LOG2PI);
+}
+
+/* log sum_p w_p N(z; (px, py)_p, R) (R15c) */
+static double particle_logL(const orc_filter* f, const double* x, const double* lw, const double* z) {
+  int Np = f->c.n_particles;
+  double mx = -INFINITY, s = 0.0;
+  for (int p = 0; p < Np; ++p) {
+    double l = lw[p] + particle_loglik(f, x + p * 5, z);
+    if (l > mx) mx = l;
+  }
+  if (mx == -INFINITY) return -INFINITY;
+  for (int p = 0; p < Np; ++p) s += exp(lw[p] + particle_loglik(f, x + p * 5, z) - mx);
+  return mx + log(s);
+}
+
+/* Particle update of one track with the detections rows[0..mc) (R15e):
+ * writes x1, lw1 and lowers *margin to the closest resampling decision. */
+static void particle_update(const orc_filter* f, uint32_t lk, uint32_t lb, const double* x0,
+                            const double* lw0, const int* rows, int mc, double* x1, double* lw1,
+                            double* margin) {
+  int Np = f->c.n_particles;
+  double* lw = (double*)malloc(sizeof(double) * Np);
+  double mx = -INFINITY;
+  for (int p = 0; p < Np; ++p) {
+    double l = lw0[p];
+    for (int r = 0; r < mc; ++r) l += particle_loglik(f, x0 + p * 5, f->Z + rows[r] * 2);
+    lw[p] = l;
+    if (l > mx) mx = l;
+  }
+  double s = 0.0;
+  for (int p = 0; p < Np; ++p) s += exp(lw[p] - mx);
+  double lse = mx + log(s), sw2 = 0.0;
+  for (int p = 0; p < Np; ++p) {
+    lw[p] -= lse;
+    sw2 += exp(2.0 * lw[p]);
+  }
+  if (1.0 / sw2 < f->c.ess_frac * Np) {
+    double u[2];
+    uint32_t key[2] = {(uint32_t)f->c.seed ^ PKEY_XOR, (uint32_t)(f->c.seed >> 32) ^ (uint32_t)f->frame};
+    uint32_t ctr[4] = {lk, lb, 0u, 3u << 24};
+    uint32_t w[4];
+    orc_philox(ctr, key, w);
+    u[0] = unit_open(w[0]);
+    int k = 0;
+    double below = 0.0, cum = exp(lw[0]);   /* cumulative weight before and through k */
+    for (int r = 0; r < Np; ++r) {
+      double target = (u[0] + r) / Np;
+      while (k < Np - 1 && cum <= target) {
+        ++k;
+        below = cum;
+        cum += exp(lw[k]);
+      }
+      double d = fabs(cum - target);
+      if (k > 0 && fabs(target - below) < d) d = fabs(target - below);
+      if (d < *margin) *margin = d;
+      memcpy(x1 + r * 5, x0 + k * 5, sizeof(double) * 5);
+      lw1[r] = -log((double)Np);
+    }
+  } else {
+    memcpy(x1, x0, sizeof(double) * 5 * Np);
+    memcpy(lw1, lw, sizeof(double) * Np);
+  }
+  free(lw);
+}
+
 orc_filter* orc_create(const orc_config* cfg) {
   if (!cfg) return NULL;
-  if (!((cfg->dim_x == 4 && cfg->dim_z == 2) || (cfg->dim_x == 6 && cfg->dim_z == 3))) return NULL;
+  if (cfg->model == 1) {
+    if (!(cfg->dim_x == 5 && cfg->dim_z == 2 && cfg->score_mode == 1 && cfg->n_particles >= 1 &&
+          cfg->sigma_a >= 0.0 && cfg->sigma_w >= 0.0 && cfg->ess_frac >= 0.0 && cfg->ess_frac <= 1.0))
+      return NULL;
+  } else if (cfg->model != 0 ||
+             !((cfg->dim_x == 4 && cfg->dim_z == 2) || (cfg->dim_x == 6 && cfg->dim_z == 3))) {
+    return NULL;
+  }
   if (cfg->h_up < 1 || cfg->h_max < 1) return NULL;
   orc_filter* f = (orc_filter*)calloc(1, sizeof(orc_filter));
   f->c = *cfg;
   f->dx = cfg->dim_x;
   f->dz = cfg->dim_z;
-  cv_model(f);
+  if (cfg->model == 0) cv_model(f);
   double Lr[9];
   if (chol(f->dz, cfg->R, Lr) || spd_inverse(f->dz, cfg->R, f->Rinv)) {
     free(f);
@@ -328,6 +486,7 @@ void orc_reset(orc_filter* f) {
   f->hyp[0].uid = orc_mix64(f->c.seed + GOLDEN);
   f->frame = 0;
   f->stage = 0;
+  f->resample_margin = INFINITY;
 }
 
 int orc_import(orc_filter* f, int frame, int H, const double* logw, const uint64_t* uid,
@@ -408,7 +567,45 @@ int orc_predict(orc_filter* f, const orc_birth* births, int n_births) {
   return 0;
 }
 
-static void predict_parent(const orc_filter* f, const hyp_t* y, par_t* P) {
+/* Particle prediction (R15a, b): survivors' particles take one CTRV step
+ * with their own accelerations; a birth's particles are drawn from its
+ * Gaussian; the moments follow (R15f).  Returns 5 when a birth covariance
+ * is not positive definite. */
+static int predict_particles(const orc_filter* f, const hyp_t* y, par_t* P) {
+  int Np = f->c.n_particles, T = P->T;
+  if (y->n > 0 && !y->x) return 5;   /* imported without particles */
+  P->x = (double*)malloc(sizeof(double) * ((size_t)T * Np * 5 + 1));
+  P->pw = (double*)malloc(sizeof(double) * ((size_t)T * Np + 1));
+  for (int t = 0; t < y->n; ++t)
+    for (int p = 0; p < Np; ++p) {
+      double n[2];
+      orc_particle_normals(f, P->lk[t], P->lb[t], (uint32_t)p, 1u, 0u, n);
+      orc_ctrv(y->x + ((size_t)t * Np + p) * 5, f->c.dt, f->c.sigma_a * n[0], f->c.sigma_w * n[1],
+               P->x + ((size_t)t * Np + p) * 5);
+      P->pw[(size_t)t * Np + p] = y->pw[(size_t)t * Np + p];
+    }
+  for (int b = 0; b < f->nb; ++b) {
+    int t = y->n + b;
+    double L[25];
+    if (chol(5, f->births[b].cov, L)) return 5;
+    for (int p = 0; p < Np; ++p) {
+      double xi[6];
+      for (int j = 0; j < 3; ++j) orc_particle_normals(f, P->lk[t], P->lb[t], (uint32_t)p, 2u, (uint32_t)j, xi + 2 * j);
+      double* xp = P->x + ((size_t)t * Np + p) * 5;
+      for (int a = 0; a < 5; ++a) {
+        double v = f->births[b].mean[a];
+        for (int k = 0; k <= a; ++k) v += L[a * 5 + k] * xi[k];
+        xp[a] = v;
+      }
+      P->pw[(size_t)t * Np + p] = -log((double)Np);
+    }
+  }
+  for (int t = 0; t < T; ++t)
+    particle_moments(Np, P->x + (size_t)t * Np * 5, P->pw + (size_t)t * Np, P->m + t * 5, P->P + t * 25);
+  return 0;
+}
+
+static int predict_parent(const orc_filter* f, const hyp_t* y, par_t* P) {
   int dx = f->dx;
   int T = y->n + f->nb;
   P->T = T;
@@ -417,6 +614,19 @@ static void predict_parent(const orc_filter* f, const hyp_t* y, par_t* P) {
   P->m = (double*)calloc(T * dx + 1, sizeof(double));
   P->P = (double*)calloc(T * dx * dx + 1, sizeof(double));
   P->p = (double*)calloc(T + 1, sizeof(double));
+  if (f->c.model == 1) {
+    for (int t = 0; t < y->n; ++t) {
+      P->lk[t] = y->lk[t];
+      P->lb[t] = y->lb[t];
+      P->p[t] = f->c.p_s;
+    }
+    for (int b = 0; b < f->nb; ++b) {
+      P->lk[y->n + b] = (uint32_t)f->frame;
+      P->lb[y->n + b] = (uint32_t)b;
+      P->p[y->n + b] = f->births[b].r;
+    }
+    return predict_particles(f, y, P);
+  }
   for (int t = 0; t < y->n; ++t) {
     const double* m0 = y->m + t * dx;
     const double* P0 = y->P + t * dx * dx;
@@ -452,6 +662,7 @@ static void predict_parent(const orc_filter* f, const hyp_t* y, par_t* P) {
     P->lb[t] = (uint32_t)b;
     P->p[t] = f->births[b].r;
   }
+  return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -598,7 +809,10 @@ static int build_table(const orc_filter* f, par_t* P) {
       if (!pair_gated(f, P, t, e, d2, NULL)) continue;
       P->meas[k] = i;
       P->d2[k] = d2;
-      P->logC[k] = log(f->c.p_d) - 0.5 * (d2 + P->logdetS[t] + dz * LOG2PI);
+      P->logC[k] = f->c.model == 1
+                       ? log(f->c.p_d) + particle_logL(f, P->x + (size_t)t * f->c.n_particles * 5,
+                                                      P->pw + (size_t)t * f->c.n_particles, f->Z + i * dz)
+                       : log(f->c.p_d) - 0.5 * (d2 + P->logdetS[t] + dz * LOG2PI);
       P->q[k] = quad_Rinv(f, e);
       memcpy(P->e + k * dz, e, sizeof(double) * dz);
       ++k;
@@ -654,6 +868,13 @@ static double joint_loglik(const orc_filter* f, const double* Ppred, int m, cons
          - 0.5 * spread - 0.5 * logdet_from_chol(dz, Lm) - 0.5 * mahal(dz, Lm, ebar);
 }
 
+/* the table's log C[i, t] (-inf when the pair is not gated) */
+static double pair_logC(const par_t* P, int t, int i) {
+  for (int j = P->ptr[t]; j < P->ptr[t + 1]; ++j)
+    if (P->meas[j] == i) return P->logC[j];
+  return -INFINITY;
+}
+
 static double child_logw(const orc_filter* f, const par_t* P, double logw_parent,
                          const uint8_t* dead, const uint16_t* theta, int* n_alive_out,
                          int* n_clutter_out) {
@@ -677,7 +898,8 @@ static double child_logw(const orc_filter* f, const par_t* P, double logw_parent
       sum_q += quad_Rinv(f, e);
       /* factorised mode: log C[i, t] of Eq. 2 */
       double d2 = mahal(dz, P->L + t * dz * dz, e);
-      sum_logC += log(f->c.p_d) - 0.5 * (d2 + P->logdetS[t] + dz * LOG2PI);
+      sum_logC += f->c.model == 1 ? pair_logC(P, t, i)
+                                  : log(f->c.p_d) - 0.5 * (d2 + P->logdetS[t] + dz * LOG2PI);
       ++m;
     }
     score += log(P->p[t]);
@@ -837,8 +1059,9 @@ int orc_update(orc_filter* f, const float* Z, int M) {
   (void)nt;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt) reduction(| : err)
   for (int h = 0; h < f->Hold; ++h) {
-    predict_parent(f, &f->old_hyp[h], &f->par[h]);
-    int e = build_table(f, &f->par[h]);
+    int e = predict_parent(f, &f->old_hyp[h], &f->par[h]);
+    if (e) { err |= e; continue; }
+    e = build_table(f, &f->par[h]);
     if (e) { err |= e; continue; }
     sample_children(f, &f->old_hyp[h], &f->par[h]);
   }
@@ -912,6 +1135,7 @@ static int cmp_i64(const void* a, const void* b) {
 
 int orc_prune(orc_filter* f) {
   if (f->stage != 2) return 6;
+  f->resample_margin = INFINITY;
   int HU = f->c.h_up, M = f->M, dx = f->dx;
   double mx = -INFINITY;
   int64_t nu = 0;
@@ -971,6 +1195,11 @@ int orc_prune(orc_filter* f) {
     y->lb = (uint32_t*)malloc(sizeof(uint32_t) * (y->n + 1));
     y->m = (double*)malloc(sizeof(double) * (y->n * dx + 1));
     y->P = (double*)malloc(sizeof(double) * (y->n * dx * dx + 1));
+    const int Np = f->c.n_particles;
+    if (f->c.model == 1) {
+      y->x = (double*)malloc(sizeof(double) * ((size_t)y->n * Np * 5 + 1));
+      y->pw = (double*)malloc(sizeof(double) * ((size_t)y->n * Np + 1));
+    }
     int* newpos = (int*)malloc(sizeof(int) * (T + 1));
     int a = 0;
     for (int t = 0; t < T; ++t) {
@@ -981,7 +1210,18 @@ int orc_prune(orc_filter* f) {
         if (th[i] == t + 1) rows[mc++] = i;
       y->lk[a] = P->lk[t];
       y->lb[a] = P->lb[t];
-      if (mc == 0) {
+      if (f->c.model == 1) {   /* particle update (R15e) and moments (R15f) */
+        double* xa = y->x + (size_t)a * Np * 5;
+        double* wa = y->pw + (size_t)a * Np;
+        if (mc == 0) {
+          memcpy(xa, P->x + (size_t)t * Np * 5, sizeof(double) * 5 * Np);
+          memcpy(wa, P->pw + (size_t)t * Np, sizeof(double) * Np);
+        } else {
+          particle_update(f, P->lk[t], P->lb[t], P->x + (size_t)t * Np * 5, P->pw + (size_t)t * Np, rows, mc,
+                          xa, wa, &f->resample_margin);
+        }
+        particle_moments(Np, xa, wa, y->m + a * dx, y->P + a * dx * dx);
+      } else if (mc == 0) {
         memcpy(y->m + a * dx, P->m + t * dx, sizeof(double) * dx);
         memcpy(y->P + a * dx * dx, P->P + t * dx * dx, sizeof(double) * dx * dx);
       } else if (kalman_multi(f, P->m + t * dx, P->P + t * dx * dx, rows, mc, y->m + a * dx,
@@ -1006,6 +1246,49 @@ int orc_prune(orc_filter* f) {
 /* ------------------------------------------------------------------ */
 /* introspection                                                        */
 /* ------------------------------------------------------------------ */
+int orc_import_particles(orc_filter* f, const double* x, const double* logw) {
+  if (f->c.model != 1) return 1;
+  int Np = f->c.n_particles;
+  size_t off = 0;
+  for (int h = 0; h < f->H; ++h) {
+    hyp_t* y = &f->hyp[h];
+    free(y->x);
+    free(y->pw);
+    y->x = (double*)malloc(sizeof(double) * ((size_t)y->n * Np * 5 + 1));
+    y->pw = (double*)malloc(sizeof(double) * ((size_t)y->n * Np + 1));
+    for (int t = 0; t < y->n; ++t, ++off) {
+      memcpy(y->x + (size_t)t * Np * 5, x + off * Np * 5, sizeof(double) * Np * 5);
+      memcpy(y->pw + (size_t)t * Np, logw + off * Np, sizeof(double) * Np);
+      particle_moments(Np, y->x + (size_t)t * Np * 5, y->pw + (size_t)t * Np, y->m + t * 5, y->P + t * 25);
+    }
+  }
+  return 0;
+}
+
+int orc_export_particles(const orc_filter* f, double* x, double* logw) {
+  if (f->c.model != 1) return 1;
+  int Np = f->c.n_particles;
+  size_t off = 0;
+  for (int h = 0; h < f->H; ++h) {
+    const hyp_t* y = &f->hyp[h];
+    for (int t = 0; t < y->n; ++t, ++off) {
+      memcpy(x + off * Np * 5, y->x + (size_t)t * Np * 5, sizeof(double) * Np * 5);
+      memcpy(logw + off * Np, y->pw + (size_t)t * Np, sizeof(double) * Np);
+    }
+  }
+  return 0;
+}
+
+int orc_slot_particles(const orc_filter* f, int h, int t, double* x, double* logw) {
+  if (f->c.model != 1 || !f->par || h < 0 || h >= f->Hold || t < 0 || t >= f->par[h].T) return 1;
+  int Np = f->c.n_particles;
+  memcpy(x, f->par[h].x + (size_t)t * Np * 5, sizeof(double) * Np * 5);
+  memcpy(logw, f->par[h].pw + (size_t)t * Np, sizeof(double) * Np);
+  return 0;
+}
+
+double orc_resample_margin(const orc_filter* f) { return f->resample_margin; }
+
 int orc_num_parents(const orc_filter* f) { return f->par ? f->Hold : 0; }
 int orc_parent_slots(const orc_filter* f, int h) {
   return (f->par && h >= 0 && h < f->Hold) ? f->par[h].T : -1;
@@ -1034,7 +1317,9 @@ int orc_pair(const orc_filter* f, int h, int t, int i, double* d2, double* logC,
   int dx = f->dx, dz = f->dz;
   innovation(f, P->m + t * dx, f->Z + i * dz, e);
   *d2 = mahal(dz, P->L + t * dz * dz, e);
-  *logC = log(f->c.p_d) - 0.5 * (*d2 + P->logdetS[t] + dz * LOG2PI);
+  *logC = f->c.model == 1 ? log(f->c.p_d) + particle_logL(f, P->x + (size_t)t * f->c.n_particles * 5,
+                                                          P->pw + (size_t)t * f->c.n_particles, f->Z + i * dz)
+                          : log(f->c.p_d) - 0.5 * (*d2 + P->logdetS[t] + dz * LOG2PI);
   *q = quad_Rinv(f, e);
   return pair_gated(f, P, t, e, *d2, NULL);
 }

@@ -28,6 +28,13 @@ typedef struct {
   uint64_t seed;
   int32_t score_mode;            /* 0 joint likelihood, 1 product of C entries */
   int32_t n_threads;             /* OpenMP threads over parents (<=0: 1) */
+  /* track model: 0 Gaussian constant velocity (Kalman), 1 weighted
+   * particles with constant turn rate and velocity (dim_x 5: px, py, v,
+   * heading, turn rate; dim_z 2; score_mode 1) */
+  int32_t model;
+  int32_t n_particles;           /* particles per track (model 1) */
+  double sigma_a, sigma_w;       /* std of the longitudinal and yaw accelerations */
+  double ess_frac;               /* resample when ESS < ess_frac * n_particles */
 } orc_config;
 
 typedef struct {
@@ -95,6 +102,23 @@ int orc_gate_eval(const orc_filter* f, int h, int t, int i, double* feat, double
  * decision is taken in), 0 keeps them in double */
 double orc_mlp_logit(const float* params, const double* feat, int round_act);
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Particle track model (model 1).  Particles of a track are [P][5]
+ * states and [P] normalised log-weights; arrays over tracks follow the
+ * order of orc_import / orc_export. */
+int orc_import_particles(orc_filter* f, const double* x, const double* logw);
+int orc_export_particles(const orc_filter* f, double* x, double* logw);
+/* predicted particles of slot t of parent h of the last update */
+int orc_slot_particles(const orc_filter* f, int h, int t, double* x, double* logw);
+/* smallest distance between a resampling target and a cumulative weight
+ * over the last prune's resamplings (INFINITY when none resampled) */
+double orc_resample_margin(const orc_filter* f);
+/* one CTRV step over dt with accelerations (a, alpha) held over it */
+void orc_ctrv(const double x[5], double dt, double a, double alpha, double out[5]);
+/* the two standard normal draws of particle p of label (lk, lb) in
+ * stream s, call j, for the frame and seed of the filter */
+void orc_particle_normals(const orc_filter* f, uint32_t lk, uint32_t lb, uint32_t p, uint32_t s,
+                          uint32_t j, double out[2]);
 uint64_t orc_mix64(uint64_t x);
 
 #ifdef __cplusplus

@@ -37,6 +37,7 @@ from typing import List, Optional, Tuple
 import numpy as np
 
 __all__ = ["SceneParams", "Scene", "PRESETS", "preset", "make_scene", "batch_scenes", "convoy_scene",
+           "CtrvParams", "ctrv_scene", "ctrv_filter_config",
            "gate_params", "GATE_NPARAM",
            "random_state", "chi2_gate"]
 
@@ -182,6 +183,114 @@ def convoy_scene(n_objects: int, seed: int, steps: int = 548, detections: int = 
             births.append((p.r_false, mean, birth_cov.copy()))
         frames.append(Frame(Z=Z, births=births, truth=truth, truth_ids=np.arange(n_objects)))
     return Scene(params=p, seed=seed, frames=frames)
+
+
+@dataclasses.dataclass(frozen=True)
+class CtrvParams:
+    """Vehicles with constant-turn-rate-and-velocity motion in the plane (the
+    paper's track model, Section 3), seen by the multi-detection sensor of
+    the constant-velocity scenes."""
+    n_objects: int = 20
+    frames: int = 40
+    extent: float = 1000.0      # objects start in [offset, offset + extent]^2
+    offset: float = 200.0       # keeps coordinates far from the origin
+    dt: float = 1.0
+    sigma: float = 3.0          # detection noise std [m]
+    sigma_a: float = 0.5        # longitudinal acceleration std [m/s^2]
+    sigma_w: float = 0.02       # yaw acceleration std [rad/s^2]
+    filter_sigma_w: float = 0.05   # the filter's yaw acceleration std (a looser model)
+    speed: Tuple[float, float] = (5.0, 15.0)
+    turn: float = 0.05          # initial turn rate ~ U(-turn, turn) [rad/s]
+    p_s: float = 0.99
+    p_d: float = 0.9
+    lambda_d: float = 1.0
+    clutter_rate: float = 10.0
+    birth_window: Tuple[int, int] = (0, 19)
+    r_birth: float = 0.5
+    r_false: float = 0.05
+    false_births: float = 1.0
+    h_max: int = 1000
+    h_up: int = 100
+    tau: float = 1e-5
+    n_particles: int = 256
+    ess_frac: float = 0.5
+
+
+def _ctrv_truth_step(x, dt, a, alpha):
+    """World motion (simulation only): one CTRV step with accelerations."""
+    px, py, v, psi, om = x
+    if abs(om) > 1e-12:
+        px2 = px + v / om * (math.sin(psi + om * dt) - math.sin(psi))
+        py2 = py + v / om * (math.cos(psi) - math.cos(psi + om * dt))
+    else:
+        px2 = px + v * math.cos(psi) * dt
+        py2 = py + v * math.sin(psi) * dt
+    return np.array([px2 + 0.5 * dt * dt * math.cos(psi) * a, py2 + 0.5 * dt * dt * math.sin(psi) * a,
+                     v + dt * a, psi + om * dt + 0.5 * dt * dt * alpha, om + dt * alpha])
+
+
+def ctrv_scene(params: CtrvParams, seed: int) -> Scene:
+    """Draw a CTRV scene: truth, detections (as make_scene), clutter over the
+    region and LMB births (one per appearing vehicle: its position plus
+    N(0, (2 sigma)^2), speed 10 +- 5 m/s, its heading plus N(0, 0.3^2), turn
+    rate 0 +- 0.05; and Poisson(false_births) uniform spurious ones).  Frame
+    truth rows are (px, py, v, heading, turn rate)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = params
+    lo, hi = p.birth_window
+    t_birth = sorted(int(rng.integers(lo, hi + 1)) for _ in range(p.n_objects))
+    sb = 2.0 * p.sigma
+    cov = np.diag([sb ** 2, sb ** 2, 5.0 ** 2, 0.3 ** 2, 0.05 ** 2])
+    cov_false = np.diag([sb ** 2, sb ** 2, 5.0 ** 2, 1.5 ** 2, 0.05 ** 2])
+    alive, frames, nxt, ptr = {}, [], 0, 0
+    for f in range(p.frames):
+        for oid in sorted(alive):
+            if rng.uniform() >= p.p_s:
+                del alive[oid]
+                continue
+            alive[oid] = _ctrv_truth_step(alive[oid], p.dt, p.sigma_a * rng.normal(),
+                                          p.sigma_w * rng.normal())
+        births = []
+        while ptr < len(t_birth) and t_birth[ptr] == f:
+            x = np.array([*(p.offset + rng.uniform(0.0, p.extent, 2)), rng.uniform(*p.speed),
+                          rng.uniform(-math.pi, math.pi), rng.uniform(-p.turn, p.turn)])
+            alive[nxt] = x
+            mean = np.array([x[0] + rng.normal(scale=sb), x[1] + rng.normal(scale=sb), 10.0,
+                             x[3] + rng.normal(scale=0.3), 0.0])
+            births.append((p.r_birth, mean, cov.copy()))
+            nxt += 1
+            ptr += 1
+        for _ in range(int(rng.poisson(p.false_births))):
+            mean = np.array([*(p.offset + rng.uniform(0.0, p.extent, 2)), 10.0,
+                             rng.uniform(-math.pi, math.pi), 0.0])
+            births.append((p.r_false, mean, cov_false.copy()))
+        Z = []
+        for oid in sorted(alive):
+            if rng.uniform() < p.p_d:
+                m = 1 + int(rng.poisson(p.lambda_d))
+                Z.append(alive[oid][:2] + p.sigma * rng.normal(size=(m, 2)))
+        nc = int(rng.poisson(p.clutter_rate))
+        if nc:
+            Z.append(p.offset + rng.uniform(0.0, p.extent, size=(nc, 2)))
+        Z = np.concatenate(Z, axis=0) if Z else np.zeros((0, 2))
+        Z = Z[rng.permutation(len(Z))].astype(np.float32)
+        ids = np.array(sorted(alive), dtype=np.int64)
+        truth = np.array([alive[i] for i in ids]) if len(ids) else np.zeros((0, 5))
+        frames.append(Frame(Z=Z, births=births, truth=truth, truth_ids=ids))
+    return Scene(params=p, seed=seed, frames=frames)
+
+
+def ctrv_filter_config(params: CtrvParams, seed: int, **overrides) -> dict:
+    """The particle filter's configuration for a CTRV scene (model 1)."""
+    p = params
+    cfg = dict(dim_x=5, dim_z=2, dt=float(np.float32(p.dt)), q=0.0,
+               R=(p.sigma ** 2 * np.eye(2)).tolist(), p_s=p.p_s, p_d=p.p_d, lambda_d=p.lambda_d,
+               clutter_rate=p.clutter_rate, volume=p.extent ** 2, gate=chi2_gate(2, 1e-4),
+               h_max=p.h_max, h_up=p.h_up, tau=p.tau, seed=(seed ^ 0x5EED) & ((1 << 64) - 1),
+               score_mode=1, model=1, n_particles=p.n_particles, sigma_a=p.sigma_a,
+               sigma_w=p.filter_sigma_w, ess_frac=p.ess_frac)
+    cfg.update(overrides)
+    return cfg
 
 
 def chi2_gate(dim_z: int, tail: float = 1e-4) -> float:
