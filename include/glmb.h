@@ -105,6 +105,27 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  /* Track model (Section 3).  0: Gaussian constant-velocity densities
+   * (Kalman update), the fields above.  1: the paper's weighted particles
+   * with constant-turn-rate-and-velocity motion: dim_x 5 (px, py, speed,
+   * heading, turn rate), dim_z 2 (px, py measured), score_mode 1, no
+   * learned gate; q is unused.  Each component holds n_particles FP64
+   * particles (1..4096); survivors take one CTRV step per frame with
+   * longitudinal and yaw accelerations ~ N(0, sigma_a^2), N(0, sigma_w^2);
+   * births are sampled from their Gaussian (SPD covariance required);
+   * Eq. 2's entry is P_D times the particle mixture likelihood, gated by
+   * the Mahalanobis test under the particles' moments; a retained track
+   * with detections W is reweighted by their likelihoods and resampled
+   * (systematic) when its effective sample size falls below
+   * ess_frac * n_particles.  Random numbers: Philox4x32-10 keyed by
+   * (seed_lo ^ 0x5851F42D, seed_hi ^ frame), counter (label_k, label_b,
+   * particle, stream << 24 | call); Box-Muller normals (streams 1 the
+   * accelerations, 2 the birth draws, 3 the resampling offset).
+   * Device memory: 2 x max_components x n_particles x 48 bytes. */
+  int32_t model;
+  int32_t n_particles;
+  double sigma_a, sigma_w;
+  double ess_frac;
 } glmb_config;
 
 /* An LMB birth component (Section 3): existence r, Gaussian density. */
@@ -224,11 +245,14 @@ glmb_status glmb_meas_assoc(glmb_handle* h, double* r_u, int cap);
 glmb_status glmb_get_info(glmb_handle* h, glmb_info* info);
 
 /* State buffer (host memory), little-endian:
- *   u32 magic 0x424D4C47 ('GLMB'), u32 version 1, i32 dim_x, i32 frame,
- *   i32 n_hyp, i32 pad, i64 n_tracks_total;
+ *   u32 magic 0x424D4C47 ('GLMB'), u32 version (1; 2 with particles),
+ *   i32 dim_x, i32 frame, i32 n_hyp, i32 pad, i64 n_tracks_total;
  *   per hypothesis: f64 logw, u64 uid, i32 n_tracks, i32 pad;
  *   per track (hypotheses in order): u32 label_k, u32 label_b,
- *     f64 mean[dim_x], f64 cov[dim_x * dim_x] (row-major).
+ *     f64 mean[dim_x], f64 cov[dim_x * dim_x] (row-major), and with the
+ *     particle model (version 2) f64 x[n_particles][5], f64
+ *     logw[n_particles] (normalised; the mean and covariance are then
+ *     recomputed from the particles on import).
  * glmb_export_state writes it into buf (cap bytes) and sets *n_out; with
  * buf == NULL it only sets *n_out.  glmb_import_state replaces the filter
  * state; the next call must be glmb_predict.  Log-weights must be

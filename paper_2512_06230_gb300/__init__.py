@@ -40,7 +40,7 @@ _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libglmb.so")
 HEADER = os.path.join(_ROOT, "include", "glmb.h")
 SOURCES = ["kernels_table.cu", "kernels_expand.cu", "kernels_prune.cu", "glmb_api.cu", "gate_mlp.cu",
-           "select_static.cu", "select_cluster.cu"]
+           "select_static.cu", "select_cluster.cu", "kernels_particle.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 
@@ -102,7 +102,9 @@ class GlmbConfig(C.Structure):
                 ("seed", C.c_uint64), ("score_mode", C.c_int32), ("max_tracks", C.c_int32),
                 ("max_meas", C.c_int32), ("max_births", C.c_int32), ("max_pairs", C.c_int64),
                 ("stream", C.c_void_p), ("max_components", C.c_int64),
-                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("model", C.c_int32), ("n_particles", C.c_int32), ("sigma_a", C.c_double),
+                ("sigma_w", C.c_double), ("ess_frac", C.c_double)]
 
 
 class GlmbBirth(C.Structure):
@@ -258,6 +260,11 @@ def make_config(cfg: dict, stream: Optional[int] = None) -> GlmbConfig:
     c.max_pairs = int(cfg.get("max_pairs", 0))
     c.max_components = int(cfg.get("max_components", 0))
     c.stream = stream
+    c.model = int(cfg.get("model", 0))
+    c.n_particles = int(cfg.get("n_particles", 0))
+    c.sigma_a = float(cfg.get("sigma_a", 0.0))
+    c.sigma_w = float(cfg.get("sigma_w", 0.0))
+    c.ess_frac = float(cfg.get("ess_frac", 0.0))
     return c
 
 
@@ -271,23 +278,28 @@ def births_array(births, dim_x: int) -> np.ndarray:
     return arr
 
 
-def pack_state(frame: int, logw, uid, tracks, dim_x: int) -> bytes:
+def pack_state(frame: int, logw, uid, tracks, dim_x: int, n_particles: int = 0) -> bytes:
     """State buffer of include/glmb.h from per-hypothesis track lists of
-    (label_k, label_b, mean, cov)."""
+    (label_k, label_b, mean, cov), with the particle model (label_k,
+    label_b, mean, cov, x[P][5], logw[P]) (version 2)."""
     H = len(logw)
     n = sum(len(t) for t in tracks)
-    out = [struct.pack("<IIiiiiq", 0x424D4C47, 1, dim_x, frame, H, 0, n)]
+    out = [struct.pack("<IIiiiiq", 0x424D4C47, 2 if n_particles else 1, dim_x, frame, H, 0, n)]
     for h in range(H):
         out.append(struct.pack("<dQii", float(logw[h]), int(uid[h]), len(tracks[h]), 0))
     for tr in tracks:
-        for (k, b, m, P) in tr:
+        for rec in tr:
+            k, b, m, P = rec[:4]
             out.append(struct.pack("<II", int(k), int(b)))
             out.append(np.asarray(m, dtype="<f8").reshape(dim_x).tobytes())
             out.append(np.asarray(P, dtype="<f8").reshape(dim_x, dim_x).tobytes())
+            if n_particles:
+                out.append(np.asarray(rec[4], dtype="<f8").reshape(n_particles, 5).tobytes())
+                out.append(np.asarray(rec[5], dtype="<f8").reshape(n_particles).tobytes())
     return b"".join(out)
 
 
-def unpack_state(buf: bytes):
+def unpack_state(buf: bytes, n_particles: int = 0):
     magic, ver, dx, frame, H, _, n = struct.unpack_from("<IIiiiiq", buf, 0)
     off = struct.calcsize("<IIiiiiq")
     logw, uid, ntr = [], [], []
@@ -307,7 +319,14 @@ def unpack_state(buf: bytes):
             off += 8 * dx
             P = np.frombuffer(buf, "<f8", dx * dx, off).reshape(dx, dx).copy()
             off += 8 * dx * dx
-            tr.append((k, b, m, P))
+            if ver == 2:
+                x = np.frombuffer(buf, "<f8", 5 * n_particles, off).reshape(n_particles, 5).copy()
+                off += 40 * n_particles
+                pw = np.frombuffer(buf, "<f8", n_particles, off).copy()
+                off += 8 * n_particles
+                tr.append((k, b, m, P, x, pw))
+            else:
+                tr.append((k, b, m, P))
         tracks.append(tr)
     return frame, np.array(logw), np.array(uid, dtype=np.uint64), tracks
 

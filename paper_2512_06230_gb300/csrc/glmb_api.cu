@@ -49,6 +49,7 @@ struct Plan {
 struct glmb_handle {
   glmb_config cfg{};
   Model md{};
+  PartModel pm{};   // particle track model (md.particle)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
@@ -265,10 +266,12 @@ bool halloc(glmb_handle* h, T** p, long long n) {
 
 bool alloc_comps(glmb_handle* h, CompTable& c, long long cap, int dx) {
   c.cap = (int)cap;
+  c.px = nullptr;
   const int ncov = dx * (dx + 1) / 2;
   return dalloc(h, &c.mhi, cap * dx) && dalloc(h, &c.mlo, cap * dx) &&
          dalloc(h, &c.cov, cap * ncov) && dalloc(h, &c.lk, cap) && dalloc(h, &c.lb, cap) &&
-         dalloc(h, &c.logp, cap) && dalloc(h, &c.log1mp, cap);
+         dalloc(h, &c.logp, cap) && dalloc(h, &c.log1mp, cap) &&
+         (!h->md.particle || dalloc(h, &c.px, cap * 6 * (long long)h->pm.np));
 }
 
 bool alloc_hyps(glmb_handle* h, HypTable& y) {
@@ -510,7 +513,13 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   if (!cfg || !out) return GLMB_E_INVALID;
   *out = nullptr;
   const glmb_config& c = *cfg;
-  if (!((c.dim_x == 4 && c.dim_z == 2) || (c.dim_x == 6 && c.dim_z == 3))) return GLMB_E_INVALID;
+  if (c.model == 1) {
+    if (!(c.dim_x == 5 && c.dim_z == 2 && c.score_mode == 1 && c.n_particles >= 1 && c.n_particles <= 4096 &&
+          c.sigma_a >= 0 && c.sigma_w >= 0 && c.ess_frac >= 0 && c.ess_frac <= 1))
+      return GLMB_E_INVALID;
+  } else if (c.model != 0 || !((c.dim_x == 4 && c.dim_z == 2) || (c.dim_x == 6 && c.dim_z == 3))) {
+    return GLMB_E_INVALID;
+  }
   if (!(c.dt > 0) || !(c.q >= 0) || !(c.p_s >= 0 && c.p_s <= 1) || !(c.p_d >= 0 && c.p_d <= 1) ||
       !(c.lambda_d >= 0) || !(c.clutter_rate >= 0) || !(c.volume > 0) || !(c.gate > 0) ||
       c.h_max < 1 || c.h_up < 1 || c.h_up > 65535 || !(c.tau > 0) || c.score_mode < 0 || c.score_mode > 1)
@@ -580,6 +589,20 @@ glmb_status glmb_create(const glmb_config* cfg, glmb_handle** out) {
   md.log_1mps = c.p_s < 1 ? (float)std::log1p(-c.p_s) : -INFINITY;
   md.seed_lo = (uint32_t)c.seed;
   md.seed_hi = (uint32_t)(c.seed >> 32);
+  md.particle = c.model == 1;
+  if (md.particle) {
+    PartModel& pm = h->pm;
+    pm.np = c.n_particles;
+    pm.dt = (double)c.dt;
+    pm.sigma_a = c.sigma_a;
+    pm.sigma_w = c.sigma_w;
+    pm.ess_frac = c.ess_frac;
+    for (int k = 0; k < 4; ++k) pm.Rinv[k] = Rinv[k];
+    pm.lnorm = 0.5 * ldR + std::log(6.283185307179586476925);
+    pm.log_pd = c.p_d > 0 ? std::log(c.p_d) : -INFINITY;
+    pm.seed_lo = md.seed_lo;
+    pm.seed_hi = md.seed_hi;
+  }
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -701,6 +724,20 @@ glmb_status stage_births(glmb_handle* h, const glmb_birth* births, int n_births)
       if (!std::isfinite(rec[k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
     for (int k = 0; k < dx * dx; ++k)
       if (!std::isfinite(rec[7 + k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
+    if (h->md.particle) {   // the particles are drawn through its Cholesky factor
+      double L[25] = {0};
+      for (int j = 0; j < 5; ++j) {
+        double d = rec[7 + j * 5 + j];
+        for (int k = 0; k < j; ++k) d -= L[j * 5 + k] * L[j * 5 + k];
+        if (!(d > 0)) return fail(h, GLMB_E_INVALID, "predict: birth %d covariance not positive definite", b);
+        L[j * 5 + j] = std::sqrt(d);
+        for (int i = j + 1; i < 5; ++i) {
+          double t = rec[7 + i * 5 + j];
+          for (int k = 0; k < j; ++k) t -= L[i * 5 + k] * L[j * 5 + k];
+          L[i * 5 + j] = t / L[j * 5 + j];
+        }
+      }
+    }
   }
   return GLMB_OK;
 }
@@ -765,7 +802,12 @@ glmb_status enqueue_predict(glmb_handle* h, const Plan& p) {
   const CompTable& B = h->comps[1 - h->cur];
   const int gp = p.fixed ? 2 * h->n_sm : std::max(1, std::min((h->T_work + 127) / 128, 8 * h->n_sm));
   prof_begin(h, kStagePredict);
-  launch_predict(h->md, A, B, h->d_fs, h->d_births, gp, h->stream);
+  if (h->md.particle) {
+    const int gpp = p.fixed ? 4 * h->n_sm : std::max(1, std::min(h->T_work, 4 * h->n_sm));
+    launch_particle_predict(h->md, h->pm, A, B, h->d_fs, h->d_births, h->d_scal + S_ERR, gpp, h->stream);
+  } else {
+    launch_predict(h->md, A, B, h->d_fs, h->d_births, gp, h->stream);
+  }
   prof_end(h, kStagePredict);
   return GLMB_OK;
 }
@@ -786,6 +828,7 @@ glmb_status enqueue_table(glmb_handle* h, const Plan& p) {
            h->scan_cap32, h->d_scal + S_ERR, h->stream);
   launch_table_write(h->md, B, P0, h->d_fs, h->d_scal + S_FP64, h->d_scal + S_ERR, gt,
                      h->stream);
+  if (h->md.particle) launch_particle_logc(h->md, h->pm, B, P0, h->d_fs, gt, h->stream);
   if (h->gate_mode != GLMB_GATE_OFF) {
     launch_gate_forward_table(h->gate_params, h->gate_thr, h->md, B, P0, h->d_fs, h->gate_logit,
                               prune ? h->gate_keep : nullptr, h->d_scal + S_ERR, 2 * h->n_sm, h->stream);
@@ -1011,6 +1054,10 @@ glmb_status enqueue_prune(glmb_handle* h, const Plan& p) {
   scan_u32(h->gc_flag, h->gc_newpos, &h->d_fs->T, 1, capT, h->d_scal + S_NKEEP, false,
            h->scan_tmp32, h->scan_cap32, h->d_scal + S_ERR, s);
   const int ggc = p.fixed ? 4 * h->n_sm : std::max(1, std::min((T + 127) / 128 + 8, 8 * h->n_sm));
+  if (h->md.particle)
+    launch_particle_remap(h->md, h->pm, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP, h->upd_src,
+                          h->upd_m, h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts,
+                          h->d_scal + S_ERR, 4 * h->n_sm, s);
   launch_gc_remap(h->md, B, A, h->gc_newpos, h->gc_flag, h->d_fs, h->d_scal + S_NKEEP, h->upd_src, h->upd_m,
                   h->upd_se, (int)h->cap_upd, h->d_scal + S_NUPD, h->pw.counts, h->d_scal + S_ERR, O.comp,
                   h->pw.counts + 1, h->cap_entries, h->hvals, h->hmask, h->d_hprev, ggc, s);
@@ -1637,7 +1684,8 @@ glmb_status glmb_export_state(glmb_handle* h, void* buf, size_t cap, size_t* n_o
   if (!h || !n_out) return GLMB_E_INVALID;
   if (h->stage != 0) return fail(h, GLMB_E_STATE, "export: frame in progress");
   const int dx = h->md.dx, ncov = h->md.ncov;
-  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx;
+  const int np = h->md.particle ? h->pm.np : 0;
+  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx + 48 * (size_t)np;
   const size_t need = sizeof(StateHeader) + sizeof(HypRec) * h->H + trk * (size_t)h->n_entries;
   *n_out = need;
   if (!buf) return GLMB_OK;
@@ -1663,8 +1711,11 @@ glmb_status glmb_export_state(glmb_handle* h, void* buf, size_t cap, size_t* n_o
     CU(cudaMemcpy(cv.data() + k * nc, A.cov + (size_t)k * A.cap, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(lk.data(), A.lk, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(lb.data(), A.lb, (size_t)h->n_comp * 4, cudaMemcpyDeviceToHost));
+  std::vector<double> px(np ? nc * 6 * (size_t)np : 0);
+  if (np && h->n_comp > 0)
+    CU(cudaMemcpy(px.data(), A.px, (size_t)h->n_comp * 6 * np * 8, cudaMemcpyDeviceToHost));
   unsigned char* p = (unsigned char*)buf;
-  StateHeader hd{0x424D4C47u, 1u, dx, h->frame, h->H, 0, h->n_entries};
+  StateHeader hd{0x424D4C47u, np ? 2u : 1u, dx, h->frame, h->H, 0, h->n_entries};
   std::memcpy(p, &hd, sizeof hd);
   p += sizeof hd;
   for (int y = 0; y < h->H; ++y) {
@@ -1688,6 +1739,15 @@ glmb_status glmb_export_state(glmb_handle* h, void* buf, size_t cap, size_t* n_o
         std::memcpy(p, &v, 8);
         p += 8;
       }
+    for (int q = 0; q < np; ++q)
+      for (int k = 0; k < 5; ++k) {
+        std::memcpy(p, &px[(c * 6 + k) * (size_t)np + q], 8);
+        p += 8;
+      }
+    if (np) {
+      std::memcpy(p, &px[(c * 6 + 5) * (size_t)np], 8 * (size_t)np);
+      p += 8 * (size_t)np;
+    }
   }
   return GLMB_OK;
 }
@@ -1698,12 +1758,13 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
   if (n < sizeof(StateHeader)) return fail(h, GLMB_E_STATE, "import: short buffer");
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof hd);
-  if (hd.magic != 0x424D4C47u || hd.version != 1u || hd.dim_x != dx || hd.n_hyp < 1 ||
+  const int np = h->md.particle ? h->pm.np : 0;
+  if (hd.magic != 0x424D4C47u || hd.version != (np ? 2u : 1u) || hd.dim_x != dx || hd.n_hyp < 1 ||
       hd.n_tracks < 0 || hd.frame < 0)
     return fail(h, GLMB_E_STATE, "import: bad header");
   if (hd.n_hyp > h->cap_h) return fail(h, GLMB_E_CAPACITY, "import: hypotheses exceed h_max");
   if (hd.n_tracks > h->cap_entries) return fail(h, GLMB_E_CAPACITY, "import: entries exceed capacity");
-  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx;
+  const size_t trk = 8 + 8 * (size_t)dx + 8 * (size_t)dx * dx + 48 * (size_t)np;
   const size_t need = sizeof(StateHeader) + sizeof(HypRec) * hd.n_hyp + trk * (size_t)hd.n_tracks;
   if (n < need) return fail(h, GLMB_E_STATE, "import: truncated buffer");
   const unsigned char* p = (const unsigned char*)buf + sizeof hd;
@@ -1726,6 +1787,7 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
   std::vector<uint32_t> comp(std::max<long long>(1, hd.n_tracks));
   std::vector<float> mh, ml, cv;
   std::vector<uint32_t> lk, lb;
+  std::vector<double> px;   // particle model: per component 6 rows of np
   for (long long e = 0; e < hd.n_tracks; ++e) {
     std::string key((const char*)p, trk);
     auto it = seen.find(key);
@@ -1755,8 +1817,41 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
     double P[36];
     std::memcpy(P, p, 8 * dx * dx);
     p += 8 * dx * dx;
-    for (int i = 0; i < dx; ++i)
-      for (int k = i; k < dx; ++k) cv.push_back((float)(0.5 * (P[i * dx + k] + P[k * dx + i])));
+    if (!np) {
+      for (int i = 0; i < dx; ++i)
+        for (int k = i; k < dx; ++k) cv.push_back((float)(0.5 * (P[i * dx + k] + P[k * dx + i])));
+      continue;
+    }
+    // particle model: the particles, and their weighted moments in place of
+    // the record's (mean rounded to FP32 with a zero low part)
+    const size_t base = px.size();
+    px.resize(base + 6 * (size_t)np);
+    for (int q = 0; q < np; ++q)
+      for (int k = 0; k < 5; ++k) {
+        std::memcpy(&px[base + (size_t)k * np + q], p, 8);
+        p += 8;
+      }
+    std::memcpy(&px[base + 5 * (size_t)np], p, 8 * (size_t)np);
+    p += 8 * (size_t)np;
+    double m[5] = {0, 0, 0, 0, 0}, C2[15] = {0};
+    for (int q = 0; q < np; ++q) {
+      const double w = std::exp(px[base + 5 * (size_t)np + q]);
+      if (!std::isfinite(w)) return fail(h, GLMB_E_STATE, "import: particle weight not finite");
+      for (int k = 0; k < 5; ++k) m[k] += w * px[base + (size_t)k * np + q];
+    }
+    for (int q = 0; q < np; ++q) {
+      const double w = std::exp(px[base + 5 * (size_t)np + q]);
+      int k = 0;
+      for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j, ++k)
+          C2[k] += w * (px[base + (size_t)i * np + q] - m[i]) * (px[base + (size_t)j * np + q] - m[j]);
+    }
+    for (int k = 0; k < 5; ++k) {
+      if (!std::isfinite(m[k])) return fail(h, GLMB_E_STATE, "import: particle not finite");
+      mh[mh.size() - 5 + k] = (float)m[k];
+      ml[ml.size() - 5 + k] = 0.f;
+    }
+    for (int k = 0; k < 15; ++k) cv.push_back((float)C2[k]);
   }
   const int nc = (int)lk.size();
   if (nc > h->cap_comp) return fail(h, GLMB_E_CAPACITY, "import: components exceed capacity");
@@ -1776,6 +1871,7 @@ glmb_status glmb_import_state(glmb_handle* h, const void* buf, size_t n) {
     }
     CU(cudaMemcpyAsync(A.lk, lk.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(A.lb, lb.data(), nc * 4, cudaMemcpyHostToDevice, h->stream));
+    if (np) CU(cudaMemcpyAsync(A.px, px.data(), px.size() * 8, cudaMemcpyHostToDevice, h->stream));
   }
   const HypTable& Y = h->hyps[h->hcur];
   CU(cudaMemcpyAsync(Y.ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, h->stream));
@@ -1952,6 +2048,8 @@ glmb_status glmb_get_children(glmb_handle* h, double* logw, int8_t* status, uint
 // ---------------------------------------------------------------------------
 glmb_status glmb_set_gate(glmb_handle* h, const float* params, float threshold, int mode) {
   if (!h) return GLMB_E_INVALID;
+  if (h->md.particle && mode != GLMB_GATE_OFF)
+    return fail(h, GLMB_E_INVALID, "set_gate: the learned gate takes Gaussian features (track model 0)");
   if (mode != GLMB_GATE_OFF && mode != GLMB_GATE_PRUNE && mode != GLMB_GATE_SCORE)
     return fail(h, GLMB_E_INVALID, "set_gate: unknown mode %d", mode);
   if (mode != GLMB_GATE_OFF) {

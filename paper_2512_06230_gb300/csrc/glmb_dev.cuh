@@ -61,6 +61,17 @@ struct Model {
   float log_ps, log_1mps;
   long long fx_log_kappa; // fixed-point log kappa (0 when kappa == 0)
   uint32_t seed_lo, seed_hi;
+  int particle;           // track model: 0 Gaussian (Kalman), 1 weighted particles (CTRV)
+};
+
+// Particle track model (model 1): the constants its kernels use, in FP64.
+struct PartModel {
+  int np;                 // particles per component
+  double dt, sigma_a, sigma_w, ess_frac;
+  double Rinv[4];         // R^-1, 2 x 2 row-major
+  double lnorm;           // (1/2) log det R + log 2 pi
+  double log_pd;
+  uint32_t seed_lo, seed_hi;
 };
 
 // Sizes of the current frame.  Kernels read them from device memory, so a
@@ -85,6 +96,8 @@ struct CompTable {
   float* logp;            // log prior existence
   float* log1mp;          // log(1 - prior existence)
   int cap;
+  double* px;             // particle model: per component 6 rows of np values
+                          // (px, py, v, heading, turn rate, log-weight)
 };
 
 struct PairTable {

@@ -60,6 +60,26 @@ void scan_u64(const unsigned long long* in, unsigned long long* out, const int* 
               long long cap, unsigned long long* total, bool total_at_end,
               unsigned long long* tmp, long long tmp_cap, unsigned* err, cudaStream_t s);
 
+// ---- particle track model (kernels_particle.cu) ----
+// prediction of the working table (one block per component): survivors'
+// particles take a CTRV step, births are sampled from their Gaussian;
+// writes the particles' moments and the labels and existences
+void launch_particle_predict(const Model& md, const PartModel& pm, const CompTable& src, const CompTable& dst,
+                             const FrameDev* fs, const double* births_dev, unsigned* err, int grid, cudaStream_t s);
+// log C of every gated pair from the particles, then the death probability
+// (after launch_table_write, which wrote the pairs)
+void launch_particle_logc(const Model& md, const PartModel& pm, const CompTable& ct, const PairTable& pt,
+                          const FrameDev* fs, int grid, cudaStream_t s);
+// the regeneration's component work: kept components copied to their
+// compacted positions, each distinct update's particle update (with
+// resampling) after them; launch_gc_remap does the index remap
+void launch_particle_remap(const Model& md, const PartModel& pm, const CompTable& src, const CompTable& dst,
+                           const uint32_t* newpos, const uint32_t* flag, const FrameDev* fs,
+                           const unsigned* n_keep_dev, const uint32_t* upd_src, const uint32_t* upd_m,
+                           const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
+                           const unsigned* n_surv_dev, unsigned* err, int grid, cudaStream_t s);
+int particle_remap_smem(int np);
+
 // ---- expansion / materialisation (kernels_expand.cu) ----
 // Test hook of the bounded device-side waits (glmb_set_wait_test): mode 0
 // runs with the normal limits; kWaitTestScan makes the first tile of every

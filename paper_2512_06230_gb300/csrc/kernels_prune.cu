@@ -626,7 +626,8 @@ __global__ void __launch_bounds__(256, DZ == 2 ? 3 : 2) gc_remap_kernel(Model md
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrComps);
     return;
   }
-  const long long total = (long long)n_src + n_upd;
+  // (the particle model's component work is particle_remap_kernel's)
+  const long long total = md.particle ? 0 : (long long)n_src + n_upd;
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
        x += (long long)gridDim.x * blockDim.x) {
     if (x < n_src) {
