@@ -60,7 +60,8 @@ INT_PEAK_NOTE = "152 SMs x 128 lanes x 2070 MHz"
 # measured with the same protocol and reported in the same line.
 DEFAULT_SCENE = "sweep_N200"
 DEFAULT_H_MAX = 20000
-DEFAULT_EXTRA = "sweep_N1000:20000,sweep_N50:1000,mid"
+PARTICLES = 256           # particles per track of the ctrv_N<n> (particle model) cells
+DEFAULT_EXTRA = "sweep_N1000:20000,sweep_N50:1000,mid,ctrv_N200:1000"
 
 
 def expansion_traffic(workload=DEFAULT_SCENE):
@@ -107,6 +108,11 @@ def scene_params(name: str, h_max=None):
     if name.startswith("sweep_N"):
         p = scenes.preset(name, h_max=DEFAULT_H_MAX if h_max is None else h_max)
         return p, 3000 + p.n_objects
+    if name.startswith("ctrv_N"):   # particle track model (CTRV vehicles)
+        n = int(name[len("ctrv_N"):])
+        p = scenes.CtrvParams(name=name, n_objects=n, frames=40, h_max=1000 if h_max is None else h_max,
+                              clutter_rate=0.2 * n, n_particles=PARTICLES)
+        return p, 5000 + n
     p = scenes.preset(name) if h_max is None else scenes.preset(name, h_max=h_max)
     return p, {"tiny": 1000, "mid": 2000}.get(name, 2000)
 
@@ -115,6 +121,8 @@ def window_start(name: str) -> int:
     """First frame of the steady window: after the birth transient."""
     if name.startswith("sweep_N"):
         return 10
+    if name.startswith("ctrv_N"):
+        return 20
     return {"tiny": 25, "mid": 50}.get(name, 0)
 
 
@@ -122,7 +130,10 @@ def scene_for_rank(args, rank, name=None, h_max=None):
     """The scene a rank runs: every rank its own seed (independent scenes)."""
     name = args.scene if name is None else name
     p, base = scene_params(name, getattr(args, "h_max", None) if h_max is None else h_max)
-    return scenes.make_scene(p, base + 7919 * rank if args.seed is None else args.seed + rank)
+    seed = base + 7919 * rank if args.seed is None else args.seed + rank
+    if isinstance(p, scenes.CtrvParams):
+        return scenes.ctrv_scene(p, seed)
+    return scenes.make_scene(p, seed)
 
 
 def filter_cfg(sc):
@@ -216,7 +227,11 @@ def workload_config(args, sc, cfg, w0=None) -> dict:
     F = len(sc.frames)
     w0 = window_start(sc.params.name) if w0 is None else w0
     p = sc.params
-    if p.dim == 3:
+    if isinstance(p, scenes.CtrvParams):
+        shape = (f"{p.name} cell: {p.n_objects} CTRV vehicles, {p.n_particles} FP64 particles per track, "
+                 f"H_max={cfg['h_max']}, clutter Poisson({p.clutter_rate:g}), P_D {p.p_d:g}, "
+                 f"1+Poisson({p.lambda_d:g}) detections")
+    elif p.dim == 3:
         shape = (f"3-D sweep cell N={p.n_objects}, H_max={cfg['h_max']}: CV in [0,{p.extent:g}]^3, "
                  f"clutter Poisson({p.clutter_rate:g}), P_D {p.p_d:g}, 1+Poisson({p.lambda_d:g}) detections")
     else:

@@ -24,7 +24,6 @@ namespace glmb {
 namespace {
 
 constexpr uint32_t kPartKeyXor = 0x5851F42Du;
-constexpr double kTwoPi = 6.283185307179586476925;
 constexpr int kPartThreads = 256;
 
 __device__ __forceinline__ double unit_open(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
@@ -35,9 +34,11 @@ __device__ __forceinline__ uint4 part_words(const PartModel& pm, int frame, uint
                   make_uint2(pm.seed_lo ^ kPartKeyXor, pm.seed_hi ^ (uint32_t)frame));
 }
 
+// cos(2 pi u) as cospi(2 u): 2 u is exact, so no rounded multiple of pi
+// enters the argument
 __device__ __forceinline__ void normal_pair(const uint4& w, double& n0, double& n1) {
-  n0 = sqrt(-2.0 * log(unit_open(w.x))) * cos(kTwoPi * unit_open(w.y));
-  n1 = sqrt(-2.0 * log(unit_open(w.z))) * cos(kTwoPi * unit_open(w.w));
+  n0 = sqrt(-2.0 * log(unit_open(w.x))) * cospi(2.0 * unit_open(w.y));
+  n1 = sqrt(-2.0 * log(unit_open(w.z))) * cospi(2.0 * unit_open(w.w));
 }
 
 // one CTRV step over dt; the arc (v / w)(sin(psi + w dt) - sin psi, ...)
@@ -46,8 +47,11 @@ __device__ __forceinline__ void ctrv(const double (&x)[5], double dt, double a, 
   const double half = 0.5 * x[4] * dt;
   const double sinc = half != 0.0 ? sin(half) / half : 1.0;
   const double vdt = x[2] * dt * sinc;
-  y[0] = x[0] + vdt * cos(x[3] + half) + 0.5 * dt * dt * cos(x[3]) * a;
-  y[1] = x[1] + vdt * sin(x[3] + half) + 0.5 * dt * dt * sin(x[3]) * a;
+  double s0, c0, s1, c1;
+  sincos(x[3], &s0, &c0);
+  sincos(x[3] + half, &s1, &c1);
+  y[0] = x[0] + vdt * c1 + 0.5 * dt * dt * c0 * a;
+  y[1] = x[1] + vdt * s1 + 0.5 * dt * dt * s0 * a;
   y[2] = x[2] + dt * a;
   y[3] = x[3] + x[4] * dt + 0.5 * dt * dt * al;
   y[4] = x[4] + dt * al;
@@ -92,11 +96,11 @@ __device__ double block_max(double v, double* red) {
 }
 
 // weighted mean and covariance of component c's particles into its moment
-// fields (mean rounded to FP32, mlo = 0)
-__device__ void write_moments(const CompTable& ct, int np, int c, double* red) {
+// fields (mean rounded to FP32, mlo = 0); wv holds the particles' weights
+__device__ void write_moments(const CompTable& ct, int np, int c, const double* wv, double* red) {
   double s[5] = {0, 0, 0, 0, 0};
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    const double w = exp(prow(ct, np, c, 5)[p]);
+    const double w = wv[p];
 #pragma unroll
     for (int k = 0; k < 5; ++k) s[k] += w * prow(ct, np, c, k)[p];
   }
@@ -105,7 +109,7 @@ __device__ void write_moments(const CompTable& ct, int np, int c, double* red) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) q[k] = 0.0;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    const double w = exp(prow(ct, np, c, 5)[p]);
+    const double w = wv[p];
     double d[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) d[k] = prow(ct, np, c, k)[p] - s[k];
@@ -126,6 +130,7 @@ __device__ void write_moments(const CompTable& ct, int np, int c, double* red) {
 #pragma unroll
     for (int k = 0; k < 15; ++k) ct.cov[(size_t)k * cap + c] = (float)q[k];
   }
+  __syncthreads();   // wv is reused by the next component
 }
 
 // lower Cholesky factor of a 5 x 5 row-major matrix (its lower triangle);
@@ -156,9 +161,10 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
                                                                         const double* __restrict__ births,
                                                                         unsigned* err) {
   pdl_enter();
+  extern __shared__ double wv[];   // [np] the component's particle weights
   __shared__ double red[(kPartThreads / 32) * 15];
   const int n = fs->n_comp, nb = fs->nb, frame = fs->frame, np = pm.np;
-  const double lw_b = -log((double)np);
+  const double lw_b = -log((double)np), w_b = 1.0 / np;
   for (int c = blockIdx.x; c < n + nb; c += gridDim.x) {
     if (c < n) {
       const uint32_t lk = src.lk[c], lb = src.lb[c];
@@ -170,7 +176,9 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
         ctrv(x, pm.dt, pm.sigma_a * n0, pm.sigma_w * n1, y);
 #pragma unroll
         for (int k = 0; k < 5; ++k) prow(dst, np, c, k)[p] = y[k];
-        prow(dst, np, c, 5)[p] = prow(src, np, c, 5)[p];
+        const double lw = prow(src, np, c, 5)[p];
+        prow(dst, np, c, 5)[p] = lw;
+        wv[p] = exp(lw);
       }
       if (threadIdx.x == 0) {
         dst.lk[c] = lk;
@@ -201,6 +209,7 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
           prow(dst, np, c, a)[p] = v;
         }
         prow(dst, np, c, 5)[p] = lw_b;
+        wv[p] = w_b;
       }
       if (threadIdx.x == 0) {
         const double r = rec[0];
@@ -211,52 +220,72 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
       }
     }
     __syncthreads();
-    write_moments(dst, np, c, red);
+    write_moments(dst, np, c, wv, red);
   }
-}
-
-// log N(z; (px, py), R) of a particle
-__device__ __forceinline__ double part_loglik(const PartModel& pm, double ex, double ey) {
-  return -0.5 * (pm.Rinv[0] * ex * ex + (pm.Rinv[1] + pm.Rinv[2]) * ex * ey + pm.Rinv[3] * ey * ey) - pm.lnorm;
 }
 
 // Compatibility entries: one warp per component, lanes over particles;
 // log C = log P_D + log sum_p w_p N(z; (px, py)_p, R) for each of the
 // component's gated pairs (the table kernels wrote the pairs, gated on
-// the moments); then the death probability from these entries.
+// the moments), then the death probability from these entries.  The
+// offsets run in FP32: a particle's position relative to the component's
+// FP32 mean, (px, py)_p - mhi, is formed once in FP64 and rounded, and a
+// pair's innovation z - mhi is the table's (exact in FP32 when z and mhi
+// are within a factor of two, as for any gated pair away from the
+// origin); z - (px, py)_p is their difference.  The mixture's sum is in
+// FP32 too (log C is stored in FP32).  Particles beyond kRegP per lane
+// are re-read from the particle rows.
+constexpr int kRegP = 8;   // particles held in registers per lane (256 per warp)
+
 __global__ void __launch_bounds__(256) particle_logc_kernel(Model md, PartModel pm, CompTable ct, PairTable pt,
                                                             const FrameDev* fs) {
   pdl_enter();
   const int T = fs->T, np = pm.np, lane = threadIdx.x & 31;
-  const float* __restrict__ Z = fs->Z;
-  if (fs->M > 0 && !__isGlobal(Z)) return;   // flagged by the count kernel
+  if (fs->M > 0 && !__isGlobal(fs->Z)) return;   // flagged by the count kernel
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const unsigned cap_p = (unsigned)min(pt.cap_pairs, (long long)0xFFFFFFFF);
+  const size_t capp = (size_t)pt.cap_pairs;
+  const float r0 = (float)pm.Rinv[0], r1 = (float)(pm.Rinv[1] + pm.Rinv[2]), r3 = (float)pm.Rinv[3];
+  const float lc0 = (float)(pm.log_pd - pm.lnorm);
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < T; c += nwarps) {
     const unsigned k0 = pt.ptr[c], k1 = min(pt.ptr[c + 1], cap_p);
+    const double mx = (double)ct.mhi[c], my = (double)ct.mhi[(size_t)ct.cap + c];
+    float ox[kRegP], oy[kRegP], ow[kRegP];
+#pragma unroll
+    for (int j = 0; j < kRegP; ++j) {
+      const int p = lane + 32 * j;
+      const bool in = p < np;
+      ox[j] = in ? (float)(prow(ct, np, c, 0)[p] - mx) : 0.f;
+      oy[j] = in ? (float)(prow(ct, np, c, 1)[p] - my) : 0.f;
+      ow[j] = in ? (float)prow(ct, np, c, 5)[p] : -INFINITY;
+    }
     float lm = -INFINITY, ls = 0.f;
     bool any = false;
     for (unsigned k = k0; k < k1; ++k) {
-      const int i = (int)pt.meas[k];
-      const double zx = Z[2 * i], zy = Z[2 * i + 1];
-      double m = -INFINITY, s = 0.0;
-      for (int p = lane; p < np; p += 32) {
-        const double l = prow(ct, np, c, 5)[p] + part_loglik(pm, zx - prow(ct, np, c, 0)[p], zy - prow(ct, np, c, 1)[p]);
+      const float ex = pt.e[k], ey = pt.e[capp + k];
+      float m = -INFINITY, s = 0.f;
+      auto push = [&](float dx, float dy, float w) {
+        const float l = w - 0.5f * (r0 * dx * dx + r1 * dx * dy + r3 * dy * dy);
         if (l > m) {
-          s = s * exp(m - l) + 1.0;
+          s = s * expf(m - l) + 1.f;
           m = l;
         } else if (l > -INFINITY) {
-          s += exp(l - m);
+          s += expf(l - m);
         }
-      }
+      };
+#pragma unroll
+      for (int j = 0; j < kRegP; ++j) push(ex - ox[j], ey - oy[j], ow[j]);
+      for (int p = lane + 32 * kRegP; p < np; p += 32)
+        push(ex - (float)(prow(ct, np, c, 0)[p] - mx), ey - (float)(prow(ct, np, c, 1)[p] - my),
+             (float)prow(ct, np, c, 5)[p]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o), s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        const double mm = fmax(m, m2);
-        s = (m == -INFINITY ? 0.0 : s * exp(m - mm)) + (m2 == -INFINITY ? 0.0 : s2 * exp(m2 - mm));
+        const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o), s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        const float mm = fmaxf(m, m2);
+        s = (m == -INFINITY ? 0.f : s * expf(m - mm)) + (m2 == -INFINITY ? 0.f : s2 * expf(m2 - mm));
         m = mm;
       }
-      const float logC = (float)(pm.log_pd + (m == -INFINITY ? -INFINITY : m + log(s)));
+      const float logC = m == -INFINITY ? -INFINITY : lc0 + m + logf(s);
       if (lane == 0) pt.logC[k] = logC;
       any = true;
       if (!md.kappa_zero) lse_push(lm, ls, logC - md.log_kappa);
@@ -333,14 +362,21 @@ __global__ void __launch_bounds__(kPartThreads) particle_remap_kernel(
     }
     mx = block_max(mx, red);
     double sv[1] = {0.0};
-    for (int p = threadIdx.x; p < np; p += blockDim.x) sv[0] += exp(prow(dst, np, d, 5)[p] - mx);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+      const double e = exp(prow(dst, np, d, 5)[p] - mx);
+      cum[p] = e;
+      sv[0] += e;
+    }
     block_sum<1>(sv, red);
-    const double lse = mx + log(sv[0]);
+    const double lse = mx + log(sv[0]), inv = 1.0 / sv[0];
+    // normalised weights cum[p] = exp(l_p - mx) / sum; the log-weights
+    // l_p - lse stay in the destination row
     double s2[1] = {0.0};
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
-      const double l = prow(dst, np, d, 5)[p] - lse;
-      prow(dst, np, d, 5)[p] = l;
-      s2[0] += exp(2.0 * l);
+      prow(dst, np, d, 5)[p] -= lse;
+      const double w = cum[p] * inv;
+      cum[p] = w;
+      s2[0] += w * w;
     }
     block_sum<1>(s2, red);
     if (1.0 / s2[0] < pm.ess_frac * np) {
@@ -349,7 +385,7 @@ __global__ void __launch_bounds__(kPartThreads) particle_remap_kernel(
       const int per = (np + blockDim.x - 1) / blockDim.x, b0 = threadIdx.x * per, b1 = min(np, b0 + per);
       double run = 0.0;
       for (int p = b0; p < b1; ++p) {
-        run += exp(prow(dst, np, d, 5)[p]);
+        run += cum[p];
         cum[p] = run;
       }
       runs[threadIdx.x] = run;
@@ -379,14 +415,17 @@ __global__ void __launch_bounds__(kPartThreads) particle_remap_kernel(
 #pragma unroll
         for (int k = 0; k < 5; ++k) prow(dst, np, d, k)[r] = prow(src, np, c, k)[lo];
       }
-      __syncthreads();   // every weight read before it is overwritten
-      for (int r = threadIdx.x; r < np; r += blockDim.x) prow(dst, np, d, 5)[r] = lw_r;
+      __syncthreads();   // every cumulative weight read before it is overwritten
+      for (int r = threadIdx.x; r < np; r += blockDim.x) {
+        prow(dst, np, d, 5)[r] = lw_r;
+        cum[r] = 1.0 / np;
+      }
     } else {
       for (int k = 0; k < 5; ++k)
         for (int p = threadIdx.x; p < np; p += blockDim.x) prow(dst, np, d, k)[p] = prow(src, np, c, k)[p];
     }
     __syncthreads();
-    write_moments(dst, np, d, red);
+    write_moments(dst, np, d, cum, red);
     if (threadIdx.x == 0) {
       dst.lk[d] = src.lk[c];
       dst.lb[d] = src.lb[c];
@@ -400,7 +439,8 @@ __global__ void __launch_bounds__(kPartThreads) particle_remap_kernel(
 
 void launch_particle_predict(const Model& md, const PartModel& pm, const CompTable& src, const CompTable& dst,
                              const FrameDev* fs, const double* births_dev, unsigned* err, int grid, cudaStream_t s) {
-  launch_k(particle_predict_kernel, grid, kPartThreads, 0, s, md, pm, src, dst, fs, births_dev, err);
+  launch_k(particle_predict_kernel, grid, kPartThreads, (size_t)pm.np * sizeof(double), s, md, pm, src, dst, fs,
+           births_dev, err);
 }
 
 void launch_particle_logc(const Model& md, const PartModel& pm, const CompTable& ct, const PairTable& pt,

@@ -190,6 +190,8 @@ class CtrvParams:
     """Vehicles with constant-turn-rate-and-velocity motion in the plane (the
     paper's track model, Section 3), seen by the multi-detection sensor of
     the constant-velocity scenes."""
+    name: str = "ctrv"
+    dim: int = 2                # the plane; positions are measured
     n_objects: int = 20
     frames: int = 40
     extent: float = 1000.0      # objects start in [offset, offset + extent]^2
@@ -315,7 +317,7 @@ class Scene:
 
     @property
     def dim_x(self) -> int:
-        return 2 * self.params.dim
+        return 5 if isinstance(self.params, CtrvParams) else 2 * self.params.dim
 
     @property
     def dim_z(self) -> int:
@@ -324,6 +326,8 @@ class Scene:
     def filter_config(self, **overrides) -> dict:
         """Model parameters of the world, as the filter's configuration."""
         p = self.params
+        if isinstance(p, CtrvParams):
+            return ctrv_filter_config(p, self.seed, **overrides)
         cfg = dict(dim_x=2 * p.dim, dim_z=p.dim, dt=float(np.float32(p.dt)), q=p.q,
                    R=(p.sigma ** 2 * np.eye(p.dim)).tolist(), p_s=p.p_s, p_d=p.p_d,
                    lambda_d=p.lambda_d,

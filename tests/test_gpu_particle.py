@@ -103,3 +103,44 @@ def test_particle_model_rejects_bad_configurations(glmb):
     bad_birth = [(0.5, np.array([300.0, 300.0, 10.0, 0.0, 0.0]), np.diag([1.0, 1.0, 1.0, 0.0, 1.0]))]
     with pytest.raises(glmb.GlmbError):
         g.predict(bad_birth)
+
+
+def test_ctrv_bench_cell_frame(oracle_mod, glmb):
+    """The benchmark's particle cell (50 CTRV vehicles, 256 particles per
+    track, H_max = 1000, seed 5050) at a steady-window frame, every step
+    compared with the oracle."""
+    p = scenes.CtrvParams(name="ctrv_N50", n_objects=50, frames=40, h_max=1000, clutter_rate=10.0,
+                          n_particles=256)
+    sc = scenes.ctrv_scene(p, 5050)
+    cfg = scenes.ctrv_filter_config(p, 5050, max_tracks=171, max_meas=256, max_births=64)
+    rep = _frame(oracle_mod, glmb, cfg, sc, 21)
+    assert rep.checks["retained"] >= 500 and rep.checks["matched_hypotheses"] >= 400
+    assert rep.excused["children"] <= parity.excused_children_bound(rep, cfg, len(sc.frames[21].Z))
+    assert rep.excused["boundary"] <= 2 + 0.001 * rep.checks["retained"]
+
+
+def test_ctrv_multi_frame_run_tracks_the_oracle(oracle_mod, glmb):
+    """Both filters from the initial GLMB over a whole CTRV scene: identical
+    hypothesis sets in most frames (random draws are keyed by hypothesis uid
+    and track label, so the two stay identical while their retained sets
+    agree), and mean OSPA (order 1, cut-off 50 m, MAP estimates against the
+    truth) within 1 % of the oracle's."""
+    from scenes.metrics import ospa
+    p = scenes.CtrvParams(n_objects=8, frames=25, h_max=100, n_particles=128)
+    sc = scenes.ctrv_scene(p, 505)
+    cfg = _cfg(p, 505)
+    o = oracle_mod.Oracle(cfg, n_threads=8)
+    g = glmb.Filter(cfg)
+    same, oo, og = 0, [], []
+    for fr in sc.frames:
+        o.step(fr.births, fr.Z)
+        g.step(fr.births, fr.Z)
+        same += set(o.export_state()[2].tolist()) == set(g.hypotheses()["uid"].tolist())
+        oo.append(ospa(o.estimates()["mean"][:, :2], fr.truth[:, :2], c=50.0, p=1.0))
+        og.append(ospa(g.estimates()["mean"][:, :2], fr.truth[:, :2], c=50.0, p=1.0))
+    g.close()
+    oo, og = np.array(oo), np.array(og)
+    print(f"\nframes with identical hypothesis sets {same}/{len(sc.frames)}; mean OSPA oracle "
+          f"{oo.mean():.4f} m, GPU {og.mean():.4f} m")
+    assert same >= len(sc.frames) // 2
+    assert abs(og.mean() - oo.mean()) <= 0.01 * oo.mean()
