@@ -579,15 +579,16 @@ def run_convoy(args, glmb, torch):
     """Section 4.1's scalability grid on the convoy workload: N copies of one
     closed track (offset delta = 2 steps), five detections per object, no
     clutter, 548 steps of 0.1 s; N x H_max over --convoy-n x --convoy-h,
-    for each score mode in --convoy-modes (0 the joint multi-detection
-    likelihood, 1 the product of C entries), --runs seeds each.  One update
+    for each mode in --convoy-modes (0 the joint multi-detection
+    likelihood, 1 the product of C entries, 2 the paper's particle (CTRV)
+    track model with --particles particles per track), --runs seeds each.  One update
     is glmb_step with the frame's detections in host memory plus the
     estimates read back (host wall clock, as the paper times an update);
     one untimed pass per filter first fills its graph cache.  Accuracy is
     the paper's: relative cardinality error and the Hungarian-matched mean
     distance, averaged over the steps of a run.  --convoy-oracle-steps
     steps of the FP64 oracle (single thread) are timed per (N, H_max) of
-    mode 0 beside it."""
+    modes 0 and 2 beside it."""
     from scenes.metrics import RunAccuracy
     import oracle
     steps = args.convoy_steps
@@ -598,8 +599,9 @@ def run_convoy(args, glmb, torch):
                 upd, acc_runs = [], []
                 for r in range(args.runs):
                     seed = (0 if args.seed is None else args.seed) + 1000 * r + N
-                    sc = scenes.convoy_scene(N, seed, steps=steps, h_max=H)
-                    cfg = sc.filter_config(score_mode=mode)
+                    sc = scenes.convoy_scene(N, seed, steps=steps, h_max=H,
+                                             particles=args.particles if mode == 2 else 0)
+                    cfg = sc.filter_config() if mode == 2 else sc.filter_config(score_mode=mode)
                     f = glmb.Filter(cfg)
                     B = [glmb.births_array(fr.births, sc.dim_x) for fr in sc.frames]
                     for k, fr in enumerate(sc.frames):            # untimed: graph captures
@@ -621,9 +623,9 @@ def run_convoy(args, glmb, torch):
                            update_ms_sem=(statistics.stdev(upd) / math.sqrt(len(upd)) if len(upd) > 1 else 0.0),
                            rel_card_error=statistics.fmean(a["rel_card_error"] for a in acc_runs),
                            tracking_error_m=statistics.fmean(a["tracking_error_m"] for a in acc_runs))
-                if mode == 0 and args.convoy_oracle_steps > 0:
+                if mode in (0, 2) and args.convoy_oracle_steps > 0:
                     sc = scenes.convoy_scene(N, 0 if args.seed is None else args.seed, steps=args.convoy_oracle_steps,
-                                             h_max=H)
+                                             h_max=H, particles=args.particles if mode == 2 else 0)
                     o = oracle.Oracle(sc.filter_config())
                     t0 = time.perf_counter()
                     for fr in sc.frames:
@@ -636,7 +638,8 @@ def run_convoy(args, glmb, torch):
     print(json.dumps({"metric": "convoy update time and accuracy (Section 4.1 grid, 1 GB300)",
                       "unit": "ms/update", "higher_is_better": False, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"convoy, D=5, lambda=0, sigma=0.25, delta=2, H_up=100, "
-                                             f"tau=1e-5, {steps} steps of 0.1 s",
+                                             f"tau=1e-5, {steps} steps of 0.1 s; mode 2: {args.particles} "
+                                             f"FP64 particles per track",
                                  "update": "glmb_step, host detections + estimates read back"},
                       "grid": grid}))
 
@@ -981,7 +984,11 @@ def main():
                     help="--scene batch: independent scenes per frame")
     ap.add_argument("--convoy-n", default="1,2,5,10,20", help="--scene convoy: object counts")
     ap.add_argument("--convoy-h", default="5,10,25,50,100", help="--scene convoy: H_max values")
-    ap.add_argument("--convoy-modes", default="0,1", help="--scene convoy: score modes")
+    ap.add_argument("--convoy-modes", default="0,1",
+                    help="--scene convoy: 0 Gaussian tracks, joint likelihood; 1 Gaussian tracks, product of "
+                         "C entries; 2 the particle (CTRV) track model, product of C entries")
+    ap.add_argument("--particles", type=int, default=PARTICLES,
+                    help="particles per track of the particle track model (--scene convoy mode 2)")
     ap.add_argument("--convoy-steps", type=int, default=548)
     ap.add_argument("--convoy-oracle-steps", type=int, default=20)
     ap.add_argument("--runs", type=int, default=3, help="--scene convoy: seeds per configuration")
