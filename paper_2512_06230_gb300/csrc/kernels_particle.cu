@@ -42,14 +42,27 @@ __device__ __forceinline__ void normal_pair(const uint4& w, double& n0, double& 
 }
 
 // one CTRV step over dt; the arc (v / w)(sin(psi + w dt) - sin psi, ...)
-// as v dt sinc(w dt / 2)(cos, sin)(psi + w dt / 2), valid at w = 0
+// as v dt sinc(h)(cos, sin)(psi + h), h = w dt / 2, valid at w = 0.  The
+// half-angle terms sin h, cos h and sinc h come from their Taylor series
+// when |h| < 0.03 (the first omitted terms, h^8 / 9! and h^8 / 8!, are
+// below 1e-16 of the sums) and (cos, sin)(psi + h) from the angle sum, so
+// a particle takes one sincos instead of three transcendental calls.
 __device__ __forceinline__ void ctrv(const double (&x)[5], double dt, double a, double al, double (&y)[5]) {
-  const double half = 0.5 * x[4] * dt;
-  const double sinc = half != 0.0 ? sin(half) / half : 1.0;
+  const double h = 0.5 * x[4] * dt;
+  double sh, ch, sinc;
+  if (fabs(h) < 0.03) {
+    const double h2 = h * h;
+    sinc = 1.0 - h2 / 6.0 * (1.0 - h2 / 20.0 * (1.0 - h2 / 42.0));
+    sh = h * sinc;
+    ch = 1.0 - 0.5 * h2 * (1.0 - h2 / 12.0 * (1.0 - h2 / 30.0));
+  } else {
+    sincos(h, &sh, &ch);
+    sinc = sh / h;
+  }
   const double vdt = x[2] * dt * sinc;
-  double s0, c0, s1, c1;
+  double s0, c0;
   sincos(x[3], &s0, &c0);
-  sincos(x[3] + half, &s1, &c1);
+  const double s1 = s0 * ch + c0 * sh, c1 = c0 * ch - s0 * sh;
   y[0] = x[0] + vdt * c1 + 0.5 * dt * dt * c0 * a;
   y[1] = x[1] + vdt * s1 + 0.5 * dt * dt * s0 * a;
   y[2] = x[2] + dt * a;

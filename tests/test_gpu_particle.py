@@ -52,10 +52,11 @@ def test_ctrv_scene_frame(oracle_mod, glmb, k):
         assert "particle_x_rel" in rep.max_err or rep.excused.get("resample_near_tie")
 
 
-@pytest.mark.parametrize("np_,ess", [(32, 1.0), (300, 0.0), (1024, 0.5)])
+@pytest.mark.parametrize("np_,ess", [(1, 0.5), (32, 1.0), (300, 0.0), (1024, 0.5), (4096, 0.5)])
 def test_particle_counts_and_resampling_rules(oracle_mod, glmb, np_, ess):
-    """Particle counts that are not a multiple of the block, one particle
-    per thread and several, resampling always (ess_frac 1) and never (0)."""
+    """A single particle (a point mass), particle counts that are not a
+    multiple of the block, one particle per thread and several, the largest
+    count (4096), resampling always (ess_frac 1) and never (0)."""
     p = scenes.CtrvParams(n_objects=5, frames=12, h_max=100, n_particles=np_, ess_frac=ess)
     sc = scenes.ctrv_scene(p, 502)
     _frame(oracle_mod, glmb, _cfg(p, 502), sc, 8)
