@@ -350,7 +350,7 @@ def rooflines(steps, peaks, workload=DEFAULT_SCENE):
     Expansion: 25 int32 lane operations per uniform (one Philox4x32-10 call
     of about 100 operations gives four uniforms), one uniform per slot and
     per detection row of every child drawn, against 152 SMs x 128 lanes x
-    2070 MHz.  Selection: the algorithmic bytes of the survey's a6+a7 row,
+    2070 MHz.  Selection: the algorithmic bytes of normalisation and top-H,
     8 B per child key per pass over two passes plus 16 B per retained
     hypothesis written, against the measured HBM copy bandwidth."""
     peak_ops = 152 * 128 * 2070e6
@@ -450,7 +450,7 @@ def run_batch(args, glmb, torch, dev):
 
 
 def run_target(args, glmb, torch, dev):
-    """The benchmark spec's comparison: the batched form with the learned gate
+    """The target comparison: the batched form with the learned gate
     against the plain single-scene form, on the same scenes and GPU.
     Scenes: --scenes held-out scenes of the batched workload's distribution
     (2-D, N ~ U{5..--target-nmax}, H ~ U{100..5000}, clutter ~ U(5, 40)),
@@ -938,7 +938,7 @@ def peaks_file():
 
 def oracle_error(oracle_state, glmb, sc, cfg, k):
     """Error of the library against the FP64 oracle for every output of one
-    frame of the timed workload (the benchmark spec's per-output error report): both
+    frame of the timed workload (the per-output error report): both
     import the oracle's own state before frame k and run frame k; the
     step-by-step comparison of the parity tests gives the largest error of
     each output and the decisions it excused."""
