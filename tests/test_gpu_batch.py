@@ -46,6 +46,60 @@ def test_batch_equals_scenes_alone(glmb):
             assert np.array_equal(ea["r"], eb["r"]) and np.array_equal(ea["mean"], eb["mean"])
 
 
+def test_batch_workload_at_full_size_equals_scenes_alone(glmb):
+    """The batched workload at its full size: 256 scenes (N ~ U{5..300},
+    H_max ~ U{100..5000}, clutter ~ U(5, 40)), detections resident in device
+    memory, frames 0-11 stepped together and one by one: every scene's
+    retained set, weights and state are identical."""
+    import torch
+    specs = scenes.batch_scenes(256, seed=4000, frames=12)
+    scs = [scenes.make_scene(p, s) for p, s in specs]
+    cfgs = [sc.filter_config(max_meas=int(p.n_objects * 0.9 * 6 + 4 * p.clutter_rate + 64), max_births=64,
+                             max_tracks=p.n_objects + 48, max_components=400 * (p.n_objects + 48),
+                             max_pairs=1 << 20) for (p, _), sc in zip(specs, scs)]
+    Zd = [[torch.from_numpy(fr.Z).cuda() if len(fr.Z) else torch.zeros((0, 2), device="cuda")
+           for fr in sc.frames] for sc in scs]
+    alone = [glmb.Filter(c) for c in cfgs]
+    batch = [glmb.Filter(c) for c in cfgs]
+    try:
+        for k in range(12):
+            for f, sc, z in zip(alone, scs, Zd):
+                f.step(sc.frames[k].births, z[k], device=True)
+            glmb.step_batch(batch, [(sc.frames[k].births, z[k]) for sc, z in zip(scs, Zd)], device=True)
+            for j, (a, b) in enumerate(zip(alone, batch)):
+                ia, la = a.retained()
+                ib, lb = b.retained()
+                assert np.array_equal(ia, ib) and np.array_equal(la, lb), (k, j)
+        for a, b in zip(alone, batch):
+            assert a.export_state() == b.export_state()
+    finally:
+        for f in alone + batch:
+            f.close()
+
+
+def test_particle_scenes_batched_equal_alone(glmb):
+    """The particle track model in the batched form: uneven CTRV scenes
+    (4-12 vehicles, 32-256 particles per track) stepped together give each
+    scene exactly its own results, particles included."""
+    scs, cfgs = [], []
+    for j, (n, npart) in enumerate(((4, 32), (8, 256), (12, 100), (6, 64))):
+        p = scenes.CtrvParams(n_objects=n, frames=8, h_max=60 + 40 * j, n_particles=npart)
+        scs.append(scenes.ctrv_scene(p, 600 + j))
+        cfgs.append(scenes.ctrv_filter_config(p, 600 + j, max_tracks=64, max_meas=256, max_births=32,
+                                              max_components=8000))
+    alone = [glmb.Filter(c) for c in cfgs]
+    batch = [glmb.Filter(c) for c in cfgs]
+    for k in range(8):
+        for f, sc in zip(alone, scs):
+            f.step(sc.frames[k].births, sc.frames[k].Z)
+        glmb.step_batch(batch, [(sc.frames[k].births, sc.frames[k].Z) for sc in scs])
+        for a, b in zip(alone, batch):
+            ia, la = a.retained()
+            ib, lb = b.retained()
+            assert np.array_equal(ia, ib) and np.array_equal(la, lb), k
+            assert a.export_state() == b.export_state(), k
+
+
 def test_tuning_does_not_change_results(glmb):
     sc = scenes.make_scene(scenes.preset("mid"), 21)
     cfg = sc.filter_config(max_meas=400, max_births=16, max_tracks=300)
