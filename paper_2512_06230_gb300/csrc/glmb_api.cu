@@ -19,7 +19,6 @@ using namespace glmb;
 namespace {
 
 constexpr unsigned long long kGolden = 0x9E3779B97F4A7C15ULL;
-constexpr int kBirthRec = 43;  // r, mean[6], cov[36]
 
 // stages timed by glmb_set_profiling
 enum { kStagePredict = 0, kStageTable, kStageExpand, kStageSelect, kStageMat, kStageGc,
@@ -724,6 +723,7 @@ glmb_status stage_births(glmb_handle* h, const glmb_birth* births, int n_births)
       if (!std::isfinite(rec[k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
     for (int k = 0; k < dx * dx; ++k)
       if (!std::isfinite(rec[7 + k])) return fail(h, GLMB_E_INVALID, "predict: birth %d not finite", b);
+    for (int k = kBirthChol; k < kBirthRec; ++k) rec[k] = 0.0;
     if (h->md.particle) {   // the particles are drawn through its Cholesky factor
       double L[25] = {0};
       for (int j = 0; j < 5; ++j) {
@@ -737,6 +737,8 @@ glmb_status stage_births(glmb_handle* h, const glmb_birth* births, int n_births)
           L[i * 5 + j] = t / L[j * 5 + j];
         }
       }
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) rec[kBirthChol + i * (i + 1) / 2 + j] = L[i * 5 + j];
     }
   }
   return GLMB_OK;
@@ -803,8 +805,8 @@ glmb_status enqueue_predict(glmb_handle* h, const Plan& p) {
   const int gp = p.fixed ? 2 * h->n_sm : std::max(1, std::min((h->T_work + 127) / 128, 8 * h->n_sm));
   prof_begin(h, kStagePredict);
   if (h->md.particle) {
-    const int gpp = p.fixed ? 4 * h->n_sm : std::max(1, std::min(h->T_work, 4 * h->n_sm));
-    launch_particle_predict(h->md, h->pm, A, B, h->d_fs, h->d_births, h->d_scal + S_ERR, gpp, h->stream);
+    const int gpp = 4 * h->n_sm;
+    launch_particle_predict(h->md, h->pm, A, B, h->d_fs, h->d_births, gpp, h->stream);
   } else {
     launch_predict(h->md, A, B, h->d_fs, h->d_births, gp, h->stream);
   }

@@ -60,12 +60,20 @@ void scan_u64(const unsigned long long* in, unsigned long long* out, const int* 
               long long cap, unsigned long long* total, bool total_at_end,
               unsigned long long* tmp, long long tmp_cap, unsigned* err, cudaStream_t s);
 
+// A birth record on the device (FP64): r, mean[6], cov[36] (dim_x x dim_x
+// row-major), and for the particle model the lower Cholesky factor of the
+// 5 x 5 covariance, packed row-major, at kBirthChol (computed by the host,
+// which refuses a covariance that is not positive definite).
+constexpr int kBirthChol = 43;
+constexpr int kBirthRec = 58;
+
 // ---- particle track model (kernels_particle.cu) ----
-// prediction of the working table (one block per component): survivors'
-// particles take a CTRV step, births are sampled from their Gaussian;
-// writes the particles' moments and the labels and existences
+// prediction of the working table: survivors' particles take a CTRV step,
+// births are sampled from their Gaussian (a flat grid over components x
+// particles), then the particles' moments (one warp per component); also
+// writes the labels and existences
 void launch_particle_predict(const Model& md, const PartModel& pm, const CompTable& src, const CompTable& dst,
-                             const FrameDev* fs, const double* births_dev, unsigned* err, int grid, cudaStream_t s);
+                             const FrameDev* fs, const double* births_dev, int grid, cudaStream_t s);
 // log C of every gated pair from the particles, then the death probability
 // (after launch_table_write, which wrote the pairs)
 void launch_particle_logc(const Model& md, const PartModel& pm, const CompTable& ct, const PairTable& pt,

@@ -146,54 +146,33 @@ __device__ void write_moments(const CompTable& ct, int np, int c, const double* 
   __syncthreads();   // wv is reused by the next component
 }
 
-// lower Cholesky factor of a 5 x 5 row-major matrix (its lower triangle);
-// false when a pivot is not positive
-__device__ bool chol5(const double* A, double (&L)[5][5]) {
-#pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    double s = A[j * 5 + j];
-    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-    if (!(s > 0.0)) return false;
-    const double d = sqrt(s);
-    L[j][j] = d;
-    for (int i = j + 1; i < 5; ++i) {
-      double t = A[i * 5 + j];
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / d;
-    }
-    for (int i = 0; i < j; ++i) L[i][j] = 0.0;
-  }
-  return true;
-}
-
-// Prediction: one block per component of the working table.  Survivor c
-// takes one CTRV step per particle with its own accelerations; birth b
-// draws its particles from N(m_B, L L^T) with weights 1/P.
-__global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md, PartModel pm, CompTable src,
-                                                                        CompTable dst, const FrameDev* fs,
-                                                                        const double* __restrict__ births,
-                                                                        unsigned* err) {
+// Prediction, particle by particle (a flat grid over the working table's
+// components x particles, so that the FP64 work of one component runs on
+// into the next without a barrier): a survivor's particle takes one CTRV
+// step with its own accelerations; a birth's particle is drawn through the
+// Cholesky factor that the host stored with the birth.  Particle 0 of each
+// component writes its label and existence.
+__global__ void __launch_bounds__(kPartThreads) particle_step_kernel(Model md, PartModel pm, CompTable src,
+                                                                     CompTable dst, const FrameDev* fs,
+                                                                     const double* __restrict__ births) {
   pdl_enter();
-  extern __shared__ double wv[];   // [np] the component's particle weights
-  __shared__ double red[(kPartThreads / 32) * 15];
   const int n = fs->n_comp, nb = fs->nb, frame = fs->frame, np = pm.np;
-  const double lw_b = -log((double)np), w_b = 1.0 / np;
-  for (int c = blockIdx.x; c < n + nb; c += gridDim.x) {
+  const long long total = (long long)(n + nb) * np;
+  const double lw_b = -log((double)np);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / np), p = (int)(i - (long long)c * np);
     if (c < n) {
       const uint32_t lk = src.lk[c], lb = src.lb[c];
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        double x[5], y[5], n0, n1;
+      double x[5], y[5], n0, n1;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) x[k] = prow(src, np, c, k)[p];
-        normal_pair(part_words(pm, frame, lk, lb, (uint32_t)p, 1u, 0u), n0, n1);
-        ctrv(x, pm.dt, pm.sigma_a * n0, pm.sigma_w * n1, y);
+      for (int k = 0; k < 5; ++k) x[k] = prow(src, np, c, k)[p];
+      normal_pair(part_words(pm, frame, lk, lb, (uint32_t)p, 1u, 0u), n0, n1);
+      ctrv(x, pm.dt, pm.sigma_a * n0, pm.sigma_w * n1, y);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) prow(dst, np, c, k)[p] = y[k];
-        const double lw = prow(src, np, c, 5)[p];
-        prow(dst, np, c, 5)[p] = lw;
-        wv[p] = exp(lw);
-      }
-      if (threadIdx.x == 0) {
+      for (int k = 0; k < 5; ++k) prow(dst, np, c, k)[p] = y[k];
+      prow(dst, np, c, 5)[p] = prow(src, np, c, 5)[p];
+      if (p == 0) {
         dst.lk[c] = lk;
         dst.lb[c] = lb;
         dst.logp[c] = md.log_ps;
@@ -201,30 +180,22 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
       }
     } else {
       const int b = c - n;
-      const double* rec = births + (size_t)b * 43;
-      double L[5][5];
-      if (!chol5(rec + 7, L)) {   // the host checks the births: not reached
-        if (threadIdx.x == 0) atomicOr(err, kErrNumeric);
-        for (int i = 0; i < 5; ++i)
-          for (int j = 0; j < 5; ++j) L[i][j] = 0.0;
+      const double* rec = births + (size_t)b * kBirthRec;
+      const double* L = rec + kBirthChol;   // lower triangle, row-major
+      double xi[6];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        normal_pair(part_words(pm, frame, (uint32_t)frame, (uint32_t)b, (uint32_t)p, 2u, (uint32_t)j), xi[2 * j],
+                    xi[2 * j + 1]);
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        double v = rec[1 + a];
+#pragma unroll
+        for (int k = 0; k <= a; ++k) v += L[a * (a + 1) / 2 + k] * xi[k];
+        prow(dst, np, c, a)[p] = v;
       }
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        double xi[6];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          normal_pair(part_words(pm, frame, (uint32_t)frame, (uint32_t)b, (uint32_t)p, 2u, (uint32_t)j), xi[2 * j],
-                      xi[2 * j + 1]);
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
-          double v = rec[1 + a];
-#pragma unroll
-          for (int k = 0; k <= a; ++k) v += L[a][k] * xi[k];
-          prow(dst, np, c, a)[p] = v;
-        }
-        prow(dst, np, c, 5)[p] = lw_b;
-        wv[p] = w_b;
-      }
-      if (threadIdx.x == 0) {
+      prow(dst, np, c, 5)[p] = lw_b;
+      if (p == 0) {
         const double r = rec[0];
         dst.lk[c] = (uint32_t)frame;
         dst.lb[c] = (uint32_t)b;
@@ -232,8 +203,64 @@ __global__ void __launch_bounds__(kPartThreads) particle_predict_kernel(Model md
         dst.log1mp[c] = r < 1.0 ? (float)log1p(-r) : -INFINITY;
       }
     }
+  }
+}
+
+// The working table's moments: one block of 64 threads per component,
+// threads over its particles, one pass with offsets from its particle 0, d_p = x_p - x_0:
+// mean = x_0 + sum w d, covariance = sum w d d^T - (sum w d)(sum w d)^T
+// (the weights sum to one), mean rounded to FP32 with a zero low part.
+__global__ void __launch_bounds__(kPartThreads) particle_moments_kernel(PartModel pm, CompTable ct,
+                                                                       const FrameDev* fs) {
+  pdl_enter();
+  __shared__ double part[kPartThreads / 32][20];
+  const int T = fs->T, np = pm.np, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = blockIdx.x; c < T; c += gridDim.x) {
+    double x0[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) x0[k] = prow(ct, np, c, k)[0];
+    double v[20];   // sum w d (5), sum w d d^T (15, packed)
+#pragma unroll
+    for (int k = 0; k < 20; ++k) v[k] = 0.0;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+      const double w = exp(prow(ct, np, c, 5)[p]);
+      double d[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        d[k] = prow(ct, np, c, k)[p] - x0[k];
+        v[k] += w * d[k];
+      }
+      int k = 5;
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i; j < 5; ++j, ++k) v[k] += w * d[i] * d[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 20; ++k) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 20; ++k) part[wid][k] = v[k];
     __syncthreads();
-    write_moments(dst, np, c, wv, red);
+    if (threadIdx.x == 0) {
+      const int nw = blockDim.x >> 5;
+      double t[20];
+      for (int k = 0; k < 20; ++k) {
+        t[k] = 0.0;
+        for (int i = 0; i < nw; ++i) t[k] += part[i][k];
+      }
+      const size_t cap = ct.cap;
+      for (int k = 0; k < 5; ++k) {
+        ct.mhi[k * cap + c] = (float)(x0[k] + t[k]);
+        ct.mlo[k * cap + c] = 0.f;
+      }
+      int k = 0;
+      for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j, ++k) ct.cov[(size_t)k * cap + c] = (float)(t[5 + k] - t[i] * t[j]);
+    }
+    __syncthreads();
   }
 }
 
@@ -451,9 +478,9 @@ __global__ void __launch_bounds__(kPartThreads) particle_remap_kernel(
 }  // namespace
 
 void launch_particle_predict(const Model& md, const PartModel& pm, const CompTable& src, const CompTable& dst,
-                             const FrameDev* fs, const double* births_dev, unsigned* err, int grid, cudaStream_t s) {
-  launch_k(particle_predict_kernel, grid, kPartThreads, (size_t)pm.np * sizeof(double), s, md, pm, src, dst, fs,
-           births_dev, err);
+                             const FrameDev* fs, const double* births_dev, int grid, cudaStream_t s) {
+  launch_k(particle_step_kernel, grid, kPartThreads, 0, s, md, pm, src, dst, fs, births_dev);
+  launch_k(particle_moments_kernel, 4 * grid, 64, 0, s, pm, dst, fs);
 }
 
 void launch_particle_logc(const Model& md, const PartModel& pm, const CompTable& ct, const PairTable& pt,

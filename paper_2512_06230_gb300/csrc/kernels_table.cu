@@ -37,7 +37,7 @@ __global__ void predict_kernel(Model md, CompTable src, CompTable ct, const Fram
   const int n = fs->n_comp, nb = fs->nb, frame = fs->frame;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n + nb; c += gridDim.x * blockDim.x) {
     if (c < n) predict_comp<DZ>(md, src, ct, c);
-    else birth_comp(md, ct, c, births + (size_t)(c - n) * 43, c - n, frame);
+    else birth_comp(md, ct, c, births + (size_t)(c - n) * kBirthRec, c - n, frame);
   }
 }
 
