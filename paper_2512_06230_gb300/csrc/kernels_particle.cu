@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) particle_logc_kernel(Model md, PartModel 
   }
 }
 
-// Regeneration: one block per kept component (copied to its compacted
+// Regeneration: one block (64 threads) per kept component (copied to its compacted
 // position) and per distinct (component, detection set) update (written
 // after the kept ones): log w_p -= (m / 2) (zbar - h_p)^T R^-1 (zbar - h_p)
 // (the product of the m detections' likelihoods up to a factor common to
@@ -493,7 +493,9 @@ void launch_particle_remap(const Model& md, const PartModel& pm, const CompTable
                            const unsigned* n_keep_dev, const uint32_t* upd_src, const uint32_t* upd_m,
                            const long long* upd_se, int cap_upd, const unsigned* n_upd_dev,
                            const unsigned* n_surv_dev, unsigned* err, int grid, cudaStream_t s) {
-  launch_k(particle_remap_kernel, grid, kPartThreads, (size_t)pm.np * sizeof(double), s, md, pm, src, dst, newpos,
+  // 64-thread blocks: several updates in flight per SM, each with short
+  // block reductions
+  launch_k(particle_remap_kernel, 4 * grid, 64, (size_t)pm.np * sizeof(double), s, md, pm, src, dst, newpos,
            flag, fs, n_keep_dev, upd_src, upd_m, upd_se, cap_upd, n_upd_dev, n_surv_dev, err);
 }
 
