@@ -303,18 +303,30 @@ __global__ void __launch_bounds__(256) particle_logc_kernel(Model md, PartModel 
     bool any = false;
     for (unsigned k = k0; k < k1; ++k) {
       const float ex = pt.e[k], ey = pt.e[capp + k];
-      float m = -INFINITY, s = 0.f;
+      // the register-held particles' terms are independent: their maximum,
+      // then the sum of their exponentials (no dependent chain through expf)
+      float l[kRegP];
+      float m = -INFINITY;
+#pragma unroll
+      for (int j = 0; j < kRegP; ++j) {
+        const float dx = ex - ox[j], dy = ey - oy[j];
+        l[j] = ow[j] - 0.5f * (r0 * dx * dx + r1 * dx * dy + r3 * dy * dy);
+        m = fmaxf(m, l[j]);
+      }
+      float s = 0.f;
+      if (m > -INFINITY) {
+#pragma unroll
+        for (int j = 0; j < kRegP; ++j) s += expf(l[j] - m);
+      }
       auto push = [&](float dx, float dy, float w) {
-        const float l = w - 0.5f * (r0 * dx * dx + r1 * dx * dy + r3 * dy * dy);
-        if (l > m) {
-          s = s * expf(m - l) + 1.f;
-          m = l;
-        } else if (l > -INFINITY) {
-          s += expf(l - m);
+        const float lv = w - 0.5f * (r0 * dx * dx + r1 * dx * dy + r3 * dy * dy);
+        if (lv > m) {
+          s = s * expf(m - lv) + 1.f;
+          m = lv;
+        } else if (lv > -INFINITY) {
+          s += expf(lv - m);
         }
       };
-#pragma unroll
-      for (int j = 0; j < kRegP; ++j) push(ex - ox[j], ey - oy[j], ow[j]);
       for (int p = lane + 32 * kRegP; p < np; p += 32)
         push(ex - (float)(prow(ct, np, c, 0)[p] - mx), ey - (float)(prow(ct, np, c, 1)[p] - my),
              (float)prow(ct, np, c, 5)[p]);
