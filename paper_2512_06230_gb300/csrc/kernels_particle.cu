@@ -330,14 +330,15 @@ __global__ void __launch_bounds__(256) particle_logc_kernel(Model md, PartModel 
       for (int p = lane + 32 * kRegP; p < np; p += 32)
         push(ex - (float)(prow(ct, np, c, 0)[p] - mx), ey - (float)(prow(ct, np, c, 1)[p] - my),
              (float)prow(ct, np, c, 5)[p]);
+      // the warp's maximum, then each lane's sum rescaled to it once and
+      // added across the warp
+      float mw = m;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float m2 = __shfl_xor_sync(0xFFFFFFFFu, m, o), s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        const float mm = fmaxf(m, m2);
-        s = (m == -INFINITY ? 0.f : s * expf(m - mm)) + (m2 == -INFINITY ? 0.f : s2 * expf(m2 - mm));
-        m = mm;
-      }
-      const float logC = m == -INFINITY ? -INFINITY : lc0 + m + logf(s);
+      for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xFFFFFFFFu, mw, o));
+      float sw = m == -INFINITY ? 0.f : s * expf(m - mw);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+      const float logC = mw == -INFINITY ? -INFINITY : lc0 + mw + logf(sw);
       if (lane == 0) pt.logC[k] = logC;
       any = true;
       if (!md.kappa_zero) lse_push(lm, ls, logC - md.log_kappa);
